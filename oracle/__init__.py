@@ -1,0 +1,336 @@
+"""Double-precision CPU oracle for the TurboGS sparse-sampled path.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` leg of ``bench.py`` may import this
+package.  The CUDA library never imports it, and the two share no code.
+
+The arithmetic lives in ``turbogs_oracle.c`` (plain C, double precision, each
+function citing the passage of TurboGS it restates); this module compiles it
+with gcc on first use and marshals numpy arrays in and out with ctypes.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "turbogs_oracle.c")
+_LIB = os.path.join(_HERE, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+# loss constants (readings of Sec. 3.7 / App. A, shared with the library as values)
+EPS_CHARBONNIER = 1e-3
+EPS_NCC = 1e-8
+BETA_EMA = 0.4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle into ``oracle/liborc.so`` (host architecture)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = C.CDLL(_LIB)
+            _declare(_lib)
+    return _lib
+
+
+_p = C.c_void_p
+_i64 = C.c_int64
+_i32 = C.c_int
+_u64 = C.c_uint64
+_u32 = C.c_uint32
+_d = C.c_double
+
+
+def _declare(L):
+    L.orc_half_to_double.argtypes = [C.c_uint16]
+    L.orc_half_to_double.restype = _d
+    L.orc_double_to_half.argtypes = [_d]
+    L.orc_double_to_half.restype = C.c_uint16
+    L.orc_sh_basis.argtypes = [_p, _p, _p]
+    L.orc_sh_basis.restype = None
+    L.orc_project.argtypes = [_i64, _p, _p, _p, _p, _p, _i32, _p, _i32, _i32, _p, _p, _p, _p, _p, _p, _p, _p]
+    L.orc_project.restype = _i32
+    L.orc_bin_tiles.argtypes = [_i64, _p, _p, _p, _i32, _i32, _p, _i64, _p, _p, _p]
+    L.orc_bin_tiles.restype = _i64
+    L.orc_mix64.argtypes = [_u64]
+    L.orc_mix64.restype = _u64
+    L.orc_hash.argtypes = [_u64, _u64, _u32, _u32, _u32, _u32]
+    L.orc_hash.restype = _u64
+    L.orc_neglog2_q32.argtypes = [_u64]
+    L.orc_neglog2_q32.restype = _u64
+    L.orc_err_weight.argtypes = [C.c_uint16]
+    L.orc_err_weight.restype = _u64
+    L.orc_choose_items.argtypes = [_i32, _p, _p, _i32, _i32, _i32, _u64, _u64, _u32, _u32, _p]
+    L.orc_choose_items.restype = _i32
+    L.orc_select.argtypes = [_i32, _i32, _p, _p, _i32, _i32, _i32, _i32, _i32, _i32, _u64, _u64, _u32,
+                             _p, _p, _p, _p, _p]
+    L.orc_select.restype = _i32
+    L.orc_render_pixels.argtypes = [_i64, _p, _p, _p, _p, _p, _p, _i32, _i32, _p, _i64, _p, _p, _p, _p,
+                                    _p, _p]
+    L.orc_render_pixels.restype = _i32
+    L.orc_render_backward.argtypes = [_i64, _p, _p, _p, _p, _p, _p, _i32, _i32, _p, _i64, _p, _p, _p]
+    L.orc_render_backward.restype = _i32
+    L.orc_project_backward.argtypes = [_i64, _p, _p, _p, _p, _p, _i32, _p, _i32, _i32, _p, _p, _p]
+    L.orc_project_backward.restype = _i32
+    L.orc_loss.argtypes = [_i32, _i32, _i32, _p, _p, _p, _p, _p, _p, _d, _d, _d, _p, _p, _p, _p, _p, _p]
+    L.orc_loss.restype = _i32
+    L.orc_cholesky_solve.argtypes = [_p, _p, _p, _i32]
+    L.orc_cholesky_solve.restype = _i32
+    L.orc_hybrid_step.argtypes = [_i64, _p, _p, _p, _p, _p, _p, _i32, _i32, _i32, _p]
+    L.orc_hybrid_step.restype = _i32
+
+
+def _c(a, dtype):
+    """Contiguous copy/view of ``a`` with ``dtype``; None stays None."""
+    if a is None:
+        return None
+    return np.ascontiguousarray(np.asarray(a), dtype=dtype)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def camera_array(cam) -> np.ndarray:
+    """[viewmat 16 (row-major world->camera), fx, fy, cx, cy, znear] in float64."""
+    v = np.asarray(cam["viewmat"], dtype=np.float64).reshape(16)
+    return np.concatenate([v, np.array([cam["fx"], cam["fy"], cam["cx"], cam["cy"], cam["znear"]],
+                                       dtype=np.float64)])
+
+
+# ----------------------------------------------------------------------------
+# wrappers
+# ----------------------------------------------------------------------------
+
+def half_to_double(h: int) -> float:
+    return lib().orc_half_to_double(int(h))
+
+
+def double_to_half(x: float) -> int:
+    return int(lib().orc_double_to_half(float(x)))
+
+
+def sh_basis(d):
+    """Real SH basis (16) and its polynomial gradient (16, 3) at unit direction d."""
+    d = _c(d, np.float64)
+    Y = np.zeros(16)
+    G = np.zeros(48)
+    lib().orc_sh_basis(_ptr(d), _ptr(Y), _ptr(G))
+    return Y, G.reshape(16, 3)
+
+
+def project(g, cam, sh_degree=3, tile_rank=None):
+    """Project Gaussians (dict of means, log_scales, quats, opacity_logits, sh)."""
+    n = int(np.asarray(g["means"]).shape[0])
+    means = _c(g["means"], np.float64)
+    ls = _c(g["log_scales"], np.float64)
+    q = _c(g["quats"], np.float64)
+    ol = _c(g["opacity_logits"], np.float64)
+    sh = _c(np.asarray(g["sh"]).reshape(n, 48), np.float64)
+    camv = camera_array(cam)
+    tr = _c(tile_rank, np.int32)
+    out = dict(xy=np.zeros((n, 2)), conic=np.zeros((n, 3)), opac=np.zeros(n), rgb=np.zeros((n, 3)),
+               depth=np.zeros(n), radius=np.zeros(n, np.int32), margin=np.zeros(n))
+    lib().orc_project(n, _ptr(means), _ptr(ls), _ptr(q), _ptr(ol), _ptr(sh), int(sh_degree), _ptr(camv),
+                      int(cam["width"]), int(cam["height"]), _ptr(tr), _ptr(out["xy"]), _ptr(out["conic"]),
+                      _ptr(out["opac"]), _ptr(out["rgb"]), _ptr(out["depth"]), _ptr(out["radius"]),
+                      _ptr(out["margin"]))
+    return out
+
+
+def bin_tiles(xy, radius, depth, width, height, tile_rank=None, capacity=None):
+    """Sorted (key, Gaussian id) pairs of every (active tile, Gaussian) overlap."""
+    xy = _c(xy, np.float32)
+    radius = _c(radius, np.int32)
+    depth = _c(depth, np.float32)
+    n = radius.shape[0]
+    tiles = ((width + 15) // 16) * ((height + 15) // 16)
+    tr = _c(tile_rank, np.int32)
+    counts = np.zeros(tiles, np.int32)
+    if capacity is None:
+        dummy = np.zeros(1, np.uint64)
+        capacity = int(lib().orc_bin_tiles(n, _ptr(xy), _ptr(radius), _ptr(depth), width, height, _ptr(tr), -1,
+                                           _ptr(dummy), _ptr(dummy), _ptr(counts)))
+    keys = np.zeros(max(capacity, 1), np.uint64)
+    vals = np.zeros(max(capacity, 1), np.int32)
+    total = lib().orc_bin_tiles(n, _ptr(xy), _ptr(radius), _ptr(depth), width, height, _ptr(tr), capacity,
+                                _ptr(keys), _ptr(vals), _ptr(counts))
+    if total < 0:
+        return None
+    return keys[:total], vals[:total], counts
+
+
+def mix64(z: int) -> int:
+    return int(lib().orc_mix64(z & (2**64 - 1)))
+
+
+def hash_(seed, it, view, stream, tile, item) -> int:
+    return int(lib().orc_hash(seed, it, view, stream, tile, item))
+
+
+def neglog2_q32(h: int) -> int:
+    return int(lib().orc_neglog2_q32(h & (2**64 - 1)))
+
+
+def err_weight(h: int) -> int:
+    return int(lib().orc_err_weight(int(h)))
+
+
+def choose_items(w, age, n, hard_pm=400, stable_pm=300, seed=0, it=0, view=0, tile=0):
+    w = _c(w, np.uint64)
+    age = _c(age, np.uint32)
+    cnt = w.shape[0]
+    out = np.zeros(cnt, np.uint8)
+    lib().orc_choose_items(cnt, _ptr(w), _ptr(age), int(n), hard_pm, stable_pm, seed, it, view, tile, _ptr(out))
+    return out.astype(bool)
+
+
+def select(err_f16_bits, age, width, height, n_select, n_pix, tile_hard_pm=400, tile_stable_pm=300,
+           pix_hard_pm=400, pix_stable_pm=300, seed=0, it=0, view=0):
+    err = _c(err_f16_bits, np.uint16)
+    age = _c(age, np.uint16)
+    tiles = ((width + 15) // 16) * ((height + 15) // 16)
+    active = np.zeros(tiles, np.int32)
+    n_active = np.zeros(1, np.int32)
+    rank = np.zeros(tiles, np.int32)
+    off = np.zeros(tiles + 1, np.int32)
+    idx = np.zeros(tiles * 256, np.uint8)
+    lib().orc_select(width, height, _ptr(err), _ptr(age), int(n_select), int(n_pix), tile_hard_pm,
+                     tile_stable_pm, pix_hard_pm, pix_stable_pm, seed, it, view, _ptr(active), _ptr(n_active),
+                     _ptr(rank), _ptr(off), _ptr(idx))
+    A = int(n_active[0])
+    return dict(active_tiles=active[:A], n_active=A, tile_rank=rank, pix_off=off[:A + 1],
+                pix_idx=idx[:off[A]])
+
+
+def pixel_coords(active_tiles, pix_off, pix_idx, width):
+    """Integer pixel coordinates [P,2] of a sampled set (tile order)."""
+    tx_n = (width + 15) // 16
+    counts = np.diff(np.asarray(pix_off))
+    tiles = np.repeat(np.asarray(active_tiles), counts)
+    l = np.asarray(pix_idx).astype(np.int32)
+    x = (tiles % tx_n) * 16 + (l % 16)
+    y = (tiles // tx_n) * 16 + (l // 16)
+    return np.stack([x, y], 1).astype(np.int32)
+
+
+def render_pixels(proj, width, height, pix_xy, bg=(0.0, 0.0, 0.0)):
+    xy = _c(proj["xy"], np.float64)
+    conic = _c(proj["conic"], np.float64)
+    opac = _c(proj["opac"], np.float64)
+    rgb = _c(proj["rgb"], np.float64)
+    depth = _c(proj["depth"], np.float64)
+    radius = _c(proj["radius"], np.int32)
+    n = radius.shape[0]
+    pix = _c(pix_xy, np.int32).reshape(-1, 2)
+    P = pix.shape[0]
+    bgv = _c(bg, np.float64)
+    out = dict(rgb=np.zeros((P, 3)), T=np.zeros(P), n_last=np.zeros(P, np.int32),
+               n_contrib=np.zeros(P, np.int32), margin=np.zeros(P))
+    lib().orc_render_pixels(n, _ptr(xy), _ptr(conic), _ptr(opac), _ptr(rgb), _ptr(depth), _ptr(radius),
+                            width, height, _ptr(bgv), P, _ptr(pix), _ptr(out["rgb"]), _ptr(out["T"]),
+                            _ptr(out["n_last"]), _ptr(out["n_contrib"]), _ptr(out["margin"]))
+    return out
+
+
+def render_backward(proj, width, height, pix_xy, dL_drgb, bg=(0.0, 0.0, 0.0)):
+    """grad2d [N,9] = (dx, dy, da, db, dc, dopacity, dr, dg, db)."""
+    xy = _c(proj["xy"], np.float64)
+    conic = _c(proj["conic"], np.float64)
+    opac = _c(proj["opac"], np.float64)
+    rgb = _c(proj["rgb"], np.float64)
+    depth = _c(proj["depth"], np.float64)
+    radius = _c(proj["radius"], np.int32)
+    n = radius.shape[0]
+    pix = _c(pix_xy, np.int32).reshape(-1, 2)
+    g = _c(dL_drgb, np.float64).reshape(-1, 3)
+    bgv = _c(bg, np.float64)
+    out = np.zeros((n, 9))
+    lib().orc_render_backward(n, _ptr(xy), _ptr(conic), _ptr(opac), _ptr(rgb), _ptr(depth), _ptr(radius),
+                              width, height, _ptr(bgv), pix.shape[0], _ptr(pix), _ptr(g), _ptr(out))
+    return out
+
+
+def project_backward(g, cam, grad2d, sh_degree=3, tile_rank=None):
+    """grads [N,59] = (means 3, log_scales 3, quats 4, opacity logit 1, sh 48)."""
+    n = int(np.asarray(g["means"]).shape[0])
+    means = _c(g["means"], np.float64)
+    ls = _c(g["log_scales"], np.float64)
+    q = _c(g["quats"], np.float64)
+    ol = _c(g["opacity_logits"], np.float64)
+    sh = _c(np.asarray(g["sh"]).reshape(n, 48), np.float64)
+    camv = camera_array(cam)
+    tr = _c(tile_rank, np.int32)
+    g2 = _c(grad2d, np.float64)
+    out = np.zeros((n, 59))
+    lib().orc_project_backward(n, _ptr(means), _ptr(ls), _ptr(q), _ptr(ol), _ptr(sh), int(sh_degree),
+                               _ptr(camv), int(cam["width"]), int(cam["height"]), _ptr(tr), _ptr(g2), _ptr(out))
+    return out
+
+
+def loss(width, height, sel, rgb, target, err_f16_bits=None, age=None, lambda_in=None,
+         eps_c=EPS_CHARBONNIER, eps_n=EPS_NCC, beta=BETA_EMA):
+    """Fused sparse loss.  Returns dict; error/age maps are updated copies."""
+    active = _c(sel["active_tiles"], np.int32)
+    off = _c(sel["pix_off"], np.int32)
+    idx = _c(sel["pix_idx"], np.uint8)
+    A = int(active.shape[0])
+    P = int(off[A])
+    rgb = _c(rgb, np.float64).reshape(-1, 3)
+    tgt = _c(target, np.float64)
+    err = None if err_f16_bits is None else np.array(err_f16_bits, dtype=np.uint16, copy=True)
+    ag = None if age is None else np.array(age, dtype=np.uint16, copy=True)
+    lam_in = _c(lambda_in, np.float64)
+    out = dict(dL_drgb=np.zeros((P, 3)), lam=np.zeros(max(A, 1)), err=np.zeros(max(P, 1)),
+               loss=np.zeros(1))
+    lib().orc_loss(width, height, A, _ptr(active), _ptr(off), _ptr(idx if idx.size else np.zeros(1, np.uint8)),
+                   _ptr(rgb), _ptr(tgt), _ptr(lam_in), eps_c, eps_n, beta, _ptr(err), _ptr(ag),
+                   _ptr(out["dL_drgb"]), _ptr(out["lam"]), _ptr(out["err"]), _ptr(out["loss"]))
+    out["lam"] = out["lam"][:A]
+    out["err"] = out["err"][:P]
+    out["loss"] = float(out["loss"][0])
+    out["err_map"] = err
+    out["age_map"] = ag
+    return out
+
+
+def cholesky_solve(A, b):
+    A = _c(A, np.float64)
+    b = _c(b, np.float64)
+    x = np.zeros_like(b)
+    rc = lib().orc_cholesky_solve(_ptr(A), _ptr(b), _ptr(x), b.shape[0])
+    if rc != 0:
+        raise np.linalg.LinAlgError("not positive definite")
+    return x
+
+
+def hybrid_step(params, grads, m, v, touched, step, mode, cfg, rows=None):
+    """One hybrid step on packed [N,59] rows (copies in, updated copies out)."""
+    p = np.array(params, dtype=np.float64, copy=True)
+    mm = np.array(m, dtype=np.float64, copy=True)
+    vv = np.array(v, dtype=np.float64, copy=True)
+    g = _c(grads, np.float64)
+    t = _c(touched, np.uint8)
+    r = _c(rows, np.float64)
+    k = 0 if rows is None else int(np.asarray(rows).shape[0])
+    c = _c(cfg, np.float64)
+    lib().orc_hybrid_step(p.shape[0], _ptr(p), _ptr(g), _ptr(mm), _ptr(vv), _ptr(t), _ptr(r), k, int(step),
+                          int(mode), _ptr(c))
+    return p, mm, vv

@@ -1,0 +1,1157 @@
+/*
+ * TurboGS double-precision CPU oracle.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference leg of bench.py may load or call this code.  The
+ * CUDA library never does, and the two share no source, header, table or
+ * constant generator: the spherical-harmonic constants below are computed from
+ * their normalisation formula, the random stream from the published SplitMix64
+ * finaliser.
+ *
+ * Every function restates, in plain double-precision C, what one step of the
+ * TurboGS training iteration computes (TurboGS, ICML 2026: Sec. 3.1 Eq. 1 for
+ * compositing, Sec. 3.3-3.5 for error/age maps and sampling, Sec. 3.7 and
+ * App. A for the loss and its gradients, Sec. 3.9 and App. A for the hybrid
+ * solver).  The projection follows the 3D Gaussian Splatting model the paper
+ * builds on (Sec. 3.1: centre, covariance from scale and rotation, opacity,
+ * SH colour, "standard 3DGS training loop").  No blocking, fusion or reordering
+ * beyond what those definitions state: each sampled pixel is rendered on its own
+ * from the full Gaussian set, each tile's loss from its own pixel list.
+ *
+ * Where a floating-point comparison decides an integer the paper leaves the
+ * precision open; the oracle then decides in single precision, the precision
+ * of the kernels (tile membership of a splat: rect_axis below).  Everything
+ * else is double precision.
+ *
+ * Pins (tests/test_oracle_*.py, run with -m "not gpu"): SH basis against
+ * scipy's spherical harmonics; closed-form image of one isotropic Gaussian;
+ * transmittance identity; pixel independence; brute-force tile overlap;
+ * sampling counts, brute-force TopK, inclusion probabilities of the weighted
+ * draw against exact enumeration of sequential draws; NCC invariances and
+ * finite differences of the loss; finite differences of the whole
+ * project -> render -> loss chain against the analytic backward; Cholesky
+ * against LU, Sherman-Morrison and J = 0 for the hybrid step; fp16 rounding
+ * against numpy.  Parity status: pinned (no function here is unpinned).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_TILE 16
+#define ORC_NSH 16
+
+/* ------------------------------------------------------------------------ */
+/* small helpers                                                            */
+/* ------------------------------------------------------------------------ */
+
+static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+/* C = A (m x k) * B (k x n), row-major */
+static void matmul(const double* A, const double* B, double* C, int m, int k, int n) {
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < k; ++l) s += A[i * k + l] * B[l * n + j];
+      C[i * n + j] = s;
+    }
+}
+
+static void transpose(const double* A, double* At, int m, int n) {
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < n; ++j) At[j * m + i] = A[i * n + j];
+}
+
+/* Rotation matrix of the unit quaternion q = (w, x, y, z). */
+static void quat_to_rot(const double q[4], double R[9]) {
+  double w = q[0], x = q[1], y = q[2], z = q[3];
+  R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+  R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+  R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* ------------------------------------------------------------------------ */
+/* fp16 <-> double (IEEE 754 binary16, round to nearest even)               */
+/* ------------------------------------------------------------------------ */
+
+double orc_half_to_double(uint16_t h) {
+  int s = (h >> 15) & 1, e = (h >> 10) & 31, m = h & 1023;
+  double v;
+  if (e == 0) v = ldexp((double)m, -24);
+  else if (e == 31) v = m ? NAN : INFINITY;
+  else v = ldexp((double)(1024 + m), e - 25);
+  return s ? -v : v;
+}
+
+uint16_t orc_double_to_half(double x) {
+  uint16_t s = signbit(x) ? 0x8000 : 0;
+  double a = fabs(x);
+  if (isnan(x)) return 0x7e00;
+  if (a < ldexp(1.0, -14)) {                 /* subnormal range: units of 2^-24 */
+    double q = rint(a * 16777216.0);         /* exact scaling, RNE */
+    return (uint16_t)(s | (uint16_t)q);      /* q == 1024 encodes the smallest normal */
+  }
+  int E;
+  double f = frexp(a, &E);                   /* a = f * 2^E, f in [0.5, 1) */
+  int e = E - 1;                             /* a = (2f) * 2^e */
+  double m = rint(2.0 * f * 1024.0);         /* in [1024, 2048] */
+  if (m >= 2048.0) { m = 1024.0; e += 1; }
+  if (e > 15) return (uint16_t)(s | 0x7c00);
+  return (uint16_t)(s | (uint16_t)((e + 15) << 10) | (uint16_t)(m - 1024.0));
+}
+
+/* ------------------------------------------------------------------------ */
+/* real spherical harmonics, degree <= 3                                    */
+/* ------------------------------------------------------------------------ */
+
+/* K_l^m = sqrt((2l+1)/(4 pi) * (l-m)!/(l+m)!) */
+static double sh_norm(int l, int m) {
+  double num = 1.0, den = 1.0;
+  for (int k = 2; k <= l - m; ++k) num *= k;
+  for (int k = 2; k <= l + m; ++k) den *= k;
+  return sqrt((2.0 * l + 1.0) / (4.0 * M_PI) * num / den);
+}
+
+/*
+ * Real SH Y_{l,m} (m = -l..l, index l*l+l+m) of a unit direction d, with the
+ * Condon-Shortley phase in the associated Legendre functions:
+ *   m > 0: sqrt2 K_l^m cos(m phi) P_l^m(cos theta)
+ *   m = 0: K_l^0 P_l^0(cos theta)
+ *   m < 0: sqrt2 K_l^|m| sin(|m| phi) P_l^|m|(cos theta)
+ * written out as polynomials of (x, y, z) on the unit sphere, using
+ * P_1^1 = -sin, P_2^1 = -3 cos sin, P_2^2 = 3 sin^2, P_3^1 = -3/2 (5cos^2-1) sin,
+ * P_3^2 = 15 cos sin^2, P_3^3 = -15 sin^3 and x = sin cos(phi), y = sin sin(phi).
+ * grad (optional, [16][3]) receives the gradient of each polynomial.
+ */
+void orc_sh_basis(const double d[3], double Y[16], double grad[48]) {
+  const double r2 = sqrt(2.0);
+  double x = d[0], y = d[1], z = d[2];
+  double c0 = sh_norm(0, 0);
+  double c1 = r2 * sh_norm(1, 1), c10 = sh_norm(1, 0);
+  double c22 = r2 * sh_norm(2, 2), c21 = r2 * sh_norm(2, 1), c20 = sh_norm(2, 0);
+  double c33 = r2 * sh_norm(3, 3), c32 = r2 * sh_norm(3, 2), c31 = r2 * sh_norm(3, 1), c30 = sh_norm(3, 0);
+  /* polynomial coefficients */
+  double k1 = -c1, k2 = c10, k3 = -c1;
+  double k4 = 6 * c22, k5 = -3 * c21, k6 = 0.5 * c20, k7 = -3 * c21, k8 = 3 * c22;
+  double k9 = -15 * c33, k10 = 30 * c32, k11 = -1.5 * c31, k12 = 0.5 * c30, k13 = -1.5 * c31,
+         k14 = 15 * c32, k15 = -15 * c33;
+  Y[0] = c0;
+  Y[1] = k1 * y;
+  Y[2] = k2 * z;
+  Y[3] = k3 * x;
+  Y[4] = k4 * x * y;
+  Y[5] = k5 * y * z;
+  Y[6] = k6 * (2 * z * z - x * x - y * y);
+  Y[7] = k7 * x * z;
+  Y[8] = k8 * (x * x - y * y);
+  Y[9] = k9 * y * (3 * x * x - y * y);
+  Y[10] = k10 * x * y * z;
+  Y[11] = k11 * y * (4 * z * z - x * x - y * y);
+  Y[12] = k12 * z * (2 * z * z - 3 * x * x - 3 * y * y);
+  Y[13] = k13 * x * (4 * z * z - x * x - y * y);
+  Y[14] = k14 * z * (x * x - y * y);
+  Y[15] = k15 * x * (x * x - 3 * y * y);
+  if (!grad) return;
+  double* g = grad;
+#define G(i, a, b, c) do { g[3 * (i)] = (a); g[3 * (i) + 1] = (b); g[3 * (i) + 2] = (c); } while (0)
+  G(0, 0, 0, 0);
+  G(1, 0, k1, 0);
+  G(2, 0, 0, k2);
+  G(3, k3, 0, 0);
+  G(4, k4 * y, k4 * x, 0);
+  G(5, 0, k5 * z, k5 * y);
+  G(6, -2 * k6 * x, -2 * k6 * y, 4 * k6 * z);
+  G(7, k7 * z, 0, k7 * x);
+  G(8, 2 * k8 * x, -2 * k8 * y, 0);
+  G(9, 6 * k9 * x * y, k9 * (3 * x * x - 3 * y * y), 0);
+  G(10, k10 * y * z, k10 * x * z, k10 * x * y);
+  G(11, -2 * k11 * x * y, k11 * (4 * z * z - x * x - 3 * y * y), 8 * k11 * y * z);
+  G(12, -6 * k12 * x * z, -6 * k12 * y * z, k12 * (6 * z * z - 3 * x * x - 3 * y * y));
+  G(13, k13 * (4 * z * z - 3 * x * x - y * y), -2 * k13 * x * y, 8 * k13 * x * z);
+  G(14, 2 * k14 * x * z, -2 * k14 * y * z, k14 * (x * x - y * y));
+  G(15, k15 * (3 * x * x - 3 * y * y), -6 * k15 * x * y, 0);
+#undef G
+}
+
+/* ------------------------------------------------------------------------ */
+/* camera                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* cam = [viewmat (16, row-major world->camera; x right, y down, z forward),
+ *        fx, fy, cx, cy, znear] */
+typedef struct {
+  double W[9], t[3], fx, fy, cx, cy, znear, campos[3];
+  int width, height, tiles_x, tiles_y;
+} cam_t;
+
+static void cam_load(const double* c, int width, int height, cam_t* o) {
+  for (int r = 0; r < 3; ++r) {
+    for (int k = 0; k < 3; ++k) o->W[r * 3 + k] = c[r * 4 + k];
+    o->t[r] = c[r * 4 + 3];
+  }
+  o->fx = c[16]; o->fy = c[17]; o->cx = c[18]; o->cy = c[19]; o->znear = c[20];
+  o->width = width; o->height = height;
+  o->tiles_x = (width + ORC_TILE - 1) / ORC_TILE;
+  o->tiles_y = (height + ORC_TILE - 1) / ORC_TILE;
+  for (int k = 0; k < 3; ++k)
+    o->campos[k] = -(o->W[0 * 3 + k] * o->t[0] + o->W[1 * 3 + k] * o->t[1] + o->W[2 * 3 + k] * o->t[2]);
+}
+
+/*
+ * Tiles [lo, hi) on one axis covered by the square [c - r, c + r]: tile k
+ * (pixels [16k, 16k+16)) is covered when 16k <= c + r and 16(k+1) > c - r.
+ * Decided in single precision (see file header).
+ */
+static void rect_axis(double c, int r, int ntiles, int* lo, int* hi) {
+  float cf = (float)c, rf = (float)r;
+  float a = floorf((cf - rf) * 0.0625f);
+  float b = floorf((cf + rf) * 0.0625f) + 1.0f;
+  a = fminf(fmaxf(a, 0.0f), (float)ntiles);
+  b = fminf(fmaxf(b, 0.0f), (float)ntiles);
+  *lo = (int)a;
+  *hi = (int)b;
+}
+
+/* distance of the single-precision rect decision to its switching points,
+ * relative to the coordinate magnitude (diagnostic for parity tests) */
+static double rect_margin(double c, int r) {
+  double a = (c - r) / 16.0, b = (c + r) / 16.0;
+  double da = fabs(a - floor(a + 0.5)), db = fabs(b - floor(b + 0.5));
+  double m = (da < db ? da : db) * 16.0;
+  return m / (fabs(c) + r + 1.0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* projection (3DGS forward model: EWA splatting + SH colour)               */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int visible;
+  double q[4], qnorm, R[9], s[3], Sigma[9];
+  double pc[3];
+  int clampx, clampy;
+  double J[6], T[6];
+  double A, B, C;           /* 2D covariance incl. +0.3 dilation */
+  double det, conic[3];
+  double lam, radius_f;
+  int radius;
+  double xy[2];
+  double v[3], vlen, dir[3];
+  double rgb_pre[3], rgb[3];
+  double opac;
+  double margin;
+} gproj_t;
+
+static double minabs(double a, double b) { return a < b ? a : b; }
+
+/*
+ * One Gaussian.  means (3), log_scales (3), quat (4, w x y z, unnormalised),
+ * opacity logit, sh [16][3].  tile_rank (nullable): [tiles] >= 0 where a tile is
+ * active; a Gaussian covering no active tile is culled.
+ */
+static void project_one(const double* mu, const double* ls, const double* qr, double ol, const double* sh,
+                        int sh_degree, const cam_t* cam, const int32_t* tile_rank, gproj_t* g) {
+  memset(g, 0, sizeof(*g));
+  g->margin = INFINITY;
+  /* camera space */
+  for (int r = 0; r < 3; ++r)
+    g->pc[r] = cam->W[r * 3 + 0] * mu[0] + cam->W[r * 3 + 1] * mu[1] + cam->W[r * 3 + 2] * mu[2] + cam->t[r];
+  double z = g->pc[2];
+  g->margin = minabs(g->margin, fabs(z - cam->znear) / cam->znear);
+  if (!(z > cam->znear)) return;
+  /* 3D covariance Sigma = R S S^T R^T */
+  g->qnorm = sqrt(qr[0] * qr[0] + qr[1] * qr[1] + qr[2] * qr[2] + qr[3] * qr[3]);
+  for (int k = 0; k < 4; ++k) g->q[k] = qr[k] / g->qnorm;
+  quat_to_rot(g->q, g->R);
+  for (int k = 0; k < 3; ++k) g->s[k] = exp(ls[k]);
+  double M[9], Mt[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) M[r * 3 + c] = g->R[r * 3 + c] * g->s[c];
+  transpose(M, Mt, 3, 3);
+  matmul(M, Mt, g->Sigma, 3, 3, 3);
+  /* local affine approximation of the perspective map (EWA) */
+  double limx = 1.3 * (0.5 * cam->width / cam->fx), limy = 1.3 * (0.5 * cam->height / cam->fy);
+  double xz = g->pc[0] / z, yz = g->pc[1] / z;
+  g->clampx = (xz < -limx || xz > limx);
+  g->clampy = (yz < -limy || yz > limy);
+  double txz = clampd(xz, -limx, limx), tyz = clampd(yz, -limy, limy);
+  g->J[0] = cam->fx / z; g->J[1] = 0.0; g->J[2] = -cam->fx * txz / z;
+  g->J[3] = 0.0; g->J[4] = cam->fy / z; g->J[5] = -cam->fy * tyz / z;
+  matmul(g->J, cam->W, g->T, 2, 3, 3);
+  double TS[6], Tt[6], S2[4];
+  matmul(g->T, g->Sigma, TS, 2, 3, 3);
+  transpose(g->T, Tt, 2, 3);
+  matmul(TS, Tt, S2, 2, 3, 2);
+  g->A = S2[0] + 0.3; g->B = S2[1]; g->C = S2[3] + 0.3;
+  g->det = g->A * g->C - g->B * g->B;
+  g->margin = minabs(g->margin, fabs(g->det) / (g->A * g->C));
+  if (!(g->det > 0.0)) return;
+  g->conic[0] = g->C / g->det; g->conic[1] = -g->B / g->det; g->conic[2] = g->A / g->det;
+  double mid = 0.5 * (g->A + g->C);
+  double disc = mid * mid - g->det;
+  g->lam = mid + sqrt(disc > 0.1 ? disc : 0.1);
+  g->radius_f = 3.0 * sqrt(g->lam);
+  g->radius = (int)ceil(g->radius_f);
+  g->margin = minabs(g->margin, fabs(g->radius_f - floor(g->radius_f + 0.5)) / (g->radius_f + 1.0));
+  g->xy[0] = cam->fx * g->pc[0] / z + cam->cx;
+  g->xy[1] = cam->fy * g->pc[1] / z + cam->cy;
+  /* tile rectangle (single-precision decision) and active-tile culling */
+  int x0, x1, y0, y1;
+  rect_axis(g->xy[0], g->radius, cam->tiles_x, &x0, &x1);
+  rect_axis(g->xy[1], g->radius, cam->tiles_y, &y0, &y1);
+  g->margin = minabs(g->margin, rect_margin(g->xy[0], g->radius));
+  g->margin = minabs(g->margin, rect_margin(g->xy[1], g->radius));
+  if ((x1 - x0) * (y1 - y0) == 0) { g->radius = 0; return; }
+  if (tile_rank) {
+    int any = 0;
+    for (int ty = y0; ty < y1 && !any; ++ty)
+      for (int tx = x0; tx < x1; ++tx)
+        if (tile_rank[ty * cam->tiles_x + tx] >= 0) { any = 1; break; }
+    if (!any) { g->radius = 0; return; }
+  }
+  g->visible = 1;
+  /* colour: SH evaluated in the direction from the camera centre */
+  for (int k = 0; k < 3; ++k) g->v[k] = mu[k] - cam->campos[k];
+  g->vlen = sqrt(g->v[0] * g->v[0] + g->v[1] * g->v[1] + g->v[2] * g->v[2]);
+  for (int k = 0; k < 3; ++k) g->dir[k] = g->v[k] / g->vlen;
+  double Y[16];
+  orc_sh_basis(g->dir, Y, NULL);
+  int nb = (sh_degree + 1) * (sh_degree + 1);
+  for (int c = 0; c < 3; ++c) {
+    double s = 0.5;
+    for (int k = 0; k < nb; ++k) s += sh[k * 3 + c] * Y[k];
+    g->rgb_pre[c] = s;
+    g->rgb[c] = s > 0.0 ? s : 0.0;
+    g->margin = minabs(g->margin, fabs(s));
+  }
+  g->opac = 1.0 / (1.0 + exp(-ol));
+}
+
+/*
+ * Project N Gaussians.  Outputs (culled Gaussians get radius 0 and zeros):
+ * xy [N,2] pixel coordinates of the centre (pixel i covers [i, i+1)),
+ * conic [N,3] = (a, b, c) of the inverse 2D covariance [[a, b], [b, c]],
+ * opac [N], rgb [N,3], depth [N] = camera-space z, radius [N],
+ * margin [N] = smallest relative distance of a discrete decision to its
+ * threshold (diagnostic, nullable).
+ */
+int orc_project(int64_t n, const double* means, const double* log_scales, const double* quats,
+                const double* opacity_logits, const double* sh, int sh_degree, const double* cam_in,
+                int width, int height, const int32_t* tile_rank, double* xy, double* conic, double* opac,
+                double* rgb, double* depth, int32_t* radius, double* margin) {
+  cam_t cam;
+  cam_load(cam_in, width, height, &cam);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    gproj_t g;
+    project_one(means + 3 * i, log_scales + 3 * i, quats + 4 * i, opacity_logits[i], sh + 48 * i, sh_degree,
+                &cam, tile_rank, &g);
+    int vis = g.visible;
+    xy[2 * i] = vis ? g.xy[0] : 0.0;
+    xy[2 * i + 1] = vis ? g.xy[1] : 0.0;
+    for (int k = 0; k < 3; ++k) {
+      conic[3 * i + k] = vis ? g.conic[k] : 0.0;
+      rgb[3 * i + k] = vis ? g.rgb[k] : 0.0;
+    }
+    opac[i] = vis ? g.opac : 0.0;
+    depth[i] = vis ? g.pc[2] : 0.0;
+    radius[i] = vis ? g.radius : 0;
+    if (margin) margin[i] = g.margin;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* tile binning (brute force)                                               */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { uint64_t key; int32_t id; } isect_t;
+
+static int cmp_isect(const void* a, const void* b) {
+  const isect_t* x = (const isect_t*)a;
+  const isect_t* y = (const isect_t*)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  return x->id < y->id ? -1 : (x->id > y->id);
+}
+
+static uint32_t f32_bits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+
+/*
+ * Every (active tile, Gaussian) pair whose rectangle covers the tile, ordered
+ * by (tile id, depth, Gaussian id): the per-tile lists K sorted by depth
+ * (Sec. 3.1).  Inputs are single precision as the library stores them.
+ * keys[i] = tile_id << 32 | float bits of depth (depth > 0 orders as an
+ * unsigned integer), vals[i] = Gaussian id, counts [tiles] per tile.
+ * Returns the number of pairs (capacity < 0: size query only), or -1 if it
+ * exceeds capacity.
+ */
+int64_t orc_bin_tiles(int64_t n, const float* xy, const int32_t* radius, const float* depth, int width,
+                      int height, const int32_t* tile_rank, int64_t capacity, uint64_t* keys, int32_t* vals,
+                      int32_t* counts) {
+  int tx_n = (width + ORC_TILE - 1) / ORC_TILE, ty_n = (height + ORC_TILE - 1) / ORC_TILE;
+  int64_t total = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (radius[i] <= 0) continue;
+    int x0, x1, y0, y1;
+    rect_axis(xy[2 * i], radius[i], tx_n, &x0, &x1);
+    rect_axis(xy[2 * i + 1], radius[i], ty_n, &y0, &y1);
+    for (int ty = y0; ty < y1; ++ty)
+      for (int tx = x0; tx < x1; ++tx)
+        if (!tile_rank || tile_rank[ty * tx_n + tx] >= 0) total++;
+  }
+  for (int t = 0; t < tx_n * ty_n; ++t) counts[t] = 0;
+  if (capacity < 0) return total;          /* size query */
+  if (total > capacity) return -1;
+  isect_t* all = (isect_t*)malloc(sizeof(isect_t) * (size_t)(total > 0 ? total : 1));
+  int64_t k = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (radius[i] <= 0) continue;
+    int x0, x1, y0, y1;
+    rect_axis(xy[2 * i], radius[i], tx_n, &x0, &x1);
+    rect_axis(xy[2 * i + 1], radius[i], ty_n, &y0, &y1);
+    for (int ty = y0; ty < y1; ++ty)
+      for (int tx = x0; tx < x1; ++tx) {
+        int t = ty * tx_n + tx;
+        if (tile_rank && tile_rank[t] < 0) continue;
+        all[k].key = ((uint64_t)t << 32) | f32_bits(depth[i]);
+        all[k].id = (int32_t)i;
+        counts[t]++;
+        k++;
+      }
+  }
+  qsort(all, (size_t)total, sizeof(isect_t), cmp_isect);
+  for (int64_t j = 0; j < total; ++j) { keys[j] = all[j].key; vals[j] = all[j].id; }
+  free(all);
+  return total;
+}
+
+/* ------------------------------------------------------------------------ */
+/* counter-based random stream and the weighted draw without replacement    */
+/* ------------------------------------------------------------------------ */
+
+/* SplitMix64 output function (Steele, Lea, Flood 2014). */
+uint64_t orc_mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+/* hash of (seed, iteration, view, stream, tile, item) */
+uint64_t orc_hash(uint64_t seed, uint64_t iter, uint32_t view, uint32_t stream, uint32_t tile, uint32_t item) {
+  uint64_t h = orc_mix64(seed + 0x9E3779B97F4A7C15ULL);
+  h = orc_mix64(h ^ iter);
+  h = orc_mix64(h ^ (((uint64_t)view << 8) | stream));
+  h = orc_mix64(h ^ (((uint64_t)tile << 16) | item));
+  return h;
+}
+
+/*
+ * -log2(u / 2^64) in fixed point with 32 fractional bits, for u = h | 1,
+ * by the binary-logarithm digit recurrence: normalise the mantissa to [1, 2),
+ * square it, and read one fractional bit per squaring (value >= 2).
+ * Integer-only, so both implementations agree bit for bit.
+ */
+uint64_t orc_neglog2_q32(uint64_t h) {
+  uint64_t u = h | 1ULL;
+  int lz = 0;
+  while (!((u << lz) & 0x8000000000000000ULL)) lz++;
+  int ip = 63 - lz;
+  uint64_t m = u << lz;
+  uint64_t frac = 0;
+  for (int i = 0; i < 32; ++i) {
+    unsigned __int128 sq = (unsigned __int128)m * m;
+    uint64_t hi = (uint64_t)(sq >> 64);
+    frac <<= 1;
+    if (hi & 0x8000000000000000ULL) { frac |= 1; m = hi; }
+    else m = hi << 1;
+  }
+  return ((uint64_t)(64 - ip) << 32) - frac;
+}
+
+/* integer weight of an fp16 error value: E * 2^24 exactly (0 for negative,
+ * NaN or infinity) */
+uint64_t orc_err_weight(uint16_t h) {
+  if (h & 0x8000) return 0;
+  int e = (h >> 10) & 31, m = h & 1023;
+  if (e == 31) return 0;
+  if (e == 0) return (uint64_t)m;
+  return (uint64_t)(1024 + m) << (e - 1);
+}
+
+typedef struct {
+  int idx;
+  uint64_t w;      /* weight for the error-proportional draw */
+  uint64_t L;      /* exponential clock -log2(U), fixed point */
+  uint32_t age;
+  uint64_t u;      /* uniform key */
+  int taken;
+} item_t;
+
+/*
+ * Order of the error-proportional draw without replacement
+ * (Efraimidis-Spirakis: ascending L_i / w_i is the order of successive
+ * weighted draws).  Items of weight 0 follow all positive weights, in uniform
+ * random order (ascending L); ties by index.
+ */
+static int cmp_hard(const void* a, const void* b) {
+  const item_t* x = (const item_t*)a;
+  const item_t* y = (const item_t*)b;
+  int xz = x->w == 0, yz = y->w == 0;
+  if (xz != yz) return xz - yz;
+  if (!xz) {
+    unsigned __int128 l = (unsigned __int128)x->L * y->w, r = (unsigned __int128)y->L * x->w;
+    if (l != r) return l < r ? -1 : 1;
+  } else if (x->L != y->L) return x->L < y->L ? -1 : 1;
+  return x->idx - y->idx;
+}
+static int cmp_age(const void* a, const void* b) {   /* descending age, ties by index */
+  const item_t* x = (const item_t*)a;
+  const item_t* y = (const item_t*)b;
+  if (x->age != y->age) return x->age > y->age ? -1 : 1;
+  return x->idx - y->idx;
+}
+static int cmp_unif(const void* a, const void* b) {  /* ascending uniform key */
+  const item_t* x = (const item_t*)a;
+  const item_t* y = (const item_t*)b;
+  if (x->u != y->u) return x->u < y->u ? -1 : 1;
+  return x->idx - y->idx;
+}
+static int cmp_idx(const void* a, const void* b) {
+  return ((const item_t*)a)->idx - ((const item_t*)b)->idx;
+}
+
+/* split of n draws: hard = round(r_hard n), stable = round(r_stable n) clamped
+ * so hard + stable <= n, rest = n - hard - stable (ratios in 1/1000) */
+static void split_counts(int n, int hard_pm, int stable_pm, int* kh, int* ks, int* kr) {
+  int h = (hard_pm * n + 500) / 1000;
+  if (h > n) h = n;
+  int s = (stable_pm * n + 500) / 1000;
+  if (s > n - h) s = n - h;
+  *kh = h; *ks = s; *kr = n - h - s;
+}
+
+/*
+ * Choose n of the items: kh by the error-proportional draw without
+ * replacement, then ks of the rest with the largest age (TopK), then the
+ * remainder uniformly without replacement.  Marks taken = 1 on the chosen.
+ */
+static void choose(item_t* it, int cnt, int n, int hard_pm, int stable_pm) {
+  int kh, ks, kr;
+  if (n > cnt) n = cnt;
+  split_counts(n, hard_pm, stable_pm, &kh, &ks, &kr);
+  item_t* tmp = (item_t*)malloc(sizeof(item_t) * (size_t)(cnt > 0 ? cnt : 1));
+  int m = 0;
+  for (int i = 0; i < cnt; ++i) tmp[m++] = it[i];
+  qsort(tmp, (size_t)m, sizeof(item_t), cmp_hard);
+  for (int i = 0; i < kh; ++i) it[tmp[i].idx].taken = 1;
+  m = 0;
+  for (int i = 0; i < cnt; ++i) if (!it[i].taken) tmp[m++] = it[i];
+  qsort(tmp, (size_t)m, sizeof(item_t), cmp_age);
+  for (int i = 0; i < ks; ++i) it[tmp[i].idx].taken = 1;
+  m = 0;
+  for (int i = 0; i < cnt; ++i) if (!it[i].taken) tmp[m++] = it[i];
+  qsort(tmp, (size_t)m, sizeof(item_t), cmp_unif);
+  for (int i = 0; i < kr; ++i) it[tmp[i].idx].taken = 1;
+  free(tmp);
+}
+
+/* streams of the random hash */
+#define ORC_STREAM_TILE_HARD 1
+#define ORC_STREAM_TILE_UNIF 2
+#define ORC_STREAM_PIX_HARD 3
+#define ORC_STREAM_PIX_UNIF 4
+
+/* exposed for the sampling pins: choose n of cnt items with given weights and
+ * ages; hash streams of the pixel level of tile `tile`. out_taken [cnt] */
+int orc_choose_items(int cnt, const uint64_t* w, const uint32_t* age, int n, int hard_pm, int stable_pm,
+                     uint64_t seed, uint64_t iter, uint32_t view, uint32_t tile, uint8_t* out_taken) {
+  item_t* it = (item_t*)malloc(sizeof(item_t) * (size_t)(cnt > 0 ? cnt : 1));
+  for (int i = 0; i < cnt; ++i) {
+    it[i].idx = i; it[i].w = w[i]; it[i].age = age[i]; it[i].taken = 0;
+    it[i].L = orc_neglog2_q32(orc_hash(seed, iter, view, ORC_STREAM_PIX_HARD, tile, (uint32_t)i));
+    it[i].u = orc_hash(seed, iter, view, ORC_STREAM_PIX_UNIF, tile, (uint32_t)i);
+  }
+  choose(it, cnt, n, hard_pm, stable_pm);
+  for (int i = 0; i < cnt; ++i) out_taken[i] = (uint8_t)it[i].taken;
+  free(it);
+  return 0;
+}
+
+/*
+ * Tile selection and tile-wise pixel sampling (Sec. 3.5).
+ * Tile level: n_select tiles, split by tile_hard_pm / tile_stable_pm; a tile's
+ * weight is the sum of its pixels' weights, its age the smallest pixel age
+ * (iterations since any of its pixels was sampled).
+ * Pixel level: in each selected tile N_pix = min(n_pix, valid pixels), split
+ * into N_hard = round(r_hard N_pix) drawn proportionally to E without
+ * replacement, N_stable = round(r_stable N_pix) of largest age among the
+ * rest, and the remainder uniformly.
+ * Outputs: active_tiles (ascending), *n_active, tile_rank [tiles] (-1 when not
+ * selected), pix_off [n_active + 1], pix_idx (local index ly*16+lx, ascending
+ * within each tile).
+ */
+int orc_select(int width, int height, const uint16_t* err, const uint16_t* age, int n_select, int n_pix,
+               int tile_hard_pm, int tile_stable_pm, int pix_hard_pm, int pix_stable_pm, uint64_t seed,
+               uint64_t iter, uint32_t view, int32_t* active_tiles, int32_t* n_active, int32_t* tile_rank,
+               int32_t* pix_off, uint8_t* pix_idx) {
+  int tx_n = (width + ORC_TILE - 1) / ORC_TILE, ty_n = (height + ORC_TILE - 1) / ORC_TILE;
+  int T = tx_n * ty_n;
+  item_t* tiles = (item_t*)malloc(sizeof(item_t) * (size_t)T);
+  for (int t = 0; t < T; ++t) {
+    int tx = t % tx_n, ty = t / tx_n;
+    uint64_t w = 0;
+    uint32_t amin = 0xFFFFFFFFu;
+    for (int ly = 0; ly < ORC_TILE; ++ly)
+      for (int lx = 0; lx < ORC_TILE; ++lx) {
+        int x = tx * ORC_TILE + lx, y = ty * ORC_TILE + ly;
+        if (x >= width || y >= height) continue;
+        w += orc_err_weight(err[(int64_t)y * width + x]);
+        uint32_t a = age[(int64_t)y * width + x];
+        if (a < amin) amin = a;
+      }
+    tiles[t].idx = t; tiles[t].w = w; tiles[t].age = amin; tiles[t].taken = 0;
+    tiles[t].L = orc_neglog2_q32(orc_hash(seed, iter, view, ORC_STREAM_TILE_HARD, (uint32_t)t, 0));
+    tiles[t].u = orc_hash(seed, iter, view, ORC_STREAM_TILE_UNIF, (uint32_t)t, 0);
+  }
+  choose(tiles, T, n_select < 0 ? 0 : n_select, tile_hard_pm, tile_stable_pm);
+  int A = 0;
+  pix_off[0] = 0;
+  item_t px[ORC_TILE * ORC_TILE];
+  for (int t = 0; t < T; ++t) {
+    tile_rank[t] = -1;
+    if (!tiles[t].taken) continue;
+    tile_rank[t] = A;
+    active_tiles[A] = t;
+    int tx = t % tx_n, ty = t / tx_n;
+    int cnt = 0;
+    for (int ly = 0; ly < ORC_TILE; ++ly)
+      for (int lx = 0; lx < ORC_TILE; ++lx) {
+        int x = tx * ORC_TILE + lx, y = ty * ORC_TILE + ly;
+        if (x >= width || y >= height) continue;
+        int l = ly * ORC_TILE + lx;
+        item_t* p = &px[cnt];
+        p->idx = cnt;
+        p->w = orc_err_weight(err[(int64_t)y * width + x]);
+        p->age = age[(int64_t)y * width + x];
+        p->L = orc_neglog2_q32(orc_hash(seed, iter, view, ORC_STREAM_PIX_HARD, (uint32_t)t, (uint32_t)l));
+        p->u = orc_hash(seed, iter, view, ORC_STREAM_PIX_UNIF, (uint32_t)t, (uint32_t)l);
+        p->taken = l;             /* stash local index; reset below */
+        cnt++;
+      }
+    int local[ORC_TILE * ORC_TILE];
+    for (int i = 0; i < cnt; ++i) { local[i] = px[i].taken; px[i].taken = 0; }
+    choose(px, cnt, n_pix, pix_hard_pm, pix_stable_pm);
+    int o = pix_off[A];
+    for (int i = 0; i < cnt; ++i)
+      if (px[i].taken) pix_idx[o++] = (uint8_t)local[i];
+    pix_off[A + 1] = o;
+    A++;
+  }
+  *n_active = A;
+  free(tiles);
+  (void)cmp_idx;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* sparse forward rendering (Eq. 1), one pixel at a time                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { double depth; int32_t id; } cand_t;
+
+static int cmp_cand(const void* a, const void* b) {
+  const cand_t* x = (const cand_t*)a;
+  const cand_t* y = (const cand_t*)b;
+  if (x->depth != y->depth) return x->depth < y->depth ? -1 : 1;
+  return x->id - y->id;
+}
+
+typedef struct {
+  int n_cand;
+  cand_t* cand;
+  /* per accepted splat k (in order) */
+  int n_acc;
+  int* acc_id;        /* Gaussian id */
+  int* acc_pos;       /* position in the candidate list */
+  double *T, *alpha, *G, *dx, *dy;
+  int* clamped;       /* alpha hit the 0.99 cap */
+  double T_final;
+  int n_last;         /* position + 1 of the last accepted splat, 0 if none */
+  double margin;
+} pixel_trace_t;
+
+static void trace_free(pixel_trace_t* p) {
+  free(p->cand); free(p->acc_id); free(p->acc_pos); free(p->T); free(p->alpha); free(p->G);
+  free(p->dx); free(p->dy); free(p->clamped);
+}
+
+/*
+ * Front-to-back compositing of pixel (px, py): the Gaussians whose tile
+ * rectangle covers the pixel's tile, ordered by depth then id; alpha_k =
+ * min(0.99, o_k exp(power_k)) with power = -(a dx^2 + c dy^2)/2 - b dx dy at
+ * the pixel centre, splats with power > 0 or alpha < 1/255 skipped, stop
+ * before the splat that would take T below 1e-4.
+ */
+static void trace_pixel(int64_t n, const double* xy, const double* conic, const double* opac,
+                        const double* depth, const int32_t* radius, int tx_n, int ty_n, int px, int py,
+                        pixel_trace_t* p) {
+  memset(p, 0, sizeof(*p));
+  p->margin = INFINITY;
+  int ptx = px / ORC_TILE, pty = py / ORC_TILE;
+  int cap = 64;
+  p->cand = (cand_t*)malloc(sizeof(cand_t) * (size_t)cap);
+  for (int64_t i = 0; i < n; ++i) {
+    if (radius[i] <= 0) continue;
+    int x0, x1, y0, y1;
+    rect_axis(xy[2 * i], radius[i], tx_n, &x0, &x1);
+    rect_axis(xy[2 * i + 1], radius[i], ty_n, &y0, &y1);
+    if (ptx < x0 || ptx >= x1 || pty < y0 || pty >= y1) continue;
+    if (p->n_cand == cap) { cap *= 2; p->cand = (cand_t*)realloc(p->cand, sizeof(cand_t) * (size_t)cap); }
+    p->cand[p->n_cand].depth = depth[i];
+    p->cand[p->n_cand].id = (int32_t)i;
+    p->n_cand++;
+  }
+  qsort(p->cand, (size_t)p->n_cand, sizeof(cand_t), cmp_cand);
+  int m = p->n_cand > 0 ? p->n_cand : 1;
+  p->acc_id = (int*)malloc(sizeof(int) * m);
+  p->acc_pos = (int*)malloc(sizeof(int) * m);
+  p->T = (double*)malloc(sizeof(double) * m);
+  p->alpha = (double*)malloc(sizeof(double) * m);
+  p->G = (double*)malloc(sizeof(double) * m);
+  p->dx = (double*)malloc(sizeof(double) * m);
+  p->dy = (double*)malloc(sizeof(double) * m);
+  p->clamped = (int*)malloc(sizeof(int) * m);
+  double cxp = px + 0.5, cyp = py + 0.5;
+  double T = 1.0;
+  for (int k = 0; k < p->n_cand; ++k) {
+    int i = p->cand[k].id;
+    if (k > 0) {
+      double d0 = p->cand[k - 1].depth, d1 = p->cand[k].depth;
+      p->margin = minabs(p->margin, (d1 - d0) / (fabs(d1) + 1e-30) * 1e2);
+    }
+    double dx = cxp - xy[2 * i], dy = cyp - xy[2 * i + 1];
+    double a = conic[3 * i], b = conic[3 * i + 1], c = conic[3 * i + 2];
+    double power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy;
+    if (power > 0.0) continue;
+    double G = exp(power);
+    double araw = opac[i] * G;
+    double alpha = araw < 0.99 ? araw : 0.99;
+    p->margin = minabs(p->margin, fabs(alpha * 255.0 - 1.0));
+    p->margin = minabs(p->margin, fabs(araw - 0.99) / 0.99);
+    if (alpha < 1.0 / 255.0) continue;
+    double Tn = T * (1.0 - alpha);
+    p->margin = minabs(p->margin, fabs(Tn - 1e-4) / 1e-4);
+    if (Tn < 1e-4) break;
+    int j = p->n_acc++;
+    p->acc_id[j] = i; p->acc_pos[j] = k;
+    p->T[j] = T; p->alpha[j] = alpha; p->G[j] = G; p->dx[j] = dx; p->dy[j] = dy;
+    p->clamped[j] = araw >= 0.99;
+    T = Tn;
+    p->n_last = k + 1;
+  }
+  p->T_final = T;
+}
+
+/*
+ * Render the listed pixels (pix_xy [P,2] integer coordinates).  Outputs
+ * rgb [P,3] = sum_k T_k alpha_k c_k + T_final bg, T_final [P], n_last [P]
+ * (position + 1 in the pixel's depth-ordered list of the last splat blended),
+ * n_contrib [P] and margin [P] (diagnostics, nullable).
+ */
+int orc_render_pixels(int64_t n, const double* xy, const double* conic, const double* opac,
+                      const double* rgb, const double* depth, const int32_t* radius, int width, int height,
+                      const double* bg, int64_t n_pix, const int32_t* pix_xy, double* out_rgb,
+                      double* out_T, int32_t* out_nlast, int32_t* out_ncontrib, double* out_margin) {
+  int tx_n = (width + ORC_TILE - 1) / ORC_TILE, ty_n = (height + ORC_TILE - 1) / ORC_TILE;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t s = 0; s < n_pix; ++s) {
+    pixel_trace_t p;
+    trace_pixel(n, xy, conic, opac, depth, radius, tx_n, ty_n, pix_xy[2 * s], pix_xy[2 * s + 1], &p);
+    for (int c = 0; c < 3; ++c) {
+      double acc = 0.0;
+      for (int j = 0; j < p.n_acc; ++j) acc += p.T[j] * p.alpha[j] * rgb[3 * p.acc_id[j] + c];
+      out_rgb[3 * s + c] = acc + p.T_final * bg[c];
+    }
+    out_T[s] = p.T_final;
+    out_nlast[s] = p.n_last;
+    if (out_ncontrib) out_ncontrib[s] = p.n_acc;
+    if (out_margin) out_margin[s] = p.margin;
+    trace_free(&p);
+  }
+  return 0;
+}
+
+/*
+ * Adjoint of the compositing for the listed pixels, given dL/dI [P,3].
+ * With S_k the colour seen behind splat k (S_n = bg,
+ * S_k = alpha_k c_k + (1 - alpha_k) S_{k+1}):
+ *   dL/dc_k = T_k alpha_k g,  dL/dalpha_k = T_k (c_k - S_{k+1}) . g,
+ * alpha = o G (0 when capped at 0.99), G = exp(power).
+ * Accumulates grad2d [N,9] = (d x, d y, d a, d b, d c, d opacity, d r, d g, d b).
+ */
+int orc_render_backward(int64_t n, const double* xy, const double* conic, const double* opac,
+                        const double* rgb, const double* depth, const int32_t* radius, int width, int height,
+                        const double* bg, int64_t n_pix, const int32_t* pix_xy, const double* dL_drgb,
+                        double* grad2d) {
+  int tx_n = (width + ORC_TILE - 1) / ORC_TILE, ty_n = (height + ORC_TILE - 1) / ORC_TILE;
+  memset(grad2d, 0, sizeof(double) * 9 * (size_t)n);
+  for (int64_t s = 0; s < n_pix; ++s) {
+    pixel_trace_t p;
+    trace_pixel(n, xy, conic, opac, depth, radius, tx_n, ty_n, pix_xy[2 * s], pix_xy[2 * s + 1], &p);
+    const double* g = dL_drgb + 3 * s;
+    double S[3] = {bg[0], bg[1], bg[2]};
+    for (int j = p.n_acc - 1; j >= 0; --j) {
+      int i = p.acc_id[j];
+      const double* c = rgb + 3 * i;
+      double T = p.T[j], al = p.alpha[j];
+      double dalpha = 0.0;
+      for (int ch = 0; ch < 3; ++ch) {
+        grad2d[9 * i + 6 + ch] += T * al * g[ch];
+        dalpha += T * (c[ch] - S[ch]) * g[ch];
+      }
+      for (int ch = 0; ch < 3; ++ch) S[ch] = al * c[ch] + (1.0 - al) * S[ch];
+      if (p.clamped[j]) continue;
+      double G = p.G[j], o = opac[i];
+      grad2d[9 * i + 5] += dalpha * G;
+      double dpow = dalpha * o * G;
+      double dx = p.dx[j], dy = p.dy[j];
+      double a = conic[3 * i], b = conic[3 * i + 1], cc = conic[3 * i + 2];
+      /* power = -(a dx^2 + c dy^2)/2 - b dx dy, dx = px + 0.5 - x */
+      grad2d[9 * i + 0] += dpow * (a * dx + b * dy);
+      grad2d[9 * i + 1] += dpow * (cc * dy + b * dx);
+      grad2d[9 * i + 2] += dpow * (-0.5 * dx * dx);
+      grad2d[9 * i + 3] += dpow * (-dx * dy);
+      grad2d[9 * i + 4] += dpow * (-0.5 * dy * dy);
+    }
+    trace_free(&p);
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* adjoint of the projection                                                */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * grads [N,59] = (means 3, log_scales 3, quats 4, opacity logit 1,
+ * sh 48 in [16][3] order) from grad2d [N,9].  Culled Gaussians get zeros.
+ */
+int orc_project_backward(int64_t n, const double* means, const double* log_scales, const double* quats,
+                         const double* opacity_logits, const double* sh, int sh_degree, const double* cam_in,
+                         int width, int height, const int32_t* tile_rank, const double* grad2d,
+                         double* grads) {
+  cam_t cam;
+  cam_load(cam_in, width, height, &cam);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double* out = grads + 59 * i;
+    memset(out, 0, sizeof(double) * 59);
+    gproj_t g;
+    const double* mu = means + 3 * i;
+    const double* shi = sh + 48 * i;
+    project_one(mu, log_scales + 3 * i, quats + 4 * i, opacity_logits[i], shi, sh_degree, &cam, tile_rank, &g);
+    if (!g.visible) continue;
+    const double* d2 = grad2d + 9 * i;
+    double dmu[3] = {0, 0, 0};
+    /* opacity */
+    out[10] = d2[5] * g.opac * (1.0 - g.opac);
+    /* colour through SH (clamp at 0 passes no gradient) */
+    double Y[16], dY[48];
+    orc_sh_basis(g.dir, Y, dY);
+    int nb = (sh_degree + 1) * (sh_degree + 1);
+    double ddir[3] = {0, 0, 0};
+    for (int c = 0; c < 3; ++c) {
+      double dc = g.rgb_pre[c] >= 0.0 ? d2[6 + c] : 0.0;
+      for (int k = 0; k < nb; ++k) {
+        out[11 + 3 * k + c] = dc * Y[k];
+        for (int a = 0; a < 3; ++a) ddir[a] += dc * shi[3 * k + c] * dY[3 * k + a];
+      }
+    }
+    double dot = ddir[0] * g.dir[0] + ddir[1] * g.dir[1] + ddir[2] * g.dir[2];
+    for (int a = 0; a < 3; ++a) dmu[a] += (ddir[a] - g.dir[a] * dot) / g.vlen;
+    /* pixel centre u = fx x/z + cx, v = fy y/z + cy */
+    double z = g.pc[2];
+    double dpc[3];
+    dpc[0] = d2[0] * cam.fx / z;
+    dpc[1] = d2[1] * cam.fy / z;
+    dpc[2] = -d2[0] * cam.fx * g.pc[0] / (z * z) - d2[1] * cam.fy * g.pc[1] / (z * z);
+    /* conic Q = Sigma2^-1: dSigma2 = -Q dQ Q, dQ symmetric with off-diagonal db/2 */
+    double Q[4] = {g.conic[0], g.conic[1], g.conic[1], g.conic[2]};
+    double dQ[4] = {d2[2], 0.5 * d2[3], 0.5 * d2[3], d2[4]};
+    double tmp[4], dS2[4];
+    matmul(Q, dQ, tmp, 2, 2, 2);
+    matmul(tmp, Q, dS2, 2, 2, 2);
+    for (int k = 0; k < 4; ++k) dS2[k] = -dS2[k];
+    /* Sigma2 = T Sigma T^T + 0.3 I, T = J W */
+    double Tt[6], tmp3[6], dSigma[9], dT[6], dS2T[6], dS2TS[6];
+    transpose(g.T, Tt, 2, 3);
+    matmul(Tt, dS2, tmp3, 3, 2, 2);        /* T^T dS2     (3x2) */
+    matmul(tmp3, g.T, dSigma, 3, 2, 3);    /* T^T dS2 T   (3x3) */
+    matmul(dS2, g.T, dS2T, 2, 2, 3);       /* dS2 T       (2x3) */
+    matmul(dS2T, g.Sigma, dS2TS, 2, 3, 3); /* dS2 T Sigma (2x3) */
+    for (int k = 0; k < 6; ++k) dT[k] = 2.0 * dS2TS[k];
+    double Wt[9], dJ[6];
+    transpose(cam.W, Wt, 3, 3);
+    matmul(dT, Wt, dJ, 2, 3, 3);
+    /* J = [[fx/z, 0, -fx tx/z], [0, fy/z, -fy ty/z]], tx = clamp(x/z) */
+    dpc[2] += dJ[0] * (-cam.fx / (z * z)) + dJ[4] * (-cam.fy / (z * z));
+    if (!g.clampx) {
+      dpc[0] += dJ[2] * (-cam.fx / (z * z));
+      dpc[2] += dJ[2] * (2.0 * cam.fx * g.pc[0] / (z * z * z));
+    } else {
+      double lim = 1.3 * (0.5 * cam.width / cam.fx) * (g.pc[0] > 0 ? 1.0 : -1.0);
+      dpc[2] += dJ[2] * (cam.fx * lim / (z * z));
+    }
+    if (!g.clampy) {
+      dpc[1] += dJ[5] * (-cam.fy / (z * z));
+      dpc[2] += dJ[5] * (2.0 * cam.fy * g.pc[1] / (z * z * z));
+    } else {
+      double lim = 1.3 * (0.5 * cam.height / cam.fy) * (g.pc[1] > 0 ? 1.0 : -1.0);
+      dpc[2] += dJ[5] * (cam.fy * lim / (z * z));
+    }
+    /* pc = W mu + t */
+    for (int a = 0; a < 3; ++a)
+      dmu[a] += cam.W[0 * 3 + a] * dpc[0] + cam.W[1 * 3 + a] * dpc[1] + cam.W[2 * 3 + a] * dpc[2];
+    out[0] = dmu[0]; out[1] = dmu[1]; out[2] = dmu[2];
+    /* Sigma = M M^T, M = R diag(s) */
+    double M[9], dM[9];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) M[r * 3 + c] = g.R[r * 3 + c] * g.s[c];
+    matmul(dSigma, M, dM, 3, 3, 3);
+    for (int k = 0; k < 9; ++k) dM[k] *= 2.0;
+    double dR[9];
+    for (int c = 0; c < 3; ++c) {
+      double ds = 0.0;
+      for (int r = 0; r < 3; ++r) ds += g.R[r * 3 + c] * dM[r * 3 + c];
+      out[3 + c] = ds * g.s[c];
+      for (int r = 0; r < 3; ++r) dR[r * 3 + c] = dM[r * 3 + c] * g.s[c];
+    }
+    /* rotation of the unit quaternion, then its normalisation */
+    double w = g.q[0], x = g.q[1], y = g.q[2], zq = g.q[3];
+    double dq[4];
+    dq[0] = dR[1] * (-2 * zq) + dR[2] * (2 * y) + dR[3] * (2 * zq) + dR[5] * (-2 * x) + dR[6] * (-2 * y) + dR[7] * (2 * x);
+    dq[1] = dR[1] * (2 * y) + dR[2] * (2 * zq) + dR[3] * (2 * y) + dR[4] * (-4 * x) + dR[5] * (-2 * w) + dR[6] * (2 * zq) + dR[7] * (2 * w) + dR[8] * (-4 * x);
+    dq[2] = dR[0] * (-4 * y) + dR[1] * (2 * x) + dR[2] * (2 * w) + dR[3] * (2 * x) + dR[5] * (2 * zq) + dR[6] * (-2 * w) + dR[7] * (2 * zq) + dR[8] * (-4 * y);
+    dq[3] = dR[0] * (-4 * zq) + dR[1] * (-2 * w) + dR[2] * (2 * x) + dR[3] * (2 * w) + dR[4] * (-4 * zq) + dR[5] * (2 * y) + dR[6] * (2 * x) + dR[7] * (2 * y);
+    double qd = dq[0] * g.q[0] + dq[1] * g.q[1] + dq[2] * g.q[2] + dq[3] * g.q[3];
+    for (int k = 0; k < 4; ++k) out[6 + k] = (dq[k] - g.q[k] * qd) / g.qnorm;
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* sparse loss: Charbonnier L1 + tile-level sparse NCC (Sec. 3.7, App. A)   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * For each active tile tau with its n sampled pixels (prediction x, target y,
+ * per colour channel):
+ *   l1(p) = sum_c sqrt((x - y)^2 + eps_c^2)
+ *   NCC_c = cov_c / sqrt(var_x,c var_y,c + eps_n), population moments over the
+ *           tile's sampled pixels; S-NCC_tau = 1 - mean_c NCC_c
+ *   lambda_tau = clip(mean_p |grad l1(p)|_1 / (mean_p g_ncc(p) + 1e-8), 0, 1),
+ *     g_ncc(p) = sum_c |n dNCC_c/dx_p,c| (per-pixel scale, no 1/n)
+ *   L = (1/|P|) sum_p l1(p) + (1/A) sum_tau lambda_tau S-NCC_tau, lambda held fixed
+ * Outputs dL/dI [P,3], lambda [A], e [P] = sum_c |x - y|, *loss; updates the
+ * fp16 error map by E <- (1 - beta) E + beta e at sampled pixels and the age map
+ * by +1 (saturating) everywhere, 0 at sampled pixels (Eqs. 3-4).
+ * lambda_in (nullable) replaces the computed lambda (for finite differences).
+ */
+int orc_loss(int width, int height, int n_active, const int32_t* active_tiles, const int32_t* pix_off,
+             const uint8_t* pix_idx, const double* rgb, const double* target, const double* lambda_in,
+             double eps_c, double eps_n, double beta, uint16_t* err_map, uint16_t* age_map, double* dL_drgb,
+             double* lambda_out, double* err_pix, double* loss_out) {
+  int tx_n = (width + ORC_TILE - 1) / ORC_TILE;
+  int64_t P = pix_off[n_active];
+  double loss = 0.0;
+  for (int j = 0; j < n_active; ++j) {
+    int t = active_tiles[j];
+    int tx = t % tx_n, ty = t / tx_n;
+    int64_t s0 = pix_off[j], s1 = pix_off[j + 1];
+    int nn = (int)(s1 - s0);
+    if (nn <= 0) { lambda_out[j] = 0.0; continue; }
+    double mx[3] = {0, 0, 0}, my[3] = {0, 0, 0};
+    for (int64_t s = s0; s < s1; ++s) {
+      int l = pix_idx[s];
+      int x = tx * ORC_TILE + (l % ORC_TILE), y = ty * ORC_TILE + (l / ORC_TILE);
+      for (int c = 0; c < 3; ++c) {
+        mx[c] += rgb[3 * s + c];
+        my[c] += target[((int64_t)y * width + x) * 3 + c];
+      }
+    }
+    for (int c = 0; c < 3; ++c) { mx[c] /= nn; my[c] /= nn; }
+    double vx[3] = {0, 0, 0}, vy[3] = {0, 0, 0}, cv[3] = {0, 0, 0};
+    for (int64_t s = s0; s < s1; ++s) {
+      int l = pix_idx[s];
+      int x = tx * ORC_TILE + (l % ORC_TILE), y = ty * ORC_TILE + (l / ORC_TILE);
+      for (int c = 0; c < 3; ++c) {
+        double dx = rgb[3 * s + c] - mx[c], dy = target[((int64_t)y * width + x) * 3 + c] - my[c];
+        vx[c] += dx * dx; vy[c] += dy * dy; cv[c] += dx * dy;
+      }
+    }
+    double D[3], ncc[3];
+    for (int c = 0; c < 3; ++c) {
+      vx[c] /= nn; vy[c] /= nn; cv[c] /= nn;
+      D[c] = sqrt(vx[c] * vy[c] + eps_n);
+      ncc[c] = cv[c] / D[c];
+    }
+    /* per-pixel gradients of both terms */
+    double sum_g1 = 0.0, sum_gn = 0.0;
+    for (int64_t s = s0; s < s1; ++s) {
+      int l = pix_idx[s];
+      int x = tx * ORC_TILE + (l % ORC_TILE), y = ty * ORC_TILE + (l / ORC_TILE);
+      for (int c = 0; c < 3; ++c) {
+        double xv = rgb[3 * s + c], yv = target[((int64_t)y * width + x) * 3 + c];
+        double d = xv - yv;
+        sum_g1 += fabs(d / sqrt(d * d + eps_c * eps_c));
+        /* n dNCC_c/dx = ((y - my) - NCC var_y (x - mx) / D) / D */
+        double gn = ((yv - my[c]) - ncc[c] * vy[c] * (xv - mx[c]) / D[c]) / D[c];
+        sum_gn += fabs(gn);
+      }
+    }
+    double lam = (sum_g1 / nn) / (sum_gn / nn + 1e-8);
+    lam = clampd(lam, 0.0, 1.0);
+    if (lambda_in) lam = lambda_in[j];
+    lambda_out[j] = lam;
+    double sncc = 1.0 - (ncc[0] + ncc[1] + ncc[2]) / 3.0;
+    loss += lam * sncc / n_active;
+    for (int64_t s = s0; s < s1; ++s) {
+      int l = pix_idx[s];
+      int x = tx * ORC_TILE + (l % ORC_TILE), y = ty * ORC_TILE + (l / ORC_TILE);
+      double e = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        double xv = rgb[3 * s + c], yv = target[((int64_t)y * width + x) * 3 + c];
+        double d = xv - yv;
+        double r = sqrt(d * d + eps_c * eps_c);
+        loss += r / (double)P;
+        e += fabs(d);
+        double dncc = ((yv - my[c]) - ncc[c] * vy[c] * (xv - mx[c]) / D[c]) / (D[c] * nn);
+        dL_drgb[3 * s + c] = d / r / (double)P - lam / (3.0 * n_active) * dncc;
+      }
+      err_pix[s] = e;
+    }
+  }
+  *loss_out = loss;
+  /* age map: +1 everywhere (saturating), then 0 at sampled pixels */
+  if (age_map) {
+    for (int64_t k = 0; k < (int64_t)width * height; ++k)
+      if (age_map[k] < 65535) age_map[k]++;
+  }
+  for (int j = 0; j < n_active; ++j) {
+    int t = active_tiles[j];
+    int tx = t % tx_n, ty = t / tx_n;
+    for (int64_t s = pix_off[j]; s < pix_off[j + 1]; ++s) {
+      int l = pix_idx[s];
+      int64_t k = (int64_t)(ty * ORC_TILE + l / ORC_TILE) * width + tx * ORC_TILE + (l % ORC_TILE);
+      if (err_map) {
+        double old = orc_half_to_double(err_map[k]);
+        err_map[k] = orc_double_to_half((1.0 - beta) * old + beta * err_pix[s]);
+      }
+      if (age_map) age_map[k] = 0;
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* hybrid solver: moment-damped LM blocks + Adam (Sec. 3.9, App. A)         */
+/* ------------------------------------------------------------------------ */
+
+/* Cholesky factorisation A = L L^T (row-major d x d) and solve A x = b. */
+static int cholesky_solve(const double* A, const double* b, double* x, int d) {
+  double L[196];
+  memset(L, 0, sizeof(L));
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double s = A[i * d + j];
+      for (int k = 0; k < j; ++k) s -= L[i * d + k] * L[j * d + k];
+      if (i == j) {
+        if (!(s > 0.0)) return -1;
+        L[i * d + i] = sqrt(s);
+      } else L[i * d + j] = s / L[j * d + j];
+    }
+  double y[14];
+  for (int i = 0; i < d; ++i) {
+    double s = b[i];
+    for (int k = 0; k < i; ++k) s -= L[i * d + k] * y[k];
+    y[i] = s / L[i * d + i];
+  }
+  for (int i = d - 1; i >= 0; --i) {
+    double s = y[i];
+    for (int k = i + 1; k < d; ++k) s -= L[k * d + i] * x[k];
+    x[i] = s / L[i * d + i];
+  }
+  return 0;
+}
+
+int orc_cholesky_solve(const double* A, const double* b, double* x, int d) {
+  return d > 14 ? -2 : cholesky_solve(A, b, x, d);
+}
+
+/*
+ * One step for the Gaussians with touched[i] != 0.  Packed parameter rows of
+ * 59: (means 3, log_scales 3, quats 4, opacity logit 1, sh 48 with the DC
+ * colour at 11..13).  cfg = [lr_means, lr_scales, lr_quats, lr_opacity,
+ * lr_sh_dc, lr_sh_rest, beta1, beta2, eps_adam, eps_lm].
+ * m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2 for all 59.
+ * mode 0: Adam with bias correction on all 59.
+ * mode 1: geometry block (0..9) and appearance block (11,12,13,10) solve
+ *         (diag(sum_k J_k^2) + diag(sqrt(v) + eps_lm)) D = -m;
+ * mode 2: the same with J^T J in full, solved by Cholesky.
+ * J rows: rows [K, N, 14] (geometry 10 then appearance 4 in the block order
+ * above), or, when rows is NULL, the single row g.  theta += lr * D; the 45
+ * higher SH coefficients always take the Adam step -lr m_hat / (sqrt(v_hat) + eps).
+ */
+int orc_hybrid_step(int64_t n, double* params, const double* grads, double* m, double* v,
+                    const uint8_t* touched, const double* rows, int k_rows, int step, int mode,
+                    const double* cfg) {
+  double b1 = cfg[6], b2 = cfg[7], eps = cfg[8], eps_lm = cfg[9];
+  double bc1 = 1.0 - pow(b1, step), bc2 = 1.0 - pow(b2, step);
+  static const int geo[10] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9};
+  static const int app[4] = {11, 12, 13, 10};
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    if (touched && !touched[i]) continue;
+    double* p = params + 59 * i;
+    const double* g = grads + 59 * i;
+    double* mi = m + 59 * i;
+    double* vi = v + 59 * i;
+    for (int k = 0; k < 59; ++k) {
+      mi[k] = b1 * mi[k] + (1.0 - b1) * g[k];
+      vi[k] = b2 * vi[k] + (1.0 - b2) * g[k] * g[k];
+    }
+    double lr[59];
+    for (int k = 0; k < 59; ++k) {
+      int grp = k < 3 ? 0 : k < 6 ? 1 : k < 10 ? 2 : k == 10 ? 3 : k < 14 ? 4 : 5;
+      lr[k] = cfg[grp];
+    }
+    if (mode == 0) {
+      for (int k = 0; k < 59; ++k) p[k] -= lr[k] * (mi[k] / bc1) / (sqrt(vi[k] / bc2) + eps);
+      continue;
+    }
+    for (int blk = 0; blk < 2; ++blk) {
+      const int* ix = blk == 0 ? geo : app;
+      int d = blk == 0 ? 10 : 4;
+      int off = blk == 0 ? 0 : 10;
+      double A[100], rhs[10], D[10];
+      memset(A, 0, sizeof(A));
+      int K = rows ? k_rows : 1;
+      for (int r = 0; r < K; ++r) {
+        double J[10];
+        for (int a = 0; a < d; ++a)
+          J[a] = rows ? rows[((int64_t)r * n + i) * 14 + off + a] : g[ix[a]];
+        for (int a = 0; a < d; ++a)
+          for (int b = 0; b < d; ++b)
+            if (mode == 2 || a == b) A[a * d + b] += J[a] * J[b];
+      }
+      for (int a = 0; a < d; ++a) {
+        A[a * d + a] += sqrt(vi[ix[a]]) + eps_lm;
+        rhs[a] = -mi[ix[a]];
+      }
+      cholesky_solve(A, rhs, D, d);
+      for (int a = 0; a < d; ++a) p[ix[a]] += lr[ix[a]] * D[a];
+    }
+    for (int k = 14; k < 59; ++k) p[k] -= lr[k] * (mi[k] / bc1) / (sqrt(vi[k] / bc2) + eps);
+  }
+  return 0;
+}
