@@ -1,0 +1,434 @@
+"""Throughput of the TurboGS sparse-sampled training step on one GB300.
+
+Workload (the sparse-training-step configuration): 500k Gaussians (means
+uniform in [-5,5]^3, log-scales N(-3.5,0.5), unit quaternions, opacity logits
+N(0,1), SH degree 3 ~ N(0,0.2)), one 1280x720 pinhole view (fov 60 deg, distance
+15), a target rendered from a second seeded Gaussian set, an error map from the
+dense render of the initial Gaussians.  A step is one full training iteration
+of the sampled path: tile selection + pixel sampling, projection, binning,
+sparse render, fused L1 + sparse-NCC loss with error/age updates, sparse
+backward, hybrid LM/Adam update.  The same library's dense path (every tile,
+every pixel) is measured beside it.
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GAUSS = 500_000
+WIDTH, HEIGHT = 1280, 720
+DISTANCE = 15.0
+EXTENT = 5.0
+TILE_FRACTION = 0.2
+PIXEL_RATE = 1.0 / 3.0
+METRIC = "train iters/s & sampled fwd+bwd Mpix/s vs dense path, 1 GB300, same PSNR"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def workload_config(frac=TILE_FRACTION, rate=PIXEL_RATE):
+    return {"workload": "sparse training step: 500k Gaussians, 1280x720 view, "
+                        f"{round(frac * 100)}% of 16x16 tiles, pixel rate {rate:.3f}",
+            "gaussians": N_GAUSS, "width": WIDTH, "height": HEIGHT, "tile_fraction": frac, "pixel_rate": rate,
+            "l2": "flushed between timed steps (256 MB write)"}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def build_scene(device):
+    import numpy as np
+    import torch
+    from paper_2606_15924_gb300 import scenes
+    from paper_2606_15924_gb300.pipeline import Trainer
+    cam = scenes.look_at((0.0, 0.0, -DISTANCE), width=WIDTH, height=HEIGHT, fov_x_deg=60.0)
+    gt = scenes.gaussians(N_GAUSS, seed=scenes.SEED_TARGET, extent=EXTENT)
+    gt_d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in gt.items()}
+    dummy = torch.zeros(HEIGHT, WIDTH, 3, device=device)
+    target = Trainer(gt_d, cam, dummy, dense=True, train=False).render_image().contiguous()
+    del gt_d
+    g = scenes.gaussians(N_GAUSS, seed=scenes.SEED_SCENE, extent=EXTENT)
+    return cam, g, target
+
+
+def make_trainer(g_np, cam, target, dense, frac, rate, device):
+    import numpy as np
+    import torch
+    from paper_2606_15924_gb300.pipeline import Trainer
+    params = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in g_np.items()}
+    tr = Trainer(params, cam, target, tile_fraction=frac, pixel_rate=rate, dense=dense)
+    tr.init_error_map()
+    return tr
+
+
+def time_replays(tr, steps, flush):
+    """Per-step device time of graph replays, L2 flushed between steps."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k)
+        ev[k][0].record()
+        tr.replay()
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev]
+
+
+def stage_times(tr, steps, flush):
+    """Device time of every call of the step: each call is its own captured
+    graph, replayed in step order with CUDA events between them on the
+    launching stream (L2 flushed before each step); plus the work counts the
+    roofline needs."""
+    import torch
+    if not getattr(tr, "stage_graphs", None):
+        tr.capture_stages()
+    acc = {n: 0.0 for n, _ in tr.stage_graphs}
+    evals = 0
+    for k in range(steps):
+        flush.fill_(k)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(len(tr.stage_graphs) + 1)]
+        e[0].record()
+        for i, (_, gr) in enumerate(tr.stage_graphs):
+            gr.replay()
+            e[i + 1].record()
+        torch.cuda.synchronize()
+        for i, (n, _) in enumerate(tr.stage_graphs):
+            acc[n] += e[i].elapsed_time(e[i + 1])
+        A = int(tr.n_active.item())
+        P = int(tr.pix_off[A].item())
+        evals += int(tr.n_last[:P].sum().item())
+    info = dict(P=P, A=A, n_isect=int(tr.n_isect.item()), evals_per_step=evals / steps,
+                touched=int(tr.touched.sum().item()) if tr.train else 0,
+                visible=int((tr.proj["radius"] > 0).sum().item()))
+    return {n: acc[n] / steps for n in acc}, info
+
+
+# FP32 operations of one alpha evaluation (offset, conic quadratic form,
+# exponent scaling, opacity product, clamp) and of one blend (1 - alpha,
+# transmittance product, weight, three colour FMAs), FMA = 2.
+FLOPS_ALPHA = 15
+FLOPS_BLEND = 10
+
+
+def roofline(stage_ms, info, peaks, peak_kind, clocks, tr):
+    """Dominant kernel's achieved fraction of its roof."""
+    dom = max(stage_ms, key=stage_ms.get)
+    t = stage_ms[dom] * 1e-3
+    sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s FP32 (FMA = 2) at the sampled clock
+    n = tr.n
+    if dom in ("render_sampled",):
+        work = info["evals_per_step"] * (FLOPS_ALPHA + FLOPS_BLEND) / 1e12
+        return dict(kernel=dom, bound="alu", achieved=work / t, peak=alu_peak, unit="TFLOP/s",
+                    frac=(work / t) / alu_peak, traffic=None,
+                    note="FP32 FLOPs of the alpha test + blend per (pixel, splat) walked, at the sampled SM clock")
+    if dom in ("backward_sampled",):
+        work = info["evals_per_step"] * 45 / 1e12
+        return dict(kernel=dom, bound="alu", achieved=work / t, peak=alu_peak, unit="TFLOP/s",
+                    frac=(work / t) / alu_peak, traffic=None,
+                    note="~45 FP32 FLOPs per (pixel, splat) replayed, at the sampled SM clock")
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    if dom == "hybrid_step":
+        byts = info["touched"] * 59 * 4 * 7
+    elif dom == "project_gaussians":
+        byts = n * (44 + 48) + info["visible"] * 192
+    elif dom == "bin_tiles":
+        byts = info["n_isect"] * 44
+    else:
+        byts = HEIGHT * WIDTH * 4 + info["P"] * 48
+    ach = byts / t / 1e9
+    return dict(kernel=dom, bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm, traffic=None)
+
+
+def e2e_replays(tr, target_host, steps):
+    """Public-API step with the view's target copied in from pinned host memory
+    and the loss read back, every step."""
+    import torch
+    loss_host = torch.zeros(1, dtype=torch.float64, pin_memory=True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(steps):
+        tr.target.copy_(target_host, non_blocking=True)
+        tr.replay()
+        loss_host.copy_(tr.loss, non_blocking=True)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    return steps / (ms * 1e-3), tr.target.numel() * 4, 8
+
+
+def cpu_baseline(cam, g_np, target_np, budget_s=20.0):
+    """The oracle as it stands on a bounded sample of the same step: full
+    projection, render + loss + backward of a sample of sampled pixels
+    (scaled to the step's pixel count), full projection adjoint and update."""
+    import numpy as np
+    import oracle
+    from paper_2606_15924_gb300 import scenes
+    T = ((WIDTH + 15) // 16) * ((HEIGHT + 15) // 16)
+    n_sel = round(TILE_FRACTION * T)
+    n_pix = math.floor(PIXEL_RATE * 256)
+    err = scenes.error_map(WIDTH, HEIGHT)
+    age = scenes.age_map(WIDTH, HEIGHT)
+    g64 = {k: v.astype(np.float64) for k, v in g_np.items()}
+    t0 = time.perf_counter()
+    sel = oracle.select(err, age, WIDTH, HEIGHT, n_select=n_sel, n_pix=n_pix, seed=0)
+    t_sel = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    pr = oracle.project(g64, cam, tile_rank=sel["tile_rank"])
+    t_proj = time.perf_counter() - t0
+    pix = oracle.pixel_coords(sel["active_tiles"], sel["pix_off"], sel["pix_idx"], WIDTH)
+    P = len(pix)
+    # sample whole tiles so the loss has its tile statistics
+    k = 2
+    while True:
+        sub = dict(active_tiles=sel["active_tiles"][:k], pix_off=sel["pix_off"][:k + 1],
+                   pix_idx=sel["pix_idx"][:sel["pix_off"][k]])
+        sp = pix[:sel["pix_off"][k]]
+        t0 = time.perf_counter()
+        r = oracle.render_pixels(pr, WIDTH, HEIGHT, sp)
+        lo = oracle.loss(WIDTH, HEIGHT, sub, r["rgb"], target_np.astype(np.float64))
+        g2 = oracle.render_backward(pr, WIDTH, HEIGHT, sp, lo["dL_drgb"])
+        t_pix = time.perf_counter() - t0
+        if t_pix > budget_s / 4 or k >= len(sel["active_tiles"]):
+            break
+        k = min(len(sel["active_tiles"]), k * 2)
+    t0 = time.perf_counter()
+    grads = oracle.project_backward(g64, cam, g2, tile_rank=sel["tile_rank"])
+    t_pb = time.perf_counter() - t0
+    touched = (np.abs(g2).sum(1) > 0).astype(np.uint8)
+    pk = np.concatenate([g64["means"], g64["log_scales"], g64["quats"], g64["opacity_logits"][:, None],
+                         g64["sh"].reshape(N_GAUSS, 48)], 1)
+    t0 = time.perf_counter()
+    oracle.hybrid_step(pk, grads, np.zeros_like(pk), np.zeros_like(pk), touched, 1, 1,
+                       [1.6e-4, 5e-3, 1e-3, 2.5e-2, 2.5e-3, 1.25e-4, 0.9, 0.999, 1e-15, 1e-8])
+    t_h = time.perf_counter() - t0
+    n_s = len(sp)
+    step_s = t_sel + t_proj + t_pix * (P / n_s) + t_pb + t_h
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": 1.0 / step_s, "unit": "iters/s", "cores": cores, "kind": "oracle",
+            "sample": f"full selection, projection, projection adjoint and update of {N_GAUSS} Gaussians; "
+                      f"render+loss+backward of {n_s} of the step's {P} sampled pixels ({k} whole tiles), "
+                      f"scaled by {P / n_s:.1f}; modelled step {step_s:.1f} s"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_2606_15924_gb300 import binding as B
+    B.device_check()
+    from paper_2606_15924_gb300.pipeline import psnr
+    peaks, peak_kind = load_peaks()
+    cam, g_np, target = build_scene(device)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    sampled = make_trainer(g_np, cam, target, False, args.fraction, args.rate, device)
+    dense = None if args.no_dense else make_trainer(g_np, cam, target, True, 1.0, 1.0, device)
+    sampled.capture()
+    if dense is not None:
+        dense.capture()
+    for _ in range(args.warmup):
+        sampled.replay()
+        if dense is not None:
+            dense.replay()
+    torch.cuda.synchronize()
+    if args.profile:
+        for name, tr in (("sampled_step", sampled), ("dense_step", dense)):
+            if tr is None:
+                continue
+            torch.cuda.nvtx.range_push(name)
+            for _ in range(args.steps):
+                tr.replay()
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+        return
+    clk = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    t_wall = time.perf_counter()
+    ms_s = time_replays(sampled, args.steps, flush)
+    ms_d = time_replays(dense, args.steps, flush) if dense is not None else None
+    t_wall = time.perf_counter() - t_wall
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    if dist is not None:
+        dist.barrier()
+    mean_s = sum(ms_s) / len(ms_s)
+    tot = torch.tensor([sum(ms_s)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    value = world * args.steps / (tot.item() * 1e-3)
+    launches = sampled.kernels_per_step
+    # per-stage times, roofline of the dominant kernel (eager pass, events on the launch stream)
+    st, info = stage_times(sampled, max(2, min(args.steps, 5)), flush)
+    roof = roofline(st, info, peaks, peak_kind, clocks, sampled)
+    roof["peak_source"] = f"{peak_kind} (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback"
+    fwdbwd_ms = st["render_sampled"] + st["backward_sampled"]
+    mpix = info["P"] / (fwdbwd_ms * 1e-3) / 1e6
+    res = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": mean_s, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scenes; the paper's datasets are not "
+                                                         "available)",
+           "config": workload_config(args.fraction, args.rate), "gpu_launches": launches * args.steps,
+           "roofline": roof, "clocks": clocks,
+           "sampled": {"iters_per_s": 1e3 / mean_s, "ms_per_step": mean_s, "sampled_pixels": info["P"],
+                       "active_tiles": info["A"], "tile_pairs": info["n_isect"], "touched": info["touched"],
+                       "visible": info["visible"], "splat_evals": info["evals_per_step"],
+                       "fwd_bwd_mpix_per_s": mpix, "stage_ms": st, "kernels_per_step": launches}}
+    if ms_d is not None:
+        mean_d = sum(ms_d) / len(ms_d)
+        st_d, info_d = stage_times(dense, 2, flush)
+        res["dense"] = {"iters_per_s": 1e3 / mean_d, "ms_per_step": mean_d, "pixels": info_d["P"],
+                        "fwd_bwd_mpix_per_s": info_d["P"] / ((st_d["render_sampled"] + st_d["backward_sampled"])
+                                                              * 1e-3) / 1e6, "stage_ms": st_d}
+        res["speedup_vs_dense"] = mean_d / mean_s
+    # end to end through the public API: target in from pinned host memory, loss out
+    tgt_host = target.detach().cpu().pin_memory()
+    e2e_v, h2d, d2h = e2e_replays(sampled, tgt_host, args.steps)
+    res["e2e"] = {"value": e2e_v * world, "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    res["quality"] = {"psnr_init_db": psnr(sampled.render_image(), target)}
+    if rank == 0 and not args.no_cpu:
+        res["cpu_baseline"] = cpu_baseline(cam, g_np, target.cpu().numpy())
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res))
+
+
+def run_reference(args):
+    """The oracle as the reference arm: rank 0 only, bounded samples of the
+    same workload on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import numpy as np
+    from paper_2606_15924_gb300 import scenes
+    cam = scenes.look_at((0.0, 0.0, -DISTANCE), width=WIDTH, height=HEIGHT, fov_x_deg=60.0)
+    g = scenes.gaussians(N_GAUSS, seed=scenes.SEED_SCENE, extent=EXTENT)
+    target = scenes.smooth_image(WIDTH, HEIGHT, seed=scenes.SEED_TARGET)
+    budget = max(8.0, 150.0 / max(1, args.steps + args.warmup))
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        last = cpu_baseline(cam, g, target, budget_s=budget)
+        if i >= args.warmup:
+            vals.append(last["value"])
+    v = sum(vals) / len(vals)
+    last["value"] = v
+    print(json.dumps({"metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": int(os.environ.get("WORLD_SIZE",
+                                                                                                    "1")),
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": workload_config(), "impl": "reference", "cpu_baseline": last,
+                      "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fraction", type=float, default=TILE_FRACTION)
+    ap.add_argument("--rate", type=float, default=PIXEL_RATE)
+    ap.add_argument("--no-dense", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="only warm-up and K replays of each path inside NVTX ranges sampled_step / dense_step "
+                         "(for an ncu launch list); prints nothing")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,291 @@
+/*
+ * turbogs.h - C ABI of the GB300 sparse-sampled Gaussian-splatting path.
+ *
+ * The calls follow the per-iteration steps of TurboGS (ICML 2026, Alg. 1):
+ * pixel sampling (step 3), sparse forward rendering (step 5), the fused sparse
+ * loss with the error/age map update (steps 4, 6, 7), the sparse backward
+ * (step 8) and the hybrid update (steps 9, 10), plus the projection and tile
+ * binning of the 3DGS rasterizer they run on (Sec. 3.1).
+ *
+ * Conventions (all entry points):
+ *  - Every array argument is a DEVICE pointer owned by the caller, contiguous,
+ *    row-major, aligned to 16 bytes.  float = IEEE binary32.  Nothing is
+ *    allocated, freed or kept by the library; scratch is passed in as
+ *    `workspace` of the size the matching *_workspace_size() call returns.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = the legacy
+ *    default stream) and never synchronise.  Counts produced on the device
+ *    (n_active, n_isect) stay on the device; kernels size their grids from the
+ *    host-side upper bounds passed in, so a sequence of calls can be captured
+ *    in a CUDA graph.
+ *  - Return value: TGS_OK, or an error code.  On TGS_ERR_INVALID_ARG nothing
+ *    was launched and no memory was written.  On TGS_ERR_CUDA a launch failed;
+ *    tgs_last_cuda_error() returns the CUDA error code.
+ *  - Image geometry: pixel (x, y) covers [x, x+1) x [y, y+1) and is sampled at
+ *    its centre (x + 0.5, y + 0.5).  Tiles are 16 x 16 pixels; tile id =
+ *    ty * tiles_x + tx with tiles_x = ceil(width / 16).  A pixel is named
+ *    inside its tile by its local index l = ly * 16 + lx (0..255).
+ *  - Thread safety: calls keep no state and may be issued from any thread.
+ */
+#ifndef TURBOGS_H
+#define TURBOGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* tgs_stream; /* = cudaStream_t */
+
+typedef enum {
+  TGS_OK = 0,
+  TGS_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or option */
+  TGS_ERR_CAPACITY = 2,    /* an output buffer is too small */
+  TGS_ERR_CUDA = 3,        /* a CUDA launch or copy failed */
+  TGS_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+  TGS_ERR_DEVICE = 5       /* no usable sm_103 device */
+} tgs_status;
+
+/* Pinhole camera.  viewmat: row-major 4x4 world-to-camera transform with
+ * camera axes x right, y down, z forward.  fx, fy, cx, cy in pixels.  A
+ * Gaussian is culled unless its camera-space depth z > znear. */
+typedef struct {
+  float viewmat[16];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+  float znear;
+} tgs_camera;
+
+/* N Gaussians, structure of arrays (Sec. 3.1: centre, covariance via scale
+ * and rotation, opacity, colour coefficients).
+ *   means [N,3], log_scales [N,3] (scale = exp), quats [N,4] (w, x, y, z; the
+ *   rotation of q/|q|), opacity_logits [N] (opacity = sigmoid), sh [N,16,3]
+ *   (real spherical harmonics of degree <= 3, coefficient-major, RGB inner).
+ * Only the first (sh_degree+1)^2 coefficients are used. */
+typedef struct {
+  const float* means;
+  const float* log_scales;
+  const float* quats;
+  const float* opacity_logits;
+  const float* sh;
+  int64_t n;
+  int32_t sh_degree;
+} tgs_gaussians;
+
+/* Mutable arrays with the layout of tgs_gaussians (parameters, gradients,
+ * first and second moments). */
+typedef struct {
+  float* means;
+  float* log_scales;
+  float* quats;
+  float* opacity_logits;
+  float* sh;
+} tgs_param_ptrs;
+
+/* Screen-space splats, the output of the projection:
+ *   xy [N,2] centre in pixel coordinates; conic_opac [N,4] = (a, b, c, o) with
+ *   [[a, b], [b, c]] the inverse 2D covariance and o the opacity; rgb [N,3];
+ *   depth [N] camera-space z; radius [N] in pixels, 0 when culled. */
+typedef struct {
+  float* xy;
+  float* conic_opac;
+  float* rgb;
+  float* depth;
+  int32_t* radius;
+} tgs_projected;
+
+/* Split of the sampled set, in units of 1/1000 (TurboGS Table 6: hard 0.4,
+ * stable 0.3, remainder mixed). */
+typedef struct {
+  int32_t tile_hard_pm, tile_stable_pm;
+  int32_t pix_hard_pm, pix_stable_pm;
+} tgs_sampling;
+
+/* Loss constants (App. A): Charbonnier epsilon, NCC epsilon, EMA ratio beta
+ * (Table 6: 0.4). */
+typedef struct {
+  float eps_charbonnier, eps_ncc, beta;
+} tgs_loss_params;
+
+/* Hybrid solver (Sec. 3.9, App. A).  lr: means, log_scales, quats, opacity,
+ * SH DC, SH rest.  mode: 0 Adam on all parameters; 1 LM blocks with the
+ * diagonal of J^T J; 2 LM blocks with the full J^T J solved by Cholesky. */
+typedef struct {
+  float lr[6];
+  float beta1, beta2, eps_adam, eps_lm;
+  int32_t mode;
+} tgs_opt;
+
+/* Library version string and CUDA error of the last failed call (per thread). */
+const char* tgs_version(void);
+int32_t tgs_last_cuda_error(void);
+const char* tgs_status_string(int32_t status);
+
+/* Checks that the current device can run the library's sm_103a code. */
+tgs_status tgs_device_check(void);
+
+/* Number of kernel nodes in a captured CUDA graph (a cudaGraph_t passed as
+ * void*), or -1 on error; for counting the kernels one replay launches. */
+int64_t tgs_graph_count_kernels(void* graph);
+
+/*
+ * select_tiles - tile selection and tile-wise error-guided pixel sampling
+ * (Sec. 3.5, Eqs. 5-6; Alg. 1 step 3).
+ *
+ * Chooses n_sel = min(n_select, T) of the T tiles of one view, then in each
+ * chosen tile N_pix = min(n_pix, valid pixels of the tile) pixels.  Each level
+ * takes round(r_hard n) items by the error-proportional draw without
+ * replacement (pixel weight = fp16 E * 2^24, tile weight = sum over its
+ * pixels), then round(r_stable n) of the rest with the largest age (a tile's
+ * age is its smallest pixel age), then the remainder uniformly.  The draws use
+ * the counter-based SplitMix64 hash of (seed, iter, view, stream, tile, item);
+ * the weighted draw is the Efraimidis-Spirakis order of E_i / w_i with E_i an
+ * exponential variate in 32-bit fixed point.  Ties go to the lower index.
+ * Results are bit-identical on every run for the same inputs.
+ *
+ *   err_map [H,W]  fp16 error map E_v (bit patterns); negative/NaN count as 0
+ *   age_map [H,W]  uint16 age map A_v
+ *   n_pix          1..256
+ *   iter_dev       nullable device uint64: when given, the iteration number is
+ *                  read from it at run time instead of `iter` (for replays of
+ *                  a captured graph)
+ *   workspace      tgs_select_tiles_workspace_size(width, height) bytes
+ * Outputs: active_tiles [n_sel] (ascending tile ids), n_active [1],
+ * tile_rank [T] (index into active_tiles, -1 when not chosen),
+ * pix_off [n_sel+1] (prefix offsets), pix_idx [n_sel * n_pix] (local pixel
+ * indices, ascending within each tile).
+ */
+size_t tgs_select_tiles_workspace_size(int32_t width, int32_t height);
+tgs_status tgs_select_tiles(const uint16_t* err_map, const uint16_t* age_map, int32_t width, int32_t height,
+                            int32_t n_select, int32_t n_pix, const tgs_sampling* cfg, uint64_t seed,
+                            uint64_t iter, const uint64_t* iter_dev, uint32_t view, void* workspace,
+                            size_t workspace_bytes,
+                            int32_t* active_tiles, int32_t* n_active, int32_t* tile_rank, int32_t* pix_off,
+                            uint8_t* pix_idx, tgs_stream stream);
+
+/*
+ * project_gaussians - EWA projection and SH colour of the 3DGS model the
+ * method rasterizes (Sec. 3.1).
+ *
+ * Sigma = R diag(exp(2 log_scale)) R^T; camera-space centre t = W mu + T; culled
+ * unless t.z > znear; Sigma2 = J W Sigma W^T J^T + 0.3 I with the perspective
+ * Jacobian J (x/z, y/z clamped to 1.3 times the half field of view); culled
+ * unless det Sigma2 > 0; radius = ceil(3 sqrt(lambda_max)),
+ * lambda_max = m + sqrt(max(0.1, m^2 - det)), m = trace/2; culled when its
+ * 16-pixel tile rectangle (tiles k with 16k <= c + r and 16k + 16 > c - r, decided
+ * in single precision) is empty or, when tile_rank is given, holds no tile with
+ * tile_rank >= 0.  rgb = max(0, sum_k sh_k Y_k(d) + 0.5) with d the unit
+ * direction from the camera centre; opacity = sigmoid(logit).
+ * Culled Gaussians get radius 0 and zeros elsewhere.
+ */
+tgs_status tgs_project_gaussians(const tgs_gaussians* g, const tgs_camera* cam, const int32_t* tile_rank,
+                                 tgs_projected* out, tgs_stream stream);
+
+/*
+ * bin_tiles - per-tile Gaussian lists sorted by depth (Sec. 3.1, the ordered
+ * sets K(p)): every (active tile, Gaussian) pair whose tile rectangle covers
+ * the tile, ordered by (tile, depth, Gaussian id), as a device radix sort of
+ * (tile | depth) keys.
+ *
+ *   proj        xy, depth, radius of the projection (radius 0 = skip)
+ *   tile_rank   [T] active-tile index or -1 (NULL: every tile active, rank = id)
+ *   n_active_max  number of ranks (T when tile_rank is NULL)
+ *   capacity    length of vals / keys
+ * Outputs: vals [capacity] Gaussian ids in order; keys [capacity] (nullable)
+ * = tile id << 32 | float bits of depth; tile_ranges [n_active_max, 2]
+ * half-open [start, end) per rank; n_isect [1] = number of pairs.  If
+ * n_isect > capacity only the first `capacity` pairs in emission order are
+ * kept, the sort and ranges are then invalid: the caller checks n_isect and
+ * retries with more capacity.
+ */
+size_t tgs_bin_tiles_workspace_size(int64_t n, int64_t capacity, int32_t n_active_max);
+tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const tgs_camera* cam, const int32_t* tile_rank,
+                         int32_t n_active_max, void* workspace, size_t workspace_bytes, int64_t capacity,
+                         int32_t* vals, uint64_t* keys, int32_t* tile_ranges, int64_t* n_isect, tgs_stream stream);
+
+/*
+ * render_sampled - sparse forward rasterization (Sec. 3.6, Eq. 1; Alg. 1
+ * step 5): for every sampled pixel of every active tile, front-to-back
+ * compositing over the tile's list: alpha = min(0.99, o exp(power)),
+ * power = -(a dx^2 + c dy^2)/2 - b dx dy at the pixel centre; splats with
+ * power > 0 or alpha < 1/255 are skipped; the walk stops before the splat
+ * that would take the transmittance below 1e-4.
+ *
+ *   active_tiles / n_active / pix_off / pix_idx   as from select_tiles
+ *   n_active_max, n_pix_max   host-side bounds (grid and block sizes)
+ *   bg [3]  host array, background colour
+ * Outputs per sampled pixel s (tile order): rgb [P,3] = sum T alpha c + T bg,
+ * T_final [P], n_last [P] = 1 + position in the tile list of the last splat
+ * blended (0 if none).
+ */
+tgs_status tgs_render_sampled(const tgs_projected* proj, const int32_t* tile_ranges, const int32_t* vals,
+                              const int32_t* active_tiles, const int32_t* n_active, int32_t n_active_max,
+                              const int32_t* pix_off, const uint8_t* pix_idx, int32_t n_pix_max,
+                              const tgs_camera* cam, const float* bg, float* rgb, float* T_final,
+                              int32_t* n_last, tgs_stream stream);
+
+/*
+ * loss_sparse_ncc - fused sparse supervision (Sec. 3.7, Eq. 8; App. A;
+ * Alg. 1 steps 4, 6, 7), one thread block per active tile:
+ *   l1(p) = sum_c sqrt((x - y)^2 + eps_c^2);
+ *   NCC_c = cov / sqrt(var_x var_y + eps_n) over the tile's sampled pixels;
+ *   lambda_tau = clip(mean_p |dl1/dx|_1 / (mean_p |n dNCC/dx|_1 + 1e-8), 0, 1);
+ *   L = (1/P) sum_p l1(p) + (1/A) sum_tau lambda_tau (1 - mean_c NCC_c),
+ *   lambda held constant in the gradient.
+ * Writes dL_drgb [P,3], lambda_tile [n_active], err_pix [P] = sum_c |x - y|
+ * (Eq. 2) and *loss (device double, overwritten).  When given, updates the
+ * error map E <- fp16((1 - beta) E + beta e) at sampled pixels (Eq. 3) and the
+ * age map A <- A + 1 (saturating at 65535) at every pixel, 0 at sampled
+ * pixels (Eq. 4).  target [H,W,3] float.
+ */
+tgs_status tgs_loss_sparse_ncc(const float* rgb, const float* target, int32_t width, int32_t height,
+                               const int32_t* active_tiles, const int32_t* n_active, int32_t n_active_max,
+                               const int32_t* pix_off, const uint8_t* pix_idx, int32_t n_pix_max,
+                               const tgs_loss_params* params, uint16_t* err_map, uint16_t* age_map,
+                               float* dL_drgb, float* lambda_tile, float* err_pix, double* loss,
+                               tgs_stream stream);
+
+/*
+ * backward_sampled - sparse backward (Sec. 3.6; Alg. 1 step 8).  Replays each
+ * sampled pixel's compositing in reverse from T_final and n_last, recovering
+ * T_k = T_{k+1} / (1 - alpha_k), and accumulates the adjoints of the screen-
+ * space splats (dL/dc_k = T_k alpha_k g, dL/dalpha_k = T_k (c_k - S_{k+1}) . g
+ * with S the colour seen behind), reduced across each warp with shuffles
+ * before one vector atomic per warp and splat, into grad2d [N,12]
+ * (caller scratch, zeroed here): (dx, dy, da, db | dc, dopacity, dr, dg |
+ * db(blue), 0, 0, 0).  Then the projection adjoint maps it to gradients of
+ * the parameters (grads, layout of tgs_gaussians) and touched [N] = 1 where
+ * grad2d is not all zero.  write_untouched = 0 leaves grads of untouched
+ * Gaussians unwritten; 1 writes zeros there.
+ */
+tgs_status tgs_backward_sampled(const tgs_gaussians* g, const tgs_camera* cam, const tgs_projected* proj,
+                                const int32_t* tile_ranges, const int32_t* vals, const int32_t* active_tiles,
+                                const int32_t* n_active, int32_t n_active_max, const int32_t* pix_off,
+                                const uint8_t* pix_idx, int32_t n_pix_max, const float* bg, const float* T_final,
+                                const int32_t* n_last, const float* dL_drgb, float* grad2d,
+                                const tgs_param_ptrs* grads, uint8_t* touched, int32_t write_untouched,
+                                tgs_stream stream);
+
+/*
+ * hybrid_step - moment-damped LM / Adam update (Sec. 3.9, Eq. 11; App. A;
+ * Alg. 1 steps 9, 10) of the Gaussians with touched[i] != 0.
+ * m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2 on every parameter; the
+ * geometry block (means, log_scales, quats: 10) and the appearance block (SH
+ * DC rgb, opacity: 4) each solve (J^T J + diag(sqrt(v) + eps_lm)) D = -m
+ * (mode 1: diagonal of J^T J; mode 2: full, Cholesky) and add lr * D; J is
+ * view_rows [k_rows, N, 14] (geometry 10, then DC r g b and opacity), or the
+ * gradient itself when view_rows is NULL.  The 45 higher SH coefficients (and
+ * everything in mode 0) take the bias-corrected Adam step
+ * -lr m_hat / (sqrt(v_hat) + eps_adam) at step `step` (>= 1), or, when
+ * step_dev (device int32) is given, at the step read from it at run time.
+ */
+tgs_status tgs_hybrid_step(const tgs_param_ptrs* params, const tgs_param_ptrs* grads, const tgs_param_ptrs* m,
+                           const tgs_param_ptrs* v, int64_t n, const uint8_t* touched, const float* view_rows,
+                           int32_t k_rows, int32_t step, const int32_t* step_dev, const tgs_opt* opt,
+                           tgs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TURBOGS_H */

@@ -212,13 +212,14 @@ static void rect_axis(double c, int r, int ntiles, int* lo, int* hi) {
   *hi = (int)b;
 }
 
-/* distance of the single-precision rect decision to its switching points,
- * relative to the coordinate magnitude (diagnostic for parity tests) */
+/* distance in pixels of the single-precision rect decision to its switching
+ * points, scaled so that 1e-4 is ~100 times the single-precision error of the
+ * centre coordinate (diagnostic for parity tests) */
 static double rect_margin(double c, int r) {
   double a = (c - r) / 16.0, b = (c + r) / 16.0;
   double da = fabs(a - floor(a + 0.5)), db = fabs(b - floor(b + 0.5));
   double m = (da < db ? da : db) * 16.0;
-  return m / (fabs(c) + r + 1.0);
+  return m / (10.0 + 0.1 * (fabs(c) + r));
 }
 
 /* ------------------------------------------------------------------------ */
@@ -723,12 +724,9 @@ static void trace_pixel(int64_t n, const double* xy, const double* conic, const 
   p->clamped = (int*)malloc(sizeof(int) * m);
   double cxp = px + 0.5, cyp = py + 0.5;
   double T = 1.0;
+  double prev_depth = -INFINITY;   /* depth of the last splat blended */
   for (int k = 0; k < p->n_cand; ++k) {
     int i = p->cand[k].id;
-    if (k > 0) {
-      double d0 = p->cand[k - 1].depth, d1 = p->cand[k].depth;
-      p->margin = minabs(p->margin, (d1 - d0) / (fabs(d1) + 1e-30) * 1e2);
-    }
     double dx = cxp - xy[2 * i], dy = cyp - xy[2 * i + 1];
     double a = conic[3 * i], b = conic[3 * i + 1], c = conic[3 * i + 2];
     double power = -0.5 * (a * dx * dx + c * dy * dy) - b * dx * dy;
@@ -739,9 +737,16 @@ static void trace_pixel(int64_t n, const double* xy, const double* conic, const 
     p->margin = minabs(p->margin, fabs(alpha * 255.0 - 1.0));
     p->margin = minabs(p->margin, fabs(araw - 0.99) / 0.99);
     if (alpha < 1.0 / 255.0) continue;
+    /* order of two blended splats of almost equal depth is a discrete
+       decision too (exact ties are ordered by id on both sides) */
+    {
+      double d1 = p->cand[k].depth;
+      if (d1 > prev_depth) p->margin = minabs(p->margin, (d1 - prev_depth) / (fabs(d1) + 1e-30) * 1e2);
+    }
     double Tn = T * (1.0 - alpha);
     p->margin = minabs(p->margin, fabs(Tn - 1e-4) / 1e-4);
     if (Tn < 1e-4) break;
+    prev_depth = p->cand[k].depth;
     int j = p->n_acc++;
     p->acc_id[j] = i; p->acc_pos[j] = k;
     p->T[j] = T; p->alpha[j] = alpha; p->G[j] = G; p->dx[j] = dx; p->dy[j] = dy;

@@ -1,0 +1,260 @@
+"""Python binding of the C ABI in include/turbogs.h (argument marshalling only).
+
+Every function here has the name of the C entry point without its ``tgs_``
+prefix, takes torch CUDA tensors (contiguous, of the dtype and shape the header
+states) and launches on the current torch stream unless one is given.  All the
+arithmetic runs in ``libturbogs.so``; importing this module loads it and raises
+if it is missing - there is no other implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libturbogs.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libturbogs.so not found at {LIB_PATH}: build it with "
+                      "`python -m paper_2606_15924_gb300.build` (needs nvcc)")
+_lib = C.CDLL(LIB_PATH)
+
+OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CUDA, ERR_TIMEOUT, ERR_DEVICE = range(6)
+
+
+class TgsError(RuntimeError):
+    def __init__(self, fn, status):
+        msg = _lib.tgs_status_string(status).decode()
+        if status == ERR_CUDA:
+            msg += f" (cudaError {_lib.tgs_last_cuda_error()})"
+        super().__init__(f"{fn}: {msg}")
+        self.status = status
+
+
+# ----------------------------------------------------------------------------
+# structs
+# ----------------------------------------------------------------------------
+
+class Camera(C.Structure):
+    _fields_ = [("viewmat", C.c_float * 16), ("fx", C.c_float), ("fy", C.c_float), ("cx", C.c_float),
+                ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32), ("znear", C.c_float)]
+
+
+class Gaussians(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p), ("n", C.c_int64), ("sh_degree", C.c_int32)]
+
+
+class ParamPtrs(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
+
+
+class Projected(C.Structure):
+    _fields_ = [("xy", C.c_void_p), ("conic_opac", C.c_void_p), ("rgb", C.c_void_p), ("depth", C.c_void_p),
+                ("radius", C.c_void_p)]
+
+
+class Sampling(C.Structure):
+    _fields_ = [("tile_hard_pm", C.c_int32), ("tile_stable_pm", C.c_int32), ("pix_hard_pm", C.c_int32),
+                ("pix_stable_pm", C.c_int32)]
+
+
+class LossParams(C.Structure):
+    _fields_ = [("eps_charbonnier", C.c_float), ("eps_ncc", C.c_float), ("beta", C.c_float)]
+
+
+class Opt(C.Structure):
+    _fields_ = [("lr", C.c_float * 6), ("beta1", C.c_float), ("beta2", C.c_float), ("eps_adam", C.c_float),
+                ("eps_lm", C.c_float), ("mode", C.c_int32)]
+
+
+_p = C.c_void_p
+_i32 = C.c_int32
+_i64 = C.c_int64
+_u64 = C.c_uint64
+_u32 = C.c_uint32
+_sz = C.c_size_t
+_P = C.POINTER
+
+_lib.tgs_version.restype = C.c_char_p
+_lib.tgs_status_string.restype = C.c_char_p
+_lib.tgs_status_string.argtypes = [_i32]
+_lib.tgs_last_cuda_error.restype = _i32
+_lib.tgs_device_check.restype = _i32
+_lib.tgs_graph_count_kernels.restype = _i64
+_lib.tgs_graph_count_kernels.argtypes = [_p]
+_lib.tgs_select_tiles_workspace_size.restype = _sz
+_lib.tgs_select_tiles_workspace_size.argtypes = [_i32, _i32]
+_lib.tgs_select_tiles.restype = _i32
+_lib.tgs_select_tiles.argtypes = [_p, _p, _i32, _i32, _i32, _i32, _P(Sampling), _u64, _u64, _p, _u32, _p, _sz,
+                                  _p, _p, _p, _p, _p, _p]
+_lib.tgs_project_gaussians.restype = _i32
+_lib.tgs_project_gaussians.argtypes = [_P(Gaussians), _P(Camera), _p, _P(Projected), _p]
+_lib.tgs_bin_tiles_workspace_size.restype = _sz
+_lib.tgs_bin_tiles_workspace_size.argtypes = [_i64, _i64, _i32]
+_lib.tgs_bin_tiles.restype = _i32
+_lib.tgs_bin_tiles.argtypes = [_P(Projected), _i64, _P(Camera), _p, _i32, _p, _sz, _i64, _p, _p, _p, _p, _p]
+_lib.tgs_render_sampled.restype = _i32
+_lib.tgs_render_sampled.argtypes = [_P(Projected), _p, _p, _p, _p, _i32, _p, _p, _i32, _P(Camera), _p, _p, _p,
+                                    _p, _p]
+_lib.tgs_loss_sparse_ncc.restype = _i32
+_lib.tgs_loss_sparse_ncc.argtypes = [_p, _p, _i32, _i32, _p, _p, _i32, _p, _p, _i32, _P(LossParams), _p, _p, _p,
+                                     _p, _p, _p, _p]
+_lib.tgs_backward_sampled.restype = _i32
+_lib.tgs_backward_sampled.argtypes = [_P(Gaussians), _P(Camera), _P(Projected), _p, _p, _p, _p, _i32, _p, _p,
+                                      _i32, _p, _p, _p, _p, _p, _P(ParamPtrs), _p, _i32, _p]
+_lib.tgs_hybrid_step.restype = _i32
+_lib.tgs_hybrid_step.argtypes = [_P(ParamPtrs), _P(ParamPtrs), _P(ParamPtrs), _P(ParamPtrs), _i64, _p, _p, _i32,
+                                 _i32, _p, _P(Opt), _p]
+
+EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_device_check", "tgs_graph_count_kernels",
+            "tgs_select_tiles_workspace_size", "tgs_select_tiles", "tgs_project_gaussians",
+            "tgs_bin_tiles_workspace_size", "tgs_bin_tiles", "tgs_render_sampled", "tgs_loss_sparse_ncc",
+            "tgs_backward_sampled", "tgs_hybrid_step"]
+
+
+def _check(fn, status):
+    if status != OK:
+        raise TgsError(fn, status)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def version() -> str:
+    return _lib.tgs_version().decode()
+
+
+def graph_count_kernels(graph) -> int:
+    """Kernel nodes in a captured torch.cuda.CUDAGraph."""
+    return int(_lib.tgs_graph_count_kernels(C.c_void_p(graph.raw_cuda_graph())))
+
+
+def device_check() -> None:
+    _check("tgs_device_check", _lib.tgs_device_check())
+
+
+def camera(cam: dict) -> Camera:
+    c = Camera()
+    vm = [float(v) for v in torch.as_tensor(cam["viewmat"], dtype=torch.float64).reshape(16).tolist()]
+    c.viewmat = (C.c_float * 16)(*vm)
+    c.fx, c.fy, c.cx, c.cy = float(cam["fx"]), float(cam["fy"]), float(cam["cx"]), float(cam["cy"])
+    c.width, c.height = int(cam["width"]), int(cam["height"])
+    c.znear = float(cam.get("znear", 0.2))
+    return c
+
+
+def gaussians(g: dict, sh_degree: int = 3) -> Gaussians:
+    return Gaussians(_ptr(g["means"]), _ptr(g["log_scales"]), _ptr(g["quats"]), _ptr(g["opacity_logits"]),
+                     _ptr(g["sh"]), int(g["means"].shape[0]), int(sh_degree))
+
+
+def param_ptrs(g: dict) -> ParamPtrs:
+    return ParamPtrs(_ptr(g["means"]), _ptr(g["log_scales"]), _ptr(g["quats"]), _ptr(g["opacity_logits"]),
+                     _ptr(g["sh"]))
+
+
+def projected(p: dict) -> Projected:
+    return Projected(_ptr(p["xy"]), _ptr(p["conic_opac"]), _ptr(p["rgb"]), _ptr(p["depth"]), _ptr(p["radius"]))
+
+
+# ----------------------------------------------------------------------------
+# entry points
+# ----------------------------------------------------------------------------
+
+def select_tiles_workspace_size(width: int, height: int) -> int:
+    return int(_lib.tgs_select_tiles_workspace_size(width, height))
+
+
+def select_tiles(err_map, age_map, width, height, n_select, n_pix, sampling, seed, it, view, workspace,
+                 active_tiles, n_active, tile_rank, pix_off, pix_idx, stream=None, iter_dev=None):
+    cfg = Sampling(*sampling)
+    _check("tgs_select_tiles", _lib.tgs_select_tiles(
+        _ptr(err_map), _ptr(age_map), int(width), int(height), int(n_select), int(n_pix), C.byref(cfg),
+        int(seed) & (2**64 - 1), int(it) & (2**64 - 1), _ptr(iter_dev), int(view), _ptr(workspace),
+        workspace.numel(),
+        _ptr(active_tiles), _ptr(n_active), _ptr(tile_rank), _ptr(pix_off), _ptr(pix_idx), _stream(stream)))
+
+
+def project_gaussians(g: dict, cam, tile_rank, out: dict, sh_degree=3, stream=None):
+    gs = gaussians(g, sh_degree)
+    cc = cam if isinstance(cam, Camera) else camera(cam)
+    pr = projected(out)
+    _check("tgs_project_gaussians", _lib.tgs_project_gaussians(C.byref(gs), C.byref(cc), _ptr(tile_rank),
+                                                               C.byref(pr), _stream(stream)))
+
+
+def bin_tiles_workspace_size(n: int, capacity: int, n_active_max: int) -> int:
+    return int(_lib.tgs_bin_tiles_workspace_size(int(n), int(capacity), int(n_active_max)))
+
+
+def bin_tiles(proj: dict, n, cam, tile_rank, n_active_max, workspace, capacity, vals, keys, tile_ranges, n_isect,
+              stream=None):
+    pr = projected(proj)
+    cc = cam if isinstance(cam, Camera) else camera(cam)
+    _check("tgs_bin_tiles", _lib.tgs_bin_tiles(
+        C.byref(pr), int(n), C.byref(cc), _ptr(tile_rank), int(n_active_max), _ptr(workspace), workspace.numel(),
+        int(capacity), _ptr(vals), _ptr(keys), _ptr(tile_ranges), _ptr(n_isect), _stream(stream)))
+
+
+def render_sampled(proj: dict, tile_ranges, vals, active_tiles, n_active, n_active_max, pix_off, pix_idx,
+                   n_pix_max, cam, bg, rgb, T_final, n_last, stream=None):
+    pr = projected(proj)
+    cc = cam if isinstance(cam, Camera) else camera(cam)
+    bgv = (C.c_float * 3)(*[float(b) for b in bg])
+    _check("tgs_render_sampled", _lib.tgs_render_sampled(
+        C.byref(pr), _ptr(tile_ranges), _ptr(vals), _ptr(active_tiles), _ptr(n_active), int(n_active_max),
+        _ptr(pix_off), _ptr(pix_idx), int(n_pix_max), C.byref(cc), bgv, _ptr(rgb), _ptr(T_final), _ptr(n_last),
+        _stream(stream)))
+
+
+def loss_sparse_ncc(rgb, target, width, height, active_tiles, n_active, n_active_max, pix_off, pix_idx, n_pix_max,
+                    loss_params, err_map, age_map, dL_drgb, lambda_tile, err_pix, loss, stream=None):
+    lp = LossParams(*[float(v) for v in loss_params])
+    _check("tgs_loss_sparse_ncc", _lib.tgs_loss_sparse_ncc(
+        _ptr(rgb), _ptr(target), int(width), int(height), _ptr(active_tiles), _ptr(n_active), int(n_active_max),
+        _ptr(pix_off), _ptr(pix_idx), int(n_pix_max), C.byref(lp), _ptr(err_map), _ptr(age_map), _ptr(dL_drgb),
+        _ptr(lambda_tile), _ptr(err_pix), _ptr(loss), _stream(stream)))
+
+
+def backward_sampled(g: dict, cam, proj: dict, tile_ranges, vals, active_tiles, n_active, n_active_max, pix_off,
+                     pix_idx, n_pix_max, bg, T_final, n_last, dL_drgb, grad2d, grads: dict, touched,
+                     write_untouched=True, sh_degree=3, stream=None):
+    gs = gaussians(g, sh_degree)
+    cc = cam if isinstance(cam, Camera) else camera(cam)
+    pr = projected(proj)
+    gp = param_ptrs(grads)
+    bgv = (C.c_float * 3)(*[float(b) for b in bg])
+    _check("tgs_backward_sampled", _lib.tgs_backward_sampled(
+        C.byref(gs), C.byref(cc), C.byref(pr), _ptr(tile_ranges), _ptr(vals), _ptr(active_tiles), _ptr(n_active),
+        int(n_active_max), _ptr(pix_off), _ptr(pix_idx), int(n_pix_max), bgv, _ptr(T_final), _ptr(n_last),
+        _ptr(dL_drgb), _ptr(grad2d), C.byref(gp), _ptr(touched), 1 if write_untouched else 0, _stream(stream)))
+
+
+def hybrid_step(params: dict, grads: dict, m: dict, v: dict, n, touched, view_rows, k_rows, step, opt,
+                stream=None, step_dev=None):
+    P, G, M, V = param_ptrs(params), param_ptrs(grads), param_ptrs(m), param_ptrs(v)
+    o = Opt()
+    lrs = opt["lr"]
+    o.lr = (C.c_float * 6)(*[float(x) for x in lrs])
+    o.beta1, o.beta2 = float(opt["beta1"]), float(opt["beta2"])
+    o.eps_adam, o.eps_lm = float(opt["eps_adam"]), float(opt["eps_lm"])
+    o.mode = int(opt["mode"])
+    _check("tgs_hybrid_step", _lib.tgs_hybrid_step(
+        C.byref(P), C.byref(G), C.byref(M), C.byref(V), int(n), _ptr(touched), _ptr(view_rows), int(k_rows),
+        int(step), _ptr(step_dev), C.byref(o), _stream(stream)))

@@ -1,0 +1,451 @@
+// EWA projection with SH colour (the 3DGS forward model TurboGS rasterizes,
+// Sec. 3.1) and its adjoint.  One thread per Gaussian; SH coefficients and
+// quaternions move as float4; a Gaussian that misses every active tile is
+// culled before its SH block is read.
+#include "tgs_common.cuh"
+
+namespace tgs {
+
+struct CamK {
+  float W[9], t[3], campos[3];
+  float fx, fy, cx, cy, znear, limx, limy;
+  int width, height, tx, ty;
+};
+
+static CamK make_cam(const tgs_camera& c) {
+  CamK k;
+  for (int r = 0; r < 3; ++r) {
+    for (int j = 0; j < 3; ++j) k.W[r * 3 + j] = c.viewmat[r * 4 + j];
+    k.t[r] = c.viewmat[r * 4 + 3];
+  }
+  for (int j = 0; j < 3; ++j) {
+    double s = 0.0;
+    for (int r = 0; r < 3; ++r) s += (double)c.viewmat[r * 4 + j] * (double)c.viewmat[r * 4 + 3];
+    k.campos[j] = (float)(-s);
+  }
+  k.fx = c.fx; k.fy = c.fy; k.cx = c.cx; k.cy = c.cy; k.znear = c.znear;
+  k.limx = (float)(1.3 * (0.5 * c.width / (double)c.fx));
+  k.limy = (float)(1.3 * (0.5 * c.height / (double)c.fy));
+  k.width = c.width; k.height = c.height;
+  k.tx = tiles_x(c.width); k.ty = tiles_y(c.height);
+  return k;
+}
+
+// Real spherical harmonics of degree <= 3 (Condon-Shortley phase), m = -l..l
+// ordered, as polynomials of the unit direction.
+#define SH_C0 0.28209479177387814f
+#define SH_C1 0.4886025119029199f
+__constant__ float kSH2[5] = {1.0925484305920792f, -1.0925484305920792f, 0.31539156525252005f,
+                              -1.0925484305920792f, 0.5462742152960396f};
+__constant__ float kSH3[7] = {-0.5900435899266435f, 2.890611442640554f, -0.4570457994644658f,
+                              0.3731763325901154f, -0.4570457994644658f, 1.445305721320277f,
+                              -0.5900435899266435f};
+
+__device__ __forceinline__ void sh_basis(float x, float y, float z, int deg, float Y[16]) {
+  Y[0] = SH_C0;
+  if (deg < 1) return;
+  Y[1] = -SH_C1 * y; Y[2] = SH_C1 * z; Y[3] = -SH_C1 * x;
+  if (deg < 2) return;
+  float xx = x * x, yy = y * y, zz = z * z;
+  Y[4] = kSH2[0] * x * y;
+  Y[5] = kSH2[1] * y * z;
+  Y[6] = kSH2[2] * (2.f * zz - xx - yy);
+  Y[7] = kSH2[3] * x * z;
+  Y[8] = kSH2[4] * (xx - yy);
+  if (deg < 3) return;
+  Y[9] = kSH3[0] * y * (3.f * xx - yy);
+  Y[10] = kSH3[1] * x * y * z;
+  Y[11] = kSH3[2] * y * (4.f * zz - xx - yy);
+  Y[12] = kSH3[3] * z * (2.f * zz - 3.f * xx - 3.f * yy);
+  Y[13] = kSH3[4] * x * (4.f * zz - xx - yy);
+  Y[14] = kSH3[5] * z * (xx - yy);
+  Y[15] = kSH3[6] * x * (xx - 3.f * yy);
+}
+
+// gradient of sum_k s_k Y_k with respect to the (unnormalised) polynomial argument
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, int deg, const float s[16], float g[3]) {
+  g[0] = g[1] = g[2] = 0.f;
+  if (deg < 1) return;
+  g[0] += -SH_C1 * s[3]; g[1] += -SH_C1 * s[1]; g[2] += SH_C1 * s[2];
+  if (deg < 2) return;
+  float xx = x * x, yy = y * y, zz = z * z;
+  g[0] += kSH2[0] * y * s[4] + kSH2[3] * z * s[7] - 2.f * kSH2[2] * x * s[6] + 2.f * kSH2[4] * x * s[8];
+  g[1] += kSH2[0] * x * s[4] + kSH2[1] * z * s[5] - 2.f * kSH2[2] * y * s[6] - 2.f * kSH2[4] * y * s[8];
+  g[2] += kSH2[1] * y * s[5] + 4.f * kSH2[2] * z * s[6] + kSH2[3] * x * s[7];
+  if (deg < 3) return;
+  g[0] += kSH3[0] * 6.f * x * y * s[9] + kSH3[1] * y * z * s[10] - 2.f * kSH3[2] * x * y * s[11] -
+          6.f * kSH3[3] * x * z * s[12] + kSH3[4] * (4.f * zz - 3.f * xx - yy) * s[13] +
+          2.f * kSH3[5] * x * z * s[14] + kSH3[6] * (3.f * xx - 3.f * yy) * s[15];
+  g[1] += kSH3[0] * (3.f * xx - 3.f * yy) * s[9] + kSH3[1] * x * z * s[10] +
+          kSH3[2] * (4.f * zz - xx - 3.f * yy) * s[11] - 6.f * kSH3[3] * y * z * s[12] -
+          2.f * kSH3[4] * x * y * s[13] - 2.f * kSH3[5] * y * z * s[14] - 6.f * kSH3[6] * x * y * s[15];
+  g[2] += kSH3[1] * x * y * s[10] + 8.f * kSH3[2] * y * z * s[11] +
+          kSH3[3] * (6.f * zz - 3.f * xx - 3.f * yy) * s[12] + 8.f * kSH3[4] * x * z * s[13] +
+          kSH3[5] * (xx - yy) * s[14];
+}
+
+// Geometry of one Gaussian up to the conic (everything but colour).
+struct Geo {
+  float pc[3];
+  float q[4], qnorm, R[9], s[3];
+  float Sig[6];  // xx xy xz yy yz zz
+  float T[6];    // J W, 2x3
+  bool clampx, clampy;
+  float A, B, C, det;
+  float conic[3];
+  int radius;
+  float xy[2];
+};
+
+// Returns false when culled by depth or determinant.
+__device__ __forceinline__ bool geometry(const CamK& cam, float3 mu, float3 ls, float4 qr, Geo& g) {
+  g.pc[0] = cam.W[0] * mu.x + cam.W[1] * mu.y + cam.W[2] * mu.z + cam.t[0];
+  g.pc[1] = cam.W[3] * mu.x + cam.W[4] * mu.y + cam.W[5] * mu.z + cam.t[1];
+  g.pc[2] = cam.W[6] * mu.x + cam.W[7] * mu.y + cam.W[8] * mu.z + cam.t[2];
+  const float z = g.pc[2];
+  if (!(z > cam.znear)) return false;
+  g.qnorm = sqrtf(qr.x * qr.x + qr.y * qr.y + qr.z * qr.z + qr.w * qr.w);
+  const float iq = 1.f / g.qnorm;
+  const float w = qr.x * iq, x = qr.y * iq, y = qr.z * iq, zq = qr.w * iq;
+  g.q[0] = w; g.q[1] = x; g.q[2] = y; g.q[3] = zq;
+  float* R = g.R;
+  R[0] = 1.f - 2.f * (y * y + zq * zq); R[1] = 2.f * (x * y - w * zq);       R[2] = 2.f * (x * zq + w * y);
+  R[3] = 2.f * (x * y + w * zq);       R[4] = 1.f - 2.f * (x * x + zq * zq); R[5] = 2.f * (y * zq - w * x);
+  R[6] = 2.f * (x * zq - w * y);       R[7] = 2.f * (y * zq + w * x);       R[8] = 1.f - 2.f * (x * x + y * y);
+  g.s[0] = expf(ls.x); g.s[1] = expf(ls.y); g.s[2] = expf(ls.z);
+  float M[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) M[r * 3 + c] = R[r * 3 + c] * g.s[c];
+  g.Sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+  g.Sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+  g.Sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+  g.Sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+  g.Sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+  g.Sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
+  const float iz = 1.f / z;
+  const float xz = g.pc[0] * iz, yz = g.pc[1] * iz;
+  g.clampx = (xz < -cam.limx) || (xz > cam.limx);
+  g.clampy = (yz < -cam.limy) || (yz > cam.limy);
+  const float txz = fminf(fmaxf(xz, -cam.limx), cam.limx);
+  const float tyz = fminf(fmaxf(yz, -cam.limy), cam.limy);
+  const float J00 = cam.fx * iz, J02 = -cam.fx * txz * iz, J11 = cam.fy * iz, J12 = -cam.fy * tyz * iz;
+  // T = J W
+  g.T[0] = J00 * cam.W[0] + J02 * cam.W[6];
+  g.T[1] = J00 * cam.W[1] + J02 * cam.W[7];
+  g.T[2] = J00 * cam.W[2] + J02 * cam.W[8];
+  g.T[3] = J11 * cam.W[3] + J12 * cam.W[6];
+  g.T[4] = J11 * cam.W[4] + J12 * cam.W[7];
+  g.T[5] = J11 * cam.W[5] + J12 * cam.W[8];
+  const float* S = g.Sig;
+  // U = T Sigma (2x3)
+  float U0 = g.T[0] * S[0] + g.T[1] * S[1] + g.T[2] * S[2];
+  float U1 = g.T[0] * S[1] + g.T[1] * S[3] + g.T[2] * S[4];
+  float U2 = g.T[0] * S[2] + g.T[1] * S[4] + g.T[2] * S[5];
+  float U3 = g.T[3] * S[0] + g.T[4] * S[1] + g.T[5] * S[2];
+  float U4 = g.T[3] * S[1] + g.T[4] * S[3] + g.T[5] * S[4];
+  float U5 = g.T[3] * S[2] + g.T[4] * S[4] + g.T[5] * S[5];
+  g.A = U0 * g.T[0] + U1 * g.T[1] + U2 * g.T[2] + 0.3f;
+  g.B = U0 * g.T[3] + U1 * g.T[4] + U2 * g.T[5];
+  g.C = U3 * g.T[3] + U4 * g.T[4] + U5 * g.T[5] + 0.3f;
+  g.det = g.A * g.C - g.B * g.B;
+  if (!(g.det > 0.f)) return false;
+  const float idet = 1.f / g.det;
+  g.conic[0] = g.C * idet; g.conic[1] = -g.B * idet; g.conic[2] = g.A * idet;
+  const float mid = 0.5f * (g.A + g.C);
+  const float lam = mid + sqrtf(fmaxf(0.1f, mid * mid - g.det));
+  g.radius = (int)ceilf(3.f * sqrtf(lam));
+  g.xy[0] = cam.fx * g.pc[0] * iz + cam.cx;
+  g.xy[1] = cam.fy * g.pc[1] * iz + cam.cy;
+  return true;
+}
+
+// Tile rectangle non-empty and (with a mask) holding an active tile.
+__device__ __forceinline__ bool touches_active(const CamK& cam, const float xy[2], int radius,
+                                               const int32_t* __restrict__ tile_rank) {
+  int x0, x1, y0, y1;
+  tile_span(xy[0], radius, cam.tx, x0, x1);
+  tile_span(xy[1], radius, cam.ty, y0, y1);
+  if ((x1 - x0) * (y1 - y0) == 0) return false;
+  if (!tile_rank) return true;
+  for (int ty = y0; ty < y1; ++ty)
+    for (int tx = x0; tx < x1; ++tx)
+      if (__ldg(tile_rank + ty * cam.tx + tx) >= 0) return true;
+  return false;
+}
+
+__global__ void __launch_bounds__(256) k_project(
+    const float* __restrict__ means, const float* __restrict__ log_scales, const float4* __restrict__ quats,
+    const float* __restrict__ ologit, const float4* __restrict__ sh, int64_t n, int sh_degree, CamK cam,
+    const int32_t* __restrict__ tile_rank, float2* __restrict__ xy_out, float4* __restrict__ conic_out,
+    float* __restrict__ rgb_out, float* __restrict__ depth_out, int32_t* __restrict__ radius_out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float3 mu = make_float3(means[3 * i], means[3 * i + 1], means[3 * i + 2]);
+  float3 ls = make_float3(log_scales[3 * i], log_scales[3 * i + 1], log_scales[3 * i + 2]);
+  float4 qr = quats[i];
+  Geo g;
+  bool vis = geometry(cam, mu, ls, qr, g) && touches_active(cam, g.xy, g.radius, tile_rank);
+  if (!vis) {
+    xy_out[i] = make_float2(0.f, 0.f);
+    conic_out[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    rgb_out[3 * i] = 0.f; rgb_out[3 * i + 1] = 0.f; rgb_out[3 * i + 2] = 0.f;
+    depth_out[i] = 0.f;
+    radius_out[i] = 0;
+    return;
+  }
+  // colour from SH in the viewing direction
+  float dx = mu.x - cam.campos[0], dy = mu.y - cam.campos[1], dz = mu.z - cam.campos[2];
+  float il = rsqrtf(dx * dx + dy * dy + dz * dz);
+  dx *= il; dy *= il; dz *= il;
+  float Y[16];
+  sh_basis(dx, dy, dz, sh_degree, Y);
+  const int nb = (sh_degree + 1) * (sh_degree + 1);
+  const float4* shp = sh + 12 * i;
+  float acc[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+  for (int k4 = 0; k4 < 12; ++k4) {
+    if (4 * k4 >= 3 * nb) break;
+    float4 v = shp[k4];
+    float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      int f = 4 * k4 + j;  // flat index k * 3 + c
+      int k = f / 3, c = f - 3 * k;
+      if (k < nb) acc[c] += e[j] * Y[k];
+    }
+  }
+  xy_out[i] = make_float2(g.xy[0], g.xy[1]);
+  conic_out[i] = make_float4(g.conic[0], g.conic[1], g.conic[2], 1.f / (1.f + expf(-ologit[i])));
+  rgb_out[3 * i] = fmaxf(acc[0], 0.f);
+  rgb_out[3 * i + 1] = fmaxf(acc[1], 0.f);
+  rgb_out[3 * i + 2] = fmaxf(acc[2], 0.f);
+  depth_out[i] = g.pc[2];
+  radius_out[i] = g.radius;
+}
+
+// Adjoint of the projection.  grad2d rows: (dx, dy, da, db | dc, do, dr, dg | db, -, -, -).
+__global__ void __launch_bounds__(256) k_project_bwd(
+    const float* __restrict__ means, const float* __restrict__ log_scales, const float4* __restrict__ quats,
+    const float* __restrict__ ologit, const float4* __restrict__ sh, int64_t n, int sh_degree, CamK cam,
+    const int32_t* __restrict__ radius, const float4* __restrict__ grad2d, float* __restrict__ g_means,
+    float* __restrict__ g_ls, float4* __restrict__ g_quats, float* __restrict__ g_ologit, float4* __restrict__ g_sh,
+    uint8_t* __restrict__ touched, int write_untouched) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga, gc = ga;
+  const bool vis = radius[i] > 0;
+  if (vis) {
+    ga = grad2d[3 * i];
+    gb = grad2d[3 * i + 1];
+    gc = grad2d[3 * i + 2];
+  }
+  const bool any = vis && (ga.x != 0.f || ga.y != 0.f || ga.z != 0.f || ga.w != 0.f || gb.x != 0.f ||
+                           gb.y != 0.f || gb.z != 0.f || gb.w != 0.f || gc.x != 0.f);
+  if (touched) touched[i] = any ? 1 : 0;
+  if (!any) {
+    if (write_untouched) {
+      g_means[3 * i] = 0.f; g_means[3 * i + 1] = 0.f; g_means[3 * i + 2] = 0.f;
+      g_ls[3 * i] = 0.f; g_ls[3 * i + 1] = 0.f; g_ls[3 * i + 2] = 0.f;
+      g_quats[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+      g_ologit[i] = 0.f;
+#pragma unroll
+      for (int k = 0; k < 12; ++k) g_sh[12 * i + k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    return;
+  }
+  float3 mu = make_float3(means[3 * i], means[3 * i + 1], means[3 * i + 2]);
+  float3 ls = make_float3(log_scales[3 * i], log_scales[3 * i + 1], log_scales[3 * i + 2]);
+  float4 qr = quats[i];
+  Geo g;
+  geometry(cam, mu, ls, qr, g);  // visible by construction (radius > 0)
+  const float d_x = ga.x, d_y = ga.y, d_a = ga.z, d_b = ga.w, d_c = gb.x, d_o = gb.y;
+  const float drgb[3] = {gb.z, gb.w, gc.x};
+  // opacity
+  const float o = 1.f / (1.f + expf(-ologit[i]));
+  g_ologit[i] = d_o * o * (1.f - o);
+  // colour
+  float vx = mu.x - cam.campos[0], vy = mu.y - cam.campos[1], vz = mu.z - cam.campos[2];
+  const float il = rsqrtf(vx * vx + vy * vy + vz * vz);
+  const float dx = vx * il, dy = vy * il, dz = vz * il;
+  float Y[16];
+  sh_basis(dx, dy, dz, sh_degree, Y);
+  const int nb = (sh_degree + 1) * (sh_degree + 1);
+  const float4* shp = sh + 12 * i;
+  float shv[48];
+#pragma unroll
+  for (int k4 = 0; k4 < 12; ++k4) {
+    float4 v = (4 * k4 < 3 * nb) ? shp[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    shv[4 * k4] = v.x; shv[4 * k4 + 1] = v.y; shv[4 * k4 + 2] = v.z; shv[4 * k4 + 3] = v.w;
+  }
+  float pre[3] = {0.5f, 0.5f, 0.5f};
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+    if (k < nb) {
+      pre[0] += shv[3 * k] * Y[k];
+      pre[1] += shv[3 * k + 1] * Y[k];
+      pre[2] += shv[3 * k + 2] * Y[k];
+    }
+  const float dc0 = pre[0] >= 0.f ? drgb[0] : 0.f;
+  const float dc1 = pre[1] >= 0.f ? drgb[1] : 0.f;
+  const float dc2 = pre[2] >= 0.f ? drgb[2] : 0.f;
+  float sk[16];
+  float gsh[48];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const bool on = k < nb;
+    gsh[3 * k] = on ? dc0 * Y[k] : 0.f;
+    gsh[3 * k + 1] = on ? dc1 * Y[k] : 0.f;
+    gsh[3 * k + 2] = on ? dc2 * Y[k] : 0.f;
+    sk[k] = on ? dc0 * shv[3 * k] + dc1 * shv[3 * k + 1] + dc2 * shv[3 * k + 2] : 0.f;
+  }
+#pragma unroll
+  for (int k4 = 0; k4 < 12; ++k4)
+    g_sh[12 * i + k4] = make_float4(gsh[4 * k4], gsh[4 * k4 + 1], gsh[4 * k4 + 2], gsh[4 * k4 + 3]);
+  float gd[3];
+  sh_basis_grad(dx, dy, dz, sh_degree, sk, gd);
+  const float dot = gd[0] * dx + gd[1] * dy + gd[2] * dz;
+  float dmu[3] = {(gd[0] - dx * dot) * il, (gd[1] - dy * dot) * il, (gd[2] - dz * dot) * il};
+  // centre
+  const float z = g.pc[2], iz = 1.f / z, iz2 = iz * iz;
+  float dpc[3];
+  dpc[0] = d_x * cam.fx * iz;
+  dpc[1] = d_y * cam.fy * iz;
+  dpc[2] = -d_x * cam.fx * g.pc[0] * iz2 - d_y * cam.fy * g.pc[1] * iz2;
+  // conic Q = Sigma2^-1: dSigma2 = -Q dQ Q, dQ symmetric with off-diagonal db/2
+  const float qa = g.conic[0], qb = g.conic[1], qc = g.conic[2];
+  const float hb = 0.5f * d_b;
+  // P = Q dQ
+  const float P00 = qa * d_a + qb * hb, P01 = qa * hb + qb * d_c;
+  const float P10 = qb * d_a + qc * hb, P11 = qb * hb + qc * d_c;
+  // dS2 = -(P Q)
+  const float S00 = -(P00 * qa + P01 * qb), S01 = -(P00 * qb + P01 * qc);
+  const float S10 = -(P10 * qa + P11 * qb), S11 = -(P10 * qb + P11 * qc);
+  const float Sym01 = 0.5f * (S01 + S10);
+  // dSigma = T^T dS2 T (3x3 symmetric)
+  const float* T = g.T;
+  float dSig[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      dSig[r * 3 + c] = T[r] * (S00 * T[c] + Sym01 * T[3 + c]) + T[3 + r] * (Sym01 * T[c] + S11 * T[3 + c]);
+  // dT = 2 dS2 T Sigma
+  const float* Sg = g.Sig;
+  const float Sfull[9] = {Sg[0], Sg[1], Sg[2], Sg[1], Sg[3], Sg[4], Sg[2], Sg[4], Sg[5]};
+  float TS[6];
+#pragma unroll
+  for (int r = 0; r < 2; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      TS[r * 3 + c] = T[r * 3] * Sfull[c] + T[r * 3 + 1] * Sfull[3 + c] + T[r * 3 + 2] * Sfull[6 + c];
+  float dT[6];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    dT[c] = 2.f * (S00 * TS[c] + Sym01 * TS[3 + c]);
+    dT[3 + c] = 2.f * (Sym01 * TS[c] + S11 * TS[3 + c]);
+  }
+  // dJ = dT W^T
+  const float* Wm = cam.W;
+  const float dJ00 = dT[0] * Wm[0] + dT[1] * Wm[1] + dT[2] * Wm[2];
+  const float dJ02 = dT[0] * Wm[6] + dT[1] * Wm[7] + dT[2] * Wm[8];
+  const float dJ11 = dT[3] * Wm[3] + dT[4] * Wm[4] + dT[5] * Wm[5];
+  const float dJ12 = dT[3] * Wm[6] + dT[4] * Wm[7] + dT[5] * Wm[8];
+  dpc[2] += dJ00 * (-cam.fx * iz2) + dJ11 * (-cam.fy * iz2);
+  if (!g.clampx) {
+    dpc[0] += dJ02 * (-cam.fx * iz2);
+    dpc[2] += dJ02 * (2.f * cam.fx * g.pc[0] * iz2 * iz);
+  } else {
+    const float lim = g.pc[0] > 0.f ? cam.limx : -cam.limx;
+    dpc[2] += dJ02 * (cam.fx * lim * iz2);
+  }
+  if (!g.clampy) {
+    dpc[1] += dJ12 * (-cam.fy * iz2);
+    dpc[2] += dJ12 * (2.f * cam.fy * g.pc[1] * iz2 * iz);
+  } else {
+    const float lim = g.pc[1] > 0.f ? cam.limy : -cam.limy;
+    dpc[2] += dJ12 * (cam.fy * lim * iz2);
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) dmu[a] += Wm[a] * dpc[0] + Wm[3 + a] * dpc[1] + Wm[6 + a] * dpc[2];
+  g_means[3 * i] = dmu[0]; g_means[3 * i + 1] = dmu[1]; g_means[3 * i + 2] = dmu[2];
+  // Sigma = M M^T, M = R diag(s): dM = 2 dSigma M
+  const float* R = g.R;
+  float M[9], dM[9];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) M[r * 3 + c] = R[r * 3 + c] * g.s[c];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      dM[r * 3 + c] = 2.f * (dSig[r * 3] * M[c] + dSig[r * 3 + 1] * M[3 + c] + dSig[r * 3 + 2] * M[6 + c]);
+  float dR[9];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    float ds = R[c] * dM[c] + R[3 + c] * dM[3 + c] + R[6 + c] * dM[6 + c];
+    g_ls[3 * i + c] = ds * g.s[c];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) dR[r * 3 + c] = dM[r * 3 + c] * g.s[c];
+  }
+  const float w = g.q[0], x = g.q[1], y = g.q[2], zq = g.q[3];
+  float dq[4];
+  dq[0] = 2.f * (-zq * dR[1] + y * dR[2] + zq * dR[3] - x * dR[5] - y * dR[6] + x * dR[7]);
+  dq[1] = 2.f * (y * dR[1] + zq * dR[2] + y * dR[3] - 2.f * x * dR[4] - w * dR[5] + zq * dR[6] + w * dR[7] -
+                 2.f * x * dR[8]);
+  dq[2] = 2.f * (-2.f * y * dR[0] + x * dR[1] + w * dR[2] + x * dR[3] + zq * dR[5] - w * dR[6] + zq * dR[7] -
+                 2.f * y * dR[8]);
+  dq[3] = 2.f * (-2.f * zq * dR[0] - w * dR[1] + x * dR[2] + w * dR[3] - 2.f * zq * dR[4] + y * dR[5] +
+                 x * dR[6] + y * dR[7]);
+  const float qd = dq[0] * w + dq[1] * x + dq[2] * y + dq[3] * zq;
+  const float iq = 1.f / g.qnorm;
+  g_quats[i] = make_float4((dq[0] - w * qd) * iq, (dq[1] - x * qd) * iq, (dq[2] - y * qd) * iq,
+                           (dq[3] - zq * qd) * iq);
+}
+
+void launch_project_bwd(const tgs_gaussians& g, const tgs_camera& cam, const int32_t* radius, const float* grad2d,
+                        const tgs_param_ptrs& grads, uint8_t* touched, int write_untouched, cudaStream_t s) {
+  if (g.n <= 0) return;
+  CamK k = make_cam(cam);
+  int blocks = (int)((g.n + 255) / 256);
+  k_project_bwd<<<blocks, 256, 0, s>>>(g.means, g.log_scales, reinterpret_cast<const float4*>(g.quats),
+                                       g.opacity_logits, reinterpret_cast<const float4*>(g.sh), g.n, g.sh_degree, k,
+                                       radius, reinterpret_cast<const float4*>(grad2d), grads.means, grads.log_scales,
+                                       reinterpret_cast<float4*>(grads.quats), grads.opacity_logits,
+                                       reinterpret_cast<float4*>(grads.sh), touched, write_untouched);
+}
+
+bool gaussians_ok(const tgs_gaussians* g) {
+  if (!g || g->n < 0 || g->sh_degree < 0 || g->sh_degree > 3) return false;
+  if (g->n == 0) return true;
+  return g->means && g->log_scales && g->quats && g->opacity_logits && g->sh && aligned4(g->means) &&
+         aligned4(g->log_scales) && aligned16(g->quats) && aligned4(g->opacity_logits) && aligned16(g->sh);
+}
+
+bool camera_ok(const tgs_camera* c) {
+  return c && c->width > 0 && c->height > 0 && c->fx > 0.f && c->fy > 0.f && c->znear > 0.f &&
+         c->width <= (1 << 16) && c->height <= (1 << 16);
+}
+
+}  // namespace tgs
+
+using namespace tgs;
+
+extern "C" tgs_status tgs_project_gaussians(const tgs_gaussians* g, const tgs_camera* cam, const int32_t* tile_rank,
+                                            tgs_projected* out, tgs_stream stream) {
+  if (!gaussians_ok(g) || !camera_ok(cam) || !out) return TGS_ERR_INVALID_ARG;
+  if (g->n == 0) return TGS_OK;
+  if (!out->xy || !out->conic_opac || !out->rgb || !out->depth || !out->radius || !aligned8(out->xy) ||
+      !aligned16(out->conic_opac))
+    return TGS_ERR_INVALID_ARG;
+  CamK k = make_cam(*cam);
+  int blocks = (int)((g->n + 255) / 256);
+  k_project<<<blocks, 256, 0, (cudaStream_t)stream>>>(
+      g->means, g->log_scales, reinterpret_cast<const float4*>(g->quats), g->opacity_logits,
+      reinterpret_cast<const float4*>(g->sh), g->n, g->sh_degree, k, tile_rank,
+      reinterpret_cast<float2*>(out->xy), reinterpret_cast<float4*>(out->conic_opac), out->rgb, out->depth,
+      out->radius);
+  return check_launch();
+}

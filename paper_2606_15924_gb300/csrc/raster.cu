@@ -1,0 +1,286 @@
+// Sparse forward rasterization and its adjoint (Sec. 3.6, Eq. 1).
+//
+// One thread block per active tile, one thread per sampled pixel of the tile
+// (block size = 32 * ceil(n_pix / 32), so a tile sampled at rate 0.1 runs as
+// one warp).  The tile's depth-ordered splat list is staged through shared
+// memory in batches of one splat per thread; a block-wide vote ends the walk
+// once every pixel has saturated.  The backward replays the same walk in
+// reverse from the stored final transmittance, recovering T_k by division,
+// and sums each splat's adjoint over the warp's pixels with shuffles before a
+// single vector atomic per warp and splat.
+#include "tgs_common.cuh"
+
+namespace tgs {
+
+void launch_project_bwd(const tgs_gaussians& g, const tgs_camera& cam, const int32_t* radius, const float* grad2d,
+                        const tgs_param_ptrs& grads, uint8_t* touched, int write_untouched, cudaStream_t s);
+bool gaussians_ok(const tgs_gaussians* g);
+bool camera_ok(const tgs_camera* c);
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTStop = 1e-4f;
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+struct Splat {
+  float2 xy;
+  float4 co;   // conic a, b, c, opacity
+  float4 rgb;  // r, g, b, (unused)
+};
+
+// alpha of a splat at offset (dx, dy) from its centre; G receives exp(power).
+// Returns false when the splat is skipped (power > 0 or alpha < 1/255).
+// Every operation is an explicitly rounded intrinsic, so the forward and the
+// backward kernels take bit-identical decisions for the same splat and pixel.
+__device__ __forceinline__ bool splat_alpha(const float4& co, float dx, float dy, float& alpha, float& G) {
+  const float ax = __fmul_rn(co.x, dx), cy = __fmul_rn(co.z, dy), by = __fmul_rn(co.y, dy);
+  const float quad = __fmaf_rn(ax, dx, __fmul_rn(cy, dy));          // a dx^2 + c dy^2
+  const float power = __fmaf_rn(-0.5f, quad, -__fmul_rn(by, dx));   // - quad / 2 - b dx dy
+  if (power > 0.f) return false;
+  G = ex2_approx(__fmul_rn(power, kLog2e));
+  alpha = fminf(kAlphaMax, __fmul_rn(co.w, G));
+  return alpha >= kAlphaMin;
+}
+
+struct RasterArgs {
+  const float2* xy;
+  const float4* conic_opac;
+  const float* rgb;
+  const int2* ranges;
+  const int32_t* vals;
+  const int32_t* active_tiles;
+  const int32_t* n_active;
+  const int32_t* pix_off;
+  const uint8_t* pix_idx;
+  int tiles_x;
+  float bg[3];
+};
+
+__global__ void k_render_fwd(RasterArgs a, float* __restrict__ out_rgb, float* __restrict__ out_T,
+                             int32_t* __restrict__ out_last) {
+  extern __shared__ Splat sm[];
+  const int j = blockIdx.x;
+  if (j >= *a.n_active) return;
+  const int t = a.active_tiles ? a.active_tiles[j] : j;
+  const int p0 = a.pix_off[j], p1 = a.pix_off[j + 1];
+  const int lane_pix = threadIdx.x;
+  const bool has_pix = p0 + lane_pix < p1;
+  const int s = p0 + lane_pix;
+  float px = 0.f, py = 0.f;
+  if (has_pix) {
+    const int l = a.pix_idx[s];
+    px = (float)((t % a.tiles_x) * TGS_TILE + (l & 15)) + 0.5f;
+    py = (float)((t / a.tiles_x) * TGS_TILE + (l >> 4)) + 0.5f;
+  }
+  const int2 range = a.ranges[j];
+  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+  int last = 0;
+  bool done = !has_pix;
+  const int B = blockDim.x;
+  for (int base = range.x; base < range.y; base += B) {
+    if (__syncthreads_count(done) == B) break;
+    const int k = base + threadIdx.x;
+    if (k < range.y) {
+      const int id = a.vals[k];
+      Splat sp;
+      sp.xy = a.xy[id];
+      sp.co = a.conic_opac[id];
+      sp.rgb = make_float4(a.rgb[3 * id], a.rgb[3 * id + 1], a.rgb[3 * id + 2], 0.f);
+      sm[threadIdx.x] = sp;
+    }
+    __syncthreads();
+    const int cnt = min(B, range.y - base);
+    if (!done) {
+      for (int q = 0; q < cnt; ++q) {
+        const Splat sp = sm[q];
+        float alpha, G;
+        if (!splat_alpha(sp.co, __fsub_rn(px, sp.xy.x), __fsub_rn(py, sp.xy.y), alpha, G)) continue;
+        const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+        if (Tn < kTStop) {
+          done = true;
+          break;
+        }
+        const float w = alpha * T;
+        C0 += w * sp.rgb.x;
+        C1 += w * sp.rgb.y;
+        C2 += w * sp.rgb.z;
+        T = Tn;
+        last = base + q + 1 - range.x;
+      }
+    }
+  }
+  if (has_pix) {
+    out_rgb[3 * s] = C0 + T * a.bg[0];
+    out_rgb[3 * s + 1] = C1 + T * a.bg[1];
+    out_rgb[3 * s + 2] = C2 + T * a.bg[2];
+    out_T[s] = T;
+    out_last[s] = last;
+  }
+}
+
+__global__ void k_render_bwd(RasterArgs a, const float* __restrict__ T_final, const int32_t* __restrict__ n_last,
+                             const float* __restrict__ dL_drgb, float* __restrict__ grad2d) {
+  extern __shared__ Splat sm[];
+  __shared__ int s_max_last;
+  const int j = blockIdx.x;
+  if (j >= *a.n_active) return;
+  const int t = a.active_tiles ? a.active_tiles[j] : j;
+  const int p0 = a.pix_off[j], p1 = a.pix_off[j + 1];
+  const bool has_pix = p0 + (int)threadIdx.x < p1;
+  const int s = p0 + threadIdx.x;
+  float px = 0.f, py = 0.f, T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+  int last = 0;
+  if (has_pix) {
+    const int l = a.pix_idx[s];
+    px = (float)((t % a.tiles_x) * TGS_TILE + (l & 15)) + 0.5f;
+    py = (float)((t / a.tiles_x) * TGS_TILE + (l >> 4)) + 0.5f;
+    T = T_final[s];
+    last = n_last[s];
+    g0 = dL_drgb[3 * s];
+    g1 = dL_drgb[3 * s + 1];
+    g2 = dL_drgb[3 * s + 2];
+  }
+  if (threadIdx.x == 0) s_max_last = 0;
+  __syncthreads();
+  if (last > 0) atomicMax(&s_max_last, last);
+  __syncthreads();
+  const int2 range = a.ranges[j];
+  const int end = range.x + s_max_last;  // no pixel blended anything past here
+  float S0 = a.bg[0], S1 = a.bg[1], S2 = a.bg[2];
+  const int B = blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (int top = end; top > range.x; top -= B) {
+    const int lo = max(range.x, top - B);
+    const int cnt = top - lo;
+    __syncthreads();
+    if ((int)threadIdx.x < cnt) {
+      const int k = lo + threadIdx.x;
+      const int id = a.vals[k];
+      Splat sp;
+      sp.xy = a.xy[id];
+      sp.co = a.conic_opac[id];
+      sp.rgb = make_float4(a.rgb[3 * id], a.rgb[3 * id + 1], a.rgb[3 * id + 2], __int_as_float(id));
+      sm[threadIdx.x] = sp;
+    }
+    __syncthreads();
+    for (int q = cnt - 1; q >= 0; --q) {
+      const Splat sp = sm[q];
+      const int pos = lo + q - range.x;  // position in the tile list
+      float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      bool hit = false;
+      if (pos < last) {
+        const float dx = __fsub_rn(px, sp.xy.x), dy = __fsub_rn(py, sp.xy.y);
+        float alpha, G;
+        if (splat_alpha(sp.co, dx, dy, alpha, G)) {
+          hit = true;
+          T = T / (1.f - alpha);  // transmittance in front of this splat
+          const float wgt = alpha * T;
+          v[6] = wgt * g0;
+          v[7] = wgt * g1;
+          v[8] = wgt * g2;
+          const float dalpha = T * ((sp.rgb.x - S0) * g0 + (sp.rgb.y - S1) * g1 + (sp.rgb.z - S2) * g2);
+          S0 = alpha * sp.rgb.x + (1.f - alpha) * S0;
+          S1 = alpha * sp.rgb.y + (1.f - alpha) * S1;
+          S2 = alpha * sp.rgb.z + (1.f - alpha) * S2;
+          if (__fmul_rn(sp.co.w, G) < kAlphaMax) {
+            v[5] = dalpha * G;
+            const float dpow = dalpha * alpha;
+            v[0] = dpow * (sp.co.x * dx + sp.co.y * dy);
+            v[1] = dpow * (sp.co.z * dy + sp.co.y * dx);
+            v[2] = -0.5f * dpow * dx * dx;
+            v[3] = -dpow * dx * dy;
+            v[4] = -0.5f * dpow * dy * dy;
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, hit)) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) v[c] = warp_sum(v[c]);
+        if (lane == 0) {
+          float* gp = grad2d + 12 * (size_t)__float_as_int(sp.rgb.w);
+          red_add_v4(gp, v[0], v[1], v[2], v[3]);
+          red_add_v4(gp + 4, v[4], v[5], v[6], v[7]);
+          atomicAdd(gp + 8, v[8]);
+        }
+      }
+    }
+  }
+}
+
+static bool raster_args(const tgs_projected* proj, const int32_t* tile_ranges, const int32_t* vals,
+                        const int32_t* active_tiles, const int32_t* n_active, const int32_t* pix_off,
+                        const uint8_t* pix_idx, const tgs_camera* cam, const float* bg, RasterArgs& a) {
+  if (!proj || !proj->xy || !proj->conic_opac || !proj->rgb || !tile_ranges || !vals || !n_active || !pix_off ||
+      !pix_idx || !camera_ok(cam) || !bg)
+    return false;
+  if (!aligned8(proj->xy) || !aligned16(proj->conic_opac) || !aligned8(tile_ranges)) return false;
+  a.xy = reinterpret_cast<const float2*>(proj->xy);
+  a.conic_opac = reinterpret_cast<const float4*>(proj->conic_opac);
+  a.rgb = proj->rgb;
+  a.ranges = reinterpret_cast<const int2*>(tile_ranges);
+  a.vals = vals;
+  a.active_tiles = active_tiles;
+  a.n_active = n_active;
+  a.pix_off = pix_off;
+  a.pix_idx = pix_idx;
+  a.tiles_x = tiles_x(cam->width);
+  a.bg[0] = bg[0];
+  a.bg[1] = bg[1];
+  a.bg[2] = bg[2];
+  return true;
+}
+
+static int block_for(int n_pix_max) { return std::min(256, std::max(32, (n_pix_max + 31) / 32 * 32)); }
+
+}  // namespace tgs
+
+using namespace tgs;
+
+extern "C" tgs_status tgs_render_sampled(const tgs_projected* proj, const int32_t* tile_ranges, const int32_t* vals,
+                                         const int32_t* active_tiles, const int32_t* n_active, int32_t n_active_max,
+                                         const int32_t* pix_off, const uint8_t* pix_idx, int32_t n_pix_max,
+                                         const tgs_camera* cam, const float* bg, float* rgb, float* T_final,
+                                         int32_t* n_last, tgs_stream stream) {
+  RasterArgs a;
+  if (n_active_max < 0 || n_pix_max < 1 || n_pix_max > 256) return TGS_ERR_INVALID_ARG;
+  if (!raster_args(proj, tile_ranges, vals, active_tiles, n_active, pix_off, pix_idx, cam, bg, a))
+    return TGS_ERR_INVALID_ARG;
+  if (!rgb || !T_final || !n_last) return TGS_ERR_INVALID_ARG;
+  if (n_active_max == 0) return TGS_OK;
+  const int B = block_for(n_pix_max);
+  k_render_fwd<<<n_active_max, B, B * sizeof(Splat), (cudaStream_t)stream>>>(a, rgb, T_final, n_last);
+  return check_launch();
+}
+
+extern "C" tgs_status tgs_backward_sampled(const tgs_gaussians* g, const tgs_camera* cam, const tgs_projected* proj,
+                                           const int32_t* tile_ranges, const int32_t* vals,
+                                           const int32_t* active_tiles, const int32_t* n_active,
+                                           int32_t n_active_max, const int32_t* pix_off, const uint8_t* pix_idx,
+                                           int32_t n_pix_max, const float* bg, const float* T_final,
+                                           const int32_t* n_last, const float* dL_drgb, float* grad2d,
+                                           const tgs_param_ptrs* grads, uint8_t* touched, int32_t write_untouched,
+                                           tgs_stream stream) {
+  RasterArgs a;
+  if (!gaussians_ok(g) || n_active_max < 0 || n_pix_max < 1 || n_pix_max > 256) return TGS_ERR_INVALID_ARG;
+  if (!raster_args(proj, tile_ranges, vals, active_tiles, n_active, pix_off, pix_idx, cam, bg, a))
+    return TGS_ERR_INVALID_ARG;
+  if (!T_final || !n_last || !dL_drgb || !grads || !proj->radius) return TGS_ERR_INVALID_ARG;
+  if (g->n > 0 && (!grad2d || !aligned16(grad2d) || !grads->means || !grads->log_scales || !grads->quats ||
+                   !grads->opacity_logits || !grads->sh || !aligned16(grads->quats) || !aligned16(grads->sh)))
+    return TGS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (g->n == 0) return TGS_OK;
+  cudaMemsetAsync(grad2d, 0, sizeof(float) * 12 * (size_t)g->n, s);
+  if (n_active_max > 0) {
+    const int B = block_for(n_pix_max);
+    k_render_bwd<<<n_active_max, B, B * sizeof(Splat), s>>>(a, T_final, n_last, dL_drgb, grad2d);
+  }
+  launch_project_bwd(*g, *cam, proj->radius, grad2d, *grads, touched, write_untouched, s);
+  return check_launch();
+}

@@ -1,0 +1,342 @@
+// Tile selection and tile-wise error-guided pixel sampling (Sec. 3.5).
+//
+// Both levels choose n items as: round(r_hard n) by the error-proportional
+// draw without replacement, round(r_stable n) of the rest with the largest age,
+// the remainder uniformly.  The weighted draw is realised as the
+// Efraimidis-Spirakis order (ascending E_i / w_i with E_i = -log2 U_i an
+// exponential clock in 32-bit fixed point), so every item's fate is decided
+// by counting the items that precede it in a total order - no sequential
+// loop, and integer-only arithmetic, hence bit-identical on every run.
+#include "scan.cuh"
+
+namespace tgs {
+
+struct SelWs {
+  uint64_t* tile_w;   // [T] sum of pixel weights
+  uint64_t* tile_L;   // [T] exponential clock
+  uint64_t* tile_u;   // [T] uniform key
+  uint32_t* tile_age; // [T] smallest pixel age
+  int32_t* rank_h;    // [T]
+  int32_t* rank_s;    // [T]
+  int32_t* rank_u;    // [T]
+  int64_t* scan_sums;
+  int64_t* total;     // [1]
+};
+
+static SelWs carve_sel(void* base, int T, size_t* total) {
+  Carver c(base);
+  SelWs w;
+  w.tile_w = c.take<uint64_t>(T);
+  w.tile_L = c.take<uint64_t>(T);
+  w.tile_u = c.take<uint64_t>(T);
+  w.tile_age = c.take<uint32_t>(T);
+  w.rank_h = c.take<int32_t>(3 * (size_t)T);
+  w.rank_s = w.rank_h + T;
+  w.rank_u = w.rank_h + 2 * T;
+  w.scan_sums = c.take<int64_t>((size_t)std::max(1, scan_blocks(T)));
+  w.total = c.take<int64_t>(1);
+  *total = c.size();
+  return w;
+}
+
+struct SelGeom {
+  int W, H, tx, T;
+};
+
+__device__ __forceinline__ int tile_valid(const SelGeom& g, int t) {
+  int tx = t % g.tx, ty = t / g.tx;
+  return min(TGS_TILE, g.W - tx * TGS_TILE) * min(TGS_TILE, g.H - ty * TGS_TILE);
+}
+
+// hard order: positive weights first by L_i / w_i ascending, then zero
+// weights by L ascending; ties by index.  true when (a) precedes (b).
+__device__ __forceinline__ bool hard_before(uint64_t wa, uint64_t La, int ia, uint64_t wb, uint64_t Lb, int ib) {
+  const bool za = wa == 0, zb = wb == 0;
+  if (za != zb) return zb;
+  if (!za) {
+    if (mul128_less(La, wb, Lb, wa)) return true;
+    if (mul128_less(Lb, wa, La, wb)) return false;
+  } else if (La != Lb) {
+    return La < Lb;
+  }
+  return ia < ib;
+}
+
+// Per-tile weight (sum), age (min) and the tile's random keys.
+// Hash prefixes of the call: the iteration comes from the host or, for graph
+// replays, from device memory.
+struct HashKeys {
+  uint64_t seed, iter;
+  const uint64_t* iter_dev;
+  uint32_t view;
+  __device__ __forceinline__ uint64_t prefix(uint32_t stream) const {
+    return hash_prefix(seed, iter_dev ? *iter_dev : iter, view, stream);
+  }
+};
+
+__global__ void __launch_bounds__(256) k_tile_stats(const uint16_t* __restrict__ err, const uint16_t* __restrict__ age,
+                                                    SelGeom g, HashKeys hk, SelWs w) {
+  __shared__ uint64_t sw[8];
+  __shared__ uint32_t sa[8];
+  const int t = blockIdx.x;
+  const int l = threadIdx.x;
+  const int x = (t % g.tx) * TGS_TILE + (l & 15), y = (t / g.tx) * TGS_TILE + (l >> 4);
+  uint64_t wv = 0;
+  uint32_t av = 0xFFFFFFFFu;
+  if (x < g.W && y < g.H) {
+    const size_t k = (size_t)y * g.W + x;
+    wv = err_weight(err[k]);
+    av = age[k];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    wv += __shfl_xor_sync(0xffffffffu, wv, o);
+    av = min(av, __shfl_xor_sync(0xffffffffu, av, o));
+  }
+  if ((l & 31) == 0) {
+    sw[l >> 5] = wv;
+    sa[l >> 5] = av;
+  }
+  __syncthreads();
+  if (l == 0) {
+    uint64_t s = 0;
+    uint32_t a = 0xFFFFFFFFu;
+    for (int k = 0; k < 8; ++k) {
+      s += sw[k];
+      a = min(a, sa[k]);
+    }
+    w.tile_w[t] = s;
+    w.tile_age[t] = a;
+    w.tile_L[t] = neglog2_q32(hash_item(hk.prefix(STREAM_TILE_HARD), (uint32_t)t, 0));
+    w.tile_u[t] = hash_item(hk.prefix(STREAM_TILE_UNIF), (uint32_t)t, 0);
+  }
+}
+
+// rank[i] += #{j in this block's chunk, eligible, preceding i} for the phase.
+// phase 0: hard order among all; 1: age order among those not taken by phase
+// 0; 2: uniform order among those not taken by phases 0 and 1.
+constexpr int RANK_CHUNK = 256;
+
+__global__ void __launch_bounds__(256) k_rank_tiles(SelWs w, int T, int phase, int kh, int ks) {
+  __shared__ uint64_t s_a[RANK_CHUNK];
+  __shared__ uint64_t s_b[RANK_CHUNK];
+  __shared__ uint8_t s_e[RANK_CHUNK];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j0 = blockIdx.y * RANK_CHUNK;
+  {
+    const int j = j0 + threadIdx.x;
+    bool e = j < T;
+    if (e && phase >= 1) e = w.rank_h[j] >= kh;
+    if (e && phase >= 2) e = w.rank_s[j] >= ks;
+    s_e[threadIdx.x] = e;
+    if (j < T) {
+      if (phase == 0) {
+        s_a[threadIdx.x] = w.tile_w[j];
+        s_b[threadIdx.x] = w.tile_L[j];
+      } else if (phase == 1) {
+        s_a[threadIdx.x] = w.tile_age[j];
+      } else {
+        s_a[threadIdx.x] = w.tile_u[j];
+      }
+    }
+  }
+  __syncthreads();
+  if (i >= T) return;
+  if (phase >= 1 && w.rank_h[i] < kh) return;
+  if (phase >= 2 && w.rank_s[i] < ks) return;
+  int cnt = 0;
+  const int jn = min(RANK_CHUNK, T - j0);
+  if (phase == 0) {
+    const uint64_t wi = w.tile_w[i], Li = w.tile_L[i];
+    for (int k = 0; k < jn; ++k) cnt += hard_before(s_a[k], s_b[k], j0 + k, wi, Li, i);
+  } else if (phase == 1) {
+    const uint32_t ai = w.tile_age[i];
+    for (int k = 0; k < jn; ++k) {
+      const uint32_t aj = (uint32_t)s_a[k];
+      cnt += s_e[k] && (aj > ai || (aj == ai && j0 + k < i));
+    }
+  } else {
+    const uint64_t ui = w.tile_u[i];
+    for (int k = 0; k < jn; ++k) {
+      const uint64_t uj = s_a[k];
+      cnt += s_e[k] && (uj < ui || (uj == ui && j0 + k < i));
+    }
+  }
+  if (cnt) atomicAdd(phase == 0 ? &w.rank_h[i] : phase == 1 ? &w.rank_s[i] : &w.rank_u[i], cnt);
+}
+
+// Pixel sampling inside one chosen tile: one block of 256 threads (one per
+// local pixel).
+__global__ void __launch_bounds__(256) k_sample_pixels(const uint16_t* __restrict__ err,
+                                                       const uint16_t* __restrict__ age, SelGeom g, int n_pix,
+                                                       int hard_pm, int stable_pm, HashKeys hk,
+                                                       const int32_t* __restrict__ active_tiles,
+                                                       const int32_t* __restrict__ n_active,
+                                                       const int32_t* __restrict__ pix_off,
+                                                       uint8_t* __restrict__ pix_idx) {
+  __shared__ uint64_t s_w[256], s_L[256], s_u[256];
+  __shared__ uint32_t s_age[256];
+  __shared__ uint8_t s_ok[256];
+  __shared__ uint32_t s_warp[8];
+  const int j = blockIdx.x;
+  if (j >= *n_active) return;
+  const int t = active_tiles[j];
+  const int l = threadIdx.x;
+  const int x = (t % g.tx) * TGS_TILE + (l & 15), y = (t / g.tx) * TGS_TILE + (l >> 4);
+  const bool valid = x < g.W && y < g.H;
+  const int nv = tile_valid(g, t);
+  const int n = min(n_pix, nv);
+  int kh, ks;
+  split_counts(n, hard_pm, stable_pm, kh, ks);
+  bool taken;
+  if (n >= nv) {
+    taken = valid;  // every valid pixel
+  } else {
+    uint64_t wv = 0, Lv = 0, uv = 0;
+    uint32_t av = 0;
+    if (valid) {
+      const size_t k = (size_t)y * g.W + x;
+      wv = err_weight(err[k]);
+      av = age[k];
+      Lv = neglog2_q32(hash_item(hk.prefix(STREAM_PIX_HARD), (uint32_t)t, (uint32_t)l));
+      uv = hash_item(hk.prefix(STREAM_PIX_UNIF), (uint32_t)t, (uint32_t)l);
+    }
+    s_w[l] = wv; s_L[l] = Lv; s_u[l] = uv; s_age[l] = av; s_ok[l] = valid;
+    __syncthreads();
+    // phase 0: hard draw
+    bool th = false;
+    if (valid && kh > 0) {
+      int c = 0;
+      for (int q = 0; q < 256 && c < kh; ++q) c += s_ok[q] && hard_before(s_w[q], s_L[q], q, wv, Lv, l);
+      th = c < kh;
+    }
+    __syncthreads();
+    s_ok[l] = valid && !th;
+    __syncthreads();
+    // phase 1: oldest among the rest
+    bool ts = false;
+    if (valid && !th && ks > 0) {
+      int c = 0;
+      for (int q = 0; q < 256 && c < ks; ++q) {
+        const uint32_t aq = s_age[q];
+        c += s_ok[q] && (aq > av || (aq == av && q < l));
+      }
+      ts = c < ks;
+    }
+    __syncthreads();
+    s_ok[l] = valid && !th && !ts;
+    __syncthreads();
+    // phase 2: uniform among the rest
+    bool tu = false;
+    const int ku = n - kh - ks;
+    if (valid && !th && !ts && ku > 0) {
+      int c = 0;
+      for (int q = 0; q < 256 && c < ku; ++q) {
+        const uint64_t uq = s_u[q];
+        c += s_ok[q] && (uq < uv || (uq == uv && q < l));
+      }
+      tu = c < ku;
+    }
+    taken = th || ts || tu;
+  }
+  // ascending compaction of the taken local indices
+  const unsigned b = __ballot_sync(0xffffffffu, taken);
+  if ((l & 31) == 0) s_warp[l >> 5] = __popc(b);
+  __syncthreads();
+  int off = 0;
+  for (int k = 0; k < (l >> 5); ++k) off += s_warp[k];
+  off += __popc(b & ((1u << (l & 31)) - 1u));
+  if (taken) pix_idx[pix_off[j] + off] = (uint8_t)l;
+}
+
+__global__ void k_sel_finish(const int64_t* __restrict__ total, int32_t* __restrict__ n_active,
+                             int32_t* __restrict__ pix_off) {
+  const int64_t v = *total;
+  *n_active = (int32_t)(v >> 32);
+  pix_off[v >> 32] = (int32_t)(v & 0xFFFFFFFFll);
+}
+
+}  // namespace tgs
+
+using namespace tgs;
+
+extern "C" size_t tgs_select_tiles_workspace_size(int32_t width, int32_t height) {
+  size_t total = 0;
+  if (width <= 0 || height <= 0) return 0;
+  carve_sel(nullptr, tiles_x(width) * tiles_y(height), &total);
+  return total;
+}
+
+extern "C" tgs_status tgs_select_tiles(const uint16_t* err_map, const uint16_t* age_map, int32_t width,
+                                       int32_t height, int32_t n_select, int32_t n_pix, const tgs_sampling* cfg,
+                                       uint64_t seed, uint64_t iter, const uint64_t* iter_dev, uint32_t view,
+                                       void* workspace, size_t workspace_bytes, int32_t* active_tiles, int32_t* n_active,
+                                       int32_t* tile_rank, int32_t* pix_off, uint8_t* pix_idx,
+                                       tgs_stream stream) {
+  if (width <= 0 || height <= 0 || width > (1 << 16) || height > (1 << 16) || n_select < 0 || n_pix < 1 ||
+      n_pix > 256 || !cfg || !err_map || !age_map || !n_active || !tile_rank || !pix_off)
+    return TGS_ERR_INVALID_ARG;
+  const int pms[4] = {cfg->tile_hard_pm, cfg->tile_stable_pm, cfg->pix_hard_pm, cfg->pix_stable_pm};
+  for (int k = 0; k < 4; ++k)
+    if (pms[k] < 0 || pms[k] > 1000) return TGS_ERR_INVALID_ARG;
+  const int T = tiles_x(width) * tiles_y(height);
+  const int n_sel = std::min(n_select, T);
+  if (n_sel > 0 && (!active_tiles || !pix_idx)) return TGS_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < tgs_select_tiles_workspace_size(width, height)) return TGS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t tot;
+  SelWs w = carve_sel(workspace, T, &tot);
+  SelGeom g{width, height, tiles_x(width), T};
+  const HashKeys hk{seed, iter, iter_dev, view};
+  int kh, ks;
+  split_counts(n_sel, cfg->tile_hard_pm, cfg->tile_stable_pm, kh, ks);
+  // ranks: a tile is taken when rank_h < kh, or (not hard) rank_s < ks, or
+  // (neither) rank_u < n_sel - kh - ks.  Choosing every tile needs no ranking.
+  cudaMemsetAsync(w.rank_h, 0, sizeof(int32_t) * 3 * (size_t)T, s);
+  if (n_sel < T && n_sel > 0) {
+    k_tile_stats<<<T, 256, 0, s>>>(err_map, age_map, g, hk, w);
+    dim3 grid((T + 255) / 256, (T + RANK_CHUNK - 1) / RANK_CHUNK);
+    if (kh > 0) k_rank_tiles<<<grid, 256, 0, s>>>(w, T, 0, kh, ks);
+    if (ks > 0) k_rank_tiles<<<grid, 256, 0, s>>>(w, T, 1, kh, ks);
+    if (n_sel - kh - ks > 0) k_rank_tiles<<<grid, 256, 0, s>>>(w, T, 2, kh, ks);
+  }
+  // compaction: packed (taken << 32 | pixels) prefix gives rank and pixel offset
+  {
+    const int32_t* rh = w.rank_h;
+    const int32_t* rs = w.rank_s;
+    const int32_t* ru = w.rank_u;
+    const int all = n_sel >= T ? 1 : 0, none = n_sel == 0 ? 1 : 0;
+    const int ku = n_sel - kh - ks;
+    const int npx = n_pix;
+    int32_t* at = active_tiles;
+    int32_t* tr = tile_rank;
+    int32_t* po = pix_off;
+    auto is_taken = [=] __device__(int64_t t) -> bool {
+      if (none) return false;
+      if (all) return true;
+      if (rh[t] < kh) return true;
+      if (rs[t] < ks) return true;
+      return rs[t] >= ks && ru[t] < ku;
+    };
+    auto load = [=] __device__(int64_t t) -> int64_t {
+      if (!is_taken(t)) return 0;
+      return (1ll << 32) | (int64_t)min(npx, tile_valid(g, (int)t));
+    };
+    auto store = [=] __device__(int64_t t, int64_t pre, int64_t v) {
+      if (v) {
+        const int r = (int)(pre >> 32);
+        tr[t] = r;
+        at[r] = (int)t;
+        po[r] = (int)(pre & 0xFFFFFFFFll);
+      } else {
+        tr[t] = -1;
+      }
+    };
+    exclusive_scan<int64_t>(load, store, nullptr, T, w.scan_sums, w.total, s);
+  }
+  k_sel_finish<<<1, 1, 0, s>>>(w.total, n_active, pix_off);
+  if (n_sel > 0)
+    k_sample_pixels<<<n_sel, 256, 0, s>>>(err_map, age_map, g, n_pix, cfg->pix_hard_pm, cfg->pix_stable_pm, hk,
+                                          active_tiles, n_active, pix_off, pix_idx);
+  return check_launch();
+}

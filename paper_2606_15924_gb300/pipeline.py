@@ -1,0 +1,272 @@
+"""One TurboGS training iteration on the GPU, built from the C-ABI calls.
+
+A ``Trainer`` owns the device buffers of one view's sparse step and runs,
+in order (Alg. 1 steps 3-10): select_tiles -> project_gaussians -> bin_tiles ->
+render_sampled -> loss_sparse_ncc (with the error/age map update) ->
+backward_sampled -> hybrid_step.  Sizes are fixed at construction and the
+iteration counters live on the device, so one step can be captured once in a
+CUDA graph and replayed.  ``dense=True`` gives the same library's plain path:
+every tile active and every pixel sampled.
+"""
+from __future__ import annotations
+
+import math
+
+import torch
+
+from . import binding as B
+from .config import Config, TILE
+
+
+def tiles_of(width: int, height: int) -> int:
+    return ((width + TILE - 1) // TILE) * ((height + TILE - 1) // TILE)
+
+
+def zeros_like_params(g: dict) -> dict:
+    return {k: torch.zeros_like(v) for k, v in g.items()}
+
+
+class Trainer:
+    def __init__(self, params: dict, cam: dict, target: torch.Tensor, tile_fraction: float = 0.2,
+                 pixel_rate: float = 1.0 / 3.0, cfg: Config | None = None, dense: bool = False,
+                 capacity: int | None = None, seed: int = 0, bg=(0.0, 0.0, 0.0), sh_degree: int = 3,
+                 view: int = 0, train: bool = True):
+        self.cfg = cfg or Config()
+        self.params = params
+        self.n = int(params["means"].shape[0])
+        self.cam = cam
+        self.ccam = B.camera(cam)
+        self.W, self.H = int(cam["width"]), int(cam["height"])
+        self.T = tiles_of(self.W, self.H)
+        self.dense = dense
+        if dense:
+            self.n_select, self.n_pix = self.T, 256
+        else:
+            self.n_select = max(1, min(self.T, round(tile_fraction * self.T)))
+            self.n_pix = max(1, min(256, math.floor(pixel_rate * 256)))
+        self.seed, self.view, self.bg, self.sh_degree = seed, view, tuple(bg), sh_degree
+        self.target = target.contiguous()
+        dev = params["means"].device
+        i32, i64, u8 = torch.int32, torch.int64, torch.uint8
+        T, N, S = self.T, self.n, self.n_select
+        P = S * self.n_pix
+        self.P_max = P
+        # optimiser state (not needed for render-only use)
+        self.train = train
+        if train:
+            self.grads = zeros_like_params(params)
+            self.m = zeros_like_params(params)
+            self.v = zeros_like_params(params)
+        # per-view maps: fp16 error (bit patterns) and uint16 age
+        self.err_map = torch.zeros(self.H, self.W, dtype=torch.int16, device=dev)
+        self.age_map = torch.zeros(self.H, self.W, dtype=torch.int16, device=dev)
+        # selection
+        self.ws_sel = torch.empty(B.select_tiles_workspace_size(self.W, self.H), dtype=u8, device=dev)
+        self.active_tiles = torch.zeros(S, dtype=i32, device=dev)
+        self.n_active = torch.zeros(1, dtype=i32, device=dev)
+        self.tile_rank = torch.zeros(T, dtype=i32, device=dev)
+        self.pix_off = torch.zeros(S + 1, dtype=i32, device=dev)
+        self.pix_idx = torch.zeros(P, dtype=u8, device=dev)
+        # projection
+        self.proj = dict(xy=torch.zeros(N, 2, device=dev), conic_opac=torch.zeros(N, 4, device=dev),
+                         rgb=torch.zeros(N, 3, device=dev), depth=torch.zeros(N, device=dev),
+                         radius=torch.zeros(N, dtype=i32, device=dev))
+        # binning
+        self.n_isect = torch.zeros(1, dtype=i64, device=dev)
+        self.ranges = torch.zeros(S, 2, dtype=i32, device=dev)
+        self.capacity = 0
+        self._alloc_bins(capacity if capacity is not None else self._probe_capacity())
+        # forward / loss / backward buffers
+        self.rgb = torch.zeros(P, 3, device=dev)
+        self.T_final = torch.zeros(P, device=dev)
+        self.n_last = torch.zeros(P, dtype=i32, device=dev)
+        self.dL = torch.zeros(P, 3, device=dev)
+        self.lam = torch.zeros(S, device=dev)
+        self.err_pix = torch.zeros(P, device=dev)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        if train:
+            self.grad2d = torch.zeros(N, 12, device=dev)
+            self.touched = torch.zeros(N, dtype=u8, device=dev)
+        # device-side counters (graph replays read them)
+        self.it_dev = torch.zeros(1, dtype=i64, device=dev)
+        self.step_dev = torch.ones(1, dtype=i32, device=dev)
+        self.graph = None
+        o = self.cfg.opt
+        self.opt = dict(lr=[o.lr_means, o.lr_scales, o.lr_quats, o.lr_opacity, o.lr_sh_dc, o.lr_sh_rest],
+                        beta1=o.beta1, beta2=o.beta2, eps_adam=o.eps_adam, eps_lm=o.eps_lm, mode=o.mode)
+        l = self.cfg.loss
+        self.loss_params = (l.eps_charbonnier, l.eps_ncc, l.beta_ema)
+
+    # ------------------------------------------------------------------ setup
+    def _alloc_bins(self, capacity: int):
+        dev = self.params["means"].device
+        self.capacity = int(capacity)
+        self.ws_bin = torch.empty(B.bin_tiles_workspace_size(self.n, self.capacity, self.n_select),
+                                  dtype=torch.uint8, device=dev)
+        self.vals = torch.zeros(max(self.capacity, 1), dtype=torch.int32, device=dev)
+
+    def _probe_capacity(self) -> int:
+        """Exact pair count of the dense view (one synchronising query at set-up),
+        with headroom for the Gaussians moving during training."""
+        dev = self.params["means"].device
+        proj = dict(xy=torch.zeros(self.n, 2, device=dev), conic_opac=torch.zeros(self.n, 4, device=dev),
+                    rgb=torch.zeros(self.n, 3, device=dev), depth=torch.zeros(self.n, device=dev),
+                    radius=torch.zeros(self.n, dtype=torch.int32, device=dev))
+        B.project_gaussians(self.params, self.ccam, None, proj, self.sh_degree)
+        ws = torch.empty(B.bin_tiles_workspace_size(self.n, 0, self.T), dtype=torch.uint8, device=dev)
+        ranges = torch.zeros(self.T, 2, dtype=torch.int32, device=dev)
+        n_isect = torch.zeros(1, dtype=torch.int64, device=dev)
+        B.bin_tiles(proj, self.n, self.ccam, None, self.T, ws, 0, None, None, ranges, n_isect)
+        need = int(n_isect.item())
+        return int(need * 1.3) + 4096
+
+    def overflowed(self) -> bool:
+        """True when the last step produced more tile pairs than the capacity
+        (reads one device value; call outside the timed loop)."""
+        return int(self.n_isect.item()) > self.capacity
+
+    # ------------------------------------------------------------------ step
+    def _select(self, n_select=None, n_pix=None, it_dev=True):
+        B.select_tiles(self.err_map, self.age_map, self.W, self.H, n_select or self.n_select, n_pix or self.n_pix,
+                       self.cfg.sampling.permille(), self.seed, 0, self.view, self.ws_sel, self.active_tiles,
+                       self.n_active, self.tile_rank, self.pix_off, self.pix_idx,
+                       iter_dev=self.it_dev if it_dev else None)
+
+    def forward(self):
+        """select -> project -> bin -> render (Alg. 1 steps 3, 5)."""
+        self._select()
+        B.project_gaussians(self.params, self.ccam, self.tile_rank, self.proj, self.sh_degree)
+        B.bin_tiles(self.proj, self.n, self.ccam, self.tile_rank, self.n_select, self.ws_bin, self.capacity,
+                    self.vals, None, self.ranges, self.n_isect)
+        B.render_sampled(self.proj, self.ranges, self.vals, self.active_tiles, self.n_active, self.n_select,
+                         self.pix_off, self.pix_idx, self.n_pix, self.ccam, self.bg, self.rgb, self.T_final,
+                         self.n_last)
+
+    def loss_and_maps(self):
+        """Fused loss with the error/age map update (Alg. 1 steps 4, 6, 7)."""
+        B.loss_sparse_ncc(self.rgb, self.target, self.W, self.H, self.active_tiles, self.n_active, self.n_select,
+                          self.pix_off, self.pix_idx, self.n_pix, self.loss_params, self.err_map, self.age_map,
+                          self.dL, self.lam, self.err_pix, self.loss)
+
+    def backward(self, write_untouched=False):
+        """Sparse backward into parameter gradients (Alg. 1 step 8)."""
+        B.backward_sampled(self.params, self.ccam, self.proj, self.ranges, self.vals, self.active_tiles,
+                           self.n_active, self.n_select, self.pix_off, self.pix_idx, self.n_pix, self.bg,
+                           self.T_final, self.n_last, self.dL, self.grad2d, self.grads, self.touched,
+                           write_untouched=write_untouched, sh_degree=self.sh_degree)
+
+    def update(self):
+        """Hybrid LM / Adam update (Alg. 1 steps 9, 10)."""
+        B.hybrid_step(self.params, self.grads, self.m, self.v, self.n, self.touched, None, 0, 1, self.opt,
+                      step_dev=self.step_dev)
+
+    def step(self):
+        """One full iteration; advances the device counters."""
+        self.forward()
+        self.loss_and_maps()
+        self.backward()
+        self.update()
+        self.it_dev.add_(1)
+        self.step_dev.add_(1)
+
+    # ------------------------------------------------------------------ graph
+    def capture(self):
+        """Capture one step in a CUDA graph (after a warm-up step)."""
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph(keep_graph=True)
+        with torch.cuda.graph(self.graph):
+            self.step()
+        self.kernels_per_step = B.graph_count_kernels(self.graph)
+        self.graph.instantiate()
+        torch.cuda.synchronize()
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
+
+    STAGES = ("select_tiles", "project_gaussians", "bin_tiles", "render_sampled", "loss_sparse_ncc",
+              "backward_sampled", "hybrid_step")
+
+    def stage_calls(self):
+        """The step as (name, callable) pairs, one per C-ABI call."""
+        def bump():
+            self.it_dev.add_(1)
+            self.step_dev.add_(1)
+        return [("select_tiles", self._select),
+                ("project_gaussians", lambda: B.project_gaussians(self.params, self.ccam, self.tile_rank, self.proj,
+                                                                  self.sh_degree)),
+                ("bin_tiles", lambda: B.bin_tiles(self.proj, self.n, self.ccam, self.tile_rank, self.n_select,
+                                                  self.ws_bin, self.capacity, self.vals, None, self.ranges,
+                                                  self.n_isect)),
+                ("render_sampled", lambda: B.render_sampled(self.proj, self.ranges, self.vals, self.active_tiles,
+                                                            self.n_active, self.n_select, self.pix_off,
+                                                            self.pix_idx, self.n_pix, self.ccam, self.bg, self.rgb,
+                                                            self.T_final, self.n_last)),
+                ("loss_sparse_ncc", self.loss_and_maps),
+                ("backward_sampled", self.backward),
+                ("hybrid_step", lambda: (self.update(), bump()))]
+
+    def capture_stages(self):
+        """One CUDA graph per call of the step, so each call's device time can
+        be measured with events between replays (run after capture())."""
+        self.stage_graphs = []
+        torch.cuda.synchronize()
+        for name, fn in self.stage_calls():
+            gr = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gr):
+                fn()
+            self.stage_graphs.append((name, gr))
+        torch.cuda.synchronize()
+        return self.stage_graphs
+
+    # ------------------------------------------------------------------ maps
+    def init_error_map(self):
+        """E_v from a dense evaluation of the current Gaussians (Sec. 3.3):
+        every tile and pixel rendered once, E = e, A = 0.  Returns the loss."""
+        d = self if self.dense else Trainer(self.params, self.cam, self.target, cfg=self.cfg, dense=True,
+                                            seed=self.seed, bg=self.bg, sh_degree=self.sh_degree, view=self.view,
+                                            train=False)
+        d.err_map, d.age_map = self.err_map, self.age_map
+        d.forward()
+        saved = d.loss_params
+        d.loss_params = (saved[0], saved[1], 1.0)
+        d.loss_and_maps()
+        d.loss_params = saved
+        self.age_map.zero_()
+        return float(d.loss.item())
+
+    def render_image(self) -> torch.Tensor:
+        """Dense render of the current Gaussians as an [H, W, 3] image (for
+        evaluation; uses the same library calls)."""
+        d = Trainer(self.params, self.cam, self.target, cfg=self.cfg, dense=True, seed=self.seed, bg=self.bg,
+                    sh_degree=self.sh_degree, view=self.view, train=False)
+        d.forward()
+        return d.scatter_image(d.rgb)
+
+    def pixel_coords(self):
+        """[P, 2] integer pixel coordinates of the current sampled set (tile order)."""
+        A = int(self.n_active.item())
+        off = self.pix_off[:A + 1].long()
+        counts = off[1:] - off[:-1]
+        tiles = torch.repeat_interleave(self.active_tiles[:A].long(), counts)
+        l = self.pix_idx[:int(off[-1])].long()
+        tx_n = (self.W + TILE - 1) // TILE
+        x = (tiles % tx_n) * TILE + (l % TILE)
+        y = (tiles // tx_n) * TILE + (l // TILE)
+        return torch.stack([x, y], 1)
+
+    def scatter_image(self, per_pixel: torch.Tensor) -> torch.Tensor:
+        xy = self.pixel_coords()
+        img = torch.zeros(self.H, self.W, per_pixel.shape[-1], device=per_pixel.device, dtype=per_pixel.dtype)
+        img[xy[:, 1], xy[:, 0]] = per_pixel[:xy.shape[0]]
+        return img
+
+
+def psnr(img: torch.Tensor, ref: torch.Tensor) -> float:
+    mse = torch.mean((img.clamp(0, 1) - ref) ** 2).item()
+    return float(10.0 * math.log10(1.0 / max(mse, 1e-12)))
