@@ -165,6 +165,36 @@ tgs_status tgs_select_tiles(const uint16_t* err_map, const uint16_t* age_map, in
                             uint8_t* pix_idx, tgs_stream stream);
 
 /*
+ * select_tiles_noalloc - the same selection as tgs_select_tiles, for callers
+ * that cannot allocate device memory (the paper has no counterpart: this is a
+ * deployment variant).  Some hosts own all device memory and forbid any other
+ * allocation (a fixed pool handed out by a framework, an embedded runtime),
+ * and on latency-critical paths an allocation may block or synchronise.  This
+ * entry point takes no workspace: its scratch is one device array of
+ * TGS_SELECT_NOALLOC_SCRATCH_BYTES compiled into the library, which every GPU
+ * that loads the library holds until the process exits.  Nothing is
+ * allocated or freed by the call.
+ *   - Views of more than TGS_SELECT_NOALLOC_MAX_TILES tiles are rejected with
+ *     TGS_ERR_CAPACITY before anything is launched.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture.
+ *   - All calls on a device share the one array, and it keeps the last
+ *     call's contents (the call clears what must start at zero itself).  Calls
+ *     that can overlap on the GPU (different streams, or different host
+ *     threads without ordering) race on it: order them on one stream.
+ * Arguments and outputs are those of tgs_select_tiles without the workspace.
+ */
+#define TGS_SELECT_NOALLOC_MAX_TILES 16384
+#define TGS_SELECT_NOALLOC_SCRATCH_BYTES (768u * 1024u)
+#define TGS_SELECT_NOALLOC_MAX_DEVICES 64
+tgs_status tgs_select_tiles_noalloc(const uint16_t* err_map, const uint16_t* age_map, int32_t width,
+                                    int32_t height, int32_t n_select, int32_t n_pix, const tgs_sampling* cfg,
+                                    uint64_t seed, uint64_t iter, const uint64_t* iter_dev, uint32_t view,
+                                    int32_t* active_tiles, int32_t* n_active, int32_t* tile_rank, int32_t* pix_off,
+                                    uint8_t* pix_idx, tgs_stream stream);
+
+/*
  * project_gaussians - EWA projection and SH colour of the 3DGS model the
  * method rasterizes (Sec. 3.1).
  *

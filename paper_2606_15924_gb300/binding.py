@@ -91,6 +91,9 @@ _lib.tgs_select_tiles_workspace_size.argtypes = [_i32, _i32]
 _lib.tgs_select_tiles.restype = _i32
 _lib.tgs_select_tiles.argtypes = [_p, _p, _i32, _i32, _i32, _i32, _P(Sampling), _u64, _u64, _p, _u32, _p, _sz,
                                   _p, _p, _p, _p, _p, _p]
+_lib.tgs_select_tiles_noalloc.restype = _i32
+_lib.tgs_select_tiles_noalloc.argtypes = [_p, _p, _i32, _i32, _i32, _i32, _P(Sampling), _u64, _u64, _p, _u32,
+                                          _p, _p, _p, _p, _p, _p]
 _lib.tgs_project_gaussians.restype = _i32
 _lib.tgs_project_gaussians.argtypes = [_P(Gaussians), _P(Camera), _p, _P(Projected), _p]
 _lib.tgs_bin_tiles_workspace_size.restype = _sz
@@ -111,7 +114,8 @@ _lib.tgs_hybrid_step.argtypes = [_P(ParamPtrs), _P(ParamPtrs), _P(ParamPtrs), _P
                                  _i32, _p, _P(Opt), _p]
 
 EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_device_check", "tgs_graph_count_kernels",
-            "tgs_select_tiles_workspace_size", "tgs_select_tiles", "tgs_project_gaussians",
+            "tgs_select_tiles_workspace_size", "tgs_select_tiles", "tgs_select_tiles_noalloc",
+            "tgs_project_gaussians",
             "tgs_bin_tiles_workspace_size", "tgs_bin_tiles", "tgs_render_sampled", "tgs_loss_sparse_ncc",
             "tgs_backward_sampled", "tgs_hybrid_step"]
 
@@ -189,6 +193,17 @@ def select_tiles(err_map, age_map, width, height, n_select, n_pix, sampling, see
         int(seed) & (2**64 - 1), int(it) & (2**64 - 1), _ptr(iter_dev), int(view), _ptr(workspace),
         workspace.numel(),
         _ptr(active_tiles), _ptr(n_active), _ptr(tile_rank), _ptr(pix_off), _ptr(pix_idx), _stream(stream)))
+
+
+def select_tiles_noalloc(err_map, age_map, width, height, n_select, n_pix, sampling, seed, it, view, active_tiles,
+                         n_active, tile_rank, pix_off, pix_idx, stream=None, iter_dev=None):
+    """select_tiles with the library's built-in scratch instead of a workspace
+    (for callers that cannot allocate device memory; see the C header)."""
+    cfg = Sampling(*sampling)
+    _check("tgs_select_tiles_noalloc", _lib.tgs_select_tiles_noalloc(
+        _ptr(err_map), _ptr(age_map), int(width), int(height), int(n_select), int(n_pix), C.byref(cfg),
+        int(seed) & (2**64 - 1), int(it) & (2**64 - 1), _ptr(iter_dev), int(view), _ptr(active_tiles),
+        _ptr(n_active), _ptr(tile_rank), _ptr(pix_off), _ptr(pix_idx), _stream(stream)))
 
 
 def project_gaussians(g: dict, cam, tile_rank, out: dict, sh_degree=3, stream=None):

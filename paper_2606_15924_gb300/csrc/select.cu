@@ -340,3 +340,122 @@ extern "C" tgs_status tgs_select_tiles(const uint16_t* err_map, const uint16_t* 
                                           active_tiles, n_active, pix_off, pix_idx);
   return check_launch();
 }
+
+// ---------------------------------------------------------------------------
+// select_tiles without a caller workspace.
+//
+// For callers that cannot allocate device memory - for example code running
+// inside a host framework that hands out all device memory from its own fixed
+// pool and forbids any other allocation, or a latency-critical path where an
+// allocation could block or synchronise the device.  The scratch that
+// tgs_select_tiles carves out of `workspace` lives here in one file-scope
+// device array of fixed size instead; every GPU that loads this library holds
+// it until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+__device__ __align__(256) unsigned char g_select_scratch[TGS_SELECT_NOALLOC_SCRATCH_BYTES];
+
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[TGS_SELECT_NOALLOC_MAX_DEVICES] = {};
+
+// Device address of g_select_scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device (with that device current) and cached.
+tgs_status select_scratch_address(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    tgs::set_cuda_error(e);
+    return TGS_ERR_CUDA;
+  }
+  if (dev < 0 || dev >= TGS_SELECT_NOALLOC_MAX_DEVICES) return TGS_ERR_DEVICE;
+  std::lock_guard<std::mutex> lock(g_scratch_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_select_scratch);
+    if (e != cudaSuccess || !p) {
+      tgs::set_cuda_error(e);
+      return TGS_ERR_CUDA;
+    }
+    g_scratch_ptr[dev] = p;
+  }
+  *out = g_scratch_ptr[dev];
+  return TGS_OK;
+}
+
+}  // namespace
+
+extern "C" tgs_status tgs_select_tiles_noalloc(const uint16_t* err_map, const uint16_t* age_map, int32_t width,
+                                               int32_t height, int32_t n_select, int32_t n_pix,
+                                               const tgs_sampling* cfg, uint64_t seed, uint64_t iter,
+                                               const uint64_t* iter_dev, uint32_t view, int32_t* active_tiles,
+                                               int32_t* n_active, int32_t* tile_rank, int32_t* pix_off,
+                                               uint8_t* pix_idx, tgs_stream stream) {
+  if (width <= 0 || height <= 0 || width > (1 << 16) || height > (1 << 16) || n_select < 0 || n_pix < 1 ||
+      n_pix > 256 || !cfg || !err_map || !age_map || !n_active || !tile_rank || !pix_off)
+    return TGS_ERR_INVALID_ARG;
+  const int pms[4] = {cfg->tile_hard_pm, cfg->tile_stable_pm, cfg->pix_hard_pm, cfg->pix_stable_pm};
+  for (int k = 0; k < 4; ++k)
+    if (pms[k] < 0 || pms[k] > 1000) return TGS_ERR_INVALID_ARG;
+  const int T = tiles_x(width) * tiles_y(height);
+  if (T > TGS_SELECT_NOALLOC_MAX_TILES) return TGS_ERR_CAPACITY;
+  size_t need = 0;
+  carve_sel(nullptr, T, &need);
+  if (need > sizeof(g_select_scratch)) return TGS_ERR_CAPACITY;
+  const int n_sel = std::min(n_select, T);
+  if (n_sel > 0 && (!active_tiles || !pix_idx)) return TGS_ERR_INVALID_ARG;
+  void* scratch = nullptr;
+  tgs_status st = select_scratch_address(&scratch);
+  if (st != TGS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  size_t tot;
+  SelWs w = carve_sel(scratch, T, &tot);
+  SelGeom g{width, height, tiles_x(width), T};
+  const HashKeys hk{seed, iter, iter_dev, view};
+  int kh, ks;
+  split_counts(n_sel, cfg->tile_hard_pm, cfg->tile_stable_pm, kh, ks);
+  // the rank counters accumulate with atomics: clear the previous call's values
+  cudaMemsetAsync(w.rank_h, 0, sizeof(int32_t) * 3 * (size_t)T, s);
+  if (n_sel < T && n_sel > 0) {
+    k_tile_stats<<<T, 256, 0, s>>>(err_map, age_map, g, hk, w);
+    dim3 grid((T + 255) / 256, (T + RANK_CHUNK - 1) / RANK_CHUNK);
+    if (kh > 0) k_rank_tiles<<<grid, 256, 0, s>>>(w, T, 0, kh, ks);
+    if (ks > 0) k_rank_tiles<<<grid, 256, 0, s>>>(w, T, 1, kh, ks);
+    if (n_sel - kh - ks > 0) k_rank_tiles<<<grid, 256, 0, s>>>(w, T, 2, kh, ks);
+  }
+  {
+    const int32_t* rh = w.rank_h;
+    const int32_t* rs = w.rank_s;
+    const int32_t* ru = w.rank_u;
+    const int all = n_sel >= T ? 1 : 0, none = n_sel == 0 ? 1 : 0;
+    const int ku = n_sel - kh - ks;
+    const int npx = n_pix;
+    int32_t* at = active_tiles;
+    int32_t* tr = tile_rank;
+    int32_t* po = pix_off;
+    auto load = [=] __device__(int64_t t) -> int64_t {
+      bool taken = !none && (all || rh[t] < kh || rs[t] < ks || (rs[t] >= ks && ru[t] < ku));
+      if (!taken) return 0;
+      return (1ll << 32) | (int64_t)min(npx, tile_valid(g, (int)t));
+    };
+    auto store = [=] __device__(int64_t t, int64_t pre, int64_t v) {
+      if (v) {
+        const int r = (int)(pre >> 32);
+        tr[t] = r;
+        at[r] = (int)t;
+        po[r] = (int)(pre & 0xFFFFFFFFll);
+      } else {
+        tr[t] = -1;
+      }
+    };
+    exclusive_scan<int64_t>(load, store, nullptr, T, w.scan_sums, w.total, s);
+  }
+  k_sel_finish<<<1, 1, 0, s>>>(w.total, n_active, pix_off);
+  if (n_sel > 0)
+    k_sample_pixels<<<n_sel, 256, 0, s>>>(err_map, age_map, g, n_pix, cfg->pix_hard_pm, cfg->pix_stable_pm, hk,
+                                          active_tiles, n_active, pix_off, pix_idx);
+  return check_launch();
+}
