@@ -172,7 +172,10 @@ def stage_times(tr, steps, flush):
         A = int(tr.n_active.item())
         P = int(tr.pix_off[A].item())
         evals += int(tr.n_last[:P].sum().item())
-    info = dict(P=P, A=A, n_isect=int(tr.n_isect.item()), evals_per_step=evals / steps,
+    rl = (tr.ranges[:A, 1] - tr.ranges[:A, 0]).float()
+    info_tiles = dict(list_mean=float(rl.mean().item()), list_max=int(rl.max().item()),
+                      n_last_mean=float(tr.n_last[:P].float().mean().item()), n_last_max=int(tr.n_last[:P].max().item()))
+    info = dict(tiles=info_tiles, P=P, A=A, n_isect=int(tr.n_isect.item()), evals_per_step=evals / steps,
                 touched=int(tr.touched.sum().item()) if tr.train else 0,
                 visible=int((tr.proj["radius"] > 0).sum().item()))
     return {n: acc[n] / steps for n in acc}, info
@@ -358,7 +361,7 @@ def run_ours(args):
            "roofline": roof, "clocks": clocks,
            "sampled": {"iters_per_s": 1e3 / mean_s, "ms_per_step": mean_s, "sampled_pixels": info["P"],
                        "active_tiles": info["A"], "tile_pairs": info["n_isect"], "touched": info["touched"],
-                       "visible": info["visible"], "splat_evals": info["evals_per_step"],
+                       "visible": info["visible"], "splat_evals": info["evals_per_step"], "tile_lists": info["tiles"],
                        "fwd_bwd_mpix_per_s": mpix, "stage_ms": st, "kernels_per_step": launches}}
     if ms_d is not None:
         mean_d = sum(ms_d) / len(ms_d)

@@ -309,11 +309,15 @@ tgs_status tgs_backward_sampled(const tgs_gaussians* g, const tgs_camera* cam, c
  * everything in mode 0) take the bias-corrected Adam step
  * -lr m_hat / (sqrt(v_hat) + eps_adam) at step `step` (>= 1), or, when
  * step_dev (device int32) is given, at the step read from it at run time.
+ * touched may be NULL (every Gaussian updated).  The touched Gaussians are
+ * first compacted into a list in `workspace`
+ * (tgs_hybrid_step_workspace_size(n) bytes), so the update kernels run dense.
  */
+size_t tgs_hybrid_step_workspace_size(int64_t n);
 tgs_status tgs_hybrid_step(const tgs_param_ptrs* params, const tgs_param_ptrs* grads, const tgs_param_ptrs* m,
                            const tgs_param_ptrs* v, int64_t n, const uint8_t* touched, const float* view_rows,
                            int32_t k_rows, int32_t step, const int32_t* step_dev, const tgs_opt* opt,
-                           tgs_stream stream);
+                           void* workspace, size_t workspace_bytes, tgs_stream stream);
 
 #ifdef __cplusplus
 }

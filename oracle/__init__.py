@@ -75,6 +75,8 @@ def _declare(L):
     L.orc_hash.restype = _u64
     L.orc_neglog2_q32.argtypes = [_u64]
     L.orc_neglog2_q32.restype = _u64
+    L.orc_hard_key.argtypes = [_u64, _u64]
+    L.orc_hard_key.restype = _d
     L.orc_err_weight.argtypes = [C.c_uint16]
     L.orc_err_weight.restype = _u64
     L.orc_choose_items.argtypes = [_i32, _p, _p, _i32, _i32, _i32, _u64, _u64, _u32, _u32, _p]
@@ -187,6 +189,10 @@ def hash_(seed, it, view, stream, tile, item) -> int:
 
 def neglog2_q32(h: int) -> int:
     return int(lib().orc_neglog2_q32(h & (2**64 - 1)))
+
+
+def hard_key(w: int, L: int) -> float:
+    return float(lib().orc_hard_key(int(w), int(L)))
 
 
 def err_weight(h: int) -> int:

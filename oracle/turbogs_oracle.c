@@ -491,18 +491,20 @@ typedef struct {
 /*
  * Order of the error-proportional draw without replacement
  * (Efraimidis-Spirakis: ascending L_i / w_i is the order of successive
- * weighted draws).  Items of weight 0 follow all positive weights, in uniform
- * random order (ascending L); ties by index.
+ * weighted draws).  The key is L / w in IEEE double precision (both integers
+ * are exact in double, the division is correctly rounded, so the key is the
+ * same on every machine); items of weight 0 follow every positive weight in
+ * uniform random order (key L * 2^900, larger than any L / w with w >= 1).
+ * Equal keys go to the lower index.
  */
+double orc_hard_key(uint64_t w, uint64_t L) {
+  return w ? (double)L / (double)w : ldexp((double)L, 900);
+}
 static int cmp_hard(const void* a, const void* b) {
   const item_t* x = (const item_t*)a;
   const item_t* y = (const item_t*)b;
-  int xz = x->w == 0, yz = y->w == 0;
-  if (xz != yz) return xz - yz;
-  if (!xz) {
-    unsigned __int128 l = (unsigned __int128)x->L * y->w, r = (unsigned __int128)y->L * x->w;
-    if (l != r) return l < r ? -1 : 1;
-  } else if (x->L != y->L) return x->L < y->L ? -1 : 1;
+  double kx = orc_hard_key(x->w, x->L), ky = orc_hard_key(y->w, y->L);
+  if (kx != ky) return kx < ky ? -1 : 1;
   return x->idx - y->idx;
 }
 static int cmp_age(const void* a, const void* b) {   /* descending age, ties by index */
@@ -511,10 +513,11 @@ static int cmp_age(const void* a, const void* b) {   /* descending age, ties by 
   if (x->age != y->age) return x->age > y->age ? -1 : 1;
   return x->idx - y->idx;
 }
-static int cmp_unif(const void* a, const void* b) {  /* ascending uniform key */
+static int cmp_unif(const void* a, const void* b) {  /* ascending top 32 hash bits, then index */
   const item_t* x = (const item_t*)a;
   const item_t* y = (const item_t*)b;
-  if (x->u != y->u) return x->u < y->u ? -1 : 1;
+  uint32_t ux = (uint32_t)(x->u >> 32), uy = (uint32_t)(y->u >> 32);
+  if (ux != uy) return ux < uy ? -1 : 1;
   return x->idx - y->idx;
 }
 static int cmp_idx(const void* a, const void* b) {

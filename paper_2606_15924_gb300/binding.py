@@ -110,14 +110,16 @@ _lib.tgs_backward_sampled.restype = _i32
 _lib.tgs_backward_sampled.argtypes = [_P(Gaussians), _P(Camera), _P(Projected), _p, _p, _p, _p, _i32, _p, _p,
                                       _i32, _p, _p, _p, _p, _p, _P(ParamPtrs), _p, _i32, _p]
 _lib.tgs_hybrid_step.restype = _i32
+_lib.tgs_hybrid_step_workspace_size.restype = _sz
+_lib.tgs_hybrid_step_workspace_size.argtypes = [_i64]
 _lib.tgs_hybrid_step.argtypes = [_P(ParamPtrs), _P(ParamPtrs), _P(ParamPtrs), _P(ParamPtrs), _i64, _p, _p, _i32,
-                                 _i32, _p, _P(Opt), _p]
+                                 _i32, _p, _P(Opt), _p, _sz, _p]
 
 EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_device_check", "tgs_graph_count_kernels",
             "tgs_select_tiles_workspace_size", "tgs_select_tiles", "tgs_select_tiles_noalloc",
             "tgs_project_gaussians",
             "tgs_bin_tiles_workspace_size", "tgs_bin_tiles", "tgs_render_sampled", "tgs_loss_sparse_ncc",
-            "tgs_backward_sampled", "tgs_hybrid_step"]
+            "tgs_backward_sampled", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step"]
 
 
 def _check(fn, status):
@@ -261,9 +263,15 @@ def backward_sampled(g: dict, cam, proj: dict, tile_ranges, vals, active_tiles, 
         _ptr(dL_drgb), _ptr(grad2d), C.byref(gp), _ptr(touched), 1 if write_untouched else 0, _stream(stream)))
 
 
+def hybrid_step_workspace_size(n: int) -> int:
+    return int(_lib.tgs_hybrid_step_workspace_size(int(n)))
+
+
 def hybrid_step(params: dict, grads: dict, m: dict, v: dict, n, touched, view_rows, k_rows, step, opt,
-                stream=None, step_dev=None):
+                workspace=None, stream=None, step_dev=None):
     P, G, M, V = param_ptrs(params), param_ptrs(grads), param_ptrs(m), param_ptrs(v)
+    if workspace is None:
+        workspace = torch.empty(hybrid_step_workspace_size(n), dtype=torch.uint8, device=params["means"].device)
     o = Opt()
     lrs = opt["lr"]
     o.lr = (C.c_float * 6)(*[float(x) for x in lrs])
@@ -272,4 +280,4 @@ def hybrid_step(params: dict, grads: dict, m: dict, v: dict, n, touched, view_ro
     o.mode = int(opt["mode"])
     _check("tgs_hybrid_step", _lib.tgs_hybrid_step(
         C.byref(P), C.byref(G), C.byref(M), C.byref(V), int(n), _ptr(touched), _ptr(view_rows), int(k_rows),
-        int(step), _ptr(step_dev), C.byref(o), _stream(stream)))
+        int(step), _ptr(step_dev), C.byref(o), _ptr(workspace), workspace.numel(), _stream(stream)))

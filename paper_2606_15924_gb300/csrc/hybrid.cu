@@ -87,18 +87,40 @@ __device__ __forceinline__ float adam_delta(float m, float v, float lr, const Op
   return -lr * (m / o.bc1) / (sqrtf(v / o.bc2) + o.eps);
 }
 
-__global__ void __launch_bounds__(128) k_hybrid(tgs_param_ptrs P, tgs_param_ptrs G, tgs_param_ptrs M,
-                                                tgs_param_ptrs V, int64_t n, const uint8_t* __restrict__ touched,
-                                                const float* __restrict__ rows, int k_rows, OptK o) {
+// Touched Gaussians appended to a list (order irrelevant: updates are
+// independent), one warp-aggregated atomic per warp.
+__global__ void __launch_bounds__(256) k_compact_touched(const uint8_t* __restrict__ touched, int64_t n,
+                                                         int32_t* __restrict__ list, int32_t* __restrict__ count) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  if (touched && !touched[i]) return;
+  const bool on = i < n && (!touched || touched[i]);
+  const unsigned b = __ballot_sync(0xffffffffu, on);
+  if (!b) return;
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == __ffs(b) - 1) base = atomicAdd(count, __popc(b));
+  base = __shfl_sync(0xffffffffu, base, __ffs(b) - 1);
+  if (on) list[base + __popc(b & ((1u << lane) - 1u))] = (int32_t)i;
+}
+
+__device__ __forceinline__ void bias_corrections(OptK& o) {
   if (o.step_dev) {
     const float st = (float)max(1, *o.step_dev);
     o.bc1 = 1.f - powf(o.b1, st);
     o.bc2 = 1.f - powf(o.b2, st);
   }
-  // geometry block: means 3, log_scales 3, quats 4
+}
+
+// LM blocks (geometry 10, appearance 4) and the first SH float4 (DC colour +
+// one higher coefficient) of each touched Gaussian.
+template <int MODE>
+__global__ void __launch_bounds__(128) k_hybrid_lm(tgs_param_ptrs P, tgs_param_ptrs G, tgs_param_ptrs M,
+                                                   tgs_param_ptrs V, int64_t n, const int32_t* __restrict__ list,
+                                                   const int32_t* __restrict__ count, const float* __restrict__ rows,
+                                                   int k_rows, OptK o) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= *count) return;
+  const int64_t i = list[q];
+  bias_corrections(o);
   float gp[10], gg[10], gm[10], gv[10];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -114,23 +136,17 @@ __global__ void __launch_bounds__(128) k_hybrid(tgs_param_ptrs P, tgs_param_ptrs
     gm[6] = c.x; gm[7] = c.y; gm[8] = c.z; gm[9] = c.w;
     gv[6] = d.x; gv[7] = d.y; gv[8] = d.z; gv[9] = d.w;
   }
-  // SH: the first float4 holds the DC colour (LM block) and the first higher
-  // coefficient; the other 11 float4 are Adam-only and are streamed below.
-  const float4* Ps = reinterpret_cast<const float4*>(P.sh) + 12 * i;
-  const float4* Gs = reinterpret_cast<const float4*>(G.sh) + 12 * i;
-  const float4* Ms = reinterpret_cast<const float4*>(M.sh) + 12 * i;
-  const float4* Vs = reinterpret_cast<const float4*>(V.sh) + 12 * i;
-  float4 p0 = Ps[0], g0 = Gs[0], m0 = Ms[0], v0 = Vs[0];
+  const float4 p0 = reinterpret_cast<const float4*>(P.sh)[12 * i], g0 = reinterpret_cast<const float4*>(G.sh)[12 * i];
+  const float4 m0 = reinterpret_cast<const float4*>(M.sh)[12 * i], v0 = reinterpret_cast<const float4*>(V.sh)[12 * i];
   float sp[4] = {p0.x, p0.y, p0.z, p0.w}, sg[4] = {g0.x, g0.y, g0.z, g0.w};
   float smm[4] = {m0.x, m0.y, m0.z, m0.w}, sv[4] = {v0.x, v0.y, v0.z, v0.w};
   float op = P.opacity_logits[i], og = G.opacity_logits[i], om = M.opacity_logits[i], ov = V.opacity_logits[i];
-  // moments
 #pragma unroll
   for (int k = 0; k < 10; ++k) moments(gg[k], gm[k], gv[k], o);
 #pragma unroll
   for (int k = 0; k < 4; ++k) moments(sg[k], smm[k], sv[k], o);
   moments(og, om, ov, o);
-  if (o.mode == 0) {
+  if (MODE == 0) {
 #pragma unroll
     for (int k = 0; k < 10; ++k) gp[k] += adam_delta(gm[k], gv[k], o.lr[k < 3 ? 0 : k < 6 ? 1 : 2], o);
 #pragma unroll
@@ -138,19 +154,18 @@ __global__ void __launch_bounds__(128) k_hybrid(tgs_param_ptrs P, tgs_param_ptrs
     op += adam_delta(om, ov, o.lr[3], o);
   } else {
     float dgeo[10];
-    lm_block<10>(gg, gm, gv, rows, k_rows, n, i, 0, o.mode, o.eps_lm, dgeo);
+    lm_block<10>(gg, gm, gv, rows, k_rows, n, i, 0, MODE, o.eps_lm, dgeo);
 #pragma unroll
     for (int k = 0; k < 10; ++k) gp[k] += o.lr[k < 3 ? 0 : k < 6 ? 1 : 2] * dgeo[k];
     const float ag[4] = {sg[0], sg[1], sg[2], og}, am[4] = {smm[0], smm[1], smm[2], om},
                 av[4] = {sv[0], sv[1], sv[2], ov};
     float dapp[4];
-    lm_block<4>(ag, am, av, rows, k_rows, n, i, 10, o.mode, o.eps_lm, dapp);
+    lm_block<4>(ag, am, av, rows, k_rows, n, i, 10, MODE, o.eps_lm, dapp);
 #pragma unroll
     for (int k = 0; k < 3; ++k) sp[k] += o.lr[4] * dapp[k];
     op += o.lr[3] * dapp[3];
   }
   sp[3] += adam_delta(smm[3], sv[3], o.lr[5], o);
-  // write back
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     P.means[3 * i + k] = gp[k]; M.means[3 * i + k] = gm[k]; V.means[3 * i + k] = gv[k];
@@ -160,22 +175,31 @@ __global__ void __launch_bounds__(128) k_hybrid(tgs_param_ptrs P, tgs_param_ptrs
   reinterpret_cast<float4*>(M.quats)[i] = make_float4(gm[6], gm[7], gm[8], gm[9]);
   reinterpret_cast<float4*>(V.quats)[i] = make_float4(gv[6], gv[7], gv[8], gv[9]);
   P.opacity_logits[i] = op; M.opacity_logits[i] = om; V.opacity_logits[i] = ov;
-  float4* Pw = reinterpret_cast<float4*>(P.sh) + 12 * i;
-  float4* Mw = reinterpret_cast<float4*>(M.sh) + 12 * i;
-  float4* Vw = reinterpret_cast<float4*>(V.sh) + 12 * i;
-  Pw[0] = make_float4(sp[0], sp[1], sp[2], sp[3]);
-  Mw[0] = make_float4(smm[0], smm[1], smm[2], smm[3]);
-  Vw[0] = make_float4(sv[0], sv[1], sv[2], sv[3]);
-  // higher SH coefficients: Adam, streamed four at a time
-#pragma unroll 2
-  for (int k = 1; k < 12; ++k) {
-    float4 pp = Ps[k], gq = Gs[k], mq = Ms[k], vq = Vs[k];
-    moments(gq.x, mq.x, vq.x, o); moments(gq.y, mq.y, vq.y, o);
-    moments(gq.z, mq.z, vq.z, o); moments(gq.w, mq.w, vq.w, o);
-    pp.x += adam_delta(mq.x, vq.x, o.lr[5], o); pp.y += adam_delta(mq.y, vq.y, o.lr[5], o);
-    pp.z += adam_delta(mq.z, vq.z, o.lr[5], o); pp.w += adam_delta(mq.w, vq.w, o.lr[5], o);
-    Pw[k] = pp; Mw[k] = mq; Vw[k] = vq;
-  }
+  reinterpret_cast<float4*>(P.sh)[12 * i] = make_float4(sp[0], sp[1], sp[2], sp[3]);
+  reinterpret_cast<float4*>(M.sh)[12 * i] = make_float4(smm[0], smm[1], smm[2], smm[3]);
+  reinterpret_cast<float4*>(V.sh)[12 * i] = make_float4(sv[0], sv[1], sv[2], sv[3]);
+}
+
+// Adam on SH float4s 1..11 of each touched Gaussian: one thread per float4,
+// eleven consecutive threads per Gaussian (176 contiguous bytes per array).
+__global__ void __launch_bounds__(256) k_adam_sh(tgs_param_ptrs P, tgs_param_ptrs G, tgs_param_ptrs M,
+                                                 tgs_param_ptrs V, const int32_t* __restrict__ list,
+                                                 const int32_t* __restrict__ count, OptK o) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (int64_t)*count * 11) return;
+  bias_corrections(o);
+  const int64_t q = e / 11;
+  const int k = 1 + (int)(e - q * 11);
+  const int64_t f = 12 * (int64_t)list[q] + k;
+  float4 pp = reinterpret_cast<const float4*>(P.sh)[f], gq = reinterpret_cast<const float4*>(G.sh)[f];
+  float4 mq = reinterpret_cast<const float4*>(M.sh)[f], vq = reinterpret_cast<const float4*>(V.sh)[f];
+  moments(gq.x, mq.x, vq.x, o); moments(gq.y, mq.y, vq.y, o);
+  moments(gq.z, mq.z, vq.z, o); moments(gq.w, mq.w, vq.w, o);
+  pp.x += adam_delta(mq.x, vq.x, o.lr[5], o); pp.y += adam_delta(mq.y, vq.y, o.lr[5], o);
+  pp.z += adam_delta(mq.z, vq.z, o.lr[5], o); pp.w += adam_delta(mq.w, vq.w, o.lr[5], o);
+  reinterpret_cast<float4*>(P.sh)[f] = pp;
+  reinterpret_cast<float4*>(M.sh)[f] = mq;
+  reinterpret_cast<float4*>(V.sh)[f] = vq;
 }
 
 static bool ptrs_ok(const tgs_param_ptrs* p) {
@@ -187,22 +211,37 @@ static bool ptrs_ok(const tgs_param_ptrs* p) {
 
 using namespace tgs;
 
+extern "C" size_t tgs_hybrid_step_workspace_size(int64_t n) {
+  return align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1), 256) + 256;
+}
+
 extern "C" tgs_status tgs_hybrid_step(const tgs_param_ptrs* params, const tgs_param_ptrs* grads,
                                       const tgs_param_ptrs* m, const tgs_param_ptrs* v, int64_t n,
                                       const uint8_t* touched, const float* view_rows, int32_t k_rows, int32_t step,
-                                      const int32_t* step_dev, const tgs_opt* opt, tgs_stream stream) {
+                                      const int32_t* step_dev, const tgs_opt* opt, void* workspace,
+                                      size_t workspace_bytes, tgs_stream stream) {
   if (n < 0 || !opt || step < 1 || opt->mode < 0 || opt->mode > 2 || (view_rows && k_rows < 1) ||
-      !(opt->beta1 >= 0.f && opt->beta1 < 1.f) || !(opt->beta2 >= 0.f && opt->beta2 < 1.f))
+      !(opt->beta1 >= 0.f && opt->beta1 < 1.f) || !(opt->beta2 >= 0.f && opt->beta2 < 1.f) || n >= INT32_MAX)
     return TGS_ERR_INVALID_ARG;
   if (n == 0) return TGS_OK;
   if (!ptrs_ok(params) || !ptrs_ok(grads) || !ptrs_ok(m) || !ptrs_ok(v)) return TGS_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < tgs_hybrid_step_workspace_size(n)) return TGS_ERR_INVALID_ARG;
   OptK o;
   for (int k = 0; k < 6; ++k) o.lr[k] = opt->lr[k];
   o.b1 = opt->beta1; o.b2 = opt->beta2; o.eps = opt->eps_adam; o.eps_lm = opt->eps_lm; o.mode = opt->mode;
   o.step_dev = step_dev;
   o.bc1 = (float)(1.0 - pow((double)opt->beta1, (double)step));
   o.bc2 = (float)(1.0 - pow((double)opt->beta2, (double)step));
-  k_hybrid<<<(int)((n + 127) / 128), 128, 0, (cudaStream_t)stream>>>(*params, *grads, *m, *v, n, touched,
-                                                                       view_rows, k_rows, o);
+  cudaStream_t s = (cudaStream_t)stream;
+  Carver c(workspace);
+  int32_t* list = c.take<int32_t>((size_t)n);
+  int32_t* count = c.take<int32_t>(1);
+  cudaMemsetAsync(count, 0, sizeof(int32_t), s);
+  k_compact_touched<<<(int)((n + 255) / 256), 256, 0, s>>>(touched, n, list, count);
+  const int lb = (int)((n + 127) / 128);
+  if (o.mode == 0) k_hybrid_lm<0><<<lb, 128, 0, s>>>(*params, *grads, *m, *v, n, list, count, view_rows, k_rows, o);
+  else if (o.mode == 1) k_hybrid_lm<1><<<lb, 128, 0, s>>>(*params, *grads, *m, *v, n, list, count, view_rows, k_rows, o);
+  else k_hybrid_lm<2><<<lb, 128, 0, s>>>(*params, *grads, *m, *v, n, list, count, view_rows, k_rows, o);
+  k_adam_sh<<<(int)((n * 11 + 255) / 256), 256, 0, s>>>(*params, *grads, *m, *v, list, count, o);
   return check_launch();
 }

@@ -9,7 +9,7 @@ namespace tgs {
 
 constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
-constexpr int RS_ROUNDS = 16;
+constexpr int RS_ROUNDS = 4;
 constexpr int RS_TILE = RS_THREADS * RS_ROUNDS;  // pairs per block
 constexpr int RS_BINS = 256;
 

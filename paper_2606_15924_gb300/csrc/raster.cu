@@ -62,6 +62,13 @@ struct RasterArgs {
   float bg[3];
 };
 
+__device__ __forceinline__ void load_splat(const RasterArgs& a, int k, Splat& sp) {
+  const int id = a.vals[k];
+  sp.xy = a.xy[id];
+  sp.co = a.conic_opac[id];
+  sp.rgb = make_float4(a.rgb[3 * id], a.rgb[3 * id + 1], a.rgb[3 * id + 2], __int_as_float(id));
+}
+
 __global__ void k_render_fwd(RasterArgs a, float* __restrict__ out_rgb, float* __restrict__ out_T,
                              int32_t* __restrict__ out_last) {
   extern __shared__ Splat sm[];
@@ -69,9 +76,8 @@ __global__ void k_render_fwd(RasterArgs a, float* __restrict__ out_rgb, float* _
   if (j >= *a.n_active) return;
   const int t = a.active_tiles ? a.active_tiles[j] : j;
   const int p0 = a.pix_off[j], p1 = a.pix_off[j + 1];
-  const int lane_pix = threadIdx.x;
-  const bool has_pix = p0 + lane_pix < p1;
-  const int s = p0 + lane_pix;
+  const bool has_pix = p0 + (int)threadIdx.x < p1;
+  const int s = p0 + threadIdx.x;
   float px = 0.f, py = 0.f;
   if (has_pix) {
     const int l = a.pix_idx[s];
@@ -83,18 +89,14 @@ __global__ void k_render_fwd(RasterArgs a, float* __restrict__ out_rgb, float* _
   int last = 0;
   bool done = !has_pix;
   const int B = blockDim.x;
+  // the next batch is fetched into registers while the current one is blended
+  Splat nxt;
+  if (range.x + (int)threadIdx.x < range.y) load_splat(a, range.x + threadIdx.x, nxt);
   for (int base = range.x; base < range.y; base += B) {
     if (__syncthreads_count(done) == B) break;
-    const int k = base + threadIdx.x;
-    if (k < range.y) {
-      const int id = a.vals[k];
-      Splat sp;
-      sp.xy = a.xy[id];
-      sp.co = a.conic_opac[id];
-      sp.rgb = make_float4(a.rgb[3 * id], a.rgb[3 * id + 1], a.rgb[3 * id + 2], 0.f);
-      sm[threadIdx.x] = sp;
-    }
+    if (base + (int)threadIdx.x < range.y) sm[threadIdx.x] = nxt;
     __syncthreads();
+    if (base + B + (int)threadIdx.x < range.y) load_splat(a, base + B + threadIdx.x, nxt);
     const int cnt = min(B, range.y - base);
     if (!done) {
       for (int q = 0; q < cnt; ++q) {
@@ -122,6 +124,36 @@ __global__ void k_render_fwd(RasterArgs a, float* __restrict__ out_rgb, float* _
     out_T[s] = T;
     out_last[s] = last;
   }
+}
+
+// Sum of v[0..7] over the warp, scattered: lane l ends with the total of
+// v[(l >> 2) & 7] (halving exchanges at distances 16, 8, 4, then a butterfly
+// over the last two bits): 9 shuffles instead of 40.
+__device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[9], int lane) {
+  float a4[4], b2[2];
+  {
+    const bool up = lane & 16;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float send = up ? v[k] : v[4 + k];
+      const float keep = up ? v[4 + k] : v[k];
+      a4[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+  }
+  {
+    const bool up = lane & 8;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float send = up ? a4[k] : a4[2 + k];
+      const float keep = up ? a4[2 + k] : a4[k];
+      b2[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+  }
+  const bool up = lane & 4;
+  float c = (up ? b2[1] : b2[0]) + __shfl_xor_sync(0xffffffffu, up ? b2[0] : b2[1], 4);
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  return c;
 }
 
 __global__ void k_render_bwd(RasterArgs a, const float* __restrict__ T_final, const int32_t* __restrict__ n_last,
@@ -155,20 +187,25 @@ __global__ void k_render_bwd(RasterArgs a, const float* __restrict__ T_final, co
   float S0 = a.bg[0], S1 = a.bg[1], S2 = a.bg[2];
   const int B = blockDim.x;
   const int lane = threadIdx.x & 31;
+  Splat nxt;
+  if (end - B + (int)threadIdx.x >= range.x && (int)threadIdx.x < B && end > range.x) {
+    const int k = end - B + threadIdx.x;
+    if (k >= range.x) load_splat(a, k, nxt);
+  }
   for (int top = end; top > range.x; top -= B) {
     const int lo = max(range.x, top - B);
     const int cnt = top - lo;
     __syncthreads();
-    if ((int)threadIdx.x < cnt) {
-      const int k = lo + threadIdx.x;
-      const int id = a.vals[k];
-      Splat sp;
-      sp.xy = a.xy[id];
-      sp.co = a.conic_opac[id];
-      sp.rgb = make_float4(a.rgb[3 * id], a.rgb[3 * id + 1], a.rgb[3 * id + 2], __int_as_float(id));
-      sm[threadIdx.x] = sp;
+    // batch [top - B, top) was fetched into slot threadIdx.x - (B - cnt)
+    {
+      const int k = top - B + (int)threadIdx.x;
+      if (k >= range.x) sm[threadIdx.x - (B - cnt)] = nxt;
     }
     __syncthreads();
+    {
+      const int k = top - 2 * B + (int)threadIdx.x;
+      if (k >= range.x) load_splat(a, k, nxt);
+    }
     for (int q = cnt - 1; q >= 0; --q) {
       const Splat sp = sm[q];
       const int pos = lo + q - range.x;  // position in the tile list
@@ -200,14 +237,11 @@ __global__ void k_render_bwd(RasterArgs a, const float* __restrict__ T_final, co
         }
       }
       if (__any_sync(0xffffffffu, hit)) {
-#pragma unroll
-        for (int c = 0; c < 9; ++c) v[c] = warp_sum(v[c]);
-        if (lane == 0) {
-          float* gp = grad2d + 12 * (size_t)__float_as_int(sp.rgb.w);
-          red_add_v4(gp, v[0], v[1], v[2], v[3]);
-          red_add_v4(gp + 4, v[4], v[5], v[6], v[7]);
-          atomicAdd(gp + 8, v[8]);
-        }
+        const float r8 = warp_reduce_scatter8(v, lane);
+        const float r9 = warp_sum(v[8]);
+        float* gp = grad2d + 12 * (size_t)__float_as_int(sp.rgb.w);
+        if ((lane & 3) == 0) atomicAdd(gp + ((lane >> 2) & 7), r8);
+        else if (lane == 1) atomicAdd(gp + 8, r9);
       }
     }
   }

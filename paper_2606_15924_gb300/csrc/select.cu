@@ -48,18 +48,14 @@ __device__ __forceinline__ int tile_valid(const SelGeom& g, int t) {
   return min(TGS_TILE, g.W - tx * TGS_TILE) * min(TGS_TILE, g.H - ty * TGS_TILE);
 }
 
-// hard order: positive weights first by L_i / w_i ascending, then zero
-// weights by L ascending; ties by index.  true when (a) precedes (b).
-__device__ __forceinline__ bool hard_before(uint64_t wa, uint64_t La, int ia, uint64_t wb, uint64_t Lb, int ib) {
-  const bool za = wa == 0, zb = wb == 0;
-  if (za != zb) return zb;
-  if (!za) {
-    if (mul128_less(La, wb, Lb, wa)) return true;
-    if (mul128_less(Lb, wa, La, wb)) return false;
-  } else if (La != Lb) {
-    return La < Lb;
-  }
-  return ia < ib;
+// Hard order: ascending L / w in IEEE double (exact operands, correctly
+// rounded division, so every machine computes the same key); weight 0 maps to
+// L * 2^900, after every positive weight.  Positive doubles order like their
+// bit patterns, so the key is used as an unsigned 64-bit integer; equal keys
+// go to the lower index.
+__device__ __forceinline__ uint64_t hard_key(uint64_t w, uint64_t L) {
+  const double k = w ? __ddiv_rn(__ull2double_rn(L), __ull2double_rn(w)) : __ull2double_rn(L) * 0x1p900;
+  return (uint64_t)__double_as_longlong(k);
 }
 
 // Per-tile weight (sum), age (min) and the tile's random keys.
@@ -115,58 +111,68 @@ __global__ void __launch_bounds__(256) k_tile_stats(const uint16_t* __restrict__
 // rank[i] += #{j in this block's chunk, eligible, preceding i} for the phase.
 // phase 0: hard order among all; 1: age order among those not taken by phase
 // 0; 2: uniform order among those not taken by phases 0 and 1.
-constexpr int RANK_CHUNK = 256;
+constexpr int RANK_CHUNK = 64;
 
 __global__ void __launch_bounds__(256) k_rank_tiles(SelWs w, int T, int phase, int kh, int ks) {
-  __shared__ uint64_t s_a[RANK_CHUNK];
-  __shared__ uint64_t s_b[RANK_CHUNK];
+  __shared__ uint64_t s_k[RANK_CHUNK];
   __shared__ uint8_t s_e[RANK_CHUNK];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j0 = blockIdx.y * RANK_CHUNK;
-  {
+  // phase key, ascending, ties to the lower index:
+  //  0: hard key; 1: (2^32 - 1 - age) (older first); 2: top 32 hash bits
+  auto key = [&](int t) -> uint64_t {
+    if (phase == 0) return hard_key(w.tile_w[t], w.tile_L[t]);
+    if (phase == 1) return 0xFFFFFFFFull - w.tile_age[t];
+    return w.tile_u[t] >> 32;
+  };
+  if (threadIdx.x < RANK_CHUNK) {
     const int j = j0 + threadIdx.x;
     bool e = j < T;
     if (e && phase >= 1) e = w.rank_h[j] >= kh;
     if (e && phase >= 2) e = w.rank_s[j] >= ks;
     s_e[threadIdx.x] = e;
-    if (j < T) {
-      if (phase == 0) {
-        s_a[threadIdx.x] = w.tile_w[j];
-        s_b[threadIdx.x] = w.tile_L[j];
-      } else if (phase == 1) {
-        s_a[threadIdx.x] = w.tile_age[j];
-      } else {
-        s_a[threadIdx.x] = w.tile_u[j];
-      }
-    }
+    s_k[threadIdx.x] = j < T ? key(j) : 0;
   }
   __syncthreads();
   if (i >= T) return;
   if (phase >= 1 && w.rank_h[i] < kh) return;
   if (phase >= 2 && w.rank_s[i] < ks) return;
+  const uint64_t ki = key(i);
   int cnt = 0;
   const int jn = min(RANK_CHUNK, T - j0);
-  if (phase == 0) {
-    const uint64_t wi = w.tile_w[i], Li = w.tile_L[i];
-    for (int k = 0; k < jn; ++k) cnt += hard_before(s_a[k], s_b[k], j0 + k, wi, Li, i);
-  } else if (phase == 1) {
-    const uint32_t ai = w.tile_age[i];
-    for (int k = 0; k < jn; ++k) {
-      const uint32_t aj = (uint32_t)s_a[k];
-      cnt += s_e[k] && (aj > ai || (aj == ai && j0 + k < i));
-    }
-  } else {
-    const uint64_t ui = w.tile_u[i];
-    for (int k = 0; k < jn; ++k) {
-      const uint64_t uj = s_a[k];
-      cnt += s_e[k] && (uj < ui || (uj == ui && j0 + k < i));
-    }
+  for (int k = 0; k < jn; ++k) {
+    const uint64_t kj = s_k[k];
+    cnt += s_e[k] && (kj < ki || (kj == ki && j0 + k < i));
   }
   if (cnt) atomicAdd(phase == 0 ? &w.rank_h[i] : phase == 1 ? &w.rank_s[i] : &w.rank_u[i], cnt);
 }
 
+// Whether (key, index l) is among the k smallest eligible (key, index) pairs
+// of the block, keys < 2^nbits: a bitwise binary search for the k-th smallest
+// key with block-wide counts, then ties at that key taken in index order.
+// Every thread of the block must call it (it synchronises).
+__device__ __forceinline__ bool block_take_k(uint64_t key, bool elig, int k, int nbits, int l,
+                                             uint32_t* s_cnt) {
+  if (k <= 0) return false;
+  uint64_t prefix = 0;
+  for (int bit = nbits - 1; bit >= 0; --bit) {
+    const uint64_t probe = prefix | ((1ull << bit) - 1ull);
+    if (__syncthreads_count(elig && key <= probe) < k) prefix |= 1ull << bit;
+  }
+  const int lt = __syncthreads_count(elig && key < prefix);
+  const bool tie = elig && key == prefix;
+  const unsigned b = __ballot_sync(0xffffffffu, tie);
+  const int lane = l & 31, warp = l >> 5;
+  if (lane == 0) s_cnt[warp] = __popc(b);
+  __syncthreads();
+  int before = __popc(b & ((1u << lane) - 1u));
+  for (int q = 0; q < warp; ++q) before += s_cnt[q];
+  __syncthreads();
+  return elig && (key < prefix || (tie && before < k - lt));
+}
+
 // Pixel sampling inside one chosen tile: one block of 256 threads (one per
-// local pixel).
+// local pixel); each phase is one exact block-wide k-selection.
 __global__ void __launch_bounds__(256) k_sample_pixels(const uint16_t* __restrict__ err,
                                                        const uint16_t* __restrict__ age, SelGeom g, int n_pix,
                                                        int hard_pm, int stable_pm, HashKeys hk,
@@ -174,14 +180,12 @@ __global__ void __launch_bounds__(256) k_sample_pixels(const uint16_t* __restric
                                                        const int32_t* __restrict__ n_active,
                                                        const int32_t* __restrict__ pix_off,
                                                        uint8_t* __restrict__ pix_idx) {
-  __shared__ uint64_t s_w[256], s_L[256], s_u[256];
-  __shared__ uint32_t s_age[256];
-  __shared__ uint8_t s_ok[256];
-  __shared__ uint32_t s_warp[8];
+  __shared__ uint32_t s_cnt[8];
   const int j = blockIdx.x;
   if (j >= *n_active) return;
   const int t = active_tiles[j];
   const int l = threadIdx.x;
+  const int lane = l & 31;
   const int x = (t % g.tx) * TGS_TILE + (l & 15), y = (t / g.tx) * TGS_TILE + (l >> 4);
   const bool valid = x < g.W && y < g.H;
   const int nv = tile_valid(g, t);
@@ -192,60 +196,28 @@ __global__ void __launch_bounds__(256) k_sample_pixels(const uint16_t* __restric
   if (n >= nv) {
     taken = valid;  // every valid pixel
   } else {
-    uint64_t wv = 0, Lv = 0, uv = 0;
+    uint64_t kh_key = 0, ku_key = 0;
     uint32_t av = 0;
     if (valid) {
       const size_t k = (size_t)y * g.W + x;
-      wv = err_weight(err[k]);
       av = age[k];
-      Lv = neglog2_q32(hash_item(hk.prefix(STREAM_PIX_HARD), (uint32_t)t, (uint32_t)l));
-      uv = hash_item(hk.prefix(STREAM_PIX_UNIF), (uint32_t)t, (uint32_t)l);
+      kh_key = hard_key(err_weight(err[k]),
+                        neglog2_q32(hash_item(hk.prefix(STREAM_PIX_HARD), (uint32_t)t, (uint32_t)l)));
+      ku_key = hash_item(hk.prefix(STREAM_PIX_UNIF), (uint32_t)t, (uint32_t)l) >> 32;
     }
-    s_w[l] = wv; s_L[l] = Lv; s_u[l] = uv; s_age[l] = av; s_ok[l] = valid;
-    __syncthreads();
-    // phase 0: hard draw
-    bool th = false;
-    if (valid && kh > 0) {
-      int c = 0;
-      for (int q = 0; q < 256 && c < kh; ++q) c += s_ok[q] && hard_before(s_w[q], s_L[q], q, wv, Lv, l);
-      th = c < kh;
-    }
-    __syncthreads();
-    s_ok[l] = valid && !th;
-    __syncthreads();
-    // phase 1: oldest among the rest
-    bool ts = false;
-    if (valid && !th && ks > 0) {
-      int c = 0;
-      for (int q = 0; q < 256 && c < ks; ++q) {
-        const uint32_t aq = s_age[q];
-        c += s_ok[q] && (aq > av || (aq == av && q < l));
-      }
-      ts = c < ks;
-    }
-    __syncthreads();
-    s_ok[l] = valid && !th && !ts;
-    __syncthreads();
-    // phase 2: uniform among the rest
-    bool tu = false;
-    const int ku = n - kh - ks;
-    if (valid && !th && !ts && ku > 0) {
-      int c = 0;
-      for (int q = 0; q < 256 && c < ku; ++q) {
-        const uint64_t uq = s_u[q];
-        c += s_ok[q] && (uq < uv || (uq == uv && q < l));
-      }
-      tu = c < ku;
-    }
+    // phase 0: error-proportional draw; 1: oldest of the rest; 2: uniform of the rest
+    const bool th = block_take_k(kh_key, valid, kh, 63, l, s_cnt);
+    const bool ts = block_take_k(0xFFFFull - av, valid && !th, ks, 16, l, s_cnt);
+    const bool tu = block_take_k(ku_key, valid && !th && !ts, n - kh - ks, 32, l, s_cnt);
     taken = th || ts || tu;
   }
   // ascending compaction of the taken local indices
   const unsigned b = __ballot_sync(0xffffffffu, taken);
-  if ((l & 31) == 0) s_warp[l >> 5] = __popc(b);
+  if (lane == 0) s_cnt[l >> 5] = __popc(b);
   __syncthreads();
   int off = 0;
-  for (int k = 0; k < (l >> 5); ++k) off += s_warp[k];
-  off += __popc(b & ((1u << (l & 31)) - 1u));
+  for (int k = 0; k < (l >> 5); ++k) off += s_cnt[k];
+  off += __popc(b & ((1u << lane) - 1u));
   if (taken) pix_idx[pix_off[j] + off] = (uint8_t)l;
 }
 

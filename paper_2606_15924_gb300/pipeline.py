@@ -87,6 +87,7 @@ class Trainer:
         if train:
             self.grad2d = torch.zeros(N, 12, device=dev)
             self.touched = torch.zeros(N, dtype=u8, device=dev)
+            self.ws_hybrid = torch.empty(B.hybrid_step_workspace_size(N), dtype=u8, device=dev)
         # device-side counters (graph replays read them)
         self.it_dev = torch.zeros(1, dtype=i64, device=dev)
         self.step_dev = torch.ones(1, dtype=i32, device=dev)
@@ -158,7 +159,7 @@ class Trainer:
     def update(self):
         """Hybrid LM / Adam update (Alg. 1 steps 9, 10)."""
         B.hybrid_step(self.params, self.grads, self.m, self.v, self.n, self.touched, None, 0, 1, self.opt,
-                      step_dev=self.step_dev)
+                      workspace=self.ws_hybrid, step_dev=self.step_dev)
 
     def step(self):
         """One full iteration; advances the device counters."""
