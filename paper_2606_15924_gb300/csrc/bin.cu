@@ -1,52 +1,52 @@
-// Tile binning: the per-tile Gaussian lists ordered by depth (Sec. 3.1),
-// built as a device LSD radix sort of (tile | depth) keys.  The low (depth)
-// digits are sorted once per visible Gaussian before the splats are
-// duplicated per tile; duplication keeps that order, so the remaining
-// (tile) digits finish the same stable sort on the much longer pair list.
-#include "radix.cuh"
+// Tile binning: the per-tile Gaussian lists ordered by depth (Sec. 3.1, the
+// depth-ordered sets K(p)) as a sort of (tile | depth | id) keys, done as a
+// counting sort on the tile digit followed by a per-tile sort of
+// (depth | id) in shared memory:
+//   1. blocks of Gaussians count their pairs per active tile in shared memory
+//      (a tile x block table of counts),
+//   2. one scan of that table in tile-major order gives every (tile, block)
+//      its output offset, hence each tile's range,
+//   3. each block scatters (depth bits << 32 | id) into its offsets with
+//      shared-memory cursors (no contended global atomics),
+//   4. one block per tile sorts its range with an ascending-only bitonic
+//      network (virtual +inf padding, so any length works), in shared memory
+//      up to kSortSmem keys and in global memory beyond.
+// Positive float depths order like their bit patterns, so the result is the
+// order (tile, depth, Gaussian id).
 #include "scan.cuh"
 
 namespace tgs {
 
+constexpr int kSortThreads = 256;
+constexpr int kSortSmem = 4096;  // keys sorted in shared memory (32 KB)
+
+constexpr int kHistBlocks = 304;          // 2 per SM: blocks of the count/scatter passes
+constexpr int kHistMaxRanks = 49152;      // shared-memory table limit (192 KB)
+
+static int hist_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(kHistBlocks, (n + 255) / 256)); }
+
 struct BinWs {
-  int32_t* counts;     // [N] active tiles covered per Gaussian
-  int32_t* vis_pos;    // [N] compacted position of visible Gaussians
-  uint32_t* dk[2];     // [N] depth keys
-  uint32_t* dv[2];     // [N] Gaussian ids
-  int64_t* offs;       // [N] emission offsets in depth order
-  int64_t* n_vis;      // [1]
-  int32_t* n_vis32;    // [1]
-  int32_t* n_sort;     // [1] min(n_isect, capacity)
-  int32_t* inv_rank;   // [n_active_max] tile id of each rank
-  uint32_t* tk[2];     // [C] tile-rank keys
-  uint32_t* tv[2];     // [C] Gaussian ids
-  int64_t* scan_sums;  // [scan blocks of N]
-  uint32_t* hist;      // radix histograms
-  uint32_t* bin_total; // [256]
+  int32_t* tile_cnt;   // [R] pairs per rank (global-atomic path)
+  int32_t* tile_fill;  // [R] scatter cursors (global-atomic path)
+  int64_t* tile_start; // [R] (global-atomic path)
+  int64_t* table;      // [R * G] counts, then offsets (shared-memory path)
+  uint64_t* keys;      // [C] (depth bits << 32 | id), grouped by tile
+  int32_t* inv_rank;   // [R] tile id of each rank
+  int64_t* scan_sums;
 };
 
-static BinWs carve_bin(void* base, int64_t n, int64_t cap, int32_t n_active_max, size_t* total) {
+static BinWs carve_bin(void* base, int64_t n, int64_t cap, int32_t n_ranks, size_t* total) {
   Carver c(base);
   BinWs w;
-  size_t nn = (size_t)std::max<int64_t>(n, 1), cc = (size_t)std::max<int64_t>(cap, 1);
-  w.counts = c.take<int32_t>(nn);
-  w.vis_pos = c.take<int32_t>(nn);
-  w.dk[0] = c.take<uint32_t>(nn);
-  w.dk[1] = c.take<uint32_t>(nn);
-  w.dv[0] = c.take<uint32_t>(nn);
-  w.dv[1] = c.take<uint32_t>(nn);
-  w.offs = c.take<int64_t>(nn);
-  w.n_vis = c.take<int64_t>(1);
-  w.n_vis32 = c.take<int32_t>(1);
-  w.n_sort = c.take<int32_t>(1);
-  w.inv_rank = c.take<int32_t>((size_t)std::max(n_active_max, 1));
-  w.tk[0] = c.take<uint32_t>(cc);
-  w.tk[1] = c.take<uint32_t>(cc);
-  w.tv[0] = c.take<uint32_t>(cc);
-  w.tv[1] = c.take<uint32_t>(cc);
-  w.scan_sums = c.take<int64_t>((size_t)std::max(1, scan_blocks(n)));
-  w.hist = c.take<uint32_t>(std::max(radix_hist_elems(n), radix_hist_elems(cap)));
-  w.bin_total = c.take<uint32_t>(RS_BINS);
+  const size_t R = (size_t)std::max(n_ranks, 1), C = (size_t)std::max<int64_t>(cap, 1);
+  const size_t RG = R * (size_t)hist_blocks(n);
+  w.tile_cnt = c.take<int32_t>(R);
+  w.tile_fill = c.take<int32_t>(R);
+  w.tile_start = c.take<int64_t>(R);
+  w.table = c.take<int64_t>(RG);
+  w.keys = c.take<uint64_t>(C);
+  w.inv_rank = c.take<int32_t>(R);
+  w.scan_sums = c.take<int64_t>((size_t)std::max(1, scan_blocks((int64_t)std::max(RG, R))));
   *total = c.size();
   return w;
 }
@@ -56,29 +56,220 @@ struct BinGeom {
   int n_ranks;  // ranks >= n_ranks count as inactive
 };
 
-__device__ __forceinline__ bool rank_active(int r, const BinGeom& g) { return r >= 0 && r < g.n_ranks; }
+__device__ __forceinline__ int rank_of(const int32_t* __restrict__ tile_rank, int t, const BinGeom& g) {
+  const int r = tile_rank ? __ldg(tile_rank + t) : t;
+  return (r >= 0 && r < g.n_ranks) ? r : -1;
+}
 
-// Number of active tiles in the rectangle of each Gaussian.
+// 1. pairs per active tile
 __global__ void __launch_bounds__(256) k_count_tiles(const float2* __restrict__ xy, const int32_t* __restrict__ radius,
                                                      int64_t n, BinGeom geo, const int32_t* __restrict__ tile_rank,
-                                                     int32_t* __restrict__ counts) {
+                                                     int32_t* __restrict__ tile_cnt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int r = radius[i];
-  int c = 0;
-  if (r > 0) {
-    const float2 p = xy[i];
-    int x0, x1, y0, y1;
-    tile_span(p.x, r, geo.tx, x0, x1);
-    tile_span(p.y, r, geo.ty, y0, y1);
-    if (!tile_rank) {
-      c = (x1 - x0) * (y1 - y0);
-    } else {
+  if (r <= 0) return;
+  const float2 p = xy[i];
+  int x0, x1, y0, y1;
+  tile_span(p.x, r, geo.tx, x0, x1);
+  tile_span(p.y, r, geo.ty, y0, y1);
+  for (int ty = y0; ty < y1; ++ty)
+    for (int tx = x0; tx < x1; ++tx) {
+      const int k = rank_of(tile_rank, ty * geo.tx + tx, geo);
+      if (k >= 0) atomicAdd(tile_cnt + k, 1);
+    }
+}
+
+// 3. scatter (depth | id) keys into the tile ranges (unordered inside a tile)
+__global__ void __launch_bounds__(256) k_scatter_keys(const float2* __restrict__ xy, const int32_t* __restrict__ radius,
+                                                      const float* __restrict__ depth, int64_t n, BinGeom geo,
+                                                      const int32_t* __restrict__ tile_rank,
+                                                      const int64_t* __restrict__ tile_start,
+                                                      int32_t* __restrict__ tile_fill, uint64_t* __restrict__ keys,
+                                                      int64_t cap) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int r = radius[i];
+  if (r <= 0) return;
+  const float2 p = xy[i];
+  const uint64_t key = ((uint64_t)__float_as_uint(depth[i]) << 32) | (uint64_t)(uint32_t)i;
+  int x0, x1, y0, y1;
+  tile_span(p.x, r, geo.tx, x0, x1);
+  tile_span(p.y, r, geo.ty, y0, y1);
+  for (int ty = y0; ty < y1; ++ty)
+    for (int tx = x0; tx < x1; ++tx) {
+      const int k = rank_of(tile_rank, ty * geo.tx + tx, geo);
+      if (k < 0) continue;
+      const int64_t pos = tile_start[k] + atomicAdd(tile_fill + k, 1);
+      if (pos < cap) keys[pos] = key;
+    }
+}
+
+// Calls f(gaussian id, rank) for every (Gaussian, active tile) pair of the
+// block's Gaussians [i0, i1).  Rectangles of up to kSmallRect tiles are walked
+// by their own lane; larger ones by the whole warp (each lane a stripe of the
+// rectangle), so a few huge splats do not serialise one thread.
+constexpr int kSmallRect = 32;
+
+template <typename F>
+__device__ __forceinline__ void for_each_pair(const float2* __restrict__ xy, const int32_t* __restrict__ radius,
+                                              int64_t i0, int64_t i1, const BinGeom& geo,
+                                              const int32_t* __restrict__ tile_rank, F f) {
+  const int lane = threadIdx.x & 31;
+  const int64_t wave = blockDim.x;
+  for (int64_t base = i0 + (threadIdx.x & ~31); base < i1; base += wave) {
+    const int64_t i = base + lane;
+    int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
+    if (i < i1) {
+      const int r = radius[i];
+      if (r > 0) {
+        const float2 p = xy[i];
+        tile_span(p.x, r, geo.tx, x0, x1);
+        tile_span(p.y, r, geo.ty, y0, y1);
+      }
+    }
+    const int area = (x1 - x0) * (y1 - y0);
+    if (area <= kSmallRect) {
       for (int ty = y0; ty < y1; ++ty)
-        for (int tx = x0; tx < x1; ++tx) c += rank_active(__ldg(tile_rank + ty * geo.tx + tx), geo);
+        for (int tx = x0; tx < x1; ++tx) {
+          const int k = rank_of(tile_rank, ty * geo.tx + tx, geo);
+          if (k >= 0) f(i, k);
+        }
+    }
+    unsigned big = __ballot_sync(0xffffffffu, area > kSmallRect);
+    while (big) {
+      const int src = __ffs(big) - 1;
+      big &= big - 1;
+      const int64_t gi = base + src;
+      const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
+      const int by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
+      const int w = bx1 - bx0, a = w * (by1 - by0);
+      for (int q = lane; q < a; q += 32) {
+        const int ty = by0 + q / w, tx = bx0 + q % w;
+        const int k = rank_of(tile_rank, ty * geo.tx + tx, geo);
+        if (k >= 0) f(gi, k);
+      }
     }
   }
-  counts[i] = c;
+}
+
+// 1'. shared-memory path: block b counts the pairs of Gaussians
+// [b * chunk, (b + 1) * chunk) per rank; table[r * G + b] = count.
+__global__ void __launch_bounds__(256) k_hist_count(const float2* __restrict__ xy, const int32_t* __restrict__ radius,
+                                                    int64_t n, int64_t chunk, BinGeom geo,
+                                                    const int32_t* __restrict__ tile_rank,
+                                                    int64_t* __restrict__ table) {
+  extern __shared__ uint32_t sh[];
+  const int R = geo.n_ranks, G = gridDim.x, b = blockIdx.x;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) sh[r] = 0;
+  __syncthreads();
+  const int64_t i0 = (int64_t)b * chunk, i1 = min(n, i0 + chunk);
+  for_each_pair(xy, radius, i0, i1, geo, tile_rank, [&](int64_t, int k) { atomicAdd(sh + k, 1u); });
+  __syncthreads();
+  for (int r = threadIdx.x; r < R; r += blockDim.x) table[(size_t)r * G + b] = sh[r];
+}
+
+// 3'. shared-memory path: scatter with shared cursors that start at the
+// block's offsets table[r * G + b] (clamped to the capacity; positions at or
+// past the capacity are dropped).
+__global__ void __launch_bounds__(256) k_hist_scatter(const float2* __restrict__ xy, const int32_t* __restrict__ radius,
+                                                      const float* __restrict__ depth, int64_t n, int64_t chunk,
+                                                      BinGeom geo, const int32_t* __restrict__ tile_rank,
+                                                      const int64_t* __restrict__ table, uint64_t* __restrict__ keys,
+                                                      int64_t cap) {
+  extern __shared__ uint32_t sh[];
+  const int R = geo.n_ranks, G = gridDim.x, b = blockIdx.x;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) sh[r] = (uint32_t)min(table[(size_t)r * G + b], cap);
+  __syncthreads();
+  const int64_t i0 = (int64_t)b * chunk, i1 = min(n, i0 + chunk);
+  for_each_pair(xy, radius, i0, i1, geo, tile_rank, [&](int64_t i, int k) {
+    const uint32_t pos = atomicAdd(sh + k, 1u);
+    if ((int64_t)pos < cap) keys[pos] = ((uint64_t)__float_as_uint(depth[i]) << 32) | (uint64_t)(uint32_t)i;
+  });
+}
+
+// Ascending-only bitonic network over n keys padded (virtually) with +inf to
+// a power of two: every compare-exchange puts the smaller key at the lower
+// index, so padding never moves.  K is shared or global memory.
+__device__ __forceinline__ void cmp_swap(uint64_t* K, int i, int j, int n) {
+  if (j < n) {
+    const uint64_t a = K[i], b = K[j];
+    if (b < a) {
+      K[i] = b;
+      K[j] = a;
+    }
+  }
+}
+
+__device__ void bitonic_sort(uint64_t* K, int n) {
+  int lg2 = 0;
+  while ((1 << lg2) < n) ++lg2;
+  const int n2 = 1 << lg2;
+  for (int lk = 1; lk <= lg2; ++lk) {
+    const int k = 1 << lk, lh = lk - 1, half = k >> 1;
+    for (int t = threadIdx.x; t < n2 / 2; t += blockDim.x) {
+      const int blk = t >> lh, off = t & (half - 1);
+      cmp_swap(K, blk * k + off, blk * k + k - 1 - off, n);
+    }
+    __syncthreads();
+    for (int ld = lk - 2; ld >= 0; --ld) {
+      const int d = 1 << ld;
+      for (int t = threadIdx.x; t < n2 / 2; t += blockDim.x) {
+        const int i = ((t >> ld) << (ld + 1)) + (t & (d - 1));
+        cmp_swap(K, i, i + d, n);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// 4. one block per active rank: sort its keys, write ids (and full keys)
+// Range of rank r: from the offset table (stride G, shared-memory path) or
+// from per-tile starts and counts (global-atomic path).
+struct RangeSrc {
+  const int64_t* table;
+  int G, R;
+  const int64_t* total;
+  const int64_t* start;
+  const int32_t* cnt;
+  __device__ __forceinline__ void get(int r, int64_t& s0, int64_t& e0) const {
+    if (table) {
+      s0 = table[(size_t)r * G];
+      e0 = r + 1 < R ? table[(size_t)(r + 1) * G] : *total;
+    } else {
+      s0 = start[r];
+      e0 = s0 + cnt[r];
+    }
+  }
+};
+
+__global__ void __launch_bounds__(kSortThreads) k_tile_sort(uint64_t* __restrict__ keys, RangeSrc src,
+                                                            const int32_t* __restrict__ inv_rank, int64_t cap,
+                                                            int32_t* __restrict__ vals, uint64_t* __restrict__ full_keys,
+                                                            int2* __restrict__ ranges) {
+  __shared__ uint64_t sk[kSortSmem];
+  const int r = blockIdx.x;
+  int64_t s0, e0;
+  src.get(r, s0, e0);
+  const int64_t s = min(s0, cap), e = min(e0, cap);  // pairs past the capacity are dropped
+  if (threadIdx.x == 0) ranges[r] = make_int2((int)s, (int)e);
+  const int n = (int)(e - s);
+  if (n <= 0) return;
+  uint64_t* K;
+  if (n <= kSortSmem) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sk[i] = keys[s + i];
+    __syncthreads();
+    K = sk;
+  } else {
+    K = keys + s;  // long list: the same network in global memory
+  }
+  bitonic_sort(K, n);
+  const uint64_t tile_hi = full_keys ? ((uint64_t)(uint32_t)inv_rank[r] << 32) : 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint64_t k = K[i];
+    vals[s + i] = (int32_t)(uint32_t)k;
+    if (full_keys) full_keys[s + i] = tile_hi | (k >> 32);
+  }
 }
 
 __global__ void k_inv_rank(const int32_t* __restrict__ tile_rank, int T, int32_t* __restrict__ inv, int n_max) {
@@ -86,60 +277,6 @@ __global__ void k_inv_rank(const int32_t* __restrict__ tile_rank, int T, int32_t
   if (t >= T) return;
   const int r = tile_rank ? tile_rank[t] : t;
   if (r >= 0 && r < n_max) inv[r] = t;
-}
-
-// Emit (tile rank, Gaussian) pairs for each visible Gaussian in depth order.
-__global__ void __launch_bounds__(256) k_emit(const uint32_t* __restrict__ dv, const int64_t* __restrict__ offs,
-                                              const int32_t* __restrict__ n_vis, const float2* __restrict__ xy,
-                                              const int32_t* __restrict__ radius, BinGeom geo,
-                                              const int32_t* __restrict__ tile_rank, int64_t cap,
-                                              uint32_t* __restrict__ tk, uint32_t* __restrict__ tv, int64_t n_max) {
-  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= min((int64_t)*n_vis, n_max)) return;
-  const uint32_t id = dv[j];
-  int64_t o = offs[j];
-  if (o >= cap) return;
-  const float2 p = xy[id];
-  const int r = radius[id];
-  int x0, x1, y0, y1;
-  tile_span(p.x, r, geo.tx, x0, x1);
-  tile_span(p.y, r, geo.ty, y0, y1);
-  for (int ty = y0; ty < y1; ++ty)
-    for (int tx = x0; tx < x1; ++tx) {
-      const int t = ty * geo.tx + tx;
-      const int rank = tile_rank ? __ldg(tile_rank + t) : t;
-      if (!rank_active(rank, geo)) continue;
-      if (o >= cap) return;
-      tk[o] = (uint32_t)rank;
-      tv[o] = id;
-      ++o;
-    }
-}
-
-__global__ void __launch_bounds__(256) k_ranges(const uint32_t* __restrict__ tk, const int32_t* __restrict__ n_sort,
-                                                int64_t n_max, int2* __restrict__ ranges) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t n = min((int64_t)*n_sort, n_max);
-  if (i >= n) return;
-  const uint32_t k = tk[i];
-  if (i == 0 || tk[i - 1] != k) ranges[k].x = (int)i;
-  if (i == n - 1 || tk[i + 1] != k) ranges[k].y = (int)(i + 1);
-}
-
-__global__ void __launch_bounds__(256) k_full_keys(const uint32_t* __restrict__ tk, const int32_t* __restrict__ vals,
-                                                   const int32_t* __restrict__ n_sort, int64_t n_max,
-                                                   const int32_t* __restrict__ inv_rank,
-                                                   const float* __restrict__ depth, uint64_t* __restrict__ keys) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= min((int64_t)*n_sort, n_max)) return;
-  const uint32_t t = (uint32_t)inv_rank[tk[i]];
-  keys[i] = ((uint64_t)t << 32) | (uint64_t)__float_as_uint(depth[vals[i]]);
-}
-
-__global__ void k_finish_counts(const int64_t* n_vis, int32_t* n_vis32, const int64_t* n_isect, int64_t cap,
-                                int32_t* n_sort) {
-  if (n_vis32) *n_vis32 = (int32_t)*n_vis;
-  if (n_sort) *n_sort = (int32_t)min(*n_isect, cap);
 }
 
 }  // namespace tgs
@@ -163,66 +300,67 @@ extern "C" tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const 
   if (!tile_rank && n_active_max < T) return TGS_ERR_INVALID_ARG;
   if (n > 0 && (!proj->xy || !proj->radius || !proj->depth || !aligned8(proj->xy))) return TGS_ERR_INVALID_ARG;
   if (capacity > 0 && !vals) return TGS_ERR_INVALID_ARG;
+  if (!aligned8(tile_ranges) || (keys && !aligned8(keys))) return TGS_ERR_INVALID_ARG;
   size_t need = tgs_bin_tiles_workspace_size(n, capacity, n_active_max);
   if (!workspace || workspace_bytes < need) return TGS_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   size_t tot;
   BinWs w = carve_bin(workspace, n, capacity, n_active_max, &tot);
   BinGeom geo{tiles_x(cam->width), tiles_y(cam->height), n_active_max};
-  if (n_active_max > 0) cudaMemsetAsync(tile_ranges, 0, sizeof(int2) * (size_t)n_active_max, s);
+  const int R = n_active_max;
+  if (R > 0) cudaMemsetAsync(tile_ranges, 0, sizeof(int2) * (size_t)R, s);
   cudaMemsetAsync(n_isect, 0, sizeof(int64_t), s);
-  cudaMemsetAsync(w.n_sort, 0, sizeof(int32_t), s);
-  if (n == 0) return check_launch();
+  if (n == 0 || R == 0) return check_launch();
   const float2* xy = reinterpret_cast<const float2*>(proj->xy);
-  const int gb = (int)((n + 255) / 256);
-  // 1. active tiles covered per Gaussian
-  k_count_tiles<<<gb, 256, 0, s>>>(xy, proj->radius, n, geo, tile_rank, w.counts);
-  // 2. compact the visible Gaussians with their depth keys
-  {
-    const int32_t* counts = w.counts;
-    const float* depth = proj->depth;
-    uint32_t* dk = w.dk[0];
-    uint32_t* dv = w.dv[0];
-    auto load = [=] __device__(int64_t i) -> int64_t { return counts[i] > 0 ? 1 : 0; };
-    auto store = [=] __device__(int64_t i, int64_t pre, int64_t v) {
-      if (v) {
-        dk[pre] = __float_as_uint(depth[i]);
-        dv[pre] = (uint32_t)i;
+  RangeSrc src{};
+  const bool shared_path = R <= kHistMaxRanks;
+  const int G = hist_blocks(n);
+  const int64_t chunk = (n + G - 1) / G;
+  const size_t smem = sizeof(int32_t) * (size_t)R;
+  if (shared_path) {
+    if (smem > 48 * 1024) {  // opt in to more than 48 KB of dynamic shared memory (per device)
+      static bool attr_set[64] = {};
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (dev < 0 || dev >= 64) return TGS_ERR_DEVICE;
+      if (!attr_set[dev]) {
+        cudaFuncSetAttribute(k_hist_count, cudaFuncAttributeMaxDynamicSharedMemorySize, kHistMaxRanks * 4);
+        cudaFuncSetAttribute(k_hist_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, kHistMaxRanks * 4);
+        attr_set[dev] = true;
       }
-    };
-    exclusive_scan<int64_t>(load, store, nullptr, n, w.scan_sums, w.n_vis, s);
+    }
+    k_hist_count<<<G, 256, smem, s>>>(xy, proj->radius, n, chunk, geo, tile_rank, w.table);
+    int64_t* tab = w.table;
+    auto load = [=] __device__(int64_t i) -> int64_t { return tab[i]; };
+    auto store = [=] __device__(int64_t i, int64_t pre, int64_t) { tab[i] = pre; };
+    exclusive_scan<int64_t>(load, store, nullptr, (int64_t)R * G, w.scan_sums, n_isect, s);
+    src.table = w.table;
+    src.G = G;
+    src.R = R;
+    src.total = n_isect;
+  } else {
+    const int gb = (int)((n + 255) / 256);
+    cudaMemsetAsync(w.tile_cnt, 0, sizeof(int32_t) * (size_t)R, s);
+    cudaMemsetAsync(w.tile_fill, 0, sizeof(int32_t) * (size_t)R, s);
+    k_count_tiles<<<gb, 256, 0, s>>>(xy, proj->radius, n, geo, tile_rank, w.tile_cnt);
+    const int32_t* cnt = w.tile_cnt;
+    int64_t* start = w.tile_start;
+    auto load = [=] __device__(int64_t r) -> int64_t { return cnt[r]; };
+    auto store = [=] __device__(int64_t r, int64_t pre, int64_t) { start[r] = pre; };
+    exclusive_scan<int64_t>(load, store, nullptr, R, w.scan_sums, n_isect, s);
+    src.start = w.tile_start;
+    src.cnt = w.tile_cnt;
   }
-  k_finish_counts<<<1, 1, 0, s>>>(w.n_vis, w.n_vis32, w.n_vis, 0, nullptr);
-  // 3. stable sort of the visible Gaussians by depth (positive floats order as uint32)
-  RadixScratch rsc{w.hist, w.bin_total};
-  int cur = radix_sort_pairs(w.dk[0], w.dv[0], w.dk[1], w.dv[1], w.n_vis32, (int32_t)n, 0, 32, rsc, nullptr, s);
-  const uint32_t* dv_sorted = w.dv[cur];
-  // 4. emission offsets in depth order; n_isect = total
-  {
-    const int32_t* counts = w.counts;
-    int64_t* offs = w.offs;
-    auto load = [=] __device__(int64_t j) -> int64_t { return counts[dv_sorted[j]]; };
-    auto store = [=] __device__(int64_t j, int64_t pre, int64_t) { offs[j] = pre; };
-    exclusive_scan<int64_t>(load, store, w.n_vis, n, w.scan_sums, n_isect, s);
-  }
-  k_finish_counts<<<1, 1, 0, s>>>(w.n_vis, nullptr, n_isect, capacity, w.n_sort);
   if (capacity == 0) return check_launch();
-  // 5. duplicate per active tile
-  k_emit<<<gb, 256, 0, s>>>(dv_sorted, w.offs, w.n_vis32, xy, proj->radius, geo, tile_rank, capacity, w.tk[0],
-                            w.tv[0], n);
-  // 6. stable sort by tile rank (the high digits of the (tile | depth) key)
-  int bits = 0;
-  while ((1ll << bits) < (int64_t)std::max(n_active_max, 1)) ++bits;
-  bits = std::max(8, (bits + 7) / 8 * 8);
-  int tcur = radix_sort_pairs(w.tk[0], w.tv[0], w.tk[1], w.tv[1], w.n_sort, (int32_t)capacity, 0, bits, rsc,
-                              reinterpret_cast<uint32_t*>(vals), s);
-  const uint32_t* tk_sorted = w.tk[tcur];
-  // 7. per-rank ranges, optional full keys
-  const int cb = (int)((capacity + 255) / 256);
-  k_ranges<<<cb, 256, 0, s>>>(tk_sorted, w.n_sort, capacity, reinterpret_cast<int2*>(tile_ranges));
-  if (keys) {
-    k_inv_rank<<<(T + 255) / 256, 256, 0, s>>>(tile_rank, T, w.inv_rank, std::max(n_active_max, 1));
-    k_full_keys<<<cb, 256, 0, s>>>(tk_sorted, vals, w.n_sort, capacity, w.inv_rank, proj->depth, keys);
+  if (shared_path) {
+    k_hist_scatter<<<G, 256, smem, s>>>(xy, proj->radius, proj->depth, n, chunk, geo, tile_rank, w.table, w.keys,
+                                        capacity);
+  } else {
+    k_scatter_keys<<<(int)((n + 255) / 256), 256, 0, s>>>(xy, proj->radius, proj->depth, n, geo, tile_rank,
+                                                          w.tile_start, w.tile_fill, w.keys, capacity);
   }
+  if (keys) k_inv_rank<<<(T + 255) / 256, 256, 0, s>>>(tile_rank, T, w.inv_rank, R);
+  k_tile_sort<<<R, kSortThreads, 0, s>>>(w.keys, src, w.inv_rank, capacity, vals, keys,
+                                         reinterpret_cast<int2*>(tile_ranges));
   return check_launch();
 }

@@ -156,10 +156,14 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[9], int l
   return c;
 }
 
+// Per-splat adjoints of a batch are summed over the block in shared memory
+// (acc, 9 floats per batch slot) and flushed once per block and splat with
+// vector atomics, instead of once per warp and splat.
 __global__ void k_render_bwd(RasterArgs a, const float* __restrict__ T_final, const int32_t* __restrict__ n_last,
                              const float* __restrict__ dL_drgb, float* __restrict__ grad2d) {
   extern __shared__ Splat sm[];
   __shared__ int s_max_last;
+  float* acc = reinterpret_cast<float*>(sm + blockDim.x);
   const int j = blockIdx.x;
   if (j >= *a.n_active) return;
   const int t = a.active_tiles ? a.active_tiles[j] : j;
@@ -187,6 +191,9 @@ __global__ void k_render_bwd(RasterArgs a, const float* __restrict__ T_final, co
   float S0 = a.bg[0], S1 = a.bg[1], S2 = a.bg[2];
   const int B = blockDim.x;
   const int lane = threadIdx.x & 31;
+  int warp_last = last;  // the warp skips splats none of its pixels blended
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) warp_last = max(warp_last, __shfl_xor_sync(0xffffffffu, warp_last, o));
   Splat nxt;
   if (end - B + (int)threadIdx.x >= range.x && (int)threadIdx.x < B && end > range.x) {
     const int k = end - B + threadIdx.x;
@@ -200,13 +207,16 @@ __global__ void k_render_bwd(RasterArgs a, const float* __restrict__ T_final, co
     {
       const int k = top - B + (int)threadIdx.x;
       if (k >= range.x) sm[threadIdx.x - (B - cnt)] = nxt;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) acc[9 * threadIdx.x + c] = 0.f;
     }
     __syncthreads();
     {
       const int k = top - 2 * B + (int)threadIdx.x;
       if (k >= range.x) load_splat(a, k, nxt);
     }
-    for (int q = cnt - 1; q >= 0; --q) {
+    const int qmax = min(cnt - 1, range.x + warp_last - 1 - lo);
+    for (int q = qmax; q >= 0; --q) {
       const Splat sp = sm[q];
       const int pos = lo + q - range.x;  // position in the tile list
       float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -239,9 +249,19 @@ __global__ void k_render_bwd(RasterArgs a, const float* __restrict__ T_final, co
       if (__any_sync(0xffffffffu, hit)) {
         const float r8 = warp_reduce_scatter8(v, lane);
         const float r9 = warp_sum(v[8]);
-        float* gp = grad2d + 12 * (size_t)__float_as_int(sp.rgb.w);
-        if ((lane & 3) == 0) atomicAdd(gp + ((lane >> 2) & 7), r8);
-        else if (lane == 1) atomicAdd(gp + 8, r9);
+        if ((lane & 3) == 0) atomicAdd(acc + 9 * q + ((lane >> 2) & 7), r8);
+        else if (lane == 1) atomicAdd(acc + 9 * q + 8, r9);
+      }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < cnt) {
+      const float* r = acc + 9 * threadIdx.x;
+      if (r[0] != 0.f || r[1] != 0.f || r[2] != 0.f || r[3] != 0.f || r[4] != 0.f || r[5] != 0.f ||
+          r[6] != 0.f || r[7] != 0.f || r[8] != 0.f) {
+        float* gp = grad2d + 12 * (size_t)__float_as_int(sm[threadIdx.x].rgb.w);
+        red_add_v4(gp, r[0], r[1], r[2], r[3]);
+        red_add_v4(gp + 4, r[4], r[5], r[6], r[7]);
+        atomicAdd(gp + 8, r[8]);
       }
     }
   }
@@ -313,7 +333,8 @@ extern "C" tgs_status tgs_backward_sampled(const tgs_gaussians* g, const tgs_cam
   cudaMemsetAsync(grad2d, 0, sizeof(float) * 12 * (size_t)g->n, s);
   if (n_active_max > 0) {
     const int B = block_for(n_pix_max);
-    k_render_bwd<<<n_active_max, B, B * sizeof(Splat), s>>>(a, T_final, n_last, dL_drgb, grad2d);
+    k_render_bwd<<<n_active_max, B, B * (sizeof(Splat) + 9 * sizeof(float)), s>>>(a, T_final, n_last, dL_drgb,
+                                                                                 grad2d);
   }
   launch_project_bwd(*g, *cam, proj->radius, grad2d, *grads, touched, write_untouched, s);
   return check_launch();
