@@ -319,6 +319,47 @@ tgs_status tgs_hybrid_step(const tgs_param_ptrs* params, const tgs_param_ptrs* g
                            int32_t k_rows, int32_t step, const int32_t* step_dev, const tgs_opt* opt,
                            void* workspace, size_t workspace_bytes, tgs_stream stream);
 
+/*
+ * Tile-error predictor (not in the paper): a 3-layer MLP 16 -> 128 -> 128 ->
+ * 1 with ReLU that predicts log(1 + mean tile error) from per-tile features,
+ * standing in for a dense refresh of stale error maps.  Weights are bfloat16
+ * (bit patterns, row-major out x in: w1 [128,16], w2 [128,128], w3 [128]),
+ * biases fp32; products accumulate in fp32.  Bias and weight updates run on
+ * an fp32 master copy: a packed vector of tgs_mlp_param_count() floats laid
+ * out as W1 | b1 | W2 | b2 | W3 | b3.
+ */
+typedef struct {
+  const uint16_t* w1;
+  const float* b1;
+  const uint16_t* w2;
+  const float* b2;
+  const uint16_t* w3;
+  const float* b3;
+} tgs_mlp;
+
+int32_t tgs_mlp_param_count(void);
+
+/* y [R] = MLP(x [R,16] fp32, zero-padded features; rounded to bf16).  When
+ * given, h1 and h2 [R,128] receive the bf16 hidden activations (post-ReLU)
+ * for the backward. */
+tgs_status tgs_mlp_forward(const tgs_mlp* w, int64_t rows, const float* x, float* y, uint16_t* h1, uint16_t* h2,
+                           tgs_stream stream);
+
+/* Gradient of L = (1/R) sum (y - t)^2 / 2 into grads (packed layout, fp32,
+ * overwritten) and *loss (device double), from the forward's x, h1, h2, y.
+ * Hidden adjoints are rounded to bf16 before they meet a bf16 operand. */
+size_t tgs_mlp_backward_workspace_size(int64_t rows);
+tgs_status tgs_mlp_backward(const tgs_mlp* w, int64_t rows, const float* x, const uint16_t* h1,
+                            const uint16_t* h2, const float* y, const float* target, float* grads, double* loss,
+                            void* workspace, size_t workspace_bytes, tgs_stream stream);
+
+/* Adam step on the fp32 master vector (params, m, v: tgs_mlp_param_count()
+ * floats) with bias correction at `step` (>= 1); writes the bf16 copies of
+ * W1, W2, W3. */
+tgs_status tgs_mlp_adam(float* params, const float* grads, float* m, float* v, int32_t step, float lr,
+                        float beta1, float beta2, float eps, uint16_t* w1, uint16_t* w2, uint16_t* w3,
+                        tgs_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

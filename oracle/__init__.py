@@ -97,6 +97,12 @@ def _declare(L):
     L.orc_cholesky_solve.restype = _i32
     L.orc_hybrid_step.argtypes = [_i64, _p, _p, _p, _p, _p, _p, _i32, _i32, _i32, _p]
     L.orc_hybrid_step.restype = _i32
+    L.orc_round_bf16.argtypes = [_d]
+    L.orc_round_bf16.restype = _d
+    L.orc_mlp_forward.argtypes = [_i64, _p, _p, _p, _p, _p, _p, _p, _i32, _p, _p, _p]
+    L.orc_mlp_forward.restype = _i32
+    L.orc_mlp_backward.argtypes = [_i64, _p, _p, _p, _p, _p, _p, _p, _p, _i32, _p, _p, _p, _p, _p, _p, _p]
+    L.orc_mlp_backward.restype = _i32
 
 
 def _c(a, dtype):
@@ -340,3 +346,41 @@ def hybrid_step(params, grads, m, v, touched, step, mode, cfg, rows=None):
     lib().orc_hybrid_step(p.shape[0], _ptr(p), _ptr(g), _ptr(mm), _ptr(vv), _ptr(t), _ptr(r), k, int(step),
                           int(mode), _ptr(c))
     return p, mm, vv
+
+
+# ----------------------------------------------------------------------------
+# tile-error predictor (MLP 16 -> 128 -> 128 -> 1)
+# ----------------------------------------------------------------------------
+
+def round_bf16(x: float) -> float:
+    return float(lib().orc_round_bf16(float(x)))
+
+
+def _mlp_w(w):
+    return [_c(w[k], np.float64) for k in ("W1", "b1", "W2", "b2", "W3", "b3")]
+
+
+def mlp_forward(x, w, bf16=True):
+    """y [R], h1 [R,128], h2 [R,128] for features x [R,16]."""
+    x = _c(x, np.float64).reshape(-1, 16)
+    R = x.shape[0]
+    W1, b1, W2, b2, W3, b3 = _mlp_w(w)
+    y, h1, h2 = np.zeros(R), np.zeros((R, 128)), np.zeros((R, 128))
+    lib().orc_mlp_forward(R, _ptr(x), _ptr(W1), _ptr(b1), _ptr(W2), _ptr(b2), _ptr(W3), _ptr(b3), int(bf16),
+                          _ptr(y), _ptr(h1), _ptr(h2))
+    return y, h1, h2
+
+
+def mlp_backward(x, t, w, bf16=True):
+    """loss and gradient dict (W1, b1, W2, b2, W3, b3) of mean (y - t)^2 / 2."""
+    x = _c(x, np.float64).reshape(-1, 16)
+    t = _c(t, np.float64)
+    R = x.shape[0]
+    W1, b1, W2, b2, W3, b3 = _mlp_w(w)
+    g = dict(W1=np.zeros((128, 16)), b1=np.zeros(128), W2=np.zeros((128, 128)), b2=np.zeros(128),
+             W3=np.zeros(128), b3=np.zeros(1))
+    loss = np.zeros(1)
+    lib().orc_mlp_backward(R, _ptr(x), _ptr(t), _ptr(W1), _ptr(b1), _ptr(W2), _ptr(b2), _ptr(W3), _ptr(b3),
+                           int(bf16), _ptr(loss), _ptr(g["W1"]), _ptr(g["b1"]), _ptr(g["W2"]), _ptr(g["b2"]),
+                           _ptr(g["W3"]), _ptr(g["b3"]))
+    return float(loss[0]), g

@@ -1163,3 +1163,116 @@ int orc_hybrid_step(int64_t n, double* params, const double* grads, double* m, d
   }
   return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* tile-error predictor: 3-layer MLP 16 -> 128 -> 128 -> 1, ReLU            */
+/* (not in the paper; a learned stand-in for refreshing stale error maps)   */
+/* ------------------------------------------------------------------------ */
+
+/* IEEE binary32 -> bfloat16 with round to nearest even, returned as a
+ * double (bfloat16 is the upper half of a binary32). */
+double orc_round_bf16(double x) {
+  float f = (float)x;
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return (double)f;  /* inf / nan */
+  uint32_t lsb = (u >> 16) & 1u;
+  u += 0x7fffu + lsb;
+  u &= 0xffff0000u;
+  memcpy(&f, &u, 4);
+  return (double)f;
+}
+
+#define MLP_IN 16
+#define MLP_H 128
+
+/*
+ * Forward of rows x [R,16] (features, zero padded).  Weights W1 [128,16],
+ * W2 [128,128], W3 [128] (out x in, row-major) and biases b1, b2, b3 [1].
+ * bf16 = 1 rounds the input, the weights and the hidden activations to
+ * bfloat16 where the kernels do (products summed exactly in double here,
+ * in fp32 there); bf16 = 0 is the plain double-precision network.
+ * Outputs y [R]; h1, h2 [R,128] post-ReLU activations (nullable).
+ */
+int orc_mlp_forward(int64_t R, const double* x, const double* W1, const double* b1, const double* W2,
+                    const double* b2, const double* W3, const double* b3, int bf16, double* y, double* h1o,
+                    double* h2o) {
+#pragma omp parallel for schedule(static) if (R > 64)
+  for (int64_t r = 0; r < R; ++r) {
+    double xin[MLP_IN], h1[MLP_H], h2[MLP_H];
+    for (int k = 0; k < MLP_IN; ++k) xin[k] = bf16 ? orc_round_bf16(x[r * MLP_IN + k]) : x[r * MLP_IN + k];
+    for (int j = 0; j < MLP_H; ++j) {
+      double s = b1[j];
+      for (int k = 0; k < MLP_IN; ++k) s += (bf16 ? orc_round_bf16(W1[j * MLP_IN + k]) : W1[j * MLP_IN + k]) * xin[k];
+      s = s > 0.0 ? s : 0.0;
+      h1[j] = bf16 ? orc_round_bf16(s) : s;
+    }
+    for (int j = 0; j < MLP_H; ++j) {
+      double s = b2[j];
+      for (int k = 0; k < MLP_H; ++k) s += (bf16 ? orc_round_bf16(W2[j * MLP_H + k]) : W2[j * MLP_H + k]) * h1[k];
+      s = s > 0.0 ? s : 0.0;
+      h2[j] = bf16 ? orc_round_bf16(s) : s;
+    }
+    double s = b3[0];
+    for (int k = 0; k < MLP_H; ++k) s += (bf16 ? orc_round_bf16(W3[k]) : W3[k]) * h2[k];
+    y[r] = s;
+    if (h1o) for (int j = 0; j < MLP_H; ++j) h1o[r * MLP_H + j] = h1[j];
+    if (h2o) for (int j = 0; j < MLP_H; ++j) h2o[r * MLP_H + j] = h2[j];
+  }
+  return 0;
+}
+
+/*
+ * Loss L = (1/R) sum_r (y_r - t_r)^2 / 2 and its gradient with respect to
+ * every weight and bias, by the chain rule through the forward above.
+ * With bf16 = 1 the backward rounds the hidden adjoints to bfloat16 before
+ * they meet a bfloat16 operand, as the kernels do.  Gradients are written
+ * (not accumulated) into dW1 [128,16], db1, dW2 [128,128], db2, dW3 [128], db3.
+ */
+int orc_mlp_backward(int64_t R, const double* x, const double* t, const double* W1, const double* b1,
+                     const double* W2, const double* b2, const double* W3, const double* b3, int bf16,
+                     double* loss, double* dW1, double* db1, double* dW2, double* db2, double* dW3, double* db3) {
+  memset(dW1, 0, sizeof(double) * MLP_H * MLP_IN);
+  memset(db1, 0, sizeof(double) * MLP_H);
+  memset(dW2, 0, sizeof(double) * MLP_H * MLP_H);
+  memset(db2, 0, sizeof(double) * MLP_H);
+  memset(dW3, 0, sizeof(double) * MLP_H);
+  db3[0] = 0.0;
+  double L = 0.0;
+  double* h1 = (double*)malloc(sizeof(double) * MLP_H);
+  double* h2 = (double*)malloc(sizeof(double) * MLP_H);
+  for (int64_t r = 0; r < R; ++r) {
+    double xin[MLP_IN], y;
+    for (int k = 0; k < MLP_IN; ++k) xin[k] = bf16 ? orc_round_bf16(x[r * MLP_IN + k]) : x[r * MLP_IN + k];
+    orc_mlp_forward(1, x + r * MLP_IN, W1, b1, W2, b2, W3, b3, bf16, &y, h1, h2);
+    double e = y - t[r];
+    L += 0.5 * e * e / (double)R;
+    double dy = e / (double)R;
+    db3[0] += dy;
+    double dh2[MLP_H], dh1[MLP_H];
+    for (int k = 0; k < MLP_H; ++k) {
+      dW3[k] += dy * h2[k];
+      double w3 = bf16 ? orc_round_bf16(W3[k]) : W3[k];
+      double d = h2[k] > 0.0 ? dy * w3 : 0.0;   /* ReLU gate */
+      dh2[k] = bf16 ? orc_round_bf16(d) : d;
+    }
+    for (int j = 0; j < MLP_H; ++j) {
+      db2[j] += dh2[j];
+      for (int k = 0; k < MLP_H; ++k) dW2[j * MLP_H + k] += dh2[j] * h1[k];
+    }
+    for (int k = 0; k < MLP_H; ++k) {
+      double s = 0.0;
+      for (int j = 0; j < MLP_H; ++j) s += dh2[j] * (bf16 ? orc_round_bf16(W2[j * MLP_H + k]) : W2[j * MLP_H + k]);
+      double d = h1[k] > 0.0 ? s : 0.0;
+      dh1[k] = bf16 ? orc_round_bf16(d) : d;
+    }
+    for (int j = 0; j < MLP_H; ++j) {
+      db1[j] += dh1[j];
+      for (int k = 0; k < MLP_IN; ++k) dW1[j * MLP_IN + k] += dh1[j] * xin[k];
+    }
+  }
+  free(h1);
+  free(h2);
+  *loss = L;
+  return 0;
+}

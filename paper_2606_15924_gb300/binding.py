@@ -66,6 +66,11 @@ class LossParams(C.Structure):
     _fields_ = [("eps_charbonnier", C.c_float), ("eps_ncc", C.c_float), ("beta", C.c_float)]
 
 
+class Mlp(C.Structure):
+    _fields_ = [("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p), ("w3", C.c_void_p),
+                ("b3", C.c_void_p)]
+
+
 class Opt(C.Structure):
     _fields_ = [("lr", C.c_float * 6), ("beta1", C.c_float), ("beta2", C.c_float), ("eps_adam", C.c_float),
                 ("eps_lm", C.c_float), ("mode", C.c_int32)]
@@ -115,11 +120,23 @@ _lib.tgs_hybrid_step_workspace_size.argtypes = [_i64]
 _lib.tgs_hybrid_step.argtypes = [_P(ParamPtrs), _P(ParamPtrs), _P(ParamPtrs), _P(ParamPtrs), _i64, _p, _p, _i32,
                                  _i32, _p, _P(Opt), _p, _sz, _p]
 
+_lib.tgs_mlp_param_count.restype = _i32
+_lib.tgs_mlp_forward.restype = _i32
+_lib.tgs_mlp_forward.argtypes = [_P(Mlp), _i64, _p, _p, _p, _p, _p]
+_lib.tgs_mlp_backward_workspace_size.restype = _sz
+_lib.tgs_mlp_backward_workspace_size.argtypes = [_i64]
+_lib.tgs_mlp_backward.restype = _i32
+_lib.tgs_mlp_backward.argtypes = [_P(Mlp), _i64, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]
+_lib.tgs_mlp_adam.restype = _i32
+_lib.tgs_mlp_adam.argtypes = [_p, _p, _p, _p, _i32, C.c_float, C.c_float, C.c_float, C.c_float, _p, _p, _p, _p]
+
 EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_device_check", "tgs_graph_count_kernels",
             "tgs_select_tiles_workspace_size", "tgs_select_tiles", "tgs_select_tiles_noalloc",
             "tgs_project_gaussians",
             "tgs_bin_tiles_workspace_size", "tgs_bin_tiles", "tgs_render_sampled", "tgs_loss_sparse_ncc",
-            "tgs_backward_sampled", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step"]
+            "tgs_backward_sampled", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step",
+            "tgs_mlp_param_count", "tgs_mlp_forward", "tgs_mlp_backward_workspace_size", "tgs_mlp_backward",
+            "tgs_mlp_adam"]
 
 
 def _check(fn, status):
@@ -281,3 +298,41 @@ def hybrid_step(params: dict, grads: dict, m: dict, v: dict, n, touched, view_ro
     _check("tgs_hybrid_step", _lib.tgs_hybrid_step(
         C.byref(P), C.byref(G), C.byref(M), C.byref(V), int(n), _ptr(touched), _ptr(view_rows), int(k_rows),
         int(step), _ptr(step_dev), C.byref(o), _ptr(workspace), workspace.numel(), _stream(stream)))
+
+
+# ----------------------------------------------------------------------------
+# tile-error predictor
+# ----------------------------------------------------------------------------
+
+def mlp_param_count() -> int:
+    return int(_lib.tgs_mlp_param_count())
+
+
+def mlp_struct(net: dict) -> Mlp:
+    """net: w1, w2, w3 (int16 tensors holding bf16 bits), b1, b2, b3 (float32)."""
+    return Mlp(_ptr(net["w1"]), _ptr(net["b1"]), _ptr(net["w2"]), _ptr(net["b2"]), _ptr(net["w3"]), _ptr(net["b3"]))
+
+
+def mlp_forward(net: dict, x, y, h1=None, h2=None, stream=None):
+    m = mlp_struct(net)
+    _check("tgs_mlp_forward", _lib.tgs_mlp_forward(C.byref(m), int(x.shape[0]), _ptr(x), _ptr(y), _ptr(h1), _ptr(h2),
+                                                   _stream(stream)))
+
+
+def mlp_backward_workspace_size(rows: int) -> int:
+    return int(_lib.tgs_mlp_backward_workspace_size(int(rows)))
+
+
+def mlp_backward(net: dict, x, h1, h2, y, target, grads, loss, workspace=None, stream=None):
+    m = mlp_struct(net)
+    if workspace is None:
+        workspace = torch.empty(mlp_backward_workspace_size(x.shape[0]), dtype=torch.uint8, device=x.device)
+    _check("tgs_mlp_backward", _lib.tgs_mlp_backward(C.byref(m), int(x.shape[0]), _ptr(x), _ptr(h1), _ptr(h2),
+                                                     _ptr(y), _ptr(target), _ptr(grads), _ptr(loss), _ptr(workspace),
+                                                     workspace.numel(), _stream(stream)))
+
+
+def mlp_adam(params, grads, m, v, step, lr, beta1, beta2, eps, net: dict, stream=None):
+    _check("tgs_mlp_adam", _lib.tgs_mlp_adam(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(step), float(lr),
+                                             float(beta1), float(beta2), float(eps), _ptr(net["w1"]),
+                                             _ptr(net["w2"]), _ptr(net["w3"]), _stream(stream)))

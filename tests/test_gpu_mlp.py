@@ -1,0 +1,90 @@
+"""GPU parity of the tile-error MLP kernels (bf16 tensor-core layers, fp32
+accumulation) against the oracle's bf16-mode network, and an Adam training
+run on a seeded regression task."""
+import numpy as np
+import pytest
+import torch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2606_15924_gb300 import binding as B
+    from paper_2606_15924_gb300.predictor import TileErrorMLP
+    B.device_check()
+    return B, TileErrorMLP
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def _features(R, seed):
+    rng = np.random.default_rng(seed)
+    x = np.zeros((R, 16), np.float32)
+    x[:, :5] = rng.normal(size=(R, 5)).astype(np.float32)
+    return x
+
+
+@pytest.mark.parametrize("R", [1, 15, 16, 1000, 4097])
+def test_forward_parity(P, orc, R):
+    B, TileErrorMLP = P
+    mlp = TileErrorMLP(seed=R)
+    x = _features(R, R)
+    xd = torch.from_numpy(x).cuda()
+    y = torch.empty(R, device="cuda")
+    h1 = torch.empty(R, 128, dtype=torch.int16, device="cuda")
+    h2 = torch.empty(R, 128, dtype=torch.int16, device="cuda")
+    B.mlp_forward(mlp.net(), xd, y, h1, h2)
+    yw, h1w, h2w = orc.mlp_forward(x, mlp.weights_fp(), bf16=True)
+    got = y.cpu().numpy()
+    assert rel_l2(got, yw) <= 1e-3
+    assert np.abs(got - yw).max() <= 1e-2 * max(1.0, np.abs(yw).max())
+    for hg, hw in ((h1, h1w), (h2, h2w)):
+        hv = hg.view(torch.bfloat16).float().cpu().numpy().astype(np.float64)
+        # fp32 vs fp64 accumulation may move a value across a bf16 rounding
+        # boundary: then the two differ by one bf16 ulp
+        diff = hv != hw
+        assert diff.mean() < 2e-3
+        ulp = np.abs(hw[diff]) * 2.0 ** -7 + 1e-30
+        assert np.all(np.abs(hv[diff] - hw[diff]) <= 1.01 * ulp)
+
+
+@pytest.mark.parametrize("R", [33, 2048, 5000])
+def test_backward_parity(P, orc, R):
+    B, TileErrorMLP = P
+    mlp = TileErrorMLP(seed=7)
+    x = _features(R, 11)
+    t = np.random.default_rng(12).normal(size=R).astype(np.float32)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    y = torch.empty(R, device="cuda")
+    h1 = torch.empty(R, 128, dtype=torch.int16, device="cuda")
+    h2 = torch.empty(R, 128, dtype=torch.int16, device="cuda")
+    B.mlp_forward(mlp.net(), xd, y, h1, h2)
+    B.mlp_backward(mlp.net(), xd, h1, h2, y, td, mlp.grads, mlp.loss)
+    loss, gw = orc.mlp_backward(x, t, mlp.weights_fp(), bf16=True)
+    assert float(mlp.loss.item()) == pytest.approx(loss, rel=1e-3)
+    g = mlp.grads.double().cpu().numpy()
+    sl = mlp._slices()
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        assert rel_l2(g[sl[name]], gw[name].reshape(-1)) <= 1e-3, (name, rel_l2(g[sl[name]], gw[name].reshape(-1)))
+
+
+def test_adam_step_and_training(P):
+    B, TileErrorMLP = P
+    mlp = TileErrorMLP(seed=3, lr=2e-3)
+    p0 = mlp.params.clone()
+    R = 4096
+    x = torch.from_numpy(_features(R, 5)).cuda()
+    # a smooth seeded target of the five features
+    t = torch.tanh(x[:, 0]) + 0.5 * x[:, 1] * x[:, 2] - 0.3 * x[:, 3] ** 2 + 0.1 * x[:, 4]
+    l0 = float(mlp.train_step(x, t).item())
+    # first Adam step from zero moments moves every parameter with a non-zero gradient by ~lr
+    d = (mlp.params - p0).abs()
+    nz = mlp.grads.abs() > 1e-5
+    assert torch.allclose(d[nz], torch.full_like(d[nz], 2e-3), rtol=1e-3)
+    for _ in range(600):
+        l = mlp.train_step(x, t)
+    l1 = float(l.item())
+    assert l1 < 0.1 * l0, (l0, l1)
