@@ -104,8 +104,11 @@ typedef struct {
 
 /* Loss constants (App. A): Charbonnier epsilon, NCC epsilon, EMA ratio beta
  * (Table 6: 0.4). */
+/* Loss constants (Sec. 3.7, App. A).  view_weight scales this view's loss and
+ * dL_drgb: 1 for one view, 1/K for the mean over K views of one step (the
+ * expectation over views in Eq. 8). */
 typedef struct {
-  float eps_charbonnier, eps_ncc, beta;
+  float eps_charbonnier, eps_ncc, beta, view_weight;
 } tgs_loss_params;
 
 /* Hybrid solver (Sec. 3.9, App. A).  lr: means, log_scales, quats, opacity,
@@ -296,6 +299,62 @@ tgs_status tgs_backward_sampled(const tgs_gaussians* g, const tgs_camera* cam, c
                                 const int32_t* n_last, const float* dL_drgb, float* grad2d,
                                 const tgs_param_ptrs* grads, uint8_t* touched, int32_t write_untouched,
                                 tgs_stream stream);
+
+/*
+ * project_backward - the projection adjoint alone (the second half of
+ * backward_sampled, Alg. 1 step 8): grad2d [N,12] of one view -> parameter
+ * gradients.  accumulate = 0 overwrites grads and touched as backward_sampled
+ * does.  accumulate = 1 sums views of one step: touched (required) must be
+ * zeroed before the first view; a Gaussian this view touches gets its
+ * gradient written when touched[i] is still 0 and added otherwise, and
+ * touched[i] becomes 1 (untouched gradients are left alone: the update reads
+ * only touched Gaussians).  view_row (nullable, 8-byte aligned) receives this
+ * view's own [N,14] gradient row in the hybrid_step layout (means, log-scales,
+ * quaternion, DC r g b, opacity logit; zeros where untouched), i.e. one
+ * K-slice of its view_rows.
+ */
+tgs_status tgs_project_backward(const tgs_gaussians* g, const tgs_camera* cam, const tgs_projected* proj,
+                                const float* grad2d, const tgs_param_ptrs* grads, uint8_t* touched,
+                                int32_t write_untouched, int32_t accumulate, float* view_row, tgs_stream stream);
+
+/*
+ * Several views in one launch (not in the paper: a batching of
+ * render_sampled / the compositing adjoint over the views of one iteration,
+ * Alg. 1 steps 5 and 8).  Persistent thread blocks (grid_ctas of them) take
+ * (view, active tile) items from an atomic counter (counter: one device
+ * int32, reset by the call) until none are left; each item is rendered
+ * exactly as render_sampled / backward_sampled render it.  Up to 16 views.
+ * Per view: the fields of render_sampled; the backward also reads dL_drgb
+ * and writes grad2d [n_gaussians, 12] (zeroed by the call).
+ */
+typedef struct {
+  tgs_projected proj;
+  const int32_t* tile_ranges;
+  const int32_t* vals;
+  const int32_t* active_tiles;
+  const int32_t* n_active;
+  int32_t n_active_max;
+  const int32_t* pix_off;
+  const uint8_t* pix_idx;
+  int32_t n_pix_max;
+  tgs_camera cam;
+  float bg[3];
+  float* rgb;
+  float* T_final;
+  int32_t* n_last;
+  const float* dL_drgb;
+  float* grad2d;
+  int64_t n_gaussians;
+} tgs_view_batch;
+
+/* Thread blocks of the batched kernels that fit on the current device at
+ * once (SMs x resident blocks per SM) for n_pix_max pixels per tile: the
+ * largest useful grid_ctas. */
+tgs_status tgs_render_batched_resident(int32_t n_pix_max, int32_t backward, int32_t* ctas);
+tgs_status tgs_render_sampled_batched(const tgs_view_batch* views, int32_t n_views, int32_t grid_ctas,
+                                      int32_t* counter, tgs_stream stream);
+tgs_status tgs_render_backward_batched(const tgs_view_batch* views, int32_t n_views, int32_t grid_ctas,
+                                       int32_t* counter, tgs_stream stream);
 
 /*
  * hybrid_step - moment-damped LM / Adam update (Sec. 3.9, Eq. 11; App. A;

@@ -1,0 +1,238 @@
+"""Several views per training iteration, rasterised in one persistent launch.
+
+At iteration t the method trains on a set of K views (Alg. 1 steps 2-10; the
+loss of Eq. 8 is an expectation over them).  ``MultiViewTrainer`` keeps one
+``Trainer`` per view for the per-view state (error and age maps, sampled
+tiles and pixels, projection, tile lists) and shares the Gaussians, their
+gradients and the optimiser moments.  One step:
+
+  per view: select_tiles -> project_gaussians -> bin_tiles
+  all views: render_sampled_batched (one persistent launch, (view, tile) queue)
+  per view: loss_sparse_ncc (view_weight 1/K)
+  all views: render_backward_batched (one persistent launch)
+  per view: project_backward (accumulating into the shared gradients, and
+            writing the view's Jacobian row for the Cholesky mode)
+  once:     hybrid_step
+
+Everything is sized at construction and the iteration counters live on the
+device, so the step is captured once in a CUDA graph.  ``autotune_grid``
+picks the persistent grid sizes by timing graph replays.
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import torch
+
+from . import binding as B
+from .config import Config
+from .pipeline import Trainer, zeros_like_params
+
+
+class MultiViewTrainer:
+    def __init__(self, params: dict, cams: list, targets: list, tile_fractions: list,
+                 pixel_rate: float = 1.0 / 3.0, cfg: Config | None = None, seed: int = 0, bg=(0.0, 0.0, 0.0),
+                 sh_degree: int = 3, view_ids: list | None = None, grid: tuple | None = None,
+                 view_rows: bool | None = None):
+        if not (1 <= len(cams) <= 16) or len(cams) != len(targets) or len(cams) != len(tile_fractions):
+            raise ValueError("1 to 16 views, one target and one tile fraction each")
+        self.cfg = cfg or Config()
+        self.params = params
+        self.n = int(params["means"].shape[0])
+        self.K = len(cams)
+        self.sh_degree, self.bg = sh_degree, tuple(bg)
+        dev = params["means"].device
+        ids = view_ids if view_ids is not None else list(range(self.K))
+        self.views = [Trainer(params, cams[k], targets[k], tile_fraction=tile_fractions[k], pixel_rate=pixel_rate,
+                              cfg=self.cfg, seed=seed, bg=bg, sh_degree=sh_degree, view=ids[k], train=False)
+                      for k in range(self.K)]
+        # one device iteration counter for all views (the hash of each view's
+        # draw also takes its view id)
+        self.it_dev = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.step_dev = torch.ones(1, dtype=torch.int32, device=dev)
+        w = 1.0 / self.K
+        for v in self.views:
+            v.it_dev = self.it_dev
+            v.loss_params = (v.loss_params[0], v.loss_params[1], v.loss_params[2], w)
+            v.grad2d = torch.zeros(self.n, 12, device=dev)
+        self.grads = zeros_like_params(params)
+        self.m = zeros_like_params(params)
+        self.v = zeros_like_params(params)
+        self.touched = torch.zeros(self.n, dtype=torch.uint8, device=dev)
+        self.ws_hybrid = torch.empty(B.hybrid_step_workspace_size(self.n), dtype=torch.uint8, device=dev)
+        o = self.cfg.opt
+        self.opt = dict(lr=[o.lr_means, o.lr_scales, o.lr_quats, o.lr_opacity, o.lr_sh_dc, o.lr_sh_rest],
+                        beta1=o.beta1, beta2=o.beta2, eps_adam=o.eps_adam, eps_lm=o.eps_lm, mode=o.mode)
+        # per-view Jacobian rows feed only the full-matrix LM mode
+        self.use_rows = (self.opt["mode"] == 2) if view_rows is None else bool(view_rows)
+        self.rows = torch.zeros(self.K, self.n, 14, device=dev) if self.use_rows else None
+        self.counters = torch.zeros(2, dtype=torch.int32, device=dev)
+        self.n_pix_max = max(v.n_pix for v in self.views)
+        res_f = B.render_batched_resident(self.n_pix_max, False)
+        res_b = B.render_batched_resident(self.n_pix_max, True)
+        self.resident = (res_f, res_b)
+        self.grid = tuple(grid) if grid is not None else (res_f, res_b)
+        self._build_batches()
+        self.graph = None
+
+    def _build_batches(self):
+        fwd, bwd = [], []
+        for v in self.views:
+            d = dict(proj=v.proj, tile_ranges=v.ranges, vals=v.vals, active_tiles=v.active_tiles,
+                     n_active=v.n_active, n_active_max=v.n_select, pix_off=v.pix_off, pix_idx=v.pix_idx,
+                     n_pix_max=v.n_pix, cam=v.ccam, bg=v.bg, rgb=v.rgb, T_final=v.T_final, n_last=v.n_last)
+            fwd.append(dict(d))
+            d.update(dL_drgb=v.dL, grad2d=v.grad2d)
+            bwd.append(d)
+        # ctypes arrays hold raw pointers: rebuilt whenever a buffer is reallocated
+        self.fwd_batch = B.view_batch(fwd)
+        self.bwd_batch = B.view_batch(bwd)
+
+    # ------------------------------------------------------------------ step
+    def forward(self):
+        for v in self.views:
+            v._select()
+            B.project_gaussians(self.params, v.ccam, v.tile_rank, v.proj, self.sh_degree)
+            B.bin_tiles(v.proj, self.n, v.ccam, v.tile_rank, v.n_select, v.ws_bin, v.capacity, v.vals, None,
+                        v.ranges, v.n_isect)
+        B.render_sampled_batched(self.fwd_batch, self.grid[0], self.counters[0:1])
+
+    def loss_and_maps(self):
+        for v in self.views:
+            v.loss_and_maps()
+
+    def backward(self):
+        B.render_backward_batched(self.bwd_batch, self.grid[1], self.counters[1:2])
+        self.touched.zero_()
+        for k, v in enumerate(self.views):
+            B.project_backward(self.params, v.ccam, v.proj, v.grad2d, self.grads, self.touched,
+                               write_untouched=False, accumulate=True,
+                               view_row=self.rows[k] if self.use_rows else None, sh_degree=self.sh_degree)
+
+    def update(self):
+        B.hybrid_step(self.params, self.grads, self.m, self.v, self.n, self.touched, self.rows,
+                      self.K if self.use_rows else 0, 1, self.opt, workspace=self.ws_hybrid, step_dev=self.step_dev)
+
+    def step(self):
+        self.forward()
+        self.loss_and_maps()
+        self.backward()
+        self.update()
+        self.it_dev.add_(1)
+        self.step_dev.add_(1)
+
+    def loss(self) -> float:
+        """Mean loss over the views of the last step (reads the device)."""
+        return float(sum(v.loss.item() for v in self.views))
+
+    def overflowed(self) -> bool:
+        return any(v.overflowed() for v in self.views)
+
+    def n_sampled(self) -> int:
+        """Sampled pixels of the last step over all views (reads the device)."""
+        return int(sum(int(v.pix_off[int(v.n_active.item())].item()) for v in self.views))
+
+    # ------------------------------------------------------------------ graph
+    def capture(self):
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            self.step()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        self.graph = torch.cuda.CUDAGraph(keep_graph=True)
+        with torch.cuda.graph(self.graph):
+            self.step()
+        self.kernels_per_step = B.graph_count_kernels(self.graph)
+        self.graph.instantiate()
+        torch.cuda.synchronize()
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
+
+    def capture_render(self):
+        """Graphs of the two persistent launches alone (for timing and tuning)."""
+        torch.cuda.synchronize()
+        self.g_fwd = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.g_fwd):
+            B.render_sampled_batched(self.fwd_batch, self.grid[0], self.counters[0:1])
+        self.g_bwd = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.g_bwd):
+            B.render_backward_batched(self.bwd_batch, self.grid[1], self.counters[1:2])
+        torch.cuda.synchronize()
+
+
+# ---------------------------------------------------------------------- tuner
+def _time_graph(g, reps: int) -> float:
+    g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        g.replay()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def grid_candidates(resident: int, sms: int) -> list:
+    """Persistent grid sizes worth trying: whole waves of SMs up to the
+    resident limit, plus the limit itself."""
+    out = {resident}
+    k = 1
+    while k * sms < resident:
+        out.add(k * sms)
+        k *= 2
+    return sorted(x for x in out if x >= 1)
+
+
+def _cache_path() -> str:
+    root = os.environ.get("TURBOGS_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "turbogs"))
+    return os.path.join(root, "grid_tune.json")
+
+
+def autotune_grid(mv: MultiViewTrainer, reps: int = 10, use_cache: bool = True) -> dict:
+    """Pick (forward, backward) persistent grid sizes for this trainer's shape
+    by timing graph replays of the two launches on the current sampled sets.
+    The choice is cached per (device, views, image sizes, tile counts, pixels
+    per tile) in a JSON file; returns {"grid": (f, b), "times": {...}}."""
+    props = torch.cuda.get_device_properties(mv.params["means"].device)
+    key = "|".join([props.name, str(mv.K)] + [f"{v.W}x{v.H}:{v.n_select}:{v.n_pix}" for v in mv.views])
+    path = _cache_path()
+    cache = {}
+    if use_cache and os.path.exists(path):
+        try:
+            cache = json.load(open(path))
+        except (OSError, ValueError):
+            cache = {}
+    if use_cache and key in cache:
+        mv.grid = tuple(cache[key]["grid"])
+        return cache[key]
+    sms = props.multi_processor_count
+    times = {"fwd": {}, "bwd": {}}
+    best = list(mv.grid)
+    for which in (0, 1):
+        best_t = None
+        for g in grid_candidates(mv.resident[which], sms):
+            grid = list(mv.grid)
+            grid[which] = g
+            mv.grid = tuple(grid)
+            mv.capture_render()
+            t = _time_graph(mv.g_fwd if which == 0 else mv.g_bwd, reps)
+            times["fwd" if which == 0 else "bwd"][g] = t
+            if best_t is None or t < best_t:
+                best_t, best[which] = t, g
+        grid = list(mv.grid)
+        grid[which] = best[which]
+        mv.grid = tuple(grid)
+    result = {"grid": list(mv.grid), "times": times}
+    if use_cache:
+        cache[key] = result
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            json.dump(cache, open(path, "w"), indent=1)
+        except OSError:
+            pass
+    return result

@@ -63,12 +63,21 @@ class Sampling(C.Structure):
 
 
 class LossParams(C.Structure):
-    _fields_ = [("eps_charbonnier", C.c_float), ("eps_ncc", C.c_float), ("beta", C.c_float)]
+    _fields_ = [("eps_charbonnier", C.c_float), ("eps_ncc", C.c_float), ("beta", C.c_float),
+                ("view_weight", C.c_float)]
 
 
 class Mlp(C.Structure):
     _fields_ = [("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p), ("w3", C.c_void_p),
                 ("b3", C.c_void_p)]
+
+
+class ViewBatch(C.Structure):
+    _fields_ = [("proj", Projected), ("tile_ranges", C.c_void_p), ("vals", C.c_void_p),
+                ("active_tiles", C.c_void_p), ("n_active", C.c_void_p), ("n_active_max", C.c_int32),
+                ("pix_off", C.c_void_p), ("pix_idx", C.c_void_p), ("n_pix_max", C.c_int32), ("cam", Camera),
+                ("bg", C.c_float * 3), ("rgb", C.c_void_p), ("T_final", C.c_void_p), ("n_last", C.c_void_p),
+                ("dL_drgb", C.c_void_p), ("grad2d", C.c_void_p), ("n_gaussians", C.c_int64)]
 
 
 class Opt(C.Structure):
@@ -114,6 +123,15 @@ _lib.tgs_loss_sparse_ncc.argtypes = [_p, _p, _i32, _i32, _p, _p, _i32, _p, _p, _
 _lib.tgs_backward_sampled.restype = _i32
 _lib.tgs_backward_sampled.argtypes = [_P(Gaussians), _P(Camera), _P(Projected), _p, _p, _p, _p, _i32, _p, _p,
                                       _i32, _p, _p, _p, _p, _p, _P(ParamPtrs), _p, _i32, _p]
+_lib.tgs_project_backward.restype = _i32
+_lib.tgs_project_backward.argtypes = [_P(Gaussians), _P(Camera), _P(Projected), _p, _P(ParamPtrs), _p, _i32, _i32,
+                                      _p, _p]
+_lib.tgs_render_batched_resident.restype = _i32
+_lib.tgs_render_batched_resident.argtypes = [_i32, _i32, _P(_i32)]
+_lib.tgs_render_sampled_batched.restype = _i32
+_lib.tgs_render_sampled_batched.argtypes = [_P(ViewBatch), _i32, _i32, _p, _p]
+_lib.tgs_render_backward_batched.restype = _i32
+_lib.tgs_render_backward_batched.argtypes = [_P(ViewBatch), _i32, _i32, _p, _p]
 _lib.tgs_hybrid_step.restype = _i32
 _lib.tgs_hybrid_step_workspace_size.restype = _sz
 _lib.tgs_hybrid_step_workspace_size.argtypes = [_i64]
@@ -134,7 +152,8 @@ EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_devi
             "tgs_select_tiles_workspace_size", "tgs_select_tiles", "tgs_select_tiles_noalloc",
             "tgs_project_gaussians",
             "tgs_bin_tiles_workspace_size", "tgs_bin_tiles", "tgs_render_sampled", "tgs_loss_sparse_ncc",
-            "tgs_backward_sampled", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step",
+            "tgs_backward_sampled", "tgs_project_backward", "tgs_render_batched_resident", "tgs_render_sampled_batched",
+            "tgs_render_backward_batched", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step",
             "tgs_mlp_param_count", "tgs_mlp_forward", "tgs_mlp_backward_workspace_size", "tgs_mlp_backward",
             "tgs_mlp_adam"]
 
@@ -259,7 +278,10 @@ def render_sampled(proj: dict, tile_ranges, vals, active_tiles, n_active, n_acti
 
 def loss_sparse_ncc(rgb, target, width, height, active_tiles, n_active, n_active_max, pix_off, pix_idx, n_pix_max,
                     loss_params, err_map, age_map, dL_drgb, lambda_tile, err_pix, loss, stream=None):
-    lp = LossParams(*[float(v) for v in loss_params])
+    vals = [float(v) for v in loss_params]
+    if len(vals) == 3:
+        vals.append(1.0)  # one view
+    lp = LossParams(*vals)
     _check("tgs_loss_sparse_ncc", _lib.tgs_loss_sparse_ncc(
         _ptr(rgb), _ptr(target), int(width), int(height), _ptr(active_tiles), _ptr(n_active), int(n_active_max),
         _ptr(pix_off), _ptr(pix_idx), int(n_pix_max), C.byref(lp), _ptr(err_map), _ptr(age_map), _ptr(dL_drgb),
@@ -278,6 +300,56 @@ def backward_sampled(g: dict, cam, proj: dict, tile_ranges, vals, active_tiles, 
         C.byref(gs), C.byref(cc), C.byref(pr), _ptr(tile_ranges), _ptr(vals), _ptr(active_tiles), _ptr(n_active),
         int(n_active_max), _ptr(pix_off), _ptr(pix_idx), int(n_pix_max), bgv, _ptr(T_final), _ptr(n_last),
         _ptr(dL_drgb), _ptr(grad2d), C.byref(gp), _ptr(touched), 1 if write_untouched else 0, _stream(stream)))
+
+
+def project_backward(g: dict, cam, proj: dict, grad2d, grads: dict, touched, write_untouched=True,
+                     accumulate=False, view_row=None, sh_degree=3, stream=None):
+    gs = gaussians(g, sh_degree)
+    cc = cam if isinstance(cam, Camera) else camera(cam)
+    pr = projected(proj)
+    gp = param_ptrs(grads)
+    _check("tgs_project_backward", _lib.tgs_project_backward(
+        C.byref(gs), C.byref(cc), C.byref(pr), _ptr(grad2d), C.byref(gp), _ptr(touched),
+        1 if write_untouched else 0, 1 if accumulate else 0, _ptr(view_row), _stream(stream)))
+
+
+def view_batch(views: list) -> C.Array:
+    """views: dicts with the per-view fields of tgs_view_batch (proj, tile_ranges,
+    vals, active_tiles, n_active, n_active_max, pix_off, pix_idx, n_pix_max, cam,
+    bg, rgb, T_final, n_last and, for the backward, dL_drgb, grad2d)."""
+    arr = (ViewBatch * len(views))()
+    for k, w in enumerate(views):
+        b = arr[k]
+        b.proj = projected(w["proj"])
+        b.tile_ranges, b.vals = _ptr(w["tile_ranges"]), _ptr(w["vals"])
+        b.active_tiles, b.n_active = _ptr(w["active_tiles"]), _ptr(w["n_active"])
+        b.n_active_max = int(w["n_active_max"])
+        b.pix_off, b.pix_idx, b.n_pix_max = _ptr(w["pix_off"]), _ptr(w["pix_idx"]), int(w["n_pix_max"])
+        b.cam = w["cam"] if isinstance(w["cam"], Camera) else camera(w["cam"])
+        b.bg = (C.c_float * 3)(*[float(x) for x in w.get("bg", (0.0, 0.0, 0.0))])
+        b.rgb, b.T_final, b.n_last = _ptr(w["rgb"]), _ptr(w["T_final"]), _ptr(w["n_last"])
+        b.dL_drgb, b.grad2d = _ptr(w.get("dL_drgb")), _ptr(w.get("grad2d"))
+        b.n_gaussians = int(w["grad2d"].shape[0]) if w.get("grad2d") is not None else 0
+    return arr
+
+
+def render_batched_resident(n_pix_max: int, backward: bool) -> int:
+    out = _i32(0)
+    _check("tgs_render_batched_resident", _lib.tgs_render_batched_resident(int(n_pix_max), 1 if backward else 0,
+                                                                             C.byref(out)))
+    return int(out.value)
+
+
+def render_sampled_batched(views, grid_ctas, counter, stream=None):
+    arr = views if isinstance(views, C.Array) else view_batch(views)
+    _check("tgs_render_sampled_batched", _lib.tgs_render_sampled_batched(arr, len(arr), int(grid_ctas),
+                                                                           _ptr(counter), _stream(stream)))
+
+
+def render_backward_batched(views, grid_ctas, counter, stream=None):
+    arr = views if isinstance(views, C.Array) else view_batch(views)
+    _check("tgs_render_backward_batched", _lib.tgs_render_backward_batched(arr, len(arr), int(grid_ctas),
+                                                                             _ptr(counter), _stream(stream)))
 
 
 def hybrid_step_workspace_size(n: int) -> int:

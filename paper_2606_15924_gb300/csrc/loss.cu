@@ -34,7 +34,7 @@ struct LossArgs {
   const int32_t* n_active;
   const int32_t* pix_off;
   const uint8_t* pix_idx;
-  float eps_c2, eps_n, beta;
+  float eps_c2, eps_n, beta, weight;
   uint16_t* err_map;
   uint16_t* age_map;
   float* dL;
@@ -125,7 +125,7 @@ __global__ void k_loss(LossArgs a) {
     const float invP = 1.f / (float)P;
     const float cn = lam / (3.f * (float)A) * inv_n;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) a.dL[3 * (size_t)s + c] = d1[c] * invP - cn * dn[c];
+    for (int c = 0; c < 3; ++c) a.dL[3 * (size_t)s + c] = (d1[c] * invP - cn * dn[c]) * a.weight;
     a.err_pix[s] = e;
     if (a.err_map) {
       const float old = __half2float(__ushort_as_half(a.err_map[pix]));
@@ -137,7 +137,7 @@ __global__ void k_loss(LossArgs a) {
     a.lambda[j] = lam;
     const double tile_loss = (double)l1 / (double)P +
                              (double)lam * (1.0 - ((double)ncc[0] + (double)ncc[1] + (double)ncc[2]) / 3.0) / (double)A;
-    atomicAdd(a.loss, tile_loss);
+    atomicAdd(a.loss, tile_loss * (double)a.weight);
   }
 }
 
@@ -173,6 +173,7 @@ extern "C" tgs_status tgs_loss_sparse_ncc(const float* rgb, const float* target,
     return TGS_ERR_INVALID_ARG;
   if (age_map && !aligned16(age_map)) return TGS_ERR_INVALID_ARG;
   if (!(params->eps_charbonnier >= 0.f) || !(params->eps_ncc >= 0.f) || !(params->beta >= 0.f) ||
+      !(params->view_weight >= 0.f) ||
       !(params->beta <= 1.f))
     return TGS_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -189,6 +190,7 @@ extern "C" tgs_status tgs_loss_sparse_ncc(const float* rgb, const float* target,
     a.eps_c2 = params->eps_charbonnier * params->eps_charbonnier;
     a.eps_n = params->eps_ncc;
     a.beta = params->beta;
+    a.weight = params->view_weight;
     a.err_map = err_map; a.age_map = age_map; a.dL = dL_drgb; a.lambda = lambda_tile; a.err_pix = err_pix;
     a.loss = loss;
     const int B = std::min(256, std::max(32, (n_pix_max + 31) / 32 * 32));

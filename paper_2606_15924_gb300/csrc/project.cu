@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(256) k_project_bwd(
     const float* __restrict__ ologit, const float4* __restrict__ sh, int64_t n, int sh_degree, CamK cam,
     const int32_t* __restrict__ radius, const float4* __restrict__ grad2d, float* __restrict__ g_means,
     float* __restrict__ g_ls, float4* __restrict__ g_quats, float* __restrict__ g_ologit, float4* __restrict__ g_sh,
-    uint8_t* __restrict__ touched, int write_untouched) {
+    uint8_t* __restrict__ touched, int write_untouched, int accumulate, float* __restrict__ row) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga, gc = ga;
@@ -243,9 +243,20 @@ __global__ void __launch_bounds__(256) k_project_bwd(
   }
   const bool any = vis && (ga.x != 0.f || ga.y != 0.f || ga.z != 0.f || ga.w != 0.f || gb.x != 0.f ||
                            gb.y != 0.f || gb.z != 0.f || gb.w != 0.f || gc.x != 0.f);
-  if (touched) touched[i] = any ? 1 : 0;
+  // accumulate: add into the gradients of Gaussians some earlier view of the
+  // same step already touched, overwrite the rest (touched is the flag)
+  const bool add = accumulate && touched[i] != 0;
+  if (touched) {
+    if (!accumulate) touched[i] = any ? 1 : 0;
+    else if (any) touched[i] = 1;
+  }
   if (!any) {
-    if (write_untouched) {
+    if (row) {
+      float2* r2 = reinterpret_cast<float2*>(row + 14 * i);
+#pragma unroll
+      for (int k = 0; k < 7; ++k) r2[k] = make_float2(0.f, 0.f);
+    }
+    if (write_untouched && !accumulate) {
       g_means[3 * i] = 0.f; g_means[3 * i + 1] = 0.f; g_means[3 * i + 2] = 0.f;
       g_ls[3 * i] = 0.f; g_ls[3 * i + 1] = 0.f; g_ls[3 * i + 2] = 0.f;
       g_quats[i] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -264,7 +275,20 @@ __global__ void __launch_bounds__(256) k_project_bwd(
   const float drgb[3] = {gb.z, gb.w, gc.x};
   // opacity
   const float o = 1.f / (1.f + expf(-ologit[i]));
-  g_ologit[i] = d_o * o * (1.f - o);
+  auto put = [&](float* p, float v) { *p = add ? *p + v : v; };
+  auto put4 = [&](float4* p, float4 v) {
+    if (add) {
+      const float4 q = *p;
+      v = make_float4(q.x + v.x, q.y + v.y, q.z + v.z, q.w + v.w);
+    }
+    *p = v;
+  };
+  // this view's own gradient row: geometry (means, log-scales, quaternion),
+  // then the SH DC colour and the opacity logit
+  float* rw = row ? row + 14 * i : nullptr;
+  const float g_o = d_o * o * (1.f - o);
+  put(g_ologit + i, g_o);
+  if (rw) rw[13] = g_o;
   // colour
   float vx = mu.x - cam.campos[0], vy = mu.y - cam.campos[1], vz = mu.z - cam.campos[2];
   const float il = rsqrtf(vx * vx + vy * vy + vz * vz);
@@ -302,7 +326,12 @@ __global__ void __launch_bounds__(256) k_project_bwd(
   }
 #pragma unroll
   for (int k4 = 0; k4 < 12; ++k4)
-    g_sh[12 * i + k4] = make_float4(gsh[4 * k4], gsh[4 * k4 + 1], gsh[4 * k4 + 2], gsh[4 * k4 + 3]);
+    put4(g_sh + 12 * i + k4, make_float4(gsh[4 * k4], gsh[4 * k4 + 1], gsh[4 * k4 + 2], gsh[4 * k4 + 3]));
+  if (rw) {
+    rw[10] = gsh[0];
+    rw[11] = gsh[1];
+    rw[12] = gsh[2];
+  }
   float gd[3];
   sh_basis_grad(dx, dy, dz, sh_degree, sk, gd);
   const float dot = gd[0] * dx + gd[1] * dy + gd[2] * dz;
@@ -369,7 +398,14 @@ __global__ void __launch_bounds__(256) k_project_bwd(
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) dmu[a] += Wm[a] * dpc[0] + Wm[3 + a] * dpc[1] + Wm[6 + a] * dpc[2];
-  g_means[3 * i] = dmu[0]; g_means[3 * i + 1] = dmu[1]; g_means[3 * i + 2] = dmu[2];
+  put(g_means + 3 * i, dmu[0]);
+  put(g_means + 3 * i + 1, dmu[1]);
+  put(g_means + 3 * i + 2, dmu[2]);
+  if (rw) {
+    rw[0] = dmu[0];
+    rw[1] = dmu[1];
+    rw[2] = dmu[2];
+  }
   // Sigma = M M^T, M = R diag(s): dM = 2 dSigma M
   const float* R = g.R;
   float M[9], dM[9];
@@ -386,7 +422,8 @@ __global__ void __launch_bounds__(256) k_project_bwd(
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     float ds = R[c] * dM[c] + R[3 + c] * dM[3 + c] + R[6 + c] * dM[6 + c];
-    g_ls[3 * i + c] = ds * g.s[c];
+    put(g_ls + 3 * i + c, ds * g.s[c]);
+    if (rw) rw[3 + c] = ds * g.s[c];
 #pragma unroll
     for (int r = 0; r < 3; ++r) dR[r * 3 + c] = dM[r * 3 + c] * g.s[c];
   }
@@ -401,12 +438,20 @@ __global__ void __launch_bounds__(256) k_project_bwd(
                  x * dR[6] + y * dR[7]);
   const float qd = dq[0] * w + dq[1] * x + dq[2] * y + dq[3] * zq;
   const float iq = 1.f / g.qnorm;
-  g_quats[i] = make_float4((dq[0] - w * qd) * iq, (dq[1] - x * qd) * iq, (dq[2] - y * qd) * iq,
-                           (dq[3] - zq * qd) * iq);
+  const float4 gq = make_float4((dq[0] - w * qd) * iq, (dq[1] - x * qd) * iq, (dq[2] - y * qd) * iq,
+                                 (dq[3] - zq * qd) * iq);
+  put4(g_quats + i, gq);
+  if (rw) {
+    rw[6] = gq.x;
+    rw[7] = gq.y;
+    rw[8] = gq.z;
+    rw[9] = gq.w;
+  }
 }
 
 void launch_project_bwd(const tgs_gaussians& g, const tgs_camera& cam, const int32_t* radius, const float* grad2d,
-                        const tgs_param_ptrs& grads, uint8_t* touched, int write_untouched, cudaStream_t s) {
+                        const tgs_param_ptrs& grads, uint8_t* touched, int write_untouched, int accumulate,
+                        float* row, cudaStream_t s) {
   if (g.n <= 0) return;
   CamK k = make_cam(cam);
   int blocks = (int)((g.n + 255) / 256);
@@ -414,7 +459,7 @@ void launch_project_bwd(const tgs_gaussians& g, const tgs_camera& cam, const int
                                        g.opacity_logits, reinterpret_cast<const float4*>(g.sh), g.n, g.sh_degree, k,
                                        radius, reinterpret_cast<const float4*>(grad2d), grads.means, grads.log_scales,
                                        reinterpret_cast<float4*>(grads.quats), grads.opacity_logits,
-                                       reinterpret_cast<float4*>(grads.sh), touched, write_untouched);
+                                       reinterpret_cast<float4*>(grads.sh), touched, write_untouched, accumulate, row);
 }
 
 bool gaussians_ok(const tgs_gaussians* g) {

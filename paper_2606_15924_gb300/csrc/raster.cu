@@ -13,7 +13,8 @@
 namespace tgs {
 
 void launch_project_bwd(const tgs_gaussians& g, const tgs_camera& cam, const int32_t* radius, const float* grad2d,
-                        const tgs_param_ptrs& grads, uint8_t* touched, int write_untouched, cudaStream_t s);
+                        const tgs_param_ptrs& grads, uint8_t* touched, int write_untouched, int accumulate,
+                        float* row, cudaStream_t s);
 bool gaussians_ok(const tgs_gaussians* g);
 bool camera_ok(const tgs_camera* c);
 
@@ -69,11 +70,10 @@ __device__ __forceinline__ void load_splat(const RasterArgs& a, int k, Splat& sp
   sp.rgb = make_float4(a.rgb[3 * id], a.rgb[3 * id + 1], a.rgb[3 * id + 2], __int_as_float(id));
 }
 
-__global__ void k_render_fwd(RasterArgs a, float* __restrict__ out_rgb, float* __restrict__ out_T,
-                             int32_t* __restrict__ out_last) {
-  extern __shared__ Splat sm[];
-  const int j = blockIdx.x;
-  if (j >= *a.n_active) return;
+// Forward of active tile j (one thread per sampled pixel; sm holds
+// blockDim.x splats).
+__device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Splat* sm, float* __restrict__ out_rgb,
+                                                float* __restrict__ out_T, int32_t* __restrict__ out_last) {
   const int t = a.active_tiles ? a.active_tiles[j] : j;
   const int p0 = a.pix_off[j], p1 = a.pix_off[j + 1];
   const bool has_pix = p0 + (int)threadIdx.x < p1;
@@ -126,6 +126,14 @@ __global__ void k_render_fwd(RasterArgs a, float* __restrict__ out_rgb, float* _
   }
 }
 
+__global__ void k_render_fwd(RasterArgs a, float* __restrict__ out_rgb, float* __restrict__ out_T,
+                             int32_t* __restrict__ out_last) {
+  extern __shared__ Splat sm[];
+  const int j = blockIdx.x;
+  if (j >= *a.n_active) return;
+  render_tile_fwd(a, j, sm, out_rgb, out_T, out_last);
+}
+
 // Sum of v[0..7] over the warp, scattered: lane l ends with the total of
 // v[(l >> 2) & 7] (halving exchanges at distances 16, 8, 4, then a butterfly
 // over the last two bits): 9 shuffles instead of 40.
@@ -159,13 +167,11 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[9], int l
 // Per-splat adjoints of a batch are summed over the block in shared memory
 // (acc, 9 floats per batch slot) and flushed once per block and splat with
 // vector atomics, instead of once per warp and splat.
-__global__ void k_render_bwd(RasterArgs a, const float* __restrict__ T_final, const int32_t* __restrict__ n_last,
-                             const float* __restrict__ dL_drgb, float* __restrict__ grad2d) {
-  extern __shared__ Splat sm[];
+__device__ __forceinline__ void render_tile_bwd(const RasterArgs& a, int j, Splat* sm,
+                                                const float* __restrict__ T_final, const int32_t* __restrict__ n_last,
+                                                const float* __restrict__ dL_drgb, float* __restrict__ grad2d) {
   __shared__ int s_max_last;
   float* acc = reinterpret_cast<float*>(sm + blockDim.x);
-  const int j = blockIdx.x;
-  if (j >= *a.n_active) return;
   const int t = a.active_tiles ? a.active_tiles[j] : j;
   const int p0 = a.pix_off[j], p1 = a.pix_off[j + 1];
   const bool has_pix = p0 + (int)threadIdx.x < p1;
@@ -267,6 +273,62 @@ __global__ void k_render_bwd(RasterArgs a, const float* __restrict__ T_final, co
   }
 }
 
+__global__ void k_render_bwd(RasterArgs a, const float* __restrict__ T_final, const int32_t* __restrict__ n_last,
+                             const float* __restrict__ dL_drgb, float* __restrict__ grad2d) {
+  extern __shared__ Splat sm[];
+  const int j = blockIdx.x;
+  if (j >= *a.n_active) return;
+  render_tile_bwd(a, j, sm, T_final, n_last, dL_drgb, grad2d);
+}
+
+// ---------------------------------------------------------------------------
+// Several views in one persistent launch: CTAs take (view, tile) items from
+// an atomic counter (items of view v are [base[v], base[v+1])) until none
+// are left.  There is no waiting on other CTAs, only one atomic per item.
+// ---------------------------------------------------------------------------
+constexpr int kMaxViews = 16;
+
+struct BatchArgs {
+  int n_views;
+  int base[kMaxViews + 1];
+  RasterArgs a[kMaxViews];
+  float* rgb[kMaxViews];
+  float* T[kMaxViews];
+  int32_t* last[kMaxViews];
+  const float* dL[kMaxViews];
+  float* grad2d[kMaxViews];
+};
+
+__device__ __forceinline__ bool next_item(const BatchArgs& b, int* counter, int* s_item, int& v, int& j) {
+  __syncthreads();  // the previous item's shared memory is no longer read
+  if (threadIdx.x == 0) *s_item = atomicAdd(counter, 1);
+  __syncthreads();
+  const int item = *s_item;
+  if (item >= b.base[b.n_views]) return false;
+  v = 0;
+  while (item >= b.base[v + 1]) ++v;
+  j = item - b.base[v];
+  return true;
+}
+
+__global__ void k_render_fwd_batched(BatchArgs b, int* __restrict__ counter) {
+  extern __shared__ Splat sm[];
+  __shared__ int s_item;
+  int v, j;
+  while (next_item(b, counter, &s_item, v, j)) {
+    if (j < *b.a[v].n_active) render_tile_fwd(b.a[v], j, sm, b.rgb[v], b.T[v], b.last[v]);
+  }
+}
+
+__global__ void k_render_bwd_batched(BatchArgs b, int* __restrict__ counter) {
+  extern __shared__ Splat sm[];
+  __shared__ int s_item;
+  int v, j;
+  while (next_item(b, counter, &s_item, v, j)) {
+    if (j < *b.a[v].n_active) render_tile_bwd(b.a[v], j, sm, b.T[v], b.last[v], b.dL[v], b.grad2d[v]);
+  }
+}
+
 static bool raster_args(const tgs_projected* proj, const int32_t* tile_ranges, const int32_t* vals,
                         const int32_t* active_tiles, const int32_t* n_active, const int32_t* pix_off,
                         const uint8_t* pix_idx, const tgs_camera* cam, const float* bg, RasterArgs& a) {
@@ -336,6 +398,93 @@ extern "C" tgs_status tgs_backward_sampled(const tgs_gaussians* g, const tgs_cam
     k_render_bwd<<<n_active_max, B, B * (sizeof(Splat) + 9 * sizeof(float)), s>>>(a, T_final, n_last, dL_drgb,
                                                                                  grad2d);
   }
-  launch_project_bwd(*g, *cam, proj->radius, grad2d, *grads, touched, write_untouched, s);
+  launch_project_bwd(*g, *cam, proj->radius, grad2d, *grads, touched, write_untouched, 0, nullptr, s);
+  return check_launch();
+}
+
+static tgs_status batch_args(const tgs_view_batch* views, int32_t n_views, bool backward, BatchArgs& b, int& B) {
+  if (!views || n_views < 1 || n_views > kMaxViews) return TGS_ERR_INVALID_ARG;
+  b.n_views = n_views;
+  b.base[0] = 0;
+  B = 32;
+  for (int v = 0; v < n_views; ++v) {
+    const tgs_view_batch& w = views[v];
+    if (w.n_active_max < 0 || w.n_pix_max < 1 || w.n_pix_max > 256) return TGS_ERR_INVALID_ARG;
+    if (!raster_args(&w.proj, w.tile_ranges, w.vals, w.active_tiles, w.n_active, w.pix_off, w.pix_idx, &w.cam,
+                     w.bg, b.a[v]))
+      return TGS_ERR_INVALID_ARG;
+    if (!w.rgb || !w.T_final || !w.n_last) return TGS_ERR_INVALID_ARG;
+    if (backward && (!w.dL_drgb || !w.grad2d || !aligned16(w.grad2d) || w.n_gaussians < 0))
+      return TGS_ERR_INVALID_ARG;
+    b.rgb[v] = w.rgb;
+    b.T[v] = w.T_final;
+    b.last[v] = w.n_last;
+    b.dL[v] = w.dL_drgb;
+    b.grad2d[v] = w.grad2d;
+    b.base[v + 1] = b.base[v] + w.n_active_max;
+    B = std::max(B, block_for(w.n_pix_max));
+  }
+  return TGS_OK;
+}
+
+extern "C" tgs_status tgs_render_batched_resident(int32_t n_pix_max, int32_t backward, int32_t* ctas) {
+  if (!ctas || n_pix_max < 1 || n_pix_max > 256) return TGS_ERR_INVALID_ARG;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return check_launch();
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int B = block_for(n_pix_max);
+  if (backward)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd_batched, B,
+                                                  B * (sizeof(Splat) + 9 * sizeof(float)));
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_fwd_batched, B, B * sizeof(Splat));
+  *ctas = sms * per_sm;
+  return check_launch();
+}
+
+extern "C" tgs_status tgs_render_sampled_batched(const tgs_view_batch* views, int32_t n_views, int32_t grid_ctas,
+                                                 int32_t* counter, tgs_stream stream) {
+  BatchArgs b;
+  int B = 32;
+  tgs_status st = batch_args(views, n_views, false, b, B);
+  if (st != TGS_OK) return st;
+  if (grid_ctas < 1 || !counter) return TGS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
+  if (b.base[n_views] == 0) return check_launch();
+  k_render_fwd_batched<<<grid_ctas, B, B * sizeof(Splat), s>>>(b, counter);
+  return check_launch();
+}
+
+extern "C" tgs_status tgs_render_backward_batched(const tgs_view_batch* views, int32_t n_views, int32_t grid_ctas,
+                                                  int32_t* counter, tgs_stream stream) {
+  BatchArgs b;
+  int B = 32;
+  tgs_status st = batch_args(views, n_views, true, b, B);
+  if (st != TGS_OK) return st;
+  if (grid_ctas < 1 || !counter) return TGS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  for (int v = 0; v < n_views; ++v)
+    if (views[v].n_gaussians > 0)
+      cudaMemsetAsync(views[v].grad2d, 0, sizeof(float) * 12 * (size_t)views[v].n_gaussians, s);
+  cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
+  if (b.base[n_views] == 0) return check_launch();
+  k_render_bwd_batched<<<grid_ctas, B, B * (sizeof(Splat) + 9 * sizeof(float)), s>>>(b, counter);
+  return check_launch();
+}
+
+extern "C" tgs_status tgs_project_backward(const tgs_gaussians* g, const tgs_camera* cam, const tgs_projected* proj,
+                                           const float* grad2d, const tgs_param_ptrs* grads, uint8_t* touched,
+                                           int32_t write_untouched, int32_t accumulate, float* view_row,
+                                           tgs_stream stream) {
+  if (!gaussians_ok(g) || !camera_ok(cam) || !proj || !grads) return TGS_ERR_INVALID_ARG;
+  if (accumulate && !touched) return TGS_ERR_INVALID_ARG;
+  if (view_row && !aligned8(view_row)) return TGS_ERR_INVALID_ARG;
+  if (g->n == 0) return TGS_OK;
+  if (!proj->radius || !grad2d || !aligned16(grad2d) || !grads->means || !grads->log_scales || !grads->quats ||
+      !grads->opacity_logits || !grads->sh || !aligned16(grads->quats) || !aligned16(grads->sh))
+    return TGS_ERR_INVALID_ARG;
+  launch_project_bwd(*g, *cam, proj->radius, grad2d, *grads, touched, write_untouched, accumulate, view_row,
+                     (cudaStream_t)stream);
   return check_launch();
 }

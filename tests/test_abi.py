@@ -39,3 +39,33 @@ def test_binding_names_match_the_abi():
         short = n[len("tgs_"):]
         if short not in ("version", "last_cuda_error", "status_string", "device_check"):
             assert hasattr(binding, short), short
+
+
+def test_ctypes_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding mirrors has the header's size and field offsets
+    (compiled with the host C compiler, no GPU needed)."""
+    import subprocess
+    from paper_2606_15924_gb300 import build
+    build.build()
+    from paper_2606_15924_gb300 import binding as B
+    mirrors = {"tgs_camera": B.Camera, "tgs_gaussians": B.Gaussians, "tgs_param_ptrs": B.ParamPtrs,
+               "tgs_projected": B.Projected, "tgs_sampling": B.Sampling, "tgs_loss_params": B.LossParams,
+               "tgs_mlp": B.Mlp, "tgs_opt": B.Opt, "tgs_view_batch": B.ViewBatch}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "turbogs.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        c, f, v = ln.split()
+        got[(c, f)] = int(v)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
