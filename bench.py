@@ -149,6 +149,26 @@ def time_replays(tr, steps, flush):
     return [a.elapsed_time(b) for a, b in ev]
 
 
+def stage_times_graphs(tr, steps, flush):
+    """Mean device time of each stage graph of ``tr`` (events between the
+    replays on the launching stream, L2 flushed before each step)."""
+    import torch
+    if not getattr(tr, "stage_graphs", None):
+        tr.capture_stages()
+    acc = {n: 0.0 for n, _ in tr.stage_graphs}
+    for k in range(steps):
+        flush.fill_(k)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(len(tr.stage_graphs) + 1)]
+        e[0].record()
+        for i, (_, gr) in enumerate(tr.stage_graphs):
+            gr.replay()
+            e[i + 1].record()
+        torch.cuda.synchronize()
+        for i, (n, _) in enumerate(tr.stage_graphs):
+            acc[n] += e[i].elapsed_time(e[i + 1])
+    return {n: acc[n] / steps for n in acc}
+
+
 def stage_times(tr, steps, flush):
     """Device time of every call of the step: each call is its own captured
     graph, replayed in step order with CUDA events between them on the
@@ -383,6 +403,110 @@ def run_ours(args):
         print(json.dumps(res))
 
 
+# ---------------------------------------------------------------------------
+# batched multi-view workload
+# ---------------------------------------------------------------------------
+
+N_BATCH_GAUSS = 3_000_000
+BW, BH = 1920, 1080
+N_BATCH_VIEWS = 8
+N_ORBIT = 120
+
+
+def batched_scene(device):
+    """3M Gaussians; 8 views of a 120-view orbit at 1920x1080 with active-tile
+    fractions drawn from U[3%, 60%]; targets = renders of a seeded
+    ground-truth cloud plus N(0, 0.01) noise."""
+    import numpy as np
+    import torch
+    from paper_2606_15924_gb300 import scenes
+    from paper_2606_15924_gb300.pipeline import Trainer
+    cams_all = scenes.orbit(N_ORBIT, DISTANCE, BW, BH)
+    rng = np.random.default_rng(scenes.SEED_MASK)
+    ids = sorted(int(i) for i in rng.choice(N_ORBIT, N_BATCH_VIEWS, replace=False))
+    fracs = [float(f) for f in rng.uniform(0.03, 0.60, N_BATCH_VIEWS)]
+    cams = [cams_all[i] for i in ids]
+    gt = scenes.gaussians(N_BATCH_GAUSS, seed=scenes.SEED_TARGET, extent=EXTENT)
+    gt_d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in gt.items()}
+    gen = torch.Generator().manual_seed(scenes.SEED_NOISE)
+    dummy = torch.zeros(BH, BW, 3, device=device)
+    targets = []
+    for cam in cams:
+        img = Trainer(gt_d, cam, dummy, dense=True, train=False).render_image()
+        noise = torch.randn(BH, BW, 3, generator=gen) * 0.01
+        targets.append((img + noise.to(device)).contiguous())
+    del gt_d
+    torch.cuda.empty_cache()
+    g = scenes.gaussians(N_BATCH_GAUSS, seed=scenes.SEED_SCENE, extent=EXTENT)
+    params = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in g.items()}
+    return params, cams, targets, ids, fracs
+
+
+def run_batched(args):
+    """8 views per iteration in one persistent launch (forward and backward)
+    against one launch per view, both inside a captured graph."""
+    import torch
+    from paper_2606_15924_gb300 import binding as B
+    from paper_2606_15924_gb300.batched import MultiViewTrainer, autotune_grid
+    B.device_check()
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    peaks, peak_kind = load_peaks()
+    params, cams, targets, ids, fracs = batched_scene(device)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+    out = {}
+    for persistent in (True, False):
+        mv = MultiViewTrainer(params, cams, targets, fracs, pixel_rate=args.rate, view_ids=ids,
+                              persistent=persistent)
+        for v in mv.views:
+            v.init_error_map()
+        mv.step()
+        torch.cuda.synchronize()
+        tune = autotune_grid(mv, reps=5, use_cache=False) if persistent else None
+        mv.capture()
+        for _ in range(args.warmup):
+            mv.replay()
+        torch.cuda.synchronize()
+        clk = ClockSampler(0)
+        clk.start()
+        ms = time_replays(mv, args.steps, flush)
+        clocks = clk.stop()
+        # every call of the step as its own graph, events between them
+        st = stage_times_graphs(mv, max(2, min(args.steps, 5)), flush)
+        fm, bm = st["render_sampled"], st["render_backward"]
+        P = mv.n_sampled()
+        evals = sum(int(v.n_last[:int(v.pix_off[int(v.n_active.item())].item())].sum().item())
+                    for v in mv.views)
+        mean = sum(ms) / len(ms)
+        sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        out["persistent" if persistent else "per_view"] = {
+            "iters_per_s": 1e3 / mean, "ms_per_step": mean, "views_per_step": mv.K,
+            "sampled_pixels": P, "active_tiles": [int(v.n_active.item()) for v in mv.views],
+            "render_fwd_ms": fm, "render_bwd_ms": bm, "fwd_bwd_mpix_per_s": P / ((fm + bm) * 1e-3) / 1e6,
+            "splat_evals": evals, "grid": list(mv.grid) if persistent else "one block per active tile",
+            "stage_ms": st,
+            "kernels_per_step": mv.kernels_per_step, "clocks": clocks,
+            "render_fwd_roofline": {"bound": "alu", "achieved": evals * (FLOPS_ALPHA + FLOPS_BLEND) / (fm * 1e-3) / 1e12,
+                                    "peak": alu_peak, "unit": "TFLOP/s"},
+            "autotune": tune}
+        out["persistent" if persistent else "per_view"]["render_fwd_roofline"]["frac"] = (
+            out["persistent" if persistent else "per_view"]["render_fwd_roofline"]["achieved"] / alu_peak)
+        del mv
+        torch.cuda.empty_cache()
+    res = {"metric": "batched multi-view train iters/s (8 views per iteration)",
+           "value": out["persistent"]["iters_per_s"], "unit": "iters/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": out["persistent"]["ms_per_step"], "higher_is_better": True,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"batched views: {N_BATCH_GAUSS // 10**6}M Gaussians, {N_BATCH_VIEWS} views of a "
+                                  f"{N_ORBIT}-view orbit at {BW}x{BH}, tile fractions U[3%,60%], "
+                                  f"pixel rate {args.rate:.3f}", "views": ids, "tile_fractions": fracs,
+                      "l2": "flushed between timed steps (256 MB write)"},
+           "peak_source": peak_kind, **out,
+           "speedup_vs_per_view": out["per_view"]["ms_per_step"] / out["persistent"]["ms_per_step"]}
+    print(json.dumps(res))
+
+
 def run_reference(args):
     """The oracle as the reference arm: rank 0 only, bounded samples of the
     same workload on the host cores."""
@@ -421,6 +545,9 @@ def main():
     ap.add_argument("--rate", type=float, default=PIXEL_RATE)
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="step", choices=["step", "batched"],
+                    help="step: the one-view sparse training step (the headline line); batched: 8 views per "
+                         "iteration in one persistent launch vs one launch per view")
     ap.add_argument("--profile", action="store_true",
                     help="only warm-up and K replays of each path inside NVTX ranges sampled_step / dense_step "
                          "(for an ncu launch list); prints nothing")
@@ -429,6 +556,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_ours(args)
 

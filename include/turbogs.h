@@ -318,6 +318,27 @@ tgs_status tgs_project_backward(const tgs_gaussians* g, const tgs_camera* cam, c
                                 int32_t write_untouched, int32_t accumulate, float* view_row, tgs_stream stream);
 
 /*
+ * project_backward_multi - the projection adjoint of K views of one step
+ * (1 <= K <= 16) in one pass: each Gaussian's parameters are read once, the
+ * adjoints of the views whose grad2d row is non-zero are summed in registers
+ * and the gradients are written once (so the result is the sum over views of
+ * project_backward).  Per view v: cams[v], radius[v] (that view's projection
+ * output), grad2d[v] [N,12] (16-byte aligned) and, when view_rows is given
+ * and view_rows[v] is not NULL, view_rows[v] [N,14] as in project_backward.
+ * The pointer arrays are host arrays of device pointers.  touched[i] (may be
+ * NULL) = 1 when any view touched Gaussian i; untouched gradients are zeroed
+ * only with write_untouched.  workspace: 16-byte aligned device scratch of
+ * tgs_project_backward_multi_workspace_size(N) bytes (the list of touched
+ * Gaussians, processed in a second pass).
+ */
+size_t tgs_project_backward_multi_workspace_size(int64_t n);
+tgs_status tgs_project_backward_multi(const tgs_gaussians* g, int32_t n_views, const tgs_camera* cams,
+                                      const int32_t* const* radius, const float* const* grad2d,
+                                      const tgs_param_ptrs* grads, uint8_t* touched, int32_t write_untouched,
+                                      float* const* view_rows, void* workspace, size_t workspace_bytes,
+                                      tgs_stream stream);
+
+/*
  * Several views in one launch (not in the paper: a batching of
  * render_sampled / the compositing adjoint over the views of one iteration,
  * Alg. 1 steps 5 and 8).  Persistent thread blocks (grid_ctas of them) take

@@ -10,8 +10,9 @@ gradients and the optimiser moments.  One step:
   all views: render_sampled_batched (one persistent launch, (view, tile) queue)
   per view: loss_sparse_ncc (view_weight 1/K)
   all views: render_backward_batched (one persistent launch)
-  per view: project_backward (accumulating into the shared gradients, and
-            writing the view's Jacobian row for the Cholesky mode)
+  all views: project_backward_multi (one pass summing the views' adjoints
+            into the shared gradients, and writing each view's Jacobian
+            row for the Cholesky mode)
   once:     hybrid_step
 
 Everything is sized at construction and the iteration counters live on the
@@ -34,7 +35,7 @@ class MultiViewTrainer:
     def __init__(self, params: dict, cams: list, targets: list, tile_fractions: list,
                  pixel_rate: float = 1.0 / 3.0, cfg: Config | None = None, seed: int = 0, bg=(0.0, 0.0, 0.0),
                  sh_degree: int = 3, view_ids: list | None = None, grid: tuple | None = None,
-                 view_rows: bool | None = None):
+                 view_rows: bool | None = None, persistent: bool = True):
         if not (1 <= len(cams) <= 16) or len(cams) != len(targets) or len(cams) != len(tile_fractions):
             raise ValueError("1 to 16 views, one target and one tile fraction each")
         self.cfg = cfg or Config()
@@ -61,13 +62,18 @@ class MultiViewTrainer:
         self.v = zeros_like_params(params)
         self.touched = torch.zeros(self.n, dtype=torch.uint8, device=dev)
         self.ws_hybrid = torch.empty(B.hybrid_step_workspace_size(self.n), dtype=torch.uint8, device=dev)
+        self.ws_adj = torch.empty(B.project_backward_multi_workspace_size(self.n), dtype=torch.uint8, device=dev)
         o = self.cfg.opt
         self.opt = dict(lr=[o.lr_means, o.lr_scales, o.lr_quats, o.lr_opacity, o.lr_sh_dc, o.lr_sh_rest],
                         beta1=o.beta1, beta2=o.beta2, eps_adam=o.eps_adam, eps_lm=o.eps_lm, mode=o.mode)
         # per-view Jacobian rows feed only the full-matrix LM mode
         self.use_rows = (self.opt["mode"] == 2) if view_rows is None else bool(view_rows)
         self.rows = torch.zeros(self.K, self.n, 14, device=dev) if self.use_rows else None
-        self.counters = torch.zeros(2, dtype=torch.int32, device=dev)
+        # persistent=False: one launch per view with one block per active
+        # tile (the same kernels without the shared queue) and one
+        # accumulating projection adjoint per view, for comparison
+        self.persistent = bool(persistent)
+        self.counters = torch.zeros(2 + 2 * self.K, dtype=torch.int32, device=dev)
         self.n_pix_max = max(v.n_pix for v in self.views)
         res_f = B.render_batched_resident(self.n_pix_max, False)
         res_b = B.render_batched_resident(self.n_pix_max, True)
@@ -88,6 +94,39 @@ class MultiViewTrainer:
         # ctypes arrays hold raw pointers: rebuilt whenever a buffer is reallocated
         self.fwd_batch = B.view_batch(fwd)
         self.bwd_batch = B.view_batch(bwd)
+        self.fwd_single = [B.view_batch([d]) for d in fwd]
+        self.bwd_single = [B.view_batch([d]) for d in bwd]
+        self.adj = B.MultiAdjoint([v.ccam for v in self.views], [v.proj["radius"] for v in self.views],
+                                  [v.grad2d for v in self.views],
+                                  [self.rows[k] for k in range(self.K)] if self.use_rows else None)
+
+    def _project_bwd(self):
+        """Projection adjoint of all views into the shared gradients: one fused
+        pass (persistent) or one accumulating launch per view."""
+        if self.persistent:
+            B.project_backward_multi(self.params, self.adj, self.grads, self.touched, write_untouched=False,
+                                     sh_degree=self.sh_degree, workspace=self.ws_adj)
+            return
+        self.touched.zero_()
+        for k, v in enumerate(self.views):
+            B.project_backward(self.params, v.ccam, v.proj, v.grad2d, self.grads, self.touched,
+                               write_untouched=False, accumulate=True,
+                               view_row=self.rows[k] if self.use_rows else None, sh_degree=self.sh_degree)
+
+    def _render_fwd(self):
+        if self.persistent:
+            B.render_sampled_batched(self.fwd_batch, self.grid[0], self.counters[0:1])
+        else:
+            for k, v in enumerate(self.views):
+                B.render_sampled_batched(self.fwd_single[k], max(1, v.n_select), self.counters[2 + k:3 + k])
+
+    def _render_bwd(self):
+        if self.persistent:
+            B.render_backward_batched(self.bwd_batch, self.grid[1], self.counters[1:2])
+        else:
+            for k, v in enumerate(self.views):
+                B.render_backward_batched(self.bwd_single[k], max(1, v.n_select),
+                                          self.counters[2 + self.K + k:3 + self.K + k])
 
     # ------------------------------------------------------------------ step
     def forward(self):
@@ -96,19 +135,15 @@ class MultiViewTrainer:
             B.project_gaussians(self.params, v.ccam, v.tile_rank, v.proj, self.sh_degree)
             B.bin_tiles(v.proj, self.n, v.ccam, v.tile_rank, v.n_select, v.ws_bin, v.capacity, v.vals, None,
                         v.ranges, v.n_isect)
-        B.render_sampled_batched(self.fwd_batch, self.grid[0], self.counters[0:1])
+        self._render_fwd()
 
     def loss_and_maps(self):
         for v in self.views:
             v.loss_and_maps()
 
     def backward(self):
-        B.render_backward_batched(self.bwd_batch, self.grid[1], self.counters[1:2])
-        self.touched.zero_()
-        for k, v in enumerate(self.views):
-            B.project_backward(self.params, v.ccam, v.proj, v.grad2d, self.grads, self.touched,
-                               write_untouched=False, accumulate=True,
-                               view_row=self.rows[k] if self.use_rows else None, sh_degree=self.sh_degree)
+        self._render_bwd()
+        self._project_bwd()
 
     def update(self):
         B.hybrid_step(self.params, self.grads, self.m, self.v, self.n, self.touched, self.rows,
@@ -132,6 +167,44 @@ class MultiViewTrainer:
     def n_sampled(self) -> int:
         """Sampled pixels of the last step over all views (reads the device)."""
         return int(sum(int(v.pix_off[int(v.n_active.item())].item()) for v in self.views))
+
+    STAGES = ("select_tiles", "project_gaussians", "bin_tiles", "render_sampled", "loss_sparse_ncc",
+              "render_backward", "project_backward", "hybrid_step")
+
+    def stage_calls(self):
+        """The step as (name, callable) pairs, each call over all views."""
+        def select():
+            for v in self.views:
+                v._select()
+
+        def project():
+            for v in self.views:
+                B.project_gaussians(self.params, v.ccam, v.tile_rank, v.proj, self.sh_degree)
+
+        def bins():
+            for v in self.views:
+                B.bin_tiles(v.proj, self.n, v.ccam, v.tile_rank, v.n_select, v.ws_bin, v.capacity, v.vals, None,
+                            v.ranges, v.n_isect)
+
+        def upd():
+            self.update()
+            self.it_dev.add_(1)
+            self.step_dev.add_(1)
+        return [("select_tiles", select), ("project_gaussians", project), ("bin_tiles", bins),
+                ("render_sampled", self._render_fwd), ("loss_sparse_ncc", self.loss_and_maps),
+                ("render_backward", self._render_bwd), ("project_backward", self._project_bwd),
+                ("hybrid_step", upd)]
+
+    def capture_stages(self):
+        self.stage_graphs = []
+        torch.cuda.synchronize()
+        for name, fn in self.stage_calls():
+            gr = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gr):
+                fn()
+            self.stage_graphs.append((name, gr))
+        torch.cuda.synchronize()
+        return self.stage_graphs
 
     # ------------------------------------------------------------------ graph
     def capture(self):
@@ -157,10 +230,10 @@ class MultiViewTrainer:
         torch.cuda.synchronize()
         self.g_fwd = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.g_fwd):
-            B.render_sampled_batched(self.fwd_batch, self.grid[0], self.counters[0:1])
+            self._render_fwd()
         self.g_bwd = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.g_bwd):
-            B.render_backward_batched(self.bwd_batch, self.grid[1], self.counters[1:2])
+            self._render_bwd()
         torch.cuda.synchronize()
 
 

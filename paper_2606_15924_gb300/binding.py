@@ -126,6 +126,11 @@ _lib.tgs_backward_sampled.argtypes = [_P(Gaussians), _P(Camera), _P(Projected), 
 _lib.tgs_project_backward.restype = _i32
 _lib.tgs_project_backward.argtypes = [_P(Gaussians), _P(Camera), _P(Projected), _p, _P(ParamPtrs), _p, _i32, _i32,
                                       _p, _p]
+_lib.tgs_project_backward_multi.restype = _i32
+_lib.tgs_project_backward_multi_workspace_size.restype = _sz
+_lib.tgs_project_backward_multi_workspace_size.argtypes = [_i64]
+_lib.tgs_project_backward_multi.argtypes = [_P(Gaussians), _i32, _P(Camera), _p, _p, _P(ParamPtrs), _p, _i32, _p,
+                                            _p, _sz, _p]
 _lib.tgs_render_batched_resident.restype = _i32
 _lib.tgs_render_batched_resident.argtypes = [_i32, _i32, _P(_i32)]
 _lib.tgs_render_sampled_batched.restype = _i32
@@ -152,7 +157,9 @@ EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_devi
             "tgs_select_tiles_workspace_size", "tgs_select_tiles", "tgs_select_tiles_noalloc",
             "tgs_project_gaussians",
             "tgs_bin_tiles_workspace_size", "tgs_bin_tiles", "tgs_render_sampled", "tgs_loss_sparse_ncc",
-            "tgs_backward_sampled", "tgs_project_backward", "tgs_render_batched_resident", "tgs_render_sampled_batched",
+            "tgs_backward_sampled", "tgs_project_backward", "tgs_project_backward_multi_workspace_size",
+            "tgs_project_backward_multi",
+            "tgs_render_batched_resident", "tgs_render_sampled_batched",
             "tgs_render_backward_batched", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step",
             "tgs_mlp_param_count", "tgs_mlp_forward", "tgs_mlp_backward_workspace_size", "tgs_mlp_backward",
             "tgs_mlp_adam"]
@@ -311,6 +318,35 @@ def project_backward(g: dict, cam, proj: dict, grad2d, grads: dict, touched, wri
     _check("tgs_project_backward", _lib.tgs_project_backward(
         C.byref(gs), C.byref(cc), C.byref(pr), _ptr(grad2d), C.byref(gp), _ptr(touched),
         1 if write_untouched else 0, 1 if accumulate else 0, _ptr(view_row), _stream(stream)))
+
+
+class MultiAdjoint:
+    """Marshalled arguments of project_backward_multi (the host pointer arrays
+    are built once; the device buffers they point to must stay alive)."""
+
+    def __init__(self, cams: list, radius: list, grad2d: list, view_rows: list | None = None):
+        K = len(cams)
+        self.K = K
+        self.cams = (Camera * K)(*[c if isinstance(c, Camera) else camera(c) for c in cams])
+        self.radius = (C.c_void_p * K)(*[_ptr(r) for r in radius])
+        self.grad2d = (C.c_void_p * K)(*[_ptr(g) for g in grad2d])
+        self.rows = None if view_rows is None else (C.c_void_p * K)(*[_ptr(r) for r in view_rows])
+
+
+def project_backward_multi_workspace_size(n: int) -> int:
+    return int(_lib.tgs_project_backward_multi_workspace_size(int(n)))
+
+
+def project_backward_multi(g: dict, adj: MultiAdjoint, grads: dict, touched, write_untouched=False, sh_degree=3,
+                           workspace=None, stream=None):
+    gs = gaussians(g, sh_degree)
+    gp = param_ptrs(grads)
+    if workspace is None:
+        workspace = torch.empty(project_backward_multi_workspace_size(gs.n), dtype=torch.uint8,
+                                device=g["means"].device)
+    _check("tgs_project_backward_multi", _lib.tgs_project_backward_multi(
+        C.byref(gs), adj.K, adj.cams, adj.radius, adj.grad2d, C.byref(gp), _ptr(touched),
+        1 if write_untouched else 0, adj.rows, _ptr(workspace), workspace.numel(), _stream(stream)))
 
 
 def view_batch(views: list) -> C.Array:

@@ -1,18 +1,23 @@
 // Tile binning: the per-tile Gaussian lists ordered by depth (Sec. 3.1, the
-// depth-ordered sets K(p)) as a sort of (tile | depth | id) keys, done as a
-// counting sort on the tile digit followed by a per-tile sort of
-// (depth | id) in shared memory:
-//   1. blocks of Gaussians count their pairs per active tile in shared memory
-//      (a tile x block table of counts),
+// depth-ordered sets K(p)) as a sort of (tile | depth | id) keys:
+//   0. the visible Gaussians are sorted by depth (stable LSD radix sort of the
+//      depth bits, ids ascending within equal depths);
+//   1. blocks take consecutive chunks of that order and count their pairs per
+//      active tile in shared memory (a tile x block table of counts),
 //   2. one scan of that table in tile-major order gives every (tile, block)
 //      its output offset, hence each tile's range,
 //   3. each block scatters (depth bits << 32 | id) into its offsets with
 //      shared-memory cursors (no contended global atomics),
-//   4. one block per tile sorts its range with an ascending-only bitonic
-//      network (virtual +inf padding, so any length works), in shared memory
-//      up to kSortSmem keys and in global memory beyond.
+//   4. because block b's chunk lies wholly before block b + 1's in (depth,
+//      id) order, a tile's range is a run of G segments that are already in
+//      order with respect to each other; only each (tile, block) segment needs
+//      sorting, which one warp does in registers (or shared memory for longer
+//      segments; a whole-block bitonic network for the rare long ones).
 // Positive float depths order like their bit patterns, so the result is the
-// order (tile, depth, Gaussian id).
+// order (tile, depth, Gaussian id).  With more active tiles than the shared
+// table holds, a global-atomic count/scatter and a per-tile sort of the whole
+// range take over.
+#include "radix.cuh"
 #include "scan.cuh"
 
 namespace tgs {
@@ -20,10 +25,13 @@ namespace tgs {
 constexpr int kSortThreads = 256;
 constexpr int kSortSmem = 4096;  // keys sorted in shared memory (32 KB)
 
-constexpr int kHistBlocks = 304;          // 2 per SM: blocks of the count/scatter passes
+constexpr int kHistBlocks = 1216;         // at most 8 chunks per SM in the count/scatter passes
+constexpr int kHistChunk = 2048;          // Gaussians per chunk below that
 constexpr int kHistMaxRanks = 49152;      // shared-memory table limit (192 KB)
 
-static int hist_blocks(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>(kHistBlocks, (n + 255) / 256)); }
+static int hist_blocks(int64_t n) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(kHistBlocks, (n + kHistChunk - 1) / kHistChunk));
+}
 
 struct BinWs {
   int32_t* tile_cnt;   // [R] pairs per rank (global-atomic path)
@@ -33,6 +41,10 @@ struct BinWs {
   uint64_t* keys;      // [C] (depth bits << 32 | id), grouped by tile
   int32_t* inv_rank;   // [R] tile id of each rank
   int64_t* scan_sums;
+  uint32_t* dk[2];     // [N] depth keys (radix sort buffers)
+  uint32_t* dv[2];     // [N] Gaussian ids
+  int32_t* n_vis;      // [1] visible Gaussians
+  RadixScratch rs;
 };
 
 static BinWs carve_bin(void* base, int64_t n, int64_t cap, int32_t n_ranks, size_t* total) {
@@ -40,6 +52,7 @@ static BinWs carve_bin(void* base, int64_t n, int64_t cap, int32_t n_ranks, size
   BinWs w;
   const size_t R = (size_t)std::max(n_ranks, 1), C = (size_t)std::max<int64_t>(cap, 1);
   const size_t RG = R * (size_t)hist_blocks(n);
+  const size_t N = (size_t)std::max<int64_t>(n, 1);
   w.tile_cnt = c.take<int32_t>(R);
   w.tile_fill = c.take<int32_t>(R);
   w.tile_start = c.take<int64_t>(R);
@@ -47,8 +60,32 @@ static BinWs carve_bin(void* base, int64_t n, int64_t cap, int32_t n_ranks, size
   w.keys = c.take<uint64_t>(C);
   w.inv_rank = c.take<int32_t>(R);
   w.scan_sums = c.take<int64_t>((size_t)std::max(1, scan_blocks((int64_t)std::max(RG, R))));
+  for (int b = 0; b < 2; ++b) {
+    w.dk[b] = c.take<uint32_t>(N);
+    w.dv[b] = c.take<uint32_t>(N);
+  }
+  w.n_vis = c.take<int32_t>(1);
+  w.rs.hist = c.take<uint32_t>(radix_hist_elems(n));
+  w.rs.bin_total = c.take<uint32_t>(RS_BINS);
   *total = c.size();
   return w;
+}
+
+// 0. depth keys of the visible Gaussians (invisible ones sort last) and the
+// visible count
+__global__ void __launch_bounds__(256) k_depth_keys(const int32_t* __restrict__ radius,
+                                                    const float* __restrict__ depth, int64_t n,
+                                                    uint32_t* __restrict__ keys, uint32_t* __restrict__ ids,
+                                                    int32_t* __restrict__ n_vis) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool vis = false;
+  if (i < n) {
+    vis = radius[i] > 0;
+    keys[i] = vis ? __float_as_uint(depth[i]) : 0xFFFFFFFFu;
+    ids[i] = (uint32_t)i;
+  }
+  const int c = __syncthreads_count(vis);
+  if (threadIdx.x == 0 && c) atomicAdd(n_vis, c);
 }
 
 struct BinGeom {
@@ -106,48 +143,57 @@ __global__ void __launch_bounds__(256) k_scatter_keys(const float2* __restrict__
 }
 
 // Calls f(gaussian id, rank) for every (Gaussian, active tile) pair of the
-// block's Gaussians [i0, i1).  Rectangles of up to kSmallRect tiles are walked
-// by their own lane; larger ones by the whole warp (each lane a stripe of the
-// rectangle), so a few huge splats do not serialise one thread.
-constexpr int kSmallRect = 32;
-
+// block's Gaussians at positions [i0, i1) (of `order`, or the ids themselves).
+// The pairs of a warp's 32 Gaussians are dealt out evenly: an inclusive warp
+// prefix of the rectangle areas numbers them, and in each round lane l takes
+// pair q = round * 32 + l, finding its Gaussian by binary search over the
+// prefix (so a few large splats do not leave the other lanes idle).
 template <typename F>
 __device__ __forceinline__ void for_each_pair(const float2* __restrict__ xy, const int32_t* __restrict__ radius,
                                               int64_t i0, int64_t i1, const BinGeom& geo,
-                                              const int32_t* __restrict__ tile_rank, F f) {
+                                              const int32_t* __restrict__ tile_rank, F f,
+                                              const uint32_t* __restrict__ order = nullptr) {
+  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t wave = blockDim.x;
   for (int64_t base = i0 + (threadIdx.x & ~31); base < i1; base += wave) {
-    const int64_t i = base + lane;
+    const int64_t pos = base + lane;
+    int id = 0;
     int x0 = 0, x1 = 0, y0 = 0, y1 = 0;
-    if (i < i1) {
-      const int r = radius[i];
+    if (pos < i1) {
+      id = order ? (int)order[pos] : (int)pos;
+      const int r = radius[id];
       if (r > 0) {
-        const float2 p = xy[i];
+        const float2 p = xy[id];
         tile_span(p.x, r, geo.tx, x0, x1);
         tile_span(p.y, r, geo.ty, y0, y1);
       }
     }
-    const int area = (x1 - x0) * (y1 - y0);
-    if (area <= kSmallRect) {
-      for (int ty = y0; ty < y1; ++ty)
-        for (int tx = x0; tx < x1; ++tx) {
-          const int k = rank_of(tile_rank, ty * geo.tx + tx, geo);
-          if (k >= 0) f(i, k);
-        }
+    const int w = x1 - x0;
+    const int area = w * (y1 - y0);
+    int incl = area;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(full, incl, o);
+      if (lane >= o) incl += y;
     }
-    unsigned big = __ballot_sync(0xffffffffu, area > kSmallRect);
-    while (big) {
-      const int src = __ffs(big) - 1;
-      big &= big - 1;
-      const int64_t gi = base + src;
-      const int bx0 = __shfl_sync(0xffffffffu, x0, src), bx1 = __shfl_sync(0xffffffffu, x1, src);
-      const int by0 = __shfl_sync(0xffffffffu, y0, src), by1 = __shfl_sync(0xffffffffu, y1, src);
-      const int w = bx1 - bx0, a = w * (by1 - by0);
-      for (int q = lane; q < a; q += 32) {
-        const int ty = by0 + q / w, tx = bx0 + q % w;
+    const int total = __shfl_sync(full, incl, 31);
+    for (int q0 = 0; q0 < total; q0 += 32) {
+      const int q = q0 + lane;
+      int lo = 0;  // first lane whose inclusive prefix exceeds q
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const int v = __shfl_sync(full, incl, lo + step - 1);
+        if (v <= q) lo += step;
+      }
+      const int o_incl = __shfl_sync(full, incl, lo), o_area = __shfl_sync(full, area, lo);
+      const int o_w = __shfl_sync(full, w, lo), o_x0 = __shfl_sync(full, x0, lo);
+      const int o_y0 = __shfl_sync(full, y0, lo), o_id = __shfl_sync(full, id, lo);
+      if (q < total) {
+        const int rem = q - (o_incl - o_area);
+        const int ty = o_y0 + rem / o_w, tx = o_x0 + rem % o_w;
         const int k = rank_of(tile_rank, ty * geo.tx + tx, geo);
-        if (k >= 0) f(gi, k);
+        if (k >= 0) f((int64_t)o_id, k);
       }
     }
   }
@@ -155,16 +201,29 @@ __device__ __forceinline__ void for_each_pair(const float2* __restrict__ xy, con
 
 // 1'. shared-memory path: block b counts the pairs of Gaussians
 // [b * chunk, (b + 1) * chunk) per rank; table[r * G + b] = count.
-__global__ void __launch_bounds__(256) k_hist_count(const float2* __restrict__ xy, const int32_t* __restrict__ radius,
-                                                    int64_t n, int64_t chunk, BinGeom geo,
-                                                    const int32_t* __restrict__ tile_rank,
-                                                    int64_t* __restrict__ table) {
+constexpr int kHistThreads = 512;
+
+// Block b's chunk of the depth order: [b * chunk, min(n_vis, (b + 1) * chunk)).
+__device__ __forceinline__ void vis_chunk(const int32_t* n_vis, int64_t& i0, int64_t& i1) {
+  const int64_t nv = *n_vis, G = gridDim.x;
+  const int64_t chunk = (nv + G - 1) / G;
+  i0 = (int64_t)blockIdx.x * chunk;
+  i1 = min(nv, i0 + chunk);
+}
+
+__global__ void __launch_bounds__(kHistThreads) k_hist_count(const float2* __restrict__ xy,
+                                                             const int32_t* __restrict__ radius,
+                                                             const uint32_t* __restrict__ order,
+                                                             const int32_t* __restrict__ n_vis, BinGeom geo,
+                                                             const int32_t* __restrict__ tile_rank,
+                                                             int64_t* __restrict__ table) {
   extern __shared__ uint32_t sh[];
   const int R = geo.n_ranks, G = gridDim.x, b = blockIdx.x;
   for (int r = threadIdx.x; r < R; r += blockDim.x) sh[r] = 0;
   __syncthreads();
-  const int64_t i0 = (int64_t)b * chunk, i1 = min(n, i0 + chunk);
-  for_each_pair(xy, radius, i0, i1, geo, tile_rank, [&](int64_t, int k) { atomicAdd(sh + k, 1u); });
+  int64_t i0, i1;
+  vis_chunk(n_vis, i0, i1);
+  for_each_pair(xy, radius, i0, i1, geo, tile_rank, [&](int64_t, int k) { atomicAdd(sh + k, 1u); }, order);
   __syncthreads();
   for (int r = threadIdx.x; r < R; r += blockDim.x) table[(size_t)r * G + b] = sh[r];
 }
@@ -172,20 +231,24 @@ __global__ void __launch_bounds__(256) k_hist_count(const float2* __restrict__ x
 // 3'. shared-memory path: scatter with shared cursors that start at the
 // block's offsets table[r * G + b] (clamped to the capacity; positions at or
 // past the capacity are dropped).
-__global__ void __launch_bounds__(256) k_hist_scatter(const float2* __restrict__ xy, const int32_t* __restrict__ radius,
-                                                      const float* __restrict__ depth, int64_t n, int64_t chunk,
-                                                      BinGeom geo, const int32_t* __restrict__ tile_rank,
-                                                      const int64_t* __restrict__ table, uint64_t* __restrict__ keys,
-                                                      int64_t cap) {
+__global__ void __launch_bounds__(kHistThreads) k_hist_scatter(const float2* __restrict__ xy,
+                                                               const int32_t* __restrict__ radius,
+                                                               const float* __restrict__ depth,
+                                                               const uint32_t* __restrict__ order,
+                                                               const int32_t* __restrict__ n_vis, BinGeom geo,
+                                                               const int32_t* __restrict__ tile_rank,
+                                                               const int64_t* __restrict__ table,
+                                                               uint64_t* __restrict__ keys, int64_t cap) {
   extern __shared__ uint32_t sh[];
   const int R = geo.n_ranks, G = gridDim.x, b = blockIdx.x;
   for (int r = threadIdx.x; r < R; r += blockDim.x) sh[r] = (uint32_t)min(table[(size_t)r * G + b], cap);
   __syncthreads();
-  const int64_t i0 = (int64_t)b * chunk, i1 = min(n, i0 + chunk);
+  int64_t i0, i1;
+  vis_chunk(n_vis, i0, i1);
   for_each_pair(xy, radius, i0, i1, geo, tile_rank, [&](int64_t i, int k) {
     const uint32_t pos = atomicAdd(sh + k, 1u);
     if ((int64_t)pos < cap) keys[pos] = ((uint64_t)__float_as_uint(depth[i]) << 32) | (uint64_t)(uint32_t)i;
-  });
+  }, order);
 }
 
 // Ascending-only bitonic network over n keys padded (virtually) with +inf to
@@ -272,6 +335,187 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(uint64_t* __restrict
   }
 }
 
+// 4'. one block per active rank: sort each (rank, block) segment.  Segments
+// of up to kLaneKeys keys are sorted by one lane each (a bitonic network in
+// registers), up to 32 by a warp in registers (a network across the lanes),
+// up to kSegWarpKeys by a warp in its slice of shared memory, longer ones by
+// the whole block afterwards.
+constexpr int kSegThreads = 256;
+constexpr int kSegWarps = kSegThreads / 32;
+constexpr int kSegWarpKeys = kSortSmem / kSegWarps;  // 512
+constexpr int kSegMaxBig = 64;
+constexpr int kLaneKeys = 8;
+
+__device__ __forceinline__ void emit_sorted(uint64_t k, int64_t pos, uint64_t tile_hi, int32_t* __restrict__ vals,
+                                            uint64_t* __restrict__ full_keys) {
+  vals[pos] = (int32_t)(uint32_t)k;
+  if (full_keys) full_keys[pos] = tile_hi | (k >> 32);
+}
+
+__device__ __forceinline__ void cx(uint64_t& a, uint64_t& b) {
+  const uint64_t lo = a < b ? a : b, hi = a < b ? b : a;
+  a = lo;
+  b = hi;
+}
+
+// One lane sorts len <= kLaneKeys keys at keys[ss...] (padding with +inf).
+__device__ __forceinline__ void lane_sort(const uint64_t* __restrict__ keys, int64_t ss, int len, uint64_t tile_hi,
+                                          int32_t* __restrict__ vals, uint64_t* __restrict__ full_keys) {
+  if (len == 1) {
+    emit_sorted(keys[ss], ss, tile_hi, vals, full_keys);
+    return;
+  }
+  uint64_t k[kLaneKeys];
+#pragma unroll
+  for (int i = 0; i < kLaneKeys; ++i) k[i] = i < len ? keys[ss + i] : ~0ull;
+  if (len <= 2) {
+    cx(k[0], k[1]);
+  } else if (len <= 4) {
+    cx(k[0], k[1]); cx(k[2], k[3]); cx(k[0], k[2]); cx(k[1], k[3]); cx(k[1], k[2]);
+  } else {
+    // bitonic network for 8
+#pragma unroll
+    for (int kk = 2; kk <= 8; kk <<= 1)
+#pragma unroll
+      for (int j = kk >> 1; j > 0; j >>= 1)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int l = i ^ j;
+          if (l > i) {
+            if ((i & kk) == 0) cx(k[i], k[l]);
+            else cx(k[l], k[i]);
+          }
+        }
+  }
+#pragma unroll
+  for (int i = 0; i < kLaneKeys; ++i)
+    if (i < len) emit_sorted(k[i], ss + i, tile_hi, vals, full_keys);
+}
+
+__device__ __forceinline__ uint64_t warp_sort32(uint64_t key, int lane) {
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const uint64_t other = __shfl_xor_sync(0xffffffffu, key, j);
+      const bool up = (lane & k) == 0 || k == 32;
+      const bool lower = (lane & j) == 0;
+      const uint64_t lo = other < key ? other : key, hi = other < key ? key : other;
+      key = (lower == up) ? lo : hi;
+    }
+  }
+  return key;
+}
+
+// Ascending-only bitonic network run by one warp over n keys in K (shared).
+__device__ void warp_bitonic(uint64_t* K, int n, int lane) {
+  int lg2 = 0;
+  while ((1 << lg2) < n) ++lg2;
+  const int n2 = 1 << lg2;
+  for (int lk = 1; lk <= lg2; ++lk) {
+    const int k = 1 << lk, lh = lk - 1, half = k >> 1;
+    for (int t = lane; t < n2 / 2; t += 32) {
+      const int blk = t >> lh, off = t & (half - 1);
+      cmp_swap(K, blk * k + off, blk * k + k - 1 - off, n);
+    }
+    __syncwarp();
+    for (int ld = lk - 2; ld >= 0; --ld) {
+      const int d = 1 << ld;
+      for (int t = lane; t < n2 / 2; t += 32) {
+        const int i = ((t >> ld) << (ld + 1)) + (t & (d - 1));
+        cmp_swap(K, i, i + d, n);
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__device__ __forceinline__ void seg_bounds(const int64_t* row, int b, int G, int64_t e0, int64_t cap, int64_t& ss,
+                                           int& len) {
+  ss = min(row[b], cap);
+  const int64_t ee = min(b + 1 < G ? row[b + 1] : e0, cap);
+  len = ee > ss ? (int)(ee - ss) : 0;
+}
+
+__global__ void __launch_bounds__(kSegThreads) k_seg_sort(uint64_t* __restrict__ keys, RangeSrc src,
+                                                          const int32_t* __restrict__ inv_rank, int64_t cap,
+                                                          int32_t* __restrict__ vals,
+                                                          uint64_t* __restrict__ full_keys,
+                                                          int2* __restrict__ ranges) {
+  __shared__ uint64_t sk[kSortSmem];
+  __shared__ int big[kSegMaxBig];
+  __shared__ int n_big;
+  const int r = blockIdx.x, G = src.G;
+  int64_t s0, e0;
+  src.get(r, s0, e0);
+  const int64_t s = min(s0, cap), e = min(e0, cap);
+  if (threadIdx.x == 0) {
+    ranges[r] = make_int2((int)s, (int)e);
+    n_big = 0;
+  }
+  __syncthreads();
+  if (e <= s) return;  // uniform across the block
+  const uint64_t tile_hi = full_keys ? ((uint64_t)(uint32_t)inv_rank[r] << 32) : 0;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t* row = src.table + (size_t)r * G;
+  uint64_t* wk = sk + w * kSegWarpKeys;
+  for (int b0 = w * 32; b0 < G; b0 += kSegWarps * 32) {
+    const int b = b0 + lane;
+    int64_t ss = 0;
+    int len = 0;
+    if (b < G) seg_bounds(row, b, G, e0, cap, ss, len);
+    if (len > 0 && len <= kLaneKeys) lane_sort(keys, ss, len, tile_hi, vals, full_keys);
+    unsigned longer = __ballot_sync(0xffffffffu, len > kLaneKeys);
+    while (longer) {
+      const int src_lane = __ffs(longer) - 1;
+      longer &= longer - 1;
+      const int64_t ls = __shfl_sync(0xffffffffu, ss, src_lane);
+      const int ll = __shfl_sync(0xffffffffu, len, src_lane);
+      if (ll <= 32) {
+        uint64_t k = lane < ll ? keys[ls + lane] : ~0ull;
+        k = warp_sort32(k, lane);
+        if (lane < ll) emit_sorted(k, ls + lane, tile_hi, vals, full_keys);
+      } else if (ll <= kSegWarpKeys) {
+        for (int i = lane; i < ll; i += 32) wk[i] = keys[ls + i];
+        __syncwarp();
+        warp_bitonic(wk, ll, lane);
+        for (int i = lane; i < ll; i += 32) emit_sorted(wk[i], ls + i, tile_hi, vals, full_keys);
+        __syncwarp();
+      } else if (lane == 0) {
+        const int q = atomicAdd(&n_big, 1);
+        if (q < kSegMaxBig) big[q] = b0 + src_lane;
+      }
+    }
+  }
+  __syncthreads();
+  const int nb = n_big;
+  if (nb > kSegMaxBig) {
+    // many long segments: sort the whole range at once (it holds them all)
+    const int n = (int)(e - s);
+    uint64_t* K = n <= kSortSmem ? sk : keys + s;
+    if (n <= kSortSmem) {
+      for (int i = threadIdx.x; i < n; i += blockDim.x) sk[i] = keys[s + i];
+      __syncthreads();
+    }
+    bitonic_sort(K, n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) emit_sorted(K[i], s + i, tile_hi, vals, full_keys);
+    return;
+  }
+  for (int q = 0; q < nb; ++q) {
+    int64_t ss;
+    int len;
+    seg_bounds(row, big[q], G, e0, cap, ss, len);
+    uint64_t* K = len <= kSortSmem ? sk : keys + ss;
+    if (len <= kSortSmem) {
+      for (int i = threadIdx.x; i < len; i += blockDim.x) sk[i] = keys[ss + i];
+      __syncthreads();
+    }
+    bitonic_sort(K, len);
+    for (int i = threadIdx.x; i < len; i += blockDim.x) emit_sorted(K[i], ss + i, tile_hi, vals, full_keys);
+    __syncthreads();
+  }
+}
+
 __global__ void k_inv_rank(const int32_t* __restrict__ tile_rank, int T, int32_t* __restrict__ inv, int n_max) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= T) return;
@@ -315,8 +559,8 @@ extern "C" tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const 
   RangeSrc src{};
   const bool shared_path = R <= kHistMaxRanks;
   const int G = hist_blocks(n);
-  const int64_t chunk = (n + G - 1) / G;
   const size_t smem = sizeof(int32_t) * (size_t)R;
+  const uint32_t* order = nullptr;
   if (shared_path) {
     if (smem > 48 * 1024) {  // opt in to more than 48 KB of dynamic shared memory (per device)
       static bool attr_set[64] = {};
@@ -329,7 +573,12 @@ extern "C" tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const 
         attr_set[dev] = true;
       }
     }
-    k_hist_count<<<G, 256, smem, s>>>(xy, proj->radius, n, chunk, geo, tile_rank, w.table);
+    cudaMemsetAsync(w.n_vis, 0, sizeof(int32_t), s);
+    k_depth_keys<<<(int)((n + 255) / 256), 256, 0, s>>>(proj->radius, proj->depth, n, w.dk[0], w.dv[0], w.n_vis);
+    const int cur = radix_sort_pairs(w.dk[0], w.dv[0], w.dk[1], w.dv[1], nullptr, (int32_t)n, 0, 32, w.rs,
+                                     nullptr, s);
+    order = w.dv[cur];
+    k_hist_count<<<G, kHistThreads, smem, s>>>(xy, proj->radius, order, w.n_vis, geo, tile_rank, w.table);
     int64_t* tab = w.table;
     auto load = [=] __device__(int64_t i) -> int64_t { return tab[i]; };
     auto store = [=] __device__(int64_t i, int64_t pre, int64_t) { tab[i] = pre; };
@@ -353,14 +602,18 @@ extern "C" tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const 
   }
   if (capacity == 0) return check_launch();
   if (shared_path) {
-    k_hist_scatter<<<G, 256, smem, s>>>(xy, proj->radius, proj->depth, n, chunk, geo, tile_rank, w.table, w.keys,
-                                        capacity);
+    k_hist_scatter<<<G, kHistThreads, smem, s>>>(xy, proj->radius, proj->depth, order, w.n_vis, geo, tile_rank,
+                                                 w.table, w.keys, capacity);
   } else {
     k_scatter_keys<<<(int)((n + 255) / 256), 256, 0, s>>>(xy, proj->radius, proj->depth, n, geo, tile_rank,
                                                           w.tile_start, w.tile_fill, w.keys, capacity);
   }
   if (keys) k_inv_rank<<<(T + 255) / 256, 256, 0, s>>>(tile_rank, T, w.inv_rank, R);
-  k_tile_sort<<<R, kSortThreads, 0, s>>>(w.keys, src, w.inv_rank, capacity, vals, keys,
+  if (shared_path)
+    k_seg_sort<<<R, kSegThreads, 0, s>>>(w.keys, src, w.inv_rank, capacity, vals, keys,
                                          reinterpret_cast<int2*>(tile_ranges));
+  else
+    k_tile_sort<<<R, kSortThreads, 0, s>>>(w.keys, src, w.inv_rank, capacity, vals, keys,
+                                           reinterpret_cast<int2*>(tile_ranges));
   return check_launch();
 }

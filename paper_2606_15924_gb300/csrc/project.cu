@@ -225,69 +225,70 @@ __global__ void __launch_bounds__(256) k_project(
   radius_out[i] = g.radius;
 }
 
+bool gaussians_ok(const tgs_gaussians* g);
+bool camera_ok(const tgs_camera* c);
+
 // Adjoint of the projection.  grad2d rows: (dx, dy, da, db | dc, do, dr, dg | db, -, -, -).
-__global__ void __launch_bounds__(256) k_project_bwd(
-    const float* __restrict__ means, const float* __restrict__ log_scales, const float4* __restrict__ quats,
-    const float* __restrict__ ologit, const float4* __restrict__ sh, int64_t n, int sh_degree, CamK cam,
-    const int32_t* __restrict__ radius, const float4* __restrict__ grad2d, float* __restrict__ g_means,
-    float* __restrict__ g_ls, float4* __restrict__ g_quats, float* __restrict__ g_ologit, float4* __restrict__ g_sh,
-    uint8_t* __restrict__ touched, int write_untouched, int accumulate, float* __restrict__ row) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga, gc = ga;
-  const bool vis = radius[i] > 0;
-  if (vis) {
-    ga = grad2d[3 * i];
-    gb = grad2d[3 * i + 1];
-    gc = grad2d[3 * i + 2];
-  }
-  const bool any = vis && (ga.x != 0.f || ga.y != 0.f || ga.z != 0.f || ga.w != 0.f || gb.x != 0.f ||
-                           gb.y != 0.f || gb.z != 0.f || gb.w != 0.f || gc.x != 0.f);
-  // accumulate: add into the gradients of Gaussians some earlier view of the
-  // same step already touched, overwrite the rest (touched is the flag)
-  const bool add = accumulate && touched[i] != 0;
-  if (touched) {
-    if (!accumulate) touched[i] = any ? 1 : 0;
-    else if (any) touched[i] = 1;
-  }
-  if (!any) {
-    if (row) {
-      float2* r2 = reinterpret_cast<float2*>(row + 14 * i);
+
+// SH-coefficient gradient accumulators of the multi-view adjoint: a
+// shared-memory column of the thread block (keeps the register count, hence
+// the occupancy, up).
+struct SmemSh {
+  float* base;  // element k at base[k * stride]
+  int stride;
+  __device__ __forceinline__ void zero() {
 #pragma unroll
-      for (int k = 0; k < 7; ++k) r2[k] = make_float2(0.f, 0.f);
-    }
-    if (write_untouched && !accumulate) {
-      g_means[3 * i] = 0.f; g_means[3 * i + 1] = 0.f; g_means[3 * i + 2] = 0.f;
-      g_ls[3 * i] = 0.f; g_ls[3 * i + 1] = 0.f; g_ls[3 * i + 2] = 0.f;
-      g_quats[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-      g_ologit[i] = 0.f;
-#pragma unroll
-      for (int k = 0; k < 12; ++k) g_sh[12 * i + k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    return;
+    for (int k = 0; k < 48; ++k) base[k * stride] = 0.f;
   }
-  float3 mu = make_float3(means[3 * i], means[3 * i + 1], means[3 * i + 2]);
-  float3 ls = make_float3(log_scales[3 * i], log_scales[3 * i + 1], log_scales[3 * i + 2]);
-  float4 qr = quats[i];
+  __device__ __forceinline__ void add(int k, float x) { base[k * stride] += x; }
+  __device__ __forceinline__ float get(int k) const { return base[k * stride]; }
+};
+
+// One view only: each float4 of the SH gradient is stored (or added to the
+// gradient array) as soon as it is complete, so nothing stays live.
+struct DirectSh {
+  float4* out;
+  bool accumulate;
+  float st[4];
+  __device__ __forceinline__ void zero() {}
+  __device__ __forceinline__ void add(int k, float x) {
+    st[k & 3] = x;
+    if ((k & 3) == 3) {
+      float4 v = make_float4(st[0], st[1], st[2], st[3]);
+      if (accumulate) {
+        const float4 q = out[k >> 2];
+        v = make_float4(q.x + v.x, q.y + v.y, q.z + v.z, q.w + v.w);
+      }
+      out[k >> 2] = v;
+    }
+  }
+};
+
+// Parameter-gradient accumulators of one Gaussian.
+template <class Sh>
+struct AdjAcc {
+  float mu[3], ls[3], q[4], o;
+  Sh sh;
+};
+
+__device__ __forceinline__ bool grad2d_nonzero(float4 ga, float4 gb, float4 gc) {
+  return ga.x != 0.f || ga.y != 0.f || ga.z != 0.f || ga.w != 0.f || gb.x != 0.f || gb.y != 0.f || gb.z != 0.f ||
+         gb.w != 0.f || gc.x != 0.f;
+}
+
+// Adds one view's adjoint of the projection of Gaussian (mu, ls, qr, opacity
+// o, SH block shp) into acc; rw (nullable) receives this view's own gradient
+// row (means, log-scales, quaternion, DC r g b, opacity logit).
+template <class Sh>
+__device__ __forceinline__ void view_adjoint(const CamK& cam, float3 mu, float3 ls, float4 qr, float o,
+                                             const float4* __restrict__ shp, int sh_degree, float4 ga, float4 gb,
+                                             float4 gc, float* __restrict__ rw, AdjAcc<Sh>& acc) {
   Geo g;
   geometry(cam, mu, ls, qr, g);  // visible by construction (radius > 0)
   const float d_x = ga.x, d_y = ga.y, d_a = ga.z, d_b = ga.w, d_c = gb.x, d_o = gb.y;
   const float drgb[3] = {gb.z, gb.w, gc.x};
-  // opacity
-  const float o = 1.f / (1.f + expf(-ologit[i]));
-  auto put = [&](float* p, float v) { *p = add ? *p + v : v; };
-  auto put4 = [&](float4* p, float4 v) {
-    if (add) {
-      const float4 q = *p;
-      v = make_float4(q.x + v.x, q.y + v.y, q.z + v.z, q.w + v.w);
-    }
-    *p = v;
-  };
-  // this view's own gradient row: geometry (means, log-scales, quaternion),
-  // then the SH DC colour and the opacity logit
-  float* rw = row ? row + 14 * i : nullptr;
   const float g_o = d_o * o * (1.f - o);
-  put(g_ologit + i, g_o);
+  acc.o += g_o;
   if (rw) rw[13] = g_o;
   // colour
   float vx = mu.x - cam.campos[0], vy = mu.y - cam.campos[1], vz = mu.z - cam.campos[2];
@@ -296,41 +297,46 @@ __global__ void __launch_bounds__(256) k_project_bwd(
   float Y[16];
   sh_basis(dx, dy, dz, sh_degree, Y);
   const int nb = (sh_degree + 1) * (sh_degree + 1);
-  const float4* shp = sh + 12 * i;
-  float shv[48];
-#pragma unroll
-  for (int k4 = 0; k4 < 12; ++k4) {
-    float4 v = (4 * k4 < 3 * nb) ? shp[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
-    shv[4 * k4] = v.x; shv[4 * k4 + 1] = v.y; shv[4 * k4 + 2] = v.z; shv[4 * k4 + 3] = v.w;
-  }
+  // the SH block is read twice (colour before the clamp, then the direction
+  // gradient) rather than held in registers; the second read hits L1.
+  // Coefficient j = 3 k + c belongs to basis function k, channel c; only
+  // j < 3 nb exist at this degree (the rest of the gradient is zero).
   float pre[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
-  for (int k = 0; k < 16; ++k)
-    if (k < nb) {
-      pre[0] += shv[3 * k] * Y[k];
-      pre[1] += shv[3 * k + 1] * Y[k];
-      pre[2] += shv[3 * k + 2] * Y[k];
+  for (int k4 = 0; k4 < 12; ++k4) {
+    if (4 * k4 >= 3 * nb) break;
+    const float4 v = shp[k4];
+    const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = 4 * k4 + u;
+      if (j < 3 * nb) pre[j % 3] += e[u] * Y[j / 3];
     }
+  }
   const float dc0 = pre[0] >= 0.f ? drgb[0] : 0.f;
   const float dc1 = pre[1] >= 0.f ? drgb[1] : 0.f;
   const float dc2 = pre[2] >= 0.f ? drgb[2] : 0.f;
+  const float dcv[3] = {dc0, dc1, dc2};
   float sk[16];
-  float gsh[48];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const bool on = k < nb;
-    gsh[3 * k] = on ? dc0 * Y[k] : 0.f;
-    gsh[3 * k + 1] = on ? dc1 * Y[k] : 0.f;
-    gsh[3 * k + 2] = on ? dc2 * Y[k] : 0.f;
-    sk[k] = on ? dc0 * shv[3 * k] + dc1 * shv[3 * k + 1] + dc2 * shv[3 * k + 2] : 0.f;
+  for (int k = 0; k < 16; ++k) sk[k] = 0.f;
+#pragma unroll
+  for (int k4 = 0; k4 < 12; ++k4) {
+    const bool any = 4 * k4 < 3 * nb;
+    const float4 v = any ? shp[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = 4 * k4 + u;
+      const bool on = j < 3 * nb;
+      if (on) sk[j / 3] += dcv[j % 3] * e[u];
+      acc.sh.add(j, on ? dcv[j % 3] * Y[j / 3] : 0.f);
+    }
   }
-#pragma unroll
-  for (int k4 = 0; k4 < 12; ++k4)
-    put4(g_sh + 12 * i + k4, make_float4(gsh[4 * k4], gsh[4 * k4 + 1], gsh[4 * k4 + 2], gsh[4 * k4 + 3]));
   if (rw) {
-    rw[10] = gsh[0];
-    rw[11] = gsh[1];
-    rw[12] = gsh[2];
+    rw[10] = dc0 * Y[0];
+    rw[11] = dc1 * Y[0];
+    rw[12] = dc2 * Y[0];
   }
   float gd[3];
   sh_basis_grad(dx, dy, dz, sh_degree, sk, gd);
@@ -397,14 +403,10 @@ __global__ void __launch_bounds__(256) k_project_bwd(
     dpc[2] += dJ12 * (cam.fy * lim * iz2);
   }
 #pragma unroll
-  for (int a = 0; a < 3; ++a) dmu[a] += Wm[a] * dpc[0] + Wm[3 + a] * dpc[1] + Wm[6 + a] * dpc[2];
-  put(g_means + 3 * i, dmu[0]);
-  put(g_means + 3 * i + 1, dmu[1]);
-  put(g_means + 3 * i + 2, dmu[2]);
-  if (rw) {
-    rw[0] = dmu[0];
-    rw[1] = dmu[1];
-    rw[2] = dmu[2];
+  for (int a = 0; a < 3; ++a) {
+    dmu[a] += Wm[a] * dpc[0] + Wm[3 + a] * dpc[1] + Wm[6 + a] * dpc[2];
+    acc.mu[a] += dmu[a];
+    if (rw) rw[a] = dmu[a];
   }
   // Sigma = M M^T, M = R diag(s): dM = 2 dSigma M
   const float* R = g.R;
@@ -421,8 +423,8 @@ __global__ void __launch_bounds__(256) k_project_bwd(
   float dR[9];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    float ds = R[c] * dM[c] + R[3 + c] * dM[3 + c] + R[6 + c] * dM[6 + c];
-    put(g_ls + 3 * i + c, ds * g.s[c]);
+    const float ds = R[c] * dM[c] + R[3 + c] * dM[3 + c] + R[6 + c] * dM[6 + c];
+    acc.ls[c] += ds * g.s[c];
     if (rw) rw[3 + c] = ds * g.s[c];
 #pragma unroll
     for (int r = 0; r < 3; ++r) dR[r * 3 + c] = dM[r * 3 + c] * g.s[c];
@@ -438,15 +440,110 @@ __global__ void __launch_bounds__(256) k_project_bwd(
                  x * dR[6] + y * dR[7]);
   const float qd = dq[0] * w + dq[1] * x + dq[2] * y + dq[3] * zq;
   const float iq = 1.f / g.qnorm;
-  const float4 gq = make_float4((dq[0] - w * qd) * iq, (dq[1] - x * qd) * iq, (dq[2] - y * qd) * iq,
-                                 (dq[3] - zq * qd) * iq);
-  put4(g_quats + i, gq);
-  if (rw) {
-    rw[6] = gq.x;
-    rw[7] = gq.y;
-    rw[8] = gq.z;
-    rw[9] = gq.w;
+  const float gq[4] = {(dq[0] - w * qd) * iq, (dq[1] - x * qd) * iq, (dq[2] - y * qd) * iq, (dq[3] - zq * qd) * iq};
+#pragma unroll
+  for (int a = 0; a < 4; ++a) {
+    acc.q[a] += gq[a];
+    if (rw) rw[6 + a] = gq[a];
   }
+}
+
+template <class Sh>
+__device__ __forceinline__ void acc_zero(AdjAcc<Sh>& a) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) a.mu[k] = a.ls[k] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a.q[k] = 0.f;
+  a.o = 0.f;
+  a.sh.zero();
+}
+
+template <class Sh, class Put4>
+__device__ __forceinline__ void store_sh(const Sh& sh, float4* out, Put4 put4) {
+#pragma unroll
+  for (int k4 = 0; k4 < 12; ++k4)
+    put4(out + k4, make_float4(sh.get(4 * k4), sh.get(4 * k4 + 1), sh.get(4 * k4 + 2), sh.get(4 * k4 + 3)));
+}
+template <class Put4>
+__device__ __forceinline__ void store_sh(const DirectSh&, float4*, Put4) {}  // stored as it was formed
+
+// Writes (add = false) or adds (add = true) acc into the gradient arrays.
+template <class Sh>
+__device__ __forceinline__ void acc_store(const AdjAcc<Sh>& a, int64_t i, bool add, float* __restrict__ g_means,
+                                          float* __restrict__ g_ls, float4* __restrict__ g_quats,
+                                          float* __restrict__ g_ologit, float4* __restrict__ g_sh) {
+  auto put = [&](float* p, float v) { *p = add ? *p + v : v; };
+  auto put4 = [&](float4* p, float4 v) {
+    if (add) {
+      const float4 q = *p;
+      v = make_float4(q.x + v.x, q.y + v.y, q.z + v.z, q.w + v.w);
+    }
+    *p = v;
+  };
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    put(g_means + 3 * i + k, a.mu[k]);
+    put(g_ls + 3 * i + k, a.ls[k]);
+  }
+  put4(g_quats + i, make_float4(a.q[0], a.q[1], a.q[2], a.q[3]));
+  put(g_ologit + i, a.o);
+  store_sh(a.sh, g_sh + 12 * i, put4);
+}
+
+__device__ __forceinline__ void zero_row(float* row, int64_t i) {
+  float2* r2 = reinterpret_cast<float2*>(row + 14 * i);
+#pragma unroll
+  for (int k = 0; k < 7; ++k) r2[k] = make_float2(0.f, 0.f);
+}
+
+__device__ __forceinline__ void zero_grads(int64_t i, float* __restrict__ g_means, float* __restrict__ g_ls,
+                                           float4* __restrict__ g_quats, float* __restrict__ g_ologit,
+                                           float4* __restrict__ g_sh) {
+  g_means[3 * i] = 0.f; g_means[3 * i + 1] = 0.f; g_means[3 * i + 2] = 0.f;
+  g_ls[3 * i] = 0.f; g_ls[3 * i + 1] = 0.f; g_ls[3 * i + 2] = 0.f;
+  g_quats[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  g_ologit[i] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 12; ++k) g_sh[12 * i + k] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(256) k_project_bwd(
+    const float* __restrict__ means, const float* __restrict__ log_scales, const float4* __restrict__ quats,
+    const float* __restrict__ ologit, const float4* __restrict__ sh, int64_t n, int sh_degree, CamK cam,
+    const int32_t* __restrict__ radius, const float4* __restrict__ grad2d, float* __restrict__ g_means,
+    float* __restrict__ g_ls, float4* __restrict__ g_quats, float* __restrict__ g_ologit, float4* __restrict__ g_sh,
+    uint8_t* __restrict__ touched, int write_untouched, int accumulate, float* __restrict__ row) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float4 ga = make_float4(0.f, 0.f, 0.f, 0.f), gb = ga, gc = ga;
+  const bool vis = radius[i] > 0;
+  if (vis) {
+    ga = grad2d[3 * i];
+    gb = grad2d[3 * i + 1];
+    gc = grad2d[3 * i + 2];
+  }
+  const bool any = vis && grad2d_nonzero(ga, gb, gc);
+  // accumulate: add into the gradients of Gaussians some earlier view of the
+  // same step already touched, overwrite the rest (touched is the flag)
+  const bool add = accumulate && touched[i] != 0;
+  if (touched) {
+    if (!accumulate) touched[i] = any ? 1 : 0;
+    else if (any) touched[i] = 1;
+  }
+  if (!any) {
+    if (row) zero_row(row, i);
+    if (write_untouched && !accumulate) zero_grads(i, g_means, g_ls, g_quats, g_ologit, g_sh);
+    return;
+  }
+  const float3 mu = make_float3(means[3 * i], means[3 * i + 1], means[3 * i + 2]);
+  const float3 ls = make_float3(log_scales[3 * i], log_scales[3 * i + 1], log_scales[3 * i + 2]);
+  const float o = 1.f / (1.f + expf(-ologit[i]));
+  AdjAcc<DirectSh> acc;
+  acc_zero(acc);
+  acc.sh.out = g_sh + 12 * i;
+  acc.sh.accumulate = add;
+  view_adjoint(cam, mu, ls, quats[i], o, sh + 12 * i, sh_degree, ga, gb, gc, row ? row + 14 * i : nullptr, acc);
+  acc_store(acc, i, add, g_means, g_ls, g_quats, g_ologit, g_sh);
 }
 
 void launch_project_bwd(const tgs_gaussians& g, const tgs_camera& cam, const int32_t* radius, const float* grad2d,
@@ -461,6 +558,147 @@ void launch_project_bwd(const tgs_gaussians& g, const tgs_camera& cam, const int
                                        reinterpret_cast<float4*>(grads.quats), grads.opacity_logits,
                                        reinterpret_cast<float4*>(grads.sh), touched, write_untouched, accumulate, row);
 }
+
+// Several views of one step in one pass: each Gaussian's parameters are read
+// once, the views that touched it add their adjoints in registers, and its
+// gradients are written once.
+constexpr int kMaxAdjViews = 16;
+struct MultiAdj {
+  int n_views;
+  CamK cam[kMaxAdjViews];
+  const int32_t* radius[kMaxAdjViews];
+  const float4* grad2d[kMaxAdjViews];
+  float* row[kMaxAdjViews];
+};
+
+// Pass 1 over every Gaussian: which views touched it (touched, zero rows of
+// the others, zero gradients if asked), and a compact list of the touched
+// ones with their view masks (order of the list is irrelevant: every entry is
+// computed on its own).
+__global__ void __launch_bounds__(256) k_adj_mark(int64_t n, MultiAdj mv, uint8_t* __restrict__ touched,
+                                                  int write_untouched, float* __restrict__ g_means,
+                                                  float* __restrict__ g_ls, float4* __restrict__ g_quats,
+                                                  float* __restrict__ g_ologit, float4* __restrict__ g_sh,
+                                                  uint2* __restrict__ list, int32_t* __restrict__ count) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = i < n;
+  unsigned hit = 0;
+  if (valid) {
+    for (int v = 0; v < mv.n_views; ++v) {
+      bool any = false;
+      if (mv.radius[v][i] > 0) {
+        const float4* gp = mv.grad2d[v] + 3 * i;
+        any = grad2d_nonzero(gp[0], gp[1], gp[2]);
+      }
+      if (any) hit |= 1u << v;
+      else if (mv.row[v]) zero_row(mv.row[v], i);
+    }
+    if (touched) touched[i] = hit ? 1 : 0;
+    if (!hit && write_untouched) zero_grads(i, g_means, g_ls, g_quats, g_ologit, g_sh);
+  }
+  const unsigned m = __ballot_sync(0xffffffffu, hit != 0);
+  if (!m) return;
+  const int lane = threadIdx.x & 31;
+  int base = 0;
+  if (lane == 0) base = atomicAdd(count, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  if (hit) list[base + __popc(m & ((1u << lane) - 1u))] = make_uint2((uint32_t)i, hit);
+}
+
+constexpr int kAdjThreads = 128;
+
+// Pass 2 over the touched Gaussians: the sum of their views' adjoints.
+__global__ void __launch_bounds__(kAdjThreads, 4) k_adj_multi(
+    const float* __restrict__ means, const float* __restrict__ log_scales, const float4* __restrict__ quats,
+    const float* __restrict__ ologit, const float4* __restrict__ sh, int sh_degree, MultiAdj mv,
+    const uint2* __restrict__ list, const int32_t* __restrict__ count, float* __restrict__ g_means,
+    float* __restrict__ g_ls, float4* __restrict__ g_quats, float* __restrict__ g_ologit,
+    float4* __restrict__ g_sh) {
+  __shared__ float s_sh[48 * kAdjThreads];
+  const int cnt = *count;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+    const uint2 it = list[e];
+    const int64_t i = it.x;
+    unsigned hit = it.y;
+    const float3 mu = make_float3(means[3 * i], means[3 * i + 1], means[3 * i + 2]);
+    const float3 ls = make_float3(log_scales[3 * i], log_scales[3 * i + 1], log_scales[3 * i + 2]);
+    const float4 qr = quats[i];
+    const float o = 1.f / (1.f + expf(-ologit[i]));
+    AdjAcc<SmemSh> acc;
+    acc.sh.base = s_sh + threadIdx.x;
+    acc.sh.stride = kAdjThreads;
+    acc_zero(acc);
+    while (hit) {
+      const int v = __ffs(hit) - 1;
+      hit &= hit - 1;
+      const float4* gp = mv.grad2d[v] + 3 * i;
+      view_adjoint(mv.cam[v], mu, ls, qr, o, sh + 12 * i, sh_degree, gp[0], gp[1], gp[2],
+                   mv.row[v] ? mv.row[v] + 14 * i : nullptr, acc);
+    }
+    acc_store(acc, i, false, g_means, g_ls, g_quats, g_ologit, g_sh);
+  }
+}
+
+}  // namespace tgs
+
+using namespace tgs;
+
+extern "C" size_t tgs_project_backward_multi_workspace_size(int64_t n) {
+  return 256 + sizeof(uint2) * (size_t)std::max<int64_t>(n, 1);
+}
+
+extern "C" tgs_status tgs_project_backward_multi(const tgs_gaussians* g, int32_t n_views, const tgs_camera* cams,
+                                                 const int32_t* const* radius, const float* const* grad2d,
+                                                 const tgs_param_ptrs* grads, uint8_t* touched,
+                                                 int32_t write_untouched, float* const* view_rows,
+                                                 void* workspace, size_t workspace_bytes, tgs_stream stream) {
+  if (!gaussians_ok(g) || n_views < 1 || n_views > kMaxAdjViews || !cams || !radius || !grad2d || !grads)
+    return TGS_ERR_INVALID_ARG;
+  if (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits || !grads->sh ||
+      !aligned16(grads->quats) || !aligned16(grads->sh))
+    return TGS_ERR_INVALID_ARG;
+  if (!workspace || !aligned16(workspace) || workspace_bytes < tgs_project_backward_multi_workspace_size(g->n))
+    return TGS_ERR_INVALID_ARG;
+  MultiAdj mv;
+  mv.n_views = n_views;
+  for (int v = 0; v < n_views; ++v) {
+    if (!camera_ok(cams + v) || !radius[v] || !grad2d[v] || !aligned16(grad2d[v])) return TGS_ERR_INVALID_ARG;
+    float* rw = view_rows ? view_rows[v] : nullptr;
+    if (rw && !aligned8(rw)) return TGS_ERR_INVALID_ARG;
+    mv.cam[v] = make_cam(cams[v]);
+    mv.radius[v] = radius[v];
+    mv.grad2d[v] = reinterpret_cast<const float4*>(grad2d[v]);
+    mv.row[v] = rw;
+  }
+  if (g->n == 0) return TGS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* count = reinterpret_cast<int32_t*>(workspace);
+  uint2* list = reinterpret_cast<uint2*>(reinterpret_cast<char*>(workspace) + 256);
+  cudaMemsetAsync(count, 0, sizeof(int32_t), s);
+  k_adj_mark<<<(int)((g->n + 255) / 256), 256, 0, s>>>(g->n, mv, touched, write_untouched, grads->means,
+                                                       grads->log_scales, reinterpret_cast<float4*>(grads->quats),
+                                                       grads->opacity_logits, reinterpret_cast<float4*>(grads->sh),
+                                                       list, count);
+  static int grid_dev[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return TGS_ERR_DEVICE;
+  if (!grid_dev[dev]) {
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_multi, kAdjThreads, 0);
+    grid_dev[dev] = std::max(1, sms * std::max(1, per_sm));
+  }
+  const int grid = (int)std::min<int64_t>(grid_dev[dev], (g->n + kAdjThreads - 1) / kAdjThreads);
+  k_adj_multi<<<grid, kAdjThreads, 0, s>>>(g->means, g->log_scales, reinterpret_cast<const float4*>(g->quats),
+                                           g->opacity_logits, reinterpret_cast<const float4*>(g->sh), g->sh_degree,
+                                           mv, list, count, grads->means, grads->log_scales,
+                                           reinterpret_cast<float4*>(grads->quats), grads->opacity_logits,
+                                           reinterpret_cast<float4*>(grads->sh));
+  return check_launch();
+}
+
+namespace tgs {
 
 bool gaussians_ok(const tgs_gaussians* g) {
   if (!g || g->n < 0 || g->sh_degree < 0 || g->sh_degree > 3) return false;

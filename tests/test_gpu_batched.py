@@ -204,3 +204,30 @@ def test_batched_rejects_bad_arguments(B):
         B.render_sampled_batched(mv.fwd_batch, 152, None)
     with pytest.raises(B.TgsError):
         B.render_backward_batched(mv.fwd_batch, 152, mv.counters[1:2])   # no dL / grad2d
+
+
+def test_fused_multiview_adjoint_equals_per_view_sum(B):
+    mv = _make(view_rows=True, mode=2)
+    mv.forward()
+    mv.loss_and_maps()
+    mv._render_bwd()
+    keys = ("means", "log_scales", "quats", "opacity_logits", "sh")
+    mv.persistent = True
+    for k in keys:
+        mv.grads[k].fill_(7.0)        # untouched entries are left alone
+    mv._project_bwd()
+    torch.cuda.synchronize()
+    fused = {k: mv.grads[k].clone() for k in keys}
+    fused_t = mv.touched.clone()
+    fused_rows = mv.rows.clone()
+    mv.persistent = False
+    mv.rows.fill_(3.0)
+    mv._project_bwd()
+    torch.cuda.synchronize()
+    assert torch.equal(fused_t, mv.touched)
+    t = fused_t.bool()
+    assert int(t.sum().item()) > 100
+    for k in keys:
+        assert _close(fused[k][t], mv.grads[k][t], rel=1e-5), k
+        assert torch.all(fused[k][~t] == 7.0), k
+    assert _close(fused_rows, mv.rows, rel=1e-6)

@@ -91,6 +91,38 @@ def test_bin_tiles_bit_exact(B, orc, n, W, H, frac):
             assert ranges[r][1] - ranges[r][0] == 0
 
 
+# Splats crowded into one tile, so that a tile's list is split into long
+# runs: (total, crowded) -> every path of the per-segment sort (registers,
+# warp shared memory, per-segment block sort, whole-range sort).
+CLUSTER_CASES = [(5000, 5000), (50000, 50000), (200000, 30000), (200000, 200000)]
+
+
+@pytest.mark.parametrize("n,n_crowd", CLUSTER_CASES)
+def test_bin_tiles_crowded_tile_bit_exact(B, orc, n, n_crowd):
+    from gpu_util import bin_dev, projected_dev
+    W, H = 256, 256
+    rng = np.random.default_rng(n + n_crowd)
+    pr = scenes.projected(n, W, H, seed=n)
+    xy = pr["xy"].copy()
+    xy[:n_crowd] = rng.uniform(100.0, 110.0, size=(n_crowd, 2))
+    pr["xy"] = xy.astype(np.float32)
+    radius = pr["radius"].copy()
+    radius[:n_crowd] = rng.integers(1, 6, n_crowd)
+    pr["radius"] = radius.astype(np.int32)
+    depth = pr["depth"].copy()
+    depth[:n_crowd] = rng.uniform(1.0, 1.01, n_crowd)     # the crowd lies in front
+    depth[:n_crowd:7] = depth[3]                         # with exact ties
+    pr["depth"] = depth.astype(np.float32)
+    keys_w, vals_w, counts_w = orc.bin_tiles(pr["xy"], pr["radius"], pr["depth"], W, H)
+    assert counts_w.max() > 4096 or n_crowd < 20000
+    cam = dict(viewmat=np.eye(4), fx=100.0, fy=100.0, cx=W / 2, cy=H / 2, width=W, height=H, znear=0.2)
+    out = bin_dev(B, projected_dev(pr), n, cam, None, 256, capacity=len(vals_w) + 7)
+    I = int(out["n_isect"].item())
+    assert I == len(vals_w)
+    np.testing.assert_array_equal(out["vals"][:I].cpu().numpy(), vals_w)
+    np.testing.assert_array_equal(out["keys"][:I].cpu().numpy().view(np.uint64), keys_w)
+
+
 def test_bin_tiles_edge_cases(B, orc):
     from gpu_util import bin_dev, projected_dev
     import torch
