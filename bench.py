@@ -507,6 +507,18 @@ def run_batched(args):
     print(json.dumps(res))
 
 
+def run_quality(args):
+    import torch
+    from paper_2606_15924_gb300 import binding as B
+    from paper_2606_15924_gb300.quality import compare
+    B.device_check()
+    device = torch.device("cuda", 0)
+    torch.cuda.set_device(device)
+    res = compare(device, n=N_GAUSS, width=WIDTH, height=HEIGHT, distance=DISTANCE, extent=EXTENT,
+                  dense_iters=args.dense_iters, tile_fraction=args.fraction, pixel_rate=args.rate)
+    print(json.dumps({"metric": "sampled vs dense training at equal PSNR (device time)", **res}))
+
+
 def run_reference(args):
     """The oracle as the reference arm: rank 0 only, bounded samples of the
     same workload on the host cores."""
@@ -545,6 +557,10 @@ def main():
     ap.add_argument("--rate", type=float, default=PIXEL_RATE)
     ap.add_argument("--no-dense", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--quality", action="store_true",
+                    help="only the equal-quality comparison: dense training for a fixed number of iterations, then "
+                         "sampled training until it is within 0.1 dB of the dense PSNR (device time)")
+    ap.add_argument("--dense-iters", type=int, default=2000)
     ap.add_argument("--workload", default="step", choices=["step", "batched"],
                     help="step: the one-view sparse training step (the headline line); batched: 8 views per "
                          "iteration in one persistent launch vs one launch per view")
@@ -556,6 +572,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.quality:
+        run_quality(args)
     elif args.workload == "batched":
         run_batched(args)
     else:

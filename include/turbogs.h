@@ -238,6 +238,28 @@ tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const tgs_camera*
                          int32_t* vals, uint64_t* keys, int32_t* tile_ranges, int64_t* n_isect, tgs_stream stream);
 
 /*
+ * Checkpoints of the sampled forward (not in the paper: they let the
+ * backward of Sec. 3.6 replay one tile's list in several independent pieces,
+ * so a sparse step has enough parallel work).  With B = the block size of the
+ * call (n_pix_max rounded up to a multiple of 32, at most 256), slot c of
+ * sampled pixel s holds float4 (T, C_r, C_g, C_b): the transmittance and
+ * accumulated colour in front of tile-list position (c + 1) B, at
+ * data[(c * stride + s) * 4].  data: device, 16-byte aligned,
+ * tgs_checkpoint_bytes(n_active_max, n_pix_max, n_slots) bytes;
+ * stride >= n_active_max * n_pix_max.  rgb: the forward's rgb output (the
+ * backward reads it).  Pass the same struct to render_sampled and
+ * backward_sampled with the same n_pix_max, or NULL to both.
+ */
+typedef struct {
+  float* data;
+  int32_t n_slots;
+  int64_t stride;
+  const float* rgb;
+} tgs_checkpoints;
+
+size_t tgs_checkpoint_bytes(int32_t n_active_max, int32_t n_pix_max, int32_t n_slots);
+
+/*
  * render_sampled - sparse forward rasterization (Sec. 3.6, Eq. 1; Alg. 1
  * step 5): for every sampled pixel of every active tile, front-to-back
  * compositing over the tile's list: alpha = min(0.99, o exp(power)),
@@ -256,7 +278,7 @@ tgs_status tgs_render_sampled(const tgs_projected* proj, const int32_t* tile_ran
                               const int32_t* active_tiles, const int32_t* n_active, int32_t n_active_max,
                               const int32_t* pix_off, const uint8_t* pix_idx, int32_t n_pix_max,
                               const tgs_camera* cam, const float* bg, float* rgb, float* T_final,
-                              int32_t* n_last, tgs_stream stream);
+                              int32_t* n_last, const tgs_checkpoints* ckpt, tgs_stream stream);
 
 /*
  * loss_sparse_ncc - fused sparse supervision (Sec. 3.7, Eq. 8; App. A;
@@ -290,7 +312,13 @@ tgs_status tgs_loss_sparse_ncc(const float* rgb, const float* target, int32_t wi
  * db(blue), 0, 0, 0).  Then the projection adjoint maps it to gradients of
  * the parameters (grads, layout of tgs_gaussians) and touched [N] = 1 where
  * grad2d is not all zero.  write_untouched = 0 leaves grads of untouched
- * Gaussians unwritten; 1 writes zeros there.
+ * Gaussians unwritten; 1 writes zeros there.  With checkpoints (ckpt, as
+ * given to render_sampled) each tile's list is replayed in independent pieces
+ * of one batch each, every piece starting from the forward's checkpoint at its
+ * back edge (S = (rgb - C) / T there), or from (T_final, bg) for the piece
+ * holding the pixel's last splat; the positions past the last slot form one
+ * more piece.  Same result up to rounding; more parallel work for sparse
+ * steps.
  */
 tgs_status tgs_backward_sampled(const tgs_gaussians* g, const tgs_camera* cam, const tgs_projected* proj,
                                 const int32_t* tile_ranges, const int32_t* vals, const int32_t* active_tiles,
@@ -298,7 +326,7 @@ tgs_status tgs_backward_sampled(const tgs_gaussians* g, const tgs_camera* cam, c
                                 const uint8_t* pix_idx, int32_t n_pix_max, const float* bg, const float* T_final,
                                 const int32_t* n_last, const float* dL_drgb, float* grad2d,
                                 const tgs_param_ptrs* grads, uint8_t* touched, int32_t write_untouched,
-                                tgs_stream stream);
+                                const tgs_checkpoints* ckpt, tgs_stream stream);
 
 /*
  * project_backward - the projection adjoint alone (the second half of

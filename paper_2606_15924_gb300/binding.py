@@ -80,6 +80,10 @@ class ViewBatch(C.Structure):
                 ("dL_drgb", C.c_void_p), ("grad2d", C.c_void_p), ("n_gaussians", C.c_int64)]
 
 
+class Checkpoints(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("n_slots", C.c_int32), ("stride", C.c_int64), ("rgb", C.c_void_p)]
+
+
 class Opt(C.Structure):
     _fields_ = [("lr", C.c_float * 6), ("beta1", C.c_float), ("beta2", C.c_float), ("eps_adam", C.c_float),
                 ("eps_lm", C.c_float), ("mode", C.c_int32)]
@@ -115,14 +119,16 @@ _lib.tgs_bin_tiles_workspace_size.argtypes = [_i64, _i64, _i32]
 _lib.tgs_bin_tiles.restype = _i32
 _lib.tgs_bin_tiles.argtypes = [_P(Projected), _i64, _P(Camera), _p, _i32, _p, _sz, _i64, _p, _p, _p, _p, _p]
 _lib.tgs_render_sampled.restype = _i32
+_lib.tgs_checkpoint_bytes.restype = _sz
+_lib.tgs_checkpoint_bytes.argtypes = [_i32, _i32, _i32]
 _lib.tgs_render_sampled.argtypes = [_P(Projected), _p, _p, _p, _p, _i32, _p, _p, _i32, _P(Camera), _p, _p, _p,
-                                    _p, _p]
+                                    _p, _P(Checkpoints), _p]
 _lib.tgs_loss_sparse_ncc.restype = _i32
 _lib.tgs_loss_sparse_ncc.argtypes = [_p, _p, _i32, _i32, _p, _p, _i32, _p, _p, _i32, _P(LossParams), _p, _p, _p,
                                      _p, _p, _p, _p]
 _lib.tgs_backward_sampled.restype = _i32
 _lib.tgs_backward_sampled.argtypes = [_P(Gaussians), _P(Camera), _P(Projected), _p, _p, _p, _p, _i32, _p, _p,
-                                      _i32, _p, _p, _p, _p, _p, _P(ParamPtrs), _p, _i32, _p]
+                                      _i32, _p, _p, _p, _p, _p, _P(ParamPtrs), _p, _i32, _P(Checkpoints), _p]
 _lib.tgs_project_backward.restype = _i32
 _lib.tgs_project_backward.argtypes = [_P(Gaussians), _P(Camera), _P(Projected), _p, _P(ParamPtrs), _p, _i32, _i32,
                                       _p, _p]
@@ -156,7 +162,8 @@ _lib.tgs_mlp_adam.argtypes = [_p, _p, _p, _p, _i32, C.c_float, C.c_float, C.c_fl
 EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_device_check", "tgs_graph_count_kernels",
             "tgs_select_tiles_workspace_size", "tgs_select_tiles", "tgs_select_tiles_noalloc",
             "tgs_project_gaussians",
-            "tgs_bin_tiles_workspace_size", "tgs_bin_tiles", "tgs_render_sampled", "tgs_loss_sparse_ncc",
+            "tgs_bin_tiles_workspace_size", "tgs_bin_tiles", "tgs_checkpoint_bytes", "tgs_render_sampled",
+            "tgs_loss_sparse_ncc",
             "tgs_backward_sampled", "tgs_project_backward", "tgs_project_backward_multi_workspace_size",
             "tgs_project_backward_multi",
             "tgs_render_batched_resident", "tgs_render_sampled_batched",
@@ -272,15 +279,29 @@ def bin_tiles(proj: dict, n, cam, tile_rank, n_active_max, workspace, capacity, 
         int(capacity), _ptr(vals), _ptr(keys), _ptr(tile_ranges), _ptr(n_isect), _stream(stream)))
 
 
+def checkpoint_bytes(n_active_max: int, n_pix_max: int, n_slots: int) -> int:
+    return int(_lib.tgs_checkpoint_bytes(int(n_active_max), int(n_pix_max), int(n_slots)))
+
+
+def checkpoints(data, n_slots: int, stride: int, rgb) -> Checkpoints:
+    """data: float32 device tensor of checkpoint_bytes(...) / 4 elements; rgb:
+    the forward's rgb output tensor."""
+    return Checkpoints(_ptr(data), int(n_slots), int(stride), _ptr(rgb))
+
+
+def _ck(ckpt):
+    return C.byref(ckpt) if ckpt is not None else None
+
+
 def render_sampled(proj: dict, tile_ranges, vals, active_tiles, n_active, n_active_max, pix_off, pix_idx,
-                   n_pix_max, cam, bg, rgb, T_final, n_last, stream=None):
+                   n_pix_max, cam, bg, rgb, T_final, n_last, stream=None, ckpt=None):
     pr = projected(proj)
     cc = cam if isinstance(cam, Camera) else camera(cam)
     bgv = (C.c_float * 3)(*[float(b) for b in bg])
     _check("tgs_render_sampled", _lib.tgs_render_sampled(
         C.byref(pr), _ptr(tile_ranges), _ptr(vals), _ptr(active_tiles), _ptr(n_active), int(n_active_max),
         _ptr(pix_off), _ptr(pix_idx), int(n_pix_max), C.byref(cc), bgv, _ptr(rgb), _ptr(T_final), _ptr(n_last),
-        _stream(stream)))
+        _ck(ckpt), _stream(stream)))
 
 
 def loss_sparse_ncc(rgb, target, width, height, active_tiles, n_active, n_active_max, pix_off, pix_idx, n_pix_max,
@@ -297,7 +318,7 @@ def loss_sparse_ncc(rgb, target, width, height, active_tiles, n_active, n_active
 
 def backward_sampled(g: dict, cam, proj: dict, tile_ranges, vals, active_tiles, n_active, n_active_max, pix_off,
                      pix_idx, n_pix_max, bg, T_final, n_last, dL_drgb, grad2d, grads: dict, touched,
-                     write_untouched=True, sh_degree=3, stream=None):
+                     write_untouched=True, sh_degree=3, stream=None, ckpt=None):
     gs = gaussians(g, sh_degree)
     cc = cam if isinstance(cam, Camera) else camera(cam)
     pr = projected(proj)
@@ -306,7 +327,8 @@ def backward_sampled(g: dict, cam, proj: dict, tile_ranges, vals, active_tiles, 
     _check("tgs_backward_sampled", _lib.tgs_backward_sampled(
         C.byref(gs), C.byref(cc), C.byref(pr), _ptr(tile_ranges), _ptr(vals), _ptr(active_tiles), _ptr(n_active),
         int(n_active_max), _ptr(pix_off), _ptr(pix_idx), int(n_pix_max), bgv, _ptr(T_final), _ptr(n_last),
-        _ptr(dL_drgb), _ptr(grad2d), C.byref(gp), _ptr(touched), 1 if write_untouched else 0, _stream(stream)))
+        _ptr(dL_drgb), _ptr(grad2d), C.byref(gp), _ptr(touched), 1 if write_untouched else 0, _ck(ckpt),
+        _stream(stream)))
 
 
 def project_backward(g: dict, cam, proj: dict, grad2d, grads: dict, touched, write_untouched=True,

@@ -72,8 +72,19 @@ __device__ __forceinline__ void load_splat(const RasterArgs& a, int k, Splat& sp
 
 // Forward of active tile j (one thread per sampled pixel; sm holds
 // blockDim.x splats).
+// Checkpoints of the sampled forward for the split backward: slot c (c = 0
+// .. n_slots - 1) of pixel s holds (T, C_r, C_g, C_b) in front of tile-list
+// position (c + 1) * B (B = the block size, one batch), at data[c * stride + s].
+struct Ckpt {
+  float4* data;
+  int n_slots;
+  int64_t stride;
+  const float* rgb;  // the forward's output (read by the backward)
+};
+
 __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Splat* sm, float* __restrict__ out_rgb,
-                                                float* __restrict__ out_T, int32_t* __restrict__ out_last) {
+                                                float* __restrict__ out_T, int32_t* __restrict__ out_last,
+                                                Ckpt ck = Ckpt{nullptr, 0, 0, nullptr}) {
   const int t = a.active_tiles ? a.active_tiles[j] : j;
   const int p0 = a.pix_off[j], p1 = a.pix_off[j + 1];
   const bool has_pix = p0 + (int)threadIdx.x < p1;
@@ -94,6 +105,10 @@ __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Spla
   if (range.x + (int)threadIdx.x < range.y) load_splat(a, range.x + threadIdx.x, nxt);
   for (int base = range.x; base < range.y; base += B) {
     if (__syncthreads_count(done) == B) break;
+    if (ck.data && has_pix) {
+      const int c = (base - range.x) / B - 1;  // state in front of this batch
+      if (c >= 0 && c < ck.n_slots) ck.data[c * ck.stride + s] = make_float4(T, C0, C1, C2);
+    }
     if (base + (int)threadIdx.x < range.y) sm[threadIdx.x] = nxt;
     __syncthreads();
     if (base + B + (int)threadIdx.x < range.y) load_splat(a, base + B + threadIdx.x, nxt);
@@ -127,11 +142,11 @@ __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Spla
 }
 
 __global__ void k_render_fwd(RasterArgs a, float* __restrict__ out_rgb, float* __restrict__ out_T,
-                             int32_t* __restrict__ out_last) {
+                             int32_t* __restrict__ out_last, Ckpt ck) {
   extern __shared__ Splat sm[];
   const int j = blockIdx.x;
   if (j >= *a.n_active) return;
-  render_tile_fwd(a, j, sm, out_rgb, out_T, out_last);
+  render_tile_fwd(a, j, sm, out_rgb, out_T, out_last, ck);
 }
 
 // Sum of v[0..7] over the warp, scattered: lane l ends with the total of
@@ -281,6 +296,134 @@ __global__ void k_render_bwd(RasterArgs a, const float* __restrict__ T_final, co
   render_tile_bwd(a, j, sm, T_final, n_last, dL_drgb, grad2d);
 }
 
+// Split backward: block (j, c) replays batch c of tile j (list positions
+// [c B, (c + 1) B)), or, for c = n_slots, every position from n_slots B to the
+// end.  A pixel whose last blended splat lies in the block's range starts from
+// (T_final, bg); one whose walk goes on past it starts from the forward's
+// checkpoint at the range's back edge, with the light from behind recovered
+// as S = (out - C) / T (out = T-weighted colours + T_final bg).  Per-splat
+// adjoints are reduced as in the whole-tile kernel.
+__global__ void k_render_bwd_split(RasterArgs a, const float* __restrict__ T_final,
+                                   const int32_t* __restrict__ n_last, const float* __restrict__ dL_drgb,
+                                   float* __restrict__ grad2d, Ckpt ck) {
+  extern __shared__ Splat sm[];
+  __shared__ int s_max_last;
+  const int j = blockIdx.x, c = blockIdx.y;
+  if (j >= *a.n_active) return;
+  float* acc = reinterpret_cast<float*>(sm + blockDim.x);
+  const int B = blockDim.x;
+  const int t = a.active_tiles ? a.active_tiles[j] : j;
+  const int p0 = a.pix_off[j], p1 = a.pix_off[j + 1];
+  const bool has_pix = p0 + (int)threadIdx.x < p1;
+  const int s = p0 + threadIdx.x;
+  int last = has_pix ? n_last[s] : 0;
+  if (threadIdx.x == 0) s_max_last = 0;
+  __syncthreads();
+  if (last > 0) atomicMax(&s_max_last, last);
+  __syncthreads();
+  const int lo_pos = c * B;                                        // first list position of the range
+  const int hi_pos = c < ck.n_slots ? min(lo_pos + B, s_max_last) : s_max_last;
+  if (hi_pos <= lo_pos) return;                                    // uniform: nothing blended here
+  const int2 range = a.ranges[j];
+  float px = 0.f, py = 0.f, T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+  float S0 = a.bg[0], S1 = a.bg[1], S2 = a.bg[2];
+  if (last <= lo_pos) last = 0;  // this pixel blended nothing in the range
+  if (last > 0) {
+    const int l = a.pix_idx[s];
+    px = (float)((t % a.tiles_x) * TGS_TILE + (l & 15)) + 0.5f;
+    py = (float)((t / a.tiles_x) * TGS_TILE + (l >> 4)) + 0.5f;
+    g0 = dL_drgb[3 * s];
+    g1 = dL_drgb[3 * s + 1];
+    g2 = dL_drgb[3 * s + 2];
+    if (c < ck.n_slots && last > lo_pos + B) {
+      const float4 q = ck.data[c * ck.stride + s];  // in front of position (c + 1) B
+      T = q.x;
+      const float iT = 1.f / q.x;
+      S0 = (ck.rgb[3 * s] - q.y) * iT;
+      S1 = (ck.rgb[3 * s + 1] - q.z) * iT;
+      S2 = (ck.rgb[3 * s + 2] - q.w) * iT;
+      last = lo_pos + B;
+    } else {
+      T = T_final[s];
+    }
+  }
+  const int lane = threadIdx.x & 31;
+  int warp_last = last;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) warp_last = max(warp_last, __shfl_xor_sync(0xffffffffu, warp_last, o));
+  const int first = range.x + lo_pos, end = range.x + hi_pos;
+  Splat nxt;
+  {
+    const int k = end - B + (int)threadIdx.x;
+    if (k >= first) load_splat(a, k, nxt);
+  }
+  for (int top = end; top > first; top -= B) {
+    const int lo = max(first, top - B);
+    const int cnt = top - lo;
+    __syncthreads();
+    {
+      const int k = top - B + (int)threadIdx.x;
+      if (k >= lo) sm[threadIdx.x - (B - cnt)] = nxt;
+#pragma unroll
+      for (int q = 0; q < 9; ++q) acc[9 * threadIdx.x + q] = 0.f;
+    }
+    __syncthreads();
+    {
+      const int k = top - 2 * B + (int)threadIdx.x;
+      if (k >= first) load_splat(a, k, nxt);
+    }
+    const int qmax = min(cnt - 1, range.x + warp_last - 1 - lo);
+    for (int q = qmax; q >= 0; --q) {
+      const Splat sp = sm[q];
+      const int pos = lo + q - range.x;
+      float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      bool hit = false;
+      if (pos < last) {
+        const float dx = __fsub_rn(px, sp.xy.x), dy = __fsub_rn(py, sp.xy.y);
+        float alpha, G;
+        if (splat_alpha(sp.co, dx, dy, alpha, G)) {
+          hit = true;
+          T = T / (1.f - alpha);
+          const float wgt = alpha * T;
+          v[6] = wgt * g0;
+          v[7] = wgt * g1;
+          v[8] = wgt * g2;
+          const float dalpha = T * ((sp.rgb.x - S0) * g0 + (sp.rgb.y - S1) * g1 + (sp.rgb.z - S2) * g2);
+          S0 = alpha * sp.rgb.x + (1.f - alpha) * S0;
+          S1 = alpha * sp.rgb.y + (1.f - alpha) * S1;
+          S2 = alpha * sp.rgb.z + (1.f - alpha) * S2;
+          if (__fmul_rn(sp.co.w, G) < kAlphaMax) {
+            v[5] = dalpha * G;
+            const float dpow = dalpha * alpha;
+            v[0] = dpow * (sp.co.x * dx + sp.co.y * dy);
+            v[1] = dpow * (sp.co.z * dy + sp.co.y * dx);
+            v[2] = -0.5f * dpow * dx * dx;
+            v[3] = -dpow * dx * dy;
+            v[4] = -0.5f * dpow * dy * dy;
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, hit)) {
+        const float r8 = warp_reduce_scatter8(v, lane);
+        const float r9 = warp_sum(v[8]);
+        if ((lane & 3) == 0) atomicAdd(acc + 9 * q + ((lane >> 2) & 7), r8);
+        else if (lane == 1) atomicAdd(acc + 9 * q + 8, r9);
+      }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < cnt) {
+      const float* r = acc + 9 * threadIdx.x;
+      if (r[0] != 0.f || r[1] != 0.f || r[2] != 0.f || r[3] != 0.f || r[4] != 0.f || r[5] != 0.f ||
+          r[6] != 0.f || r[7] != 0.f || r[8] != 0.f) {
+        float* gp = grad2d + 12 * (size_t)__float_as_int(sm[threadIdx.x].rgb.w);
+        red_add_v4(gp, r[0], r[1], r[2], r[3]);
+        red_add_v4(gp + 4, r[4], r[5], r[6], r[7]);
+        atomicAdd(gp + 8, r[8]);
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Several views in one persistent launch: CTAs take (view, tile) items from
 // an atomic counter (items of view v are [base[v], base[v+1])) until none
@@ -358,19 +501,38 @@ static int block_for(int n_pix_max) { return std::min(256, std::max(32, (n_pix_m
 
 using namespace tgs;
 
+// Checkpoint buffer checks: stride covers every sampled pixel slot.
+static bool ckpt_of(const tgs_checkpoints* c, int32_t n_active_max, int32_t n_pix_max, const float* rgb, Ckpt& k) {
+  k = Ckpt{nullptr, 0, 0, nullptr};
+  if (!c || c->n_slots <= 0) return true;
+  if (!c->data || !aligned16(c->data) || c->stride < (int64_t)n_active_max * n_pix_max) return false;
+  k.data = reinterpret_cast<float4*>(c->data);
+  k.n_slots = c->n_slots;
+  k.stride = c->stride;
+  k.rgb = rgb;
+  return true;
+}
+
+extern "C" size_t tgs_checkpoint_bytes(int32_t n_active_max, int32_t n_pix_max, int32_t n_slots) {
+  if (n_active_max <= 0 || n_pix_max <= 0 || n_slots <= 0) return 0;
+  return sizeof(float4) * (size_t)n_slots * (size_t)n_active_max * (size_t)n_pix_max;
+}
+
 extern "C" tgs_status tgs_render_sampled(const tgs_projected* proj, const int32_t* tile_ranges, const int32_t* vals,
                                          const int32_t* active_tiles, const int32_t* n_active, int32_t n_active_max,
                                          const int32_t* pix_off, const uint8_t* pix_idx, int32_t n_pix_max,
                                          const tgs_camera* cam, const float* bg, float* rgb, float* T_final,
-                                         int32_t* n_last, tgs_stream stream) {
+                                         int32_t* n_last, const tgs_checkpoints* ckpt, tgs_stream stream) {
   RasterArgs a;
   if (n_active_max < 0 || n_pix_max < 1 || n_pix_max > 256) return TGS_ERR_INVALID_ARG;
   if (!raster_args(proj, tile_ranges, vals, active_tiles, n_active, pix_off, pix_idx, cam, bg, a))
     return TGS_ERR_INVALID_ARG;
   if (!rgb || !T_final || !n_last) return TGS_ERR_INVALID_ARG;
+  Ckpt ck;
+  if (!ckpt_of(ckpt, n_active_max, n_pix_max, rgb, ck)) return TGS_ERR_INVALID_ARG;
   if (n_active_max == 0) return TGS_OK;
   const int B = block_for(n_pix_max);
-  k_render_fwd<<<n_active_max, B, B * sizeof(Splat), (cudaStream_t)stream>>>(a, rgb, T_final, n_last);
+  k_render_fwd<<<n_active_max, B, B * sizeof(Splat), (cudaStream_t)stream>>>(a, rgb, T_final, n_last, ck);
   return check_launch();
 }
 
@@ -381,7 +543,7 @@ extern "C" tgs_status tgs_backward_sampled(const tgs_gaussians* g, const tgs_cam
                                            int32_t n_pix_max, const float* bg, const float* T_final,
                                            const int32_t* n_last, const float* dL_drgb, float* grad2d,
                                            const tgs_param_ptrs* grads, uint8_t* touched, int32_t write_untouched,
-                                           tgs_stream stream) {
+                                           const tgs_checkpoints* ckpt, tgs_stream stream) {
   RasterArgs a;
   if (!gaussians_ok(g) || n_active_max < 0 || n_pix_max < 1 || n_pix_max > 256) return TGS_ERR_INVALID_ARG;
   if (!raster_args(proj, tile_ranges, vals, active_tiles, n_active, pix_off, pix_idx, cam, bg, a))
@@ -390,13 +552,20 @@ extern "C" tgs_status tgs_backward_sampled(const tgs_gaussians* g, const tgs_cam
   if (g->n > 0 && (!grad2d || !aligned16(grad2d) || !grads->means || !grads->log_scales || !grads->quats ||
                    !grads->opacity_logits || !grads->sh || !aligned16(grads->quats) || !aligned16(grads->sh)))
     return TGS_ERR_INVALID_ARG;
+  Ckpt ck;
+  if (!ckpt_of(ckpt, n_active_max, n_pix_max, ckpt ? ckpt->rgb : nullptr, ck)) return TGS_ERR_INVALID_ARG;
+  if (ck.data && !ck.rgb) return TGS_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   if (g->n == 0) return TGS_OK;
   cudaMemsetAsync(grad2d, 0, sizeof(float) * 12 * (size_t)g->n, s);
   if (n_active_max > 0) {
     const int B = block_for(n_pix_max);
-    k_render_bwd<<<n_active_max, B, B * (sizeof(Splat) + 9 * sizeof(float)), s>>>(a, T_final, n_last, dL_drgb,
-                                                                                 grad2d);
+    const size_t smem = B * (sizeof(Splat) + 9 * sizeof(float));
+    if (ck.data)
+      k_render_bwd_split<<<dim3(n_active_max, ck.n_slots + 1), B, smem, s>>>(a, T_final, n_last, dL_drgb, grad2d,
+                                                                             ck);
+    else
+      k_render_bwd<<<n_active_max, B, smem, s>>>(a, T_final, n_last, dL_drgb, grad2d);
   }
   launch_project_bwd(*g, *cam, proj->radius, grad2d, *grads, touched, write_untouched, 0, nullptr, s);
   return check_launch();

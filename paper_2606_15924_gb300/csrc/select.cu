@@ -147,28 +147,226 @@ __global__ void __launch_bounds__(256) k_rank_tiles(SelWs w, int T, int phase, i
   if (cnt) atomicAdd(phase == 0 ? &w.rank_h[i] : phase == 1 ? &w.rank_s[i] : &w.rank_u[i], cnt);
 }
 
-// Whether (key, index l) is among the k smallest eligible (key, index) pairs
-// of the block, keys < 2^nbits: a bitwise binary search for the k-th smallest
-// key with block-wide counts, then ties at that key taken in index order.
-// Every thread of the block must call it (it synchronises).
-__device__ __forceinline__ bool block_take_k(uint64_t key, bool elig, int k, int nbits, int l,
-                                             uint32_t* s_cnt) {
-  if (k <= 0) return false;
-  uint64_t prefix = 0;
-  for (int bit = nbits - 1; bit >= 0; --bit) {
-    const uint64_t probe = prefix | ((1ull << bit) - 1ull);
-    if (__syncthreads_count(elig && key <= probe) < k) prefix |= 1ull << bit;
+// Exact block-wide k-selection by radix select: the k smallest (key, index)
+// pairs among the eligible items of the block, keys < 2^nbits, items held
+// ITEMS per thread in index order (thread t holds t * ITEMS + j).  The k-th
+// smallest key K is found one 8-bit digit at a time from the top (a shared
+// histogram of the keys that match the digits found so far, and one warp
+// locating the digit where the running count reaches k); every key below K is
+// taken, and the ties at K in index order until k are reached.  Every thread
+// of the block must call it (it synchronises); k is the same on all threads.
+struct RadixSelSmem {
+  uint32_t hist[256];
+  uint32_t dmin[2], dmax[2];  // by pass parity: a pass never overwrites what the previous one still reads
+  int32_t warp_sum[32];
+  int32_t total;
+  int32_t digit;
+  int32_t below;
+};
+
+// Exclusive prefix over threads of v (thread order); *total receives the sum.
+__device__ __forceinline__ int64_t block_excl_sum(int64_t v, RadixSelSmem& sm, int64_t* s64, int64_t& total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  int64_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
   }
-  const int lt = __syncthreads_count(elig && key < prefix);
-  const bool tie = elig && key == prefix;
-  const unsigned b = __ballot_sync(0xffffffffu, tie);
-  const int lane = l & 31, warp = l >> 5;
-  if (lane == 0) s_cnt[warp] = __popc(b);
+  if (lane == 31) s64[w] = x;
   __syncthreads();
-  int before = __popc(b & ((1u << lane) - 1u));
-  for (int q = 0; q < warp; ++q) before += s_cnt[q];
+  if (w == 0) {
+    int64_t t = lane < nw ? s64[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < nw) s64[lane] = t;
+  }
   __syncthreads();
-  return elig && (key < prefix || (tie && before < k - lt));
+  const int64_t before = (w > 0 ? s64[w - 1] : 0) + x - v;
+  total = s64[nw - 1];
+  __syncthreads();
+  return before;
+}
+
+template <int ITEMS>
+__device__ void block_radix_select(const uint64_t (&key)[ITEMS], const bool (&elig)[ITEMS], int k, int nbits,
+                                   bool (&taken)[ITEMS], RadixSelSmem& sm, int64_t* s64) {
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) taken[j] = false;
+  if (k <= 0) return;
+  int mine = 0;
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) mine += elig[j];
+  int64_t n_elig;
+  block_excl_sum(mine, sm, s64, n_elig);
+  if (k >= n_elig) {
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) taken[j] = elig[j];
+    return;
+  }
+  uint64_t prefix = 0, mask = 0;
+  int kk = k;  // rank (from 1) of the sought key among the keys matching the prefix
+  for (int shift = ((nbits + 7) / 8) * 8 - 8; shift >= 0; shift -= 8) {
+    // Leading digits are often the same for every key still in play (the
+    // exponent of the hard keys, say): a block-wide min/max of the digit finds
+    // those passes, which need no histogram (and would otherwise pile every
+    // increment onto one shared-memory bin).
+    uint32_t dmin = 255u, dmax = 0u;
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j)
+      if (elig[j] && (key[j] & mask) == prefix) {
+        const uint32_t d = (uint32_t)((key[j] >> shift) & 255u);
+        dmin = min(dmin, d);
+        dmax = max(dmax, d);
+      }
+    dmin = __reduce_min_sync(0xffffffffu, dmin);
+    dmax = __reduce_max_sync(0xffffffffu, dmax);
+    const int par = (shift >> 3) & 1;
+    if (threadIdx.x == 0) {
+      sm.dmin[par] = 255u;
+      sm.dmax[par] = 0u;
+    }
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) sm.hist[b] = 0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+      atomicMin(&sm.dmin[par], dmin);
+      atomicMax(&sm.dmax[par], dmax);
+    }
+    __syncthreads();
+    if (sm.dmin[par] == sm.dmax[par]) {  // one digit: every key in play has it
+      prefix |= (uint64_t)sm.dmin[par] << shift;
+      mask |= 255ull << shift;
+      continue;
+    }
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j)
+      if (elig[j] && (key[j] & mask) == prefix) atomicAdd(&sm.hist[(key[j] >> shift) & 255u], 1u);
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      uint32_t c[8], sum = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        c[q] = sm.hist[lane * 8 + q];
+        sum += c[q];
+      }
+      uint32_t incl = sum;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const uint32_t excl = incl - sum;
+      if (excl < (uint32_t)kk && (uint32_t)kk <= incl) {
+        uint32_t run = excl;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (run + c[q] >= (uint32_t)kk) {
+            sm.digit = lane * 8 + q;
+            sm.below = (int)run;
+            break;
+          }
+          run += c[q];
+        }
+      }
+    }
+    __syncthreads();
+    prefix |= (uint64_t)sm.digit << shift;
+    mask |= 255ull << shift;
+    kk -= sm.below;
+  }
+  // every key below K = prefix is taken; of the keys equal to K, the first kk
+  int ties = 0;
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) ties += elig[j] && key[j] == prefix;
+  int64_t all_ties;
+  int before = (int)block_excl_sum(ties, sm, s64, all_ties);
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const bool tie = elig[j] && key[j] == prefix;
+    taken[j] = elig[j] && (key[j] < prefix || (tie && before < kk));
+    before += tie;
+  }
+}
+
+// Tile level in one block of 1024 threads (up to 1024 * ITEMS tiles): the
+// three phases, then the ascending compaction into active_tiles, tile_rank,
+// pix_off and n_active.
+constexpr int kSelThreads = 1024;
+constexpr int kSelBlockMaxTiles = kSelThreads * 16;
+
+template <int ITEMS>
+__global__ void __launch_bounds__(kSelThreads) k_select_block(SelWs w, SelGeom g, int n_sel, int kh, int ks,
+                                                              int n_pix, int32_t* __restrict__ active_tiles,
+                                                              int32_t* __restrict__ n_active,
+                                                              int32_t* __restrict__ tile_rank,
+                                                              int32_t* __restrict__ pix_off) {
+  __shared__ RadixSelSmem sm;
+  __shared__ int64_t s64[32];
+  const int T = g.T;
+  const bool all = n_sel >= T;
+  uint64_t key[ITEMS];
+  bool valid[ITEMS], elig[ITEMS], th[ITEMS], ts[ITEMS], tu[ITEMS];
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const int i = threadIdx.x * ITEMS + j;
+    valid[j] = i < T;
+    elig[j] = valid[j];
+    key[j] = (valid[j] && !all && n_sel > 0) ? hard_key(w.tile_w[i], w.tile_L[i]) : 0;
+  }
+  if (all || n_sel <= 0) {
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      th[j] = all && valid[j];
+      ts[j] = tu[j] = false;
+    }
+  } else {
+    block_radix_select<ITEMS>(key, elig, kh, 64, th, sm, s64);
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const int i = threadIdx.x * ITEMS + j;
+      elig[j] = valid[j] && !th[j];
+      key[j] = valid[j] ? 0xFFFFull - min(w.tile_age[i], 0xFFFFu) : 0;
+    }
+    block_radix_select<ITEMS>(key, elig, ks, 16, ts, sm, s64);
+#pragma unroll
+    for (int j = 0; j < ITEMS; ++j) {
+      const int i = threadIdx.x * ITEMS + j;
+      elig[j] = valid[j] && !th[j] && !ts[j];
+      key[j] = valid[j] ? (w.tile_u[i] >> 32) : 0;
+    }
+    block_radix_select<ITEMS>(key, elig, n_sel - kh - ks, 32, tu, sm, s64);
+  }
+  // compaction: (taken count << 32 | pixel count) prefix in tile order
+  int64_t mine = 0;
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const int i = threadIdx.x * ITEMS + j;
+    if (th[j] || ts[j] || tu[j]) mine += (1ll << 32) | (int64_t)min(n_pix, tile_valid(g, i));
+  }
+  int64_t total;
+  int64_t pre = block_excl_sum(mine, sm, s64, total);
+#pragma unroll
+  for (int j = 0; j < ITEMS; ++j) {
+    const int i = threadIdx.x * ITEMS + j;
+    if (!valid[j]) continue;
+    if (th[j] || ts[j] || tu[j]) {
+      const int r = (int)(pre >> 32);
+      tile_rank[i] = r;
+      active_tiles[r] = i;
+      pix_off[r] = (int)(pre & 0xFFFFFFFFll);
+      pre += (1ll << 32) | (int64_t)min(n_pix, tile_valid(g, i));
+    } else {
+      tile_rank[i] = -1;
+    }
+  }
+  if (threadIdx.x == 0) {
+    *n_active = (int32_t)(total >> 32);
+    pix_off[total >> 32] = (int32_t)(total & 0xFFFFFFFFll);
+  }
 }
 
 // Pixel sampling inside one chosen tile: one block of 256 threads (one per
@@ -181,6 +379,8 @@ __global__ void __launch_bounds__(256) k_sample_pixels(const uint16_t* __restric
                                                        const int32_t* __restrict__ pix_off,
                                                        uint8_t* __restrict__ pix_idx) {
   __shared__ uint32_t s_cnt[8];
+  __shared__ RadixSelSmem sm;
+  __shared__ int64_t s64[32];
   const int j = blockIdx.x;
   if (j >= *n_active) return;
   const int t = active_tiles[j];
@@ -206,10 +406,16 @@ __global__ void __launch_bounds__(256) k_sample_pixels(const uint16_t* __restric
       ku_key = hash_item(hk.prefix(STREAM_PIX_UNIF), (uint32_t)t, (uint32_t)l) >> 32;
     }
     // phase 0: error-proportional draw; 1: oldest of the rest; 2: uniform of the rest
-    const bool th = block_take_k(kh_key, valid, kh, 63, l, s_cnt);
-    const bool ts = block_take_k(0xFFFFull - av, valid && !th, ks, 16, l, s_cnt);
-    const bool tu = block_take_k(ku_key, valid && !th && !ts, n - kh - ks, 32, l, s_cnt);
-    taken = th || ts || tu;
+    uint64_t key[1] = {kh_key};
+    bool el[1] = {valid}, th[1], ts[1], tu[1];
+    block_radix_select<1>(key, el, kh, 64, th, sm, s64);
+    key[0] = 0xFFFFull - av;
+    el[0] = valid && !th[0];
+    block_radix_select<1>(key, el, ks, 16, ts, sm, s64);
+    key[0] = ku_key;
+    el[0] = valid && !th[0] && !ts[0];
+    block_radix_select<1>(key, el, n - kh - ks, 32, tu, sm, s64);
+    taken = th[0] || ts[0] || tu[0];
   }
   // ascending compaction of the taken local indices
   const unsigned b = __ballot_sync(0xffffffffu, taken);
@@ -231,6 +437,75 @@ __global__ void k_sel_finish(const int64_t* __restrict__ total, int32_t* __restr
 }  // namespace tgs
 
 using namespace tgs;
+
+// The launch sequence shared by both entry points (arguments checked).
+static tgs_status launch_select(const uint16_t* err_map, const uint16_t* age_map, int32_t width, int32_t height,
+                                int n_sel, int32_t n_pix, const tgs_sampling* cfg, uint64_t seed, uint64_t iter,
+                                const uint64_t* iter_dev, uint32_t view, void* scratch, int32_t* active_tiles,
+                                int32_t* n_active, int32_t* tile_rank, int32_t* pix_off, uint8_t* pix_idx,
+                                cudaStream_t s) {
+  const int T = tiles_x(width) * tiles_y(height);
+  size_t tot;
+  SelWs w = carve_sel(scratch, T, &tot);
+  SelGeom g{width, height, tiles_x(width), T};
+  const HashKeys hk{seed, iter, iter_dev, view};
+  int kh, ks;
+  split_counts(n_sel, cfg->tile_hard_pm, cfg->tile_stable_pm, kh, ks);
+  if (n_sel < T && n_sel > 0) k_tile_stats<<<T, 256, 0, s>>>(err_map, age_map, g, hk, w);
+  if (T <= kSelBlockMaxTiles) {
+    // one block: the three phases and the compaction
+    if (T <= kSelThreads * 4)
+      k_select_block<4><<<1, kSelThreads, 0, s>>>(w, g, n_sel, kh, ks, n_pix, active_tiles, n_active, tile_rank,
+                                                   pix_off);
+    else if (T <= kSelThreads * 8)
+      k_select_block<8><<<1, kSelThreads, 0, s>>>(w, g, n_sel, kh, ks, n_pix, active_tiles, n_active, tile_rank,
+                                                   pix_off);
+    else
+      k_select_block<16><<<1, kSelThreads, 0, s>>>(w, g, n_sel, kh, ks, n_pix, active_tiles, n_active, tile_rank,
+                                                    pix_off);
+  } else {
+    // many tiles: ranks by pairwise counting, then a device-wide scan.  A
+    // tile is taken when rank_h < kh, or (not hard) rank_s < ks, or
+    // (neither) rank_u < n_sel - kh - ks.
+    cudaMemsetAsync(w.rank_h, 0, sizeof(int32_t) * 3 * (size_t)T, s);
+    if (n_sel < T && n_sel > 0) {
+      dim3 grid((T + 255) / 256, (T + RANK_CHUNK - 1) / RANK_CHUNK);
+      if (kh > 0) k_rank_tiles<<<grid, 256, 0, s>>>(w, T, 0, kh, ks);
+      if (ks > 0) k_rank_tiles<<<grid, 256, 0, s>>>(w, T, 1, kh, ks);
+      if (n_sel - kh - ks > 0) k_rank_tiles<<<grid, 256, 0, s>>>(w, T, 2, kh, ks);
+    }
+    const int32_t* rh = w.rank_h;
+    const int32_t* rs = w.rank_s;
+    const int32_t* ru = w.rank_u;
+    const int all = n_sel >= T ? 1 : 0, none = n_sel == 0 ? 1 : 0;
+    const int ku = n_sel - kh - ks;
+    const int npx = n_pix;
+    int32_t* at = active_tiles;
+    int32_t* tr = tile_rank;
+    int32_t* po = pix_off;
+    auto load = [=] __device__(int64_t t) -> int64_t {
+      const bool taken = !none && (all || rh[t] < kh || rs[t] < ks || (rs[t] >= ks && ru[t] < ku));
+      if (!taken) return 0;
+      return (1ll << 32) | (int64_t)min(npx, tile_valid(g, (int)t));
+    };
+    auto store = [=] __device__(int64_t t, int64_t pre, int64_t v) {
+      if (v) {
+        const int r = (int)(pre >> 32);
+        tr[t] = r;
+        at[r] = (int)t;
+        po[r] = (int)(pre & 0xFFFFFFFFll);
+      } else {
+        tr[t] = -1;
+      }
+    };
+    exclusive_scan<int64_t>(load, store, nullptr, T, w.scan_sums, w.total, s);
+    k_sel_finish<<<1, 1, 0, s>>>(w.total, n_active, pix_off);
+  }
+  if (n_sel > 0)
+    k_sample_pixels<<<n_sel, 256, 0, s>>>(err_map, age_map, g, n_pix, cfg->pix_hard_pm, cfg->pix_stable_pm, hk,
+                                          active_tiles, n_active, pix_off, pix_idx);
+  return check_launch();
+}
 
 extern "C" size_t tgs_select_tiles_workspace_size(int32_t width, int32_t height) {
   size_t total = 0;
@@ -255,62 +530,8 @@ extern "C" tgs_status tgs_select_tiles(const uint16_t* err_map, const uint16_t* 
   const int n_sel = std::min(n_select, T);
   if (n_sel > 0 && (!active_tiles || !pix_idx)) return TGS_ERR_INVALID_ARG;
   if (!workspace || workspace_bytes < tgs_select_tiles_workspace_size(width, height)) return TGS_ERR_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  size_t tot;
-  SelWs w = carve_sel(workspace, T, &tot);
-  SelGeom g{width, height, tiles_x(width), T};
-  const HashKeys hk{seed, iter, iter_dev, view};
-  int kh, ks;
-  split_counts(n_sel, cfg->tile_hard_pm, cfg->tile_stable_pm, kh, ks);
-  // ranks: a tile is taken when rank_h < kh, or (not hard) rank_s < ks, or
-  // (neither) rank_u < n_sel - kh - ks.  Choosing every tile needs no ranking.
-  cudaMemsetAsync(w.rank_h, 0, sizeof(int32_t) * 3 * (size_t)T, s);
-  if (n_sel < T && n_sel > 0) {
-    k_tile_stats<<<T, 256, 0, s>>>(err_map, age_map, g, hk, w);
-    dim3 grid((T + 255) / 256, (T + RANK_CHUNK - 1) / RANK_CHUNK);
-    if (kh > 0) k_rank_tiles<<<grid, 256, 0, s>>>(w, T, 0, kh, ks);
-    if (ks > 0) k_rank_tiles<<<grid, 256, 0, s>>>(w, T, 1, kh, ks);
-    if (n_sel - kh - ks > 0) k_rank_tiles<<<grid, 256, 0, s>>>(w, T, 2, kh, ks);
-  }
-  // compaction: packed (taken << 32 | pixels) prefix gives rank and pixel offset
-  {
-    const int32_t* rh = w.rank_h;
-    const int32_t* rs = w.rank_s;
-    const int32_t* ru = w.rank_u;
-    const int all = n_sel >= T ? 1 : 0, none = n_sel == 0 ? 1 : 0;
-    const int ku = n_sel - kh - ks;
-    const int npx = n_pix;
-    int32_t* at = active_tiles;
-    int32_t* tr = tile_rank;
-    int32_t* po = pix_off;
-    auto is_taken = [=] __device__(int64_t t) -> bool {
-      if (none) return false;
-      if (all) return true;
-      if (rh[t] < kh) return true;
-      if (rs[t] < ks) return true;
-      return rs[t] >= ks && ru[t] < ku;
-    };
-    auto load = [=] __device__(int64_t t) -> int64_t {
-      if (!is_taken(t)) return 0;
-      return (1ll << 32) | (int64_t)min(npx, tile_valid(g, (int)t));
-    };
-    auto store = [=] __device__(int64_t t, int64_t pre, int64_t v) {
-      if (v) {
-        const int r = (int)(pre >> 32);
-        tr[t] = r;
-        at[r] = (int)t;
-        po[r] = (int)(pre & 0xFFFFFFFFll);
-      } else {
-        tr[t] = -1;
-      }
-    };
-    exclusive_scan<int64_t>(load, store, nullptr, T, w.scan_sums, w.total, s);
-  }
-  k_sel_finish<<<1, 1, 0, s>>>(w.total, n_active, pix_off);
-  if (n_sel > 0)
-    k_sample_pixels<<<n_sel, 256, 0, s>>>(err_map, age_map, g, n_pix, cfg->pix_hard_pm, cfg->pix_stable_pm, hk,
-                                          active_tiles, n_active, pix_off, pix_idx);
-  return check_launch();
+  return launch_select(err_map, age_map, width, height, n_sel, n_pix, cfg, seed, iter, iter_dev, view, workspace,
+                       active_tiles, n_active, tile_rank, pix_off, pix_idx, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -382,52 +603,6 @@ extern "C" tgs_status tgs_select_tiles_noalloc(const uint16_t* err_map, const ui
   void* scratch = nullptr;
   tgs_status st = select_scratch_address(&scratch);
   if (st != TGS_OK) return st;
-  cudaStream_t s = (cudaStream_t)stream;
-  size_t tot;
-  SelWs w = carve_sel(scratch, T, &tot);
-  SelGeom g{width, height, tiles_x(width), T};
-  const HashKeys hk{seed, iter, iter_dev, view};
-  int kh, ks;
-  split_counts(n_sel, cfg->tile_hard_pm, cfg->tile_stable_pm, kh, ks);
-  // the rank counters accumulate with atomics: clear the previous call's values
-  cudaMemsetAsync(w.rank_h, 0, sizeof(int32_t) * 3 * (size_t)T, s);
-  if (n_sel < T && n_sel > 0) {
-    k_tile_stats<<<T, 256, 0, s>>>(err_map, age_map, g, hk, w);
-    dim3 grid((T + 255) / 256, (T + RANK_CHUNK - 1) / RANK_CHUNK);
-    if (kh > 0) k_rank_tiles<<<grid, 256, 0, s>>>(w, T, 0, kh, ks);
-    if (ks > 0) k_rank_tiles<<<grid, 256, 0, s>>>(w, T, 1, kh, ks);
-    if (n_sel - kh - ks > 0) k_rank_tiles<<<grid, 256, 0, s>>>(w, T, 2, kh, ks);
-  }
-  {
-    const int32_t* rh = w.rank_h;
-    const int32_t* rs = w.rank_s;
-    const int32_t* ru = w.rank_u;
-    const int all = n_sel >= T ? 1 : 0, none = n_sel == 0 ? 1 : 0;
-    const int ku = n_sel - kh - ks;
-    const int npx = n_pix;
-    int32_t* at = active_tiles;
-    int32_t* tr = tile_rank;
-    int32_t* po = pix_off;
-    auto load = [=] __device__(int64_t t) -> int64_t {
-      bool taken = !none && (all || rh[t] < kh || rs[t] < ks || (rs[t] >= ks && ru[t] < ku));
-      if (!taken) return 0;
-      return (1ll << 32) | (int64_t)min(npx, tile_valid(g, (int)t));
-    };
-    auto store = [=] __device__(int64_t t, int64_t pre, int64_t v) {
-      if (v) {
-        const int r = (int)(pre >> 32);
-        tr[t] = r;
-        at[r] = (int)t;
-        po[r] = (int)(pre & 0xFFFFFFFFll);
-      } else {
-        tr[t] = -1;
-      }
-    };
-    exclusive_scan<int64_t>(load, store, nullptr, T, w.scan_sums, w.total, s);
-  }
-  k_sel_finish<<<1, 1, 0, s>>>(w.total, n_active, pix_off);
-  if (n_sel > 0)
-    k_sample_pixels<<<n_sel, 256, 0, s>>>(err_map, age_map, g, n_pix, cfg->pix_hard_pm, cfg->pix_stable_pm, hk,
-                                          active_tiles, n_active, pix_off, pix_idx);
-  return check_launch();
+  return launch_select(err_map, age_map, width, height, n_sel, n_pix, cfg, seed, iter, iter_dev, view, scratch,
+                       active_tiles, n_active, tile_rank, pix_off, pix_idx, (cudaStream_t)stream);
 }

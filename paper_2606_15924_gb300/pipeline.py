@@ -27,6 +27,8 @@ def zeros_like_params(g: dict) -> dict:
 
 
 class Trainer:
+    CKPT_POSITIONS = 2048
+
     def __init__(self, params: dict, cam: dict, target: torch.Tensor, tile_fraction: float = 0.2,
                  pixel_rate: float = 1.0 / 3.0, cfg: Config | None = None, dense: bool = False,
                  capacity: int | None = None, seed: int = 0, bg=(0.0, 0.0, 0.0), sh_degree: int = 3,
@@ -84,6 +86,14 @@ class Trainer:
         self.lam = torch.zeros(S, device=dev)
         self.err_pix = torch.zeros(P, device=dev)
         self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        # forward checkpoints for the split backward (sampled training only):
+        # one slot per batch of the tile list up to CKPT_POSITIONS positions
+        self.ckpt = None
+        if train and not dense:
+            blk = min(256, max(32, (self.n_pix + 31) // 32 * 32))  # the kernels' block size
+            n_slots = max(1, self.CKPT_POSITIONS // blk)
+            self.ck_data = torch.empty(B.checkpoint_bytes(S, self.n_pix, n_slots) // 4, device=dev)
+            self.ckpt = B.checkpoints(self.ck_data, n_slots, S * self.n_pix, self.rgb)
         if train:
             self.grad2d = torch.zeros(N, 12, device=dev)
             self.touched = torch.zeros(N, dtype=u8, device=dev)
@@ -141,7 +151,7 @@ class Trainer:
                     self.vals, None, self.ranges, self.n_isect)
         B.render_sampled(self.proj, self.ranges, self.vals, self.active_tiles, self.n_active, self.n_select,
                          self.pix_off, self.pix_idx, self.n_pix, self.ccam, self.bg, self.rgb, self.T_final,
-                         self.n_last)
+                         self.n_last, ckpt=self.ckpt)
 
     def loss_and_maps(self):
         """Fused loss with the error/age map update (Alg. 1 steps 4, 6, 7)."""
@@ -154,7 +164,7 @@ class Trainer:
         B.backward_sampled(self.params, self.ccam, self.proj, self.ranges, self.vals, self.active_tiles,
                            self.n_active, self.n_select, self.pix_off, self.pix_idx, self.n_pix, self.bg,
                            self.T_final, self.n_last, self.dL, self.grad2d, self.grads, self.touched,
-                           write_untouched=write_untouched, sh_degree=self.sh_degree)
+                           write_untouched=write_untouched, sh_degree=self.sh_degree, ckpt=self.ckpt)
 
     def update(self):
         """Hybrid LM / Adam update (Alg. 1 steps 9, 10)."""
@@ -207,7 +217,7 @@ class Trainer:
                 ("render_sampled", lambda: B.render_sampled(self.proj, self.ranges, self.vals, self.active_tiles,
                                                             self.n_active, self.n_select, self.pix_off,
                                                             self.pix_idx, self.n_pix, self.ccam, self.bg, self.rgb,
-                                                            self.T_final, self.n_last)),
+                                                            self.T_final, self.n_last, ckpt=self.ckpt)),
                 ("loss_sparse_ncc", self.loss_and_maps),
                 ("backward_sampled", self.backward),
                 ("hybrid_step", lambda: (self.update(), bump()))]

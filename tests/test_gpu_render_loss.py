@@ -204,9 +204,13 @@ def test_loss_parity(B, orc, W, H, n_select, n_pix):
     assert np.all(np.abs(got_e - want_e) <= ulp)     # one fp16 ulp
 
 
-def test_backward_parity(B, orc):
+@pytest.mark.parametrize("split", [False, True])
+def test_backward_parity(B, orc, split):
     """grad2d and the parameter gradients of the tiny scene against the
-    oracle's analytic backward (relative L2 <= 1e-3 per parameter group)."""
+    oracle's analytic backward (relative L2 <= 1e-3 per parameter group);
+    split: the backward replays each tile list in pieces from the forward's
+    checkpoints (few slots, so pieces, checkpoint starts and the tail piece
+    all occur)."""
     from gpu_util import bin_dev, dev, empty_projected, gaussians_dev, render_dev, select_dev, select_host
     g, cam = _c0(seed=5, n=3000)
     g["log_scales"] += 1.0
@@ -222,6 +226,19 @@ def test_backward_parity(B, orc):
         B.project_gaussians(gd, cam, sel["tile_rank"], pd)
         binned = bin_dev(B, pd, n, cam, sel["tile_rank"], sel["n_sel"], capacity=300000)
         out = render_dev(B, pd, binned, sel, n_pix, cam)
+        ck = None
+        if split:
+            blk = min(256, (n_pix + 31) // 32 * 32)
+            longest = int(out["n_last"].max().item())
+            assert longest > blk                              # at least two pieces
+            slots = max(1, min(3, longest // blk - 1))        # and a tail piece past the slots
+            stride = sel["n_sel"] * n_pix
+            ck_data = torch.full((B.checkpoint_bytes(sel["n_sel"], n_pix, slots) // 4,), float("nan"),
+                                 device="cuda")
+            ck = B.checkpoints(ck_data, slots, stride, out["rgb"])
+            B.render_sampled(pd, binned["ranges"], binned["vals"], sel["active_tiles"], sel["n_active"],
+                             sel["n_sel"], sel["pix_off"], sel["pix_idx"], n_pix, cam, (0.0, 0.0, 0.0), out["rgb"],
+                             out["T"], out["n_last"], ckpt=ck)
         P = int(sh["pix_off"][-1])
         pix = orc.pixel_coords(sh["active_tiles"], sh["pix_off"], sh["pix_idx"], W)
         # one dL/dI drives both sides (a seeded input, not computed by either)
@@ -231,7 +248,7 @@ def test_backward_parity(B, orc):
         touched = torch.zeros(n, dtype=torch.uint8, device="cuda")
         B.backward_sampled(gd, cam, pd, binned["ranges"], binned["vals"], sel["active_tiles"], sel["n_active"],
                            sel["n_sel"], sel["pix_off"], sel["pix_idx"], n_pix, (0.0, 0.0, 0.0), out["T"],
-                           out["n_last"], dev(dLd), grad2d, grads, touched)
+                           out["n_last"], dev(dLd), grad2d, grads, touched, ckpt=ck)
         g64 = {k: v.astype(np.float64) for k, v in g.items()}
         prw = orc.project(g64, cam, tile_rank=sh["tile_rank"])
         g2w = orc.render_backward(prw, W, H, pix, dLd.astype(np.float64))
