@@ -203,39 +203,76 @@ def stage_times(tr, steps, flush):
 
 # FP32 operations of one alpha evaluation (offset, conic quadratic form,
 # exponent scaling, opacity product, clamp) and of one blend (1 - alpha,
-# transmittance product, weight, three colour FMAs), FMA = 2.
+# transmittance product, weight, three colour FMAs), FMA = 2; the backward
+# replay of one (pixel, splat): alpha again, the transmittance division, the
+# colour and alpha adjoints, the conic and centre adjoints (about 45).
 FLOPS_ALPHA = 15
 FLOPS_BLEND = 10
+FLOPS_BWD = 45
 
 
-def roofline(stage_ms, info, peaks, peak_kind, clocks, tr):
-    """Dominant kernel's achieved fraction of its roof."""
-    dom = max(stage_ms, key=stage_ms.get)
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def source_digest(files) -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(stage: str):
+    """DRAM bytes per launch of the stage's kernel from the committed ncu
+    summary, or None when there is none or the kernel's sources changed since
+    it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f).get(stage)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("sources_sha256") != source_digest(rec.get("sources", [])):
+        return None
+    return rec.get("bytes_per_launch")
+
+
+# Stages that are one kernel of the library (render_backward also zeroes
+# grad2d first); the others chain several small kernels.
+SINGLE_KERNEL_STAGES = ("render_sampled", "render_backward", "project_backward", "project_gaussians")
+
+
+def roofline(stage_ms, info, peaks, peak_kind, clocks, tr, dom=None):
+    """A stage's kernel against its roof (achieved from its live CUDA-event
+    time and its algorithmic work); by default the longest single kernel."""
+    if dom is None:
+        dom = max((k for k in stage_ms if k in SINGLE_KERNEL_STAGES), key=stage_ms.get)
     t = stage_ms[dom] * 1e-3
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s FP32 (FMA = 2) at the sampled clock
     n = tr.n
-    if dom in ("render_sampled",):
-        work = info["evals_per_step"] * (FLOPS_ALPHA + FLOPS_BLEND) / 1e12
+    if dom in ("render_sampled", "render_backward"):
+        per = FLOPS_ALPHA + FLOPS_BLEND if dom == "render_sampled" else FLOPS_BWD
+        work = info["evals_per_step"] * per / 1e12
         return dict(kernel=dom, bound="alu", achieved=work / t, peak=alu_peak, unit="TFLOP/s",
-                    frac=(work / t) / alu_peak, traffic=None,
-                    note="FP32 FLOPs of the alpha test + blend per (pixel, splat) walked, at the sampled SM clock")
-    if dom in ("backward_sampled",):
-        work = info["evals_per_step"] * 45 / 1e12
-        return dict(kernel=dom, bound="alu", achieved=work / t, peak=alu_peak, unit="TFLOP/s",
-                    frac=(work / t) / alu_peak, traffic=None,
-                    note="~45 FP32 FLOPs per (pixel, splat) replayed, at the sampled SM clock")
+                    frac=(work / t) / alu_peak, traffic=measured_traffic(dom),
+                    note=f"{per} FP32 FLOPs per (pixel, splat) walked, at the sampled SM clock")
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     if dom == "hybrid_step":
         byts = info["touched"] * 59 * 4 * 7
     elif dom == "project_gaussians":
         byts = n * (44 + 48) + info["visible"] * 192
+    elif dom == "project_backward":
+        byts = n * 5 + info["visible"] * 48 + info["touched"] * 236 * 2
     elif dom == "bin_tiles":
         byts = info["n_isect"] * 44
-    else:
-        byts = HEIGHT * WIDTH * 4 + info["P"] * 48
+    elif dom == "select_tiles":
+        byts = tr.H * tr.W * 4
+    else:  # loss: target gather, rgb, gradient, error and age maps
+        byts = tr.H * tr.W * 2 + info["P"] * 48
     ach = byts / t / 1e9
-    return dict(kernel=dom, bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm, traffic=None)
+    return dict(kernel=dom, bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                traffic=measured_traffic(dom))
 
 
 def e2e_replays(tr, target_host, steps):
@@ -371,7 +408,8 @@ def run_ours(args):
     st, info = stage_times(sampled, max(2, min(args.steps, 5)), flush)
     roof = roofline(st, info, peaks, peak_kind, clocks, sampled)
     roof["peak_source"] = f"{peak_kind} (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback"
-    fwdbwd_ms = st["render_sampled"] + st["backward_sampled"]
+    stage_roofs = {k: roofline(st, info, peaks, peak_kind, clocks, sampled, dom=k) for k in st}
+    fwdbwd_ms = st["render_sampled"] + st["render_backward"] + st["project_backward"]
     mpix = info["P"] / (fwdbwd_ms * 1e-3) / 1e6
     res = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": mean_s, "higher_is_better": True, "scaling": "weak",
@@ -382,13 +420,16 @@ def run_ours(args):
            "sampled": {"iters_per_s": 1e3 / mean_s, "ms_per_step": mean_s, "sampled_pixels": info["P"],
                        "active_tiles": info["A"], "tile_pairs": info["n_isect"], "touched": info["touched"],
                        "visible": info["visible"], "splat_evals": info["evals_per_step"], "tile_lists": info["tiles"],
-                       "fwd_bwd_mpix_per_s": mpix, "stage_ms": st, "kernels_per_step": launches}}
+                       "fwd_bwd_mpix_per_s": mpix, "stage_ms": st, "kernels_per_step": launches,
+                       "stage_rooflines": {k: {"bound": v["bound"], "achieved": v["achieved"], "unit": v["unit"],
+                                               "frac": v["frac"]} for k, v in stage_roofs.items()}}}
     if ms_d is not None:
         mean_d = sum(ms_d) / len(ms_d)
         st_d, info_d = stage_times(dense, 2, flush)
         res["dense"] = {"iters_per_s": 1e3 / mean_d, "ms_per_step": mean_d, "pixels": info_d["P"],
-                        "fwd_bwd_mpix_per_s": info_d["P"] / ((st_d["render_sampled"] + st_d["backward_sampled"])
-                                                              * 1e-3) / 1e6, "stage_ms": st_d}
+                        "fwd_bwd_mpix_per_s": info_d["P"] / ((st_d["render_sampled"] + st_d["render_backward"] +
+                                                               st_d["project_backward"]) * 1e-3) / 1e6,
+                        "stage_ms": st_d}
         res["speedup_vs_dense"] = mean_d / mean_s
     # end to end through the public API: target in from pinned host memory, loss out
     tgt_host = target.detach().cpu().pin_memory()

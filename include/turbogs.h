@@ -329,6 +329,18 @@ tgs_status tgs_backward_sampled(const tgs_gaussians* g, const tgs_camera* cam, c
                                 const tgs_checkpoints* ckpt, tgs_stream stream);
 
 /*
+ * render_backward_sampled - the first half of backward_sampled alone: zeroes
+ * grad2d [n_gaussians, 12] and accumulates the compositing adjoint into it
+ * (arguments as in backward_sampled).
+ */
+tgs_status tgs_render_backward_sampled(const tgs_projected* proj, const int32_t* tile_ranges, const int32_t* vals,
+                                       const int32_t* active_tiles, const int32_t* n_active, int32_t n_active_max,
+                                       const int32_t* pix_off, const uint8_t* pix_idx, int32_t n_pix_max,
+                                       const tgs_camera* cam, const float* bg, const float* T_final,
+                                       const int32_t* n_last, const float* dL_drgb, float* grad2d,
+                                       int64_t n_gaussians, const tgs_checkpoints* ckpt, tgs_stream stream);
+
+/*
  * project_backward - the projection adjoint alone (the second half of
  * backward_sampled, Alg. 1 step 8): grad2d [N,12] of one view -> parameter
  * gradients.  accumulate = 0 overwrites grads and touched as backward_sampled
@@ -395,6 +407,12 @@ typedef struct {
   float* grad2d;
   int64_t n_gaussians;
 } tgs_view_batch;
+
+/* Advances the device-side iteration counters of a captured step by one
+ * (iter_dev as read by select_tiles, step_dev as read by hybrid_step; either
+ * may be NULL).  Not in the paper: the counters let one captured step be
+ * replayed. */
+tgs_status tgs_advance_counters(int64_t* iter_dev, int32_t* step_dev, tgs_stream stream);
 
 /* Thread blocks of the batched kernels that fit on the current device at
  * once (SMs x resident blocks per SM) for n_pix_max pixels per tile: the

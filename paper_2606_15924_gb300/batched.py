@@ -154,8 +154,7 @@ class MultiViewTrainer:
         self.loss_and_maps()
         self.backward()
         self.update()
-        self.it_dev.add_(1)
-        self.step_dev.add_(1)
+        B.advance_counters(self.it_dev, self.step_dev)
 
     def loss(self) -> float:
         """Mean loss over the views of the last step (reads the device)."""
@@ -188,8 +187,7 @@ class MultiViewTrainer:
 
         def upd():
             self.update()
-            self.it_dev.add_(1)
-            self.step_dev.add_(1)
+            B.advance_counters(self.it_dev, self.step_dev)
         return [("select_tiles", select), ("project_gaussians", project), ("bin_tiles", bins),
                 ("render_sampled", self._render_fwd), ("loss_sparse_ncc", self.loss_and_maps),
                 ("render_backward", self._render_bwd), ("project_backward", self._project_bwd),

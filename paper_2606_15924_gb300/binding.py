@@ -104,6 +104,8 @@ _lib.tgs_last_cuda_error.restype = _i32
 _lib.tgs_device_check.restype = _i32
 _lib.tgs_graph_count_kernels.restype = _i64
 _lib.tgs_graph_count_kernels.argtypes = [_p]
+_lib.tgs_advance_counters.restype = _i32
+_lib.tgs_advance_counters.argtypes = [_p, _p, _p]
 _lib.tgs_select_tiles_workspace_size.restype = _sz
 _lib.tgs_select_tiles_workspace_size.argtypes = [_i32, _i32]
 _lib.tgs_select_tiles.restype = _i32
@@ -129,6 +131,9 @@ _lib.tgs_loss_sparse_ncc.argtypes = [_p, _p, _i32, _i32, _p, _p, _i32, _p, _p, _
 _lib.tgs_backward_sampled.restype = _i32
 _lib.tgs_backward_sampled.argtypes = [_P(Gaussians), _P(Camera), _P(Projected), _p, _p, _p, _p, _i32, _p, _p,
                                       _i32, _p, _p, _p, _p, _p, _P(ParamPtrs), _p, _i32, _P(Checkpoints), _p]
+_lib.tgs_render_backward_sampled.restype = _i32
+_lib.tgs_render_backward_sampled.argtypes = [_P(Projected), _p, _p, _p, _p, _i32, _p, _p, _i32, _P(Camera), _p, _p,
+                                             _p, _p, _p, _i64, _P(Checkpoints), _p]
 _lib.tgs_project_backward.restype = _i32
 _lib.tgs_project_backward.argtypes = [_P(Gaussians), _P(Camera), _P(Projected), _p, _P(ParamPtrs), _p, _i32, _i32,
                                       _p, _p]
@@ -160,11 +165,12 @@ _lib.tgs_mlp_adam.restype = _i32
 _lib.tgs_mlp_adam.argtypes = [_p, _p, _p, _p, _i32, C.c_float, C.c_float, C.c_float, C.c_float, _p, _p, _p, _p]
 
 EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_device_check", "tgs_graph_count_kernels",
+            "tgs_advance_counters",
             "tgs_select_tiles_workspace_size", "tgs_select_tiles", "tgs_select_tiles_noalloc",
             "tgs_project_gaussians",
             "tgs_bin_tiles_workspace_size", "tgs_bin_tiles", "tgs_checkpoint_bytes", "tgs_render_sampled",
             "tgs_loss_sparse_ncc",
-            "tgs_backward_sampled", "tgs_project_backward", "tgs_project_backward_multi_workspace_size",
+            "tgs_backward_sampled", "tgs_render_backward_sampled", "tgs_project_backward", "tgs_project_backward_multi_workspace_size",
             "tgs_project_backward_multi",
             "tgs_render_batched_resident", "tgs_render_sampled_batched",
             "tgs_render_backward_batched", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step",
@@ -199,6 +205,10 @@ def version() -> str:
 def graph_count_kernels(graph) -> int:
     """Kernel nodes in a captured torch.cuda.CUDAGraph."""
     return int(_lib.tgs_graph_count_kernels(C.c_void_p(graph.raw_cuda_graph())))
+
+
+def advance_counters(iter_dev=None, step_dev=None, stream=None):
+    _check("tgs_advance_counters", _lib.tgs_advance_counters(_ptr(iter_dev), _ptr(step_dev), _stream(stream)))
 
 
 def device_check() -> None:
@@ -329,6 +339,17 @@ def backward_sampled(g: dict, cam, proj: dict, tile_ranges, vals, active_tiles, 
         int(n_active_max), _ptr(pix_off), _ptr(pix_idx), int(n_pix_max), bgv, _ptr(T_final), _ptr(n_last),
         _ptr(dL_drgb), _ptr(grad2d), C.byref(gp), _ptr(touched), 1 if write_untouched else 0, _ck(ckpt),
         _stream(stream)))
+
+
+def render_backward_sampled(proj: dict, tile_ranges, vals, active_tiles, n_active, n_active_max, pix_off, pix_idx,
+                            n_pix_max, cam, bg, T_final, n_last, dL_drgb, grad2d, stream=None, ckpt=None):
+    pr = projected(proj)
+    cc = cam if isinstance(cam, Camera) else camera(cam)
+    bgv = (C.c_float * 3)(*[float(b) for b in bg])
+    _check("tgs_render_backward_sampled", _lib.tgs_render_backward_sampled(
+        C.byref(pr), _ptr(tile_ranges), _ptr(vals), _ptr(active_tiles), _ptr(n_active), int(n_active_max),
+        _ptr(pix_off), _ptr(pix_idx), int(n_pix_max), C.byref(cc), bgv, _ptr(T_final), _ptr(n_last), _ptr(dL_drgb),
+        _ptr(grad2d), int(grad2d.shape[0]), _ck(ckpt), _stream(stream)))
 
 
 def project_backward(g: dict, cam, proj: dict, grad2d, grads: dict, touched, write_untouched=True,

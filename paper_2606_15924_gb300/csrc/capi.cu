@@ -57,3 +57,16 @@ extern "C" int64_t tgs_graph_count_kernels(void* graph) {
   delete[] nodes;
   return k;
 }
+
+namespace {
+__global__ void k_advance_counters(int64_t* it, int32_t* step) {
+  if (it) *it += 1;
+  if (step) *step += 1;
+}
+}  // namespace
+
+extern "C" tgs_status tgs_advance_counters(int64_t* iter_dev, int32_t* step_dev, tgs_stream stream) {
+  if (!iter_dev && !step_dev) return TGS_ERR_INVALID_ARG;
+  k_advance_counters<<<1, 1, 0, (cudaStream_t)stream>>>(iter_dev, step_dev);
+  return tgs::check_launch();
+}

@@ -536,6 +536,38 @@ extern "C" tgs_status tgs_render_sampled(const tgs_projected* proj, const int32_
   return check_launch();
 }
 
+extern "C" tgs_status tgs_render_backward_sampled(const tgs_projected* proj, const int32_t* tile_ranges,
+                                                  const int32_t* vals, const int32_t* active_tiles,
+                                                  const int32_t* n_active, int32_t n_active_max,
+                                                  const int32_t* pix_off, const uint8_t* pix_idx, int32_t n_pix_max,
+                                                  const tgs_camera* cam, const float* bg, const float* T_final,
+                                                  const int32_t* n_last, const float* dL_drgb, float* grad2d,
+                                                  int64_t n_gaussians, const tgs_checkpoints* ckpt,
+                                                  tgs_stream stream) {
+  RasterArgs a;
+  if (n_gaussians < 0 || n_active_max < 0 || n_pix_max < 1 || n_pix_max > 256) return TGS_ERR_INVALID_ARG;
+  if (!raster_args(proj, tile_ranges, vals, active_tiles, n_active, pix_off, pix_idx, cam, bg, a))
+    return TGS_ERR_INVALID_ARG;
+  if (!T_final || !n_last || !dL_drgb) return TGS_ERR_INVALID_ARG;
+  if (n_gaussians > 0 && (!grad2d || !aligned16(grad2d))) return TGS_ERR_INVALID_ARG;
+  Ckpt ck;
+  if (!ckpt_of(ckpt, n_active_max, n_pix_max, ckpt ? ckpt->rgb : nullptr, ck)) return TGS_ERR_INVALID_ARG;
+  if (ck.data && !ck.rgb) return TGS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_gaussians == 0) return TGS_OK;
+  cudaMemsetAsync(grad2d, 0, sizeof(float) * 12 * (size_t)n_gaussians, s);
+  if (n_active_max > 0) {
+    const int B = block_for(n_pix_max);
+    const size_t smem = B * (sizeof(Splat) + 9 * sizeof(float));
+    if (ck.data)
+      k_render_bwd_split<<<dim3(n_active_max, ck.n_slots + 1), B, smem, s>>>(a, T_final, n_last, dL_drgb, grad2d,
+                                                                             ck);
+    else
+      k_render_bwd<<<n_active_max, B, smem, s>>>(a, T_final, n_last, dL_drgb, grad2d);
+  }
+  return check_launch();
+}
+
 extern "C" tgs_status tgs_backward_sampled(const tgs_gaussians* g, const tgs_camera* cam, const tgs_projected* proj,
                                            const int32_t* tile_ranges, const int32_t* vals,
                                            const int32_t* active_tiles, const int32_t* n_active,
@@ -552,22 +584,12 @@ extern "C" tgs_status tgs_backward_sampled(const tgs_gaussians* g, const tgs_cam
   if (g->n > 0 && (!grad2d || !aligned16(grad2d) || !grads->means || !grads->log_scales || !grads->quats ||
                    !grads->opacity_logits || !grads->sh || !aligned16(grads->quats) || !aligned16(grads->sh)))
     return TGS_ERR_INVALID_ARG;
-  Ckpt ck;
-  if (!ckpt_of(ckpt, n_active_max, n_pix_max, ckpt ? ckpt->rgb : nullptr, ck)) return TGS_ERR_INVALID_ARG;
-  if (ck.data && !ck.rgb) return TGS_ERR_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  if (g->n == 0) return TGS_OK;
-  cudaMemsetAsync(grad2d, 0, sizeof(float) * 12 * (size_t)g->n, s);
-  if (n_active_max > 0) {
-    const int B = block_for(n_pix_max);
-    const size_t smem = B * (sizeof(Splat) + 9 * sizeof(float));
-    if (ck.data)
-      k_render_bwd_split<<<dim3(n_active_max, ck.n_slots + 1), B, smem, s>>>(a, T_final, n_last, dL_drgb, grad2d,
-                                                                             ck);
-    else
-      k_render_bwd<<<n_active_max, B, smem, s>>>(a, T_final, n_last, dL_drgb, grad2d);
-  }
-  launch_project_bwd(*g, *cam, proj->radius, grad2d, *grads, touched, write_untouched, 0, nullptr, s);
+  const tgs_status st = tgs_render_backward_sampled(proj, tile_ranges, vals, active_tiles, n_active, n_active_max,
+                                                    pix_off, pix_idx, n_pix_max, cam, bg, T_final, n_last, dL_drgb,
+                                                    grad2d, g->n, ckpt, stream);
+  if (st != TGS_OK || g->n == 0) return st;
+  launch_project_bwd(*g, *cam, proj->radius, grad2d, *grads, touched, write_untouched, 0, nullptr,
+                     (cudaStream_t)stream);
   return check_launch();
 }
 

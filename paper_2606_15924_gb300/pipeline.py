@@ -159,12 +159,21 @@ class Trainer:
                           self.pix_off, self.pix_idx, self.n_pix, self.loss_params, self.err_map, self.age_map,
                           self.dL, self.lam, self.err_pix, self.loss)
 
+    def render_backward(self):
+        """Compositing adjoint into grad2d (first half of Alg. 1 step 8)."""
+        B.render_backward_sampled(self.proj, self.ranges, self.vals, self.active_tiles, self.n_active,
+                                  self.n_select, self.pix_off, self.pix_idx, self.n_pix, self.ccam, self.bg,
+                                  self.T_final, self.n_last, self.dL, self.grad2d, ckpt=self.ckpt)
+
+    def project_backward(self, write_untouched=False):
+        """Projection adjoint into the parameter gradients (second half)."""
+        B.project_backward(self.params, self.ccam, self.proj, self.grad2d, self.grads, self.touched,
+                           write_untouched=write_untouched, sh_degree=self.sh_degree)
+
     def backward(self, write_untouched=False):
         """Sparse backward into parameter gradients (Alg. 1 step 8)."""
-        B.backward_sampled(self.params, self.ccam, self.proj, self.ranges, self.vals, self.active_tiles,
-                           self.n_active, self.n_select, self.pix_off, self.pix_idx, self.n_pix, self.bg,
-                           self.T_final, self.n_last, self.dL, self.grad2d, self.grads, self.touched,
-                           write_untouched=write_untouched, sh_degree=self.sh_degree, ckpt=self.ckpt)
+        self.render_backward()
+        self.project_backward(write_untouched)
 
     def update(self):
         """Hybrid LM / Adam update (Alg. 1 steps 9, 10)."""
@@ -177,8 +186,7 @@ class Trainer:
         self.loss_and_maps()
         self.backward()
         self.update()
-        self.it_dev.add_(1)
-        self.step_dev.add_(1)
+        B.advance_counters(self.it_dev, self.step_dev)
 
     # ------------------------------------------------------------------ graph
     def capture(self):
@@ -201,13 +209,12 @@ class Trainer:
         self.graph.replay()
 
     STAGES = ("select_tiles", "project_gaussians", "bin_tiles", "render_sampled", "loss_sparse_ncc",
-              "backward_sampled", "hybrid_step")
+              "render_backward", "project_backward", "hybrid_step")
 
     def stage_calls(self):
         """The step as (name, callable) pairs, one per C-ABI call."""
         def bump():
-            self.it_dev.add_(1)
-            self.step_dev.add_(1)
+            B.advance_counters(self.it_dev, self.step_dev)
         return [("select_tiles", self._select),
                 ("project_gaussians", lambda: B.project_gaussians(self.params, self.ccam, self.tile_rank, self.proj,
                                                                   self.sh_degree)),
@@ -219,7 +226,8 @@ class Trainer:
                                                             self.pix_idx, self.n_pix, self.ccam, self.bg, self.rgb,
                                                             self.T_final, self.n_last, ckpt=self.ckpt)),
                 ("loss_sparse_ncc", self.loss_and_maps),
-                ("backward_sampled", self.backward),
+                ("render_backward", self.render_backward),
+                ("project_backward", self.project_backward),
                 ("hybrid_step", lambda: (self.update(), bump()))]
 
     def capture_stages(self):
