@@ -473,9 +473,12 @@ tgs_status tgs_mlp_forward(const tgs_mlp* w, int64_t rows, const float* x, float
 
 /* Gradient of L = (1/R) sum (y - t)^2 / 2 into grads (packed layout, fp32,
  * overwritten) and *loss (device double), from the forward's x, h1, h2, y.
- * Hidden adjoints are rounded to bf16 before they meet a bf16 operand. */
+ * Hidden adjoints are rounded to bf16 before they meet a bf16 operand.  R is
+ * rows, or min(rows, *rows_dev) when rows_dev (device int32) is given: the
+ * rows past it are padding and take no part. */
 size_t tgs_mlp_backward_workspace_size(int64_t rows);
-tgs_status tgs_mlp_backward(const tgs_mlp* w, int64_t rows, const float* x, const uint16_t* h1,
+tgs_status tgs_mlp_backward(const tgs_mlp* w, int64_t rows, const int32_t* rows_dev, const float* x,
+                            const uint16_t* h1,
                             const uint16_t* h2, const float* y, const float* target, float* grads, double* loss,
                             void* workspace, size_t workspace_bytes, tgs_stream stream);
 
@@ -485,6 +488,46 @@ tgs_status tgs_mlp_backward(const tgs_mlp* w, int64_t rows, const float* x, cons
 tgs_status tgs_mlp_adam(float* params, const float* grads, float* m, float* v, int32_t step, float lr,
                         float beta1, float beta2, float eps, uint16_t* w1, uint16_t* w2, uint16_t* w3,
                         tgs_stream stream);
+
+/*
+ * Tile memory and features of the tile-error predictor (not in the paper,
+ * which refreshes a stale view's error map by rendering it, Sec. 3.3).
+ *
+ * tile_observe - after a step's loss: for each active rank j, the tile's
+ * record mem[t] (float4: list length, mean T_final, mean err_pix over its
+ * sampled pixels, 1 = observed) and mem_iter[t] = the iteration (iter_dev when
+ * given); target[j] (nullable) = log(1 + mean err_pix), minus the same of the
+ * tile's previous observation when residual = 1 and there was one; 0 for
+ * ranks past n_active.  mem [T,4] (16-byte aligned), mem_iter [T]: the view's
+ * memory, zero before the first observation.
+ */
+tgs_status tgs_tile_observe(const int32_t* active_tiles, const int32_t* n_active, int32_t n_active_max,
+                            const int32_t* pix_off, const int32_t* tile_ranges, const float* T_final,
+                            const float* err_pix, uint64_t iter, const uint64_t* iter_dev, float* mem,
+                            int64_t* mem_iter, float* target, int32_t residual, tgs_stream stream);
+
+/*
+ * tile_features - x [n_rows_max, 16] (16-byte aligned) for tiles rows[r]
+ * (r < *n_rows; zero rows after) or, with rows NULL, for every tile r <
+ * n_rows_max: log(1 + list length), mean T_final (1 if never observed),
+ * log(1 + error), view_cos (cosine between this view and a reference view
+ * direction, from the host), log(1 + iterations since the observation;
+ * 1e6 if never), cosine of the tile centre's ray to the optical axis, 1 if
+ * observed; slots 7-15 zero.
+ */
+tgs_status tgs_tile_features(const float* mem, const int64_t* mem_iter, const int32_t* rows, const int32_t* n_rows,
+                             int32_t n_rows_max, const tgs_camera* cam, float view_cos, uint64_t iter,
+                             const uint64_t* iter_dev, float* x, tgs_stream stream);
+
+/*
+ * tile_refresh - rescales each tile of the fp16 error map [H,W] so that its
+ * mean is exp(p) - 1, p = pred[t] (+ base[16 t + 2], the tile's last observed
+ * log error from tile_features, when base is given: pred are then residuals),
+ * clamped at 0 below, keeping the shape within the tile; a tile whose mean
+ * is 0 is set to the prediction everywhere.
+ */
+tgs_status tgs_tile_refresh(const float* pred, const float* base, uint16_t* err_map, int32_t width, int32_t height,
+                            tgs_stream stream);
 
 #ifdef __cplusplus
 }

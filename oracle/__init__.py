@@ -103,6 +103,12 @@ def _declare(L):
     L.orc_mlp_forward.restype = _i32
     L.orc_mlp_backward.argtypes = [_i64, _p, _p, _p, _p, _p, _p, _p, _p, _i32, _p, _p, _p, _p, _p, _p, _p]
     L.orc_mlp_backward.restype = _i32
+    L.orc_tile_observe.argtypes = [_i32, _p, _p, _p, _p, _p, _i64, _p, _p, _p, _i32]
+    L.orc_tile_observe.restype = None
+    L.orc_tile_features.argtypes = [_i32, _p, _p, _p, _i32, _d, _d, _d, _d, _d, _i64, _p]
+    L.orc_tile_features.restype = None
+    L.orc_tile_refresh.argtypes = [_p, _p, _p, _i32, _i32]
+    L.orc_tile_refresh.restype = None
 
 
 def _c(a, dtype):
@@ -384,3 +390,40 @@ def mlp_backward(x, t, w, bf16=True):
                            int(bf16), _ptr(loss), _ptr(g["W1"]), _ptr(g["b1"]), _ptr(g["W2"]), _ptr(g["b2"]),
                            _ptr(g["W3"]), _ptr(g["b3"]))
     return float(loss[0]), g
+
+
+# ----------------------------------------------------------------------------
+# tile memory, features and refresh (tile-error predictor)
+# ----------------------------------------------------------------------------
+
+def tile_observe(n_active, active_tiles, pix_off, ranges, T_final, err_pix, iter_, mem, mem_iter, residual=False):
+    """Updates mem [T,4] (float64) and mem_iter [T] (int64) in place; returns
+    the targets [n_active]."""
+    L = lib()
+    at, po = _c(active_tiles, np.int32), _c(pix_off, np.int32)
+    rg = _c(ranges, np.int32)
+    Tf, ep = _c(T_final, np.float64), _c(err_pix, np.float64)
+    assert mem.dtype == np.float64 and mem.flags.c_contiguous and mem_iter.dtype == np.int64
+    tgt = np.zeros(max(int(n_active), 1))
+    L.orc_tile_observe(int(n_active), _ptr(at), _ptr(po), _ptr(rg), _ptr(Tf), _ptr(ep), int(iter_), _ptr(mem),
+                       _ptr(mem_iter), _ptr(tgt), 1 if residual else 0)
+    return tgt[:int(n_active)]
+
+
+def tile_features(mem, mem_iter, cam, rows=None, n_rows=None, view_cos=1.0, iter_=0):
+    L = lib()
+    W = int(cam["width"])
+    r = _c(rows, np.int32)
+    n = int(n_rows if n_rows is not None else (len(rows) if rows is not None else mem.shape[0]))
+    x = np.zeros((max(n, 1), 16))
+    L.orc_tile_features(n, _ptr(r), _ptr(_c(mem, np.float64)), _ptr(_c(mem_iter, np.int64)), W, float(cam["fx"]),
+                        float(cam["fy"]), float(cam["cx"]), float(cam["cy"]), float(view_cos), int(iter_), _ptr(x))
+    return x[:n]
+
+
+def tile_refresh(pred, err_f16_bits, width, height, base=None):
+    """Returns the refreshed error map (uint16 fp16 bit patterns)."""
+    L = lib()
+    e = np.array(err_f16_bits, dtype=np.uint16, copy=True, order="C")
+    L.orc_tile_refresh(_ptr(_c(pred, np.float64)), _ptr(_c(base, np.float64)), _ptr(e), int(width), int(height))
+    return e

@@ -1276,3 +1276,84 @@ int orc_mlp_backward(int64_t R, const double* x, const double* t, const double* 
   *loss = L;
   return 0;
 }
+
+/* ------------------------------------------------------------------------
+ * Tile memory, features and error-map refresh of the tile-error predictor
+ * (not in the paper; it refreshes a stale view's error map by rendering it,
+ * Sec. 3.3).  Written from their definitions.
+ * ---------------------------------------------------------------------- */
+
+/* For each active rank j < n_active: tile t = active_tiles[j] records
+ * (list length, mean T_final, mean err_pix over its sampled pixels, 1) and
+ * the iteration; target[j] = log(1 + mean err_pix), less the same of the
+ * tile's previous observation when residual and there was one. */
+void orc_tile_observe(int n_active, const int32_t* active_tiles, const int32_t* pix_off, const int32_t* ranges,
+                      const double* T_final, const double* err_pix, int64_t iter, double* mem, int64_t* mem_iter,
+                      double* target, int residual) {
+  for (int j = 0; j < n_active; ++j) {
+    int p0 = pix_off[j], p1 = pix_off[j + 1], n = p1 - p0 > 0 ? p1 - p0 : 1;
+    double st = 0.0, se = 0.0;
+    for (int p = p0; p < p1; ++p) {
+      st += T_final[p];
+      se += err_pix[p];
+    }
+    int t = active_tiles[j];
+    double prev = (residual && mem[4 * t + 3] > 0.0) ? log1p(mem[4 * t + 2]) : 0.0;
+    mem[4 * t + 0] = (double)(ranges[2 * j + 1] - ranges[2 * j]);
+    mem[4 * t + 1] = st / n;
+    mem[4 * t + 2] = se / n;
+    mem[4 * t + 3] = 1.0;
+    mem_iter[t] = iter;
+    if (target) target[j] = log1p(se / n) - prev;
+  }
+}
+
+/* Features of tile t: the angle between the optical axis and the ray through
+ * the tile centre (u, v) from the pinhole (fx, fy, cx, cy) enters as its
+ * cosine. */
+void orc_tile_features(int n_rows, const int32_t* rows, const double* mem, const int64_t* mem_iter, int width,
+                       double fx, double fy, double cx, double cy, double view_cos, int64_t iter, double* x) {
+  int tx = (width + 15) / 16;
+  for (int r = 0; r < n_rows; ++r) {
+    int t = rows ? rows[r] : r;
+    double* f = x + 16 * (size_t)r;
+    for (int k = 0; k < 16; ++k) f[k] = 0.0;
+    int seen = mem[4 * t + 3] > 0.0;
+    double age = seen ? (double)(iter - mem_iter[t] > 0 ? iter - mem_iter[t] : 0) : 1e6;
+    double u = ((t % tx) * 16 + 8 - cx) / fx, v = ((t / tx) * 16 + 8 - cy) / fy;
+    f[0] = log1p(mem[4 * t + 0]);
+    f[1] = seen ? mem[4 * t + 1] : 1.0;
+    f[2] = log1p(mem[4 * t + 2]);
+    f[3] = view_cos;
+    f[4] = log1p(age);
+    f[5] = cos(atan(sqrt(u * u + v * v)));
+    f[6] = seen ? 1.0 : 0.0;
+  }
+}
+
+/* Each tile's fp16 error values scaled so their mean is exp(p) - 1,
+ * p = pred (+ the tile's feature 2 from base, when predictions are residuals),
+ * clamped at 0 below; a tile of mean 0 takes the prediction
+ * everywhere.  Values are rounded to fp16 (nearest even). */
+void orc_tile_refresh(const double* pred, const double* base, uint16_t* err, int width, int height) {
+  int tx = (width + 15) / 16, ty = (height + 15) / 16;
+  for (int t = 0; t < tx * ty; ++t) {
+    int x0 = (t % tx) * 16, y0 = (t / tx) * 16;
+    double s = 0.0;
+    int n = 0;
+    for (int y = y0; y < y0 + 16 && y < height; ++y)
+      for (int x = x0; x < x0 + 16 && x < width; ++x) {
+        s += orc_half_to_double(err[(size_t)y * width + x]);
+        ++n;
+      }
+    double mean = s / (n > 0 ? n : 1);
+    double p = pred[t] + (base ? base[16 * (size_t)t + 2] : 0.0);
+    double want = expm1(p > 0.0 ? p : 0.0);
+    for (int y = y0; y < y0 + 16 && y < height; ++y)
+      for (int x = x0; x < x0 + 16 && x < width; ++x) {
+        size_t k = (size_t)y * width + x;
+        double e = orc_half_to_double(err[k]);
+        err[k] = orc_double_to_half(mean > 0.0 ? e * (want / mean) : want);
+      }
+  }
+}

@@ -160,7 +160,13 @@ _lib.tgs_mlp_forward.argtypes = [_P(Mlp), _i64, _p, _p, _p, _p, _p]
 _lib.tgs_mlp_backward_workspace_size.restype = _sz
 _lib.tgs_mlp_backward_workspace_size.argtypes = [_i64]
 _lib.tgs_mlp_backward.restype = _i32
-_lib.tgs_mlp_backward.argtypes = [_P(Mlp), _i64, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]
+_lib.tgs_mlp_backward.argtypes = [_P(Mlp), _i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]
+_lib.tgs_tile_observe.restype = _i32
+_lib.tgs_tile_observe.argtypes = [_p, _p, _i32, _p, _p, _p, _p, _u64, _p, _p, _p, _p, _i32, _p]
+_lib.tgs_tile_features.restype = _i32
+_lib.tgs_tile_features.argtypes = [_p, _p, _p, _p, _i32, _P(Camera), C.c_float, _u64, _p, _p, _p]
+_lib.tgs_tile_refresh.restype = _i32
+_lib.tgs_tile_refresh.argtypes = [_p, _p, _p, _i32, _i32, _p]
 _lib.tgs_mlp_adam.restype = _i32
 _lib.tgs_mlp_adam.argtypes = [_p, _p, _p, _p, _i32, C.c_float, C.c_float, C.c_float, C.c_float, _p, _p, _p, _p]
 
@@ -175,7 +181,7 @@ EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_devi
             "tgs_render_batched_resident", "tgs_render_sampled_batched",
             "tgs_render_backward_batched", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step",
             "tgs_mlp_param_count", "tgs_mlp_forward", "tgs_mlp_backward_workspace_size", "tgs_mlp_backward",
-            "tgs_mlp_adam"]
+            "tgs_mlp_adam", "tgs_tile_observe", "tgs_tile_features", "tgs_tile_refresh"]
 
 
 def _check(fn, status):
@@ -474,16 +480,42 @@ def mlp_backward_workspace_size(rows: int) -> int:
     return int(_lib.tgs_mlp_backward_workspace_size(int(rows)))
 
 
-def mlp_backward(net: dict, x, h1, h2, y, target, grads, loss, workspace=None, stream=None):
+def mlp_backward(net: dict, x, h1, h2, y, target, grads, loss, workspace=None, stream=None, rows_dev=None):
     m = mlp_struct(net)
     if workspace is None:
         workspace = torch.empty(mlp_backward_workspace_size(x.shape[0]), dtype=torch.uint8, device=x.device)
-    _check("tgs_mlp_backward", _lib.tgs_mlp_backward(C.byref(m), int(x.shape[0]), _ptr(x), _ptr(h1), _ptr(h2),
-                                                     _ptr(y), _ptr(target), _ptr(grads), _ptr(loss), _ptr(workspace),
-                                                     workspace.numel(), _stream(stream)))
+    _check("tgs_mlp_backward", _lib.tgs_mlp_backward(C.byref(m), int(x.shape[0]), _ptr(rows_dev), _ptr(x), _ptr(h1),
+                                                     _ptr(h2), _ptr(y), _ptr(target), _ptr(grads), _ptr(loss),
+                                                     _ptr(workspace), workspace.numel(), _stream(stream)))
 
 
 def mlp_adam(params, grads, m, v, step, lr, beta1, beta2, eps, net: dict, stream=None):
     _check("tgs_mlp_adam", _lib.tgs_mlp_adam(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(step), float(lr),
                                              float(beta1), float(beta2), float(eps), _ptr(net["w1"]),
                                              _ptr(net["w2"]), _ptr(net["w3"]), _stream(stream)))
+
+
+# ----------------------------------------------------------------------------
+# tile memory and features of the tile-error predictor
+# ----------------------------------------------------------------------------
+
+def tile_observe(active_tiles, n_active, n_active_max, pix_off, tile_ranges, T_final, err_pix, mem, mem_iter,
+                 target=None, it=0, iter_dev=None, residual=False, stream=None):
+    _check("tgs_tile_observe", _lib.tgs_tile_observe(
+        _ptr(active_tiles), _ptr(n_active), int(n_active_max), _ptr(pix_off), _ptr(tile_ranges), _ptr(T_final),
+        _ptr(err_pix), int(it) & (2**64 - 1), _ptr(iter_dev), _ptr(mem), _ptr(mem_iter), _ptr(target),
+        1 if residual else 0, _stream(stream)))
+
+
+def tile_features(mem, mem_iter, cam, x, rows=None, n_rows=None, n_rows_max=None, view_cos=1.0, it=0,
+                  iter_dev=None, stream=None):
+    cc = cam if isinstance(cam, Camera) else camera(cam)
+    nmax = int(n_rows_max if n_rows_max is not None else x.shape[0])
+    _check("tgs_tile_features", _lib.tgs_tile_features(
+        _ptr(mem), _ptr(mem_iter), _ptr(rows), _ptr(n_rows), nmax, C.byref(cc), float(view_cos),
+        int(it) & (2**64 - 1), _ptr(iter_dev), _ptr(x), _stream(stream)))
+
+
+def tile_refresh(pred, err_map, width, height, base=None, stream=None):
+    _check("tgs_tile_refresh", _lib.tgs_tile_refresh(_ptr(pred), _ptr(base), _ptr(err_map), int(width), int(height),
+                                                     _stream(stream)))

@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(128) k_mlp_forward(MlpK w, const float* __rest
 __global__ void __launch_bounds__(128) k_mlp_backward_act(MlpK w, const uint16_t* __restrict__ h1,
                                                           const uint16_t* __restrict__ h2,
                                                           const float* __restrict__ y, const float* __restrict__ t,
-                                                          int64_t R, float* __restrict__ dy_out,
+                                                          int64_t R, const int32_t* __restrict__ R_dev,
+                                                          float* __restrict__ dy_out,
                                                           uint16_t* __restrict__ dh2_out,
                                                           uint16_t* __restrict__ dh1_out, double* __restrict__ loss) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -195,12 +196,15 @@ __global__ void __launch_bounds__(128) k_mlp_backward_act(MlpK w, const uint16_t
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, tq = lane & 3;
   const int64_t tiles = (R + 15) / 16;
+  // rows past Re are padding: no error, no gradient
+  const int64_t Re = R_dev ? (*R_dev > 0 ? (*R_dev < R ? (int64_t)*R_dev : R) : 0) : R;
+  const float inv = Re > 0 ? 1.f / (float)Re : 0.f;
   double lsum = 0.0;
   for (int64_t tile = (int64_t)blockIdx.x * 4 + warp; tile < tiles; tile += (int64_t)gridDim.x * 4) {
     const int64_t row0 = tile * 16, r_lo = row0 + g, r_hi = row0 + g + 8;
-    const float e_lo = r_lo < R ? y[r_lo] - t[r_lo] : 0.f, e_hi = r_hi < R ? y[r_hi] - t[r_hi] : 0.f;
-    if (tq == 0) lsum += 0.5 * ((double)e_lo * e_lo + (double)e_hi * e_hi) / (double)R;
-    const float dy_lo = e_lo / (float)R, dy_hi = e_hi / (float)R;
+    const float e_lo = r_lo < Re ? y[r_lo] - t[r_lo] : 0.f, e_hi = r_hi < Re ? y[r_hi] - t[r_hi] : 0.f;
+    if (tq == 0) lsum += 0.5 * ((double)e_lo * e_lo + (double)e_hi * e_hi) * (double)inv;
+    const float dy_lo = e_lo * inv, dy_hi = e_hi * inv;
     if (tq == 0) {
       if (r_lo < R) dy_out[r_lo] = dy_lo;
       if (r_hi < R) dy_out[r_hi] = dy_hi;
@@ -360,7 +364,8 @@ extern "C" size_t tgs_mlp_backward_workspace_size(int64_t rows) {
   return align_up(R * 4, 256) + 2 * align_up(R * MH * 2, 256);
 }
 
-extern "C" tgs_status tgs_mlp_backward(const tgs_mlp* w, int64_t rows, const float* x, const uint16_t* h1,
+extern "C" tgs_status tgs_mlp_backward(const tgs_mlp* w, int64_t rows, const int32_t* rows_dev, const float* x,
+                                       const uint16_t* h1,
                                        const uint16_t* h2, const float* y, const float* target, float* grads,
                                        double* loss, void* workspace, size_t workspace_bytes, tgs_stream stream) {
   if (!mlp_ok(w) || rows < 0 || !grads || !loss) return TGS_ERR_INVALID_ARG;
@@ -382,7 +387,8 @@ extern "C" tgs_status tgs_mlp_backward(const tgs_mlp* w, int64_t rows, const flo
     cudaFuncSetAttribute(k_mlp_backward_act, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr[dev] = true;
   }
-  k_mlp_backward_act<<<mlp_grid(rows), 128, smem, s>>>(mlp_k(w), h1, h2, y, target, rows, dy, dh2, dh1, loss);
+  k_mlp_backward_act<<<mlp_grid(rows), 128, smem, s>>>(mlp_k(w), h1, h2, y, target, rows, rows_dev, dy, dh2, dh1,
+                                                        loss);
   dim3 gg(MH, (unsigned)((rows + kGradRows - 1) / kGradRows));
   k_mlp_wgrad<<<gg, 128, 0, s>>>(x, h1, h2, dy, dh2, dh1, rows, grads);
   return check_launch();

@@ -244,9 +244,10 @@ class Trainer:
         return self.stage_graphs
 
     # ------------------------------------------------------------------ maps
-    def init_error_map(self):
+    def init_error_map(self, on_dense=None):
         """E_v from a dense evaluation of the current Gaussians (Sec. 3.3):
-        every tile and pixel rendered once, E = e, A = 0.  Returns the loss."""
+        every tile and pixel rendered once, E = e, A = 0.  Returns the loss.
+        on_dense(d) (optional) sees the dense evaluation after its loss."""
         d = self if self.dense else Trainer(self.params, self.cam, self.target, cfg=self.cfg, dense=True,
                                             seed=self.seed, bg=self.bg, sh_degree=self.sh_degree, view=self.view,
                                             train=False)
@@ -256,6 +257,8 @@ class Trainer:
         d.loss_params = (saved[0], saved[1], 1.0)
         d.loss_and_maps()
         d.loss_params = saved
+        if on_dense is not None:
+            on_dense(d)
         self.age_map.zero_()
         return float(d.loss.item())
 

@@ -71,15 +71,141 @@ class TileErrorMLP:
         B.mlp_forward(self.net(), x.contiguous(), y)
         return y
 
-    def train_step(self, x: torch.Tensor, target: torch.Tensor) -> torch.Tensor:
-        """One Adam step on mean (y - t)^2 / 2; returns the loss (device)."""
+    def train_step(self, x: torch.Tensor, target: torch.Tensor, rows_dev=None) -> torch.Tensor:
+        """One Adam step on mean (y - t)^2 / 2 over the first rows_dev rows (all
+        when None); returns the loss of the batch before the step (device)."""
         R = x.shape[0]
         x = x.contiguous()
         y = torch.empty(R, device=x.device)
         h1 = torch.empty(R, HID, dtype=torch.int16, device=x.device)
         h2 = torch.empty(R, HID, dtype=torch.int16, device=x.device)
         B.mlp_forward(self.net(), x, y, h1, h2)
-        B.mlp_backward(self.net(), x, h1, h2, y, target.contiguous(), self.grads, self.loss)
+        B.mlp_backward(self.net(), x, h1, h2, y, target.contiguous(), self.grads, self.loss, rows_dev=rows_dev)
         self.step_count += 1
         B.mlp_adam(self.params, self.grads, self.m, self.v, self.step_count, self.lr, 0.9, 0.999, 1e-8, self.net())
         return self.loss
+
+
+class TileMemory:
+    """What one view last observed in each of its tiles (list length, mean
+    final transmittance, mean error, iteration), kept on the device."""
+
+    def __init__(self, n_tiles: int, device):
+        self.mem = torch.zeros(n_tiles, 4, device=device)
+        self.it = torch.zeros(n_tiles, dtype=torch.int64, device=device)
+
+
+class TileErrorPredictor:
+    """Online-trained tile-error predictor for a set of views.
+
+    After each step's loss, ``observe_and_train`` forms the features of the
+    step's active tiles from the view's tile memory as it was, records the new
+    observations and takes one training step.  The network predicts a tile's
+    log(1 + mean error) now; with residual=True it predicts instead the change
+    since the tile's last observation, added to that stale value.  ``refresh`` brings a stale
+    view's error map up to date before its next selection: with the network's
+    predictions when its recent error (the loss of each batch before it was
+    trained on, smoothed) is below ``max_mse``, otherwise with the plain
+    refresh - a dense render of the view (Sec. 3.3), which is also what judges
+    the network (``judge``)."""
+
+    def __init__(self, device="cuda", seed: int = 0, lr: float = 1e-3, max_mse: float = 0.02,
+                 min_batches: int = 50, residual: bool = False):
+        self.mlp = TileErrorMLP(device, seed, lr)
+        self.residual = residual
+        self.device = device
+        self.memories = {}
+        self.max_mse, self.min_batches = max_mse, min_batches
+        self.batches = 0
+        self.recent_mse = None
+        self.refreshes = {"predicted": 0, "plain": 0}
+
+    def memory(self, tr) -> TileMemory:
+        if tr.view not in self.memories:
+            self.memories[tr.view] = TileMemory(tr.T, self.device)
+        return self.memories[tr.view]
+
+    def init_view(self, tr, it: int = 0) -> float:
+        """The plain initial refresh of a view (dense evaluation), also filling
+        its tile memory; returns the loss."""
+        mem = self.memory(tr)
+        return tr.init_error_map(on_dense=lambda d: B.tile_observe(
+            d.active_tiles, d.n_active, d.n_select, d.pix_off, d.ranges, d.T_final, d.err_pix, mem.mem, mem.it,
+            None, it=it))
+
+    def observe_and_train(self, tr, it: int, view_cos: float = 1.0, train: bool = True):
+        mem = self.memory(tr)
+        A = tr.n_select
+        x = torch.empty(A, 16, device=self.device)
+        target = torch.empty(A, device=self.device)
+        B.tile_features(mem.mem, mem.it, tr.ccam, x, rows=tr.active_tiles, n_rows=tr.n_active, n_rows_max=A,
+                        view_cos=view_cos, it=it)
+        B.tile_observe(tr.active_tiles, tr.n_active, A, tr.pix_off, tr.ranges, tr.T_final, tr.err_pix, mem.mem,
+                       mem.it, target, it=it, residual=self.residual)
+        if train:
+            loss = self.mlp.train_step(x, target, rows_dev=tr.n_active)
+            mse = 2.0 * float(loss.item())
+            self.batches += 1
+            self.recent_mse = mse if self.recent_mse is None else 0.9 * self.recent_mse + 0.1 * mse
+
+    def features(self, tr, it: int, view_cos: float = 1.0) -> torch.Tensor:
+        mem = self.memory(tr)
+        x = torch.empty(tr.T, 16, device=self.device)
+        B.tile_features(mem.mem, mem.it, tr.ccam, x, n_rows_max=tr.T, view_cos=view_cos, it=it)
+        return x
+
+    def predict(self, tr, it: int, view_cos: float = 1.0) -> torch.Tensor:
+        """Predicted log(1 + mean error) of every tile of the view [T]."""
+        x = self.features(tr, it, view_cos)
+        r = self.mlp.predict(x)
+        return r + x[:, 2] if self.residual else r
+
+    def trusted(self) -> bool:
+        return self.batches >= self.min_batches and self.recent_mse is not None and self.recent_mse <= self.max_mse
+
+    def refresh(self, tr, it: int, view_cos: float = 1.0) -> str:
+        if self.trusted():
+            x = self.features(tr, it, view_cos)
+            B.tile_refresh(self.mlp.predict(x), tr.err_map, tr.W, tr.H, base=x if self.residual else None)
+            self.refreshes["predicted"] += 1
+            return "predicted"
+        self.init_view(tr, it)
+        self.refreshes["plain"] += 1
+        return "plain"
+
+    def judge(self, tr, it: int, view_cos: float = 1.0) -> dict:
+        """Scores the predictions for a view against a dense evaluation (the
+        plain refresh) without changing the view's state: mean squared error
+        of log(1 + tile error), and the same for the view's current error map."""
+        from .pipeline import Trainer
+        pred = self.predict(tr, it, view_cos)
+        d = Trainer(tr.params, tr.cam, tr.target, cfg=tr.cfg, dense=True, seed=tr.seed, bg=tr.bg,
+                    sh_degree=tr.sh_degree, view=tr.view, train=False)
+        d.forward()
+        d.loss_and_maps()
+        truth = torch.zeros(tr.T, device=self.device)
+        A = int(d.n_active.item())
+        off = d.pix_off[:A + 1].long()
+        cnt = (off[1:] - off[:-1]).clamp(min=1).float()
+        seg = torch.repeat_interleave(torch.arange(A, device=self.device), off[1:] - off[:-1])
+        truth.index_add_(0, d.active_tiles[:A].long()[seg], d.err_pix[:int(off[-1])])
+        truth[d.active_tiles[:A].long()] /= cnt
+        lt = torch.log1p(truth)
+        stale = tile_means(tr.err_map, tr.W, tr.H)
+        return dict(mse_pred=float(((pred - lt) ** 2).mean().item()),
+                    mse_stale=float(((torch.log1p(stale) - lt) ** 2).mean().item()),
+                    truth=lt, pred=pred, stale=torch.log1p(stale))
+
+
+def tile_means(err_map: torch.Tensor, W: int, H: int) -> torch.Tensor:
+    """Per-tile mean of an fp16 error map (bit patterns in int16), [T]."""
+    from .config import TILE
+    e = err_map.view(torch.float16).float()
+    ty, tx = (H + TILE - 1) // TILE, (W + TILE - 1) // TILE
+    pad = torch.zeros(ty * TILE, tx * TILE, device=e.device)
+    ones = torch.zeros_like(pad)
+    pad[:H, :W] = e
+    ones[:H, :W] = 1.0
+    s = pad.view(ty, TILE, tx, TILE).sum((1, 3))
+    c = ones.view(ty, TILE, tx, TILE).sum((1, 3))
+    return (s / c).reshape(-1)
