@@ -436,6 +436,7 @@ def run_ours(args):
     e2e_v, h2d, d2h = e2e_replays(sampled, tgt_host, args.steps)
     res["e2e"] = {"value": e2e_v * world, "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
     res["quality"] = {"psnr_init_db": psnr(sampled.render_image(), target)}
+    res["mlp"] = mlp_bench(device, peaks)
     if rank == 0 and not args.no_cpu:
         res["cpu_baseline"] = cpu_baseline(cam, g_np, target.cpu().numpy())
     if dist is not None:
@@ -546,6 +547,56 @@ def run_batched(args):
            "peak_source": peak_kind, **out,
            "speedup_vs_per_view": out["per_view"]["ms_per_step"] / out["persistent"]["ms_per_step"]}
     print(json.dumps(res))
+
+
+MLP_ROWS = 200 * 8487   # tile rows of a 200-view orbit at 1957x1091
+
+
+def mlp_bench(device, peaks, steps: int = 10) -> dict:
+    """The tile-error MLP's forward and training step over one row per tile of
+    a 200-view set, against the bf16 tensor peak: 2 (16*128 + 128*128 + 128)
+    FLOPs per row forward, twice that more for the backward."""
+    import torch
+    from paper_2606_15924_gb300 import binding as B
+    from paper_2606_15924_gb300.predictor import TileErrorMLP, HID
+    R = MLP_ROWS
+    mlp = TileErrorMLP(device)
+    g = torch.Generator(device="cpu").manual_seed(4)
+    x = torch.randn(R, 16, generator=g).to(device)
+    t = torch.randn(R, generator=g).to(device)
+    y = torch.empty(R, device=device)
+    h1 = torch.empty(R, HID, dtype=torch.int16, device=device)
+    h2 = torch.empty(R, HID, dtype=torch.int16, device=device)
+    ws = torch.empty(B.mlp_backward_workspace_size(R), dtype=torch.uint8, device=device)
+
+    def fwd():
+        B.mlp_forward(mlp.net(), x, y, h1, h2)
+
+    def train():
+        fwd()
+        B.mlp_backward(mlp.net(), x, h1, h2, y, t, mlp.grads, mlp.loss, workspace=ws)
+        B.mlp_adam(mlp.params, mlp.grads, mlp.m, mlp.v, 1, 1e-4, 0.9, 0.999, 1e-8, mlp.net())
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(steps):
+            fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / steps
+    f_ms, t_ms = timed(fwd), timed(train)
+    flop = 2.0 * R * (16 * 128 + 128 * 128 + 128)
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    return {"rows": R, "forward_ms": f_ms, "train_step_ms": t_ms,
+            "forward_roofline": {"bound": "tensor", "achieved": flop / (f_ms * 1e-3) / 1e12, "peak": peak,
+                                 "unit": "TFLOP/s", "frac": flop / (f_ms * 1e-3) / 1e12 / peak,
+                                 "note": "bf16 mma.sync, fp32 accumulate; peak = measured cuBLAS bf16 (burst)"},
+            "train_roofline": {"achieved": 3 * flop / (t_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                               "frac": 3 * flop / (t_ms * 1e-3) / 1e12 / peak}}
 
 
 def run_quality(args):
