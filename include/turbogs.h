@@ -255,6 +255,9 @@ typedef struct {
   int32_t n_slots;
   int64_t stride;
   const float* rgb;
+  int32_t* tile_last;  /* nullable [n_active_max]: per active rank, the longest
+                          blended run of its pixels (written by the forward, lets
+                          the backward skip empty pieces without reading n_last) */
 } tgs_checkpoints;
 
 size_t tgs_checkpoint_bytes(int32_t n_active_max, int32_t n_pix_max, int32_t n_slots);
@@ -386,7 +389,11 @@ tgs_status tgs_project_backward_multi(const tgs_gaussians* g, int32_t n_views, c
  * int32, reset by the call) until none are left; each item is rendered
  * exactly as render_sampled / backward_sampled render it.  Up to 16 views.
  * Per view: the fields of render_sampled; the backward also reads dL_drgb
- * and writes grad2d [n_gaussians, 12] (zeroed by the call).
+ * and writes grad2d [n_gaussians, 12] (zeroed by the call).  With checkpoints
+ * (ckpt.data, rgb = the view's rgb output) the forward stores them and the
+ * backward replays every tile in pieces as backward_sampled does; the
+ * checkpoint interval is the batch's block size (the largest n_pix_max of
+ * the views, rounded up to a multiple of 32).
  */
 typedef struct {
   tgs_projected proj;
@@ -406,6 +413,7 @@ typedef struct {
   const float* dL_drgb;
   float* grad2d;
   int64_t n_gaussians;
+  tgs_checkpoints ckpt;  /* n_slots = 0: none; else the same n_slots in every view */
 } tgs_view_batch;
 
 /* Advances the device-side iteration counters of a captured step by one

@@ -35,7 +35,7 @@ class MultiViewTrainer:
     def __init__(self, params: dict, cams: list, targets: list, tile_fractions: list,
                  pixel_rate: float = 1.0 / 3.0, cfg: Config | None = None, seed: int = 0, bg=(0.0, 0.0, 0.0),
                  sh_degree: int = 3, view_ids: list | None = None, grid: tuple | None = None,
-                 view_rows: bool | None = None, persistent: bool = True):
+                 view_rows: bool | None = None, persistent: bool = True, checkpoints: bool | None = None):
         if not (1 <= len(cams) <= 16) or len(cams) != len(targets) or len(cams) != len(tile_fractions):
             raise ValueError("1 to 16 views, one target and one tile fraction each")
         self.cfg = cfg or Config()
@@ -75,6 +75,19 @@ class MultiViewTrainer:
         self.persistent = bool(persistent)
         self.counters = torch.zeros(2 + 2 * self.K, dtype=torch.int32, device=dev)
         self.n_pix_max = max(v.n_pix for v in self.views)
+        # checkpoints for the split backward, every CKPT_POSITIONS / block size
+        # list positions (the batch's block size is its interval)
+        blk = min(256, max(32, (self.n_pix_max + 31) // 32 * 32))
+        if checkpoints is None:  # split only when the views' tiles cannot fill the GPU
+            checkpoints = sum(v.n_select for v in self.views) < 4 * B.render_batched_resident(self.n_pix_max, True)
+        self.ck_slots = max(1, Trainer.CKPT_POSITIONS // blk) if checkpoints else 0
+        for v in self.views:
+            if self.ck_slots:
+                v.ck_data = torch.empty(B.checkpoint_bytes(v.n_select, v.n_pix, self.ck_slots) // 4, device=dev)
+                v.ck_last = torch.zeros(v.n_select, dtype=torch.int32, device=dev)
+                v.ckpt = B.checkpoints(v.ck_data, self.ck_slots, v.n_select * v.n_pix, v.rgb, v.ck_last)
+            else:
+                v.ckpt = None
         res_f = B.render_batched_resident(self.n_pix_max, False)
         res_b = B.render_batched_resident(self.n_pix_max, True)
         self.resident = (res_f, res_b)
@@ -87,7 +100,8 @@ class MultiViewTrainer:
         for v in self.views:
             d = dict(proj=v.proj, tile_ranges=v.ranges, vals=v.vals, active_tiles=v.active_tiles,
                      n_active=v.n_active, n_active_max=v.n_select, pix_off=v.pix_off, pix_idx=v.pix_idx,
-                     n_pix_max=v.n_pix, cam=v.ccam, bg=v.bg, rgb=v.rgb, T_final=v.T_final, n_last=v.n_last)
+                     n_pix_max=v.n_pix, cam=v.ccam, bg=v.bg, rgb=v.rgb, T_final=v.T_final, n_last=v.n_last,
+                     ckpt=v.ckpt)
             fwd.append(dict(d))
             d.update(dL_drgb=v.dL, grad2d=v.grad2d)
             bwd.append(d)
@@ -125,7 +139,7 @@ class MultiViewTrainer:
             B.render_backward_batched(self.bwd_batch, self.grid[1], self.counters[1:2])
         else:
             for k, v in enumerate(self.views):
-                B.render_backward_batched(self.bwd_single[k], max(1, v.n_select),
+                B.render_backward_batched(self.bwd_single[k], max(1, v.n_select * (self.ck_slots + 1)),
                                           self.counters[2 + self.K + k:3 + self.K + k])
 
     # ------------------------------------------------------------------ step

@@ -72,16 +72,18 @@ class Mlp(C.Structure):
                 ("b3", C.c_void_p)]
 
 
+class Checkpoints(C.Structure):
+    _fields_ = [("data", C.c_void_p), ("n_slots", C.c_int32), ("stride", C.c_int64), ("rgb", C.c_void_p),
+                ("tile_last", C.c_void_p)]
+
+
 class ViewBatch(C.Structure):
     _fields_ = [("proj", Projected), ("tile_ranges", C.c_void_p), ("vals", C.c_void_p),
                 ("active_tiles", C.c_void_p), ("n_active", C.c_void_p), ("n_active_max", C.c_int32),
                 ("pix_off", C.c_void_p), ("pix_idx", C.c_void_p), ("n_pix_max", C.c_int32), ("cam", Camera),
                 ("bg", C.c_float * 3), ("rgb", C.c_void_p), ("T_final", C.c_void_p), ("n_last", C.c_void_p),
-                ("dL_drgb", C.c_void_p), ("grad2d", C.c_void_p), ("n_gaussians", C.c_int64)]
-
-
-class Checkpoints(C.Structure):
-    _fields_ = [("data", C.c_void_p), ("n_slots", C.c_int32), ("stride", C.c_int64), ("rgb", C.c_void_p)]
+                ("dL_drgb", C.c_void_p), ("grad2d", C.c_void_p), ("n_gaussians", C.c_int64),
+                ("ckpt", Checkpoints)]
 
 
 class Opt(C.Structure):
@@ -299,10 +301,10 @@ def checkpoint_bytes(n_active_max: int, n_pix_max: int, n_slots: int) -> int:
     return int(_lib.tgs_checkpoint_bytes(int(n_active_max), int(n_pix_max), int(n_slots)))
 
 
-def checkpoints(data, n_slots: int, stride: int, rgb) -> Checkpoints:
+def checkpoints(data, n_slots: int, stride: int, rgb, tile_last=None) -> Checkpoints:
     """data: float32 device tensor of checkpoint_bytes(...) / 4 elements; rgb:
-    the forward's rgb output tensor."""
-    return Checkpoints(_ptr(data), int(n_slots), int(stride), _ptr(rgb))
+    the forward's rgb output tensor; tile_last: optional int32 [n_active_max]."""
+    return Checkpoints(_ptr(data), int(n_slots), int(stride), _ptr(rgb), _ptr(tile_last))
 
 
 def _ck(ckpt):
@@ -401,7 +403,8 @@ def project_backward_multi(g: dict, adj: MultiAdjoint, grads: dict, touched, wri
 def view_batch(views: list) -> C.Array:
     """views: dicts with the per-view fields of tgs_view_batch (proj, tile_ranges,
     vals, active_tiles, n_active, n_active_max, pix_off, pix_idx, n_pix_max, cam,
-    bg, rgb, T_final, n_last and, for the backward, dL_drgb, grad2d)."""
+    bg, rgb, T_final, n_last, optionally ckpt (a Checkpoints) and, for the
+    backward, dL_drgb, grad2d)."""
     arr = (ViewBatch * len(views))()
     for k, w in enumerate(views):
         b = arr[k]
@@ -415,6 +418,8 @@ def view_batch(views: list) -> C.Array:
         b.rgb, b.T_final, b.n_last = _ptr(w["rgb"]), _ptr(w["T_final"]), _ptr(w["n_last"])
         b.dL_drgb, b.grad2d = _ptr(w.get("dL_drgb")), _ptr(w.get("grad2d"))
         b.n_gaussians = int(w["grad2d"].shape[0]) if w.get("grad2d") is not None else 0
+        if w.get("ckpt") is not None:
+            b.ckpt = w["ckpt"]
     return arr
 
 

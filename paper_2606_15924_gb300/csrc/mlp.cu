@@ -266,42 +266,90 @@ __global__ void __launch_bounds__(128) k_mlp_backward_act(MlpK w, const uint16_t
   if (lane == 0 && lsum != 0.0) atomicAdd(loss, lsum);
 }
 
-// Backward, part 2: weight gradients, sums over rows of outer products.
-// Block (out row j, row chunk): thread k accumulates dW[j][k] over the chunk.
-constexpr int kGradRows = 256;
+// Backward, part 2: weight gradients, sums over rows of outer products.  A
+// block takes a chunk of rows, stages kWgRows of them at a time in shared
+// memory (each row read once), and every thread accumulates a fixed set of
+// weights in registers: thread t owns dW2[t / 2][64 (t % 2) ... + 63],
+// dW1[t / 2][8 (t % 2) ... + 7], the biases of unit t / 2 (even t) and dW3[t]
+// (t < 128).  One atomic flush per block and weight.
+constexpr int kWgThreads = 256;
+constexpr int kWgRows = 32;
 
-__global__ void __launch_bounds__(128) k_mlp_wgrad(const float* __restrict__ x, const uint16_t* __restrict__ h1,
-                                                   const uint16_t* __restrict__ h2, const float* __restrict__ dy,
-                                                   const uint16_t* __restrict__ dh2, const uint16_t* __restrict__ dh1,
-                                                   int64_t R, float* __restrict__ grads) {
-  const int j = blockIdx.x;  // output unit of layers 1 and 2
-  const int k = threadIdx.x; // input unit (layer 2), and of layer 1 when < 16
-  const int64_t r0 = (int64_t)blockIdx.y * kGradRows, r1 = min(R, r0 + kGradRows);
-  float gw2 = 0.f, gw1 = 0.f, gb2 = 0.f, gb1 = 0.f, gw3 = 0.f, gb3 = 0.f;
-  for (int64_t r = r0; r < r1; ++r) {
-    const float d2 = __uint_as_float((uint32_t)dh2[r * MH + j] << 16);
-    const float d1 = __uint_as_float((uint32_t)dh1[r * MH + j] << 16);
-    gw2 += d2 * __uint_as_float((uint32_t)h1[r * MH + k] << 16);
-    if (k < MI) gw1 += d1 * round_bf16(x[r * MI + k]);
-    if (k == 0) {
-      gb2 += d2;
-      gb1 += d1;
+__global__ void __launch_bounds__(kWgThreads) k_mlp_wgrad(const float* __restrict__ x,
+                                                          const uint16_t* __restrict__ h1,
+                                                          const uint16_t* __restrict__ h2,
+                                                          const float* __restrict__ dy,
+                                                          const uint16_t* __restrict__ dh2,
+                                                          const uint16_t* __restrict__ dh1, int64_t R,
+                                                          int64_t chunk, float* __restrict__ grads) {
+  __shared__ __align__(16) uint16_t s_h1[kWgRows][MH];
+  __shared__ __align__(16) uint16_t s_h2[kWgRows][MH];
+  __shared__ __align__(16) uint16_t s_d2[kWgRows][MH];
+  __shared__ __align__(16) uint16_t s_d1[kWgRows][MH];
+  __shared__ float s_x[kWgRows][MI];
+  __shared__ float s_dy[kWgRows];
+  const int t = threadIdx.x, j = t >> 1, half = t & 1;
+  const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = min(R, r0 + chunk);
+  float a2[64], a1[8];
+#pragma unroll
+  for (int k = 0; k < 64; ++k) a2[k] = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a1[k] = 0.f;
+  float b1 = 0.f, b2 = 0.f, w3 = 0.f, b3 = 0.f;
+  auto bf = [](uint32_t bits16) { return __uint_as_float(bits16 << 16); };
+  for (int64_t rb = r0; rb < r1; rb += kWgRows) {
+    const int n = r1 - rb < kWgRows ? (int)(r1 - rb) : kWgRows;
+    __syncthreads();
+    // stage the rows: 16-byte loads of the bf16 rows, scalar for x and dy
+    for (int i = t; i < kWgRows * (MH / 8); i += kWgThreads) {
+      const int r = i / (MH / 8), c = (i % (MH / 8)) * 8;
+      uint4 z = make_uint4(0u, 0u, 0u, 0u);
+      const bool in = r < n;
+      const size_t g = (size_t)(rb + r) * MH + c;
+      *reinterpret_cast<uint4*>(&s_h1[r][c]) = in ? *reinterpret_cast<const uint4*>(h1 + g) : z;
+      *reinterpret_cast<uint4*>(&s_h2[r][c]) = in ? *reinterpret_cast<const uint4*>(h2 + g) : z;
+      *reinterpret_cast<uint4*>(&s_d2[r][c]) = in ? *reinterpret_cast<const uint4*>(dh2 + g) : z;
+      *reinterpret_cast<uint4*>(&s_d1[r][c]) = in ? *reinterpret_cast<const uint4*>(dh1 + g) : z;
     }
-    if (j == 0) {
-      gw3 += dy[r] * __uint_as_float((uint32_t)h2[r * MH + k] << 16);
-      if (k == 0) gb3 += dy[r];
+    for (int i = t; i < kWgRows * MI; i += kWgThreads) {
+      const int r = i / MI, c = i % MI;
+      s_x[r][c] = r < n ? round_bf16(x[(size_t)(rb + r) * MI + c]) : 0.f;
+    }
+    if (t < kWgRows) s_dy[t] = t < n ? dy[rb + t] : 0.f;
+    __syncthreads();
+    for (int r = 0; r < n; ++r) {
+      const float d2 = bf(s_d2[r][j]), d1 = bf(s_d1[r][j]);
+      const uint4* hp = reinterpret_cast<const uint4*>(&s_h1[r][64 * half]);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const uint4 v = hp[q];
+        const uint32_t u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          a2[8 * q + 2 * e] += d2 * bf(u[e] & 0xFFFFu);
+          a2[8 * q + 2 * e + 1] += d2 * bf(u[e] >> 16);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) a1[k] += d1 * s_x[r][8 * half + k];
+      if (!half) {
+        b2 += d2;
+        b1 += d1;
+      }
+      if (t < MH) w3 += s_dy[r] * bf(s_h2[r][t]);
+      if (t == 0) b3 += s_dy[r];
     }
   }
-  atomicAdd(grads + OFF_W2 + j * MH + k, gw2);
-  if (k < MI) atomicAdd(grads + OFF_W1 + j * MI + k, gw1);
-  if (k == 0) {
-    atomicAdd(grads + OFF_B2 + j, gb2);
-    atomicAdd(grads + OFF_B1 + j, gb1);
+#pragma unroll
+  for (int k = 0; k < 64; ++k) atomicAdd(grads + OFF_W2 + j * MH + 64 * half + k, a2[k]);
+#pragma unroll
+  for (int k = 0; k < 8; ++k) atomicAdd(grads + OFF_W1 + j * MI + 8 * half + k, a1[k]);
+  if (!half) {
+    atomicAdd(grads + OFF_B2 + j, b2);
+    atomicAdd(grads + OFF_B1 + j, b1);
   }
-  if (j == 0) {
-    atomicAdd(grads + OFF_W3 + k, gw3);
-    if (k == 0) atomicAdd(grads + OFF_B3, gb3);
-  }
+  if (t < MH) atomicAdd(grads + OFF_W3 + t, w3);
+  if (t == 0) atomicAdd(grads + OFF_B3, b3);
 }
 
 // Adam on the fp32 master parameters; refreshes the bf16 weight copies.
@@ -389,8 +437,12 @@ extern "C" tgs_status tgs_mlp_backward(const tgs_mlp* w, int64_t rows, const int
   }
   k_mlp_backward_act<<<mlp_grid(rows), 128, smem, s>>>(mlp_k(w), h1, h2, y, target, rows, rows_dev, dy, dh2, dh1,
                                                         loss);
-  dim3 gg(MH, (unsigned)((rows + kGradRows - 1) / kGradRows));
-  k_mlp_wgrad<<<gg, 128, 0, s>>>(x, h1, h2, dy, dh2, dh1, rows, grads);
+  // chunks: whole kWgRows groups, at most 4 blocks per SM's worth
+  const int64_t groups = (rows + kWgRows - 1) / kWgRows;
+  const int64_t per = std::max<int64_t>(1, (groups + 152 * 4 - 1) / (152 * 4));
+  const int64_t chunk = per * kWgRows;
+  k_mlp_wgrad<<<(unsigned)((rows + chunk - 1) / chunk), kWgThreads, 0, s>>>(x, h1, h2, dy, dh2, dh1, rows, chunk,
+                                                                          grads);
   return check_launch();
 }
 

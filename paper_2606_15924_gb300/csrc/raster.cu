@@ -79,12 +79,13 @@ struct Ckpt {
   float4* data;
   int n_slots;
   int64_t stride;
-  const float* rgb;  // the forward's output (read by the backward)
+  const float* rgb;    // the forward's output (read by the backward)
+  int32_t* tile_last;  // [active rank] longest blended run of the tile's pixels (nullable)
 };
 
 __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Splat* sm, float* __restrict__ out_rgb,
                                                 float* __restrict__ out_T, int32_t* __restrict__ out_last,
-                                                Ckpt ck = Ckpt{nullptr, 0, 0, nullptr}) {
+                                                Ckpt ck = Ckpt{nullptr, 0, 0, nullptr, nullptr}) {
   const int t = a.active_tiles ? a.active_tiles[j] : j;
   const int p0 = a.pix_off[j], p1 = a.pix_off[j + 1];
   const bool has_pix = p0 + (int)threadIdx.x < p1;
@@ -138,6 +139,15 @@ __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Spla
     out_rgb[3 * s + 2] = C2 + T * a.bg[2];
     out_T[s] = T;
     out_last[s] = last;
+  }
+  if (ck.tile_last) {  // the tile's longest blended run, for the pieces of the backward
+    __shared__ int s_tl;
+    __syncthreads();
+    if (threadIdx.x == 0) s_tl = 0;
+    __syncthreads();
+    if (last > 0) atomicMax(&s_tl, last);
+    __syncthreads();
+    if (threadIdx.x == 0) ck.tile_last[j] = s_tl;
   }
 }
 
@@ -303,27 +313,33 @@ __global__ void k_render_bwd(RasterArgs a, const float* __restrict__ T_final, co
 // checkpoint at the range's back edge, with the light from behind recovered
 // as S = (out - C) / T (out = T-weighted colours + T_final bg).  Per-splat
 // adjoints are reduced as in the whole-tile kernel.
-__global__ void k_render_bwd_split(RasterArgs a, const float* __restrict__ T_final,
-                                   const int32_t* __restrict__ n_last, const float* __restrict__ dL_drgb,
-                                   float* __restrict__ grad2d, Ckpt ck) {
-  extern __shared__ Splat sm[];
+__device__ __forceinline__ void render_piece_bwd(const RasterArgs& a, int j, int c, Splat* sm,
+                                                 const float* __restrict__ T_final,
+                                                 const int32_t* __restrict__ n_last,
+                                                 const float* __restrict__ dL_drgb, float* __restrict__ grad2d,
+                                                 const Ckpt& ck) {
   __shared__ int s_max_last;
-  const int j = blockIdx.x, c = blockIdx.y;
-  if (j >= *a.n_active) return;
   float* acc = reinterpret_cast<float*>(sm + blockDim.x);
   const int B = blockDim.x;
   const int t = a.active_tiles ? a.active_tiles[j] : j;
   const int p0 = a.pix_off[j], p1 = a.pix_off[j + 1];
   const bool has_pix = p0 + (int)threadIdx.x < p1;
   const int s = p0 + threadIdx.x;
-  int last = has_pix ? n_last[s] : 0;
-  if (threadIdx.x == 0) s_max_last = 0;
-  __syncthreads();
-  if (last > 0) atomicMax(&s_max_last, last);
-  __syncthreads();
+  int max_last;
+  if (ck.tile_last) {
+    max_last = ck.tile_last[j];  // from the forward
+  } else {
+    const int l0 = has_pix ? n_last[s] : 0;
+    if (threadIdx.x == 0) s_max_last = 0;
+    __syncthreads();
+    if (l0 > 0) atomicMax(&s_max_last, l0);
+    __syncthreads();
+    max_last = s_max_last;
+  }
   const int lo_pos = c * B;                                        // first list position of the range
-  const int hi_pos = c < ck.n_slots ? min(lo_pos + B, s_max_last) : s_max_last;
+  const int hi_pos = c < ck.n_slots ? min(lo_pos + B, max_last) : max_last;
   if (hi_pos <= lo_pos) return;                                    // uniform: nothing blended here
+  int last = has_pix ? n_last[s] : 0;
   const int2 range = a.ranges[j];
   float px = 0.f, py = 0.f, T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
   float S0 = a.bg[0], S1 = a.bg[1], S2 = a.bg[2];
@@ -424,6 +440,15 @@ __global__ void k_render_bwd_split(RasterArgs a, const float* __restrict__ T_fin
   }
 }
 
+__global__ void k_render_bwd_split(RasterArgs a, const float* __restrict__ T_final,
+                                   const int32_t* __restrict__ n_last, const float* __restrict__ dL_drgb,
+                                   float* __restrict__ grad2d, Ckpt ck) {
+  extern __shared__ Splat sm[];
+  const int j = blockIdx.x;
+  if (j >= *a.n_active) return;
+  render_piece_bwd(a, j, blockIdx.y, sm, T_final, n_last, dL_drgb, grad2d, ck);
+}
+
 // ---------------------------------------------------------------------------
 // Several views in one persistent launch: CTAs take (view, tile) items from
 // an atomic counter (items of view v are [base[v], base[v+1])) until none
@@ -433,6 +458,7 @@ constexpr int kMaxViews = 16;
 
 struct BatchArgs {
   int n_views;
+  int pieces;  // backward items per tile: 1, or checkpoint slots + 1
   int base[kMaxViews + 1];
   RasterArgs a[kMaxViews];
   float* rgb[kMaxViews];
@@ -440,6 +466,7 @@ struct BatchArgs {
   int32_t* last[kMaxViews];
   const float* dL[kMaxViews];
   float* grad2d[kMaxViews];
+  Ckpt ck[kMaxViews];
 };
 
 __device__ __forceinline__ bool next_item(const BatchArgs& b, int* counter, int* s_item, int& v, int& j) {
@@ -454,21 +481,54 @@ __device__ __forceinline__ bool next_item(const BatchArgs& b, int* counter, int*
   return true;
 }
 
+// The same, claiming `step` consecutive items per atomic: the first is
+// returned in *first (shared), the caller walks them.
+__device__ __forceinline__ bool next_items(const BatchArgs& b, int* counter, int* s_item, int step, int& first) {
+  __syncthreads();
+  if (threadIdx.x == 0) *s_item = atomicAdd(counter, step);
+  __syncthreads();
+  first = *s_item;
+  return first < b.base[b.n_views];
+}
+
+__device__ __forceinline__ void item_view(const BatchArgs& b, int item, int& v, int& q) {
+  v = 0;
+  while (item >= b.base[v + 1]) ++v;
+  q = item - b.base[v];
+}
+
 __global__ void k_render_fwd_batched(BatchArgs b, int* __restrict__ counter) {
   extern __shared__ Splat sm[];
   __shared__ int s_item;
   int v, j;
   while (next_item(b, counter, &s_item, v, j)) {
-    if (j < *b.a[v].n_active) render_tile_fwd(b.a[v], j, sm, b.rgb[v], b.T[v], b.last[v]);
+    if (j < *b.a[v].n_active) render_tile_fwd(b.a[v], j, sm, b.rgb[v], b.T[v], b.last[v], b.ck[v]);
   }
 }
+
+// Items are (view, tile, piece) with the pieces of a tile consecutive; with
+// one piece per tile this is the whole-tile backward.
+constexpr int kPieceClaim = 4;  // pieces claimed per atomic in the split backward
 
 __global__ void k_render_bwd_batched(BatchArgs b, int* __restrict__ counter) {
   extern __shared__ Splat sm[];
   __shared__ int s_item;
-  int v, j;
-  while (next_item(b, counter, &s_item, v, j)) {
-    if (j < *b.a[v].n_active) render_tile_bwd(b.a[v], j, sm, b.T[v], b.last[v], b.dL[v], b.grad2d[v]);
+  int v, q;
+  if (b.pieces == 1) {
+    while (next_item(b, counter, &s_item, v, q))
+      if (q < *b.a[v].n_active) render_tile_bwd(b.a[v], q, sm, b.T[v], b.last[v], b.dL[v], b.grad2d[v]);
+    return;
+  }
+  int first;
+  while (next_items(b, counter, &s_item, kPieceClaim, first)) {
+    const int end = min(first + kPieceClaim, b.base[b.n_views]);
+    for (int item = first; item < end; ++item) {
+      item_view(b, item, v, q);
+      const int j = q / b.pieces, c = q - j * b.pieces;
+      if (j >= *b.a[v].n_active) continue;
+      __syncthreads();  // the previous piece's shared memory is no longer read
+      render_piece_bwd(b.a[v], j, c, sm, b.T[v], b.last[v], b.dL[v], b.grad2d[v], b.ck[v]);
+    }
   }
 }
 
@@ -503,13 +563,14 @@ using namespace tgs;
 
 // Checkpoint buffer checks: stride covers every sampled pixel slot.
 static bool ckpt_of(const tgs_checkpoints* c, int32_t n_active_max, int32_t n_pix_max, const float* rgb, Ckpt& k) {
-  k = Ckpt{nullptr, 0, 0, nullptr};
+  k = Ckpt{nullptr, 0, 0, nullptr, nullptr};
   if (!c || c->n_slots <= 0) return true;
   if (!c->data || !aligned16(c->data) || c->stride < (int64_t)n_active_max * n_pix_max) return false;
   k.data = reinterpret_cast<float4*>(c->data);
   k.n_slots = c->n_slots;
   k.stride = c->stride;
   k.rgb = rgb;
+  k.tile_last = c->tile_last;
   return true;
 }
 
@@ -598,6 +659,9 @@ static tgs_status batch_args(const tgs_view_batch* views, int32_t n_views, bool 
   b.n_views = n_views;
   b.base[0] = 0;
   B = 32;
+  // checkpoints: all views or none, with one slot count
+  const int slots = views[0].ckpt.n_slots > 0 ? views[0].ckpt.n_slots : 0;
+  b.pieces = backward && slots > 0 ? slots + 1 : 1;
   for (int v = 0; v < n_views; ++v) {
     const tgs_view_batch& w = views[v];
     if (w.n_active_max < 0 || w.n_pix_max < 1 || w.n_pix_max > 256) return TGS_ERR_INVALID_ARG;
@@ -612,7 +676,10 @@ static tgs_status batch_args(const tgs_view_batch* views, int32_t n_views, bool 
     b.last[v] = w.n_last;
     b.dL[v] = w.dL_drgb;
     b.grad2d[v] = w.grad2d;
-    b.base[v + 1] = b.base[v] + w.n_active_max;
+    if ((w.ckpt.n_slots > 0 ? w.ckpt.n_slots : 0) != slots) return TGS_ERR_INVALID_ARG;
+    if (!ckpt_of(&w.ckpt, w.n_active_max, w.n_pix_max, w.rgb, b.ck[v])) return TGS_ERR_INVALID_ARG;
+    if (b.ck[v].data && w.ckpt.rgb && w.ckpt.rgb != w.rgb) return TGS_ERR_INVALID_ARG;
+    b.base[v + 1] = b.base[v] + w.n_active_max * (backward ? b.pieces : 1);
     B = std::max(B, block_for(w.n_pix_max));
   }
   return TGS_OK;

@@ -86,14 +86,16 @@ class Trainer:
         self.lam = torch.zeros(S, device=dev)
         self.err_pix = torch.zeros(P, device=dev)
         self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
-        # forward checkpoints for the split backward (sampled training only):
-        # one slot per batch of the tile list up to CKPT_POSITIONS positions
+        # forward checkpoints for the split backward: only when the step has
+        # too few tiles to fill the GPU (sparse sampling); one slot per batch
+        # of the tile list up to CKPT_POSITIONS positions
         self.ckpt = None
-        if train and not dense:
+        if train and not dense and self.n_select < 4 * B.render_batched_resident(self.n_pix, True):
             blk = min(256, max(32, (self.n_pix + 31) // 32 * 32))  # the kernels' block size
             n_slots = max(1, self.CKPT_POSITIONS // blk)
             self.ck_data = torch.empty(B.checkpoint_bytes(S, self.n_pix, n_slots) // 4, device=dev)
-            self.ckpt = B.checkpoints(self.ck_data, n_slots, S * self.n_pix, self.rgb)
+            self.ck_last = torch.zeros(S, dtype=torch.int32, device=dev)
+            self.ckpt = B.checkpoints(self.ck_data, n_slots, S * self.n_pix, self.rgb, self.ck_last)
         if train:
             self.grad2d = torch.zeros(N, 12, device=dev)
             self.touched = torch.zeros(N, dtype=u8, device=dev)

@@ -23,7 +23,7 @@ def B():
     return binding
 
 
-def _make(view_rows=False, mode=1, n=20000):
+def _make(view_rows=False, mode=1, n=20000, checkpoints=None):
     from gpu_util import dev, gaussians_dev
     from paper_2606_15924_gb300.batched import MultiViewTrainer
     from paper_2606_15924_gb300.config import Config
@@ -34,7 +34,7 @@ def _make(view_rows=False, mode=1, n=20000):
     targets = [dev(scenes.smooth_image(W, H, seed=10 + k)) for k in range(4)]
     cfg = Config()
     cfg.opt.mode = mode
-    mv = MultiViewTrainer(g, cams, targets, FRACTIONS, cfg=cfg, view_rows=view_rows)
+    mv = MultiViewTrainer(g, cams, targets, FRACTIONS, cfg=cfg, view_rows=view_rows, checkpoints=checkpoints)
     for k, v in enumerate(mv.views):
         v.err_map.copy_(dev(scenes.error_map(W, H, seed=k).view(np.int16)))
     return mv
@@ -93,8 +93,10 @@ def _close(a, b, rel=2e-5):
     return float((a - b).abs().max().item()) <= rel * scale + 1e-9
 
 
-def test_batched_backward_and_accumulated_gradients(B):
-    mv = _make(view_rows=True, mode=2)
+@pytest.mark.parametrize("split", [False, True])
+def test_batched_backward_and_accumulated_gradients(B, split):
+    mv = _make(view_rows=True, mode=2, checkpoints=split)
+    assert (mv.ck_slots > 0) == split
     mv.forward()
     mv.loss_and_maps()
     mv.backward()

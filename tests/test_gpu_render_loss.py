@@ -235,7 +235,9 @@ def test_backward_parity(B, orc, split):
             stride = sel["n_sel"] * n_pix
             ck_data = torch.full((B.checkpoint_bytes(sel["n_sel"], n_pix, slots) // 4,), float("nan"),
                                  device="cuda")
-            ck = B.checkpoints(ck_data, slots, stride, out["rgb"])
+            # the second case also has the forward record each tile's longest run
+            tl = torch.full((sel["n_sel"],), -1, dtype=torch.int32, device="cuda") if n_pix == 256 else None
+            ck = B.checkpoints(ck_data, slots, stride, out["rgb"], tl)
             B.render_sampled(pd, binned["ranges"], binned["vals"], sel["active_tiles"], sel["n_active"],
                              sel["n_sel"], sel["pix_off"], sel["pix_idx"], n_pix, cam, (0.0, 0.0, 0.0), out["rgb"],
                              out["T"], out["n_last"], ckpt=ck)
@@ -249,6 +251,11 @@ def test_backward_parity(B, orc, split):
         B.backward_sampled(gd, cam, pd, binned["ranges"], binned["vals"], sel["active_tiles"], sel["n_active"],
                            sel["n_sel"], sel["pix_off"], sel["pix_idx"], n_pix, (0.0, 0.0, 0.0), out["T"],
                            out["n_last"], dev(dLd), grad2d, grads, touched, ckpt=ck)
+        if split and tl is not None:   # the recorded runs are the per-tile maxima of n_last
+            nl = out["n_last"].cpu().numpy()
+            off = sh["pix_off"]
+            want_tl = [int(nl[off[r]:off[r + 1]].max(initial=0)) for r in range(len(off) - 1)]
+            np.testing.assert_array_equal(tl.cpu().numpy()[:len(want_tl)], want_tl)
         g64 = {k: v.astype(np.float64) for k, v in g.items()}
         prw = orc.project(g64, cam, tile_rank=sh["tile_rank"])
         g2w = orc.render_backward(prw, W, H, pix, dLd.astype(np.float64))
