@@ -435,8 +435,14 @@ def run_ours(args):
     tgt_host = target.detach().cpu().pin_memory()
     e2e_v, h2d, d2h = e2e_replays(sampled, tgt_host, args.steps)
     res["e2e"] = {"value": e2e_v * world, "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
-    res["quality"] = {"psnr_init_db": psnr(sampled.render_image(), target)}
     res["mlp"] = mlp_bench(device, peaks)
+    if not args.no_quality:
+        from paper_2606_15924_gb300.quality import compare
+        del sampled, dense
+        torch.cuda.empty_cache()
+        res["quality"] = quality_summary(compare(device, n=N_GAUSS, width=WIDTH, height=HEIGHT, distance=DISTANCE,
+                                                 extent=EXTENT, dense_iters=args.dense_iters,
+                                                 settings=quality_settings(args)))
     if rank == 0 and not args.no_cpu:
         res["cpu_baseline"] = cpu_baseline(cam, g_np, target.cpu().numpy())
     if dist is not None:
@@ -607,8 +613,26 @@ def run_quality(args):
     device = torch.device("cuda", 0)
     torch.cuda.set_device(device)
     res = compare(device, n=N_GAUSS, width=WIDTH, height=HEIGHT, distance=DISTANCE, extent=EXTENT,
-                  dense_iters=args.dense_iters, tile_fraction=args.fraction, pixel_rate=args.rate)
+                  dense_iters=args.dense_iters, settings=quality_settings(args))
     print(json.dumps({"metric": "sampled vs dense training at equal PSNR (device time)", **res}))
+
+
+def quality_settings(args):
+    """The bench's own (tile fraction, pixel rate), the larger tile fraction of
+    the configured 5-40% range, and the paper's sampling in every tile."""
+    out = [(args.fraction, args.rate), (0.4, PIXEL_RATE), (1.0, PIXEL_RATE)]
+    return list(dict.fromkeys(out))
+
+
+def quality_summary(res):
+    """Compact per-setting result of quality.compare for the bench line."""
+    out = {"workload": res["workload"], "dense_psnr_db": res["dense"]["psnr"],
+           "dense_iters": res["dense"]["iters"], "dense_ms": res["dense"]["ms"], "psnr_goal_db": res["psnr_goal"]}
+    for name, s in res["sampled"].items():
+        out[name] = {k: s.get(k) for k in ("tile_fraction", "pixel_rate", "iters_per_s_ratio", "reached",
+                                           "time_to_goal_ms", "dense_time_to_goal_ms", "time_speedup", "psnr",
+                                           "iters", "ms")}
+    return out
 
 
 def run_reference(args):
@@ -653,6 +677,7 @@ def main():
                     help="only the equal-quality comparison: dense training for a fixed number of iterations, then "
                          "sampled training until it is within 0.1 dB of the dense PSNR (device time)")
     ap.add_argument("--dense-iters", type=int, default=2000)
+    ap.add_argument("--no-quality", action="store_true", help="skip the equal-PSNR comparison in the default run")
     ap.add_argument("--workload", default="step", choices=["step", "batched"],
                     help="step: the one-view sparse training step (the headline line); batched: 8 views per "
                          "iteration in one persistent launch vs one launch per view")

@@ -100,6 +100,10 @@ class Trainer:
             self.grad2d = torch.zeros(N, 12, device=dev)
             self.touched = torch.zeros(N, dtype=u8, device=dev)
             self.ws_hybrid = torch.empty(B.hybrid_step_workspace_size(N), dtype=u8, device=dev)
+            # the projection adjoint runs over a compacted list of the touched
+            # Gaussians (the multi-view adjoint with one view)
+            self.ws_adj = torch.empty(B.project_backward_multi_workspace_size(N), dtype=u8, device=dev)
+            self.adj = B.MultiAdjoint([self.ccam], [self.proj["radius"]], [self.grad2d])
         # device-side counters (graph replays read them)
         self.it_dev = torch.zeros(1, dtype=i64, device=dev)
         self.step_dev = torch.ones(1, dtype=i32, device=dev)
@@ -169,8 +173,8 @@ class Trainer:
 
     def project_backward(self, write_untouched=False):
         """Projection adjoint into the parameter gradients (second half)."""
-        B.project_backward(self.params, self.ccam, self.proj, self.grad2d, self.grads, self.touched,
-                           write_untouched=write_untouched, sh_degree=self.sh_degree)
+        B.project_backward_multi(self.params, self.adj, self.grads, self.touched, write_untouched=write_untouched,
+                                 sh_degree=self.sh_degree, workspace=self.ws_adj)
 
     def backward(self, write_untouched=False):
         """Sparse backward into parameter gradients (Alg. 1 step 8)."""

@@ -93,9 +93,13 @@ def time_to(curve: list, psnr: float):
 
 def compare(device, n: int = 500_000, width: int = 1280, height: int = 720, distance: float = 15.0,
             extent: float = 5.0, dense_iters: int = 2000, eval_every: int = 250, tile_fraction: float = 0.2,
-            pixel_rate: float = 1.0 / 3.0, time_cap: float = 1.5) -> dict:
+            pixel_rate: float = 1.0 / 3.0, time_cap: float = 1.5, settings=None) -> dict:
     """Dense for dense_iters iterations; sampled until it is within 0.1 dB of
-    the dense final PSNR or has used time_cap x the dense device time."""
+    the dense final PSNR or has used time_cap x the dense device time.
+    settings: list of (tile_fraction, pixel_rate) for the sampled runs (one
+    dense run serves them all); default the single given pair."""
+    if settings is None:
+        settings = [(tile_fraction, pixel_rate)]
     cam = scenes.look_at((0.0, 0.0, -distance), width=width, height=height)
     gt = scenes.gaussians(n, seed=scenes.SEED_TARGET, extent=extent)
     gt_d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in gt.items()}
@@ -103,13 +107,12 @@ def compare(device, n: int = 500_000, width: int = 1280, height: int = 720, dist
     target = Trainer(gt_d, cam, dummy, dense=True, train=False).render_image().contiguous()
     del gt_d
     init = perturbed_init(gt, extent)
-    out = {"workload": f"{n} Gaussians, {width}x{height}, perturbed ground truth",
-           "tile_fraction": tile_fraction, "pixel_rate": pixel_rate}
+    out = {"workload": f"{n} Gaussians, {width}x{height}, perturbed ground truth"}
     runs = {}
-    for name in ("dense", "sampled"):
+    for name, (frac, rate) in [("dense", (1.0, 1.0))] + [(f"sampled_{f:g}_{r:.3g}", (f, r)) for f, r in settings]:
         params = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in init.items()}
         dense = name == "dense"
-        tr = Trainer(params, cam, target, tile_fraction=tile_fraction, pixel_rate=pixel_rate, dense=dense)
+        tr = Trainer(params, cam, target, tile_fraction=frac, pixel_rate=rate, dense=dense)
         ev = Evaluator(params, cam, target)
         t_init = 0.0
         if not dense:
@@ -125,21 +128,25 @@ def compare(device, n: int = 500_000, width: int = 1280, height: int = 720, dist
             r = train_curve(tr, ev, dense_iters, eval_every)
         else:
             goal = runs["dense"]["psnr"] - 0.1
-            r = train_curve(tr, ev, 10 ** 7, eval_every * 4, stop_psnr=goal,
+            r = train_curve(tr, ev, 10 ** 7, eval_every * 2, stop_psnr=goal,
                             max_ms=time_cap * runs["dense"]["ms"])
             r["error_map_init_ms"] = t_init
         r["overflowed"] = tr.overflowed()
+        if not dense:
+            r.update(tile_fraction=frac, pixel_rate=rate)
         runs[name] = r
         del tr, ev, params
         torch.cuda.empty_cache()
-    d, s = runs["dense"], runs["sampled"]
+    d = runs.pop("dense")
     goal = d["psnr"] - 0.1
-    t_s = time_to(s["curve"], goal)
-    out.update(dense=d, sampled=s, psnr_goal=goal,
-               iters_per_s_ratio=s["iters_per_s"] / d["iters_per_s"],
-               reached=t_s is not None,
-               time_to_goal_ms={"dense": time_to(d["curve"], goal), "sampled": None if t_s is None else
-                                t_s + s.get("error_map_init_ms", 0.0)})
-    if t_s is not None:
-        out["time_speedup"] = out["time_to_goal_ms"]["dense"] / out["time_to_goal_ms"]["sampled"]
+    t_d = time_to(d["curve"], goal)
+    out.update(dense=d, psnr_goal=goal, sampled={})
+    for name, s in runs.items():
+        t_s = time_to(s["curve"], goal)
+        s.update(iters_per_s_ratio=s["iters_per_s"] / d["iters_per_s"], reached=t_s is not None,
+                 time_to_goal_ms=None if t_s is None else t_s + s.get("error_map_init_ms", 0.0),
+                 dense_time_to_goal_ms=t_d)
+        if t_s is not None:
+            s["time_speedup"] = t_d / s["time_to_goal_ms"]
+        out["sampled"][name] = s
     return out
