@@ -218,8 +218,11 @@ tgs_status tgs_project_gaussians(const tgs_gaussians* g, const tgs_camera* cam, 
 /*
  * bin_tiles - per-tile Gaussian lists sorted by depth (Sec. 3.1, the ordered
  * sets K(p)): every (active tile, Gaussian) pair whose tile rectangle covers
- * the tile, ordered by (tile, depth, Gaussian id), as a device radix sort of
- * (tile | depth) keys.
+ * the tile, ordered by (tile, depth, Gaussian id): a counting sort on the
+ * active-tile rank (shared-memory histograms per chunk of Gaussians) and a
+ * sort within each tile.  When capacity exceeds 2048 pairs per tile of the
+ * view (long lists), the Gaussians are first radix-sorted by depth so that
+ * only short segments of each list need sorting; the result is the same.
  *
  *   proj        xy, depth, radius of the projection (radius 0 = skip)
  *   tile_rank   [T] active-tile index or -1 (NULL: every tile active, rank = id)

@@ -1,7 +1,10 @@
 // Tile binning: the per-tile Gaussian lists ordered by depth (Sec. 3.1, the
 // depth-ordered sets K(p)) as a sort of (tile | depth | id) keys:
-//   0. the visible Gaussians are sorted by depth (stable LSD radix sort of the
-//      depth bits, ids ascending within equal depths);
+//   0. when the lists are long (the caller's capacity averages more than 2048
+//      pairs per tile), the visible Gaussians are first sorted by depth
+//      (stable LSD radix sort of the depth bits, ids ascending within equal
+//      depths); otherwise the chunks below are runs of ids and step 4 sorts
+//      every tile's whole list (in shared memory up to kSortSmem keys);
 //   1. blocks take consecutive chunks of that order and count their pairs per
 //      active tile in shared memory (a tile x block table of counts),
 //   2. one scan of that table in tile-major order gives every (tile, block)
@@ -204,8 +207,8 @@ __device__ __forceinline__ void for_each_pair(const float2* __restrict__ xy, con
 constexpr int kHistThreads = 512;
 
 // Block b's chunk of the depth order: [b * chunk, min(n_vis, (b + 1) * chunk)).
-__device__ __forceinline__ void vis_chunk(const int32_t* n_vis, int64_t& i0, int64_t& i1) {
-  const int64_t nv = *n_vis, G = gridDim.x;
+__device__ __forceinline__ void vis_chunk(const int32_t* n_vis, int64_t n_host, int64_t& i0, int64_t& i1) {
+  const int64_t nv = n_vis ? *n_vis : n_host, G = gridDim.x;
   const int64_t chunk = (nv + G - 1) / G;
   i0 = (int64_t)blockIdx.x * chunk;
   i1 = min(nv, i0 + chunk);
@@ -214,15 +217,15 @@ __device__ __forceinline__ void vis_chunk(const int32_t* n_vis, int64_t& i0, int
 __global__ void __launch_bounds__(kHistThreads) k_hist_count(const float2* __restrict__ xy,
                                                              const int32_t* __restrict__ radius,
                                                              const uint32_t* __restrict__ order,
-                                                             const int32_t* __restrict__ n_vis, BinGeom geo,
-                                                             const int32_t* __restrict__ tile_rank,
+                                                             const int32_t* __restrict__ n_vis, int64_t n,
+                                                             BinGeom geo, const int32_t* __restrict__ tile_rank,
                                                              int64_t* __restrict__ table) {
   extern __shared__ uint32_t sh[];
   const int R = geo.n_ranks, G = gridDim.x, b = blockIdx.x;
   for (int r = threadIdx.x; r < R; r += blockDim.x) sh[r] = 0;
   __syncthreads();
   int64_t i0, i1;
-  vis_chunk(n_vis, i0, i1);
+  vis_chunk(n_vis, n, i0, i1);
   for_each_pair(xy, radius, i0, i1, geo, tile_rank, [&](int64_t, int k) { atomicAdd(sh + k, 1u); }, order);
   __syncthreads();
   for (int r = threadIdx.x; r < R; r += blockDim.x) table[(size_t)r * G + b] = sh[r];
@@ -235,8 +238,8 @@ __global__ void __launch_bounds__(kHistThreads) k_hist_scatter(const float2* __r
                                                                const int32_t* __restrict__ radius,
                                                                const float* __restrict__ depth,
                                                                const uint32_t* __restrict__ order,
-                                                               const int32_t* __restrict__ n_vis, BinGeom geo,
-                                                               const int32_t* __restrict__ tile_rank,
+                                                               const int32_t* __restrict__ n_vis, int64_t n,
+                                                               BinGeom geo, const int32_t* __restrict__ tile_rank,
                                                                const int64_t* __restrict__ table,
                                                                uint64_t* __restrict__ keys, int64_t cap) {
   extern __shared__ uint32_t sh[];
@@ -244,7 +247,7 @@ __global__ void __launch_bounds__(kHistThreads) k_hist_scatter(const float2* __r
   for (int r = threadIdx.x; r < R; r += blockDim.x) sh[r] = (uint32_t)min(table[(size_t)r * G + b], cap);
   __syncthreads();
   int64_t i0, i1;
-  vis_chunk(n_vis, i0, i1);
+  vis_chunk(n_vis, n, i0, i1);
   for_each_pair(xy, radius, i0, i1, geo, tile_rank, [&](int64_t i, int k) {
     const uint32_t pos = atomicAdd(sh + k, 1u);
     if ((int64_t)pos < cap) keys[pos] = ((uint64_t)__float_as_uint(depth[i]) << 32) | (uint64_t)(uint32_t)i;
@@ -561,6 +564,12 @@ extern "C" tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const 
   const int G = hist_blocks(n);
   const size_t smem = sizeof(int32_t) * (size_t)R;
   const uint32_t* order = nullptr;
+  // The depth presort pays off only when tile lists outgrow the shared-memory
+  // sort: it is used when the capacity (sized by the caller from the pairs of
+  // all tiles) averages more than half of kSortSmem per tile.  Without it the
+  // chunks are runs of ids and every tile's whole list is sorted.
+  const bool presort = shared_path && capacity > 0 && capacity > (int64_t)(kSortSmem / 2) * T;
+  const int32_t* n_vis = presort ? w.n_vis : nullptr;
   if (shared_path) {
     if (smem > 48 * 1024) {  // opt in to more than 48 KB of dynamic shared memory (per device)
       static bool attr_set[64] = {};
@@ -573,12 +582,15 @@ extern "C" tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const 
         attr_set[dev] = true;
       }
     }
-    cudaMemsetAsync(w.n_vis, 0, sizeof(int32_t), s);
-    k_depth_keys<<<(int)((n + 255) / 256), 256, 0, s>>>(proj->radius, proj->depth, n, w.dk[0], w.dv[0], w.n_vis);
-    const int cur = radix_sort_pairs(w.dk[0], w.dv[0], w.dk[1], w.dv[1], nullptr, (int32_t)n, 0, 32, w.rs,
-                                     nullptr, s);
-    order = w.dv[cur];
-    k_hist_count<<<G, kHistThreads, smem, s>>>(xy, proj->radius, order, w.n_vis, geo, tile_rank, w.table);
+    if (presort) {
+      cudaMemsetAsync(w.n_vis, 0, sizeof(int32_t), s);
+      k_depth_keys<<<(int)((n + 255) / 256), 256, 0, s>>>(proj->radius, proj->depth, n, w.dk[0], w.dv[0],
+                                                          w.n_vis);
+      const int cur = radix_sort_pairs(w.dk[0], w.dv[0], w.dk[1], w.dv[1], nullptr, (int32_t)n, 0, 32, w.rs,
+                                       nullptr, s);
+      order = w.dv[cur];
+    }
+    k_hist_count<<<G, kHistThreads, smem, s>>>(xy, proj->radius, order, n_vis, n, geo, tile_rank, w.table);
     int64_t* tab = w.table;
     auto load = [=] __device__(int64_t i) -> int64_t { return tab[i]; };
     auto store = [=] __device__(int64_t i, int64_t pre, int64_t) { tab[i] = pre; };
@@ -602,14 +614,14 @@ extern "C" tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const 
   }
   if (capacity == 0) return check_launch();
   if (shared_path) {
-    k_hist_scatter<<<G, kHistThreads, smem, s>>>(xy, proj->radius, proj->depth, order, w.n_vis, geo, tile_rank,
+    k_hist_scatter<<<G, kHistThreads, smem, s>>>(xy, proj->radius, proj->depth, order, n_vis, n, geo, tile_rank,
                                                  w.table, w.keys, capacity);
   } else {
     k_scatter_keys<<<(int)((n + 255) / 256), 256, 0, s>>>(xy, proj->radius, proj->depth, n, geo, tile_rank,
                                                           w.tile_start, w.tile_fill, w.keys, capacity);
   }
   if (keys) k_inv_rank<<<(T + 255) / 256, 256, 0, s>>>(tile_rank, T, w.inv_rank, R);
-  if (shared_path)
+  if (presort)
     k_seg_sort<<<R, kSegThreads, 0, s>>>(w.keys, src, w.inv_rank, capacity, vals, keys,
                                          reinterpret_cast<int2*>(tile_ranges));
   else

@@ -117,10 +117,10 @@ __global__ void __launch_bounds__(128) k_hybrid_lm(tgs_param_ptrs P, tgs_param_p
                                                    tgs_param_ptrs V, int64_t n, const int32_t* __restrict__ list,
                                                    const int32_t* __restrict__ count, const float* __restrict__ rows,
                                                    int k_rows, OptK o) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= *count) return;
-  const int64_t i = list[q];
   bias_corrections(o);
+  const int64_t cnt = *count;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t i = list[q];
   float gp[10], gg[10], gm[10], gv[10];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(128) k_hybrid_lm(tgs_param_ptrs P, tgs_param_p
   reinterpret_cast<float4*>(P.sh)[12 * i] = make_float4(sp[0], sp[1], sp[2], sp[3]);
   reinterpret_cast<float4*>(M.sh)[12 * i] = make_float4(smm[0], smm[1], smm[2], smm[3]);
   reinterpret_cast<float4*>(V.sh)[12 * i] = make_float4(sv[0], sv[1], sv[2], sv[3]);
+  }
 }
 
 // Adam on SH float4s 1..11 of each touched Gaussian: one thread per float4,
@@ -185,9 +186,9 @@ __global__ void __launch_bounds__(128) k_hybrid_lm(tgs_param_ptrs P, tgs_param_p
 __global__ void __launch_bounds__(256) k_adam_sh(tgs_param_ptrs P, tgs_param_ptrs G, tgs_param_ptrs M,
                                                  tgs_param_ptrs V, const int32_t* __restrict__ list,
                                                  const int32_t* __restrict__ count, OptK o) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (int64_t)*count * 11) return;
   bias_corrections(o);
+  const int64_t total = (int64_t)*count * 11;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
   const int64_t q = e / 11;
   const int k = 1 + (int)(e - q * 11);
   const int64_t f = 12 * (int64_t)list[q] + k;
@@ -200,6 +201,7 @@ __global__ void __launch_bounds__(256) k_adam_sh(tgs_param_ptrs P, tgs_param_ptr
   reinterpret_cast<float4*>(P.sh)[f] = pp;
   reinterpret_cast<float4*>(M.sh)[f] = mq;
   reinterpret_cast<float4*>(V.sh)[f] = vq;
+  }
 }
 
 static bool ptrs_ok(const tgs_param_ptrs* p) {
@@ -238,10 +240,15 @@ extern "C" tgs_status tgs_hybrid_step(const tgs_param_ptrs* params, const tgs_pa
   int32_t* count = c.take<int32_t>(1);
   cudaMemsetAsync(count, 0, sizeof(int32_t), s);
   k_compact_touched<<<(int)((n + 255) / 256), 256, 0, s>>>(touched, n, list, count);
-  const int lb = (int)((n + 127) / 128);
+  // the touched count lives on the device: grid-stride loops over it with
+  // grids of a few waves of the GPU (not one thread per Gaussian)
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int lb = (int)std::min<int64_t>((n + 127) / 128, (int64_t)sms * 16);
+  const int sb = (int)std::min<int64_t>((n * 11 + 255) / 256, (int64_t)sms * 16);
   if (o.mode == 0) k_hybrid_lm<0><<<lb, 128, 0, s>>>(*params, *grads, *m, *v, n, list, count, view_rows, k_rows, o);
   else if (o.mode == 1) k_hybrid_lm<1><<<lb, 128, 0, s>>>(*params, *grads, *m, *v, n, list, count, view_rows, k_rows, o);
   else k_hybrid_lm<2><<<lb, 128, 0, s>>>(*params, *grads, *m, *v, n, list, count, view_rows, k_rows, o);
-  k_adam_sh<<<(int)((n * 11 + 255) / 256), 256, 0, s>>>(*params, *grads, *m, *v, list, count, o);
+  k_adam_sh<<<sb, 256, 0, s>>>(*params, *grads, *m, *v, list, count, o);
   return check_launch();
 }

@@ -59,8 +59,9 @@ BIN_CASES = [
 ]
 
 
+@pytest.mark.parametrize("presort", [False, True])
 @pytest.mark.parametrize("n,W,H,frac", BIN_CASES)
-def test_bin_tiles_bit_exact(B, orc, n, W, H, frac):
+def test_bin_tiles_bit_exact(B, orc, n, W, H, frac, presort):
     from gpu_util import bin_dev, dev, projected_dev, tile_count
     pr = scenes.projected(n, W, H, seed=n + W)
     T = tile_count(W, H)
@@ -74,8 +75,8 @@ def test_bin_tiles_bit_exact(B, orc, n, W, H, frac):
     want = orc.bin_tiles(pr["xy"], pr["radius"], pr["depth"], W, H, rank)
     keys_w, vals_w, counts_w = want
     cam = dict(viewmat=np.eye(4), fx=100.0, fy=100.0, cx=W / 2, cy=H / 2, width=W, height=H, znear=0.2)
-    out = bin_dev(B, projected_dev(pr), n, cam, None if rank is None else dev(rank), n_active_max,
-                  capacity=len(vals_w) + 100)
+    cap = max(len(vals_w) + 100, 2049 * T) if presort else len(vals_w) + 100
+    out = bin_dev(B, projected_dev(pr), n, cam, None if rank is None else dev(rank), n_active_max, capacity=cap)
     I = int(out["n_isect"].item())
     assert I == len(vals_w)
     np.testing.assert_array_equal(out["vals"][:I].cpu().numpy(), vals_w)
@@ -97,8 +98,11 @@ def test_bin_tiles_bit_exact(B, orc, n, W, H, frac):
 CLUSTER_CASES = [(5000, 5000), (50000, 50000), (200000, 30000), (200000, 200000)]
 
 
+@pytest.mark.parametrize("presort", [False, True])
 @pytest.mark.parametrize("n,n_crowd", CLUSTER_CASES)
-def test_bin_tiles_crowded_tile_bit_exact(B, orc, n, n_crowd):
+def test_bin_tiles_crowded_tile_bit_exact(B, orc, n, n_crowd, presort):
+    """presort: a capacity above 2048 pairs per tile makes bin_tiles sort the
+    Gaussians by depth first and sort only segments of each tile's list."""
     from gpu_util import bin_dev, projected_dev
     W, H = 256, 256
     rng = np.random.default_rng(n + n_crowd)
@@ -116,7 +120,8 @@ def test_bin_tiles_crowded_tile_bit_exact(B, orc, n, n_crowd):
     keys_w, vals_w, counts_w = orc.bin_tiles(pr["xy"], pr["radius"], pr["depth"], W, H)
     assert counts_w.max() > 4096 or n_crowd < 20000
     cam = dict(viewmat=np.eye(4), fx=100.0, fy=100.0, cx=W / 2, cy=H / 2, width=W, height=H, znear=0.2)
-    out = bin_dev(B, projected_dev(pr), n, cam, None, 256, capacity=len(vals_w) + 7)
+    cap = max(len(vals_w) + 7, 2049 * 256) if presort else len(vals_w) + 7
+    out = bin_dev(B, projected_dev(pr), n, cam, None, 256, capacity=cap)
     I = int(out["n_isect"].item())
     assert I == len(vals_w)
     np.testing.assert_array_equal(out["vals"][:I].cpu().numpy(), vals_w)
