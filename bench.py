@@ -575,8 +575,16 @@ def mlp_bench(device, peaks, steps: int = 10) -> dict:
     h2 = torch.empty(R, HID, dtype=torch.int16, device=device)
     ws = torch.empty(B.mlp_backward_workspace_size(R), dtype=torch.uint8, device=device)
 
+    status = torch.zeros(1, dtype=torch.int32, device=device)
+
     def fwd():
         B.mlp_forward(mlp.net(), x, y, h1, h2)
+
+    def fwd_tc():
+        B.mlp_forward_tc(mlp.net(), x, y, h1, h2, status=status)
+
+    def infer_tc():
+        B.mlp_forward_tc(mlp.net(), x, y, status=status)
 
     def train():
         fwd()
@@ -595,12 +603,19 @@ def mlp_bench(device, peaks, steps: int = 10) -> dict:
         b.synchronize()
         return a.elapsed_time(b) / steps
     f_ms, t_ms = timed(fwd), timed(train)
+    ftc_ms, itc_ms = timed(fwd_tc), timed(infer_tc)
     flop = 2.0 * R * (16 * 128 + 128 * 128 + 128)
     peak = float(peaks.get("bf16_tflops", 1900.0))
-    return {"rows": R, "forward_ms": f_ms, "train_step_ms": t_ms,
-            "forward_roofline": {"bound": "tensor", "achieved": flop / (f_ms * 1e-3) / 1e12, "peak": peak,
-                                 "unit": "TFLOP/s", "frac": flop / (f_ms * 1e-3) / 1e12 / peak,
-                                 "note": "bf16 mma.sync, fp32 accumulate; peak = measured cuBLAS bf16 (burst)"},
+
+    def roof(ms, note):
+        a = flop / (ms * 1e-3) / 1e12
+        return {"bound": "tensor", "achieved": a, "peak": peak, "unit": "TFLOP/s", "frac": a / peak, "note": note}
+    return {"rows": R, "forward_ms": f_ms, "forward_tc_ms": ftc_ms, "inference_tc_ms": itc_ms,
+            "train_step_ms": t_ms, "tc_status": int(status.item()),
+            "forward_roofline": roof(f_ms, "mma.sync m16n8k16 bf16, fp32 accumulate, h1/h2 stored"),
+            "forward_tc_roofline": roof(ftc_ms, "tcgen05.mma bf16, TMEM accumulators, h1/h2 stored"),
+            "inference_tc_roofline": roof(itc_ms, "tcgen05.mma bf16, TMEM accumulators, y only"),
+            "peak_note": "peak = measured cuBLAS bf16 (burst)",
             "train_roofline": {"achieved": 3 * flop / (t_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                                "frac": 3 * flop / (t_ms * 1e-3) / 1e12 / peak}}
 

@@ -482,6 +482,13 @@ int32_t tgs_mlp_param_count(void);
 tgs_status tgs_mlp_forward(const tgs_mlp* w, int64_t rows, const float* x, float* y, uint16_t* h1, uint16_t* h2,
                            tgs_stream stream);
 
+/* The same forward on the tcgen05 tensor cores (128-row tiles, operands in
+ * shared memory, accumulators in tensor memory); x, w1, w2, h1, h2 16-byte
+ * aligned.  status (nullable device int32) is set to 1 if a wait for the
+ * tensor cores timed out (the call's outputs are then incomplete). */
+tgs_status tgs_mlp_forward_tc(const tgs_mlp* w, int64_t rows, const float* x, float* y, uint16_t* h1, uint16_t* h2,
+                              int32_t* status, tgs_stream stream);
+
 /* Gradient of L = (1/R) sum (y - t)^2 / 2 into grads (packed layout, fp32,
  * overwritten) and *loss (device double), from the forward's x, h1, h2, y.
  * Hidden adjoints are rounded to bf16 before they meet a bf16 operand.  R is

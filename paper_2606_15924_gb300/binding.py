@@ -159,6 +159,8 @@ _lib.tgs_hybrid_step.argtypes = [_P(ParamPtrs), _P(ParamPtrs), _P(ParamPtrs), _P
 _lib.tgs_mlp_param_count.restype = _i32
 _lib.tgs_mlp_forward.restype = _i32
 _lib.tgs_mlp_forward.argtypes = [_P(Mlp), _i64, _p, _p, _p, _p, _p]
+_lib.tgs_mlp_forward_tc.restype = _i32
+_lib.tgs_mlp_forward_tc.argtypes = [_P(Mlp), _i64, _p, _p, _p, _p, _p, _p]
 _lib.tgs_mlp_backward_workspace_size.restype = _sz
 _lib.tgs_mlp_backward_workspace_size.argtypes = [_i64]
 _lib.tgs_mlp_backward.restype = _i32
@@ -182,7 +184,8 @@ EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_devi
             "tgs_project_backward_multi",
             "tgs_render_batched_resident", "tgs_render_sampled_batched",
             "tgs_render_backward_batched", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step",
-            "tgs_mlp_param_count", "tgs_mlp_forward", "tgs_mlp_backward_workspace_size", "tgs_mlp_backward",
+            "tgs_mlp_param_count", "tgs_mlp_forward", "tgs_mlp_forward_tc", "tgs_mlp_backward_workspace_size",
+            "tgs_mlp_backward",
             "tgs_mlp_adam", "tgs_tile_observe", "tgs_tile_features", "tgs_tile_refresh"]
 
 
@@ -479,6 +482,12 @@ def mlp_forward(net: dict, x, y, h1=None, h2=None, stream=None):
     m = mlp_struct(net)
     _check("tgs_mlp_forward", _lib.tgs_mlp_forward(C.byref(m), int(x.shape[0]), _ptr(x), _ptr(y), _ptr(h1), _ptr(h2),
                                                    _stream(stream)))
+
+
+def mlp_forward_tc(net: dict, x, y, h1=None, h2=None, status=None, stream=None):
+    m = mlp_struct(net)
+    _check("tgs_mlp_forward_tc", _lib.tgs_mlp_forward_tc(C.byref(m), int(x.shape[0]), _ptr(x), _ptr(y), _ptr(h1),
+                                                         _ptr(h2), _ptr(status), _stream(stream)))
 
 
 def mlp_backward_workspace_size(rows: int) -> int:

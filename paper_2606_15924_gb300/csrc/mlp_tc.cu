@@ -1,0 +1,302 @@
+// Forward of the tile-error MLP on the 5th-generation tensor cores
+// (tcgen05): 128-row tiles, bf16 operands in shared memory, fp32
+// accumulators in tensor memory (TMEM).
+//
+// One CTA of 128 threads (4 warps) loops over 128-row tiles:
+//   1. every thread converts its row of x to bf16 into the A tile of layer 1;
+//   2. one thread issues D1 = X W1^T (M 128, N 128, K 16) into TMEM columns
+//      0-127 and commits to an mbarrier;
+//   3. every thread reads its row of D1 (tcgen05.ld, 32 columns at a time),
+//      adds b1, applies ReLU, rounds to bf16 and writes the row into the A
+//      tile of layer 2 (and to h1);
+//   4. one thread issues D2 = H1 W2^T as eight K-16 steps into columns
+//      128-255;
+//   5. every thread reads its row of D2, adds b2, applies ReLU, rounds to
+//      bf16 (h2) and takes the dot product with W3 (bf16) in fp32: y.
+// The arithmetic is that of the mma.sync forward: bf16 products, fp32 sums.
+//
+// Operands use the canonical K-major layout without swizzle: 8-row x 16-byte
+// core matrices stored as 128 contiguous bytes; consecutive core matrices
+// along K are LBO = 128 bytes apart, consecutive 8-row groups SBO bytes apart.
+// Waits on the mbarrier are bounded: on a timeout the CTA records it in the
+// status word, waits (bounded) for its MMAs, frees its TMEM and stops.
+#include <cuda_bf16.h>
+
+#include "tgs_common.cuh"
+
+namespace tgs {
+namespace {
+
+constexpr int TI = 16, TH = 128, TM = 128;  // input width, hidden width, rows per tile
+constexpr int kTcThreads = 128;
+constexpr uint32_t kTmemCols = 256;         // D1 (0-127) and D2 (128-255)
+constexpr long long kWaitLimit = 1ll << 22; // try_wait rounds before giving up
+
+// byte offsets of the shared-memory operand tiles
+constexpr uint32_t SBO_K16 = (TI / 8) * 128;    // 8-row group stride of a K = 16 tile
+constexpr uint32_t SBO_K128 = (TH / 8) * 128;   // of a K = 128 tile
+constexpr uint32_t OFF_W1S = 0;                             // W1 [128 n][16 k]
+constexpr uint32_t OFF_W2S = OFF_W1S + TH * TI * 2;         // W2 [128 n][128 k]
+constexpr uint32_t OFF_XS = OFF_W2S + TH * TH * 2;          // X  [128 m][16 k]
+constexpr uint32_t OFF_HS = OFF_XS + TM * TI * 2;           // H1 [128 m][128 k]
+constexpr uint32_t OFF_PAR = OFF_HS + TM * TH * 2;          // b1, b2, w3 (fp32), b3
+constexpr uint32_t SMEM_USED = OFF_PAR + (3 * TH + 4) * 4;
+// requested dynamic shared memory: more than a third of the SM's, so that at
+// most two CTAs (2 x 256 TMEM columns = all 512) share an SM and an
+// allocation never waits for another CTA
+constexpr uint32_t SMEM_REQ = 100 * 1024;
+static_assert(SMEM_USED <= SMEM_REQ, "shared memory layout");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// byte offset of element (row, k) in a K-major no-swizzle tile
+__device__ __forceinline__ uint32_t core_off(int row, int k, uint32_t sbo) {
+  return (uint32_t)(row >> 3) * sbo + (uint32_t)(k >> 3) * 128u + (uint32_t)(row & 7) * 16u + (uint32_t)(k & 7) * 2u;
+}
+
+// shared-memory matrix descriptor: start, LBO, SBO (all >> 4), version 1,
+// no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: fp32 accumulate, bf16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TH >> 3) << 17) |
+                            ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+// Bounded wait for the mbarrier's phase `parity` to complete.
+__device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) {
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, P1;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int k = 0; k < 32; ++k) v[k] = __uint_as_float(r[k]);
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+struct TcArgs {
+  const uint16_t *w1, *w2, *w3;
+  const float *b1, *b2, *b3;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(TcArgs w, const float* __restrict__ x, int64_t R,
+                                                                  float* __restrict__ y, uint16_t* __restrict__ h1,
+                                                                  uint16_t* __restrict__ h2,
+                                                                  int32_t* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_mbar;
+  const int t = threadIdx.x, warp = t >> 5;
+  float* par = reinterpret_cast<float*>(sm + OFF_PAR);  // b1 [128], b2 [128], w3 [128], b3
+  // weights into the canonical layouts (each 16-byte chunk = 8 k-values of one row)
+  for (int i = t; i < TH * (TI / 8); i += kTcThreads) {
+    const int n = i / (TI / 8), k8 = (i % (TI / 8)) * 8;
+    *reinterpret_cast<uint4*>(sm + OFF_W1S + core_off(n, k8, SBO_K16)) =
+        *reinterpret_cast<const uint4*>(w.w1 + n * TI + k8);
+  }
+  for (int i = t; i < TH * (TH / 8); i += kTcThreads) {
+    const int n = i / (TH / 8), k8 = (i % (TH / 8)) * 8;
+    *reinterpret_cast<uint4*>(sm + OFF_W2S + core_off(n, k8, SBO_K128)) =
+        *reinterpret_cast<const uint4*>(w.w2 + n * TH + k8);
+  }
+  for (int i = t; i < TH; i += kTcThreads) {
+    par[i] = w.b1[i];
+    par[TH + i] = w.b2[i];
+    par[2 * TH + i] = __uint_as_float((uint32_t)w.w3[i] << 16);
+  }
+  if (t == 0) {
+    par[3 * TH] = w.b3[0];
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t mbar = smem_u32(&s_mbar);
+  const uint32_t base = smem_u32(sm);
+  const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lanes
+  uint32_t phase = 0;
+  bool failed = false;  // uniform across the CTA (decided by __syncthreads_or)
+  const int64_t tiles = (R + TM - 1) / TM;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t row = tile * TM + t;
+    const bool valid = row < R;
+    // 1. x row -> bf16 A tile of layer 1
+    {
+      float xv[TI];
+#pragma unroll
+      for (int k = 0; k < TI; k += 4) {
+        const float4 v = valid ? *reinterpret_cast<const float4*>(x + row * TI + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        xv[k] = v.x; xv[k + 1] = v.y; xv[k + 2] = v.z; xv[k + 3] = v.w;
+      }
+#pragma unroll
+      for (int k8 = 0; k8 < TI; k8 += 8)
+        *reinterpret_cast<uint4*>(sm + OFF_XS + core_off(t, k8, SBO_K16)) =
+            make_uint4(pack2(xv[k8], xv[k8 + 1]), pack2(xv[k8 + 2], xv[k8 + 3]), pack2(xv[k8 + 4], xv[k8 + 5]),
+                       pack2(xv[k8 + 6], xv[k8 + 7]));
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    // 2. layer 1 (one K-16 step)
+    if (t == 0) {
+      mma_bf16(tmem, sdesc(base + OFF_XS, 128, SBO_K16), sdesc(base + OFF_W1S, 128, SBO_K16), 0u);
+      commit(mbar);
+    }
+    if (__syncthreads_or(!wait_parity(mbar, phase))) {
+      failed = true;
+      break;
+    }
+    phase ^= 1u;
+    fence_after();
+    // 3. epilogue 1: h1 = bf16(relu(D1 + b1)) -> A tile of layer 2 (and h1)
+#pragma unroll 1
+    for (int c0 = 0; c0 < TH; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + lane_addr + (uint32_t)c0, v);
+      uint32_t pk[16];
+#pragma unroll
+      for (int k = 0; k < 32; k += 2)
+        pk[k / 2] = pack2(fmaxf(v[k] + par[c0 + k], 0.f), fmaxf(v[k + 1] + par[c0 + k + 1], 0.f));
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint4 u = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+        *reinterpret_cast<uint4*>(sm + OFF_HS + core_off(t, c0 + 8 * q, SBO_K128)) = u;
+        if (h1 && valid) *reinterpret_cast<uint4*>(h1 + row * TH + c0 + 8 * q) = u;
+      }
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    // 4. layer 2 (eight K-16 steps)
+    if (t == 0) {
+#pragma unroll
+      for (int kk = 0; kk < TH / 16; ++kk)
+        mma_bf16(tmem + TH, sdesc(base + OFF_HS + kk * 256, 128, SBO_K128),
+                 sdesc(base + OFF_W2S + kk * 256, 128, SBO_K128), kk > 0 ? 1u : 0u);
+      commit(mbar);
+    }
+    if (__syncthreads_or(!wait_parity(mbar, phase))) {
+      failed = true;
+      break;
+    }
+    phase ^= 1u;
+    fence_after();
+    // 5. epilogue 2: h2 = bf16(relu(D2 + b2)), y = W3 . h2 + b3
+    float acc = 0.f;
+#pragma unroll 1
+    for (int c0 = 0; c0 < TH; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + lane_addr + (uint32_t)(TH + c0), v);
+      uint32_t pk[16];
+#pragma unroll
+      for (int k = 0; k < 32; k += 2) {
+        pk[k / 2] = pack2(fmaxf(v[k] + par[TH + c0 + k], 0.f), fmaxf(v[k + 1] + par[TH + c0 + k + 1], 0.f));
+        acc += __uint_as_float(pk[k / 2] << 16) * par[2 * TH + c0 + k] +
+               __uint_as_float(pk[k / 2] & 0xffff0000u) * par[2 * TH + c0 + k + 1];
+      }
+      if (h2 && valid) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          *reinterpret_cast<uint4*>(h2 + row * TH + c0 + 8 * q) =
+              make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+      }
+    }
+    if (valid) y[row] = acc + par[3 * TH];
+    // every thread is done reading TMEM and the A tiles before the next MMAs
+    fence_before();
+    __syncthreads();
+    fence_after();
+  }
+  if (failed) {
+    if (t == 0 && status) atomicExch(status, 1);
+    wait_parity(mbar, phase);  // the MMAs still in flight (phase not yet observed; bounded)
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+}  // namespace
+}  // namespace tgs
+
+using namespace tgs;
+
+extern "C" tgs_status tgs_mlp_forward_tc(const tgs_mlp* w, int64_t rows, const float* x, float* y, uint16_t* h1,
+                                         uint16_t* h2, int32_t* status, tgs_stream stream) {
+  if (!w || !w->w1 || !w->w2 || !w->w3 || !w->b1 || !w->b2 || !w->b3 || rows < 0 || (rows > 0 && (!x || !y)))
+    return TGS_ERR_INVALID_ARG;
+  if (!aligned16(w->w1) || !aligned16(w->w2) || !aligned16(x) || (h1 && !aligned16(h1)) || (h2 && !aligned16(h2)))
+    return TGS_ERR_INVALID_ARG;
+  if (rows == 0) return TGS_OK;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return check_launch();
+  static bool attr[64] = {};
+  if (dev < 0 || dev >= 64) return TGS_ERR_DEVICE;
+  if (!attr[dev]) {
+    cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_REQ);
+    attr[dev] = true;
+  }
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = (rows + TM - 1) / TM;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 2ll * sms));
+  k_mlp_forward_tc<<<grid, kTcThreads, SMEM_REQ, (cudaStream_t)stream>>>(
+      TcArgs{w->w1, w->w2, w->w3, w->b1, w->b2, w->b3}, x, rows, y, h1, h2, status);
+  return check_launch();
+}

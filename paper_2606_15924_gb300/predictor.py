@@ -1,7 +1,7 @@
 """Learned tile-error predictor (an extension; the paper has no counterpart).
 
 A 3-layer MLP (16 -> 128 -> 128 -> 1, ReLU; bf16 weights, fp32 accumulate)
-run by the library's own kernels predicts log(1 + mean tile error) from
+run by the library's own kernels (forward on the tcgen05 tensor cores) predicts log(1 + mean tile error) from
 per-tile features, so tile selection can use fresh predictions for views
 whose error maps are stale instead of a dense refresh render.  Master weights
 are fp32 (packed W1 | b1 | W2 | b2 | W3 | b3); the kernels read bf16 copies.
@@ -67,8 +67,9 @@ class TileErrorMLP:
                     b2=p[sl["b2"]], W3=p[sl["W3"]], b3=p[sl["b3"]])
 
     def predict(self, x: torch.Tensor) -> torch.Tensor:
+        """Inference on the tcgen05 tensor cores."""
         y = torch.empty(x.shape[0], device=x.device)
-        B.mlp_forward(self.net(), x.contiguous(), y)
+        B.mlp_forward_tc(self.net(), x.contiguous(), y)
         return y
 
     def train_step(self, x: torch.Tensor, target: torch.Tensor, rows_dev=None) -> torch.Tensor:
@@ -79,7 +80,7 @@ class TileErrorMLP:
         y = torch.empty(R, device=x.device)
         h1 = torch.empty(R, HID, dtype=torch.int16, device=x.device)
         h2 = torch.empty(R, HID, dtype=torch.int16, device=x.device)
-        B.mlp_forward(self.net(), x, y, h1, h2)
+        B.mlp_forward_tc(self.net(), x, y, h1, h2)
         B.mlp_backward(self.net(), x, h1, h2, y, target.contiguous(), self.grads, self.loss, rows_dev=rows_dev)
         self.step_count += 1
         B.mlp_adam(self.params, self.grads, self.m, self.v, self.step_count, self.lr, 0.9, 0.999, 1e-8, self.net())

@@ -27,8 +27,11 @@ def _features(R, seed):
     return x
 
 
+@pytest.mark.parametrize("tc", [False, True])
 @pytest.mark.parametrize("R", [1, 15, 16, 1000, 4097])
-def test_forward_parity(P, orc, R):
+def test_forward_parity(P, orc, R, tc):
+    """tc: the tcgen05 kernel (128-row tiles, accumulators in tensor memory);
+    otherwise the mma.sync kernel."""
     B, TileErrorMLP = P
     mlp = TileErrorMLP(seed=R)
     x = _features(R, R)
@@ -36,7 +39,12 @@ def test_forward_parity(P, orc, R):
     y = torch.empty(R, device="cuda")
     h1 = torch.empty(R, 128, dtype=torch.int16, device="cuda")
     h2 = torch.empty(R, 128, dtype=torch.int16, device="cuda")
-    B.mlp_forward(mlp.net(), xd, y, h1, h2)
+    if tc:
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        B.mlp_forward_tc(mlp.net(), xd, y, h1, h2, status=status)
+        assert int(status.item()) == 0
+    else:
+        B.mlp_forward(mlp.net(), xd, y, h1, h2)
     yw, h1w, h2w = orc.mlp_forward(x, mlp.weights_fp(), bf16=True)
     got = y.cpu().numpy()
     assert rel_l2(got, yw) <= 1e-3
