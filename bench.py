@@ -239,7 +239,8 @@ def measured_traffic(stage: str):
 
 # Stages that are one kernel of the library (render_backward also zeroes
 # grad2d first); the others chain several small kernels.
-SINGLE_KERNEL_STAGES = ("render_sampled", "render_backward", "project_backward", "project_gaussians")
+SINGLE_KERNEL_STAGES = ("render_sampled", "render_backward", "project_backward", "project_backward_update",
+                        "project_gaussians")
 
 
 def roofline(stage_ms, info, peaks, peak_kind, clocks, tr, dom=None):
@@ -264,6 +265,8 @@ def roofline(stage_ms, info, peaks, peak_kind, clocks, tr, dom=None):
         byts = n * (44 + 48) + info["visible"] * 192
     elif dom == "project_backward":
         byts = n * 5 + info["visible"] * 48 + info["touched"] * 236 * 2
+    elif dom == "project_backward_update":  # params, m, v read and written; no gradient
+        byts = n * 5 + info["visible"] * 48 + info["touched"] * 236 * 6
     elif dom == "bin_tiles":
         byts = info["n_isect"] * 44
     elif dom == "select_tiles":
@@ -409,7 +412,8 @@ def run_ours(args):
     roof = roofline(st, info, peaks, peak_kind, clocks, sampled)
     roof["peak_source"] = f"{peak_kind} (MEASURED_PEAKS.json)" if peak_kind == "measured" else "fallback"
     stage_roofs = {k: roofline(st, info, peaks, peak_kind, clocks, sampled, dom=k) for k in st}
-    fwdbwd_ms = st["render_sampled"] + st["render_backward"] + st["project_backward"]
+    fwdbwd_ms = st["render_sampled"] + st["render_backward"] + st.get("project_backward",
+                                                                       st.get("project_backward_update", 0.0))
     mpix = info["P"] / (fwdbwd_ms * 1e-3) / 1e6
     res = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": mean_s, "higher_is_better": True, "scaling": "weak",
@@ -428,7 +432,9 @@ def run_ours(args):
         st_d, info_d = stage_times(dense, 2, flush)
         res["dense"] = {"iters_per_s": 1e3 / mean_d, "ms_per_step": mean_d, "pixels": info_d["P"],
                         "fwd_bwd_mpix_per_s": info_d["P"] / ((st_d["render_sampled"] + st_d["render_backward"] +
-                                                               st_d["project_backward"]) * 1e-3) / 1e6,
+                                                               st_d.get("project_backward",
+                                                                        st_d.get("project_backward_update", 0.0)))
+                                                              * 1e-3) / 1e6,
                         "stage_ms": st_d}
         res["speedup_vs_dense"] = mean_d / mean_s
     # end to end through the public API: target in from pinned host memory, loss out

@@ -385,6 +385,23 @@ tgs_status tgs_project_backward_multi(const tgs_gaussians* g, int32_t n_views, c
                                       tgs_stream stream);
 
 /*
+ * project_backward_update - project_backward_multi followed by hybrid_step in
+ * one pass (modes 0 and 1 of tgs_opt, whose update of a Gaussian needs only
+ * its own summed gradient): for each Gaussian that a view touched, the sum
+ * of the views' projection adjoints is formed in registers and shared memory
+ * and the Gaussian's parameters (params, in place), m and v are updated at
+ * once; no gradient is written.  touched as in project_backward_multi;
+ * workspace: tgs_project_backward_multi_workspace_size(n) bytes, 16-byte
+ * aligned.  Mode 2 (per-view Jacobian rows, Cholesky) is rejected: use
+ * project_backward_multi with view_rows and hybrid_step.
+ */
+tgs_status tgs_project_backward_update(const tgs_param_ptrs* params, int64_t n, int32_t sh_degree, int32_t n_views,
+                                       const tgs_camera* cams, const int32_t* const* radius,
+                                       const float* const* grad2d, const tgs_param_ptrs* m, const tgs_param_ptrs* v,
+                                       uint8_t* touched, const tgs_opt* opt, int32_t step, const int32_t* step_dev,
+                                       void* workspace, size_t workspace_bytes, tgs_stream stream);
+
+/*
  * Several views in one launch (not in the paper: a batching of
  * render_sampled / the compositing adjoint over the views of one iteration,
  * Alg. 1 steps 5 and 8).  Persistent thread blocks (grid_ctas of them) take

@@ -163,11 +163,25 @@ class MultiViewTrainer:
         B.hybrid_step(self.params, self.grads, self.m, self.v, self.n, self.touched, self.rows,
                       self.K if self.use_rows else 0, 1, self.opt, workspace=self.ws_hybrid, step_dev=self.step_dev)
 
+    @property
+    def fused(self) -> bool:
+        """Adjoint and update in one pass: the fused path of the persistent
+        trainer in modes 0 and 1 (no per-view rows)."""
+        return self.persistent and self.opt["mode"] in (0, 1) and not self.use_rows
+
+    def backward_update(self):
+        B.project_backward_update(self.params, self.adj, self.m, self.v, self.touched, self.opt, 1,
+                                  step_dev=self.step_dev, sh_degree=self.sh_degree, workspace=self.ws_adj)
+
     def step(self):
         self.forward()
         self.loss_and_maps()
-        self.backward()
-        self.update()
+        if self.fused:
+            self._render_bwd()
+            self.backward_update()
+        else:
+            self.backward()
+            self.update()
         B.advance_counters(self.it_dev, self.step_dev)
 
     def loss(self) -> float:
@@ -202,10 +216,12 @@ class MultiViewTrainer:
         def upd():
             self.update()
             B.advance_counters(self.it_dev, self.step_dev)
+        tail = ([("project_backward_update", lambda: (self.backward_update(),
+                                                      B.advance_counters(self.it_dev, self.step_dev)))]
+                if self.fused else [("project_backward", self._project_bwd), ("hybrid_step", upd)])
         return [("select_tiles", select), ("project_gaussians", project), ("bin_tiles", bins),
                 ("render_sampled", self._render_fwd), ("loss_sparse_ncc", self.loss_and_maps),
-                ("render_backward", self._render_bwd), ("project_backward", self._project_bwd),
-                ("hybrid_step", upd)]
+                ("render_backward", self._render_bwd)] + tail
 
     def capture_stages(self):
         self.stage_graphs = []

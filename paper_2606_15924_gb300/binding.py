@@ -144,6 +144,9 @@ _lib.tgs_project_backward_multi_workspace_size.restype = _sz
 _lib.tgs_project_backward_multi_workspace_size.argtypes = [_i64]
 _lib.tgs_project_backward_multi.argtypes = [_P(Gaussians), _i32, _P(Camera), _p, _p, _P(ParamPtrs), _p, _i32, _p,
                                             _p, _sz, _p]
+_lib.tgs_project_backward_update.restype = _i32
+_lib.tgs_project_backward_update.argtypes = [_P(ParamPtrs), _i64, _i32, _i32, _P(Camera), _p, _p, _P(ParamPtrs),
+                                             _P(ParamPtrs), _p, _P(Opt), _i32, _p, _p, _sz, _p]
 _lib.tgs_render_batched_resident.restype = _i32
 _lib.tgs_render_batched_resident.argtypes = [_i32, _i32, _P(_i32)]
 _lib.tgs_render_sampled_batched.restype = _i32
@@ -181,7 +184,7 @@ EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_devi
             "tgs_bin_tiles_workspace_size", "tgs_bin_tiles", "tgs_checkpoint_bytes", "tgs_render_sampled",
             "tgs_loss_sparse_ncc",
             "tgs_backward_sampled", "tgs_render_backward_sampled", "tgs_project_backward", "tgs_project_backward_multi_workspace_size",
-            "tgs_project_backward_multi",
+            "tgs_project_backward_multi", "tgs_project_backward_update",
             "tgs_render_batched_resident", "tgs_render_sampled_batched",
             "tgs_render_backward_batched", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step",
             "tgs_mlp_param_count", "tgs_mlp_forward", "tgs_mlp_forward_tc", "tgs_mlp_backward_workspace_size",
@@ -449,17 +452,35 @@ def hybrid_step_workspace_size(n: int) -> int:
     return int(_lib.tgs_hybrid_step_workspace_size(int(n)))
 
 
+def opt_struct(opt: dict) -> Opt:
+    o = Opt()
+    o.lr = (C.c_float * 6)(*[float(x) for x in opt["lr"]])
+    o.beta1, o.beta2 = float(opt["beta1"]), float(opt["beta2"])
+    o.eps_adam, o.eps_lm = float(opt["eps_adam"]), float(opt["eps_lm"])
+    o.mode = int(opt["mode"])
+    return o
+
+
+def project_backward_update(params: dict, adj, m: dict, v: dict, touched, opt: dict, step=1, step_dev=None,
+                            sh_degree=3, workspace=None, stream=None):
+    P, M, V = param_ptrs(params), param_ptrs(m), param_ptrs(v)
+    n = int(params["means"].shape[0])
+    if workspace is None:
+        workspace = torch.empty(project_backward_multi_workspace_size(n), dtype=torch.uint8,
+                                device=params["means"].device)
+    o = opt_struct(opt)
+    _check("tgs_project_backward_update", _lib.tgs_project_backward_update(
+        C.byref(P), n, int(sh_degree), adj.K, adj.cams, adj.radius, adj.grad2d, C.byref(M), C.byref(V),
+        _ptr(touched), C.byref(o), int(step), _ptr(step_dev), _ptr(workspace), workspace.numel(),
+        _stream(stream)))
+
+
 def hybrid_step(params: dict, grads: dict, m: dict, v: dict, n, touched, view_rows, k_rows, step, opt,
                 workspace=None, stream=None, step_dev=None):
     P, G, M, V = param_ptrs(params), param_ptrs(grads), param_ptrs(m), param_ptrs(v)
     if workspace is None:
         workspace = torch.empty(hybrid_step_workspace_size(n), dtype=torch.uint8, device=params["means"].device)
-    o = Opt()
-    lrs = opt["lr"]
-    o.lr = (C.c_float * 6)(*[float(x) for x in lrs])
-    o.beta1, o.beta2 = float(opt["beta1"]), float(opt["beta2"])
-    o.eps_adam, o.eps_lm = float(opt["eps_adam"]), float(opt["eps_lm"])
-    o.mode = int(opt["mode"])
+    o = opt_struct(opt)
     _check("tgs_hybrid_step", _lib.tgs_hybrid_step(
         C.byref(P), C.byref(G), C.byref(M), C.byref(V), int(n), _ptr(touched), _ptr(view_rows), int(k_rows),
         int(step), _ptr(step_dev), C.byref(o), _ptr(workspace), workspace.numel(), _stream(stream)))

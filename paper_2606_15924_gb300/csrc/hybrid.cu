@@ -4,88 +4,9 @@
 // (J^T J + diag(sqrt(v) + eps)) D = -m (Cholesky in mode 2), the 45 higher SH
 // coefficients take a bias-corrected Adam step.  Untouched Gaussians are not
 // read or written.
-#include "tgs_common.cuh"
+#include "hybrid_math.cuh"
 
 namespace tgs {
-
-struct OptK {
-  float lr[6];
-  float b1, b2, eps, eps_lm, bc1, bc2;
-  int mode;
-  const int32_t* step_dev;  // when set, bias corrections use this step
-};
-
-template <int D>
-__device__ __forceinline__ void lm_block(const float (&g)[D], const float (&m)[D], const float (&v)[D],
-                                         const float* __restrict__ rows, int k_rows, int64_t n, int64_t i, int off,
-                                         int mode, float eps_lm, float (&out)[D]) {
-  if (mode == 1) {
-    float jj[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) jj[a] = rows ? 0.f : g[a] * g[a];
-    for (int r = 0; rows && r < k_rows; ++r) {
-      const float* row = rows + ((size_t)r * n + i) * 14 + off;
-#pragma unroll
-      for (int a = 0; a < D; ++a) jj[a] += row[a] * row[a];
-    }
-#pragma unroll
-    for (int a = 0; a < D; ++a) out[a] = -m[a] / (jj[a] + sqrtf(v[a]) + eps_lm);
-    return;
-  }
-  // full J^T J: lower triangle, then Cholesky A = L L^T and two triangular solves
-  float A[D][D];
-#pragma unroll
-  for (int a = 0; a < D; ++a)
-#pragma unroll
-    for (int b = 0; b <= a; ++b) A[a][b] = rows ? 0.f : g[a] * g[b];
-  for (int r = 0; rows && r < k_rows; ++r) {
-    const float* row = rows + ((size_t)r * n + i) * 14 + off;
-    float J[D];
-#pragma unroll
-    for (int a = 0; a < D; ++a) J[a] = row[a];
-#pragma unroll
-    for (int a = 0; a < D; ++a)
-#pragma unroll
-      for (int b = 0; b <= a; ++b) A[a][b] += J[a] * J[b];
-  }
-#pragma unroll
-  for (int a = 0; a < D; ++a) A[a][a] += sqrtf(v[a]) + eps_lm;
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-#pragma unroll
-    for (int b = 0; b <= a; ++b) {
-      float s = A[a][b];
-#pragma unroll
-      for (int k = 0; k < b; ++k) s -= A[a][k] * A[b][k];
-      if (a == b) A[a][a] = sqrtf(fmaxf(s, 1e-30f));
-      else A[a][b] = s / A[b][b];
-    }
-  }
-  float y[D];
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    float s = -m[a];
-#pragma unroll
-    for (int k = 0; k < a; ++k) s -= A[a][k] * y[k];
-    y[a] = s / A[a][a];
-  }
-#pragma unroll
-  for (int a = D - 1; a >= 0; --a) {
-    float s = y[a];
-#pragma unroll
-    for (int k = a + 1; k < D; ++k) s -= A[k][a] * out[k];
-    out[a] = s / A[a][a];
-  }
-}
-
-__device__ __forceinline__ void moments(float g, float& m, float& v, const OptK& o) {
-  m = o.b1 * m + (1.f - o.b1) * g;
-  v = o.b2 * v + (1.f - o.b2) * g * g;
-}
-
-__device__ __forceinline__ float adam_delta(float m, float v, float lr, const OptK& o) {
-  return -lr * (m / o.bc1) / (sqrtf(v / o.bc2) + o.eps);
-}
 
 // Touched Gaussians appended to a list (order irrelevant: updates are
 // independent), one warp-aggregated atomic per warp.
@@ -102,13 +23,6 @@ __global__ void __launch_bounds__(256) k_compact_touched(const uint8_t* __restri
   if (on) list[base + __popc(b & ((1u << lane) - 1u))] = (int32_t)i;
 }
 
-__device__ __forceinline__ void bias_corrections(OptK& o) {
-  if (o.step_dev) {
-    const float st = (float)max(1, *o.step_dev);
-    o.bc1 = 1.f - powf(o.b1, st);
-    o.bc2 = 1.f - powf(o.b2, st);
-  }
-}
 
 // LM blocks (geometry 10, appearance 4) and the first SH float4 (DC colour +
 // one higher coefficient) of each touched Gaussian.
@@ -121,63 +35,17 @@ __global__ void __launch_bounds__(128) k_hybrid_lm(tgs_param_ptrs P, tgs_param_p
   const int64_t cnt = *count;
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += (int64_t)gridDim.x * blockDim.x) {
   const int64_t i = list[q];
-  float gp[10], gg[10], gm[10], gv[10];
+  float gg[10];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    gp[k] = P.means[3 * i + k]; gg[k] = G.means[3 * i + k]; gm[k] = M.means[3 * i + k]; gv[k] = V.means[3 * i + k];
-    gp[3 + k] = P.log_scales[3 * i + k]; gg[3 + k] = G.log_scales[3 * i + k];
-    gm[3 + k] = M.log_scales[3 * i + k]; gv[3 + k] = V.log_scales[3 * i + k];
+    gg[k] = G.means[3 * i + k];
+    gg[3 + k] = G.log_scales[3 * i + k];
   }
-  {
-    const float4 a = reinterpret_cast<const float4*>(P.quats)[i], b = reinterpret_cast<const float4*>(G.quats)[i];
-    const float4 c = reinterpret_cast<const float4*>(M.quats)[i], d = reinterpret_cast<const float4*>(V.quats)[i];
-    gp[6] = a.x; gp[7] = a.y; gp[8] = a.z; gp[9] = a.w;
-    gg[6] = b.x; gg[7] = b.y; gg[8] = b.z; gg[9] = b.w;
-    gm[6] = c.x; gm[7] = c.y; gm[8] = c.z; gm[9] = c.w;
-    gv[6] = d.x; gv[7] = d.y; gv[8] = d.z; gv[9] = d.w;
-  }
-  const float4 p0 = reinterpret_cast<const float4*>(P.sh)[12 * i], g0 = reinterpret_cast<const float4*>(G.sh)[12 * i];
-  const float4 m0 = reinterpret_cast<const float4*>(M.sh)[12 * i], v0 = reinterpret_cast<const float4*>(V.sh)[12 * i];
-  float sp[4] = {p0.x, p0.y, p0.z, p0.w}, sg[4] = {g0.x, g0.y, g0.z, g0.w};
-  float smm[4] = {m0.x, m0.y, m0.z, m0.w}, sv[4] = {v0.x, v0.y, v0.z, v0.w};
-  float op = P.opacity_logits[i], og = G.opacity_logits[i], om = M.opacity_logits[i], ov = V.opacity_logits[i];
-#pragma unroll
-  for (int k = 0; k < 10; ++k) moments(gg[k], gm[k], gv[k], o);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) moments(sg[k], smm[k], sv[k], o);
-  moments(og, om, ov, o);
-  if (MODE == 0) {
-#pragma unroll
-    for (int k = 0; k < 10; ++k) gp[k] += adam_delta(gm[k], gv[k], o.lr[k < 3 ? 0 : k < 6 ? 1 : 2], o);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) sp[k] += adam_delta(smm[k], sv[k], o.lr[4], o);
-    op += adam_delta(om, ov, o.lr[3], o);
-  } else {
-    float dgeo[10];
-    lm_block<10>(gg, gm, gv, rows, k_rows, n, i, 0, MODE, o.eps_lm, dgeo);
-#pragma unroll
-    for (int k = 0; k < 10; ++k) gp[k] += o.lr[k < 3 ? 0 : k < 6 ? 1 : 2] * dgeo[k];
-    const float ag[4] = {sg[0], sg[1], sg[2], og}, am[4] = {smm[0], smm[1], smm[2], om},
-                av[4] = {sv[0], sv[1], sv[2], ov};
-    float dapp[4];
-    lm_block<4>(ag, am, av, rows, k_rows, n, i, 10, MODE, o.eps_lm, dapp);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) sp[k] += o.lr[4] * dapp[k];
-    op += o.lr[3] * dapp[3];
-  }
-  sp[3] += adam_delta(smm[3], sv[3], o.lr[5], o);
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    P.means[3 * i + k] = gp[k]; M.means[3 * i + k] = gm[k]; V.means[3 * i + k] = gv[k];
-    P.log_scales[3 * i + k] = gp[3 + k]; M.log_scales[3 * i + k] = gm[3 + k]; V.log_scales[3 * i + k] = gv[3 + k];
-  }
-  reinterpret_cast<float4*>(P.quats)[i] = make_float4(gp[6], gp[7], gp[8], gp[9]);
-  reinterpret_cast<float4*>(M.quats)[i] = make_float4(gm[6], gm[7], gm[8], gm[9]);
-  reinterpret_cast<float4*>(V.quats)[i] = make_float4(gv[6], gv[7], gv[8], gv[9]);
-  P.opacity_logits[i] = op; M.opacity_logits[i] = om; V.opacity_logits[i] = ov;
-  reinterpret_cast<float4*>(P.sh)[12 * i] = make_float4(sp[0], sp[1], sp[2], sp[3]);
-  reinterpret_cast<float4*>(M.sh)[12 * i] = make_float4(smm[0], smm[1], smm[2], smm[3]);
-  reinterpret_cast<float4*>(V.sh)[12 * i] = make_float4(sv[0], sv[1], sv[2], sv[3]);
+  const float4 b = reinterpret_cast<const float4*>(G.quats)[i];
+  gg[6] = b.x; gg[7] = b.y; gg[8] = b.z; gg[9] = b.w;
+  const float4 g0 = reinterpret_cast<const float4*>(G.sh)[12 * i];
+  const float sg[4] = {g0.x, g0.y, g0.z, g0.w};
+  lm_update_one<MODE>(P, M, V, n, i, gg, sg, G.opacity_logits[i], rows, k_rows, o);
   }
 }
 
@@ -191,16 +59,8 @@ __global__ void __launch_bounds__(256) k_adam_sh(tgs_param_ptrs P, tgs_param_ptr
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
   const int64_t q = e / 11;
   const int k = 1 + (int)(e - q * 11);
-  const int64_t f = 12 * (int64_t)list[q] + k;
-  float4 pp = reinterpret_cast<const float4*>(P.sh)[f], gq = reinterpret_cast<const float4*>(G.sh)[f];
-  float4 mq = reinterpret_cast<const float4*>(M.sh)[f], vq = reinterpret_cast<const float4*>(V.sh)[f];
-  moments(gq.x, mq.x, vq.x, o); moments(gq.y, mq.y, vq.y, o);
-  moments(gq.z, mq.z, vq.z, o); moments(gq.w, mq.w, vq.w, o);
-  pp.x += adam_delta(mq.x, vq.x, o.lr[5], o); pp.y += adam_delta(mq.y, vq.y, o.lr[5], o);
-  pp.z += adam_delta(mq.z, vq.z, o.lr[5], o); pp.w += adam_delta(mq.w, vq.w, o.lr[5], o);
-  reinterpret_cast<float4*>(P.sh)[f] = pp;
-  reinterpret_cast<float4*>(M.sh)[f] = mq;
-  reinterpret_cast<float4*>(V.sh)[f] = vq;
+  const int64_t i = list[q];
+  adam_sh_one(P, M, V, i, k, reinterpret_cast<const float4*>(G.sh)[12 * i + k], o);
   }
 }
 
@@ -228,12 +88,7 @@ extern "C" tgs_status tgs_hybrid_step(const tgs_param_ptrs* params, const tgs_pa
   if (n == 0) return TGS_OK;
   if (!ptrs_ok(params) || !ptrs_ok(grads) || !ptrs_ok(m) || !ptrs_ok(v)) return TGS_ERR_INVALID_ARG;
   if (!workspace || workspace_bytes < tgs_hybrid_step_workspace_size(n)) return TGS_ERR_INVALID_ARG;
-  OptK o;
-  for (int k = 0; k < 6; ++k) o.lr[k] = opt->lr[k];
-  o.b1 = opt->beta1; o.b2 = opt->beta2; o.eps = opt->eps_adam; o.eps_lm = opt->eps_lm; o.mode = opt->mode;
-  o.step_dev = step_dev;
-  o.bc1 = (float)(1.0 - pow((double)opt->beta1, (double)step));
-  o.bc2 = (float)(1.0 - pow((double)opt->beta2, (double)step));
+  OptK o = make_optk(opt, step, step_dev);
   cudaStream_t s = (cudaStream_t)stream;
   Carver c(workspace);
   int32_t* list = c.take<int32_t>((size_t)n);

@@ -2,7 +2,7 @@
 // Sec. 3.1) and its adjoint.  One thread per Gaussian; SH coefficients and
 // quaternions move as float4; a Gaussian that misses every active tile is
 // culled before its SH block is read.
-#include "tgs_common.cuh"
+#include "hybrid_math.cuh"
 
 namespace tgs {
 
@@ -639,6 +639,51 @@ __global__ void __launch_bounds__(kAdjThreads, 4) k_adj_multi(
   }
 }
 
+// Fused: the adjoint of the touched Gaussians summed over the views, then
+// at once the hybrid update of their parameters and moments (modes 0 and 1:
+// the update of each Gaussian needs only its own gradient), so the gradient
+// never goes to memory.
+template <int MODE>
+__global__ void __launch_bounds__(kAdjThreads, 3) k_adj_update(
+    tgs_param_ptrs P, tgs_param_ptrs M, tgs_param_ptrs V, int64_t n, int sh_degree, MultiAdj mv,
+    const uint2* __restrict__ list, const int32_t* __restrict__ count, OptK o) {
+  __shared__ float s_sh[48 * kAdjThreads];
+  bias_corrections(o);
+  const int cnt = *count;
+  const float4* quats = reinterpret_cast<const float4*>(P.quats);
+  const float4* sh = reinterpret_cast<const float4*>(P.sh);
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+    const uint2 it = list[e];
+    const int64_t i = it.x;
+    unsigned hit = it.y;
+    const float3 mu = make_float3(P.means[3 * i], P.means[3 * i + 1], P.means[3 * i + 2]);
+    const float3 ls = make_float3(P.log_scales[3 * i], P.log_scales[3 * i + 1], P.log_scales[3 * i + 2]);
+    const float4 qr = quats[i];
+    const float o_s = 1.f / (1.f + expf(-P.opacity_logits[i]));
+    AdjAcc<SmemSh> acc;
+    acc.sh.base = s_sh + threadIdx.x;
+    acc.sh.stride = kAdjThreads;
+    acc_zero(acc);
+    while (hit) {
+      const int v = __ffs(hit) - 1;
+      hit &= hit - 1;
+      const float4* gp = mv.grad2d[v] + 3 * i;
+      view_adjoint(mv.cam[v], mu, ls, qr, o_s, sh + 12 * i, sh_degree, gp[0], gp[1], gp[2],
+                   mv.row[v] ? mv.row[v] + 14 * i : nullptr, acc);
+    }
+    const float gg[10] = {acc.mu[0], acc.mu[1], acc.mu[2], acc.ls[0], acc.ls[1], acc.ls[2],
+                          acc.q[0],  acc.q[1],  acc.q[2],  acc.q[3]};
+    const float sg[4] = {acc.sh.get(0), acc.sh.get(1), acc.sh.get(2), acc.sh.get(3)};
+    lm_update_one<MODE>(P, M, V, n, i, gg, sg, acc.o, nullptr, 0, o);
+#pragma unroll 1
+    for (int k4 = 1; k4 < 12; ++k4)
+      adam_sh_one(P, M, V, i, k4,
+                  make_float4(acc.sh.get(4 * k4), acc.sh.get(4 * k4 + 1), acc.sh.get(4 * k4 + 2),
+                              acc.sh.get(4 * k4 + 3)),
+                  o);
+  }
+}
+
 }  // namespace tgs
 
 using namespace tgs;
@@ -695,6 +740,66 @@ extern "C" tgs_status tgs_project_backward_multi(const tgs_gaussians* g, int32_t
                                            mv, list, count, grads->means, grads->log_scales,
                                            reinterpret_cast<float4*>(grads->quats), grads->opacity_logits,
                                            reinterpret_cast<float4*>(grads->sh));
+  return check_launch();
+}
+
+extern "C" tgs_status tgs_project_backward_update(const tgs_param_ptrs* params, int64_t n, int32_t sh_degree,
+                                                  int32_t n_views, const tgs_camera* cams,
+                                                  const int32_t* const* radius, const float* const* grad2d,
+                                                  const tgs_param_ptrs* m, const tgs_param_ptrs* v,
+                                                  uint8_t* touched, const tgs_opt* opt, int32_t step,
+                                                  const int32_t* step_dev, void* workspace, size_t workspace_bytes,
+                                                  tgs_stream stream) {
+  if (!params || n < 0 || n >= INT32_MAX || sh_degree < 0 || sh_degree > 3 || n_views < 1 ||
+      n_views > kMaxAdjViews || !cams || !radius || !grad2d || !m || !v || !opt || step < 1 || opt->mode < 0 ||
+      opt->mode > 1 || !(opt->beta1 >= 0.f && opt->beta1 < 1.f) || !(opt->beta2 >= 0.f && opt->beta2 < 1.f))
+    return TGS_ERR_INVALID_ARG;
+  const tgs_gaussians gs{params->means, params->log_scales, params->quats, params->opacity_logits, params->sh, n,
+                         sh_degree};
+  const tgs_gaussians* g = &gs;
+  if (!gaussians_ok(g)) return TGS_ERR_INVALID_ARG;
+  for (const tgs_param_ptrs* q : {m, v})
+    if (!q->means || !q->log_scales || !q->quats || !q->opacity_logits || !q->sh || !aligned16(q->quats) ||
+        !aligned16(q->sh))
+      return TGS_ERR_INVALID_ARG;
+  if (!workspace || !aligned16(workspace) || workspace_bytes < tgs_project_backward_multi_workspace_size(g->n))
+    return TGS_ERR_INVALID_ARG;
+  MultiAdj mv;
+  mv.n_views = n_views;
+  for (int k = 0; k < n_views; ++k) {
+    if (!camera_ok(cams + k) || !radius[k] || !grad2d[k] || !aligned16(grad2d[k])) return TGS_ERR_INVALID_ARG;
+    mv.cam[k] = make_cam(cams[k]);
+    mv.radius[k] = radius[k];
+    mv.grad2d[k] = reinterpret_cast<const float4*>(grad2d[k]);
+    mv.row[k] = nullptr;
+  }
+  if (g->n == 0) return TGS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* count = reinterpret_cast<int32_t*>(workspace);
+  uint2* list = reinterpret_cast<uint2*>(reinterpret_cast<char*>(workspace) + 256);
+  cudaMemsetAsync(count, 0, sizeof(int32_t), s);
+  // the mark pass writes no gradients (nothing to zero)
+  k_adj_mark<<<(int)((g->n + 255) / 256), 256, 0, s>>>(g->n, mv, touched, 0, nullptr, nullptr, nullptr, nullptr,
+                                                       nullptr, list, count);
+  static int grid_dev[64][2] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) return TGS_ERR_DEVICE;
+  const int md = opt->mode;
+  if (!grid_dev[dev][md]) {
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (md == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_update<0>, kAdjThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_update<1>, kAdjThreads, 0);
+    grid_dev[dev][md] = std::max(1, sms * std::max(1, per_sm));
+  }
+  const int grid = (int)std::min<int64_t>(grid_dev[dev][md], (g->n + kAdjThreads - 1) / kAdjThreads);
+  const tgs_param_ptrs P = *params;
+  const OptK o = make_optk(opt, step, step_dev);
+  if (md == 0)
+    k_adj_update<0><<<grid, kAdjThreads, 0, s>>>(P, *m, *v, g->n, g->sh_degree, mv, list, count, o);
+  else
+    k_adj_update<1><<<grid, kAdjThreads, 0, s>>>(P, *m, *v, g->n, g->sh_degree, mv, list, count, o);
   return check_launch();
 }
 

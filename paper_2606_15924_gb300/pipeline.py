@@ -32,8 +32,9 @@ class Trainer:
     def __init__(self, params: dict, cam: dict, target: torch.Tensor, tile_fraction: float = 0.2,
                  pixel_rate: float = 1.0 / 3.0, cfg: Config | None = None, dense: bool = False,
                  capacity: int | None = None, seed: int = 0, bg=(0.0, 0.0, 0.0), sh_degree: int = 3,
-                 view: int = 0, train: bool = True):
+                 view: int = 0, train: bool = True, fuse_update: bool = True):
         self.cfg = cfg or Config()
+        self.fuse_update = fuse_update
         self.params = params
         self.n = int(params["means"].shape[0])
         self.cam = cam
@@ -186,12 +187,26 @@ class Trainer:
         B.hybrid_step(self.params, self.grads, self.m, self.v, self.n, self.touched, None, 0, 1, self.opt,
                       workspace=self.ws_hybrid, step_dev=self.step_dev)
 
+    def backward_update(self):
+        """Projection adjoint and hybrid update in one pass (modes 0, 1):
+        the parameter gradients are not written."""
+        B.project_backward_update(self.params, self.adj, self.m, self.v, self.touched, self.opt, 1,
+                                  step_dev=self.step_dev, sh_degree=self.sh_degree, workspace=self.ws_adj)
+
+    @property
+    def fused(self) -> bool:
+        return self.fuse_update and self.opt["mode"] in (0, 1)
+
     def step(self):
         """One full iteration; advances the device counters."""
         self.forward()
         self.loss_and_maps()
-        self.backward()
-        self.update()
+        if self.fused:
+            self.render_backward()
+            self.backward_update()
+        else:
+            self.backward()
+            self.update()
         B.advance_counters(self.it_dev, self.step_dev)
 
     # ------------------------------------------------------------------ graph
@@ -232,9 +247,9 @@ class Trainer:
                                                             self.pix_idx, self.n_pix, self.ccam, self.bg, self.rgb,
                                                             self.T_final, self.n_last, ckpt=self.ckpt)),
                 ("loss_sparse_ncc", self.loss_and_maps),
-                ("render_backward", self.render_backward),
-                ("project_backward", self.project_backward),
-                ("hybrid_step", lambda: (self.update(), bump()))]
+                ("render_backward", self.render_backward)] + (
+                [("project_backward_update", lambda: (self.backward_update(), bump()))] if self.fused else
+                [("project_backward", self.project_backward), ("hybrid_step", lambda: (self.update(), bump()))])
 
     def capture_stages(self):
         """One CUDA graph per call of the step, so each call's device time can

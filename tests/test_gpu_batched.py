@@ -233,3 +233,44 @@ def test_fused_multiview_adjoint_equals_per_view_sum(B):
         assert _close(fused[k][t], mv.grads[k][t], rel=1e-5), k
         assert torch.all(fused[k][~t] == 7.0), k
     assert _close(fused_rows, mv.rows, rel=1e-6)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("views", [1, 4])
+def test_fused_adjoint_update_equals_separate_calls(B, mode, views):
+    """project_backward_update == project_backward_multi + hybrid_step on the
+    same state (parameters, moments, touched), one view or several."""
+    mv = _make(mode=mode)
+    mv.forward()
+    mv.loss_and_maps()
+    mv._render_bwd()
+    torch.cuda.synchronize()
+    keys = ("means", "log_scales", "quats", "opacity_logits", "sh")
+    rng = torch.Generator(device="cuda").manual_seed(5)
+    m0 = {k: torch.rand(mv.m[k].shape, generator=rng, device="cuda") * 1e-3 for k in keys}
+    v0 = {k: torch.rand(mv.v[k].shape, generator=rng, device="cuda") * 1e-4 for k in keys}
+    p0 = {k: mv.params[k].clone() for k in keys}
+    adj = mv.adj if views == 4 else B.MultiAdjoint([mv.views[1].ccam], [mv.views[1].proj["radius"]],
+                                                   [mv.views[1].grad2d])
+    step = torch.full((1,), 3, dtype=torch.int32, device="cuda")
+    # separate calls
+    pa = {k: p0[k].clone() for k in keys}
+    ma = {k: m0[k].clone() for k in keys}
+    va = {k: v0[k].clone() for k in keys}
+    grads = {k: torch.zeros_like(p0[k]) for k in keys}
+    ta = torch.zeros(mv.n, dtype=torch.uint8, device="cuda")
+    B.project_backward_multi(pa, adj, grads, ta, write_untouched=False)
+    B.hybrid_step(pa, grads, ma, va, mv.n, ta, None, 0, 1, mv.opt, step_dev=step)
+    # fused
+    pb = {k: p0[k].clone() for k in keys}
+    mb = {k: m0[k].clone() for k in keys}
+    vb = {k: v0[k].clone() for k in keys}
+    tb = torch.zeros(mv.n, dtype=torch.uint8, device="cuda")
+    B.project_backward_update(pb, adj, mb, vb, tb, mv.opt, 1, step_dev=step)
+    torch.cuda.synchronize()
+    assert torch.equal(ta, tb) and int(ta.sum().item()) > 100
+    for k in keys:
+        for a, b, name in ((pa[k], pb[k], "param"), (ma[k], mb[k], "m"), (va[k], vb[k], "v")):
+            assert torch.allclose(a, b, rtol=1e-5, atol=1e-9), (k, name, float((a - b).abs().max()))
+        untouched = ~ta.bool()
+        assert torch.equal(pb[k][untouched], p0[k][untouched])     # untouched Gaussians keep their state
