@@ -57,7 +57,43 @@ def load_peaks():
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 
+class NvmlClocks:
+    """SM clock and clock-event reasons read through NVML's C API (ctypes), so
+    that a timed region of a few milliseconds still gets samples.  Read-only:
+    no setting of the GPU is touched."""
+    # nvmlClocksEventReasons bits (nvml.h)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, gpu_index):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(gpu_index), ctypes.byref(self.h)) != 0:
+            raise OSError("no NVML handle")
+        try:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        v = ctypes.c_uint()
+        self.max_mhz = float(v.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ctypes.byref(v)) == 0 else None
+
+    def sample(self):
+        ct = self.ct
+        v, r = ct.c_uint(), ct.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(v)) != 0:
+            return None
+        reasons = []
+        if self.reasons_fn(self.h, ct.byref(r)) == 0:
+            reasons = [nm for bit, nm in self.REASONS.items() if r.value & bit]
+        return float(v.value), reasons
+
+
 class ClockSampler:
+    """Clocks during the timed region: NVML every 2 ms in a thread where the
+    library loads, else nvidia-smi every 200 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -65,9 +101,20 @@ class ClockSampler:
     def __init__(self, gpu_index=0):
         self.gpu = gpu_index
         self.proc = None
+        self.nvml = None
         self.lines = []
+        self.samples = []
+        self.stop_flag = threading.Event()
 
     def start(self):
+        try:
+            self.nvml = NvmlClocks(self.gpu)
+        except OSError:
+            self.nvml = None
+        if self.nvml is not None:
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+            return
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
                                           "--format=csv,noheader,nounits", "-lms", "200"],
@@ -77,11 +124,25 @@ class ClockSampler:
         except OSError:
             self.proc = None
 
+    def _poll(self):
+        while not self.stop_flag.is_set():
+            s = self.nvml.sample()
+            if s is not None:
+                self.samples.append(s)
+            self.stop_flag.wait(0.002)
+
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
     def stop(self):
+        if self.nvml is not None:
+            self.stop_flag.set()
+            self.t.join(timeout=5)
+            sm = [s[0] for s in self.samples]
+            reasons = sorted({r for s in self.samples for r in s[1]})
+            return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": self.nvml.max_mhz,
+                    "reasons": reasons, "samples": len(sm), "source": "nvml"}
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -104,7 +165,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": "nvidia-smi"}
 
 
 # ---------------------------------------------------------------------------
@@ -564,14 +625,14 @@ def run_batched(args):
 MLP_ROWS = 200 * 8487   # tile rows of a 200-view orbit at 1957x1091
 
 
-def mlp_bench(device, peaks, steps: int = 10) -> dict:
+def mlp_bench(device, peaks, steps: int = 10, rows: int = MLP_ROWS) -> dict:
     """The tile-error MLP's forward and training step over one row per tile of
     a 200-view set, against the bf16 tensor peak: 2 (16*128 + 128*128 + 128)
     FLOPs per row forward, twice that more for the backward."""
     import torch
     from paper_2606_15924_gb300 import binding as B
     from paper_2606_15924_gb300.predictor import TileErrorMLP, HID
-    R = MLP_ROWS
+    R = int(rows)
     mlp = TileErrorMLP(device)
     g = torch.Generator(device="cpu").manual_seed(4)
     x = torch.randn(R, 16, generator=g).to(device)
@@ -699,6 +760,8 @@ def main():
                          "sampled training until it is within 0.1 dB of the dense PSNR (device time)")
     ap.add_argument("--dense-iters", type=int, default=2000)
     ap.add_argument("--no-quality", action="store_true", help="skip the equal-PSNR comparison in the default run")
+    ap.add_argument("--mlp-rows", type=int, default=0,
+                    help="only the tile-error MLP kernels on this many rows (for a small profile), one JSON line")
     ap.add_argument("--workload", default="step", choices=["step", "batched"],
                     help="step: the one-view sparse training step (the headline line); batched: 8 views per "
                          "iteration in one persistent launch vs one launch per view")
@@ -710,6 +773,13 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.mlp_rows > 0:
+        import torch
+        from paper_2606_15924_gb300 import binding as B
+        B.device_check()
+        peaks, _ = load_peaks()
+        print(json.dumps({"metric": "tile-error MLP", **mlp_bench(torch.device("cuda", 0), peaks,
+                                                                 rows=args.mlp_rows)}))
     elif args.quality:
         run_quality(args)
     elif args.workload == "batched":
