@@ -9,18 +9,13 @@
 namespace tgs {
 
 // Touched Gaussians appended to a list (order irrelevant: updates are
-// independent), one warp-aggregated atomic per warp.
+// independent), one atomic per block.
 __global__ void __launch_bounds__(256) k_compact_touched(const uint8_t* __restrict__ touched, int64_t n,
                                                          int32_t* __restrict__ list, int32_t* __restrict__ count) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool on = i < n && (!touched || touched[i]);
-  const unsigned b = __ballot_sync(0xffffffffu, on);
-  if (!b) return;
-  const int lane = threadIdx.x & 31;
-  int base = 0;
-  if (lane == __ffs(b) - 1) base = atomicAdd(count, __popc(b));
-  base = __shfl_sync(0xffffffffu, base, __ffs(b) - 1);
-  if (on) list[base + __popc(b & ((1u << lane) - 1u))] = (int32_t)i;
+  const int64_t pos = block_append(on, count);
+  if (on) list[pos] = (int32_t)i;
 }
 
 

@@ -8,10 +8,19 @@ namespace tgs {
 
 struct OptK {
   float lr[6];
-  float b1, b2, eps, eps_lm, bc1, bc2;
+  float b1, b2, eps, eps_lm, ibc1, ibc2;  // ibc: reciprocals of the bias corrections 1 - beta^t
   int mode;
   const int32_t* step_dev;  // when set, bias corrections use this step
 };
+
+// Square root and quotient through the SFU approximations (relative error a
+// few 1e-7): the update's step sizes need no more, and the IEEE forms cost
+// several times the instructions of the moment arithmetic around them.
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 template <int D>
 __device__ __forceinline__ void lm_block(const float (&g)[D], const float (&m)[D], const float (&v)[D],
@@ -27,7 +36,7 @@ __device__ __forceinline__ void lm_block(const float (&g)[D], const float (&m)[D
       for (int a = 0; a < D; ++a) jj[a] += row[a] * row[a];
     }
 #pragma unroll
-    for (int a = 0; a < D; ++a) out[a] = -m[a] / (jj[a] + sqrtf(v[a]) + eps_lm);
+    for (int a = 0; a < D; ++a) out[a] = __fdividef(-m[a], jj[a] + sqrt_approx(v[a]) + eps_lm);
     return;
   }
   // full J^T J: lower triangle, then Cholesky A = L L^T and two triangular solves
@@ -82,14 +91,14 @@ __device__ __forceinline__ void moments(float g, float& m, float& v, const OptK&
 }
 
 __device__ __forceinline__ float adam_delta(float m, float v, float lr, const OptK& o) {
-  return -lr * (m / o.bc1) / (sqrtf(v / o.bc2) + o.eps);
+  return __fdividef(-lr * (m * o.ibc1), sqrt_approx(v * o.ibc2) + o.eps);
 }
 
 __device__ __forceinline__ void bias_corrections(OptK& o) {
   if (o.step_dev) {
     const float st = (float)max(1, *o.step_dev);
-    o.bc1 = 1.f - powf(o.b1, st);
-    o.bc2 = 1.f - powf(o.b2, st);
+    o.ibc1 = 1.f / (1.f - powf(o.b1, st));
+    o.ibc2 = 1.f / (1.f - powf(o.b2, st));
   }
 }
 
@@ -181,8 +190,8 @@ inline OptK make_optk(const tgs_opt* opt, int32_t step, const int32_t* step_dev)
   for (int k = 0; k < 6; ++k) o.lr[k] = opt->lr[k];
   o.b1 = opt->beta1; o.b2 = opt->beta2; o.eps = opt->eps_adam; o.eps_lm = opt->eps_lm; o.mode = opt->mode;
   o.step_dev = step_dev;
-  o.bc1 = (float)(1.0 - pow((double)opt->beta1, (double)step));
-  o.bc2 = (float)(1.0 - pow((double)opt->beta2, (double)step));
+  o.ibc1 = (float)(1.0 / (1.0 - pow((double)opt->beta1, (double)step)));
+  o.ibc2 = (float)(1.0 / (1.0 - pow((double)opt->beta2, (double)step)));
   return o;
 }
 

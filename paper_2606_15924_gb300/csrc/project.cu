@@ -596,13 +596,8 @@ __global__ void __launch_bounds__(256) k_adj_mark(int64_t n, MultiAdj mv, uint8_
     if (touched) touched[i] = hit ? 1 : 0;
     if (!hit && write_untouched) zero_grads(i, g_means, g_ls, g_quats, g_ologit, g_sh);
   }
-  const unsigned m = __ballot_sync(0xffffffffu, hit != 0);
-  if (!m) return;
-  const int lane = threadIdx.x & 31;
-  int base = 0;
-  if (lane == 0) base = atomicAdd(count, __popc(m));
-  base = __shfl_sync(0xffffffffu, base, 0);
-  if (hit) list[base + __popc(m & ((1u << lane) - 1u))] = make_uint2((uint32_t)i, hit);
+  const int64_t pos = block_append(hit != 0, count);
+  if (hit) list[pos] = make_uint2((uint32_t)i, hit);
 }
 
 constexpr int kAdjThreads = 128;
@@ -643,44 +638,94 @@ __global__ void __launch_bounds__(kAdjThreads, 4) k_adj_multi(
 // at once the hybrid update of their parameters and moments (modes 0 and 1:
 // the update of each Gaussian needs only its own gradient), so the gradient
 // never goes to memory.
+//
+// A block takes 128 list entries at a time in two phases.  Phase 1, one
+// thread per Gaussian: the adjoint (SH gradient into a shared-memory column)
+// and the update of the LM blocks and SH float4 0.  Phase 2, the whole block:
+// the Adam update of SH float4s 1..11 of the 128 Gaussians, a quad of lanes
+// on four consecutive float4s of one row (64 contiguous bytes per Gaussian
+// and load), eight Gaussians per warp, every load of a lane issued before its
+// first store.  The column stride kShStride = 130 keeps both phases free of
+// shared-memory bank conflicts (phase 1: bank 2k + t; phase 2: bank
+// 8 kk + g8 + const over the warp's lanes).
+constexpr int kShStride = 130;
+
 template <int MODE>
 __global__ void __launch_bounds__(kAdjThreads, 3) k_adj_update(
     tgs_param_ptrs P, tgs_param_ptrs M, tgs_param_ptrs V, int64_t n, int sh_degree, MultiAdj mv,
     const uint2* __restrict__ list, const int32_t* __restrict__ count, OptK o) {
-  __shared__ float s_sh[48 * kAdjThreads];
+  __shared__ float s_sh[48 * kShStride];
+  __shared__ uint32_t s_idx[kAdjThreads];
   bias_corrections(o);
   const int cnt = *count;
   const float4* quats = reinterpret_cast<const float4*>(P.quats);
   const float4* sh = reinterpret_cast<const float4*>(P.sh);
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
-    const uint2 it = list[e];
-    const int64_t i = it.x;
-    unsigned hit = it.y;
-    const float3 mu = make_float3(P.means[3 * i], P.means[3 * i + 1], P.means[3 * i + 2]);
-    const float3 ls = make_float3(P.log_scales[3 * i], P.log_scales[3 * i + 1], P.log_scales[3 * i + 2]);
-    const float4 qr = quats[i];
-    const float o_s = 1.f / (1.f + expf(-P.opacity_logits[i]));
-    AdjAcc<SmemSh> acc;
-    acc.sh.base = s_sh + threadIdx.x;
-    acc.sh.stride = kAdjThreads;
-    acc_zero(acc);
-    while (hit) {
-      const int v = __ffs(hit) - 1;
-      hit &= hit - 1;
-      const float4* gp = mv.grad2d[v] + 3 * i;
-      view_adjoint(mv.cam[v], mu, ls, qr, o_s, sh + 12 * i, sh_degree, gp[0], gp[1], gp[2],
-                   mv.row[v] ? mv.row[v] + 14 * i : nullptr, acc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int kk = lane >> 3, g8 = lane & 7;
+  for (int b0 = blockIdx.x * kAdjThreads; b0 < cnt; b0 += gridDim.x * kAdjThreads) {
+    const int e = b0 + threadIdx.x;
+    if (e < cnt) {
+      const uint2 it = list[e];
+      const int64_t i = it.x;
+      unsigned hit = it.y;
+      const float3 mu = make_float3(P.means[3 * i], P.means[3 * i + 1], P.means[3 * i + 2]);
+      const float3 ls = make_float3(P.log_scales[3 * i], P.log_scales[3 * i + 1], P.log_scales[3 * i + 2]);
+      const float4 qr = quats[i];
+      const float o_s = 1.f / (1.f + expf(-P.opacity_logits[i]));
+      AdjAcc<SmemSh> acc;
+      acc.sh.base = s_sh + threadIdx.x;
+      acc.sh.stride = kShStride;
+      acc_zero(acc);
+      while (hit) {
+        const int v = __ffs(hit) - 1;
+        hit &= hit - 1;
+        const float4* gp = mv.grad2d[v] + 3 * i;
+        view_adjoint(mv.cam[v], mu, ls, qr, o_s, sh + 12 * i, sh_degree, gp[0], gp[1], gp[2],
+                     mv.row[v] ? mv.row[v] + 14 * i : nullptr, acc);
+      }
+      const float gg[10] = {acc.mu[0], acc.mu[1], acc.mu[2], acc.ls[0], acc.ls[1], acc.ls[2],
+                            acc.q[0],  acc.q[1],  acc.q[2],  acc.q[3]};
+      const float sg[4] = {acc.sh.get(0), acc.sh.get(1), acc.sh.get(2), acc.sh.get(3)};
+      lm_update_one<MODE>(P, M, V, n, i, gg, sg, acc.o, nullptr, 0, o);
+      s_idx[threadIdx.x] = it.x;
     }
-    const float gg[10] = {acc.mu[0], acc.mu[1], acc.mu[2], acc.ls[0], acc.ls[1], acc.ls[2],
-                          acc.q[0],  acc.q[1],  acc.q[2],  acc.q[3]};
-    const float sg[4] = {acc.sh.get(0), acc.sh.get(1), acc.sh.get(2), acc.sh.get(3)};
-    lm_update_one<MODE>(P, M, V, n, i, gg, sg, acc.o, nullptr, 0, o);
+    __syncthreads();
+    const int ng = min(kAdjThreads, cnt - b0);
 #pragma unroll 1
-    for (int k4 = 1; k4 < 12; ++k4)
-      adam_sh_one(P, M, V, i, k4,
-                  make_float4(acc.sh.get(4 * k4), acc.sh.get(4 * k4 + 1), acc.sh.get(4 * k4 + 2),
-                              acc.sh.get(4 * k4 + 3)),
-                  o);
+    for (int pass = 0; pass < kAdjThreads / 32; ++pass) {
+      const int gl = 32 * pass + 8 * warp + g8;
+      if (gl < ng) {
+        const int64_t row = 12 * (int64_t)s_idx[gl];
+        float4 pp[3], mq[3], vq[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const int k4 = kk + 4 * r;
+          if (k4 == 0) continue;
+          pp[r] = reinterpret_cast<const float4*>(P.sh)[row + k4];
+          mq[r] = reinterpret_cast<const float4*>(M.sh)[row + k4];
+          vq[r] = reinterpret_cast<const float4*>(V.sh)[row + k4];
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const int k4 = kk + 4 * r;
+          if (k4 == 0) continue;
+          const float* c = s_sh + (4 * k4) * kShStride + gl;
+          const float gq[4] = {c[0], c[kShStride], c[2 * kShStride], c[3 * kShStride]};
+          float* p4 = &pp[r].x;
+          float* m4 = &mq[r].x;
+          float* v4 = &vq[r].x;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            moments(gq[u], m4[u], v4[u], o);
+            p4[u] += adam_delta(m4[u], v4[u], o.lr[5], o);
+          }
+          reinterpret_cast<float4*>(P.sh)[row + k4] = pp[r];
+          reinterpret_cast<float4*>(M.sh)[row + k4] = mq[r];
+          reinterpret_cast<float4*>(V.sh)[row + k4] = vq[r];
+        }
+      }
+    }
+    __syncthreads();
   }
 }
 

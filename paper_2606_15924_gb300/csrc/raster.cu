@@ -22,6 +22,7 @@ constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTStop = 1e-4f;
+constexpr int kUnroll = 4;  // splats per step of the forward walk
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -114,22 +115,33 @@ __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Spla
     __syncthreads();
     if (base + B + (int)threadIdx.x < range.y) load_splat(a, base + B + threadIdx.x, nxt);
     const int cnt = min(B, range.y - base);
-    if (!done) {
-      for (int q = 0; q < cnt; ++q) {
-        const Splat sp = sm[q];
-        float alpha, G;
-        if (!splat_alpha(sp.co, __fsub_rn(px, sp.xy.x), __fsub_rn(py, sp.xy.y), alpha, G)) continue;
-        const float Tn = __fmul_rn(T, __fsub_rn(1.f, alpha));
+    // kUnroll splats at a time: their alphas do not depend on T, so they are
+    // evaluated together and only the blend runs in list order.  B is a
+    // multiple of 32, so sm[q0 .. q0 + kUnroll - 1] stays inside the batch.
+    for (int q0 = 0; q0 < cnt && !done; q0 += kUnroll) {
+      float al[kUnroll];
+      bool ok[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const float2 xy = sm[q0 + u].xy;
+        float G;
+        ok[u] = splat_alpha(sm[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G) && q0 + u < cnt;
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        if (!ok[u]) continue;
+        const float Tn = __fmul_rn(T, __fsub_rn(1.f, al[u]));
         if (Tn < kTStop) {
           done = true;
           break;
         }
-        const float w = alpha * T;
-        C0 += w * sp.rgb.x;
-        C1 += w * sp.rgb.y;
-        C2 += w * sp.rgb.z;
+        const float4 rgb = sm[q0 + u].rgb;
+        const float w = al[u] * T;
+        C0 += w * rgb.x;
+        C1 += w * rgb.y;
+        C2 += w * rgb.z;
         T = Tn;
-        last = base + q + 1 - range.x;
+        last = base + q0 + u + 1 - range.x;
       }
     }
   }
@@ -257,7 +269,7 @@ __device__ __forceinline__ void render_tile_bwd(const RasterArgs& a, int j, Spla
         float alpha, G;
         if (splat_alpha(sp.co, dx, dy, alpha, G)) {
           hit = true;
-          T = T / (1.f - alpha);  // transmittance in front of this splat
+          T = __fdividef(T, 1.f - alpha);  // transmittance in front of this splat (1 - alpha >= 0.01)
           const float wgt = alpha * T;
           v[6] = wgt * g0;
           v[7] = wgt * g1;
@@ -399,7 +411,7 @@ __device__ __forceinline__ void render_piece_bwd(const RasterArgs& a, int j, int
         float alpha, G;
         if (splat_alpha(sp.co, dx, dy, alpha, G)) {
           hit = true;
-          T = T / (1.f - alpha);
+          T = __fdividef(T, 1.f - alpha);
           const float wgt = alpha * T;
           v[6] = wgt * g0;
           v[7] = wgt * g1;

@@ -70,39 +70,38 @@ struct HashKeys {
   }
 };
 
-__global__ void __launch_bounds__(256) k_tile_stats(const uint16_t* __restrict__ err, const uint16_t* __restrict__ age,
-                                                    SelGeom g, HashKeys hk, SelWs w) {
-  __shared__ uint64_t sw[8];
-  __shared__ uint32_t sa[8];
-  const int t = blockIdx.x;
-  const int l = threadIdx.x;
-  const int x = (t % g.tx) * TGS_TILE + (l & 15), y = (t / g.tx) * TGS_TILE + (l >> 4);
+// One warp per tile, eight tiles per block: lane l sums the error weights
+// and takes the minimum age of the eight pixels (row l / 2, columns
+// 8 (l % 2) .. + 7), then the warp reduces.
+constexpr int kStatsTilesPerBlock = 8;
+
+__global__ void __launch_bounds__(32 * kStatsTilesPerBlock) k_tile_stats(const uint16_t* __restrict__ err,
+                                                                         const uint16_t* __restrict__ age,
+                                                                         SelGeom g, HashKeys hk, SelWs w) {
+  const int t = blockIdx.x * kStatsTilesPerBlock + (threadIdx.x >> 5);
+  if (t >= g.T) return;  // whole warps
+  const int l = threadIdx.x & 31;
+  const int y = (t / g.tx) * TGS_TILE + (l >> 1), x0 = (t % g.tx) * TGS_TILE + 8 * (l & 1);
   uint64_t wv = 0;
   uint32_t av = 0xFFFFFFFFu;
-  if (x < g.W && y < g.H) {
-    const size_t k = (size_t)y * g.W + x;
-    wv = err_weight(err[k]);
-    av = age[k];
+  if (y < g.H) {
+    const size_t row = (size_t)y * g.W;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      if (x0 + u < g.W) {
+        wv += err_weight(err[row + x0 + u]);
+        av = min(av, (uint32_t)age[row + x0 + u]);
+      }
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     wv += __shfl_xor_sync(0xffffffffu, wv, o);
     av = min(av, __shfl_xor_sync(0xffffffffu, av, o));
   }
-  if ((l & 31) == 0) {
-    sw[l >> 5] = wv;
-    sa[l >> 5] = av;
-  }
-  __syncthreads();
   if (l == 0) {
-    uint64_t s = 0;
-    uint32_t a = 0xFFFFFFFFu;
-    for (int k = 0; k < 8; ++k) {
-      s += sw[k];
-      a = min(a, sa[k]);
-    }
-    w.tile_w[t] = s;
-    w.tile_age[t] = a;
+    w.tile_w[t] = wv;
+    w.tile_age[t] = av;
     w.tile_L[t] = neglog2_q32(hash_item(hk.prefix(STREAM_TILE_HARD), (uint32_t)t, 0));
     w.tile_u[t] = hash_item(hk.prefix(STREAM_TILE_UNIF), (uint32_t)t, 0);
   }
@@ -162,6 +161,7 @@ struct RadixSelSmem {
   int32_t total;
   int32_t digit;
   int32_t below;
+  int32_t count;  // keys in the chosen digit's bin
 };
 
 // Exclusive prefix over threads of v (thread order); *total receives the sum.
@@ -267,6 +267,7 @@ __device__ void block_radix_select(const uint64_t (&key)[ITEMS], const bool (&el
           if (run + c[q] >= (uint32_t)kk) {
             sm.digit = lane * 8 + q;
             sm.below = (int)run;
+            sm.count = (int)c[q];
             break;
           }
           run += c[q];
@@ -277,6 +278,14 @@ __device__ void block_radix_select(const uint64_t (&key)[ITEMS], const bool (&el
     prefix |= (uint64_t)sm.digit << shift;
     mask |= 255ull << shift;
     kk -= sm.below;
+    if (kk == sm.count) {
+      // every key matching the prefix is taken, so the digits below decide
+      // nothing: the k smallest are the keys whose leading digits are at most
+      // the prefix
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j) taken[j] = elig[j] && (key[j] & mask) <= prefix;
+      return;
+    }
   }
   // every key below K = prefix is taken; of the keys equal to K, the first kk
   int ties = 0;
@@ -451,7 +460,9 @@ static tgs_status launch_select(const uint16_t* err_map, const uint16_t* age_map
   const HashKeys hk{seed, iter, iter_dev, view};
   int kh, ks;
   split_counts(n_sel, cfg->tile_hard_pm, cfg->tile_stable_pm, kh, ks);
-  if (n_sel < T && n_sel > 0) k_tile_stats<<<T, 256, 0, s>>>(err_map, age_map, g, hk, w);
+  if (n_sel < T && n_sel > 0)
+    k_tile_stats<<<(T + kStatsTilesPerBlock - 1) / kStatsTilesPerBlock, 32 * kStatsTilesPerBlock, 0, s>>>(
+        err_map, age_map, g, hk, w);
   if (T <= kSelBlockMaxTiles) {
     // one block: the three phases and the compaction
     if (T <= kSelThreads * 4)

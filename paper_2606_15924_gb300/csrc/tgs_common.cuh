@@ -156,4 +156,28 @@ __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float 
                : "memory");
 }
 
+// Position of this thread's entry in a list appended to by every block, with
+// one atomic on the length counter per block (a counter hit once per warp by
+// thousands of warps serialises in L2).  Entries of a block keep thread
+// order.  Every thread of the block calls it, once per kernel; blockDim.x is
+// a multiple of 32.  The result is meaningful only where on is true.
+__device__ __forceinline__ int64_t block_append(bool on, int32_t* count) {
+  __shared__ int s_off[33];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned b = __ballot_sync(0xffffffffu, on);
+  if (lane == 0) s_off[w] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int k = 0; k < nw; ++k) {
+      const int c = s_off[k];
+      s_off[k] = tot;
+      tot += c;
+    }
+    s_off[32] = tot ? atomicAdd(count, tot) : 0;
+  }
+  __syncthreads();
+  return (int64_t)s_off[32] + s_off[w] + __popc(b & ((1u << lane) - 1u));
+}
+
 }  // namespace tgs
