@@ -309,11 +309,88 @@ struct RangeSrc {
   }
 };
 
+// Register-tiled bitonic sort of N = kSortThreads * E keys (E a power of two
+// up to 16) for the tile lists that fit in shared memory.  Thread t holds the
+// keys at positions t E .. t E + E - 1 in registers.  A compare-exchange
+// stage at distance j runs in registers for j < E, through warp shuffles for
+// E <= j < 32 E, and through shared memory only for j >= 32 E: of the
+// log2(N) (log2(N) + 1) / 2 stages, at most 6 touch shared memory (the
+// whole-list network in shared memory reads and writes every key at every
+// stage, which is what bounded it).  The shared-memory layout pads one word
+// after every E, so that both the blocked (t E + r) and the exchange accesses
+// hit distinct banks.
+__device__ __forceinline__ int pad_idx(int i, int E) { return E > 1 ? i + i / E : i; }
+
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m) {
+  const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, m);
+  const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), m);
+  return ((uint64_t)hi << 32) | lo;
+}
+
+// Sorts sm[pad_idx(0 .. N - 1, E)] ascending in place (N = kSortThreads E).
+// Both stage loops have compile-time trip counts and are unrolled, so every
+// distance j, and with it the kind of stage, is a constant.
+template <int E>
+__device__ __forceinline__ void bitonic_tile(uint64_t* sm) {
+  constexpr int N = kSortThreads * E;
+  constexpr int L = (N >= 4096) ? 12 : (N >= 2048) ? 11 : (N >= 1024) ? 10 : (N >= 512) ? 9 : 8;
+  static_assert((1 << L) == N, "N is a power of two from 256 to 4096");
+  const int t = threadIdx.x, base = t * E;
+  uint64_t k[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) k[r] = sm[pad_idx(base + r, E)];
+#pragma unroll
+  for (int lk = 1; lk <= L; ++lk) {
+    const int kk = 1 << lk;
+    const bool up = (base & kk) == 0;  // for kk > E the direction is the thread's
+#pragma unroll
+    for (int lj = lk - 1; lj >= 0; --lj) {
+      const int j = 1 << lj;
+      if (j < E) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          if (r & j) continue;
+          const bool u = ((base + r) & kk) == 0;
+          const uint64_t a = k[r], b = k[r | j];
+          const bool sw = (b < a) == u;  // a == b: no change either way
+          k[r] = sw ? b : a;
+          k[r | j] = sw ? a : b;
+        }
+        continue;
+      }
+      const int m = j / E;  // partner thread t ^ m
+      const bool keep_min = ((t & m) == 0) == up;
+      if (m < 32) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const uint64_t y = shfl_xor_u64(k[r], m);
+          k[r] = ((y < k[r]) == keep_min) ? y : k[r];
+        }
+      } else {
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < E; ++r) sm[pad_idx(base + r, E)] = k[r];
+        __syncthreads();
+        const int pb = (t ^ m) * E;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+          const uint64_t y = sm[pad_idx(pb + r, E)];
+          k[r] = ((y < k[r]) == keep_min) ? y : k[r];
+        }
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < E; ++r) sm[pad_idx(base + r, E)] = k[r];
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kSortThreads) k_tile_sort(uint64_t* __restrict__ keys, RangeSrc src,
                                                             const int32_t* __restrict__ inv_rank, int64_t cap,
                                                             int32_t* __restrict__ vals, uint64_t* __restrict__ full_keys,
                                                             int2* __restrict__ ranges) {
-  __shared__ uint64_t sk[kSortSmem];
+  __shared__ uint64_t sk[kSortSmem + kSortSmem / 16];
   const int r = blockIdx.x;
   int64_t s0, e0;
   src.get(r, s0, e0);
@@ -321,18 +398,30 @@ __global__ void __launch_bounds__(kSortThreads) k_tile_sort(uint64_t* __restrict
   if (threadIdx.x == 0) ranges[r] = make_int2((int)s, (int)e);
   const int n = (int)(e - s);
   if (n <= 0) return;
-  uint64_t* K;
-  if (n <= kSortSmem) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) sk[i] = keys[s + i];
-    __syncthreads();
-    K = sk;
-  } else {
-    K = keys + s;  // long list: the same network in global memory
-  }
-  bitonic_sort(K, n);
   const uint64_t tile_hi = full_keys ? ((uint64_t)(uint32_t)inv_rank[r] << 32) : 0;
+  if (n > kSortSmem) {  // long list: the whole-list network in global memory
+    bitonic_sort(keys + s, n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const uint64_t k = keys[s + i];
+      vals[s + i] = (int32_t)(uint32_t)k;
+      if (full_keys) full_keys[s + i] = tile_hi | (k >> 32);
+    }
+    return;
+  }
+  const int E = n <= kSortThreads ? 1 : n <= 2 * kSortThreads ? 2 : n <= 4 * kSortThreads ? 4
+              : n <= 8 * kSortThreads ? 8 : 16;
+  const int N = kSortThreads * E;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) sk[pad_idx(i, E)] = i < n ? keys[s + i] : ~0ull;
+  __syncthreads();
+  switch (E) {
+    case 1: bitonic_tile<1>(sk); break;
+    case 2: bitonic_tile<2>(sk); break;
+    case 4: bitonic_tile<4>(sk); break;
+    case 8: bitonic_tile<8>(sk); break;
+    default: bitonic_tile<16>(sk); break;
+  }
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const uint64_t k = K[i];
+    const uint64_t k = sk[pad_idx(i, E)];
     vals[s + i] = (int32_t)(uint32_t)k;
     if (full_keys) full_keys[s + i] = tile_hi | (k >> 32);
   }

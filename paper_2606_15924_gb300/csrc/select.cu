@@ -70,38 +70,88 @@ struct HashKeys {
   }
 };
 
-// One warp per tile, eight tiles per block: lane l sums the error weights
-// and takes the minimum age of the eight pixels (row l / 2, columns
-// 8 (l % 2) .. + 7), then the warp reduces.
-constexpr int kStatsTilesPerBlock = 8;
+// 32 tiles per block of 8 warps, 4 tiles per warp: lane l sums the error
+// weights and takes the minimum age of eight pixels of each (row l / 2,
+// columns 8 (l % 2) .. + 7; one 16-byte load per map where the row allows
+// it), all four tiles' loads in flight together, then the warp reduces.  The
+// draws (-log2 of a hash, 32 dependent squarings) then run one tile per lane
+// of the first warp.
+constexpr int kStatsTiles = 32;
+constexpr int kStatsPerWarp = kStatsTiles / 8;
 
-__global__ void __launch_bounds__(32 * kStatsTilesPerBlock) k_tile_stats(const uint16_t* __restrict__ err,
-                                                                         const uint16_t* __restrict__ age,
-                                                                         SelGeom g, HashKeys hk, SelWs w) {
-  const int t = blockIdx.x * kStatsTilesPerBlock + (threadIdx.x >> 5);
-  if (t >= g.T) return;  // whole warps
-  const int l = threadIdx.x & 31;
-  const int y = (t / g.tx) * TGS_TILE + (l >> 1), x0 = (t % g.tx) * TGS_TILE + 8 * (l & 1);
-  uint64_t wv = 0;
-  uint32_t av = 0xFFFFFFFFu;
-  if (y < g.H) {
-    const size_t row = (size_t)y * g.W;
+__device__ __forceinline__ void pixel_row8(const uint16_t* __restrict__ err, const uint16_t* __restrict__ age,
+                                           const SelGeom& g, int t, int lane, bool vec, uint64_t& wv,
+                                           uint32_t& av) {
+  wv = 0;
+  av = 0xFFFFFFFFu;
+  if (t >= g.T) return;
+  const int y = (t / g.tx) * TGS_TILE + (lane >> 1), x0 = (t % g.tx) * TGS_TILE + 8 * (lane & 1);
+  if (y >= g.H) return;
+  const size_t p = (size_t)y * g.W + x0;
+  uint16_t e[8], a[8];
+  if (vec && x0 + 8 <= g.W) {  // 16-byte aligned: both maps are, and x0 and W are multiples of 8
+    const uint4 ev = *reinterpret_cast<const uint4*>(err + p), avv = *reinterpret_cast<const uint4*>(age + p);
+    const uint32_t ew[4] = {ev.x, ev.y, ev.z, ev.w}, aw[4] = {avv.x, avv.y, avv.z, avv.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      e[2 * u] = (uint16_t)(ew[u] & 0xFFFFu);
+      e[2 * u + 1] = (uint16_t)(ew[u] >> 16);
+      a[2 * u] = (uint16_t)(aw[u] & 0xFFFFu);
+      a[2 * u + 1] = (uint16_t)(aw[u] >> 16);
+    }
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
+      wv += err_weight(e[u]);
+      av = min(av, (uint32_t)a[u]);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
       if (x0 + u < g.W) {
-        wv += err_weight(err[row + x0 + u]);
-        av = min(av, (uint32_t)age[row + x0 + u]);
+        wv += err_weight(err[p + u]);
+        av = min(av, (uint32_t)age[p + u]);
       }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_tile_stats(const uint16_t* __restrict__ err,
+                                                    const uint16_t* __restrict__ age, SelGeom g, HashKeys hk,
+                                                    SelWs w, bool vec) {
+  __shared__ uint64_t s_w[kStatsTiles];
+  __shared__ uint32_t s_a[kStatsTiles];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t0 = blockIdx.x * kStatsTiles;
+  uint64_t wv[kStatsPerWarp];
+  uint32_t av[kStatsPerWarp];
+#pragma unroll
+  for (int q = 0; q < kStatsPerWarp; ++q)
+    pixel_row8(err, age, g, t0 + kStatsPerWarp * warp + q, lane, vec, wv[q], av[q]);
+#pragma unroll
+  for (int q = 0; q < kStatsPerWarp; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      wv[q] += __shfl_xor_sync(0xffffffffu, wv[q], o);
+      av[q] = min(av[q], __shfl_xor_sync(0xffffffffu, av[q], o));
     }
   }
+  if (lane < kStatsPerWarp) {
+    // lane q keeps tile q of the warp (register arrays indexed by constants)
+    uint64_t ww = wv[0];
+    uint32_t aa = av[0];
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    wv += __shfl_xor_sync(0xffffffffu, wv, o);
-    av = min(av, __shfl_xor_sync(0xffffffffu, av, o));
+    for (int q = 1; q < kStatsPerWarp; ++q)
+      if (lane == q) {
+        ww = wv[q];
+        aa = av[q];
+      }
+    s_w[kStatsPerWarp * warp + lane] = ww;
+    s_a[kStatsPerWarp * warp + lane] = aa;
   }
-  if (l == 0) {
-    w.tile_w[t] = wv;
-    w.tile_age[t] = av;
+  __syncthreads();
+  const int t = t0 + lane;
+  if (warp == 0 && t < g.T) {
+    w.tile_w[t] = s_w[lane];
+    w.tile_age[t] = s_a[lane];
     w.tile_L[t] = neglog2_q32(hash_item(hk.prefix(STREAM_TILE_HARD), (uint32_t)t, 0));
     w.tile_u[t] = hash_item(hk.prefix(STREAM_TILE_UNIF), (uint32_t)t, 0);
   }
@@ -149,23 +199,26 @@ __global__ void __launch_bounds__(256) k_rank_tiles(SelWs w, int T, int phase, i
 // Exact block-wide k-selection by radix select: the k smallest (key, index)
 // pairs among the eligible items of the block, keys < 2^nbits, items held
 // ITEMS per thread in index order (thread t holds t * ITEMS + j).  The k-th
-// smallest key K is found one 8-bit digit at a time from the top (a shared
-// histogram of the keys that match the digits found so far, and one warp
-// locating the digit where the running count reaches k); every key below K is
-// taken, and the ties at K in index order until k are reached.  Every thread
-// of the block must call it (it synchronises); k is the same on all threads.
+// smallest key K is found one 8-bit digit at a time from the top: a pass
+// first takes the block-wide minimum and maximum of the digit over the keys
+// that match the digits found so far (one digit: nothing to count), else
+// counts them in a shared histogram, and every warp then locates the digit
+// where the running count reaches k by itself (no second barrier).  Once the
+// chosen bin holds exactly the keys still wanted, those are taken and the
+// lower digits are never looked at; otherwise every key below K is taken, and
+// the ties at K in index order until k are reached.  Every thread of the
+// block must call it (it synchronises); k is the same on all threads.
+// Buffers that a pass writes before a barrier and reads after it alternate
+// between two copies, so that the next pass never overwrites what a slower
+// warp still reads.
 struct RadixSelSmem {
-  uint32_t hist[256];
-  uint32_t dmin[2], dmax[2];  // by pass parity: a pass never overwrites what the previous one still reads
-  int32_t warp_sum[32];
-  int32_t total;
-  int32_t digit;
-  int32_t below;
-  int32_t count;  // keys in the chosen digit's bin
+  uint32_t hist[2][256];
+  uint32_t wmin[2][32], wmax[2][32];
+  int32_t wcnt[2][32];
 };
 
-// Exclusive prefix over threads of v (thread order); *total receives the sum.
-__device__ __forceinline__ int64_t block_excl_sum(int64_t v, RadixSelSmem& sm, int64_t* s64, int64_t& total) {
+// Exclusive prefix over threads of v (thread order); total receives the sum.
+__device__ __forceinline__ int64_t block_excl_sum(int64_t v, int64_t* s64, int64_t& total) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
   int64_t x = v;
 #pragma unroll
@@ -175,33 +228,33 @@ __device__ __forceinline__ int64_t block_excl_sum(int64_t v, RadixSelSmem& sm, i
   }
   if (lane == 31) s64[w] = x;
   __syncthreads();
-  if (w == 0) {
-    int64_t t = lane < nw ? s64[lane] : 0;
+  int64_t t = lane < nw ? s64[lane] : 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
-    }
-    if (lane < nw) s64[lane] = t;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+    if (lane >= o) t += y;
   }
+  const int64_t upto = __shfl_sync(0xffffffffu, t, w > 0 ? w - 1 : 0);  // warps 0 .. w - 1
+  total = __shfl_sync(0xffffffffu, t, nw - 1);
   __syncthreads();
-  const int64_t before = (w > 0 ? s64[w - 1] : 0) + x - v;
-  total = s64[nw - 1];
-  __syncthreads();
-  return before;
+  return (w > 0 ? upto : 0) + x - v;
 }
 
+// call: 0, 1, 2 ... for consecutive selections of one kernel (buffer parity).
 template <int ITEMS>
 __device__ void block_radix_select(const uint64_t (&key)[ITEMS], const bool (&elig)[ITEMS], int k, int nbits,
-                                   bool (&taken)[ITEMS], RadixSelSmem& sm, int64_t* s64) {
+                                   bool (&taken)[ITEMS], RadixSelSmem& sm, int64_t* s64, int call) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) taken[j] = false;
   if (k <= 0) return;
   int mine = 0;
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) mine += elig[j];
-  int64_t n_elig;
-  block_excl_sum(mine, sm, s64, n_elig);
+  mine = __reduce_add_sync(0xffffffffu, mine);
+  if (lane == 0) sm.wcnt[call & 1][w] = mine;
+  __syncthreads();
+  const int n_elig = __reduce_add_sync(0xffffffffu, lane < nw ? sm.wcnt[call & 1][lane] : 0);
   if (k >= n_elig) {
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) taken[j] = elig[j];
@@ -209,11 +262,9 @@ __device__ void block_radix_select(const uint64_t (&key)[ITEMS], const bool (&el
   }
   uint64_t prefix = 0, mask = 0;
   int kk = k;  // rank (from 1) of the sought key among the keys matching the prefix
+  int hp = 0;  // histogram passes so far (buffer parity)
   for (int shift = ((nbits + 7) / 8) * 8 - 8; shift >= 0; shift -= 8) {
-    // Leading digits are often the same for every key still in play (the
-    // exponent of the hard keys, say): a block-wide min/max of the digit finds
-    // those passes, which need no histogram (and would otherwise pile every
-    // increment onto one shared-memory bin).
+    const int par = (shift >> 3) & 1;
     uint32_t dmin = 255u, dmax = 0u;
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j)
@@ -224,61 +275,79 @@ __device__ void block_radix_select(const uint64_t (&key)[ITEMS], const bool (&el
       }
     dmin = __reduce_min_sync(0xffffffffu, dmin);
     dmax = __reduce_max_sync(0xffffffffu, dmax);
-    const int par = (shift >> 3) & 1;
-    if (threadIdx.x == 0) {
-      sm.dmin[par] = 255u;
-      sm.dmax[par] = 0u;
+    if (lane == 0) {
+      sm.wmin[par][w] = dmin;
+      sm.wmax[par][w] = dmax;
     }
-    for (int b = threadIdx.x; b < 256; b += blockDim.x) sm.hist[b] = 0;
+    uint32_t* h = sm.hist[hp & 1];
+    for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) {
-      atomicMin(&sm.dmin[par], dmin);
-      atomicMax(&sm.dmax[par], dmax);
-    }
-    __syncthreads();
-    if (sm.dmin[par] == sm.dmax[par]) {  // one digit: every key in play has it
-      prefix |= (uint64_t)sm.dmin[par] << shift;
+    const uint32_t lo = __reduce_min_sync(0xffffffffu, lane < nw ? sm.wmin[par][lane] : 255u);
+    const uint32_t hi = __reduce_max_sync(0xffffffffu, lane < nw ? sm.wmax[par][lane] : 0u);
+    if (lo == hi) {  // one digit: every key in play has it
+      prefix |= (uint64_t)lo << shift;
       mask |= 255ull << shift;
       continue;
     }
+    const uint32_t span = hi - lo + 1u;
+    if (span <= 32u) {
+      // few distinct digits (exponent bits, small ages): counted per warp by
+      // ballots, lane q holding digit lo + q, then one atomic per warp and
+      // digit (shared atomics on a few hot bins would serialise)
+      uint32_t cnt = 0;
 #pragma unroll
-    for (int j = 0; j < ITEMS; ++j)
-      if (elig[j] && (key[j] & mask) == prefix) atomicAdd(&sm.hist[(key[j] >> shift) & 255u], 1u);
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
-      uint32_t c[8], sum = 0;
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        c[q] = sm.hist[lane * 8 + q];
-        sum += c[q];
-      }
-      uint32_t incl = sum;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const uint32_t excl = incl - sum;
-      if (excl < (uint32_t)kk && (uint32_t)kk <= incl) {
-        uint32_t run = excl;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          if (run + c[q] >= (uint32_t)kk) {
-            sm.digit = lane * 8 + q;
-            sm.below = (int)run;
-            sm.count = (int)c[q];
-            break;
-          }
-          run += c[q];
+      for (int j = 0; j < ITEMS; ++j) {
+        const uint32_t d = elig[j] && (key[j] & mask) == prefix ? (uint32_t)((key[j] >> shift) & 255u) - lo : 32u;
+        for (uint32_t q = 0; q < span; ++q) {
+          const uint32_t b = __ballot_sync(0xffffffffu, d == q);
+          if ((uint32_t)lane == q) cnt += __popc(b);
         }
       }
+      if (cnt) atomicAdd(&h[lo + lane], cnt);
+    } else {
+#pragma unroll
+      for (int j = 0; j < ITEMS; ++j)
+        if (elig[j] && (key[j] & mask) == prefix) atomicAdd(&h[(key[j] >> shift) & 255u], 1u);
     }
     __syncthreads();
-    prefix |= (uint64_t)sm.digit << shift;
+    ++hp;
+    // every warp: the digit where the running count reaches kk
+    uint32_t c[8], sum = 0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      c[q] = h[lane * 8 + q];
+      sum += c[q];
+    }
+    uint32_t incl = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    const uint32_t excl = incl - sum;
+    const unsigned at = __ballot_sync(0xffffffffu, excl < (uint32_t)kk && (uint32_t)kk <= incl);
+    const int src = __ffs(at) - 1;  // exactly one lane: 1 <= kk <= keys in play
+    int digit = 0, below = 0, count = 0;
+    if (lane == src) {
+      uint32_t run = excl;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        if (run + c[q] >= (uint32_t)kk) {
+          digit = lane * 8 + q;
+          below = (int)run;
+          count = (int)c[q];
+          break;
+        }
+        run += c[q];
+      }
+    }
+    digit = __shfl_sync(0xffffffffu, digit, src);
+    below = __shfl_sync(0xffffffffu, below, src);
+    count = __shfl_sync(0xffffffffu, count, src);
+    prefix |= (uint64_t)digit << shift;
     mask |= 255ull << shift;
-    kk -= sm.below;
-    if (kk == sm.count) {
+    kk -= below;
+    if (kk == count) {
       // every key matching the prefix is taken, so the digits below decide
       // nothing: the k smallest are the keys whose leading digits are at most
       // the prefix
@@ -292,7 +361,7 @@ __device__ void block_radix_select(const uint64_t (&key)[ITEMS], const bool (&el
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) ties += elig[j] && key[j] == prefix;
   int64_t all_ties;
-  int before = (int)block_excl_sum(ties, sm, s64, all_ties);
+  int before = (int)block_excl_sum(ties, s64, all_ties);
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
     const bool tie = elig[j] && key[j] == prefix;
@@ -333,21 +402,21 @@ __global__ void __launch_bounds__(kSelThreads) k_select_block(SelWs w, SelGeom g
       ts[j] = tu[j] = false;
     }
   } else {
-    block_radix_select<ITEMS>(key, elig, kh, 64, th, sm, s64);
+    block_radix_select<ITEMS>(key, elig, kh, 64, th, sm, s64, 0);
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
       const int i = threadIdx.x * ITEMS + j;
       elig[j] = valid[j] && !th[j];
       key[j] = valid[j] ? 0xFFFFull - min(w.tile_age[i], 0xFFFFu) : 0;
     }
-    block_radix_select<ITEMS>(key, elig, ks, 16, ts, sm, s64);
+    block_radix_select<ITEMS>(key, elig, ks, 16, ts, sm, s64, 1);
 #pragma unroll
     for (int j = 0; j < ITEMS; ++j) {
       const int i = threadIdx.x * ITEMS + j;
       elig[j] = valid[j] && !th[j] && !ts[j];
       key[j] = valid[j] ? (w.tile_u[i] >> 32) : 0;
     }
-    block_radix_select<ITEMS>(key, elig, n_sel - kh - ks, 32, tu, sm, s64);
+    block_radix_select<ITEMS>(key, elig, n_sel - kh - ks, 32, tu, sm, s64, 2);
   }
   // compaction: (taken count << 32 | pixel count) prefix in tile order
   int64_t mine = 0;
@@ -357,7 +426,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select_block(SelWs w, SelGeom g
     if (th[j] || ts[j] || tu[j]) mine += (1ll << 32) | (int64_t)min(n_pix, tile_valid(g, i));
   }
   int64_t total;
-  int64_t pre = block_excl_sum(mine, sm, s64, total);
+  int64_t pre = block_excl_sum(mine, s64, total);
 #pragma unroll
   for (int j = 0; j < ITEMS; ++j) {
     const int i = threadIdx.x * ITEMS + j;
@@ -417,13 +486,13 @@ __global__ void __launch_bounds__(256) k_sample_pixels(const uint16_t* __restric
     // phase 0: error-proportional draw; 1: oldest of the rest; 2: uniform of the rest
     uint64_t key[1] = {kh_key};
     bool el[1] = {valid}, th[1], ts[1], tu[1];
-    block_radix_select<1>(key, el, kh, 64, th, sm, s64);
+    block_radix_select<1>(key, el, kh, 64, th, sm, s64, 0);
     key[0] = 0xFFFFull - av;
     el[0] = valid && !th[0];
-    block_radix_select<1>(key, el, ks, 16, ts, sm, s64);
+    block_radix_select<1>(key, el, ks, 16, ts, sm, s64, 1);
     key[0] = ku_key;
     el[0] = valid && !th[0] && !ts[0];
-    block_radix_select<1>(key, el, n - kh - ks, 32, tu, sm, s64);
+    block_radix_select<1>(key, el, n - kh - ks, 32, tu, sm, s64, 2);
     taken = th[0] || ts[0] || tu[0];
   }
   // ascending compaction of the taken local indices
@@ -461,8 +530,8 @@ static tgs_status launch_select(const uint16_t* err_map, const uint16_t* age_map
   int kh, ks;
   split_counts(n_sel, cfg->tile_hard_pm, cfg->tile_stable_pm, kh, ks);
   if (n_sel < T && n_sel > 0)
-    k_tile_stats<<<(T + kStatsTilesPerBlock - 1) / kStatsTilesPerBlock, 32 * kStatsTilesPerBlock, 0, s>>>(
-        err_map, age_map, g, hk, w);
+    k_tile_stats<<<(T + kStatsTiles - 1) / kStatsTiles, 256, 0, s>>>(
+        err_map, age_map, g, hk, w, aligned16(err_map) && aligned16(age_map) && width % 8 == 0);
   if (T <= kSelBlockMaxTiles) {
     // one block: the three phases and the compaction
     if (T <= kSelThreads * 4)

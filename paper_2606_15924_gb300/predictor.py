@@ -111,7 +111,7 @@ class TileErrorPredictor:
     the network (``judge``)."""
 
     def __init__(self, device="cuda", seed: int = 0, lr: float = 1e-3, max_mse: float = 0.02,
-                 min_batches: int = 50, residual: bool = False):
+                 min_batches: int = 50, residual: bool = False, replay: int = 2048):
         self.mlp = TileErrorMLP(device, seed, lr)
         self.residual = residual
         self.device = device
@@ -120,6 +120,28 @@ class TileErrorPredictor:
         self.batches = 0
         self.recent_mse = None
         self.refreshes = {"predicted": 0, "plain": 0}
+        # replay ring of the latest observations (features as they were, target):
+        # each training step runs on all of it, not only on the step's few tiles
+        self.replay = int(replay)
+        self.buf_x = torch.zeros(max(self.replay, 1), IN, device=device)
+        self.buf_t = torch.zeros(max(self.replay, 1), device=device)
+        self.buf_n = 0
+        self.buf_head = 0
+
+    def _push(self, x: torch.Tensor, t: torch.Tensor):
+        cap = self.replay
+        A = x.shape[0]
+        if A > cap:
+            x, t, A = x[A - cap:], t[A - cap:], cap
+        i = self.buf_head
+        k = min(A, cap - i)
+        self.buf_x[i:i + k] = x[:k]
+        self.buf_t[i:i + k] = t[:k]
+        if k < A:
+            self.buf_x[:A - k] = x[k:]
+            self.buf_t[:A - k] = t[k:]
+        self.buf_head = (i + A) % cap
+        self.buf_n = min(self.buf_n + A, cap)
 
     def memory(self, tr) -> TileMemory:
         if tr.view not in self.memories:
@@ -135,19 +157,31 @@ class TileErrorPredictor:
             None, it=it))
 
     def observe_and_train(self, tr, it: int, view_cos: float = 1.0, train: bool = True):
+        """The step's active tiles: features from the memory as it was, then the
+        new observations recorded; with train, the error on them before
+        training (smoothed into recent_mse) and one Adam step.  With a replay
+        ring the step trains on the ring (this step's rows and the latest
+        before them), else on this step's rows alone.  The sampled step selects
+        exactly n_select tiles, so every row of the batch is an observation."""
         mem = self.memory(tr)
         A = tr.n_select
-        x = torch.empty(A, 16, device=self.device)
-        target = torch.empty(A, device=self.device)
+        x = torch.zeros(A, IN, device=self.device)
+        target = torch.zeros(A, device=self.device)
         B.tile_features(mem.mem, mem.it, tr.ccam, x, rows=tr.active_tiles, n_rows=tr.n_active, n_rows_max=A,
                         view_cos=view_cos, it=it)
         B.tile_observe(tr.active_tiles, tr.n_active, A, tr.pix_off, tr.ranges, tr.T_final, tr.err_pix, mem.mem,
                        mem.it, target, it=it, residual=self.residual)
-        if train:
+        if not train:
+            return
+        if self.replay:
+            mse = float(((self.mlp.predict(x) - target) ** 2).mean().item())
+            self._push(x, target)
+            self.mlp.train_step(self.buf_x[:self.buf_n], self.buf_t[:self.buf_n])
+        else:
             loss = self.mlp.train_step(x, target, rows_dev=tr.n_active)
             mse = 2.0 * float(loss.item())
-            self.batches += 1
-            self.recent_mse = mse if self.recent_mse is None else 0.9 * self.recent_mse + 0.1 * mse
+        self.batches += 1
+        self.recent_mse = mse if self.recent_mse is None else 0.9 * self.recent_mse + 0.1 * mse
 
     def features(self, tr, it: int, view_cos: float = 1.0) -> torch.Tensor:
         mem = self.memory(tr)

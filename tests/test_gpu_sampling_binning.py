@@ -128,6 +128,36 @@ def test_bin_tiles_crowded_tile_bit_exact(B, orc, n, n_crowd, presort):
     np.testing.assert_array_equal(out["keys"][:I].cpu().numpy().view(np.uint64), keys_w)
 
 
+# One tile's list grown through each size band of the per-tile sort (up to
+# 256, 512, 1024, 2048 and 4096 keys in registers, and past 4096 in global
+# memory), with exact depth ties, on the path without the depth presort.
+@pytest.mark.parametrize("n_crowd", [200, 300, 700, 1500, 3000, 3900, 4200])
+def test_bin_tiles_sort_bands_bit_exact(B, orc, n_crowd):
+    from gpu_util import bin_dev, projected_dev
+    W, H = 256, 256
+    n = n_crowd + 500
+    rng = np.random.default_rng(n_crowd)
+    pr = scenes.projected(n, W, H, seed=n)
+    xy = pr["xy"].copy()
+    xy[:n_crowd] = rng.uniform(101.0, 107.0, size=(n_crowd, 2))   # inside tile (6, 6)
+    pr["xy"] = xy.astype(np.float32)
+    radius = pr["radius"].copy()
+    radius[:n_crowd] = 1
+    pr["radius"] = radius.astype(np.int32)
+    depth = pr["depth"].copy()
+    depth[:n_crowd] = rng.uniform(1.0, 1.01, n_crowd)
+    depth[:n_crowd:5] = depth[2]                          # exact ties
+    pr["depth"] = depth.astype(np.float32)
+    keys_w, vals_w, counts_w = orc.bin_tiles(pr["xy"], pr["radius"], pr["depth"], W, H)
+    assert counts_w.max() >= n_crowd
+    cam = dict(viewmat=np.eye(4), fx=100.0, fy=100.0, cx=W / 2, cy=H / 2, width=W, height=H, znear=0.2)
+    out = bin_dev(B, projected_dev(pr), n, cam, None, 256, capacity=len(vals_w) + 3)
+    I = int(out["n_isect"].item())
+    assert I == len(vals_w)
+    np.testing.assert_array_equal(out["vals"][:I].cpu().numpy(), vals_w)
+    np.testing.assert_array_equal(out["keys"][:I].cpu().numpy().view(np.uint64), keys_w)
+
+
 def test_bin_tiles_edge_cases(B, orc):
     from gpu_util import bin_dev, projected_dev
     import torch
