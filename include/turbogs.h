@@ -243,11 +243,11 @@ tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const tgs_camera*
 /*
  * Checkpoints of the sampled forward (not in the paper: they let the
  * backward of Sec. 3.6 replay one tile's list in several independent pieces,
- * so a sparse step has enough parallel work).  With B = the block size of the
- * call (n_pix_max rounded up to a multiple of 32, at most 256), slot c of
- * sampled pixel s holds float4 (T, C_r, C_g, C_b): the transmittance and
- * accumulated colour in front of tile-list position (c + 1) B, at
- * data[(c * stride + s) * 4].  data: device, 16-byte aligned,
+ * so a sparse step has enough parallel work).  Slot c of sampled pixel s
+ * holds float4 (T, C_r, C_g, C_b): the transmittance and accumulated colour
+ * in front of tile-list position 32 (c + 1), at data[(c * stride + s) * 4],
+ * written by every pixel whose walk reaches that position (the others' slots
+ * are never read).  data: device, 16-byte aligned,
  * tgs_checkpoint_bytes(n_active_max, n_pix_max, n_slots) bytes;
  * stride >= n_active_max * n_pix_max.  rgb: the forward's rgb output (the
  * backward reads it).  Pass the same struct to render_sampled and
@@ -320,11 +320,11 @@ tgs_status tgs_loss_sparse_ncc(const float* rgb, const float* target, int32_t wi
  * grad2d is not all zero.  write_untouched = 0 leaves grads of untouched
  * Gaussians unwritten; 1 writes zeros there.  With checkpoints (ckpt, as
  * given to render_sampled) each tile's list is replayed in independent pieces
- * of one batch each, every piece starting from the forward's checkpoint at its
- * back edge (S = (rgb - C) / T there), or from (T_final, bg) for the piece
- * holding the pixel's last splat; the positions past the last slot form one
- * more piece.  Same result up to rounding; more parallel work for sparse
- * steps.
+ * of 32 positions, one warp each over all of the tile's sampled pixels, every
+ * piece starting from the forward's checkpoint at its back edge
+ * (S = (rgb - C) / T there), or from (T_final, bg) for the piece holding the
+ * pixel's last splat; the positions past the last slot form one more piece.
+ * Same result up to rounding; more parallel work for sparse steps.
  */
 tgs_status tgs_backward_sampled(const tgs_gaussians* g, const tgs_camera* cam, const tgs_projected* proj,
                                 const int32_t* tile_ranges, const int32_t* vals, const int32_t* active_tiles,
@@ -411,9 +411,8 @@ tgs_status tgs_project_backward_update(const tgs_param_ptrs* params, int64_t n, 
  * Per view: the fields of render_sampled; the backward also reads dL_drgb
  * and writes grad2d [n_gaussians, 12] (zeroed by the call).  With checkpoints
  * (ckpt.data, rgb = the view's rgb output) the forward stores them and the
- * backward replays every tile in pieces as backward_sampled does; the
- * checkpoint interval is the batch's block size (the largest n_pix_max of
- * the views, rounded up to a multiple of 32).
+ * backward replays every tile in pieces as backward_sampled does, each warp
+ * of the persistent blocks taking its own (view, tile, piece) items.
  */
 typedef struct {
   tgs_projected proj;
@@ -444,7 +443,8 @@ tgs_status tgs_advance_counters(int64_t* iter_dev, int32_t* step_dev, tgs_stream
 
 /* Thread blocks of the batched kernels that fit on the current device at
  * once (SMs x resident blocks per SM) for n_pix_max pixels per tile: the
- * largest useful grid_ctas. */
+ * largest useful grid_ctas.  backward: 0 the forward, 1 the backward without
+ * checkpoints (whole tiles), 2 the backward in pieces (with checkpoints). */
 tgs_status tgs_render_batched_resident(int32_t n_pix_max, int32_t backward, int32_t* ctas);
 tgs_status tgs_render_sampled_batched(const tgs_view_batch* views, int32_t n_views, int32_t grid_ctas,
                                       int32_t* counter, tgs_stream stream);

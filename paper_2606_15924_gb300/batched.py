@@ -75,12 +75,11 @@ class MultiViewTrainer:
         self.persistent = bool(persistent)
         self.counters = torch.zeros(2 + 2 * self.K, dtype=torch.int32, device=dev)
         self.n_pix_max = max(v.n_pix for v in self.views)
-        # checkpoints for the split backward, every CKPT_POSITIONS / block size
-        # list positions (the batch's block size is its interval)
-        blk = min(256, max(32, (self.n_pix_max + 31) // 32 * 32))
+        # checkpoints for the split backward: one slot every CKPT_EVERY list
+        # positions, up to CKPT_POSITIONS
         if checkpoints is None:  # split only when the views' tiles cannot fill the GPU
-            checkpoints = sum(v.n_select for v in self.views) < 4 * B.render_batched_resident(self.n_pix_max, True)
-        self.ck_slots = max(1, Trainer.CKPT_POSITIONS // blk) if checkpoints else 0
+            checkpoints = sum(v.n_select for v in self.views) < 4 * B.render_batched_resident(self.n_pix_max, 1)
+        self.ck_slots = Trainer.CKPT_POSITIONS // Trainer.CKPT_EVERY if checkpoints else 0
         for v in self.views:
             if self.ck_slots:
                 v.ck_data = torch.empty(B.checkpoint_bytes(v.n_select, v.n_pix, self.ck_slots) // 4, device=dev)
@@ -89,7 +88,7 @@ class MultiViewTrainer:
             else:
                 v.ckpt = None
         res_f = B.render_batched_resident(self.n_pix_max, False)
-        res_b = B.render_batched_resident(self.n_pix_max, True)
+        res_b = B.render_batched_resident(self.n_pix_max, 2 if self.ck_slots else 1)
         self.resident = (res_f, res_b)
         self.grid = tuple(grid) if grid is not None else (res_f, res_b)
         self._build_batches()

@@ -429,9 +429,11 @@ def view_batch(views: list) -> C.Array:
     return arr
 
 
-def render_batched_resident(n_pix_max: int, backward: bool) -> int:
+def render_batched_resident(n_pix_max: int, backward) -> int:
+    """backward: 0 / False the forward, 1 / True the whole-tile backward, 2 the
+    backward in pieces (with checkpoints)."""
     out = _i32(0)
-    _check("tgs_render_batched_resident", _lib.tgs_render_batched_resident(int(n_pix_max), 1 if backward else 0,
+    _check("tgs_render_batched_resident", _lib.tgs_render_batched_resident(int(n_pix_max), int(backward),
                                                                              C.byref(out)))
     return int(out.value)
 

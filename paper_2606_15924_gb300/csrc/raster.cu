@@ -23,6 +23,7 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kTStop = 1e-4f;
 constexpr int kUnroll = 4;  // splats per step of the forward walk
+constexpr int kCkptEvery = 32;  // list positions per checkpoint slot (a multiple of kUnroll)
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -75,7 +76,8 @@ __device__ __forceinline__ void load_splat(const RasterArgs& a, int k, Splat& sp
 // blockDim.x splats).
 // Checkpoints of the sampled forward for the split backward: slot c (c = 0
 // .. n_slots - 1) of pixel s holds (T, C_r, C_g, C_b) in front of tile-list
-// position (c + 1) * B (B = the block size, one batch), at data[c * stride + s].
+// position (c + 1) kCkptEvery, at data[c * stride + s]; written by every
+// pixel whose walk reaches that position.
 struct Ckpt {
   float4* data;
   int n_slots;
@@ -107,41 +109,45 @@ __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Spla
   if (range.x + (int)threadIdx.x < range.y) load_splat(a, range.x + threadIdx.x, nxt);
   for (int base = range.x; base < range.y; base += B) {
     if (__syncthreads_count(done) == B) break;
-    if (ck.data && has_pix) {
-      const int c = (base - range.x) / B - 1;  // state in front of this batch
-      if (c >= 0 && c < ck.n_slots) ck.data[c * ck.stride + s] = make_float4(T, C0, C1, C2);
-    }
     if (base + (int)threadIdx.x < range.y) sm[threadIdx.x] = nxt;
     __syncthreads();
     if (base + B + (int)threadIdx.x < range.y) load_splat(a, base + B + threadIdx.x, nxt);
     const int cnt = min(B, range.y - base);
-    // kUnroll splats at a time: their alphas do not depend on T, so they are
-    // evaluated together and only the blend runs in list order.  B is a
-    // multiple of 32, so sm[q0 .. q0 + kUnroll - 1] stays inside the batch.
-    for (int q0 = 0; q0 < cnt && !done; q0 += kUnroll) {
-      float al[kUnroll];
-      bool ok[kUnroll];
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const float2 xy = sm[q0 + u].xy;
-        float G;
-        ok[u] = splat_alpha(sm[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G) && q0 + u < cnt;
+    // Runs of kCkptEvery positions (B is a multiple of it): the checkpoint in
+    // front of each run, then kUnroll splats at a time: their alphas do not
+    // depend on T, so they are evaluated together and only the blend runs in
+    // list order (sm[q0 .. q0 + kUnroll - 1] stays inside the batch).
+    for (int q32 = 0; q32 < cnt && !done; q32 += kCkptEvery) {
+      if (ck.data) {
+        const int c = (base - range.x + q32) / kCkptEvery - 1;  // state in front of this run
+        if (c >= 0 && c < ck.n_slots) ck.data[c * ck.stride + s] = make_float4(T, C0, C1, C2);
       }
+      const int qe = min(cnt, q32 + kCkptEvery);
+      for (int q0 = q32; q0 < qe && !done; q0 += kUnroll) {
+        float al[kUnroll];
+        bool ok[kUnroll];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        if (!ok[u]) continue;
-        const float Tn = __fmul_rn(T, __fsub_rn(1.f, al[u]));
-        if (Tn < kTStop) {
-          done = true;
-          break;
+        for (int u = 0; u < kUnroll; ++u) {
+          const float2 xy = sm[q0 + u].xy;
+          float G;
+          ok[u] = splat_alpha(sm[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G) && q0 + u < qe;
         }
-        const float4 rgb = sm[q0 + u].rgb;
-        const float w = al[u] * T;
-        C0 += w * rgb.x;
-        C1 += w * rgb.y;
-        C2 += w * rgb.z;
-        T = Tn;
-        last = base + q0 + u + 1 - range.x;
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          if (!ok[u]) continue;
+          const float Tn = __fmul_rn(T, __fsub_rn(1.f, al[u]));
+          if (Tn < kTStop) {
+            done = true;
+            break;
+          }
+          const float4 rgb = sm[q0 + u].rgb;
+          const float w = al[u] * T;
+          C0 += w * rgb.x;
+          C1 += w * rgb.y;
+          C2 += w * rgb.z;
+          T = Tn;
+          last = base + q0 + u + 1 - range.x;
+        }
       }
     }
   }
@@ -318,147 +324,149 @@ __global__ void k_render_bwd(RasterArgs a, const float* __restrict__ T_final, co
   render_tile_bwd(a, j, sm, T_final, n_last, dL_drgb, grad2d);
 }
 
-// Split backward: block (j, c) replays batch c of tile j (list positions
-// [c B, (c + 1) B)), or, for c = n_slots, every position from n_slots B to the
-// end.  A pixel whose last blended splat lies in the block's range starts from
-// (T_final, bg); one whose walk goes on past it starts from the forward's
-// checkpoint at the range's back edge, with the light from behind recovered
-// as S = (out - C) / T (out = T-weighted colours + T_final bg).  Per-splat
-// adjoints are reduced as in the whole-tile kernel.
-__device__ __forceinline__ void render_piece_bwd(const RasterArgs& a, int j, int c, Splat* sm,
-                                                 const float* __restrict__ T_final,
-                                                 const int32_t* __restrict__ n_last,
-                                                 const float* __restrict__ dL_drgb, float* __restrict__ grad2d,
-                                                 const Ckpt& ck) {
-  __shared__ int s_max_last;
-  float* acc = reinterpret_cast<float*>(sm + blockDim.x);
-  const int B = blockDim.x;
+// Split backward, one warp per piece: piece c of tile j is list positions
+// [c E, (c + 1) E) (E = kCkptEvery), or from n_slots E to the end for
+// c = n_slots, replayed for every sampled pixel of the tile, PPL pixels per
+// lane (pixel p0 + lane + 32 u).  A pixel whose last blended splat lies in
+// the piece starts from (T_final, bg); one whose walk goes on past it starts
+// from the forward's checkpoint at the piece's back edge, with the light
+// from behind recovered as S = (out - C) / T (out = T-weighted colours +
+// T_final bg).  The lane first sums its pixels' adjoints of a splat in
+// registers, so one warp reduction serves 32 PPL pixels, and the warp's
+// totals go straight to the Gaussian's gradient row (two vector atomics and
+// one scalar).  Warps never wait on each other: each stages its splats, one
+// per lane, in its own slice of shared memory (sm, 32 entries).
+template <int PPL>
+__device__ __forceinline__ void render_piece_bwd_warp(const RasterArgs& a, int j, int c, Splat* sm,
+                                                      const float* __restrict__ T_final,
+                                                      const int32_t* __restrict__ n_last,
+                                                      const float* __restrict__ dL_drgb,
+                                                      float* __restrict__ grad2d, const Ckpt& ck) {
+  constexpr int E = kCkptEvery;
+  const int lane = threadIdx.x & 31;
   const int t = a.active_tiles ? a.active_tiles[j] : j;
   const int p0 = a.pix_off[j], p1 = a.pix_off[j + 1];
-  const bool has_pix = p0 + (int)threadIdx.x < p1;
-  const int s = p0 + threadIdx.x;
   int max_last;
   if (ck.tile_last) {
     max_last = ck.tile_last[j];  // from the forward
   } else {
-    const int l0 = has_pix ? n_last[s] : 0;
-    if (threadIdx.x == 0) s_max_last = 0;
-    __syncthreads();
-    if (l0 > 0) atomicMax(&s_max_last, l0);
-    __syncthreads();
-    max_last = s_max_last;
-  }
-  const int lo_pos = c * B;                                        // first list position of the range
-  const int hi_pos = c < ck.n_slots ? min(lo_pos + B, max_last) : max_last;
-  if (hi_pos <= lo_pos) return;                                    // uniform: nothing blended here
-  int last = has_pix ? n_last[s] : 0;
-  const int2 range = a.ranges[j];
-  float px = 0.f, py = 0.f, T = 1.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-  float S0 = a.bg[0], S1 = a.bg[1], S2 = a.bg[2];
-  if (last <= lo_pos) last = 0;  // this pixel blended nothing in the range
-  if (last > 0) {
-    const int l = a.pix_idx[s];
-    px = (float)((t % a.tiles_x) * TGS_TILE + (l & 15)) + 0.5f;
-    py = (float)((t / a.tiles_x) * TGS_TILE + (l >> 4)) + 0.5f;
-    g0 = dL_drgb[3 * s];
-    g1 = dL_drgb[3 * s + 1];
-    g2 = dL_drgb[3 * s + 2];
-    if (c < ck.n_slots && last > lo_pos + B) {
-      const float4 q = ck.data[c * ck.stride + s];  // in front of position (c + 1) B
-      T = q.x;
-      const float iT = 1.f / q.x;
-      S0 = (ck.rgb[3 * s] - q.y) * iT;
-      S1 = (ck.rgb[3 * s + 1] - q.z) * iT;
-      S2 = (ck.rgb[3 * s + 2] - q.w) * iT;
-      last = lo_pos + B;
-    } else {
-      T = T_final[s];
+    int m = 0;
+#pragma unroll
+    for (int u = 0; u < PPL; ++u) {
+      const int s = p0 + lane + 32 * u;
+      if (s < p1) m = max(m, n_last[s]);
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    max_last = m;
   }
-  const int lane = threadIdx.x & 31;
-  int warp_last = last;
+  const int lo_pos = c * E;
+  const int hi_pos = c < ck.n_slots ? min(lo_pos + E, max_last) : max_last;
+  if (hi_pos <= lo_pos) return;  // warp-uniform: nothing blended here
+  float px[PPL], py[PPL], T[PPL], g0[PPL], g1[PPL], g2[PPL], S0[PPL], S1[PPL], S2[PPL];
+  int last[PPL];
+  int warp_last = 0;
+#pragma unroll
+  for (int u = 0; u < PPL; ++u) {
+    const int s = p0 + lane + 32 * u;
+    last[u] = s < p1 ? n_last[s] : 0;
+    if (last[u] <= lo_pos) last[u] = 0;  // this pixel blended nothing in the piece
+    px[u] = py[u] = 0.f;
+    T[u] = 1.f;
+    g0[u] = g1[u] = g2[u] = 0.f;
+    S0[u] = a.bg[0];
+    S1[u] = a.bg[1];
+    S2[u] = a.bg[2];
+    if (last[u] > 0) {
+      const int l = a.pix_idx[s];
+      px[u] = (float)((t % a.tiles_x) * TGS_TILE + (l & 15)) + 0.5f;
+      py[u] = (float)((t / a.tiles_x) * TGS_TILE + (l >> 4)) + 0.5f;
+      g0[u] = dL_drgb[3 * s];
+      g1[u] = dL_drgb[3 * s + 1];
+      g2[u] = dL_drgb[3 * s + 2];
+      if (c < ck.n_slots && last[u] > lo_pos + E) {
+        const float4 q = ck.data[c * ck.stride + s];  // in front of position (c + 1) E
+        T[u] = q.x;
+        const float iT = 1.f / q.x;
+        S0[u] = (ck.rgb[3 * s] - q.y) * iT;
+        S1[u] = (ck.rgb[3 * s + 1] - q.z) * iT;
+        S2[u] = (ck.rgb[3 * s + 2] - q.w) * iT;
+        last[u] = lo_pos + E;
+      } else {
+        T[u] = T_final[s];
+      }
+    }
+    warp_last = max(warp_last, last[u]);
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) warp_last = max(warp_last, __shfl_xor_sync(0xffffffffu, warp_last, o));
-  const int first = range.x + lo_pos, end = range.x + hi_pos;
-  Splat nxt;
-  {
-    const int k = end - B + (int)threadIdx.x;
-    if (k >= first) load_splat(a, k, nxt);
-  }
-  for (int top = end; top > first; top -= B) {
-    const int lo = max(first, top - B);
-    const int cnt = top - lo;
-    __syncthreads();
-    {
-      const int k = top - B + (int)threadIdx.x;
-      if (k >= lo) sm[threadIdx.x - (B - cnt)] = nxt;
-#pragma unroll
-      for (int q = 0; q < 9; ++q) acc[9 * threadIdx.x + q] = 0.f;
-    }
-    __syncthreads();
-    {
-      const int k = top - 2 * B + (int)threadIdx.x;
-      if (k >= first) load_splat(a, k, nxt);
-    }
-    const int qmax = min(cnt - 1, range.x + warp_last - 1 - lo);
-    for (int q = qmax; q >= 0; --q) {
+  const int2 range = a.ranges[j];
+  const int first = range.x + lo_pos, end = range.x + min(hi_pos, warp_last);
+  for (int top = end; top > first; top -= 32) {
+    const int lo = max(first, top - 32);
+    __syncwarp();
+    if (lo + lane < top) load_splat(a, lo + lane, sm[lane]);
+    __syncwarp();
+    for (int q = top - lo - 1; q >= 0; --q) {
       const Splat sp = sm[q];
-      const int pos = lo + q - range.x;
+      const int pos = lo + q - range.x;  // position in the tile list
       float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       bool hit = false;
-      if (pos < last) {
-        const float dx = __fsub_rn(px, sp.xy.x), dy = __fsub_rn(py, sp.xy.y);
+#pragma unroll
+      for (int u = 0; u < PPL; ++u) {
+        if (pos >= last[u]) continue;
+        const float dx = __fsub_rn(px[u], sp.xy.x), dy = __fsub_rn(py[u], sp.xy.y);
         float alpha, G;
-        if (splat_alpha(sp.co, dx, dy, alpha, G)) {
-          hit = true;
-          T = __fdividef(T, 1.f - alpha);
-          const float wgt = alpha * T;
-          v[6] = wgt * g0;
-          v[7] = wgt * g1;
-          v[8] = wgt * g2;
-          const float dalpha = T * ((sp.rgb.x - S0) * g0 + (sp.rgb.y - S1) * g1 + (sp.rgb.z - S2) * g2);
-          S0 = alpha * sp.rgb.x + (1.f - alpha) * S0;
-          S1 = alpha * sp.rgb.y + (1.f - alpha) * S1;
-          S2 = alpha * sp.rgb.z + (1.f - alpha) * S2;
-          if (__fmul_rn(sp.co.w, G) < kAlphaMax) {
-            v[5] = dalpha * G;
-            const float dpow = dalpha * alpha;
-            v[0] = dpow * (sp.co.x * dx + sp.co.y * dy);
-            v[1] = dpow * (sp.co.z * dy + sp.co.y * dx);
-            v[2] = -0.5f * dpow * dx * dx;
-            v[3] = -dpow * dx * dy;
-            v[4] = -0.5f * dpow * dy * dy;
-          }
+        if (!splat_alpha(sp.co, dx, dy, alpha, G)) continue;
+        hit = true;
+        T[u] = __fdividef(T[u], 1.f - alpha);  // transmittance in front of this splat (1 - alpha >= 0.01)
+        const float wgt = alpha * T[u];
+        v[6] += wgt * g0[u];
+        v[7] += wgt * g1[u];
+        v[8] += wgt * g2[u];
+        const float dalpha = T[u] * ((sp.rgb.x - S0[u]) * g0[u] + (sp.rgb.y - S1[u]) * g1[u] +
+                                     (sp.rgb.z - S2[u]) * g2[u]);
+        S0[u] = alpha * sp.rgb.x + (1.f - alpha) * S0[u];
+        S1[u] = alpha * sp.rgb.y + (1.f - alpha) * S1[u];
+        S2[u] = alpha * sp.rgb.z + (1.f - alpha) * S2[u];
+        if (__fmul_rn(sp.co.w, G) < kAlphaMax) {
+          v[5] += dalpha * G;
+          const float dpow = dalpha * alpha;
+          v[0] += dpow * (sp.co.x * dx + sp.co.y * dy);
+          v[1] += dpow * (sp.co.z * dy + sp.co.y * dx);
+          v[2] += -0.5f * dpow * dx * dx;
+          v[3] += -dpow * dx * dy;
+          v[4] += -0.5f * dpow * dy * dy;
         }
       }
-      if (__any_sync(0xffffffffu, hit)) {
-        const float r8 = warp_reduce_scatter8(v, lane);
-        const float r9 = warp_sum(v[8]);
-        if ((lane & 3) == 0) atomicAdd(acc + 9 * q + ((lane >> 2) & 7), r8);
-        else if (lane == 1) atomicAdd(acc + 9 * q + 8, r9);
-      }
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < cnt) {
-      const float* r = acc + 9 * threadIdx.x;
-      if (r[0] != 0.f || r[1] != 0.f || r[2] != 0.f || r[3] != 0.f || r[4] != 0.f || r[5] != 0.f ||
-          r[6] != 0.f || r[7] != 0.f || r[8] != 0.f) {
-        float* gp = grad2d + 12 * (size_t)__float_as_int(sm[threadIdx.x].rgb.w);
-        red_add_v4(gp, r[0], r[1], r[2], r[3]);
-        red_add_v4(gp + 4, r[4], r[5], r[6], r[7]);
-        atomicAdd(gp + 8, r[8]);
-      }
+      if (!__any_sync(0xffffffffu, hit)) continue;
+      const float r8 = warp_reduce_scatter8(v, lane);  // lane 4 k + (0..3): component k
+      const float r9 = warp_sum(v[8]);
+      // components 0..3 to lane 0, 4..7 to lane 16
+      const float c1 = __shfl_down_sync(0xffffffffu, r8, 4);
+      const float c2 = __shfl_down_sync(0xffffffffu, r8, 8);
+      const float c3 = __shfl_down_sync(0xffffffffu, r8, 12);
+      float* gp = grad2d + 12 * (size_t)__float_as_int(sp.rgb.w);
+      if (lane == 0 || lane == 16) red_add_v4(gp + (lane >> 2), r8, c1, c2, c3);
+      else if (lane == 1) atomicAdd(gp + 8, r9);
     }
   }
 }
 
-__global__ void k_render_bwd_split(RasterArgs a, const float* __restrict__ T_final,
-                                   const int32_t* __restrict__ n_last, const float* __restrict__ dL_drgb,
-                                   float* __restrict__ grad2d, Ckpt ck) {
-  extern __shared__ Splat sm[];
+constexpr int kBwdWarps = 4;  // pieces per block of the one-view split backward
+
+template <int PPL>
+__global__ void __launch_bounds__(32 * kBwdWarps) k_render_bwd_warp(RasterArgs a, const float* __restrict__ T_final,
+                                                                   const int32_t* __restrict__ n_last,
+                                                                   const float* __restrict__ dL_drgb,
+                                                                   float* __restrict__ grad2d, Ckpt ck) {
+  __shared__ Splat sm[kBwdWarps][32];
   const int j = blockIdx.x;
   if (j >= *a.n_active) return;
-  render_piece_bwd(a, j, blockIdx.y, sm, T_final, n_last, dL_drgb, grad2d, ck);
+  const int w = threadIdx.x >> 5;
+  const int c = blockIdx.y * kBwdWarps + w;
+  if (c > ck.n_slots) return;  // warp-uniform; the kernel has no block-wide barrier
+  render_piece_bwd_warp<PPL>(a, j, c, sm[w], T_final, n_last, dL_drgb, grad2d, ck);
 }
 
 // ---------------------------------------------------------------------------
@@ -518,28 +526,39 @@ __global__ void k_render_fwd_batched(BatchArgs b, int* __restrict__ counter) {
   }
 }
 
-// Items are (view, tile, piece) with the pieces of a tile consecutive; with
-// one piece per tile this is the whole-tile backward.
-constexpr int kPieceClaim = 4;  // pieces claimed per atomic in the split backward
-
+// Whole tiles, one item per block (the backward without checkpoints).
 __global__ void k_render_bwd_batched(BatchArgs b, int* __restrict__ counter) {
   extern __shared__ Splat sm[];
   __shared__ int s_item;
   int v, q;
-  if (b.pieces == 1) {
-    while (next_item(b, counter, &s_item, v, q))
-      if (q < *b.a[v].n_active) render_tile_bwd(b.a[v], q, sm, b.T[v], b.last[v], b.dL[v], b.grad2d[v]);
-    return;
-  }
-  int first;
-  while (next_items(b, counter, &s_item, kPieceClaim, first)) {
-    const int end = min(first + kPieceClaim, b.base[b.n_views]);
+  while (next_item(b, counter, &s_item, v, q))
+    if (q < *b.a[v].n_active) render_tile_bwd(b.a[v], q, sm, b.T[v], b.last[v], b.dL[v], b.grad2d[v]);
+}
+
+// With checkpoints: items are (view, tile, piece) with the pieces of a tile
+// consecutive; each warp claims kPieceClaim of them per atomic and replays
+// them as the one-view split backward does.
+constexpr int kPieceClaim = 4;
+constexpr int kBatchBwdWarps = 4;
+
+template <int PPL>
+__global__ void __launch_bounds__(32 * kBatchBwdWarps) k_render_bwd_batched_warp(BatchArgs b,
+                                                                                int* __restrict__ counter) {
+  __shared__ Splat sm[kBatchBwdWarps][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int total = b.base[b.n_views];
+  for (;;) {
+    int first = 0;
+    if (lane == 0) first = atomicAdd(counter, kPieceClaim);
+    first = __shfl_sync(0xffffffffu, first, 0);
+    if (first >= total) return;
+    const int end = min(first + kPieceClaim, total);
     for (int item = first; item < end; ++item) {
+      int v, q;
       item_view(b, item, v, q);
       const int j = q / b.pieces, c = q - j * b.pieces;
       if (j >= *b.a[v].n_active) continue;
-      __syncthreads();  // the previous piece's shared memory is no longer read
-      render_piece_bwd(b.a[v], j, c, sm, b.T[v], b.last[v], b.dL[v], b.grad2d[v], b.ck[v]);
+      render_piece_bwd_warp<PPL>(b.a[v], j, c, sm[w], b.T[v], b.last[v], b.dL[v], b.grad2d[v], b.ck[v]);
     }
   }
 }
@@ -632,10 +651,18 @@ extern "C" tgs_status tgs_render_backward_sampled(const tgs_projected* proj, con
   if (n_active_max > 0) {
     const int B = block_for(n_pix_max);
     const size_t smem = B * (sizeof(Splat) + 9 * sizeof(float));
-    if (ck.data)
-      k_render_bwd_split<<<dim3(n_active_max, ck.n_slots + 1), B, smem, s>>>(a, T_final, n_last, dL_drgb, grad2d,
-                                                                             ck);
-    else
+    if (ck.data) {
+      // one warp per piece, kBwdWarps pieces per block, B / 32 pixels per lane
+      const dim3 grid(n_active_max, (ck.n_slots + 1 + kBwdWarps - 1) / kBwdWarps);
+      switch (B / 32) {
+#define TGS_BWD_WARP(P) \
+  case P: k_render_bwd_warp<P><<<grid, 32 * kBwdWarps, 0, s>>>(a, T_final, n_last, dL_drgb, grad2d, ck); break;
+        TGS_BWD_WARP(1) TGS_BWD_WARP(2) TGS_BWD_WARP(3) TGS_BWD_WARP(4)
+        TGS_BWD_WARP(5) TGS_BWD_WARP(6) TGS_BWD_WARP(7)
+        default: k_render_bwd_warp<8><<<grid, 32 * kBwdWarps, 0, s>>>(a, T_final, n_last, dL_drgb, grad2d, ck);
+#undef TGS_BWD_WARP
+      }
+    } else
       k_render_bwd<<<n_active_max, B, smem, s>>>(a, T_final, n_last, dL_drgb, grad2d);
   }
   return check_launch();
@@ -697,13 +724,28 @@ static tgs_status batch_args(const tgs_view_batch* views, int32_t n_views, bool 
   return TGS_OK;
 }
 
+static int bwd_warp_blocks_per_sm(int ppl) {
+  int per_sm = 0;
+  const int T = 32 * kBatchBwdWarps;
+  switch (ppl) {
+#define TGS_OCC(P) \
+  case P: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd_batched_warp<P>, T, 0); break;
+    TGS_OCC(1) TGS_OCC(2) TGS_OCC(3) TGS_OCC(4) TGS_OCC(5) TGS_OCC(6) TGS_OCC(7)
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd_batched_warp<8>, T, 0);
+#undef TGS_OCC
+  }
+  return per_sm;
+}
+
 extern "C" tgs_status tgs_render_batched_resident(int32_t n_pix_max, int32_t backward, int32_t* ctas) {
-  if (!ctas || n_pix_max < 1 || n_pix_max > 256) return TGS_ERR_INVALID_ARG;
+  if (!ctas || n_pix_max < 1 || n_pix_max > 256 || backward < 0 || backward > 2) return TGS_ERR_INVALID_ARG;
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return check_launch();
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int B = block_for(n_pix_max);
-  if (backward)
+  if (backward == 2)
+    per_sm = bwd_warp_blocks_per_sm(B / 32);
+  else if (backward)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd_batched, B,
                                                   B * (sizeof(Splat) + 9 * sizeof(float)));
   else
@@ -739,7 +781,18 @@ extern "C" tgs_status tgs_render_backward_batched(const tgs_view_batch* views, i
       cudaMemsetAsync(views[v].grad2d, 0, sizeof(float) * 12 * (size_t)views[v].n_gaussians, s);
   cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
   if (b.base[n_views] == 0) return check_launch();
-  k_render_bwd_batched<<<grid_ctas, B, B * (sizeof(Splat) + 9 * sizeof(float)), s>>>(b, counter);
+  if (b.pieces == 1) {
+    k_render_bwd_batched<<<grid_ctas, B, B * (sizeof(Splat) + 9 * sizeof(float)), s>>>(b, counter);
+    return check_launch();
+  }
+  switch (B / 32) {
+#define TGS_BWD_BATCH(P) \
+  case P: k_render_bwd_batched_warp<P><<<grid_ctas, 32 * kBatchBwdWarps, 0, s>>>(b, counter); break;
+    TGS_BWD_BATCH(1) TGS_BWD_BATCH(2) TGS_BWD_BATCH(3) TGS_BWD_BATCH(4)
+    TGS_BWD_BATCH(5) TGS_BWD_BATCH(6) TGS_BWD_BATCH(7)
+    default: k_render_bwd_batched_warp<8><<<grid_ctas, 32 * kBatchBwdWarps, 0, s>>>(b, counter);
+#undef TGS_BWD_BATCH
+  }
   return check_launch();
 }
 

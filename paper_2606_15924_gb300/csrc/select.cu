@@ -13,7 +13,7 @@ namespace tgs {
 
 struct SelWs {
   uint64_t* tile_w;   // [T] sum of pixel weights
-  uint64_t* tile_L;   // [T] exponential clock
+  uint64_t* tile_key; // [T] hard key: bits of the double L / w (exponential clock over weight)
   uint64_t* tile_u;   // [T] uniform key
   uint32_t* tile_age; // [T] smallest pixel age
   int32_t* rank_h;    // [T]
@@ -27,7 +27,7 @@ static SelWs carve_sel(void* base, int T, size_t* total) {
   Carver c(base);
   SelWs w;
   w.tile_w = c.take<uint64_t>(T);
-  w.tile_L = c.take<uint64_t>(T);
+  w.tile_key = c.take<uint64_t>(T);
   w.tile_u = c.take<uint64_t>(T);
   w.tile_age = c.take<uint32_t>(T);
   w.rank_h = c.take<int32_t>(3 * (size_t)T);
@@ -152,7 +152,9 @@ __global__ void __launch_bounds__(256) k_tile_stats(const uint16_t* __restrict__
   if (warp == 0 && t < g.T) {
     w.tile_w[t] = s_w[lane];
     w.tile_age[t] = s_a[lane];
-    w.tile_L[t] = neglog2_q32(hash_item(hk.prefix(STREAM_TILE_HARD), (uint32_t)t, 0));
+    // the FP64 division runs here, spread over the grid, and not in the
+    // single-block selection (FP64 throughput is low on this part)
+    w.tile_key[t] = hard_key(s_w[lane], neglog2_q32(hash_item(hk.prefix(STREAM_TILE_HARD), (uint32_t)t, 0)));
     w.tile_u[t] = hash_item(hk.prefix(STREAM_TILE_UNIF), (uint32_t)t, 0);
   }
 }
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(256) k_rank_tiles(SelWs w, int T, int phase, i
   // phase key, ascending, ties to the lower index:
   //  0: hard key; 1: (2^32 - 1 - age) (older first); 2: top 32 hash bits
   auto key = [&](int t) -> uint64_t {
-    if (phase == 0) return hard_key(w.tile_w[t], w.tile_L[t]);
+    if (phase == 0) return w.tile_key[t];
     if (phase == 1) return 0xFFFFFFFFull - w.tile_age[t];
     return w.tile_u[t] >> 32;
   };
@@ -393,7 +395,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select_block(SelWs w, SelGeom g
     const int i = threadIdx.x * ITEMS + j;
     valid[j] = i < T;
     elig[j] = valid[j];
-    key[j] = (valid[j] && !all && n_sel > 0) ? hard_key(w.tile_w[i], w.tile_L[i]) : 0;
+    key[j] = (valid[j] && !all && n_sel > 0) ? w.tile_key[i] : 0;
   }
   if (all || n_sel <= 0) {
 #pragma unroll

@@ -28,6 +28,7 @@ def zeros_like_params(g: dict) -> dict:
 
 class Trainer:
     CKPT_POSITIONS = 2048
+    CKPT_EVERY = 32       # list positions per checkpoint slot (fixed by the kernels)
 
     def __init__(self, params: dict, cam: dict, target: torch.Tensor, tile_fraction: float = 0.2,
                  pixel_rate: float = 1.0 / 3.0, cfg: Config | None = None, dense: bool = False,
@@ -88,12 +89,11 @@ class Trainer:
         self.err_pix = torch.zeros(P, device=dev)
         self.loss = torch.zeros(1, dtype=torch.float64, device=dev)
         # forward checkpoints for the split backward: only when the step has
-        # too few tiles to fill the GPU (sparse sampling); one slot per batch
-        # of the tile list up to CKPT_POSITIONS positions
+        # too few tiles to fill the GPU (sparse sampling); one slot every
+        # CKPT_EVERY positions of the tile list up to CKPT_POSITIONS
         self.ckpt = None
-        if train and not dense and self.n_select < 4 * B.render_batched_resident(self.n_pix, True):
-            blk = min(256, max(32, (self.n_pix + 31) // 32 * 32))  # the kernels' block size
-            n_slots = max(1, self.CKPT_POSITIONS // blk)
+        if train and not dense and self.n_select < 4 * B.render_batched_resident(self.n_pix, 1):
+            n_slots = self.CKPT_POSITIONS // self.CKPT_EVERY
             self.ck_data = torch.empty(B.checkpoint_bytes(S, self.n_pix, n_slots) // 4, device=dev)
             self.ck_last = torch.zeros(S, dtype=torch.int32, device=dev)
             self.ckpt = B.checkpoints(self.ck_data, n_slots, S * self.n_pix, self.rgb, self.ck_last)

@@ -208,9 +208,9 @@ def test_loss_parity(B, orc, W, H, n_select, n_pix):
 def test_backward_parity(B, orc, split):
     """grad2d and the parameter gradients of the tiny scene against the
     oracle's analytic backward (relative L2 <= 1e-3 per parameter group);
-    split: the backward replays each tile list in pieces from the forward's
-    checkpoints (few slots, so pieces, checkpoint starts and the tail piece
-    all occur)."""
+    split: the backward replays each tile list in pieces of 32 positions from
+    the forward's checkpoints (few slots, so that a long tail piece occurs, or
+    the trainer's 64), at 1, 3, 5 and 8 pixels per lane."""
     from gpu_util import bin_dev, dev, empty_projected, gaussians_dev, render_dev, select_dev, select_host
     g, cam = _c0(seed=5, n=3000)
     g["log_scales"] += 1.0
@@ -218,7 +218,8 @@ def test_backward_parity(B, orc, split):
     n = 3000
     err, age = scenes.error_map(W, H), scenes.age_map(W, H)
     target = scenes.smooth_image(W, H, seed=2)
-    for n_select, n_pix in ((64, 84), (256, 256)):
+    # n_pix 25, 84, 150, 256: 1, 3, 5 and 8 pixels per lane in the warp-per-piece backward
+    for n_select, n_pix in ((64, 84), (256, 256), (64, 25), (64, 150)):
         sel = select_dev(B, err, age, W, H, n_select, n_pix, seed=4)
         sh = select_host(sel)
         gd = gaussians_dev(g)
@@ -228,15 +229,16 @@ def test_backward_parity(B, orc, split):
         out = render_dev(B, pd, binned, sel, n_pix, cam)
         ck = None
         if split:
-            blk = min(256, (n_pix + 31) // 32 * 32)
+            every = 32                                        # list positions per slot
             longest = int(out["n_last"].max().item())
-            assert longest > blk                              # at least two pieces
-            slots = max(1, min(3, longest // blk - 1))        # and a tail piece past the slots
+            assert longest > 4 * every                        # several pieces
+            # few slots (a long tail piece past them) or as many as the trainer uses
+            slots = 3 if n_pix in (25, 84) else 64
             stride = sel["n_sel"] * n_pix
             ck_data = torch.full((B.checkpoint_bytes(sel["n_sel"], n_pix, slots) // 4,), float("nan"),
                                  device="cuda")
             # the second case also has the forward record each tile's longest run
-            tl = torch.full((sel["n_sel"],), -1, dtype=torch.int32, device="cuda") if n_pix == 256 else None
+            tl = torch.full((sel["n_sel"],), -1, dtype=torch.int32, device="cuda") if n_pix in (150, 256) else None
             ck = B.checkpoints(ck_data, slots, stride, out["rgb"], tl)
             B.render_sampled(pd, binned["ranges"], binned["vals"], sel["active_tiles"], sel["n_active"],
                              sel["n_sel"], sel["pix_off"], sel["pix_idx"], n_pix, cam, (0.0, 0.0, 0.0), out["rgb"],
