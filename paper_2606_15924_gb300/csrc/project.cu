@@ -203,16 +203,19 @@ __global__ void __launch_bounds__(256) k_project(
   sh_basis(dx, dy, dz, sh_degree, Y);
   const int nb = (sh_degree + 1) * (sh_degree + 1);
   const float4* shp = sh + 12 * i;
+  // the whole row (48 floats at every degree) in one round of loads: a loop
+  // that stops at the degree would wait for each load in turn
+  float4 row[12];
+#pragma unroll
+  for (int k4 = 0; k4 < 12; ++k4) row[k4] = ldg_f4_now(shp + k4);
   float acc[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
   for (int k4 = 0; k4 < 12; ++k4) {
-    if (4 * k4 >= 3 * nb) break;
-    float4 v = shp[k4];
-    float e[4] = {v.x, v.y, v.z, v.w};
+    const float e[4] = {row[k4].x, row[k4].y, row[k4].z, row[k4].w};
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      int f = 4 * k4 + j;  // flat index k * 3 + c
-      int k = f / 3, c = f - 3 * k;
+      const int f = 4 * k4 + j;  // flat index k * 3 + c
+      const int k = f / 3, c = f - 3 * k;
       if (k < nb) acc[c] += e[j] * Y[k];
     }
   }
@@ -301,16 +304,23 @@ __device__ __forceinline__ void view_adjoint(const CamK& cam, float3 mu, float3 
   // gradient) rather than held in registers; the second read hits L1.
   // Coefficient j = 3 k + c belongs to basis function k, channel c; only
   // j < 3 nb exist at this degree (the rest of the gradient is zero).
+  // loads in groups of four float4 issued together (a loop that stops at the
+  // degree would wait for each load in turn); the row has 48 floats at every
+  // degree
   float pre[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
-  for (int k4 = 0; k4 < 12; ++k4) {
-    if (4 * k4 >= 3 * nb) break;
-    const float4 v = shp[k4];
-    const float e[4] = {v.x, v.y, v.z, v.w};
+  for (int g4 = 0; g4 < 12; g4 += 4) {
+    float4 q[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int j = 4 * k4 + u;
-      if (j < 3 * nb) pre[j % 3] += e[u] * Y[j / 3];
+    for (int r = 0; r < 4; ++r) q[r] = shp[g4 + r];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float e[4] = {q[r].x, q[r].y, q[r].z, q[r].w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = 4 * (g4 + r) + u;
+        if (j < 3 * nb) pre[j % 3] += e[u] * Y[j / 3];
+      }
     }
   }
   const float dc0 = pre[0] >= 0.f ? drgb[0] : 0.f;
@@ -321,16 +331,20 @@ __device__ __forceinline__ void view_adjoint(const CamK& cam, float3 mu, float3 
 #pragma unroll
   for (int k = 0; k < 16; ++k) sk[k] = 0.f;
 #pragma unroll
-  for (int k4 = 0; k4 < 12; ++k4) {
-    const bool any = 4 * k4 < 3 * nb;
-    const float4 v = any ? shp[k4] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float e[4] = {v.x, v.y, v.z, v.w};
+  for (int g4 = 0; g4 < 12; g4 += 4) {
+    float4 q[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int j = 4 * k4 + u;
-      const bool on = j < 3 * nb;
-      if (on) sk[j / 3] += dcv[j % 3] * e[u];
-      acc.sh.add(j, on ? dcv[j % 3] * Y[j / 3] : 0.f);
+    for (int r = 0; r < 4; ++r) q[r] = shp[g4 + r];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const float e[4] = {q[r].x, q[r].y, q[r].z, q[r].w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int j = 4 * (g4 + r) + u;
+        const bool on = j < 3 * nb;
+        if (on) sk[j / 3] += dcv[j % 3] * e[u];
+        acc.sh.add(j, on ? dcv[j % 3] * Y[j / 3] : 0.f);
+      }
     }
   }
   if (rw) {

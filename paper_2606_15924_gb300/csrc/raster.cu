@@ -132,21 +132,21 @@ __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Spla
           float G;
           ok[u] = splat_alpha(sm[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G) && q0 + u < qe;
         }
+        // the blend without branches: a splat past the stopping one, or
+        // skipped, leaves the state as it is
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-          if (!ok[u]) continue;
           const float Tn = __fmul_rn(T, __fsub_rn(1.f, al[u]));
-          if (Tn < kTStop) {
-            done = true;
-            break;
-          }
+          const bool stop = ok[u] && !done && Tn < kTStop;
+          const bool take = ok[u] && !done && !stop;
+          done = done || stop;
           const float4 rgb = sm[q0 + u].rgb;
           const float w = al[u] * T;
-          C0 += w * rgb.x;
-          C1 += w * rgb.y;
-          C2 += w * rgb.z;
-          T = Tn;
-          last = base + q0 + u + 1 - range.x;
+          C0 = take ? C0 + w * rgb.x : C0;
+          C1 = take ? C1 + w * rgb.y : C1;
+          C2 = take ? C2 + w * rgb.z : C2;
+          T = take ? Tn : T;
+          last = take ? base + q0 + u + 1 - range.x : last;
         }
       }
     }

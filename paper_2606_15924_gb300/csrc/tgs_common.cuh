@@ -150,6 +150,17 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// 16-byte load through the read-only path as a volatile asm statement, so
+// that a run of them is issued in program order, ahead of the arithmetic that
+// uses them (the compiler otherwise sinks each load to its first use).
+__device__ __forceinline__ float4 ldg_f4_now(const float4* p) {
+  float4 v;
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p));
+  return v;
+}
+
 // vector atomic add of 4 floats (sm_90+ red.global.add.v4.f32)
 __device__ __forceinline__ void red_add_v4(float* addr, float a, float b, float c, float d) {
   asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b), "f"(c), "f"(d)
