@@ -51,6 +51,18 @@ __device__ __forceinline__ bool splat_alpha(const float4& co, float dx, float dy
   return alpha >= kAlphaMin;
 }
 
+// The same decision without a branch: alpha and G are computed in every case
+// (for power > 0, G may be +inf and alpha 0.99, finite either way), and the
+// return value says whether the splat counts.
+__device__ __forceinline__ bool splat_alpha_nb(const float4& co, float dx, float dy, float& alpha, float& G) {
+  const float ax = __fmul_rn(co.x, dx), cy = __fmul_rn(co.z, dy), by = __fmul_rn(co.y, dy);
+  const float quad = __fmaf_rn(ax, dx, __fmul_rn(cy, dy));
+  const float power = __fmaf_rn(-0.5f, quad, -__fmul_rn(by, dx));
+  G = ex2_approx(__fmul_rn(power, kLog2e));
+  alpha = fminf(kAlphaMax, __fmul_rn(co.w, G));
+  return power <= 0.f && alpha >= kAlphaMin;
+}
+
 struct RasterArgs {
   const float2* xy;
   const float4* conic_opac;
@@ -130,7 +142,7 @@ __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Spla
         for (int u = 0; u < kUnroll; ++u) {
           const float2 xy = sm[q0 + u].xy;
           float G;
-          ok[u] = splat_alpha(sm[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G) && q0 + u < qe;
+          ok[u] = splat_alpha_nb(sm[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G) && q0 + u < qe;
         }
         // the blend without branches: a splat past the stopping one, or
         // skipped, leaves the state as it is
