@@ -101,50 +101,6 @@ __device__ __forceinline__ int rank_of(const int32_t* __restrict__ tile_rank, in
   return (r >= 0 && r < g.n_ranks) ? r : -1;
 }
 
-// 1. pairs per active tile
-__global__ void __launch_bounds__(256) k_count_tiles(const float2* __restrict__ xy, const int32_t* __restrict__ radius,
-                                                     int64_t n, BinGeom geo, const int32_t* __restrict__ tile_rank,
-                                                     int32_t* __restrict__ tile_cnt) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int r = radius[i];
-  if (r <= 0) return;
-  const float2 p = xy[i];
-  int x0, x1, y0, y1;
-  tile_span(p.x, r, geo.tx, x0, x1);
-  tile_span(p.y, r, geo.ty, y0, y1);
-  for (int ty = y0; ty < y1; ++ty)
-    for (int tx = x0; tx < x1; ++tx) {
-      const int k = rank_of(tile_rank, ty * geo.tx + tx, geo);
-      if (k >= 0) atomicAdd(tile_cnt + k, 1);
-    }
-}
-
-// 3. scatter (depth | id) keys into the tile ranges (unordered inside a tile)
-__global__ void __launch_bounds__(256) k_scatter_keys(const float2* __restrict__ xy, const int32_t* __restrict__ radius,
-                                                      const float* __restrict__ depth, int64_t n, BinGeom geo,
-                                                      const int32_t* __restrict__ tile_rank,
-                                                      const int64_t* __restrict__ tile_start,
-                                                      int32_t* __restrict__ tile_fill, uint64_t* __restrict__ keys,
-                                                      int64_t cap) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int r = radius[i];
-  if (r <= 0) return;
-  const float2 p = xy[i];
-  const uint64_t key = ((uint64_t)__float_as_uint(depth[i]) << 32) | (uint64_t)(uint32_t)i;
-  int x0, x1, y0, y1;
-  tile_span(p.x, r, geo.tx, x0, x1);
-  tile_span(p.y, r, geo.ty, y0, y1);
-  for (int ty = y0; ty < y1; ++ty)
-    for (int tx = x0; tx < x1; ++tx) {
-      const int k = rank_of(tile_rank, ty * geo.tx + tx, geo);
-      if (k < 0) continue;
-      const int64_t pos = tile_start[k] + atomicAdd(tile_fill + k, 1);
-      if (pos < cap) keys[pos] = key;
-    }
-}
-
 // Calls f(gaussian id, rank) for every (Gaussian, active tile) pair of the
 // block's Gaussians at positions [i0, i1) (of `order`, or the ids themselves).
 // The pairs of a warp's 32 Gaussians are dealt out evenly: an inclusive warp
@@ -200,6 +156,32 @@ __device__ __forceinline__ void for_each_pair(const float2* __restrict__ xy, con
       }
     }
   }
+}
+
+// 1''. pairs per active tile with global atomics, 256 Gaussians per block,
+// their pairs dealt out evenly over the lanes.
+__global__ void __launch_bounds__(256) k_count_pairs(const float2* __restrict__ xy,
+                                                     const int32_t* __restrict__ radius, int64_t n, BinGeom geo,
+                                                     const int32_t* __restrict__ tile_rank,
+                                                     int32_t* __restrict__ tile_cnt) {
+  const int64_t i0 = (int64_t)blockIdx.x * 256, i1 = min(n, i0 + 256);
+  for_each_pair(xy, radius, i0, i1, geo, tile_rank, [&](int64_t, int k) { atomicAdd(tile_cnt + k, 1); });
+}
+
+// 3''. scatter with global cursors (order inside a tile arbitrary: the
+// per-tile sort that follows orders it).
+__global__ void __launch_bounds__(256) k_scatter_pairs(const float2* __restrict__ xy,
+                                                       const int32_t* __restrict__ radius,
+                                                       const float* __restrict__ depth, int64_t n, BinGeom geo,
+                                                       const int32_t* __restrict__ tile_rank,
+                                                       const int64_t* __restrict__ tile_start,
+                                                       int32_t* __restrict__ tile_fill, uint64_t* __restrict__ keys,
+                                                       int64_t cap) {
+  const int64_t i0 = (int64_t)blockIdx.x * 256, i1 = min(n, i0 + 256);
+  for_each_pair(xy, radius, i0, i1, geo, tile_rank, [&](int64_t i, int k) {
+    const int64_t pos = tile_start[k] + atomicAdd(tile_fill + k, 1);
+    if (pos < cap) keys[pos] = ((uint64_t)__float_as_uint(depth[i]) << 32) | (uint64_t)(uint32_t)i;
+  });
 }
 
 // 1'. shared-memory path: block b counts the pairs of Gaussians
@@ -649,6 +631,9 @@ extern "C" tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const 
   if (n == 0 || R == 0) return check_launch();
   const float2* xy = reinterpret_cast<const float2*>(proj->xy);
   RangeSrc src{};
+  // Per-chunk histograms in shared memory and an offset table, while the
+  // ranks fit in shared memory: global per-tile counters and cursors take
+  // every pair's atomic on a few hundred addresses, several times slower.
   const bool shared_path = R <= kHistMaxRanks;
   const int G = hist_blocks(n);
   const size_t smem = sizeof(int32_t) * (size_t)R;
@@ -692,7 +677,7 @@ extern "C" tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const 
     const int gb = (int)((n + 255) / 256);
     cudaMemsetAsync(w.tile_cnt, 0, sizeof(int32_t) * (size_t)R, s);
     cudaMemsetAsync(w.tile_fill, 0, sizeof(int32_t) * (size_t)R, s);
-    k_count_tiles<<<gb, 256, 0, s>>>(xy, proj->radius, n, geo, tile_rank, w.tile_cnt);
+    k_count_pairs<<<gb, 256, 0, s>>>(xy, proj->radius, n, geo, tile_rank, w.tile_cnt);
     const int32_t* cnt = w.tile_cnt;
     int64_t* start = w.tile_start;
     auto load = [=] __device__(int64_t r) -> int64_t { return cnt[r]; };
@@ -706,8 +691,8 @@ extern "C" tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const 
     k_hist_scatter<<<G, kHistThreads, smem, s>>>(xy, proj->radius, proj->depth, order, n_vis, n, geo, tile_rank,
                                                  w.table, w.keys, capacity);
   } else {
-    k_scatter_keys<<<(int)((n + 255) / 256), 256, 0, s>>>(xy, proj->radius, proj->depth, n, geo, tile_rank,
-                                                          w.tile_start, w.tile_fill, w.keys, capacity);
+    k_scatter_pairs<<<(int)((n + 255) / 256), 256, 0, s>>>(xy, proj->radius, proj->depth, n, geo, tile_rank,
+                                                           w.tile_start, w.tile_fill, w.keys, capacity);
   }
   if (keys) k_inv_rank<<<(T + 255) / 256, 256, 0, s>>>(tile_rank, T, w.inv_rank, R);
   if (presort)

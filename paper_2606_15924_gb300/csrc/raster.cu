@@ -98,6 +98,11 @@ struct Ckpt {
   int32_t* tile_last;  // [active rank] longest blended run of the tile's pixels (nullable)
 };
 
+// SELECT: the blend of each group of kUnroll splats with selects instead of
+// branches (more instructions, shorter dependent chains) - the better choice
+// when few warps share an SM (a sparse step); with many warps per SM the
+// branches' skipped work wins.  Both produce the same bits.
+template <bool SELECT>
 __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Splat* sm, float* __restrict__ out_rgb,
                                                 float* __restrict__ out_T, int32_t* __restrict__ out_last,
                                                 Ckpt ck = Ckpt{nullptr, 0, 0, nullptr, nullptr}) {
@@ -142,7 +147,28 @@ __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Spla
         for (int u = 0; u < kUnroll; ++u) {
           const float2 xy = sm[q0 + u].xy;
           float G;
-          ok[u] = splat_alpha_nb(sm[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G) && q0 + u < qe;
+          ok[u] = (SELECT ? splat_alpha_nb(sm[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G)
+                          : splat_alpha(sm[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G)) &&
+                  q0 + u < qe;
+        }
+        if (!SELECT) {
+#pragma unroll
+          for (int u = 0; u < kUnroll; ++u) {
+            if (!ok[u]) continue;
+            const float Tn = __fmul_rn(T, __fsub_rn(1.f, al[u]));
+            if (Tn < kTStop) {
+              done = true;
+              break;
+            }
+            const float4 rgb = sm[q0 + u].rgb;
+            const float w = al[u] * T;
+            C0 += w * rgb.x;
+            C1 += w * rgb.y;
+            C2 += w * rgb.z;
+            T = Tn;
+            last = base + q0 + u + 1 - range.x;
+          }
+          continue;
         }
         // the blend without branches: a splat past the stopping one, or
         // skipped, leaves the state as it is
@@ -181,12 +207,13 @@ __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Spla
   }
 }
 
+template <bool SELECT>
 __global__ void k_render_fwd(RasterArgs a, float* __restrict__ out_rgb, float* __restrict__ out_T,
                              int32_t* __restrict__ out_last, Ckpt ck) {
   extern __shared__ Splat sm[];
   const int j = blockIdx.x;
   if (j >= *a.n_active) return;
-  render_tile_fwd(a, j, sm, out_rgb, out_T, out_last, ck);
+  render_tile_fwd<SELECT>(a, j, sm, out_rgb, out_T, out_last, ck);
 }
 
 // Sum of v[0..7] over the warp, scattered: lane l ends with the total of
@@ -534,7 +561,7 @@ __global__ void k_render_fwd_batched(BatchArgs b, int* __restrict__ counter) {
   __shared__ int s_item;
   int v, j;
   while (next_item(b, counter, &s_item, v, j)) {
-    if (j < *b.a[v].n_active) render_tile_fwd(b.a[v], j, sm, b.rgb[v], b.T[v], b.last[v], b.ck[v]);
+    if (j < *b.a[v].n_active) render_tile_fwd<false>(b.a[v], j, sm, b.rgb[v], b.T[v], b.last[v], b.ck[v]);
   }
 }
 
@@ -600,6 +627,15 @@ static bool raster_args(const tgs_projected* proj, const int32_t* tile_ranges, c
 
 static int block_for(int n_pix_max) { return std::min(256, std::max(32, (n_pix_max + 31) / 32 * 32)); }
 
+// SMs of the current device (cached per device).
+static int sm_count() {
+  static int sms[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (!sms[dev]) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+  return std::max(1, sms[dev]);
+}
+
 }  // namespace tgs
 
 using namespace tgs;
@@ -636,7 +672,11 @@ extern "C" tgs_status tgs_render_sampled(const tgs_projected* proj, const int32_
   if (!ckpt_of(ckpt, n_active_max, n_pix_max, rgb, ck)) return TGS_ERR_INVALID_ARG;
   if (n_active_max == 0) return TGS_OK;
   const int B = block_for(n_pix_max);
-  k_render_fwd<<<n_active_max, B, B * sizeof(Splat), (cudaStream_t)stream>>>(a, rgb, T_final, n_last, ck);
+  // selects when the launch gives fewer than 16 warps per SM
+  if ((int64_t)n_active_max * (B / 32) < 16 * (int64_t)sm_count())
+    k_render_fwd<true><<<n_active_max, B, B * sizeof(Splat), (cudaStream_t)stream>>>(a, rgb, T_final, n_last, ck);
+  else
+    k_render_fwd<false><<<n_active_max, B, B * sizeof(Splat), (cudaStream_t)stream>>>(a, rgb, T_final, n_last, ck);
   return check_launch();
 }
 

@@ -1,5 +1,5 @@
 // Device-wide exclusive prefix sum in three launches (reduce, scan of block
-// sums, downsweep).  The element count may live on the device; grids are
+// sums, downsweep), or one for up to SCAN_CHUNK elements.  The element count may live on the device; grids are
 // sized from a host-side upper bound so the sequence can be graph-captured.
 #pragma once
 #include "tgs_common.cuh"
@@ -102,6 +102,31 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(Load load, Store sto
     }
 }
 
+// Up to SCAN_CHUNK elements: the whole scan in one block and one launch.
+template <typename T, typename Load, typename Store>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_single(Load load, Store store, const int64_t* n_dev,
+                                                              int64_t n_host, T* total_out) {
+  __shared__ T wt[32];
+  const int64_t n = load_count(n_dev, n_host);
+  const int64_t base = (int64_t)threadIdx.x * SCAN_ITEMS;
+  T v[SCAN_ITEMS];
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    v[k] = (base + k < n) ? load(base + k) : T(0);
+    s += v[k];
+  }
+  T total;
+  T run = block_exclusive_scan<T>(s, wt, total);
+#pragma unroll
+  for (int k = 0; k < SCAN_ITEMS; ++k)
+    if (base + k < n) {
+      store(base + k, run, v[k]);
+      run += v[k];
+    }
+  if (threadIdx.x == 0 && total_out) *total_out = total;
+}
+
 inline int scan_blocks(int64_t n_host) { return (int)((n_host + SCAN_CHUNK - 1) / SCAN_CHUNK); }
 
 // Exclusive scan: store(i, prefix_i, value_i) for i < n; *total_out = sum.
@@ -110,7 +135,10 @@ template <typename T, typename Load, typename Store>
 void exclusive_scan(Load load, Store store, const int64_t* n_dev, int64_t n_host, T* block_sums, T* total_out,
                     cudaStream_t s) {
   int nb = scan_blocks(n_host);
-  if (nb == 0) nb = 1;
+  if (nb <= 1) {
+    k_scan_single<T, Load, Store><<<1, SCAN_THREADS, 0, s>>>(load, store, n_dev, n_host, total_out);
+    return;
+  }
   k_scan_reduce<T, Load><<<nb, SCAN_THREADS, 0, s>>>(load, n_dev, n_host, block_sums);
   k_scan_block_sums<T><<<1, 1024, 0, s>>>(block_sums, nb, total_out);
   k_scan_down<T, Load, Store><<<nb, SCAN_THREADS, 0, s>>>(load, store, n_dev, n_host, block_sums);

@@ -119,6 +119,34 @@ def test_full_mask_equals_dense_bitwise(B, orc):
     np.testing.assert_array_equal(img[spix[:, 1], spix[:, 0]], s_got["rgb"])
 
 
+def test_forward_blend_variants_bitwise(B, orc):
+    """The forward picks its blend by how many warps the launch has (selects
+    for a sparse launch, branches for a dense one); both give the same bits.
+    The same 64 active tiles are rendered once with n_active_max = 64 and
+    once with an upper bound large enough for the branch variant (the blocks
+    past n_active exit at once)."""
+    from gpu_util import bin_dev, dev, projected_dev, select_dev
+    W = H = 256
+    pr = scenes.projected(4000, W, H, seed=91)
+    err, age = scenes.error_map(W, H), scenes.age_map(W, H)
+    n_pix = 256
+    sel = select_dev(B, err, age, W, H, 64, n_pix, seed=5)
+    pd = projected_dev(pr)
+    cam = dict(viewmat=np.eye(4), fx=100.0, fy=100.0, cx=W / 2, cy=H / 2, width=W, height=H, znear=0.2)
+    binned = bin_dev(B, pd, 4000, cam, sel["tile_rank"], sel["n_sel"], capacity=300000)
+    outs = []
+    for n_active_max in (sel["n_sel"], 20000):   # 20000 blocks x 8 warps: many warps per SM
+        P = sel["n_sel"] * n_pix
+        o = dict(rgb=torch.zeros(P, 3, device="cuda"), T=torch.zeros(P, device="cuda"),
+                 n_last=torch.zeros(P, dtype=torch.int32, device="cuda"))
+        B.render_sampled(pd, binned["ranges"], binned["vals"], sel["active_tiles"], sel["n_active"], n_active_max,
+                         sel["pix_off"], sel["pix_idx"], n_pix, cam, (0.1, 0.2, 0.3), o["rgb"], o["T"], o["n_last"])
+        outs.append(o)
+    torch.cuda.synchronize()
+    for k in ("rgb", "T", "n_last"):
+        assert torch.equal(outs[0][k], outs[1][k]), k
+
+
 def test_render_chain_from_gaussians(B, orc):
     """Raw Gaussians of the tiny configuration through project -> bin ->
     render on the GPU against the oracle's double-precision chain."""
