@@ -582,6 +582,13 @@ def run_batched(args):
         for _ in range(args.warmup):
             mv.replay()
         torch.cuda.synchronize()
+        if args.profile:  # replays inside an NVTX range for an ncu launch list, persistent launches only
+            torch.cuda.nvtx.range_push("batched_step")
+            for _ in range(args.steps):
+                mv.replay()
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+            return
         clk = ClockSampler(0)
         clk.start()
         ms = time_replays(mv, args.steps, flush)
