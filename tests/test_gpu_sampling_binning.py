@@ -130,9 +130,12 @@ def test_bin_tiles_crowded_tile_bit_exact(B, orc, n, n_crowd, presort):
 
 # One tile's list grown through each size band of the per-tile sort (up to
 # 256, 512, 1024, 2048 and 4096 keys in registers, and past 4096 in global
-# memory), with exact depth ties, on the path without the depth presort.
+# memory), with exact depth ties.  presort: the same lists through the depth
+# presort and the segment sort (whole list in shared memory up to 4096 keys,
+# with segments sorted per lane, per warp and per block).
+@pytest.mark.parametrize("presort", [False, True])
 @pytest.mark.parametrize("n_crowd", [200, 300, 700, 1500, 3000, 3900, 4200])
-def test_bin_tiles_sort_bands_bit_exact(B, orc, n_crowd):
+def test_bin_tiles_sort_bands_bit_exact(B, orc, n_crowd, presort):
     from gpu_util import bin_dev, projected_dev
     W, H = 256, 256
     n = n_crowd + 500
@@ -151,7 +154,8 @@ def test_bin_tiles_sort_bands_bit_exact(B, orc, n_crowd):
     keys_w, vals_w, counts_w = orc.bin_tiles(pr["xy"], pr["radius"], pr["depth"], W, H)
     assert counts_w.max() >= n_crowd
     cam = dict(viewmat=np.eye(4), fx=100.0, fy=100.0, cx=W / 2, cy=H / 2, width=W, height=H, znear=0.2)
-    out = bin_dev(B, projected_dev(pr), n, cam, None, 256, capacity=len(vals_w) + 3)
+    cap = max(len(vals_w) + 3, 2049 * 256) if presort else len(vals_w) + 3
+    out = bin_dev(B, projected_dev(pr), n, cam, None, 256, capacity=cap)
     I = int(out["n_isect"].item())
     assert I == len(vals_w)
     np.testing.assert_array_equal(out["vals"][:I].cpu().numpy(), vals_w)
