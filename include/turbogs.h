@@ -506,6 +506,12 @@ tgs_status tgs_mlp_forward(const tgs_mlp* w, int64_t rows, const float* x, float
 tgs_status tgs_mlp_forward_tc(const tgs_mlp* w, int64_t rows, const float* x, float* y, uint16_t* h1, uint16_t* h2,
                               int32_t* status, tgs_stream stream);
 
+/* Failure drill of the timeout path above (not in the paper): one CTA of the
+ * same kernel allocates its tensor memory, waits a short bounded time on an
+ * mbarrier phase that nothing completes, sets *status (device int32) to 1,
+ * frees the tensor memory and returns.  No tensor-core work is issued. */
+tgs_status tgs_mlp_tc_wait_drill(int32_t* status, tgs_stream stream);
+
 /* Gradient of L = (1/R) sum (y - t)^2 / 2 into grads (packed layout, fp32,
  * overwritten) and *loss (device double), from the forward's x, h1, h2, y.
  * Hidden adjoints are rounded to bf16 before they meet a bf16 operand.  R is

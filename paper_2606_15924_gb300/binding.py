@@ -164,6 +164,8 @@ _lib.tgs_mlp_forward.restype = _i32
 _lib.tgs_mlp_forward.argtypes = [_P(Mlp), _i64, _p, _p, _p, _p, _p]
 _lib.tgs_mlp_forward_tc.restype = _i32
 _lib.tgs_mlp_forward_tc.argtypes = [_P(Mlp), _i64, _p, _p, _p, _p, _p, _p]
+_lib.tgs_mlp_tc_wait_drill.restype = _i32
+_lib.tgs_mlp_tc_wait_drill.argtypes = [_p, _p]
 _lib.tgs_mlp_backward_workspace_size.restype = _sz
 _lib.tgs_mlp_backward_workspace_size.argtypes = [_i64]
 _lib.tgs_mlp_backward.restype = _i32
@@ -187,7 +189,7 @@ EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_devi
             "tgs_project_backward_multi", "tgs_project_backward_update",
             "tgs_render_batched_resident", "tgs_render_sampled_batched",
             "tgs_render_backward_batched", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step",
-            "tgs_mlp_param_count", "tgs_mlp_forward", "tgs_mlp_forward_tc", "tgs_mlp_backward_workspace_size",
+            "tgs_mlp_param_count", "tgs_mlp_forward", "tgs_mlp_forward_tc", "tgs_mlp_tc_wait_drill", "tgs_mlp_backward_workspace_size",
             "tgs_mlp_backward",
             "tgs_mlp_adam", "tgs_tile_observe", "tgs_tile_features", "tgs_tile_refresh"]
 
@@ -511,6 +513,10 @@ def mlp_forward_tc(net: dict, x, y, h1=None, h2=None, status=None, stream=None):
     m = mlp_struct(net)
     _check("tgs_mlp_forward_tc", _lib.tgs_mlp_forward_tc(C.byref(m), int(x.shape[0]), _ptr(x), _ptr(y), _ptr(h1),
                                                          _ptr(h2), _ptr(status), _stream(stream)))
+
+
+def mlp_tc_wait_drill(status, stream=None):
+    _check("tgs_mlp_tc_wait_drill", _lib.tgs_mlp_tc_wait_drill(_ptr(status), _stream(stream)))
 
 
 def mlp_backward_workspace_size(rows: int) -> int:

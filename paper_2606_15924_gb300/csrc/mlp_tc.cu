@@ -31,6 +31,7 @@ constexpr int TI = 16, TH = 128, TM = 128;  // input width, hidden width, rows p
 constexpr int kTcThreads = 128;
 constexpr uint32_t kTmemCols = 256;         // D1 (0-127) and D2 (128-255)
 constexpr long long kWaitLimit = 1ll << 22; // try_wait rounds before giving up
+constexpr long long kDrillLimit = 1024;     // the same for the timeout drill
 
 // byte offsets of the shared-memory operand tiles
 constexpr uint32_t SBO_K16 = (TI / 8) * 128;    // 8-row group stride of a K = 16 tile
@@ -81,8 +82,8 @@ __device__ __forceinline__ void commit(uint32_t mbar) {
 }
 
 // Bounded wait for the mbarrier's phase `parity` to complete.
-__device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) {
-  for (long long it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity, long long limit = kWaitLimit) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
@@ -128,30 +129,30 @@ struct TcArgs {
 __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(TcArgs w, const float* __restrict__ x, int64_t R,
                                                                   float* __restrict__ y, uint16_t* __restrict__ h1,
                                                                   uint16_t* __restrict__ h2,
-                                                                  int32_t* __restrict__ status) {
+                                                                  int32_t* __restrict__ status, int drill) {
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_mbar;
   const int t = threadIdx.x, warp = t >> 5;
   float* par = reinterpret_cast<float*>(sm + OFF_PAR);  // b1 [128], b2 [128], w3 [128], b3
   // weights into the canonical layouts (each 16-byte chunk = 8 k-values of one row)
-  for (int i = t; i < TH * (TI / 8); i += kTcThreads) {
+  for (int i = t; !drill && i < TH * (TI / 8); i += kTcThreads) {
     const int n = i / (TI / 8), k8 = (i % (TI / 8)) * 8;
     *reinterpret_cast<uint4*>(sm + OFF_W1S + core_off(n, k8, SBO_K16)) =
         *reinterpret_cast<const uint4*>(w.w1 + n * TI + k8);
   }
-  for (int i = t; i < TH * (TH / 8); i += kTcThreads) {
+  for (int i = t; !drill && i < TH * (TH / 8); i += kTcThreads) {
     const int n = i / (TH / 8), k8 = (i % (TH / 8)) * 8;
     *reinterpret_cast<uint4*>(sm + OFF_W2S + core_off(n, k8, SBO_K128)) =
         *reinterpret_cast<const uint4*>(w.w2 + n * TH + k8);
   }
-  for (int i = t; i < TH; i += kTcThreads) {
+  for (int i = t; !drill && i < TH; i += kTcThreads) {
     par[i] = w.b1[i];
     par[TH + i] = w.b2[i];
     par[2 * TH + i] = __uint_as_float((uint32_t)w.w3[i] << 16);
   }
   if (t == 0) {
-    par[3 * TH] = w.b3[0];
+    if (!drill) par[3 * TH] = w.b3[0];
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -169,8 +170,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(TcArgs w, cons
   const uint32_t base = smem_u32(sm);
   const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;  // this warp's TMEM lanes
   uint32_t phase = 0;
-  bool failed = false;  // uniform across the CTA (decided by __syncthreads_or)
-  const int64_t tiles = (R + TM - 1) / TM;
+  bool failed = false;   // uniform across the CTA (decided by __syncthreads_or)
+  bool pending = false;  // MMAs committed whose completion was not observed
+  // drill: the timeout path on a phase that nothing completes (no MMA issued)
+  if (drill && __syncthreads_or(!wait_parity(mbar, phase, kDrillLimit))) failed = true;
+  const int64_t tiles = drill ? 0 : (R + TM - 1) / TM;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t row = tile * TM + t;
     const bool valid = row < R;
@@ -198,7 +202,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(TcArgs w, cons
       commit(mbar);
     }
     if (__syncthreads_or(!wait_parity(mbar, phase))) {
-      failed = true;
+      failed = pending = true;
       break;
     }
     phase ^= 1u;
@@ -232,7 +236,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(TcArgs w, cons
       commit(mbar);
     }
     if (__syncthreads_or(!wait_parity(mbar, phase))) {
-      failed = true;
+      failed = pending = true;
       break;
     }
     phase ^= 1u;
@@ -265,7 +269,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(TcArgs w, cons
   }
   if (failed) {
     if (t == 0 && status) atomicExch(status, 1);
-    wait_parity(mbar, phase);  // the MMAs still in flight (phase not yet observed; bounded)
+    if (pending) wait_parity(mbar, phase);  // the MMAs still in flight (phase not yet observed; bounded)
   }
   fence_before();
   __syncthreads();
@@ -297,6 +301,21 @@ extern "C" tgs_status tgs_mlp_forward_tc(const tgs_mlp* w, int64_t rows, const f
   const int64_t tiles = (rows + TM - 1) / TM;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 2ll * sms));
   k_mlp_forward_tc<<<grid, kTcThreads, SMEM_REQ, (cudaStream_t)stream>>>(
-      TcArgs{w->w1, w->w2, w->w3, w->b1, w->b2, w->b3}, x, rows, y, h1, h2, status);
+      TcArgs{w->w1, w->w2, w->w3, w->b1, w->b2, w->b3}, x, rows, y, h1, h2, status, 0);
+  return check_launch();
+}
+
+extern "C" tgs_status tgs_mlp_tc_wait_drill(int32_t* status, tgs_stream stream) {
+  if (!status) return TGS_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return check_launch();
+  static bool attr[64] = {};
+  if (dev < 0 || dev >= 64) return TGS_ERR_DEVICE;
+  if (!attr[dev]) {
+    cudaFuncSetAttribute(k_mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_REQ);
+    attr[dev] = true;
+  }
+  k_mlp_forward_tc<<<1, kTcThreads, SMEM_REQ, (cudaStream_t)stream>>>(TcArgs{}, nullptr, 0, nullptr, nullptr,
+                                                                       nullptr, status, 1);
   return check_launch();
 }

@@ -96,3 +96,25 @@ def test_adam_step_and_training(P):
         l = mlp.train_step(x, t)
     l1 = float(l.item())
     assert l1 < 0.1 * l0, (l0, l1)
+
+
+def test_tc_wait_timeout_drill(P):
+    """The tcgen05 kernel's bounded wait, made to run out on an mbarrier phase
+    that nothing completes: the kernel records status 1, frees its tensor
+    memory and returns, and the context stays usable (a forward right after
+    succeeds with status 0 and matches the mma.sync forward)."""
+    B, TileErrorMLP = P
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.mlp_tc_wait_drill(status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 1
+    mlp = TileErrorMLP(seed=3)
+    xd = torch.from_numpy(_features(300, 3)).cuda()
+    y = torch.empty(300, device="cuda")
+    y_ref = torch.empty(300, device="cuda")
+    st2 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.mlp_forward_tc(mlp.net(), xd, y, status=st2)
+    B.mlp_forward(mlp.net(), xd, y_ref)
+    torch.cuda.synchronize()
+    assert int(st2.item()) == 0
+    assert rel_l2(y.cpu().numpy(), y_ref.cpu().numpy()) <= 1e-3
