@@ -196,12 +196,17 @@ __device__ __forceinline__ void vis_chunk(const int32_t* n_vis, int64_t n_host, 
   i1 = min(nv, i0 + chunk);
 }
 
+// With reserve (per-rank counters, zeroed): instead of its counts, the block
+// stores in table[r * G + b] the offset of its pairs inside rank r's list,
+// reserved with one atomic per rank it touches (blocks land in any order
+// within a list: only for lists that are sorted whole afterwards).
 __global__ void __launch_bounds__(kHistThreads) k_hist_count(const float2* __restrict__ xy,
                                                              const int32_t* __restrict__ radius,
                                                              const uint32_t* __restrict__ order,
                                                              const int32_t* __restrict__ n_vis, int64_t n,
                                                              BinGeom geo, const int32_t* __restrict__ tile_rank,
-                                                             int64_t* __restrict__ table) {
+                                                             int64_t* __restrict__ table,
+                                                             int32_t* __restrict__ reserve) {
   extern __shared__ uint32_t sh[];
   const int R = geo.n_ranks, G = gridDim.x, b = blockIdx.x;
   for (int r = threadIdx.x; r < R; r += blockDim.x) sh[r] = 0;
@@ -210,7 +215,12 @@ __global__ void __launch_bounds__(kHistThreads) k_hist_count(const float2* __res
   vis_chunk(n_vis, n, i0, i1);
   for_each_pair(xy, radius, i0, i1, geo, tile_rank, [&](int64_t, int k) { atomicAdd(sh + k, 1u); }, order);
   __syncthreads();
-  for (int r = threadIdx.x; r < R; r += blockDim.x) table[(size_t)r * G + b] = sh[r];
+  if (reserve) {
+    for (int r = threadIdx.x; r < R; r += blockDim.x)
+      if (sh[r]) table[(size_t)r * G + b] = atomicAdd(reserve + r, (int32_t)sh[r]);
+  } else {
+    for (int r = threadIdx.x; r < R; r += blockDim.x) table[(size_t)r * G + b] = sh[r];
+  }
 }
 
 // 3'. shared-memory path: scatter with shared cursors that start at the
@@ -223,10 +233,15 @@ __global__ void __launch_bounds__(kHistThreads) k_hist_scatter(const float2* __r
                                                                const int32_t* __restrict__ n_vis, int64_t n,
                                                                BinGeom geo, const int32_t* __restrict__ tile_rank,
                                                                const int64_t* __restrict__ table,
+                                                               const int64_t* __restrict__ rank_start,
                                                                uint64_t* __restrict__ keys, int64_t cap) {
   extern __shared__ uint32_t sh[];
   const int R = geo.n_ranks, G = gridDim.x, b = blockIdx.x;
-  for (int r = threadIdx.x; r < R; r += blockDim.x) sh[r] = (uint32_t)min(table[(size_t)r * G + b], cap);
+  // the table holds absolute offsets, or (rank_start given) offsets within
+  // each rank's list; entries of ranks the block has no pair in are not read
+  // back as positions
+  for (int r = threadIdx.x; r < R; r += blockDim.x)
+    sh[r] = (uint32_t)min(table[(size_t)r * G + b] + (rank_start ? rank_start[r] : 0), cap);
   __syncthreads();
   int64_t i0, i1;
   vis_chunk(n_vis, n, i0, i1);
@@ -664,15 +679,32 @@ extern "C" tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const 
                                        nullptr, s);
       order = w.dv[cur];
     }
-    k_hist_count<<<G, kHistThreads, smem, s>>>(xy, proj->radius, order, n_vis, n, geo, tile_rank, w.table);
-    int64_t* tab = w.table;
-    auto load = [=] __device__(int64_t i) -> int64_t { return tab[i]; };
-    auto store = [=] __device__(int64_t i, int64_t pre, int64_t) { tab[i] = pre; };
-    exclusive_scan<int64_t>(load, store, nullptr, (int64_t)R * G, w.scan_sums, n_isect, s);
-    src.table = w.table;
-    src.G = G;
-    src.R = R;
-    src.total = n_isect;
+    if (presort) {
+      // segments must follow the chunk order: a scan of the whole table
+      k_hist_count<<<G, kHistThreads, smem, s>>>(xy, proj->radius, order, n_vis, n, geo, tile_rank, w.table,
+                                                 nullptr);
+      int64_t* tab = w.table;
+      auto load = [=] __device__(int64_t i) -> int64_t { return tab[i]; };
+      auto store = [=] __device__(int64_t i, int64_t pre, int64_t) { tab[i] = pre; };
+      exclusive_scan<int64_t>(load, store, nullptr, (int64_t)R * G, w.scan_sums, n_isect, s);
+      src.table = w.table;
+      src.G = G;
+      src.R = R;
+      src.total = n_isect;
+    } else {
+      // lists are sorted whole afterwards: blocks reserve their runs with
+      // per-rank atomics, and only the R rank totals are scanned
+      cudaMemsetAsync(w.tile_cnt, 0, sizeof(int32_t) * (size_t)R, s);
+      k_hist_count<<<G, kHistThreads, smem, s>>>(xy, proj->radius, order, n_vis, n, geo, tile_rank, w.table,
+                                                 w.tile_cnt);
+      const int32_t* cnt = w.tile_cnt;
+      int64_t* start = w.tile_start;
+      auto load = [=] __device__(int64_t r) -> int64_t { return cnt[r]; };
+      auto store = [=] __device__(int64_t r, int64_t pre, int64_t) { start[r] = pre; };
+      exclusive_scan<int64_t>(load, store, nullptr, R, w.scan_sums, n_isect, s);
+      src.start = w.tile_start;
+      src.cnt = w.tile_cnt;
+    }
   } else {
     const int gb = (int)((n + 255) / 256);
     cudaMemsetAsync(w.tile_cnt, 0, sizeof(int32_t) * (size_t)R, s);
@@ -689,7 +721,7 @@ extern "C" tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const 
   if (capacity == 0) return check_launch();
   if (shared_path) {
     k_hist_scatter<<<G, kHistThreads, smem, s>>>(xy, proj->radius, proj->depth, order, n_vis, n, geo, tile_rank,
-                                                 w.table, w.keys, capacity);
+                                                 w.table, presort ? nullptr : w.tile_start, w.keys, capacity);
   } else {
     k_scatter_pairs<<<(int)((n + 255) / 256), 256, 0, s>>>(xy, proj->radius, proj->depth, n, geo, tile_rank,
                                                            w.tile_start, w.tile_fill, w.keys, capacity);
