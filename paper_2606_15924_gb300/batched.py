@@ -77,8 +77,14 @@ class MultiViewTrainer:
         self.n_pix_max = max(v.n_pix for v in self.views)
         # checkpoints for the split backward: one slot every CKPT_EVERY list
         # positions, up to CKPT_POSITIONS
-        if checkpoints is None:  # split only when the views' tiles cannot fill the GPU
-            checkpoints = sum(v.n_select for v in self.views) < 4 * B.render_batched_resident(self.n_pix_max, 1)
+        if checkpoints is None:
+            # with the persistent launch the warp-per-piece backward beats the
+            # whole-tile one even when the views' tiles fill the GPU (8 views
+            # of 3M Gaussians at 1920x1080: 1.57 against 1.70 ms); one launch
+            # per view keeps the whole-tile kernel (its pieces past the last
+            # slot would run as one long tail per tile).  Checkpoints cost
+            # n_pix x 64 float4 per active tile.
+            checkpoints = self.persistent
         self.ck_slots = Trainer.CKPT_POSITIONS // Trainer.CKPT_EVERY if checkpoints else 0
         for v in self.views:
             if self.ck_slots:
