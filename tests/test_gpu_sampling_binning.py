@@ -27,6 +27,7 @@ SELECT_CASES = [
     (1280, 720, 720, 84, (0, 0, 0, 0)),            # uniform only
     (37, 21, 3, 1, (400, 300, 400, 300)),          # one pixel per tile, partial tiles
     (64, 64, 0, 10, (400, 300, 400, 300)),         # nothing selected
+    (4096, 1040, 1664, 25, (400, 300, 400, 300)),  # 16 640 tiles: past the one-block selection (pairwise ranks)
 ]
 
 
