@@ -1,0 +1,87 @@
+"""The headline workload at full size, in the launch configuration the bench
+times (500k Gaussians, one 1280x720 view, 20 % of the tiles, 85 sampled
+pixels per tile, checkpoints every 32 list positions for the warp-per-piece
+backward), checked against the oracle on outputs it can compute one by one:
+the selection (bit for bit), the projection of every Gaussian, the forward at
+512 seeded sampled pixels, and the backward of a seeded dL/dI that is
+non-zero at those 512 pixels only (so that both sides sum the same terms)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2606_15924_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+MARGIN = 1e-4
+W, H, N = 1280, 720, 500_000
+N_SEL, N_PIX = 720, 85
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def test_full_size_step_against_oracle(orc):
+    from paper_2606_15924_gb300 import binding as B
+    from gpu_util import bin_dev, dev, empty_projected, gaussians_dev, projected_host, select_dev, select_host
+    B.device_check()
+    g = scenes.gaussians(N, seed=scenes.SEED_SCENE, extent=5.0)
+    cam = scenes.look_at((0.0, 0.0, -15.0), width=W, height=H, fov_x_deg=60.0)
+    err, age = scenes.error_map(W, H, seed=21), scenes.age_map(W, H, seed=22)
+    # selection, bit for bit
+    sel = select_dev(B, err, age, W, H, N_SEL, N_PIX, seed=7, it=3)
+    sel_o = orc.select(err, age, W, H, n_select=N_SEL, n_pix=N_PIX, seed=7, it=3)
+    sh = select_host(sel)
+    np.testing.assert_array_equal(sh["active_tiles"], sel_o["active_tiles"])
+    np.testing.assert_array_equal(sh["pix_idx"], sel_o["pix_idx"])
+    # projection of every Gaussian
+    gd = gaussians_dev(g)
+    pd = empty_projected(N)
+    B.project_gaussians(gd, cam, sel["tile_rank"], pd)
+    g64 = {k: v.astype(np.float64) for k, v in g.items()}
+    prw = orc.project(g64, cam, tile_rank=sel_o["tile_rank"])
+    got = projected_host(pd)
+    sure_g = prw["margin"] > MARGIN
+    assert sure_g.mean() > 0.99
+    np.testing.assert_array_equal(got["radius"][sure_g], prw["radius"][sure_g])
+    m = sure_g & (prw["radius"] > 0)
+    assert m.sum() > 100_000
+    np.testing.assert_allclose(got["xy"][m], prw["xy"][m], rtol=1e-5, atol=1e-3)
+    np.testing.assert_allclose(got["rgb"][m], prw["rgb"][m], atol=1e-5)
+    # binning and the forward with checkpoints, as the trainer runs them
+    binned = bin_dev(B, pd, N, cam, sel["tile_rank"], sel["n_sel"], capacity=4_000_000, want_keys=False)
+    I = int(binned["n_isect"].item())
+    assert 0 < I < 4_000_000
+    P = int(sh["pix_off"][-1])
+    slots = 64
+    rgb = torch.zeros(P, 3, device="cuda")
+    T = torch.zeros(P, device="cuda")
+    n_last = torch.zeros(P, dtype=torch.int32, device="cuda")
+    ck_data = torch.empty(B.checkpoint_bytes(N_SEL, N_PIX, slots) // 4, device="cuda")
+    tl = torch.zeros(N_SEL, dtype=torch.int32, device="cuda")
+    ck = B.checkpoints(ck_data, slots, N_SEL * N_PIX, rgb, tl)
+    B.render_sampled(pd, binned["ranges"], binned["vals"], sel["active_tiles"], sel["n_active"], sel["n_sel"],
+                     sel["pix_off"], sel["pix_idx"], N_PIX, cam, (0.0, 0.0, 0.0), rgb, T, n_last, ckpt=ck)
+    rng = np.random.default_rng(11)
+    S = np.sort(rng.choice(P, 512, replace=False))
+    pix = orc.pixel_coords(sel_o["active_tiles"], sel_o["pix_off"], sel_o["pix_idx"], W)[S]
+    want = orc.render_pixels(prw, W, H, pix)
+    sure_p = want["margin"] > MARGIN
+    assert sure_p.mean() > 0.95
+    np.testing.assert_array_equal(n_last.cpu().numpy()[S][sure_p], want["n_last"][sure_p])
+    assert np.abs(rgb.cpu().numpy()[S][sure_p] - want["rgb"][sure_p]).max() <= 1e-4
+    assert np.abs(T.cpu().numpy()[S][sure_p] - want["T"][sure_p]).max() <= 1e-4
+    # the backward from the checkpoints, dL/dI seeded and non-zero at S only
+    dL = np.zeros((P, 3), np.float32)
+    dL[S] = rng.normal(0.0, 1e-3, (len(S), 3)).astype(np.float32)
+    grad2d = torch.zeros(N, 12, device="cuda")
+    B.render_backward_sampled(pd, binned["ranges"], binned["vals"], sel["active_tiles"], sel["n_active"],
+                              sel["n_sel"], sel["pix_off"], sel["pix_idx"], N_PIX, cam, (0.0, 0.0, 0.0), T, n_last,
+                              dev(dL), grad2d, ckpt=ck)
+    g2w = orc.render_backward(prw, W, H, pix, dL[S].astype(np.float64))
+    g2g = grad2d.cpu().numpy()
+    touched = np.abs(g2w).sum(1) > 0
+    assert touched.sum() > 1000
+    ok = sure_g
+    for c in range(9):
+        assert rel_l2(g2g[ok, c], g2w[ok, c]) <= 1e-3, (c, rel_l2(g2g[ok, c], g2w[ok, c]))
