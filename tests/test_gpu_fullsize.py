@@ -3,8 +3,9 @@ times (500k Gaussians, one 1280x720 view, 20 % of the tiles, 85 sampled
 pixels per tile, checkpoints every 32 list positions for the warp-per-piece
 backward), checked against the oracle on outputs it can compute one by one:
 the selection (bit for bit), the projection of every Gaussian, the forward at
-512 seeded sampled pixels, and the backward of a seeded dL/dI that is
-non-zero at those 512 pixels only (so that both sides sum the same terms)."""
+512 seeded sampled pixels, the backward of a seeded dL/dI that is non-zero at
+those 512 pixels only (so that both sides sum the same terms), and the fused
+projection adjoint + hybrid update (mode 1) of the Gaussians it touches."""
 import numpy as np
 import pytest
 import torch
@@ -85,3 +86,56 @@ def test_full_size_step_against_oracle(orc):
     ok = sure_g
     for c in range(9):
         assert rel_l2(g2g[ok, c], g2w[ok, c]) <= 1e-3, (c, rel_l2(g2g[ok, c], g2w[ok, c]))
+
+    # the projection adjoint fused with the hybrid update (diagonal LM, mode 1), as the step runs it
+    gw = orc.project_backward(g64, cam, g2w, tile_rank=sel_o["tile_rank"])        # [N, 59]
+    cfg = np.array([1.6e-4, 5e-3, 1e-3, 2.5e-2, 2.5e-3, 1.25e-4, 0.9, 0.999, 1e-15, 1e-8])
+    opt = dict(lr=cfg[:6], beta1=cfg[6], beta2=cfg[7], eps_adam=cfg[8], eps_lm=cfg[9], mode=1)
+    step = 4
+    p0 = np.concatenate([g["means"], g["log_scales"], g["quats"], g["opacity_logits"][:, None],
+                         np.asarray(g["sh"]).reshape(N, 48)], 1).astype(np.float32)
+    m0 = rng.normal(0.0, 1e-4, p0.shape).astype(np.float32)
+    v0 = rng.uniform(1e-8, 1e-6, p0.shape).astype(np.float32)
+    t_w = (np.abs(g2w).sum(1) > 0) & (prw["radius"] > 0)
+    pw, mw, vw = orc.hybrid_step(p0.astype(np.float64), gw, m0.astype(np.float64), v0.astype(np.float64),
+                                 t_w.astype(np.uint8), step, 1, cfg)
+
+    def split(a):
+        a = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        return dict(means=a[:, 0:3].contiguous(), log_scales=a[:, 3:6].contiguous(), quats=a[:, 6:10].contiguous(),
+                    opacity_logits=a[:, 10].contiguous(), sh=a[:, 11:59].contiguous().view(N, 16, 3))
+
+    def join(d):
+        return np.concatenate([d["means"].cpu().numpy(), d["log_scales"].cpu().numpy(), d["quats"].cpu().numpy(),
+                               d["opacity_logits"].cpu().numpy()[:, None], d["sh"].cpu().numpy().reshape(N, 48)], 1)
+
+    P_, M_, V_ = split(p0), split(m0), split(v0)
+    touched = torch.zeros(N, dtype=torch.uint8, device="cuda")
+    adj = B.MultiAdjoint([cam], [pd["radius"]], [grad2d])
+    B.project_backward_update(P_, adj, M_, V_, touched, opt, step)
+    torch.cuda.synchronize()
+    t_g = touched.cpu().numpy().astype(bool)
+    both = t_g & t_w & sure_g
+    assert both.sum() > 1000 and (t_g[sure_g] == t_w[sure_g]).mean() > 0.999
+    # parameters are stored in fp32: the update lands rounded to the parameter's ulp, which for
+    # means of a few units is a visible share of a step of ~1e-4; the step is compared where it
+    # is well above that rounding, and every element within the rounding plus the gradient's
+    # own tolerance
+    pg = join(P_).astype(np.float64)
+    dp_g, dp_w = pg - p0, pw - p0
+    ulp = np.spacing(np.abs(pw).astype(np.float32)).astype(np.float64)
+    within = np.abs(pg - pw) <= 1.5 * ulp + 2e-3 * np.abs(dp_w) + 1e-12
+    assert within[both].mean() > 0.999
+    big = np.abs(dp_w) > 2000 * ulp
+    checked = 0
+    for name, (a, b) in dict(means=(0, 3), scales=(3, 6), quats=(6, 10), opacity=(10, 11), sh_dc=(11, 14),
+                             sh_rest=(14, 59)).items():
+        sel_b = big[both, a:b]
+        if sel_b.sum() > 100:
+            e = rel_l2(dp_g[both, a:b][sel_b], dp_w[both, a:b][sel_b])
+            assert e <= 1e-3, (name, e)
+            checked += 1
+        assert rel_l2(join(M_)[both, a:b], mw[both, a:b]) <= 1e-3, name
+    assert checked >= 3
+    untouched = ~t_g
+    np.testing.assert_array_equal(join(P_)[untouched], p0[untouched])
