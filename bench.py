@@ -339,6 +339,34 @@ def roofline(stage_ms, info, peaks, peak_kind, clocks, tr, dom=None):
                 traffic=measured_traffic(dom))
 
 
+def error_stats_time(tr, info, flush, clocks, peaks, reps: int = 5) -> dict:
+    """The error back-projection statistics of Sec. 3.8 (a pass after the
+    loss, not part of the timed step) on the step's sampled pixels: device ms
+    per call (events on the launch stream, L2 flushed before each) and its
+    FP32 rate (15 FLOPs for the alpha test + 12 for the weights and the
+    distance per (pixel, splat) walked)."""
+    import torch
+    from paper_2606_15924_gb300 import binding as B
+    stats = torch.zeros(tr.n, 4, device=tr.params["means"].device)
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ms = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        a.record(stream)
+        B.error_stats_sampled(tr.proj, tr.ranges, tr.vals, tr.active_tiles, tr.n_active, tr.n_select, tr.pix_off,
+                              tr.pix_idx, tr.n_pix, tr.ccam, tr.n_last, tr.err_pix, stats, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = sorted(ms)[len(ms) // 2]
+    sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = info["evals_per_step"] * 27 / (t * 1e-3) / 1e12
+    return {"ms": t, "bound": "alu", "achieved": achieved, "unit": "TFLOP/s", "frac": achieved / alu_peak,
+            "note": "Sec. 3.8 statistics over the step's sampled pixels; not in the timed step"}
+
+
 def e2e_replays(tr, target_host, steps):
     """Public-API step with the view's target copied in from pinned host memory
     and the loss read back, every step."""
@@ -476,6 +504,7 @@ def run_ours(args):
     fwdbwd_ms = st["render_sampled"] + st["render_backward"] + st.get("project_backward",
                                                                        st.get("project_backward_update", 0.0))
     mpix = info["P"] / (fwdbwd_ms * 1e-3) / 1e6
+    err_stats = error_stats_time(sampled, info, flush, clocks, peaks)
     res = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": mean_s, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded scenes; the paper's datasets are not "
@@ -486,6 +515,7 @@ def run_ours(args):
                        "active_tiles": info["A"], "tile_pairs": info["n_isect"], "touched": info["touched"],
                        "visible": info["visible"], "splat_evals": info["evals_per_step"], "tile_lists": info["tiles"],
                        "fwd_bwd_mpix_per_s": mpix, "stage_ms": st, "kernels_per_step": launches,
+                       "error_stats": err_stats,
                        "stage_rooflines": {k: {"bound": v["bound"], "achieved": v["achieved"], "unit": v["unit"],
                                                "frac": v["frac"]} for k, v in stage_roofs.items()}}}
     if ms_d is not None:

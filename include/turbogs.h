@@ -308,6 +308,26 @@ tgs_status tgs_loss_sparse_ncc(const float* rgb, const float* target, int32_t wi
                                tgs_stream stream);
 
 /*
+ * error_stats_sampled - error back-projection statistics (Sec. 3.8, Eq.
+ * gauss_err_accum; Alg. 1 step 11), a pass of its own after the loss.  For
+ * every sampled pixel p and every splat k it blended (list positions below
+ * n_last, alpha as render_sampled computes it), with compositing weight
+ * w = T_k alpha_k and D = sqrt(a dx^2 + 2 b dx dy + c dy^2) the conic
+ * Mahalanobis distance of the pixel centre from the splat, adds
+ * (e(p) w, w, D w, 0) to stats [n_gaussians, 4] (device float, 16-byte
+ * aligned; zeroed first unless accumulate = 1, which sums over the views of
+ * an iteration).  err_pix [P]: the per-pixel error e(p) (as loss_sparse_ncc
+ * writes it); n_last [P]: as render_sampled writes it.  Other arguments as in
+ * render_sampled.  The normalised statistics E / (W + eps), D / (W + eps)
+ * are left to the caller.
+ */
+tgs_status tgs_error_stats_sampled(const tgs_projected* proj, const int32_t* tile_ranges, const int32_t* vals,
+                                   const int32_t* active_tiles, const int32_t* n_active, int32_t n_active_max,
+                                   const int32_t* pix_off, const uint8_t* pix_idx, int32_t n_pix_max,
+                                   const tgs_camera* cam, const int32_t* n_last, const float* err_pix,
+                                   float* stats, int64_t n_gaussians, int32_t accumulate, tgs_stream stream);
+
+/*
  * backward_sampled - sparse backward (Sec. 3.6; Alg. 1 step 8).  Replays each
  * sampled pixel's compositing in reverse from T_final and n_last, recovering
  * T_k = T_{k+1} / (1 - alpha_k), and accumulates the adjoints of the screen-

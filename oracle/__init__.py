@@ -89,6 +89,8 @@ def _declare(L):
     L.orc_render_pixels.restype = _i32
     L.orc_render_backward.argtypes = [_i64, _p, _p, _p, _p, _p, _p, _i32, _i32, _p, _i64, _p, _p, _p]
     L.orc_render_backward.restype = _i32
+    L.orc_error_stats.argtypes = [_i64, _p, _p, _p, _p, _p, _i32, _i32, _i64, _p, _p, _p]
+    L.orc_error_stats.restype = _i32
     L.orc_project_backward.argtypes = [_i64, _p, _p, _p, _p, _p, _i32, _p, _i32, _i32, _p, _p, _p]
     L.orc_project_backward.restype = _i32
     L.orc_loss.argtypes = [_i32, _i32, _i32, _p, _p, _p, _p, _p, _p, _d, _d, _d, _p, _p, _p, _p, _p, _p]
@@ -283,6 +285,24 @@ def render_backward(proj, width, height, pix_xy, dL_drgb, bg=(0.0, 0.0, 0.0)):
     out = np.zeros((n, 9))
     lib().orc_render_backward(n, _ptr(xy), _ptr(conic), _ptr(opac), _ptr(rgb), _ptr(depth), _ptr(radius),
                               width, height, _ptr(bgv), pix.shape[0], _ptr(pix), _ptr(g), _ptr(out))
+    return out
+
+
+def error_stats(proj, width, height, pix_xy, err):
+    """Sec. 3.8, Eq. gauss_err_accum over the listed pixels: stats [N,3] =
+    (sum e w, sum w, sum D w) with w = T alpha the compositing weight and D the
+    conic Mahalanobis distance of the pixel centre from the splat."""
+    xy = _c(proj["xy"], np.float64)
+    conic = _c(proj["conic"], np.float64)
+    opac = _c(proj["opac"], np.float64)
+    depth = _c(proj["depth"], np.float64)
+    radius = _c(proj["radius"], np.int32)
+    n = radius.shape[0]
+    pix = _c(pix_xy, np.int32).reshape(-1, 2)
+    e = _c(err, np.float64).reshape(-1)
+    out = np.zeros((n, 3))
+    lib().orc_error_stats(n, _ptr(xy), _ptr(conic), _ptr(opac), _ptr(depth), _ptr(radius), width, height,
+                          pix.shape[0], _ptr(pix), _ptr(e), _ptr(out))
     return out
 
 

@@ -836,6 +836,38 @@ int orc_render_backward(int64_t n, const double* xy, const double* conic, const 
   return 0;
 }
 
+/*
+ * Error back-projection statistics (Sec. 3.8, Eq. gauss_err_accum) over the
+ * listed pixels.  With w = T_k alpha_k the compositing weight of splat k at
+ * pixel p (as the forward above composites it), stats [N,3] receives
+ * (sum_p e(p) w, sum_p w, sum_p D w), where D = sqrt(a dx^2 + 2 b dx dy +
+ * c dy^2) is the conic Mahalanobis distance of the pixel centre from the
+ * splat's centre.  err [P]: the per-pixel error e(p).
+ */
+int orc_error_stats(int64_t n, const double* xy, const double* conic, const double* opac, const double* depth,
+                    const int32_t* radius, int width, int height, int64_t n_pix, const int32_t* pix_xy,
+                    const double* err, double* stats) {
+  int tx_n = (width + ORC_TILE - 1) / ORC_TILE, ty_n = (height + ORC_TILE - 1) / ORC_TILE;
+  memset(stats, 0, sizeof(double) * 3 * (size_t)n);
+  for (int64_t s = 0; s < n_pix; ++s) {
+    pixel_trace_t p;
+    trace_pixel(n, xy, conic, opac, depth, radius, tx_n, ty_n, pix_xy[2 * s], pix_xy[2 * s + 1], &p);
+    for (int j = 0; j < p.n_acc; ++j) {
+      int i = p.acc_id[j];
+      double w = p.T[j] * p.alpha[j];
+      double dx = p.dx[j], dy = p.dy[j];
+      double a = conic[3 * i], b = conic[3 * i + 1], c = conic[3 * i + 2];
+      double q = a * dx * dx + 2.0 * b * dx * dy + c * dy * dy;
+      double D = sqrt(q > 0.0 ? q : 0.0);
+      stats[3 * i] += err[s] * w;
+      stats[3 * i + 1] += w;
+      stats[3 * i + 2] += D * w;
+    }
+    trace_free(&p);
+  }
+  return 0;
+}
+
 /* ------------------------------------------------------------------------ */
 /* adjoint of the projection                                                */
 /* ------------------------------------------------------------------------ */

@@ -134,6 +134,9 @@ _lib.tgs_backward_sampled.restype = _i32
 _lib.tgs_backward_sampled.argtypes = [_P(Gaussians), _P(Camera), _P(Projected), _p, _p, _p, _p, _i32, _p, _p,
                                       _i32, _p, _p, _p, _p, _p, _P(ParamPtrs), _p, _i32, _P(Checkpoints), _p]
 _lib.tgs_render_backward_sampled.restype = _i32
+_lib.tgs_error_stats_sampled.restype = _i32
+_lib.tgs_error_stats_sampled.argtypes = [_P(Projected), _p, _p, _p, _p, _i32, _p, _p, _i32, _P(Camera), _p, _p, _p,
+                                         _i64, _i32, _p]
 _lib.tgs_render_backward_sampled.argtypes = [_P(Projected), _p, _p, _p, _p, _i32, _p, _p, _i32, _P(Camera), _p, _p,
                                              _p, _p, _p, _i64, _P(Checkpoints), _p]
 _lib.tgs_project_backward.restype = _i32
@@ -185,7 +188,7 @@ EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_devi
             "tgs_project_gaussians",
             "tgs_bin_tiles_workspace_size", "tgs_bin_tiles", "tgs_checkpoint_bytes", "tgs_render_sampled",
             "tgs_loss_sparse_ncc",
-            "tgs_backward_sampled", "tgs_render_backward_sampled", "tgs_project_backward", "tgs_project_backward_multi_workspace_size",
+            "tgs_backward_sampled", "tgs_render_backward_sampled", "tgs_error_stats_sampled", "tgs_project_backward", "tgs_project_backward_multi_workspace_size",
             "tgs_project_backward_multi", "tgs_project_backward_update",
             "tgs_render_batched_resident", "tgs_render_sampled_batched",
             "tgs_render_backward_batched", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step",
@@ -366,6 +369,17 @@ def render_backward_sampled(proj: dict, tile_ranges, vals, active_tiles, n_activ
         C.byref(pr), _ptr(tile_ranges), _ptr(vals), _ptr(active_tiles), _ptr(n_active), int(n_active_max),
         _ptr(pix_off), _ptr(pix_idx), int(n_pix_max), C.byref(cc), bgv, _ptr(T_final), _ptr(n_last), _ptr(dL_drgb),
         _ptr(grad2d), int(grad2d.shape[0]), _ck(ckpt), _stream(stream)))
+
+
+def error_stats_sampled(proj: dict, tile_ranges, vals, active_tiles, n_active, n_active_max, pix_off, pix_idx,
+                        n_pix_max, cam, n_last, err_pix, stats, accumulate=False, stream=None):
+    """stats [N, 4] float: (sum e w, sum w, sum D w, 0) per Gaussian (Sec. 3.8)."""
+    pr = projected(proj)
+    cc = cam if isinstance(cam, Camera) else camera(cam)
+    _check("tgs_error_stats_sampled", _lib.tgs_error_stats_sampled(
+        C.byref(pr), _ptr(tile_ranges), _ptr(vals), _ptr(active_tiles), _ptr(n_active), int(n_active_max),
+        _ptr(pix_off), _ptr(pix_idx), int(n_pix_max), C.byref(cc), _ptr(n_last), _ptr(err_pix), _ptr(stats),
+        int(stats.shape[0]), 1 if accumulate else 0, _stream(stream)))
 
 
 def project_backward(g: dict, cam, proj: dict, grad2d, grads: dict, touched, write_untouched=True,

@@ -508,6 +508,71 @@ __global__ void __launch_bounds__(32 * kBwdWarps) k_render_bwd_warp(RasterArgs a
   render_piece_bwd_warp<PPL>(a, j, c, sm[w], T_final, n_last, dL_drgb, grad2d, ck);
 }
 
+// Error back-projection statistics (Sec. 3.8, Eq. gauss_err_accum): one
+// block per active tile, one thread per sampled pixel, walking the tile's
+// list front to back up to the pixel's n_last (the forward's stopping
+// decision) and recomputing alpha and T as the forward does.  For each splat
+// the warp sums (e w, w, D w) over its pixels (w = T alpha, D the conic
+// Mahalanobis distance) and one lane adds them to the Gaussian's float4 row.
+__global__ void k_error_stats(RasterArgs a, const int32_t* __restrict__ n_last, const float* __restrict__ err_pix,
+                              float* __restrict__ stats) {
+  extern __shared__ Splat sm[];
+  __shared__ int s_max_last;
+  const int j = blockIdx.x;
+  if (j >= *a.n_active) return;
+  const int t = a.active_tiles ? a.active_tiles[j] : j;
+  const int p0 = a.pix_off[j], p1 = a.pix_off[j + 1];
+  const bool has_pix = p0 + (int)threadIdx.x < p1;
+  const int s = p0 + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  float px = 0.f, py = 0.f, e = 0.f, T = 1.f;
+  int last = 0;
+  if (has_pix) {
+    const int l = a.pix_idx[s];
+    px = (float)((t % a.tiles_x) * TGS_TILE + (l & 15)) + 0.5f;
+    py = (float)((t / a.tiles_x) * TGS_TILE + (l >> 4)) + 0.5f;
+    e = err_pix[s];
+    last = n_last[s];
+  }
+  if (threadIdx.x == 0) s_max_last = 0;
+  __syncthreads();
+  if (last > 0) atomicMax(&s_max_last, last);
+  __syncthreads();
+  const int2 range = a.ranges[j];
+  const int end = range.x + s_max_last;
+  const int B = blockDim.x;
+  for (int base = range.x; base < end; base += B) {
+    __syncthreads();  // the previous batch is no longer read
+    if (base + (int)threadIdx.x < end) load_splat(a, base + threadIdx.x, sm[threadIdx.x]);
+    __syncthreads();
+    const int cnt = min(B, end - base);
+    for (int q = 0; q < cnt; ++q) {
+      const Splat sp = sm[q];
+      float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+      bool on = false;
+      if (base + q - range.x < last) {
+        const float dx = __fsub_rn(px, sp.xy.x), dy = __fsub_rn(py, sp.xy.y);
+        float alpha, G;
+        if (splat_alpha(sp.co, dx, dy, alpha, G)) {
+          const float w = alpha * T;
+          const float qf = sp.co.x * dx * dx + 2.f * sp.co.y * dx * dy + sp.co.z * dy * dy;
+          const float D = sqrtf(fmaxf(qf, 0.f));
+          v0 = e * w;
+          v1 = w;
+          v2 = D * w;
+          T = __fmul_rn(T, __fsub_rn(1.f, alpha));  // the forward's transmittance sequence
+          on = true;
+        }
+      }
+      if (!__any_sync(0xffffffffu, on)) continue;
+      v0 = warp_sum(v0);
+      v1 = warp_sum(v1);
+      v2 = warp_sum(v2);
+      if (lane == 0) red_add_v4(stats + 4 * (size_t)__float_as_int(sp.rgb.w), v0, v1, v2, 0.f);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Several views in one persistent launch: CTAs take (view, tile) items from
 // an atomic counter (items of view v are [base[v], base[v+1])) until none
@@ -716,6 +781,29 @@ extern "C" tgs_status tgs_render_backward_sampled(const tgs_projected* proj, con
       }
     } else
       k_render_bwd<<<n_active_max, B, smem, s>>>(a, T_final, n_last, dL_drgb, grad2d);
+  }
+  return check_launch();
+}
+
+extern "C" tgs_status tgs_error_stats_sampled(const tgs_projected* proj, const int32_t* tile_ranges,
+                                              const int32_t* vals, const int32_t* active_tiles,
+                                              const int32_t* n_active, int32_t n_active_max, const int32_t* pix_off,
+                                              const uint8_t* pix_idx, int32_t n_pix_max, const tgs_camera* cam,
+                                              const int32_t* n_last, const float* err_pix, float* stats,
+                                              int64_t n_gaussians, int32_t accumulate, tgs_stream stream) {
+  RasterArgs a;
+  const float bg[3] = {0.f, 0.f, 0.f};
+  if (n_gaussians < 0 || n_active_max < 0 || n_pix_max < 1 || n_pix_max > 256) return TGS_ERR_INVALID_ARG;
+  if (!raster_args(proj, tile_ranges, vals, active_tiles, n_active, pix_off, pix_idx, cam, bg, a))
+    return TGS_ERR_INVALID_ARG;
+  if (!n_last || !err_pix) return TGS_ERR_INVALID_ARG;
+  if (n_gaussians > 0 && (!stats || !aligned16(stats))) return TGS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_gaussians == 0) return TGS_OK;
+  if (!accumulate) cudaMemsetAsync(stats, 0, sizeof(float) * 4 * (size_t)n_gaussians, s);
+  if (n_active_max > 0) {
+    const int B = block_for(n_pix_max);
+    k_error_stats<<<n_active_max, B, B * sizeof(Splat), s>>>(a, n_last, err_pix, stats);
   }
   return check_launch();
 }

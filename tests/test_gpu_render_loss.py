@@ -336,3 +336,44 @@ def test_hybrid_step_parity(B, orc, mode):
     dp_g, dp_w = join(P_) - p, pw - p
     assert rel_l2(dp_g, dp_w) <= 1e-3
     np.testing.assert_allclose(join(P_), pw, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("n_select,n_pix", [(64, 84), (256, 256)])
+def test_error_stats_parity(B, orc, n_select, n_pix):
+    """Sec. 3.8 error back-projection statistics (sum e w, sum w, sum D w per
+    Gaussian) against the oracle, from a seeded per-pixel error that both
+    sides take as input; with accumulate the second call adds to the first."""
+    from gpu_util import bin_dev, dev, empty_projected, gaussians_dev, render_dev, select_dev, select_host
+    g, cam = _c0(seed=5, n=3000)
+    g["log_scales"] += 1.0
+    W = H = 256
+    n = 3000
+    err, age = scenes.error_map(W, H), scenes.age_map(W, H)
+    sel = select_dev(B, err, age, W, H, n_select, n_pix, seed=4)
+    sh = select_host(sel)
+    gd = gaussians_dev(g)
+    pd = empty_projected(n)
+    B.project_gaussians(gd, cam, sel["tile_rank"], pd)
+    binned = bin_dev(B, pd, n, cam, sel["tile_rank"], sel["n_sel"], capacity=300000)
+    out = render_dev(B, pd, binned, sel, n_pix, cam)
+    P = int(sh["pix_off"][-1])
+    pix = orc.pixel_coords(sh["active_tiles"], sh["pix_off"], sh["pix_idx"], W)
+    e = np.random.default_rng(9).uniform(0.0, 2.0, P).astype(np.float32)
+    stats = torch.zeros(n, 4, device="cuda")
+    args = (pd, binned["ranges"], binned["vals"], sel["active_tiles"], sel["n_active"], sel["n_sel"], sel["pix_off"],
+            sel["pix_idx"], n_pix, cam, out["n_last"], dev(e))
+    B.error_stats_sampled(*args, stats)
+    torch.cuda.synchronize()
+    got = stats.cpu().numpy().astype(np.float64)
+    g64 = {k: v.astype(np.float64) for k, v in g.items()}
+    prw = orc.project(g64, cam, tile_rank=sh["tile_rank"])
+    want = orc.error_stats(prw, W, H, pix, e.astype(np.float64))
+    ok = prw["margin"] > MARGIN
+    assert (want[ok, 1] > 0).sum() > 200
+    for c in range(3):
+        assert rel_l2(got[ok, c], want[ok, c]) <= 1e-3, (c, rel_l2(got[ok, c], want[ok, c]))
+    assert np.all(got[:, 3] == 0.0)
+    B.error_stats_sampled(*args, stats, accumulate=True)
+    torch.cuda.synchronize()
+    # float atomics sum in a different order on each call: equal up to rounding
+    np.testing.assert_allclose(stats.cpu().numpy()[:, :3], 2.0 * got[:, :3], rtol=1e-5, atol=1e-6)

@@ -144,3 +144,54 @@ def test_projection_culls(orc):
     rank = np.full(16, -1, np.int32)
     pr2 = orc.project(g, cam, tile_rank=rank)
     assert np.all(pr2["radius"] == 0)
+
+
+def test_error_stats_identities(orc):
+    """Sec. 3.8 statistics: the compositing weights of a pixel sum to
+    1 - T_final, so sum_i W_i = sum_p (1 - T_final(p)) and sum_i E_i =
+    sum_p e(p) (1 - T_final(p)); D is non-negative."""
+    g = scenes.gaussians(3000, seed=3, log_scale_mean=-2.3)
+    cam = scenes.look_at((0, 0, -4), width=64, height=64)
+    pr = orc.project(g, cam)
+    ys, xs = np.mgrid[0:64, 0:64]
+    pix = np.stack([xs.ravel(), ys.ravel()], 1).astype(np.int32)
+    rng = np.random.default_rng(5)
+    pix = pix[rng.choice(len(pix), 900, replace=False)]
+    e = rng.uniform(0.0, 2.0, len(pix))
+    st = orc.error_stats(pr, 64, 64, pix, e)
+    out = orc.render_pixels(pr, 64, 64, pix)
+    assert (out["n_contrib"] > 3).mean() > 0.5
+    assert st[:, 1].sum() == pytest.approx((1.0 - out["T"]).sum(), rel=1e-12)
+    assert st[:, 0].sum() == pytest.approx((e * (1.0 - out["T"])).sum(), rel=1e-12)
+    assert np.all(st[:, 2] >= 0.0) and st[:, 2].sum() > 0.0
+    assert np.all(st[pr["radius"] <= 0] == 0.0)
+
+
+@pytest.mark.parametrize("sigma,opacity", [(0.05, 0.7), (0.2, 0.3)])
+def test_error_stats_one_gaussian_closed_form(orc, sigma, opacity):
+    """One isotropic Gaussian in front of the camera: T = 1 at every pixel, so
+    w = alpha = o exp(-r^2 / (2 s2)) and D = r / sqrt(s2) (s2 the screen-space
+    variance), for every pixel whose alpha passes 1/255."""
+    dc = np.array([0.3, -0.2, 1.1])
+    d = 4.0
+    g, cam = _one_gaussian(sigma, opacity, dc, d)
+    W, H = cam["width"], cam["height"]
+    s2 = (cam["fx"] * sigma / d) ** 2 + 0.3
+    pr = orc.project(g, cam)
+    ys, xs = np.mgrid[0:H, 0:W]
+    pix = np.stack([xs.ravel(), ys.ravel()], 1).astype(np.int32)
+    e = np.linspace(0.1, 1.0, len(pix))
+    st = orc.error_stats(pr, W, H, pix, e)
+    r2 = (pix[:, 0] + 0.5 - W / 2) ** 2 + (pix[:, 1] + 0.5 - H / 2) ** 2
+    a = np.minimum(0.99, opacity * np.exp(-0.5 * r2 / s2))
+    on = a >= 1.0 / 255.0
+    # the tile rectangle of the radius bounds which pixels can see the splat
+    r = int(pr["radius"][0])
+    tx0, tx1 = max(0, int((W / 2 - r) // 16)), min(W // 16, int((W / 2 + r) // 16) + 1)
+    ty0, ty1 = max(0, int((H / 2 - r) // 16)), min(H // 16, int((H / 2 + r) // 16) + 1)
+    inside = (pix[:, 0] // 16 >= tx0) & (pix[:, 0] // 16 < tx1) & (pix[:, 1] // 16 >= ty0) & (pix[:, 1] // 16 < ty1)
+    on &= inside
+    assert on.sum() > 20
+    assert st[0, 1] == pytest.approx(a[on].sum(), rel=1e-10)
+    assert st[0, 0] == pytest.approx((e * a)[on].sum(), rel=1e-10)
+    assert st[0, 2] == pytest.approx((np.sqrt(r2 / s2) * a)[on].sum(), rel=1e-10)
