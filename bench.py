@@ -339,6 +339,17 @@ def roofline(stage_ms, info, peaks, peak_kind, clocks, tr, dom=None):
                 traffic=measured_traffic(dom))
 
 
+def replica_throughput(total_ms: float, steps: int, world: int, dist=None, device=None) -> float:
+    """Whole-job iters/s of `world` independent replicas that each timed
+    `steps` steps in total_ms: the slowest rank bounds the job (max over the
+    ranks, an all-reduce when a process group is given)."""
+    import torch
+    tot = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    if dist is not None:
+        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    return world * steps / (tot.item() * 1e-3)
+
+
 def error_stats_time(tr, info, flush, clocks, peaks, reps: int = 5) -> dict:
     """The error back-projection statistics of Sec. 3.8 (a pass after the
     loss, not part of the timed step) on the step's sampled pixels: device ms
@@ -491,10 +502,7 @@ def run_ours(args):
     if dist is not None:
         dist.barrier()
     mean_s = sum(ms_s) / len(ms_s)
-    tot = torch.tensor([sum(ms_s)], dtype=torch.float64, device=device)
-    if dist is not None:
-        dist.all_reduce(tot, op=dist.ReduceOp.MAX)
-    value = world * args.steps / (tot.item() * 1e-3)
+    value = replica_throughput(sum(ms_s), args.steps, world, dist, device)
     launches = sampled.kernels_per_step
     # per-stage times, roofline of the dominant kernel (eager pass, events on the launch stream)
     st, info = stage_times(sampled, max(2, min(args.steps, 5)), flush)

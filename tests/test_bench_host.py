@@ -76,3 +76,35 @@ def test_quality_settings_unique():
     assert s == [(0.4, bench.PIXEL_RATE), (1.0, bench.PIXEL_RATE)]
     args = types.SimpleNamespace(fraction=0.2, rate=bench.PIXEL_RATE)
     assert len(bench.quality_settings(args)) == 3
+
+
+def _replica_rank(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # rank r timed its 10 steps in 20 + 5 r ms: the job is bound by the slowest
+    v = bench.replica_throughput(20.0 + 5.0 * rank, 10, world, dist)
+    out[rank] = v
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_replica_throughput_two_gloo_ranks():
+    """The N > 1 path of the bench (independent replicas, max over ranks) on
+    two CPU processes."""
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    procs = [ctx.Process(target=_replica_rank, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    want = 2 * 10 / (25.0e-3)
+    assert out[0] == pytest.approx(want) and out[1] == pytest.approx(want)
+    assert bench.replica_throughput(20.0, 10, 1) == pytest.approx(10 / 20e-3)
