@@ -106,7 +106,7 @@ typedef struct {
  * (Table 6: 0.4). */
 /* Loss constants (Sec. 3.7, App. A).  view_weight scales this view's loss and
  * dL_drgb: 1 for one view, 1/K for the mean over K views of one step (the
- * expectation over views in Eq. 8). */
+ * expectation over views in Eq. 11). */
 typedef struct {
   float eps_charbonnier, eps_ncc, beta, view_weight;
 } tgs_loss_params;
@@ -134,7 +134,7 @@ int64_t tgs_graph_count_kernels(void* graph);
 
 /*
  * select_tiles - tile selection and tile-wise error-guided pixel sampling
- * (Sec. 3.5, Eqs. 5-6; Alg. 1 step 3).
+ * (Sec. 3.5, Eqs. 7-8; Alg. 1 step 3).
  *
  * Chooses n_sel = min(n_select, T) of the T tiles of one view, then in each
  * chosen tile N_pix = min(n_pix, valid pixels of the tile) pixels.  Each level
@@ -287,7 +287,7 @@ tgs_status tgs_render_sampled(const tgs_projected* proj, const int32_t* tile_ran
                               int32_t* n_last, const tgs_checkpoints* ckpt, tgs_stream stream);
 
 /*
- * loss_sparse_ncc - fused sparse supervision (Sec. 3.7, Eq. 8; App. A;
+ * loss_sparse_ncc - fused sparse supervision (Sec. 3.7, Eqs. 9-11; App. A;
  * Alg. 1 steps 4, 6, 7), one thread block per active tile:
  *   l1(p) = sum_c sqrt((x - y)^2 + eps_c^2);
  *   NCC_c = cov / sqrt(var_x var_y + eps_n) over the tile's sampled pixels;
@@ -308,8 +308,8 @@ tgs_status tgs_loss_sparse_ncc(const float* rgb, const float* target, int32_t wi
                                tgs_stream stream);
 
 /*
- * error_stats_sampled - error back-projection statistics (Sec. 3.8, Eq.
- * gauss_err_accum; Alg. 1 step 11), a pass of its own after the loss.  For
+ * error_stats_sampled - error back-projection statistics (Sec. 3.8, Eq. 12;
+ * Alg. 1 step 11), a pass of its own after the loss.  For
  * every sampled pixel p and every splat k it blended (list positions below
  * n_last, alpha as render_sampled computes it), with compositing weight
  * w = T_k alpha_k and D = sqrt(a dx^2 + 2 b dx dy + c dy^2) the conic
@@ -472,7 +472,7 @@ tgs_status tgs_render_backward_batched(const tgs_view_batch* views, int32_t n_vi
                                        int32_t* counter, tgs_stream stream);
 
 /*
- * hybrid_step - moment-damped LM / Adam update (Sec. 3.9, Eq. 11; App. A;
+ * hybrid_step - moment-damped LM / Adam update (Sec. 3.9, Eq. 14; App. A;
  * Alg. 1 steps 9, 10) of the Gaussians with touched[i] != 0.
  * m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2 on every parameter; the
  * geometry block (means, log_scales, quats: 10) and the appearance block (SH

@@ -289,7 +289,7 @@ def render_backward(proj, width, height, pix_xy, dL_drgb, bg=(0.0, 0.0, 0.0)):
 
 
 def error_stats(proj, width, height, pix_xy, err):
-    """Sec. 3.8, Eq. gauss_err_accum over the listed pixels: stats [N,3] =
+    """Sec. 3.8, Eq. 12 over the listed pixels: stats [N,3] =
     (sum e w, sum w, sum D w) with w = T alpha the compositing weight and D the
     conic Mahalanobis distance of the pixel centre from the splat."""
     xy = _c(proj["xy"], np.float64)

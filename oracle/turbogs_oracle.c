@@ -837,7 +837,7 @@ int orc_render_backward(int64_t n, const double* xy, const double* conic, const 
 }
 
 /*
- * Error back-projection statistics (Sec. 3.8, Eq. gauss_err_accum) over the
+ * Error back-projection statistics (Sec. 3.8, Eq. 12) over the
  * listed pixels.  With w = T_k alpha_k the compositing weight of splat k at
  * pixel p (as the forward above composites it), stats [N,3] receives
  * (sum_p e(p) w, sum_p w, sum_p D w), where D = sqrt(a dx^2 + 2 b dx dy +

@@ -1,7 +1,7 @@
 """Several views per training iteration, rasterised in one persistent launch.
 
 At iteration t the method trains on a set of K views (Alg. 1 steps 2-10; the
-loss of Eq. 8 is an expectation over them).  ``MultiViewTrainer`` keeps one
+loss of Eq. 11 is an expectation over them).  ``MultiViewTrainer`` keeps one
 ``Trainer`` per view for the per-view state (error and age maps, sampled
 tiles and pixels, projection, tile lists) and shares the Gaussians, their
 gradients and the optimiser moments.  One step:

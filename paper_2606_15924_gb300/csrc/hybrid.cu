@@ -1,4 +1,4 @@
-// Moment-damped Levenberg-Marquardt / Adam hybrid update (Sec. 3.9, Eq. 11;
+// Moment-damped Levenberg-Marquardt / Adam hybrid update (Sec. 3.9, Eq. 14;
 // App. A).  One thread per Gaussian, all state in registers: the 10-parameter
 // geometry block and the 4-parameter appearance block each solve
 // (J^T J + diag(sqrt(v) + eps)) D = -m (Cholesky in mode 2), the 45 higher SH

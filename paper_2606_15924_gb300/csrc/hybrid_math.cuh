@@ -1,5 +1,5 @@
 // The per-parameter arithmetic of the moment-damped LM / Adam hybrid update
-// (Sec. 3.9, Eq. 11; App. A), shared by the update kernels and the fused
+// (Sec. 3.9, Eq. 14; App. A), shared by the update kernels and the fused
 // projection-adjoint-and-update kernel.
 #pragma once
 #include "tgs_common.cuh"

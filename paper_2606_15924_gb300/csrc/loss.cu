@@ -1,4 +1,4 @@
-// Fused sparse supervision (Sec. 3.7, Eq. 8; App. A): Charbonnier L1,
+// Fused sparse supervision (Sec. 3.7, Eqs. 9-11; App. A): Charbonnier L1,
 // tile-level sparse NCC with the gradient-balanced weight, the per-pixel error
 // of Eq. 2 and the error/age map updates of Eqs. 3-4.  One thread block per
 // active tile, one thread per sampled pixel; tile moments are two-pass block

@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(32 * kBwdWarps) k_render_bwd_warp(RasterArgs a
   render_piece_bwd_warp<PPL>(a, j, c, sm[w], T_final, n_last, dL_drgb, grad2d, ck);
 }
 
-// Error back-projection statistics (Sec. 3.8, Eq. gauss_err_accum): one
+// Error back-projection statistics (Sec. 3.8, Eq. 12): one
 // block per active tile, one thread per sampled pixel, walking the tile's
 // list front to back up to the pixel's n_last (the forward's stopping
 // decision) and recomputing alpha and T as the forward does.  For each splat
