@@ -11,10 +11,11 @@
  * Every function restates, in plain double-precision C, what one step of the
  * TurboGS training iteration computes (TurboGS, ICML 2026: Sec. 3.1 Eq. 1 for
  * compositing, Sec. 3.3-3.5 for error/age maps and sampling, Sec. 3.7 and
- * App. A for the loss and its gradients, Sec. 3.9 and App. A for the hybrid
- * solver).  The projection follows the 3D Gaussian Splatting model the paper
- * builds on (Sec. 3.1: centre, covariance from scale and rotation, opacity,
- * SH colour, "standard 3DGS training loop").  No blocking, fusion or reordering
+ * App. A for the loss and its gradients, Sec. 3.8 for the error
+ * back-projection statistics, Sec. 3.9 and App. A for the hybrid solver).  The
+ * projection follows the 3D Gaussian Splatting model the paper builds on
+ * (Sec. 3.1: centre, covariance from scale and rotation, opacity, SH colour;
+ * the paper defers the rest to the standard 3DGS pipeline).  No blocking, fusion or reordering
  * beyond what those definitions state: each sampled pixel is rendered on its own
  * from the full Gaussian set, each tile's loss from its own pixel list.
  *
