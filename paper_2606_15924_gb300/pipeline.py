@@ -3,7 +3,10 @@
 A ``Trainer`` owns the device buffers of one view's sparse step and runs,
 in order (Alg. 1 steps 3-10): select_tiles -> project_gaussians -> bin_tiles ->
 render_sampled -> loss_sparse_ncc (with the error/age map update) ->
-backward_sampled -> hybrid_step.  Sizes are fixed at construction and the
+backward_sampled -> hybrid_step; for the Adam and diagonal-LM modes the
+projection adjoint and the update run as one call (project_backward_update),
+and a sparse step keeps forward checkpoints for the warp-per-piece backward.
+Sizes are fixed at construction and the
 iteration counters live on the device, so one step can be captured once in a
 CUDA graph and replayed.  ``dense=True`` gives the same library's plain path:
 every tile active and every pixel sampled.
