@@ -107,8 +107,8 @@ class TileErrorPredictor:
     view's error map up to date before its next selection: with the network's
     predictions when its recent error (the loss of each batch before it was
     trained on, smoothed) is below ``max_mse``, otherwise with the plain
-    refresh - a dense render of the view (Sec. 3.3), which is also what judges
-    the network (``judge``)."""
+    refresh - a dense render of the view (Sec. 3.3), which is also what scores
+    the network (``assess``)."""
 
     def __init__(self, device="cuda", seed: int = 0, lr: float = 1e-3, max_mse: float = 0.02,
                  min_batches: int = 50, residual: bool = False, replay: int = 2048):
@@ -208,7 +208,7 @@ class TileErrorPredictor:
         self.refreshes["plain"] += 1
         return "plain"
 
-    def judge(self, tr, it: int, view_cos: float = 1.0) -> dict:
+    def assess(self, tr, it: int, view_cos: float = 1.0) -> dict:
         """Scores the predictions for a view against a dense evaluation (the
         plain refresh) without changing the view's state: mean squared error
         of log(1 + tile error), and the same for the view's current error map."""

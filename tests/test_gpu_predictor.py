@@ -1,6 +1,6 @@
 """Tile-error predictor on the GPU: the tile memory, feature and refresh
 kernels against the oracle, and what the online-trained network gains over
-the stale error maps of the plain method (judged by dense evaluations)."""
+the stale error maps of the plain method (scored by dense evaluations)."""
 import math
 
 import numpy as np
@@ -98,8 +98,8 @@ def test_online_predictor_beats_stale_error_maps(B):
     targets rendered from the truth); each step trains one randomly drawn view
     on 10% of its tiles with the plain sampler while the network learns from
     the step's measured tile errors, so most tiles of most views are long
-    unobserved when they are judged - the regime of a large view set.  A dense
-    evaluation of every third view (the plain refresh) then judges the
+    unobserved when they are scored - the regime of a large view set.  A dense
+    evaluation of every third view (the plain refresh) then scores the
     per-tile estimates.  The network's estimates must be clearly closer to the
     truth than the stale error maps the plain method would select from, pick
     tiles holding about as much of the error, and cost a fraction of the
@@ -141,7 +141,7 @@ def test_online_predictor_beats_stale_error_maps(B):
     assert pred.batches == steps and pred.recent_mse is not None
     mse_p, mse_s, mass_p, mass_s, mass_best = [], [], [], [], []
     for v, tr in list(enumerate(trs))[::3]:
-        j = pred.judge(tr, it=steps + 1, view_cos=float(np.dot(_view_dir(cams[v]), prev)))
+        j = pred.assess(tr, it=steps + 1, view_cos=float(np.dot(_view_dir(cams[v]), prev)))
         mse_p.append(j["mse_pred"])
         mse_s.append(j["mse_stale"])
         truth = torch.expm1(j["truth"])
