@@ -188,6 +188,61 @@ tgs_status tgs_select_tiles(const uint16_t* err_map, const uint16_t* age_map, in
  *     threads without ordering) race on it: order them on one stream.
  * Arguments and outputs are those of tgs_select_tiles without the workspace.
  */
+
+/*
+ * view_error_sums - the per-view error totals behind the anchor choice of
+ * geometry-aware view sampling (Sec. 3.4, Eq. 5: the mean of E_v over the
+ * image domain, which is this sum divided by W H).
+ *
+ *   err_maps   device fp16 error maps (bit patterns), view v at
+ *              err_maps + v * view_stride, each [H,W] row-major; negative,
+ *              NaN and infinite values count as 0 (as in select_tiles)
+ *   sums [V]   device out: sum over the view's pixels of E * 2^24, exact in
+ *              integers (every fp16 value is an integer multiple of 2^-24)
+ * Requires 1 <= n_views, width, height; W H <= 2^23 (so a sum stays below
+ * 2^63); view_stride >= W H.  The 16-byte path is taken when err_maps and
+ * view_stride * 2 are multiples of 16 and W H of 8.  sums is overwritten.
+ * Results are independent of the launch order (integer addition).
+ */
+#define TGS_VIEW_MAX_PIXELS (1 << 23)
+tgs_status tgs_view_error_sums(const uint16_t* err_maps, int32_t n_views, int64_t view_stride, int32_t width,
+                               int32_t height, uint64_t* sums, tgs_stream stream);
+
+/*
+ * sample_views - geometry-aware view sampling (Sec. 3.4, Eqs. 5-6; Alg. 1
+ * step 2): K views for one iteration, drawn without replacement from a view
+ * stack.
+ *   1. If fewer than K views are on the stack, every view is put back on it
+ *      (the refill; the draw below is by weight, so the reshuffle the paper
+ *      pairs with it has no effect and is not a separate step).
+ *   2. The anchor v* is the stack view with the largest error sum (Eq. 5;
+ *      equal sums go to the lower index).
+ *   3. The other K - 1 are drawn from the remaining stack views, one after
+ *      another, each with probability proportional to
+ *        pi(u) = exp(-lambda_d |c_u - c_v*| - lambda_theta (1 - <d_u, d_v*>))
+ *      (Eq. 6), c_u the camera centre -R^T t and d_u its unit forward axis
+ *      (the third row of R, normalised) from cams[u].viewmat.  The draws are
+ *      the K - 1 smallest Efraimidis-Spirakis keys
+ *        log2(-log2 U_u) + log2(e) (lambda_d |c_u - c_v*| + lambda_theta (1 - <d_u, d_v*>))
+ *      with -log2 U_u from the SplitMix64 hash of (seed, iter, stream 5,
+ *      item u) in 32-bit fixed point and its log2 by the same digit
+ *      recurrence; everything else in IEEE double without fused operations,
+ *      so a run gives the same views on every machine.  Equal keys go to the
+ *      lower index.
+ *   4. The K views leave the stack.
+ *
+ *   err_sums [V]  device, from tgs_view_error_sums (or any non-negative totals)
+ *   cams [V]      device camera array
+ *   stack [V]     device uint8 in/out: 1 while the view is on the stack
+ *                 (start with all ones)
+ *   views [K]     device out: views[0] = v*, then the K - 1 draws ascending
+ * Requires 1 <= K <= V <= TGS_VIEW_SAMPLE_MAX_VIEWS and finite, non-negative
+ * lambda_d, lambda_theta.
+ */
+#define TGS_VIEW_SAMPLE_MAX_VIEWS 8192
+tgs_status tgs_sample_views(const uint64_t* err_sums, const tgs_camera* cams, int32_t n_views, int32_t k,
+                            double lambda_d, double lambda_theta, uint64_t seed, uint64_t iter, uint8_t* stack,
+                            int32_t* views, tgs_stream stream);
 #define TGS_SELECT_NOALLOC_MAX_TILES 16384
 #define TGS_SELECT_NOALLOC_SCRATCH_BYTES (768u * 1024u)
 #define TGS_SELECT_NOALLOC_MAX_DEVICES 64

@@ -111,6 +111,14 @@ def _declare(L):
     L.orc_tile_features.restype = None
     L.orc_tile_refresh.argtypes = [_p, _p, _p, _i32, _i32]
     L.orc_tile_refresh.restype = None
+    L.orc_view_error_sums.argtypes = [_p, _i32, _i64, _i32, _i32, _p]
+    L.orc_view_error_sums.restype = None
+    L.orc_log2_q32.argtypes = [_u64]
+    L.orc_log2_q32.restype = _u64
+    L.orc_view_pose.argtypes = [_p, _p, _p]
+    L.orc_view_pose.restype = None
+    L.orc_sample_views.argtypes = [_p, _p, _i32, _i32, _d, _d, _u64, _u64, _p, _p]
+    L.orc_sample_views.restype = None
 
 
 def _c(a, dtype):
@@ -447,3 +455,62 @@ def tile_refresh(pred, err_f16_bits, width, height, base=None):
     e = np.array(err_f16_bits, dtype=np.uint16, copy=True, order="C")
     L.orc_tile_refresh(_ptr(_c(pred, np.float64)), _ptr(_c(base, np.float64)), _ptr(e), int(width), int(height))
     return e
+
+
+# ----------------------------------------------------------------------------
+# view sampling and its schedule (Sec. 3.4; App. A)
+# ----------------------------------------------------------------------------
+
+def view_error_sums(maps_f16_bits) -> np.ndarray:
+    """Per view, the exact sum of E * 2^24 over its pixels (Eq. 5 times
+    W H 2^24).  maps [V,H,W] fp16 bit patterns."""
+    m = _c(maps_f16_bits, np.uint16)
+    V, H, W = m.shape
+    out = np.zeros(V, np.uint64)
+    lib().orc_view_error_sums(_ptr(m), V, H * W, W, H, _ptr(out))
+    return out
+
+
+def log2_q32(x: int) -> int:
+    return int(lib().orc_log2_q32(int(x)))
+
+
+def view_pose(viewmat):
+    """(centre, unit forward axis) of a row-major world-to-camera matrix."""
+    v = _c(np.asarray(viewmat).reshape(16), np.float32)
+    c, d = np.zeros(3), np.zeros(3)
+    lib().orc_view_pose(_ptr(v), _ptr(c), _ptr(d))
+    return c, d
+
+
+def sample_views(sums, viewmats, k, lambda_d, lambda_theta, seed=0, it=0, stack=None):
+    """One geometry-aware draw (Eqs. 5-6).  Returns (views [k]: anchor first,
+    then the draws ascending; the updated stack [V] uint8)."""
+    s = _c(sums, np.uint64)
+    vm = _c(np.asarray(viewmats).reshape(-1, 16), np.float32)
+    V = s.shape[0]
+    st = np.ones(V, np.uint8) if stack is None else np.array(stack, dtype=np.uint8, copy=True, order="C")
+    out = np.zeros(k, np.int32)
+    lib().orc_sample_views(_ptr(s), _ptr(vm), V, int(k), float(lambda_d), float(lambda_theta), int(seed), int(it),
+                           _ptr(st), _ptr(out))
+    return out, st
+
+
+def sampling_schedule(t, E_t, E_init, K_max=10, K_min=3, alpha=3.0, tau_until=3500, lam=1.0, eps=1e-8):
+    """(K_t, r_tile) of the adaptive schedule (App. A, Eqs. 15-16).
+
+    r = clip(E_t / (E_init + eps), 0, 1), phi = sin(pi/2 sqrt(r)),
+    rho = 1 - clip(t / tau_until, 0, 1) (the appendix's definition, 1 at the
+    start and 0 from tau_until on), g = 1 - rho phi;
+    r_tile = r_min + (r_max - r_min) g with r_min = lam / K_max and
+    r_max = lam / K_min; K_t = round(K_min + (K_max - K_min) exp(-alpha g)),
+    rounding halves up."""
+    import math
+    r = min(max(E_t / (E_init + eps), 0.0), 1.0)
+    phi = math.sin(0.5 * math.pi * math.sqrt(r))
+    rho = 1.0 - min(max(t / tau_until, 0.0), 1.0)
+    g = 1.0 - rho * phi
+    r_min, r_max = lam / K_max, lam / K_min
+    r_tile = r_min + (r_max - r_min) * g
+    K = int(math.floor(K_min + (K_max - K_min) * math.exp(-alpha * g) + 0.5))
+    return K, r_tile

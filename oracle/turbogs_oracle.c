@@ -10,7 +10,8 @@
  *
  * Every function restates, in plain double-precision C, what one step of the
  * TurboGS training iteration computes (TurboGS, ICML 2026: Sec. 3.1 Eq. 1 for
- * compositing, Sec. 3.3-3.5 for error/age maps and sampling, Sec. 3.7 and
+ * compositing, Sec. 3.3-3.5 for error/age maps, view and pixel sampling
+ * (view sampling: Sec. 3.4 Eqs. 5-6), Sec. 3.7 and
  * App. A for the loss and its gradients, Sec. 3.8 for the error
  * back-projection statistics, Sec. 3.9 and App. A for the hybrid solver).  The
  * projection follows the 3D Gaussian Splatting model the paper builds on
@@ -28,7 +29,9 @@
  * scipy's spherical harmonics; closed-form image of one isotropic Gaussian;
  * transmittance identity; pixel independence; brute-force tile overlap;
  * sampling counts, brute-force TopK, inclusion probabilities of the weighted
- * draw against exact enumeration of sequential draws; NCC invariances and
+ * draw against exact enumeration of sequential draws (tiles, pixels and
+ * views); exact view error sums against fp16 values summed in numpy; camera
+ * pose against the look-at construction; NCC invariances and
  * finite differences of the loss; finite differences of the whole
  * project -> render -> loss chain against the analytic backward; Cholesky
  * against LU, Sherman-Morrison and J = 0 for the hybrid step; fp16 rounding
@@ -1389,4 +1392,130 @@ void orc_tile_refresh(const double* pred, const double* base, uint16_t* err, int
         err[k] = orc_double_to_half(mean > 0.0 ? e * (want / mean) : want);
       }
   }
+}
+
+/* ------------------------------------------------------------------------ */
+/* geometry-aware view sampling (Sec. 3.4, Eqs. 5-6; Alg. 1 step 2)         */
+/* ------------------------------------------------------------------------ */
+
+/* Eq. 5 before the division: the sum of E_v over the view's W H pixels, as
+ * the exact integer sum of E * 2^24 (the weight of the tile draw, so
+ * negative, NaN and infinite values count as 0).  The mean view error is
+ * sums[v] / 2^24 / (W H). */
+void orc_view_error_sums(const uint16_t* maps, int n_views, int64_t view_stride, int width, int height,
+                         uint64_t* sums) {
+  int64_t n = (int64_t)width * height;
+  for (int v = 0; v < n_views; ++v) {
+    uint64_t s = 0;
+    for (int64_t p = 0; p < n; ++p) s += orc_err_weight(maps[(int64_t)v * view_stride + p]);
+    sums[v] = s;
+  }
+}
+
+/* log2(x) * 2^32 for x >= 1, by the digit recurrence of orc_neglog2_q32:
+ * the integer part is the position of the leading bit, each squaring of the
+ * mantissa normalised to [1, 2) gives one fractional bit. */
+uint64_t orc_log2_q32(uint64_t x) {
+  int ip = 63;
+  while (!(x >> ip)) ip--;
+  uint64_t m = x << (63 - ip);
+  uint64_t frac = 0;
+  for (int i = 0; i < 32; ++i) {
+    unsigned __int128 sq = (unsigned __int128)m * m;
+    uint64_t hi = (uint64_t)(sq >> 64);
+    frac <<= 1;
+    if (hi >> 63) { frac |= 1; m = hi; }
+    else m = hi << 1;
+  }
+  return ((uint64_t)ip << 32) | frac;
+}
+
+/* Camera centre c = -R^T t and unit viewing direction (the camera's forward
+ * axis, the third row of R) of a row-major world-to-camera matrix whose
+ * camera looks along +z. */
+void orc_view_pose(const float* viewmat, double* c, double* d) {
+  const float* M = viewmat;
+  for (int j = 0; j < 3; ++j) {
+    double s = (double)M[j] * (double)M[3];
+    s = s + (double)M[4 + j] * (double)M[7];
+    s = s + (double)M[8 + j] * (double)M[11];
+    c[j] = -s;
+  }
+  double f0 = M[8], f1 = M[9], f2 = M[10];
+  double n = sqrt((f0 * f0 + f1 * f1) + f2 * f2);
+  d[0] = f0 / n;
+  d[1] = f1 / n;
+  d[2] = f2 / n;
+}
+
+typedef struct {
+  int idx;
+  double key;
+} vkey_t;
+
+static int cmp_vkey(const void* a, const void* b) {
+  const vkey_t* x = (const vkey_t*)a;
+  const vkey_t* y = (const vkey_t*)b;
+  if (x->key != y->key) return x->key < y->key ? -1 : 1;
+  return x->idx - y->idx;
+}
+
+#define ORC_STREAM_VIEW 5
+
+/*
+ * K views for iteration `iter`, drawn from the view stack (stack[v] = 1 while
+ * view v is on it; updated in place):
+ *   - when fewer than K views are on the stack, all views go back on it;
+ *   - the anchor v* is the stack view with the largest mean error (Eq. 5;
+ *     equal means: the lower index);
+ *   - the remaining K - 1 are drawn without replacement from the other stack
+ *     views, each draw with probability proportional to
+ *     pi(u) = exp(-lambda_d |c_u - c_v*| - lambda_theta (1 - <d_u, d_v*>))
+ *     (Eq. 6).  Successive weighted draws are realised as the Efraimidis-
+ *     Spirakis order: with the exponential clock L_u = -log2 U_u of the
+ *     view's hash (stream 5), the draws are the K - 1 smallest L_u / pi(u),
+ *     compared through their base-2 logarithms
+ *       log2 L_u + log2(e) (lambda_d |c_u - c_v*| + lambda_theta (1 - <d_u, d_v*>)),
+ *     log2 L_u from the digit recurrence above (equal keys: the lower index);
+ *   - the K views leave the stack.
+ * views [K]: the anchor, then the draws in ascending view order.
+ */
+void orc_sample_views(const uint64_t* sums, const float* viewmats, int n_views, int k, double lambda_d,
+                      double lambda_theta, uint64_t seed, uint64_t iter, uint8_t* stack, int32_t* views) {
+  int on_stack = 0;
+  for (int v = 0; v < n_views; ++v) on_stack += stack[v] != 0;
+  if (on_stack < k)
+    for (int v = 0; v < n_views; ++v) stack[v] = 1;
+  int anchor = -1;
+  for (int v = 0; v < n_views; ++v)
+    if (stack[v] && (anchor < 0 || sums[v] > sums[anchor])) anchor = v;
+  double ca[3], da[3];
+  orc_view_pose(viewmats + 16 * (size_t)anchor, ca, da);
+  vkey_t* cand = (vkey_t*)malloc(sizeof(vkey_t) * (size_t)n_views);
+  int m = 0;
+  for (int u = 0; u < n_views; ++u) {
+    if (!stack[u] || u == anchor) continue;
+    double c[3], d[3];
+    orc_view_pose(viewmats + 16 * (size_t)u, c, d);
+    double dx = c[0] - ca[0], dy = c[1] - ca[1], dz = c[2] - ca[2];
+    double dist = sqrt((dx * dx + dy * dy) + dz * dz);
+    double cosv = (d[0] * da[0] + d[1] * da[1]) + d[2] * da[2];
+    double s = lambda_d * dist + lambda_theta * (1.0 - cosv);
+    uint64_t L = orc_neglog2_q32(orc_hash(seed, iter, 0, ORC_STREAM_VIEW, (uint32_t)u, 0));
+    double lg = (double)(int64_t)(orc_log2_q32(L) - (32ULL << 32)) * 2.3283064365386963e-10; /* 2^-32 */
+    cand[m].idx = u;
+    cand[m].key = (lg + s * 1.4426950408889634) + 0.0; /* log2(e) */
+    m++;
+  }
+  qsort(cand, (size_t)m, sizeof(vkey_t), cmp_vkey);
+  uint8_t* drawn = (uint8_t*)calloc((size_t)n_views, 1);
+  for (int i = 0; i < k - 1; ++i) drawn[cand[i].idx] = 1;
+  views[0] = anchor;
+  int o = 1;
+  for (int u = 0; u < n_views; ++u)
+    if (drawn[u]) views[o++] = u;
+  for (int u = 0; u < n_views; ++u)
+    if (drawn[u] || u == anchor) stack[u] = 0;
+  free(drawn);
+  free(cand);
 }

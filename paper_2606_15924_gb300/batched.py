@@ -18,6 +18,13 @@ gradients and the optimiser moments.  One step:
 Everything is sized at construction and the iteration counters live on the
 device, so the step is captured once in a CUDA graph.  ``autotune_grid``
 picks the persistent grid sizes by timing graph replays.
+
+A trainer may also hold a pool of more views than it trains at once
+(``max_active``): ``set_views`` then picks the views (and pixels per tile) of
+the next steps, as the adaptive schedule and geometry-aware view sampling of
+Sec. 3.4 do every iteration (``ScheduledTrainer``).  Every pool view keeps
+its own maps and buffers resident; the active set's batch descriptors are
+rebuilt on the host, and such steps run without a captured graph.
 """
 from __future__ import annotations
 
@@ -35,25 +42,31 @@ class MultiViewTrainer:
     def __init__(self, params: dict, cams: list, targets: list, tile_fractions: list,
                  pixel_rate: float = 1.0 / 3.0, cfg: Config | None = None, seed: int = 0, bg=(0.0, 0.0, 0.0),
                  sh_degree: int = 3, view_ids: list | None = None, grid: tuple | None = None,
-                 view_rows: bool | None = None, persistent: bool = True, checkpoints: bool | None = None):
-        if not (1 <= len(cams) <= 16) or len(cams) != len(targets) or len(cams) != len(tile_fractions):
-            raise ValueError("1 to 16 views, one target and one tile fraction each")
+                 view_rows: bool | None = None, persistent: bool = True, checkpoints: bool | None = None,
+                 max_active: int | None = None):
+        if not cams or len(cams) != len(targets) or len(cams) != len(tile_fractions):
+            raise ValueError("one target and one tile fraction per view")
+        # views trained together (one batch of the persistent launches)
+        self.max_active = min(len(cams), 16) if max_active is None else int(max_active)
+        if not 1 <= self.max_active <= 16 or (max_active is None and len(cams) > 16):
+            raise ValueError("1 to 16 views per step (a larger pool needs max_active)")
         self.cfg = cfg or Config()
         self.params = params
         self.n = int(params["means"].shape[0])
-        self.K = len(cams)
         self.sh_degree, self.bg = sh_degree, tuple(bg)
         dev = params["means"].device
-        ids = view_ids if view_ids is not None else list(range(self.K))
-        self.views = [Trainer(params, cams[k], targets[k], tile_fraction=tile_fractions[k], pixel_rate=pixel_rate,
-                              cfg=self.cfg, seed=seed, bg=bg, sh_degree=sh_degree, view=ids[k], train=False)
-                      for k in range(self.K)]
+        ids = view_ids if view_ids is not None else list(range(len(cams)))
+        self.pool = [Trainer(params, cams[k], targets[k], tile_fraction=tile_fractions[k], pixel_rate=pixel_rate,
+                             cfg=self.cfg, seed=seed, bg=bg, sh_degree=sh_degree, view=ids[k], train=False)
+                     for k in range(len(cams))]
+        self.views = self.pool[:self.max_active]
+        self.K = len(self.views)
         # one device iteration counter for all views (the hash of each view's
         # draw also takes its view id)
         self.it_dev = torch.zeros(1, dtype=torch.int64, device=dev)
         self.step_dev = torch.ones(1, dtype=torch.int32, device=dev)
         w = 1.0 / self.K
-        for v in self.views:
+        for v in self.pool:
             v.it_dev = self.it_dev
             v.loss_params = (v.loss_params[0], v.loss_params[1], v.loss_params[2], w)
             v.grad2d = torch.zeros(self.n, 12, device=dev)
@@ -68,13 +81,13 @@ class MultiViewTrainer:
                         beta1=o.beta1, beta2=o.beta2, eps_adam=o.eps_adam, eps_lm=o.eps_lm, mode=o.mode)
         # per-view Jacobian rows feed only the full-matrix LM mode
         self.use_rows = (self.opt["mode"] == 2) if view_rows is None else bool(view_rows)
-        self.rows = torch.zeros(self.K, self.n, 14, device=dev) if self.use_rows else None
+        self.rows = torch.zeros(self.max_active, self.n, 14, device=dev) if self.use_rows else None
         # persistent=False: one launch per view with one block per active
         # tile (the same kernels without the shared queue) and one
         # accumulating projection adjoint per view, for comparison
         self.persistent = bool(persistent)
-        self.counters = torch.zeros(2 + 2 * self.K, dtype=torch.int32, device=dev)
-        self.n_pix_max = max(v.n_pix for v in self.views)
+        self.counters = torch.zeros(2 + 2 * self.max_active, dtype=torch.int32, device=dev)
+        self.n_pix_max = max(v.n_pix for v in self.pool)
         # checkpoints for the split backward: one slot every CKPT_EVERY list
         # positions, up to CKPT_POSITIONS
         if checkpoints is None:
@@ -86,7 +99,7 @@ class MultiViewTrainer:
             # n_pix x 64 float4 per active tile.
             checkpoints = self.persistent
         self.ck_slots = Trainer.CKPT_POSITIONS // Trainer.CKPT_EVERY if checkpoints else 0
-        for v in self.views:
+        for v in self.pool:
             if self.ck_slots:
                 v.ck_data = torch.empty(B.checkpoint_bytes(v.n_select, v.n_pix, self.ck_slots) // 4, device=dev)
                 v.ck_last = torch.zeros(v.n_select, dtype=torch.int32, device=dev)
@@ -118,6 +131,27 @@ class MultiViewTrainer:
         self.adj = B.MultiAdjoint([v.ccam for v in self.views], [v.proj["radius"] for v in self.views],
                                   [v.grad2d for v in self.views],
                                   [self.rows[k] for k in range(self.K)] if self.use_rows else None)
+
+    def set_views(self, ids, n_pix: int | None = None):
+        """Trains pool views ``ids`` (at most max_active, distinct) from the
+        next step on, each with loss weight 1/len(ids) and, when given, n_pix
+        sampled pixels per tile (at most the pixels the pool was sized for).
+        Steps after this run eagerly (a captured graph holds the old set)."""
+        ids = [int(i) for i in ids]
+        if not 1 <= len(ids) <= self.max_active or len(set(ids)) != len(ids) or \
+                not all(0 <= i < len(self.pool) for i in ids):
+            raise ValueError("1 to max_active distinct pool views")
+        views = [self.pool[i] for i in ids]
+        if n_pix is not None and not all(1 <= n_pix <= v.P_max // v.n_select for v in views):
+            raise ValueError("n_pix above the pool's allocation")
+        self.views, self.K = views, len(views)
+        w = 1.0 / self.K
+        for v in views:
+            v.loss_params = (v.loss_params[0], v.loss_params[1], v.loss_params[2], w)
+            if n_pix is not None:
+                v.n_pix = int(n_pix)
+        self._build_batches()
+        self.graph = None
 
     def _project_bwd(self):
         """Projection adjoint of all views into the shared gradients: one fused

@@ -179,6 +179,10 @@ _lib.tgs_tile_features.restype = _i32
 _lib.tgs_tile_features.argtypes = [_p, _p, _p, _p, _i32, _P(Camera), C.c_float, _u64, _p, _p, _p]
 _lib.tgs_tile_refresh.restype = _i32
 _lib.tgs_tile_refresh.argtypes = [_p, _p, _p, _i32, _i32, _p]
+_lib.tgs_view_error_sums.restype = _i32
+_lib.tgs_view_error_sums.argtypes = [_p, _i32, _i64, _i32, _i32, _p, _p]
+_lib.tgs_sample_views.restype = _i32
+_lib.tgs_sample_views.argtypes = [_p, _p, _i32, _i32, C.c_double, C.c_double, _u64, _u64, _p, _p, _p]
 _lib.tgs_mlp_adam.restype = _i32
 _lib.tgs_mlp_adam.argtypes = [_p, _p, _p, _p, _i32, C.c_float, C.c_float, C.c_float, C.c_float, _p, _p, _p, _p]
 
@@ -194,7 +198,8 @@ EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_devi
             "tgs_render_backward_batched", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step",
             "tgs_mlp_param_count", "tgs_mlp_forward", "tgs_mlp_forward_tc", "tgs_mlp_tc_wait_drill", "tgs_mlp_backward_workspace_size",
             "tgs_mlp_backward",
-            "tgs_mlp_adam", "tgs_tile_observe", "tgs_tile_features", "tgs_tile_refresh"]
+            "tgs_mlp_adam", "tgs_tile_observe", "tgs_tile_features", "tgs_tile_refresh",
+            "tgs_view_error_sums", "tgs_sample_views"]
 
 
 def _check(fn, status):
@@ -242,6 +247,13 @@ def camera(cam: dict) -> Camera:
     c.width, c.height = int(cam["width"]), int(cam["height"])
     c.znear = float(cam.get("znear", 0.2))
     return c
+
+
+def camera_array(cams, device="cuda") -> torch.Tensor:
+    """Device array of tgs_camera structs (a uint8 tensor of len(cams) *
+    sizeof(tgs_camera) bytes), for the calls that take one camera per view."""
+    arr = (Camera * len(cams))(*[c if isinstance(c, Camera) else camera(c) for c in cams])
+    return torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).to(device)
 
 
 def gaussians(g: dict, sh_degree: int = 3) -> Gaussians:
@@ -576,3 +588,27 @@ def tile_features(mem, mem_iter, cam, x, rows=None, n_rows=None, n_rows_max=None
 def tile_refresh(pred, err_map, width, height, base=None, stream=None):
     _check("tgs_tile_refresh", _lib.tgs_tile_refresh(_ptr(pred), _ptr(base), _ptr(err_map), int(width), int(height),
                                                      _stream(stream)))
+
+
+def view_error_sums(err_maps, sums, stream=None):
+    """err_maps [V,H,W] int16 (fp16 bit patterns, contiguous); sums [V] int64
+    receives the exact totals of E * 2^24 (Eq. 5 times W H 2^24)."""
+    V, H, W = (int(x) for x in err_maps.shape)
+    if sums.dtype != torch.int64 or sums.numel() < V:
+        raise ValueError("sums: int64 [V]")
+    _check("tgs_view_error_sums", _lib.tgs_view_error_sums(_ptr(err_maps), V, H * W, W, H, _ptr(sums),
+                                                           _stream(stream)))
+
+
+def sample_views(err_sums, cams, k, lambda_d, lambda_theta, seed, it, stack, views, stream=None):
+    """Geometry-aware draw of k views (Eqs. 5-6): err_sums [V] int64 from
+    view_error_sums, cams from camera_array, stack [V] uint8 (in/out), views
+    [k] int32 (anchor first, then the draws ascending)."""
+    V = int(err_sums.numel())
+    if stack.dtype != torch.uint8 or stack.numel() != V or views.dtype != torch.int32 or views.numel() < k:
+        raise ValueError("stack: uint8 [V]; views: int32 [k]")
+    if cams.dtype != torch.uint8 or cams.numel() != V * C.sizeof(Camera):
+        raise ValueError("cams: camera_array of V cameras")
+    _check("tgs_sample_views", _lib.tgs_sample_views(
+        _ptr(err_sums), _ptr(cams), V, int(k), float(lambda_d), float(lambda_theta), int(seed) & (2**64 - 1),
+        int(it) & (2**64 - 1), _ptr(stack), _ptr(views), _stream(stream)))

@@ -64,6 +64,9 @@ class ScheduleConfig:
     K_min: int = 3
     alpha: float = 3.0
     lambda_base: float = 0.8
+    # tile pixel sampling scale lambda, in (0, 1] (Table 6 gives the range);
+    # 1 makes the late rate lambda / K_min = 1/3, the rate of the sparse step
+    lam: float = 1.0
 
 
 @dataclass
