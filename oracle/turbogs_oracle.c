@@ -28,6 +28,7 @@
  * Pins (tests/test_oracle_*.py, run with -m "not gpu"): SH basis against
  * scipy's spherical harmonics; closed-form image of one isotropic Gaussian;
  * transmittance identity; pixel independence; brute-force tile overlap;
+ * rotated anisotropic and off-centre projections, SH view direction;
  * sampling counts, brute-force TopK, inclusion probabilities of the weighted
  * draw against exact enumeration of sequential draws (tiles, pixels and
  * views); exact view error sums against fp16 values summed in numpy; camera
