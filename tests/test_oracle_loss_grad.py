@@ -150,6 +150,18 @@ def test_lambda_reading(orc):
     del n
 
 
+def test_lambda_is_clipped_at_one(orc):
+    """A prediction that is the target plus a constant has NCC = 1 and a
+    vanishing NCC gradient, so the gradient ratio is huge: lambda = 1."""
+    W = H = 16
+    rng = np.random.default_rng(6)
+    target = rng.uniform(0, 0.5, (H, W, 3))
+    sel = _tile_sel(W, H, [0], 60, rng)
+    y = _gather(target, sel, W)
+    o = orc.loss(W, H, sel, y + 0.4, target)
+    assert o["lam"][0] == 1.0
+
+
 def test_ema_and_age_recurrences(orc):
     W, H = 48, 32
     rng = np.random.default_rng(6)

@@ -18,8 +18,9 @@ def _one_gaussian(sigma, opacity, dc, d=4.0, W=64, H=48):
     return g, cam
 
 
-@pytest.mark.parametrize("sigma,opacity", [(0.05, 0.7), (0.2, 0.3), (0.01, 0.95)])
+@pytest.mark.parametrize("sigma,opacity", [(0.05, 0.7), (0.2, 0.3), (0.01, 0.95), (0.4, 0.999)])
 def test_closed_form_isotropic_gaussian(orc, sigma, opacity):
+    """(0.4, 0.999): alpha near the centre exceeds 0.99 and takes the cap."""
     dc = np.array([0.3, -0.2, 1.1])
     d = 4.0
     g, cam = _one_gaussian(sigma, opacity, dc, d)
@@ -48,6 +49,8 @@ def test_closed_form_isotropic_gaussian(orc, sigma, opacity):
     alpha[~inside] = 0
     np.testing.assert_allclose(out["rgb"], alpha[:, None] * col[None, :], atol=1e-12)
     np.testing.assert_allclose(out["T"], 1 - alpha, atol=1e-12)
+    if opacity * math.exp(-0.25 / s2) > 0.99:
+        assert out["T"].min() == pytest.approx(0.01, abs=1e-15)
 
 
 def test_transmittance_identity(orc):
@@ -137,9 +140,11 @@ def test_bin_tiles_brute_force(orc):
 def test_projection_culls(orc):
     g = scenes.gaussians(50, seed=11)
     g["means"][:10, 2] = -4.1     # behind the camera at z = -4 looking at +z
+    g["means"][10:12] = [[0.0, 0.0, -3.85], [0.01, 0.0, -3.75]]   # depth 0.15 < znear = 0.2 < 0.25
     cam = scenes.look_at((0, 0, -4), width=64, height=64)
     pr = orc.project(g, cam)
-    assert np.all(pr["radius"][:10] == 0)
+    assert np.all(pr["radius"][:11] == 0)
+    assert pr["radius"][11] > 0
     # an active-tile mask culls splats that touch no active tile
     rank = np.full(16, -1, np.int32)
     pr2 = orc.project(g, cam, tile_rank=rank)
@@ -195,3 +200,82 @@ def test_error_stats_one_gaussian_closed_form(orc, sigma, opacity):
     assert st[0, 1] == pytest.approx(a[on].sum(), rel=1e-10)
     assert st[0, 0] == pytest.approx((e * a)[on].sum(), rel=1e-10)
     assert st[0, 2] == pytest.approx((np.sqrt(r2 / s2) * a)[on].sum(), rel=1e-10)
+
+
+@pytest.mark.parametrize("opacity,blended", [(0.6, 10), (0.3, 25), (0.85, 4)])
+def test_stop_before_transmittance_falls_below_1e_4(orc, opacity, blended):
+    """Co-centred splats along the optical axis, seen at the pixel under
+    their common centre (odd image size: the centre is a pixel centre, so
+    alpha = opacity exactly): the walk blends k splats while
+    (1 - opacity)^k >= 1e-4 and stops before the one that would go below."""
+    W, H, n = 65, 49, 40
+    k = 0
+    while (1.0 - opacity) ** (k + 1) >= 1e-4:
+        k += 1
+    assert k == blended
+    g = dict(means=np.stack([np.zeros(n), np.zeros(n), np.linspace(-1.0, 2.0, n)], 1),
+             log_scales=np.full((n, 3), math.log(0.05)), quats=np.tile([1.0, 0, 0, 0], (n, 1)),
+             opacity_logits=np.full(n, math.log(opacity / (1 - opacity))), sh=np.zeros((n, 16, 3)))
+    g["sh"][:, 0, :] = 0.4
+    cam = scenes.look_at((0.0, 0.0, -4.0), width=W, height=H, fov_x_deg=50.0)
+    pr = orc.project(g, cam)
+    out = orc.render_pixels(pr, W, H, np.array([[32, 24]], np.int32))
+    assert out["n_contrib"][0] == blended
+    assert out["T"][0] == pytest.approx((1.0 - opacity) ** blended, rel=1e-12)
+    col = 0.4 * 0.5 / math.sqrt(math.pi) + 0.5
+    assert out["rgb"][0, 0] == pytest.approx(col * (1.0 - (1.0 - opacity) ** blended), rel=1e-12)
+
+
+@pytest.mark.parametrize("theta", [0.5, -1.2])
+def test_error_stats_distance_of_a_rotated_gaussian(orc, theta):
+    """Sec. 3.8's distance D = sqrt(d^T Sigma2^-1 d) with its cross term, for a
+    rotated anisotropic Gaussian alone (T = 1, w = alpha): Sigma2 from the
+    closed form (f / z)^2 Rz D Rz^T + 0.3 I at the image centre; pixels within
+    the splat's radius square (inside its tile rectangle)."""
+    d, W, H = 4.0, 64, 48
+    sc = np.array([0.12, 0.04, 0.05])
+    g = dict(means=np.zeros((1, 3)), log_scales=np.log(sc)[None], quats=np.array([[math.cos(theta / 2), 0, 0,
+                                                                                     math.sin(theta / 2)]]),
+             opacity_logits=np.array([math.log(0.8 / 0.2)]), sh=np.zeros((1, 16, 3)))
+    cam = scenes.look_at((0.0, 0.0, -d), width=W, height=H, fov_x_deg=50.0)
+    f = cam["fx"]
+    c, s_ = math.cos(theta), math.sin(theta)
+    Rz = np.array([[c, -s_, 0.0], [s_, c, 0.0], [0.0, 0.0, 1.0]])
+    S2 = (f / d) ** 2 * (Rz @ np.diag(sc ** 2) @ Rz.T)[:2, :2] + 0.3 * np.eye(2)
+    Q = np.linalg.inv(S2)
+    pr = orc.project(g, cam)
+    r = int(pr["radius"][0])
+    ys, xs = np.mgrid[0:H, 0:W]
+    pix = np.stack([xs.ravel(), ys.ravel()], 1).astype(np.int32)
+    dv = pix + 0.5 - np.array([W / 2, H / 2])
+    pix, dv = pix[np.abs(dv).max(1) < r], dv[np.abs(dv).max(1) < r]
+    e = np.linspace(0.2, 1.0, len(pix))
+    st = orc.error_stats(pr, W, H, pix, e)
+    q = np.einsum("pi,ij,pj->p", dv, Q, dv)
+    a = np.minimum(0.99, 0.8 * np.exp(-0.5 * q))
+    on = a >= 1.0 / 255.0
+    assert on.sum() > 50 and abs(Q[0, 1]) > 1e-3 * Q[0, 0]
+    assert st[0, 1] == pytest.approx(a[on].sum(), rel=1e-9)
+    assert st[0, 2] == pytest.approx((np.sqrt(q) * a)[on].sum(), rel=1e-9)
+
+
+def test_jacobian_clamp_off_screen(orc):
+    """A large isotropic Gaussian beyond the right edge, at x/z = 1.5
+    tan(fov_x / 2) (outside the 1.3 clamp), still reaching into the image:
+    its centre uses the true x/z, its covariance J with x/z clamped to
+    1.3 tan(fov_x / 2): Sigma2 = s^2 J J^T + 0.3 I."""
+    d, W, H, s = 4.0, 64, 48, 0.5
+    cam = scenes.look_at((0.0, 0.0, -d), width=W, height=H, fov_x_deg=50.0)
+    f = cam["fx"]
+    half = 0.5 * W / f
+    x0 = 1.5 * half * d
+    g = dict(means=np.array([[x0, 0.0, 0.0]]), log_scales=np.full((1, 3), math.log(s)),
+             quats=np.array([[1.0, 0, 0, 0]]), opacity_logits=np.array([2.0]), sh=np.zeros((1, 16, 3)))
+    pr = orc.project(g, cam)
+    assert pr["radius"][0] > 0
+    np.testing.assert_allclose(pr["xy"][0], [f * x0 / d + W / 2, H / 2], rtol=1e-12)
+    tx = 1.3 * half
+    J = np.array([[f / d, 0.0, -f * tx / d], [0.0, f / d, 0.0]])
+    S2 = s * s * J @ J.T + 0.3 * np.eye(2)
+    inv = np.linalg.inv(S2)
+    np.testing.assert_allclose(pr["conic"][0], [inv[0, 0], inv[0, 1], inv[1, 1]], rtol=1e-10)

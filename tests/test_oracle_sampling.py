@@ -3,6 +3,7 @@ exact counts, brute-force TopK, the error-proportional draw against exact
 enumeration of successive weighted draws without replacement, uniformity of
 the remainder, and structural properties of the sampled set."""
 import itertools
+import math
 
 import numpy as np
 import pytest
@@ -33,6 +34,27 @@ def test_split_counts_and_extremes(orc):
     assert orc.choose_items(w, age, 99).all()
     for n in range(11):
         assert orc.choose_items(w, age, n, seed=3).sum() == n
+
+
+@pytest.mark.parametrize("hard_pm,stable_pm", [(400, 600), (500, 500), (400, 300)])
+def test_split_rounds_half_up_and_clamps(orc, hard_pm, stable_pm):
+    """N_hard = round(r_hard n), N_stable = round(r_stable n) (halves up),
+    N_stable cut so that N_hard + N_stable <= n.  Items 0..n-1 carry all the
+    weight and items n..2n-1 all the age, so the hard draw can only take the
+    first group and the oldest-first draw the second."""
+    for n in range(1, 13):
+        kh = int(math.floor(hard_pm * n / 1000 + 0.5))
+        ks = min(int(math.floor(stable_pm * n / 1000 + 0.5)), n - kh)
+        w = np.zeros(3 * n, np.uint64)
+        w[:n] = 1000
+        age = np.zeros(3 * n, np.uint32)
+        age[n:2 * n] = 50
+        got = orc.choose_items(w, age, n, hard_pm=hard_pm, stable_pm=stable_pm, seed=n)
+        assert got.sum() == n
+        if kh + ks == n:                               # no uniform remainder to blur the groups
+            assert got[:n].sum() == kh and got[n:2 * n].sum() == ks, (n, kh, ks)
+        else:
+            assert got[:n].sum() >= kh and got[n:2 * n].sum() >= ks
 
 
 def test_topk_age_brute_force(orc):
@@ -151,3 +173,16 @@ def test_hard_pixels_follow_error(orc):
         got.append(e[P[:, 1], P[:, 0]].mean())
     assert abs(np.mean(got) - want) < 0.03 * want
     assert want > 1.5 * e.mean()
+
+
+def test_tile_age_is_the_smallest_pixel_age(orc):
+    """A tile's age is its smallest pixel age (the iterations since any of its
+    pixels was sampled): a tile with one very old pixel among fresh ones is
+    younger than a tile whose pixels are all moderately old."""
+    W, H = 64, 16                                   # tiles 0..3 in one row
+    age = np.full((H, W), 2, np.uint16)
+    age[5, 3] = 900                                 # tile 0: one old pixel, the rest age 2
+    age[:, 16:32] = 40                              # tile 1: every pixel age 40
+    err = np.zeros((H, W), np.uint16)
+    sel = orc.select(err, age, W, H, n_select=1, n_pix=4, tile_hard_pm=0, tile_stable_pm=1000)
+    assert sel["active_tiles"].tolist() == [1]
