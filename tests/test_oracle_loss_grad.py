@@ -262,3 +262,51 @@ def test_chain_finite_differences(orc, seed):
                 bad.append((i, k, fd, grads[i, k]))
     assert checked > 0.7 * p0.size, checked
     assert not bad, bad[:10]
+
+
+def test_chain_finite_differences_clamped_jacobian(orc):
+    """The chain's finite differences for large Gaussians whose centres lie
+    beyond the Jacobian clamp (x/z or y/z past 1.3 tan of the half field of
+    view, on all four sides) while their splats still reach into the image,
+    next to two on screen."""
+    W, H = 48, 40
+    cam = scenes.look_at((0.0, 0.0, -4.0), width=W, height=H)
+    d = 4.0
+    tx, ty = 0.5 * W / cam["fx"], 0.5 * H / cam["fy"]
+    means = np.array([[1.2 * 1.3 * tx * d, 0.1, 0.0], [-1.2 * 1.3 * tx * d, -0.2, 0.3],
+                      [0.15, 1.2 * 1.3 * ty * d, 0.0], [-0.1, -1.2 * 1.3 * ty * d, -0.2],
+                      [0.2, 0.1, 0.5], [-0.3, -0.2, -0.4]])
+    n = len(means)
+    rng = np.random.default_rng(8)
+    g = dict(means=means, log_scales=np.log(np.array([[0.6, 0.5, 0.7]] * 4 + [[0.2, 0.15, 0.25]] * 2))
+             + rng.normal(0.0, 0.05, (n, 3)),
+             quats=rng.normal(size=(n, 4)), opacity_logits=rng.normal(0.5, 0.3, n),
+             sh=rng.normal(0.0, 0.3, (n, 16, 3)))
+    sel = _tile_sel(W, H, list(range(9)), 48, rng)
+    target = scenes.smooth_image(W, H, seed=9).astype(np.float64)
+    p0 = _pack(g)
+    lo, r, pr, pix, sig0 = _forward(orc, p0, cam, sel, target)
+    xz = p0[:4, 0] / (p0[:4, 2] + d)
+    yz = p0[:4, 1] / (p0[:4, 2] + d)
+    assert np.all((np.abs(xz) > 1.3 * tx) | (np.abs(yz) > 1.3 * ty))
+    assert np.all(pr["radius"][:4] > 0)                  # clamped, and still reaching the image
+    lam = lo["lam"]
+    g2 = orc.render_backward(pr, W, H, pix, lo["dL_drgb"])
+    grads = orc.project_backward(_unpack(p0), cam, g2)
+    h = 1e-6
+    checked, bad = 0, []
+    for i in range(4):
+        for k in range(11):                              # means, scales, rotation, opacity
+            pp, pm = p0.copy(), p0.copy()
+            pp[i, k] += h
+            pm[i, k] -= h
+            lp, rp, _, _, sp = _forward(orc, pp, cam, sel, target, lam)
+            lm, rm, _, _, sm = _forward(orc, pm, cam, sel, target, lam)
+            if sp != sig0 or sm != sig0 or min(rp["margin"].min(), rm["margin"].min()) < 1e-4:
+                continue
+            fd = (lp["loss"] - lm["loss"]) / (2 * h)
+            checked += 1
+            if abs(fd - grads[i, k]) > 1e-5 * max(abs(fd), 1e-3):
+                bad.append((i, k, fd, grads[i, k]))
+    assert checked > 0.7 * 44, checked
+    assert not bad, bad[:10]

@@ -2,6 +2,8 @@
 conversion, finite differences of the double-precision network, the bf16
 mode equal to the plain network when every value is exactly representable,
 and ReLU gating."""
+import math
+
 import numpy as np
 import pytest
 import torch
@@ -77,3 +79,16 @@ def test_relu_gating(orc):
     np.testing.assert_allclose(h2, np.maximum(w["b2"], 0)[None, :].repeat(10, 0))
     _, g = orc.mlp_backward(x, rng.normal(size=10), w, bf16=False)
     assert np.all(g["W1"] == 0) and np.all(g["b1"] == 0) and np.all(g["W2"] == 0)
+
+
+def test_bf16_rounding_ties_to_even(orc):
+    """Values exactly half way between two bfloat16 neighbours round to the
+    one with an even last bit (1 + 2^-8 -> 1, 1 + 3 * 2^-8 -> 1 + 2^-6 ...),
+    as torch's conversion does."""
+    import torch
+    for base in (1.0, -3.0, 0.75, 1024.0):
+        ulp = 2.0 ** (math.floor(math.log2(abs(base))) - 7)     # bf16 spacing in base's binade
+        for k in range(-6, 7):
+            x = base + (k + 0.5) * ulp * (1 if base > 0 else -1)
+            want = float(torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).float())
+            assert orc.round_bf16(x) == want, (x, orc.round_bf16(x), want)

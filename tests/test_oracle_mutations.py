@@ -206,10 +206,52 @@ MUTATIONS = [
     ('znear_cull', 'test_oracle_render.py',
      'if (!(z > cam->znear)) return;',
      'if (!(z > 0.0)) return;'),
+    ('bwd_clamp_dz', 'test_oracle_loss_grad.py',
+     'dpc[2] += dJ[2] * (cam.fx * lim / (z * z));',
+     'dpc[2] += 0.0 * dJ[2];'),
+    ('bwd_scale', 'test_oracle_loss_grad.py',
+     'out[3 + c] = ds * g.s[c];',
+     'out[3 + c] = ds;'),
+    ('bwd_dS2_sign', 'test_oracle_loss_grad.py',
+     'for (int k = 0; k < 4; ++k) dS2[k] = -dS2[k];',
+     ''),
+    ('bwd_dT2', 'test_oracle_loss_grad.py',
+     'for (int k = 0; k < 6; ++k) dT[k] = 2.0 * dS2TS[k];',
+     'for (int k = 0; k < 6; ++k) dT[k] = dS2TS[k];'),
+    ('bin_id_order', 'test_oracle_render.py',
+     'return x->id < y->id ? -1 : (x->id > y->id);',
+     'return x->id > y->id ? -1 : (x->id < y->id);'),
+    ('bf16_ties', 'test_oracle_mlp.py',
+     'u += 0x7fffu + lsb;',
+     'u += 0x8000u;'),
+    ('fp16_subnormal', 'test_oracle_basics.py',
+     'double q = rint(a * 16777216.0);',
+     'double q = floor(a * 16777216.0);'),
+    ('chol_index', 'test_oracle_hybrid.py',
+     'for (int k = i + 1; k < d; ++k) s -= L[k * d + i] * x[k];',
+     'for (int k = i + 1; k < d; ++k) s -= L[i * d + k] * x[k];'),
+    ('neglog2_int', 'test_oracle_basics.py',
+     'return ((uint64_t)(64 - ip) << 32) - frac;',
+     'return ((uint64_t)(63 - ip) << 32) - frac;'),
+    ('err_weight_sub', 'test_oracle_basics.py',
+     'if (e == 0) return (uint64_t)m;',
+     'if (e == 0) return (uint64_t)m << 1;'),
+    ('refresh_mean0', 'test_oracle_predictor.py',
+     'err[k] = orc_double_to_half(mean > 0.0 ? e * (want / mean) : want);',
+     'err[k] = orc_double_to_half(mean > 0.0 ? e * (want / mean) : 0.0);'),
+    ('mlp_bwd_dW2', 'test_oracle_mlp.py',
+     'for (int k = 0; k < MLP_H; ++k) dW2[j * MLP_H + k] += dh2[j] * h1[k];',
+     'for (int k = 0; k < MLP_H; ++k) dW2[k * MLP_H + j] += dh2[j] * h1[k];'),
+    ('mlp_bwd_loss', 'test_oracle_mlp.py',
+     'double dy = e / (double)R;',
+     'double dy = e;'),
+    ('sh_dir_grad', 'test_oracle_loss_grad.py',
+     'for (int a = 0; a < 3; ++a) dmu[a] += (ddir[a] - g.dir[a] * dot) / g.vlen;',
+     'for (int a = 0; a < 3; ++a) dmu[a] += ddir[a] / g.vlen;'),
 ]
 
 DEFAULT = {"no_dilation", "T_stop", "stats_D", "bwd_dalpha", "ncc_sample_var", "ema_swap", "lm_damp",
-           "split_floor", "hard_key_inv", "view_key_sign", "mlp_relu2", "feat_centre"}
+           "split_floor", "hard_key_inv", "view_key_sign", "mlp_relu2", "feat_centre", "bwd_clamp_dz"}
 ALL = os.environ.get("TURBOGS_ALL_MUTATIONS") == "1"
 CASES = [m for m in MUTATIONS if ALL or m[0] in DEFAULT]
 
