@@ -113,3 +113,5 @@ def test_table6_defaults():
         t6["T_fast"], t6["tau_until_fast"], t6["tau_from"], t6["K_max"], t6["K_min"],
         t6["alpha_view_schedule"], t6["lambda_base"])
     assert cfg.TILE == t6["tile_size"]
+    lo, hi = t6["lambda_tile_scale_range"]
+    assert lo < s.lam <= hi
