@@ -11,6 +11,7 @@ with gcc on first use and marshals numpy arrays in and out with ctypes.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -505,7 +506,6 @@ def sampling_schedule(t, E_t, E_init, K_max=10, K_min=3, alpha=3.0, tau_until=35
     r_tile = r_min + (r_max - r_min) g with r_min = lam / K_max and
     r_max = lam / K_min; K_t = round(K_min + (K_max - K_min) exp(-alpha g)),
     rounding halves up."""
-    import math
     r = min(max(E_t / (E_init + eps), 0.0), 1.0)
     phi = math.sin(0.5 * math.pi * math.sqrt(r))
     rho = 1.0 - min(max(t / tau_until, 0.0), 1.0)
