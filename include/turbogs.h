@@ -2,10 +2,12 @@
  * turbogs.h - C ABI of the GB300 sparse-sampled Gaussian-splatting path.
  *
  * The calls follow the per-iteration steps of TurboGS (ICML 2026, Alg. 1):
- * pixel sampling (step 3), sparse forward rendering (step 5), the fused sparse
- * loss with the error/age map update (steps 4, 6, 7), the sparse backward
- * (step 8) and the hybrid update (steps 9, 10), plus the projection and tile
- * binning of the 3DGS rasterizer they run on (Sec. 3.1).
+ * view selection (step 2: per-view error totals and the geometry-aware
+ * draw), pixel sampling (step 3), sparse forward rendering (step 5), the
+ * fused sparse loss with the error/age map update (steps 4, 6, 7), the sparse
+ * backward (step 8), the hybrid update (steps 9, 10) and the error
+ * back-projection statistics (step 11), plus the projection and tile binning
+ * of the 3DGS rasterizer they run on (Sec. 3.1).
  *
  * Conventions (all entry points):
  *  - Every array argument is a DEVICE pointer owned by the caller, contiguous,
