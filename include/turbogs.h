@@ -104,9 +104,8 @@ typedef struct {
   int32_t pix_hard_pm, pix_stable_pm;
 } tgs_sampling;
 
-/* Loss constants (App. A): Charbonnier epsilon, NCC epsilon, EMA ratio beta
- * (Table 6: 0.4). */
-/* Loss constants (Sec. 3.7, App. A).  view_weight scales this view's loss and
+/* Loss constants (Sec. 3.7, App. A): Charbonnier epsilon, NCC epsilon, EMA
+ * ratio beta (Table 6: 0.4).  view_weight scales this view's loss and
  * dL_drgb: 1 for one view, 1/K for the mean over K views of one step (the
  * expectation over views in Eq. 11). */
 typedef struct {
@@ -149,7 +148,8 @@ int64_t tgs_graph_count_kernels(void* graph);
  * exponential variate in 32-bit fixed point.  Ties go to the lower index.
  * Results are bit-identical on every run for the same inputs.
  *
- *   err_map [H,W]  fp16 error map E_v (bit patterns); negative/NaN count as 0
+ *   err_map [H,W]  fp16 error map E_v (bit patterns); negative, NaN and
+ *                  infinite values count as 0
  *   age_map [H,W]  uint16 age map A_v
  *   n_pix          1..256
  *   iter_dev       nullable device uint64: when given, the iteration number is
