@@ -190,6 +190,14 @@ tgs_status tgs_select_tiles(const uint16_t* err_map, const uint16_t* age_map, in
  *     threads without ordering) race on it: order them on one stream.
  * Arguments and outputs are those of tgs_select_tiles without the workspace.
  */
+#define TGS_SELECT_NOALLOC_MAX_TILES 16384
+#define TGS_SELECT_NOALLOC_SCRATCH_BYTES (768u * 1024u)
+#define TGS_SELECT_NOALLOC_MAX_DEVICES 64
+tgs_status tgs_select_tiles_noalloc(const uint16_t* err_map, const uint16_t* age_map, int32_t width,
+                                    int32_t height, int32_t n_select, int32_t n_pix, const tgs_sampling* cfg,
+                                    uint64_t seed, uint64_t iter, const uint64_t* iter_dev, uint32_t view,
+                                    int32_t* active_tiles, int32_t* n_active, int32_t* tile_rank, int32_t* pix_off,
+                                    uint8_t* pix_idx, tgs_stream stream);
 
 /*
  * view_error_sums - the per-view error totals behind the anchor choice of
@@ -245,14 +253,6 @@ tgs_status tgs_view_error_sums(const uint16_t* err_maps, int32_t n_views, int64_
 tgs_status tgs_sample_views(const uint64_t* err_sums, const tgs_camera* cams, int32_t n_views, int32_t k,
                             double lambda_d, double lambda_theta, uint64_t seed, uint64_t iter, uint8_t* stack,
                             int32_t* views, tgs_stream stream);
-#define TGS_SELECT_NOALLOC_MAX_TILES 16384
-#define TGS_SELECT_NOALLOC_SCRATCH_BYTES (768u * 1024u)
-#define TGS_SELECT_NOALLOC_MAX_DEVICES 64
-tgs_status tgs_select_tiles_noalloc(const uint16_t* err_map, const uint16_t* age_map, int32_t width,
-                                    int32_t height, int32_t n_select, int32_t n_pix, const tgs_sampling* cfg,
-                                    uint64_t seed, uint64_t iter, const uint64_t* iter_dev, uint32_t view,
-                                    int32_t* active_tiles, int32_t* n_active, int32_t* tile_rank, int32_t* pix_off,
-                                    uint8_t* pix_idx, tgs_stream stream);
 
 /*
  * project_gaussians - EWA projection and SH colour of the 3DGS model the
