@@ -1102,7 +1102,8 @@ int orc_loss(int width, int height, int n_active, const int32_t* active_tiles, c
 /* hybrid solver: moment-damped LM blocks + Adam (Sec. 3.9, App. A)         */
 /* ------------------------------------------------------------------------ */
 
-/* Cholesky factorisation A = L L^T (row-major d x d) and solve A x = b. */
+/* Cholesky factorisation A = L L^T (row-major d x d) and solve A x = b: the
+ * block solve of the LM step (Sec. 3.9, Eq. 14). */
 static int cholesky_solve(const double* A, const double* b, double* x, int d) {
   double L[196];
   memset(L, 0, sizeof(L));
@@ -1415,7 +1416,9 @@ void orc_view_error_sums(const uint16_t* maps, int n_views, int64_t view_stride,
 
 /* log2(x) * 2^32 for x >= 1, by the digit recurrence of orc_neglog2_q32:
  * the integer part is the position of the leading bit, each squaring of the
- * mantissa normalised to [1, 2) gives one fractional bit. */
+ * mantissa normalised to [1, 2) gives one fractional bit.  It turns the view
+ * draw's exponential clocks into logarithms, so that the weights of Sec. 3.4
+ * Eq. 6 enter the keys as sums. */
 uint64_t orc_log2_q32(uint64_t x) {
   int ip = 63;
   while (!(x >> ip)) ip--;
@@ -1433,7 +1436,7 @@ uint64_t orc_log2_q32(uint64_t x) {
 
 /* Camera centre c = -R^T t and unit viewing direction (the camera's forward
  * axis, the third row of R) of a row-major world-to-camera matrix whose
- * camera looks along +z. */
+ * camera looks along +z: the c_u and d_u of Sec. 3.4 Eq. 6. */
 void orc_view_pose(const float* viewmat, double* c, double* d) {
   const float* M = viewmat;
   for (int j = 0; j < 3; ++j) {
