@@ -120,6 +120,8 @@ def _declare(L):
     L.orc_view_pose.restype = None
     L.orc_sample_views.argtypes = [_p, _p, _i32, _i32, _d, _d, _u64, _u64, _p, _p]
     L.orc_sample_views.restype = None
+    L.orc_gaussian_scores.argtypes = [_i64, _p, _i32, _d, _d, _d, _p, _p]
+    L.orc_gaussian_scores.restype = None
 
 
 def _c(a, dtype):
@@ -514,3 +516,18 @@ def sampling_schedule(t, E_t, E_init, K_max=10, K_min=3, alpha=3.0, tau_until=35
     r_tile = r_min + (r_max - r_min) * g
     K = int(math.floor(K_min + (K_max - K_min) * math.exp(-alpha * g) + 0.5))
     return K, r_tile
+
+
+# ----------------------------------------------------------------------------
+# density control scores (Sec. 3.8)
+# ----------------------------------------------------------------------------
+
+def gaussian_scores(stats, t, tau_until=3500, lambda_base=0.8, eps=1e-8):
+    """(e [N], s [N]) of Eq. 13 from statistics rows (E, W, D, ...) of
+    Eq. 12 at iteration t; the progress rho = min(1, t / tau_until)."""
+    st = _c(stats, np.float64)
+    n, stride = st.shape
+    e, s = np.zeros(n), np.zeros(n)
+    rho = min(1.0, max(0.0, t / tau_until))
+    lib().orc_gaussian_scores(n, _ptr(st), stride, float(lambda_base), rho, float(eps), _ptr(e), _ptr(s))
+    return e, s

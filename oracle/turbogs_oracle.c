@@ -13,7 +13,8 @@
  * compositing, Sec. 3.3-3.5 for error/age maps, view and pixel sampling
  * (view sampling: Sec. 3.4 Eqs. 5-6), Sec. 3.7 and
  * App. A for the loss and its gradients, Sec. 3.8 for the error
- * back-projection statistics, Sec. 3.9 and App. A for the hybrid solver).  The
+ * back-projection statistics and the difficulty scores of Eq. 13 (no kernel
+ * yet), Sec. 3.9 and App. A for the hybrid solver).  The
  * projection follows the 3D Gaussian Splatting model the paper builds on
  * (Sec. 3.1: centre, covariance from scale and rotation, opacity, SH colour;
  * the paper defers the rest to the standard 3DGS pipeline).  No blocking, fusion or reordering
@@ -1522,4 +1523,29 @@ void orc_sample_views(const uint64_t* sums, const float* viewmats, int n_views, 
     if (drawn[u] || u == anchor) stack[u] = 0;
   free(drawn);
   free(cand);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gaussian difficulty scores of error-driven density control               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Sec. 3.8, Eq. 13, from the statistics of Eq. 12 (rows of `stride` doubles
+ * holding E_i, W_i, D_i first, as orc_error_stats writes them):
+ *   e_i = E_i / (W_i + eps), d_i = D_i / (W_i + eps),
+ *   s_i = e_i + lambda_eff d_i, lambda_eff = lambda_base (1 - rho),
+ * with rho in [0, 1] the training progress (Alg. 1: min(1, t / tau_until)).
+ * Dividing by the visibility W_i removes the bias towards often-seen
+ * Gaussians.  e_out and s_out are [n].
+ */
+void orc_gaussian_scores(int64_t n, const double* stats, int stride, double lambda_base, double rho, double eps,
+                         double* e_out, double* s_out) {
+  double lambda_eff = lambda_base * (1.0 - rho);
+  for (int64_t i = 0; i < n; ++i) {
+    const double* r = stats + (int64_t)stride * i;
+    double e = r[0] / (r[1] + eps);
+    double d = r[2] / (r[1] + eps);
+    e_out[i] = e;
+    s_out[i] = e + lambda_eff * d;
+  }
 }

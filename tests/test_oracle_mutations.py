@@ -248,6 +248,18 @@ MUTATIONS = [
     ('sh_dir_grad', 'test_oracle_loss_grad.py',
      'for (int a = 0; a < 3; ++a) dmu[a] += (ddir[a] - g.dir[a] * dot) / g.vlen;',
      'for (int a = 0; a < 3; ++a) dmu[a] += ddir[a] / g.vlen;'),
+    ('score_fade_dir', 'test_oracle_density.py',
+     'double lambda_eff = lambda_base * (1.0 - rho);',
+     'double lambda_eff = lambda_base * rho;'),
+    ('score_no_norm', 'test_oracle_density.py',
+     'double e = r[0] / (r[1] + eps);',
+     'double e = r[0];'),
+    ('score_swap_ed', 'test_oracle_density.py',
+     '    s_out[i] = e + lambda_eff * d;',
+     '    s_out[i] = d + lambda_eff * e;'),
+    ('score_d_by_e', 'test_oracle_density.py',
+     'double d = r[2] / (r[1] + eps);',
+     'double d = r[2] / (r[0] + eps);'),
 ]
 
 DEFAULT = {"no_dilation", "T_stop", "stats_D", "bwd_dalpha", "ncc_sample_var", "ema_swap", "lm_damp",
