@@ -183,7 +183,13 @@ tgs_status tgs_select_tiles(const uint16_t* err_map, const uint16_t* age_map, in
  *     TGS_ERR_CAPACITY before anything is launched.
  *   - The first call on a device looks up the array's device address (with
  *     that device current) and caches it; make that first call before any
- *     stream capture.
+ *     stream capture.  The cached address belongs to the device's current
+ *     context: after cudaDeviceReset (or any teardown of the primary context)
+ *     the library's module is loaded again and the array may move, so a
+ *     process that resets a device must not call this entry point on it
+ *     again.
+ *   - Devices with an ordinal of TGS_SELECT_NOALLOC_MAX_DEVICES or more get
+ *     TGS_ERR_CAPACITY (the address cache has that many entries).
  *   - All calls on a device share the one array, and it keeps the last
  *     call's contents (the call clears what must start at zero itself).  Calls
  *     that can overlap on the GPU (different streams, or different host

@@ -1534,7 +1534,10 @@ void orc_sample_views(const uint64_t* sums, const float* viewmats, int n_views, 
  * holding E_i, W_i, D_i first, as orc_error_stats writes them):
  *   e_i = E_i / (W_i + eps), d_i = D_i / (W_i + eps),
  *   s_i = e_i + lambda_eff d_i, lambda_eff = lambda_base (1 - rho),
- * with rho in [0, 1] the training progress (Alg. 1: min(1, t / tau_until)).
+ * with rho the training progress.  Eq. 13 states rho in [0, 1); Alg. 1 computes
+ * it as min(1, t / tau_until), which reaches 1 from t = tau_until on.  Taking
+ * Alg. 1's formula there (so that lambda_eff = 0 once densification ends) is
+ * a reading of the two passages; the caller passes rho.
  * Dividing by the visibility W_i removes the bias towards often-seen
  * Gaussians.  e_out and s_out are [n].
  */

@@ -473,7 +473,7 @@ tgs_status select_scratch_address(void** out) {
     tgs::set_cuda_error(e);
     return TGS_ERR_CUDA;
   }
-  if (dev < 0 || dev >= TGS_SELECT_NOALLOC_MAX_DEVICES) return TGS_ERR_DEVICE;
+  if (dev < 0 || dev >= TGS_SELECT_NOALLOC_MAX_DEVICES) return TGS_ERR_CAPACITY;  // the cache's size
   std::lock_guard<std::mutex> lock(g_scratch_mu);
   if (!g_scratch_ptr[dev]) {
     void* p = nullptr;

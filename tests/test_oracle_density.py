@@ -36,7 +36,13 @@ def _one_gaussian_stats(orc, err):
 
 def test_constant_error_scores_that_error(orc):
     st, _, _ = _one_gaussian_stats(orc, lambda n: np.full(n, 0.37))
-    e, s = orc.gaussian_scores(st, t=10 ** 6)         # past tau_until: no distance term
+    # inside Eq. 13's stated range rho in [0, 1): e is the error itself, the
+    # distance term only adds to s
+    for t in (0, 1000, 3000):
+        e, s = orc.gaussian_scores(st, t=t)
+        assert e[0] == pytest.approx(0.37, rel=1e-7) and s[0] > e[0]
+    # the end point rho = 1 (Alg. 1's min(1, t / tau_until) from tau_until on): no distance term
+    e, s = orc.gaussian_scores(st, t=10 ** 6)
     assert e[0] == pytest.approx(0.37, rel=1e-7) and s[0] == pytest.approx(0.37, rel=1e-7)
 
 
