@@ -44,6 +44,17 @@ def workload_config(frac=TILE_FRACTION, rate=PIXEL_RATE):
             "l2": "flushed between timed steps (256 MB write)"}
 
 
+def sm_count() -> int:
+    """Streaming multiprocessors of the current CUDA device."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def alu_peak_tflops(sm_mhz: float) -> float:
+    """FP32 peak (FMA = 2 FLOPs) at the given SM clock: SMs x 128 lanes x 2."""
+    return sm_count() * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -311,7 +322,7 @@ def roofline(stage_ms, info, peaks, peak_kind, clocks, tr, dom=None):
         dom = max((k for k in stage_ms if k in SINGLE_KERNEL_STAGES), key=stage_ms.get)
     t = stage_ms[dom] * 1e-3
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s FP32 (FMA = 2) at the sampled clock
+    alu_peak = alu_peak_tflops(sm_mhz)  # TFLOP/s FP32 at the sampled clock
     n = tr.n
     if dom in ("render_sampled", "render_backward"):
         per = FLOPS_ALPHA + FLOPS_BLEND if dom == "render_sampled" else FLOPS_BWD
@@ -372,7 +383,7 @@ def error_stats_time(tr, info, flush, clocks, peaks, reps: int = 5) -> dict:
         ms.append(a.elapsed_time(b))
     t = sorted(ms)[len(ms) // 2]
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    alu_peak = alu_peak_tflops(sm_mhz)
     achieved = info["evals_per_step"] * 27 / (t * 1e-3) / 1e12
     return {"ms": t, "bound": "alu", "achieved": achieved, "unit": "TFLOP/s", "frac": achieved / alu_peak,
             "note": "Sec. 3.8 statistics over the step's sampled pixels; not in the timed step"}
@@ -681,7 +692,7 @@ def run_batched(args):
                     for v in mv.views)
         mean = sum(ms) / len(ms)
         sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-        alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        alu_peak = alu_peak_tflops(sm_mhz)
         out["persistent" if persistent else "per_view"] = {
             "iters_per_s": 1e3 / mean, "ms_per_step": mean, "views_per_step": mv.K,
             "sampled_pixels": P, "active_tiles": [int(v.n_active.item()) for v in mv.views],

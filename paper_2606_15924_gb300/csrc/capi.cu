@@ -4,6 +4,18 @@
 namespace tgs {
 static thread_local int32_t g_last_cuda_error = 0;
 void set_cuda_error(cudaError_t e) { g_last_cuda_error = (int32_t)e; }
+int device_sm_count() {
+  static int sms[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  if (dev >= 64) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }
+  if (!sms[dev]) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
+  return sms[dev] > 0 ? sms[dev] : 1;
+}
 }  // namespace tgs
 
 extern "C" const char* tgs_version(void) { return "turbogs-gb300 0.1.0 (sm_103a)"; }

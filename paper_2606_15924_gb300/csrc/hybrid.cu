@@ -92,8 +92,7 @@ extern "C" tgs_status tgs_hybrid_step(const tgs_param_ptrs* params, const tgs_pa
   k_compact_touched<<<(int)((n + 255) / 256), 256, 0, s>>>(touched, n, list, count);
   // the touched count lives on the device: grid-stride loops over it with
   // grids of a few waves of the GPU (not one thread per Gaussian)
-  int dev = 0, sms = 152;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = device_sm_count();
   const int lb = (int)std::min<int64_t>((n + 127) / 128, (int64_t)sms * 16);
   const int sb = (int)std::min<int64_t>((n * 11 + 255) / 256, (int64_t)sms * 16);
   if (o.mode == 0) k_hybrid_lm<0><<<lb, 128, 0, s>>>(*params, *grads, *m, *v, n, list, count, view_rows, k_rows, o);

@@ -381,7 +381,7 @@ static MlpK mlp_k(const tgs_mlp* w) { return MlpK{w->w1, w->w2, w->w3, w->b1, w-
 
 static int mlp_grid(int64_t R) {
   const int64_t tiles = (R + 15) / 16;
-  return (int)std::max<int64_t>(1, std::min<int64_t>((tiles + 3) / 4, 152 * 8));
+  return (int)std::max<int64_t>(1, std::min<int64_t>((tiles + 3) / 4, (int64_t)device_sm_count() * 8));
 }
 
 }  // namespace tgs
@@ -439,7 +439,8 @@ extern "C" tgs_status tgs_mlp_backward(const tgs_mlp* w, int64_t rows, const int
                                                         loss);
   // chunks: whole kWgRows groups, at most 4 blocks per SM's worth
   const int64_t groups = (rows + kWgRows - 1) / kWgRows;
-  const int64_t per = std::max<int64_t>(1, (groups + 152 * 4 - 1) / (152 * 4));
+  const int64_t waves = (int64_t)device_sm_count() * 4;
+  const int64_t per = std::max<int64_t>(1, (groups + waves - 1) / waves);
   const int64_t chunk = per * kWgRows;
   k_mlp_wgrad<<<(unsigned)((rows + chunk - 1) / chunk), kWgThreads, 0, s>>>(x, h1, h2, dy, dh2, dh1, rows, chunk,
                                                                           grads);

@@ -692,14 +692,6 @@ static bool raster_args(const tgs_projected* proj, const int32_t* tile_ranges, c
 
 static int block_for(int n_pix_max) { return std::min(256, std::max(32, (n_pix_max + 31) / 32 * 32)); }
 
-// SMs of the current device (cached per device).
-static int sm_count() {
-  static int sms[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
-  if (!sms[dev]) cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev);
-  return std::max(1, sms[dev]);
-}
 
 }  // namespace tgs
 
@@ -738,7 +730,7 @@ extern "C" tgs_status tgs_render_sampled(const tgs_projected* proj, const int32_
   if (n_active_max == 0) return TGS_OK;
   const int B = block_for(n_pix_max);
   // selects when the launch gives fewer than 16 warps per SM
-  if ((int64_t)n_active_max * (B / 32) < 16 * (int64_t)sm_count())
+  if ((int64_t)n_active_max * (B / 32) < 16 * (int64_t)device_sm_count())
     k_render_fwd<true><<<n_active_max, B, B * sizeof(Splat), (cudaStream_t)stream>>>(a, rgb, T_final, n_last, ck);
   else
     k_render_fwd<false><<<n_active_max, B, B * sizeof(Splat), (cudaStream_t)stream>>>(a, rgb, T_final, n_last, ck);

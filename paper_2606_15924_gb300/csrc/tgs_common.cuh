@@ -15,6 +15,8 @@ namespace tgs {
 
 // Records the CUDA error of the calling thread's last failed call.
 void set_cuda_error(cudaError_t e);
+// Streaming multiprocessors of the current device (cached per device; 1 on error).
+int device_sm_count();
 
 // Returns TGS_ERR_CUDA (and records the error) when the last launch failed.
 inline tgs_status check_launch() {

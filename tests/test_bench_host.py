@@ -36,7 +36,8 @@ def test_clock_sampler_parses_nvidia_smi_lines():
     assert out["source"] == "nvidia-smi"
 
 
-def test_roofline_record():
+def test_roofline_record(monkeypatch):
+    monkeypatch.setattr(bench, "sm_count", lambda: 152)   # no device here: the GB300's SM count
     tr = types.SimpleNamespace(n=1000, H=720, W=1280)
     st = {"render_backward": 0.1, "project_gaussians": 0.04, "render_sampled": 0.05}
     info = {"evals_per_step": 1.0e6, "visible": 500, "touched": 200, "n_isect": 5000, "P": 61200}
