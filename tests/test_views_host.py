@@ -81,3 +81,41 @@ def test_view_sampler_default_distance_weight(V):
     assert one.lambda_d == 0.0
     with pytest.raises(ValueError):
         V.ViewSampler([], device="cpu")
+
+
+def test_library_schedule_closed_forms():
+    """The library's own host schedule (App. A, Eqs. 15-16), pinned to the
+    closed forms directly rather than to the oracle's copy: at t = 0 with the
+    initial error, rho = 1 and phi = 1 give K = K_max and r = lambda / K_max;
+    from tau_until on (or with no error left) g = 1 gives
+    K = round(K_min + (K_max - K_min) e^-alpha) and r = lambda / K_min;
+    phi(1/4) = sin(pi/4); the error ratio is clipped to [0, 1]."""
+    import math
+    from paper_2606_15924_gb300.config import ScheduleConfig
+    from paper_2606_15924_gb300.views import pixels_per_tile, sampling_schedule
+    s = ScheduleConfig()
+    assert (s.K_max, s.K_min, s.alpha, s.tau_until, s.lam) == (10, 3, 3.0, 3500, 1.0)   # Table 6
+    K, r = sampling_schedule(0, 0.7, 0.7, s)
+    assert K == 10 and r == pytest.approx(1.0 / 10, rel=1e-7)
+    k_late = math.floor(3 + 7 * math.exp(-3.0) + 0.5)
+    assert k_late == 3
+    for t, e, e0 in ((3500, 0.7, 0.7), (9000, 0.1, 0.7), (0, 0.0, 0.7), (100, 0.0, 2.0)):
+        K, r = sampling_schedule(t, e, e0, s)
+        assert K == k_late and r == pytest.approx(1.0 / 3, rel=1e-7)
+    # phi(1/4) = sin(pi/4) at t = 0: g = 1 - sqrt(2)/2
+    K, r = sampling_schedule(0, 0.25, 1.0, s)
+    g = 1.0 - math.sqrt(0.5)
+    assert r == pytest.approx(0.1 + (1.0 / 3 - 0.1) * g, rel=1e-7)
+    assert K == math.floor(3 + 7 * math.exp(-3.0 * g) + 0.5)
+    # halfway to tau_until with the initial error: rho = 1/2, phi = 1, g = 1/2
+    K, r = sampling_schedule(1750, 1.0, 1.0, s)
+    assert r == pytest.approx(0.1 + (1.0 / 3 - 0.1) * 0.5, rel=1e-7)
+    assert K == math.floor(3 + 7 * math.exp(-1.5) + 0.5)
+    # lambda scales both rates
+    K, r = sampling_schedule(0, 1.0, 1.0, ScheduleConfig(lam=0.5))
+    assert r == pytest.approx(0.05, rel=1e-7)
+    # more error than at the start counts as the start
+    assert sampling_schedule(100, 5.0, 1.0, s) == sampling_schedule(100, 1.0, 1.0, s)
+    # the pixel count per full tile
+    assert pixels_per_tile(1.0 / 3) == 85 and pixels_per_tile(0.1) == 26
+    assert pixels_per_tile(0.0) == 1 and pixels_per_tile(2.0) == 256
