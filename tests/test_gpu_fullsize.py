@@ -3,9 +3,11 @@ times (500k Gaussians, one 1280x720 view, 20 % of the tiles, 85 sampled
 pixels per tile, checkpoints every 32 list positions for the warp-per-piece
 backward), checked against the oracle on outputs it can compute one by one:
 the selection (bit for bit), the projection of every Gaussian, the forward at
-512 seeded sampled pixels, the backward of a seeded dL/dI that is non-zero at
-those 512 pixels only (so that both sides sum the same terms), and the fused
-projection adjoint + hybrid update (mode 1) of the Gaussians it touches."""
+512 seeded sampled pixels, the fused loss with the error/age map updates over
+every sampled pixel (on the forward's output), the backward of a seeded dL/dI
+that is non-zero at those 512 pixels only (so that both sides sum the same
+terms), and the fused projection adjoint + hybrid update (mode 1) of the
+Gaussians it touches."""
 import numpy as np
 import pytest
 import torch
@@ -72,6 +74,27 @@ def test_full_size_step_against_oracle(orc):
     np.testing.assert_array_equal(n_last.cpu().numpy()[S][sure_p], want["n_last"][sure_p])
     assert np.abs(rgb.cpu().numpy()[S][sure_p] - want["rgb"][sure_p]).max() <= 1e-4
     assert np.abs(T.cpu().numpy()[S][sure_p] - want["T"][sure_p]).max() <= 1e-4
+    # the fused loss (Sec. 3.7 Eqs. 9-11; App. A) with the error EMA and age updates (Sec. 3.3,
+    # Eqs. 2-4) over all of the step's sampled pixels, on the forward's own output
+    tgt = scenes.smooth_image(W, H, seed=31)
+    err_d, age_d = dev(err), dev(age)
+    dLl = torch.zeros(P, 3, device="cuda")
+    lam = torch.zeros(N_SEL, device="cuda")
+    e_pix = torch.zeros(P, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float64, device="cuda")
+    B.loss_sparse_ncc(rgb, dev(tgt), W, H, sel["active_tiles"], sel["n_active"], sel["n_sel"], sel["pix_off"],
+                      sel["pix_idx"], N_PIX, (1e-3, 1e-8, 0.4), err_d, age_d, dLl, lam, e_pix, loss)
+    rgb_h = rgb.cpu().numpy().astype(np.float64)
+    lo = orc.loss(W, H, sel_o, rgb_h, tgt.astype(np.float64), err_f16_bits=err, age=age)
+    assert float(loss.item()) == pytest.approx(lo["loss"], rel=1e-5)
+    np.testing.assert_allclose(lam.cpu().numpy()[:len(lo["lam"])], lo["lam"], rtol=1e-4, atol=1e-7)
+    np.testing.assert_allclose(e_pix.cpu().numpy(), lo["err"], atol=1e-6)
+    assert rel_l2(dLl.cpu().numpy(), lo["dL_drgb"]) <= 1e-4
+    np.testing.assert_array_equal(age_d.cpu().numpy(), lo["age_map"])   # ages exactly
+    got_e = err_d.cpu().numpy().view(np.float16).astype(np.float64)
+    want_e = lo["err_map"].view(np.float16).astype(np.float64)
+    ulp = np.spacing(np.abs(want_e).astype(np.float16)).astype(np.float64)
+    assert np.all(np.abs(got_e - want_e) <= ulp)                         # one fp16 ulp
     # the backward from the checkpoints, dL/dI seeded and non-zero at S only
     dL = np.zeros((P, 3), np.float32)
     dL[S] = rng.normal(0.0, 1e-3, (len(S), 3)).astype(np.float32)

@@ -47,6 +47,7 @@ def test_forward_parity(P, orc, R, tc):
         B.mlp_forward(mlp.net(), xd, y, h1, h2)
     yw, h1w, h2w = orc.mlp_forward(x, mlp.weights_fp(), bf16=True)
     got = y.cpu().numpy()
+    print(f"mlp forward R={R} tc={tc}: y rel L2 {rel_l2(got, yw):.3e}")
     assert rel_l2(got, yw) <= 1e-3
     assert np.abs(got - yw).max() <= 1e-2 * max(1.0, np.abs(yw).max())
     for hg, hw in ((h1, h1w), (h2, h2w)):
@@ -75,6 +76,8 @@ def test_backward_parity(P, orc, R):
     assert float(mlp.loss.item()) == pytest.approx(loss, rel=1e-3)
     g = mlp.grads.double().cpu().numpy()
     sl = mlp._slices()
+    print(f"mlp backward R={R}: loss rel {abs(float(mlp.loss.item()) - loss) / abs(loss):.3e}, " +
+          ", ".join(f"{k} {rel_l2(g[sl[k]], gw[k].reshape(-1)):.3e}" for k in ("W1", "b1", "W2", "b2", "W3", "b3")))
     for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
         assert rel_l2(g[sl[name]], gw[name].reshape(-1)) <= 1e-3, (name, rel_l2(g[sl[name]], gw[name].reshape(-1)))
 
