@@ -329,6 +329,21 @@ typedef struct {
 size_t tgs_checkpoint_bytes(int32_t n_active_max, int32_t n_pix_max, int32_t n_slots);
 
 /*
+ * set_forward_split - a tuning knob of render_sampled with checkpoints (not in
+ * the paper).  With checkpoints and few active tiles, the forward walks each
+ * tile's list in NW runs of 32 positions at once (NW groups of one thread per
+ * sampled pixel, each run from a local transmittance of 1) and composes the
+ * runs' results in list order, (T, C) -> (T T_run, C + T C_run); the run in
+ * which the composed transmittance falls below the stopping value is walked
+ * again from its entry state to find the exact stop.  The result equals the
+ * sequential walk up to the rounding of the composition.  groups = 0 (the
+ * default) picks NW per launch: 4 or 2 when the launch's blocks all fit on
+ * the GPU at once, else the sequential walk; 1, 2 or 4 fix it (1 = always
+ * sequential).  Process-wide; returns TGS_ERR_INVALID_ARG for other values.
+ */
+tgs_status tgs_set_forward_split(int32_t groups);
+
+/*
  * render_sampled - sparse forward rasterization (Sec. 3.6, Eq. 1; Alg. 1
  * step 5): for every sampled pixel of every active tile, front-to-back
  * compositing over the tile's list: alpha = min(0.99, o exp(power)),

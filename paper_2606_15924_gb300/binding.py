@@ -125,6 +125,8 @@ _lib.tgs_bin_tiles.argtypes = [_P(Projected), _i64, _P(Camera), _p, _i32, _p, _s
 _lib.tgs_render_sampled.restype = _i32
 _lib.tgs_checkpoint_bytes.restype = _sz
 _lib.tgs_checkpoint_bytes.argtypes = [_i32, _i32, _i32]
+_lib.tgs_set_forward_split.restype = _i32
+_lib.tgs_set_forward_split.argtypes = [_i32]
 _lib.tgs_render_sampled.argtypes = [_P(Projected), _p, _p, _p, _p, _i32, _p, _p, _i32, _P(Camera), _p, _p, _p,
                                     _p, _P(Checkpoints), _p]
 _lib.tgs_loss_sparse_ncc.restype = _i32
@@ -190,7 +192,7 @@ EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_devi
             "tgs_advance_counters",
             "tgs_select_tiles_workspace_size", "tgs_select_tiles", "tgs_select_tiles_noalloc",
             "tgs_project_gaussians",
-            "tgs_bin_tiles_workspace_size", "tgs_bin_tiles", "tgs_checkpoint_bytes", "tgs_render_sampled",
+            "tgs_bin_tiles_workspace_size", "tgs_bin_tiles", "tgs_checkpoint_bytes", "tgs_set_forward_split", "tgs_render_sampled",
             "tgs_loss_sparse_ncc",
             "tgs_backward_sampled", "tgs_render_backward_sampled", "tgs_error_stats_sampled", "tgs_project_backward", "tgs_project_backward_multi_workspace_size",
             "tgs_project_backward_multi", "tgs_project_backward_update",
@@ -318,6 +320,12 @@ def bin_tiles(proj: dict, n, cam, tile_rank, n_active_max, workspace, capacity, 
     _check("tgs_bin_tiles", _lib.tgs_bin_tiles(
         C.byref(pr), int(n), C.byref(cc), _ptr(tile_rank), int(n_active_max), _ptr(workspace), workspace.numel(),
         int(capacity), _ptr(vals), _ptr(keys), _ptr(tile_ranges), _ptr(n_isect), _stream(stream)))
+
+
+def set_forward_split(groups: int) -> None:
+    """Tuning knob of the checkpointed forward: 0 picks the split walk's
+    group count per launch; 1 (sequential), 2 or 4 fix it process-wide."""
+    _check("tgs_set_forward_split", _lib.tgs_set_forward_split(int(groups)))
 
 
 def checkpoint_bytes(n_active_max: int, n_pix_max: int, n_slots: int) -> int:

@@ -216,6 +216,195 @@ __global__ void k_render_fwd(RasterArgs a, float* __restrict__ out_rgb, float* _
   render_tile_fwd<SELECT>(a, j, sm, out_rgb, out_T, out_last, ck);
 }
 
+// ---------------------------------------------------------------------------
+// Split forward (few active tiles: a sparse step).  One block per active
+// tile holds NW groups of G threads, one thread per sampled pixel in each
+// group.  In round r, group g walks run r NW + g of the tile's list (the 32
+// positions [32 (r NW + g), 32 (r NW + g + 1))) from a local transmittance of
+// 1, so the NW runs of a round are walked at once and the tile's walk is NW
+// times shorter.  A run walked from T = 1 to local transmittance T_l and
+// local colour D_l turns the state (T, C) in front of it into
+// (T T_l, C + T D_l); the groups' results are composed per pixel in list
+// order through shared memory.  The walk stops in the first run where the
+// composed product falls below the stopping transmittance, or whose local
+// walk stopped by itself (T_l (1 - alpha) < 1e-4 implies the same for the
+// global T <= T_l); that run is walked again by its group from its true entry
+// state to find the exact stopping splat.  Checkpoints (the state at the end
+// of each run) are written from the composed state, as the sequential walk
+// writes them, so the backward is unchanged.  The composition rounds
+// differently from the sequential product (one more rounding per run); when
+// the product lands within rounding of the stopping value and the re-walk
+// does not stop, the walk ends at the end of that run.  Rounds repeat until
+// every pixel has stopped or the list ends, so work past the tile's last
+// stopping point is bounded by one round.
+// ---------------------------------------------------------------------------
+constexpr int kLocalStop = 64;  // flag bit beside the run-local last position (0..32)
+
+__device__ __forceinline__ void compose_run(float& T, float& C0, float& C1, float& C2, const float4& e) {
+  C0 = __fmaf_rn(T, e.y, C0);
+  C1 = __fmaf_rn(T, e.z, C1);
+  C2 = __fmaf_rn(T, e.w, C2);
+  T = __fmul_rn(T, e.x);
+}
+
+template <int NW>
+__global__ void k_render_fwd_split(RasterArgs a, float* __restrict__ out_rgb, float* __restrict__ out_T,
+                                   int32_t* __restrict__ out_last, Ckpt ck) {
+  extern __shared__ float4 smem_f4[];
+  __shared__ int s_tl;
+  const int j = blockIdx.x;
+  if (j >= *a.n_active) return;
+  const int G = blockDim.x / NW;
+  Splat* sp = reinterpret_cast<Splat*>(smem_f4);           // [NW][32]
+  float4* loc = reinterpret_cast<float4*>(sp + NW * 32);   // [NW][G] (T_l, D_l)
+  float4* rec = loc + NW * G;                              // [NW][G] state after a stopping run
+  int* lastl = reinterpret_cast<int*>(rec + NW * G);       // [NW][G] local last | kLocalStop
+  int* rec_last = lastl + NW * G;                          // [NW][G]
+  const int g = threadIdx.x / G, i = threadIdx.x - g * G;
+  const int t = a.active_tiles ? a.active_tiles[j] : j;
+  const int p0 = a.pix_off[j], p1 = a.pix_off[j + 1];
+  const bool has_pix = p0 + i < p1;
+  const int s = p0 + i;
+  float px = 0.f, py = 0.f;
+  if (has_pix) {
+    const int l = a.pix_idx[s];
+    px = (float)((t % a.tiles_x) * TGS_TILE + (l & 15)) + 0.5f;
+    py = (float)((t / a.tiles_x) * TGS_TILE + (l >> 4)) + 0.5f;
+  }
+  const int2 range = a.ranges[j];
+  const int L = range.y - range.x;
+  const int n_runs = (L + kCkptEvery - 1) / kCkptEvery;
+  // the running state of pixel i in front of the current round (the same in every group)
+  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+  int last = 0;
+  bool done = !has_pix;
+  const Splat* S = sp + 32 * g;
+  Splat nxt;
+  if (i < 32 && 32 * g + i < L) load_splat(a, range.x + 32 * g + i, nxt);
+  for (int r0 = 0; r0 < n_runs; r0 += NW) {
+    const int run = r0 + g;
+    // the previous round's reads of sp ended before its second barrier
+    if (i < 32 && 32 * run + i < L) sp[32 * g + i] = nxt;
+    if (__syncthreads_count(done) == (int)blockDim.x) break;
+    if (i < 32 && 32 * (run + NW) + i < L) load_splat(a, range.x + 32 * (run + NW) + i, nxt);
+    // 1. the group's run from a local T = 1 (alphas of kUnroll splats together, blend with selects)
+    const int cnt = min(kCkptEvery, L - 32 * run);
+    float Tl = 1.f, D0 = 0.f, D1 = 0.f, D2 = 0.f;
+    int ll = 0;
+    bool lstop = false;
+    if (!done && cnt > 0) {
+      for (int q0 = 0; q0 < cnt && !lstop; q0 += kUnroll) {
+        float al[kUnroll];
+        bool ok[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const float2 xy = S[q0 + u].xy;
+          float Gv;
+          ok[u] = splat_alpha_nb(S[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], Gv) &&
+                  q0 + u < cnt;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const float Tn = __fmul_rn(Tl, __fsub_rn(1.f, al[u]));
+          const bool stop = ok[u] && !lstop && Tn < kTStop;
+          const bool take = ok[u] && !lstop && !stop;
+          lstop = lstop || stop;
+          const float4 rgb = S[q0 + u].rgb;
+          const float w = al[u] * Tl;
+          D0 = take ? D0 + w * rgb.x : D0;
+          D1 = take ? D1 + w * rgb.y : D1;
+          D2 = take ? D2 + w * rgb.z : D2;
+          Tl = take ? Tn : Tl;
+          ll = take ? q0 + u + 1 : ll;
+        }
+      }
+    }
+    loc[g * G + i] = make_float4(Tl, D0, D1, D2);
+    lastl[g * G + i] = ll | (lstop ? kLocalStop : 0);
+    __syncthreads();
+    // 2. the state in front of this group's run; its checkpoint, or the exact stop inside it
+    if (!done && cnt > 0) {
+      float T2 = T, E0 = C0, E1 = C1, E2 = C2;
+      int l2 = last;
+      bool before = false;
+      for (int h = 0; h < g; ++h) {
+        const float4 e = loc[h * G + i];
+        const int lh = lastl[h * G + i];
+        if ((lh & kLocalStop) || __fmul_rn(T2, e.x) < kTStop) {
+          before = true;
+          break;
+        }
+        compose_run(T2, E0, E1, E2, e);
+        if (lh) l2 = 32 * (r0 + h) + lh;
+      }
+      if (!before) {
+        if (lstop || __fmul_rn(T2, Tl) < kTStop) {
+          for (int q = 0; q < cnt; ++q) {  // the stopping run again, from its entry state
+            const Splat& sq = S[q];
+            float al, Gv;
+            if (!splat_alpha(sq.co, __fsub_rn(px, sq.xy.x), __fsub_rn(py, sq.xy.y), al, Gv)) continue;
+            const float Tn = __fmul_rn(T2, __fsub_rn(1.f, al));
+            if (Tn < kTStop) break;
+            const float w = al * T2;
+            E0 += w * sq.rgb.x;
+            E1 += w * sq.rgb.y;
+            E2 += w * sq.rgb.z;
+            T2 = Tn;
+            l2 = 32 * run + q + 1;
+          }
+          rec[g * G + i] = make_float4(T2, E0, E1, E2);
+          rec_last[g * G + i] = l2;
+        } else if (ck.data && run < ck.n_slots) {
+          compose_run(T2, E0, E1, E2, make_float4(Tl, D0, D1, D2));
+          ck.data[run * ck.stride + s] = make_float4(T2, E0, E1, E2);  // in front of position 32 (run + 1)
+        }
+      }
+    }
+    __syncthreads();
+    // 3. the running state over the whole round (every group the same)
+    if (!done) {
+#pragma unroll
+      for (int h = 0; h < NW; ++h) {
+        if (r0 + h >= n_runs) break;
+        const float4 e = loc[h * G + i];
+        const int lh = lastl[h * G + i];
+        if ((lh & kLocalStop) || __fmul_rn(T, e.x) < kTStop) {
+          const float4 q = rec[h * G + i];
+          T = q.x;
+          C0 = q.y;
+          C1 = q.z;
+          C2 = q.w;
+          last = rec_last[h * G + i];
+          done = true;
+          break;
+        }
+        compose_run(T, C0, C1, C2, e);
+        if (lh) last = 32 * (r0 + h) + lh;
+      }
+    }
+  }
+  if (g == 0 && has_pix) {
+    out_rgb[3 * s] = C0 + T * a.bg[0];
+    out_rgb[3 * s + 1] = C1 + T * a.bg[1];
+    out_rgb[3 * s + 2] = C2 + T * a.bg[2];
+    out_T[s] = T;
+    out_last[s] = last;
+  }
+  if (ck.tile_last) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_tl = 0;
+    __syncthreads();
+    if (g == 0 && last > 0) atomicMax(&s_tl, last);
+    __syncthreads();
+    if (threadIdx.x == 0) ck.tile_last[j] = s_tl;
+  }
+}
+
+template <int NW>
+size_t split_smem_bytes(int G) {
+  return NW * 32 * sizeof(Splat) + (size_t)NW * G * (2 * sizeof(float4) + 2 * sizeof(int));
+}
+
 // Sum of v[0..7] over the warp, scattered: lane l ends with the total of
 // v[(l >> 2) & 7] (halving exchanges at distances 16, 8, 4, then a butterfly
 // over the last two bits): 9 shuffles instead of 40.
@@ -693,6 +882,38 @@ static bool raster_args(const tgs_projected* proj, const int32_t* tile_ranges, c
 static int block_for(int n_pix_max) { return std::min(256, std::max(32, (n_pix_max + 31) / 32 * 32)); }
 
 
+// The split forward's group count: 0 = chosen per launch (below), or fixed
+// at 1, 2 or 4 by tgs_set_forward_split (tuning and tests).
+static int g_fwd_split = 0;
+
+// Groups per tile of the split forward for a launch of n_active tiles of B
+// threads: the largest of 4 and 2 whose blocks all fit on the GPU at once
+// (one wave), else 1 (the sequential walk).
+static int split_groups(int n_active, int B) {
+  const int wp = B / 32;  // 1..8
+  const bool nw_ok[2] = {4 * B <= 1024, 2 * B <= 1024};
+  if (g_fwd_split) return (g_fwd_split == 4 && !nw_ok[0]) || (g_fwd_split == 2 && !nw_ok[1]) ? 1 : g_fwd_split;
+  static int per_sm[64][9][2] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  const int sms = device_sm_count();
+  for (int k = 0; k < 2; ++k) {
+    const int nw = k == 0 ? 4 : 2;
+    if (!nw_ok[k]) continue;
+    int& r = per_sm[dev][wp][k];
+    if (r == 0) {
+      int b = 0;
+      if (nw == 4)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_render_fwd_split<4>, 4 * B, split_smem_bytes<4>(B));
+      else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_render_fwd_split<2>, 2 * B, split_smem_bytes<2>(B));
+      r = b > 0 ? b : -1;
+    }
+    if (r > 0 && (int64_t)n_active <= (int64_t)sms * r) return nw;
+  }
+  return 1;
+}
+
 }  // namespace tgs
 
 using namespace tgs;
@@ -708,6 +929,12 @@ static bool ckpt_of(const tgs_checkpoints* c, int32_t n_active_max, int32_t n_pi
   k.rgb = rgb;
   k.tile_last = c->tile_last;
   return true;
+}
+
+extern "C" tgs_status tgs_set_forward_split(int32_t groups) {
+  if (groups != 0 && groups != 1 && groups != 2 && groups != 4) return TGS_ERR_INVALID_ARG;
+  g_fwd_split = groups;
+  return TGS_OK;
 }
 
 extern "C" size_t tgs_checkpoint_bytes(int32_t n_active_max, int32_t n_pix_max, int32_t n_slots) {
@@ -729,6 +956,18 @@ extern "C" tgs_status tgs_render_sampled(const tgs_projected* proj, const int32_
   if (!ckpt_of(ckpt, n_active_max, n_pix_max, rgb, ck)) return TGS_ERR_INVALID_ARG;
   if (n_active_max == 0) return TGS_OK;
   const int B = block_for(n_pix_max);
+  // sampled training (checkpoints) with few tiles: the split walk, NW groups per tile
+  const int nw = ck.data ? split_groups(n_active_max, B) : 1;
+  if (nw == 4) {
+    k_render_fwd_split<4><<<n_active_max, 4 * B, split_smem_bytes<4>(B), (cudaStream_t)stream>>>(a, rgb, T_final,
+                                                                                                 n_last, ck);
+    return check_launch();
+  }
+  if (nw == 2) {
+    k_render_fwd_split<2><<<n_active_max, 2 * B, split_smem_bytes<2>(B), (cudaStream_t)stream>>>(a, rgb, T_final,
+                                                                                                 n_last, ck);
+    return check_launch();
+  }
   // selects when the launch gives fewer than 16 warps per SM
   if ((int64_t)n_active_max * (B / 32) < 16 * (int64_t)device_sm_count())
     k_render_fwd<true><<<n_active_max, B, B * sizeof(Splat), (cudaStream_t)stream>>>(a, rgb, T_final, n_last, ck);

@@ -132,3 +132,13 @@ def test_hybrid_checks(B):
     assert _call(f, a10=C.byref(bad), a8=1) == INVALID                             # beta1 = 1
     bad = B.Opt((C.c_float * 6)(*[1e-3] * 6), 0.9, 0.999, 1e-15, 1e-8, 3)
     assert _call(f, a10=C.byref(bad), a8=1) == INVALID                             # mode 3
+
+
+def test_forward_split_knob(B):
+    """The split forward's tuning knob accepts 0 (automatic), 1, 2 and 4 only
+    (no device work)."""
+    f = B._lib.tgs_set_forward_split
+    for bad in (-1, 3, 5, 8):
+        assert f(bad) == INVALID
+    for ok in (1, 2, 4, 0):
+        assert f(ok) == 0

@@ -48,8 +48,9 @@ def test_forward_parity(P, orc, R, tc):
     yw, h1w, h2w = orc.mlp_forward(x, mlp.weights_fp(), bf16=True)
     got = y.cpu().numpy()
     print(f"mlp forward R={R} tc={tc}: y rel L2 {rel_l2(got, yw):.3e}")
-    assert rel_l2(got, yw) <= 1e-3
-    assert np.abs(got - yw).max() <= 1e-2 * max(1.0, np.abs(yw).max())
+    # measured on GB300: at most 1.4e-5 (4097 rows); the bound leaves a factor of 7
+    assert rel_l2(got, yw) <= 1e-4
+    assert np.abs(got - yw).max() <= 1e-3 * max(1.0, np.abs(yw).max())
     for hg, hw in ((h1, h1w), (h2, h2w)):
         hv = hg.view(torch.bfloat16).float().cpu().numpy().astype(np.float64)
         # fp32 vs fp64 accumulation may move a value across a bf16 rounding
@@ -73,13 +74,14 @@ def test_backward_parity(P, orc, R):
     B.mlp_forward(mlp.net(), xd, y, h1, h2)
     B.mlp_backward(mlp.net(), xd, h1, h2, y, td, mlp.grads, mlp.loss)
     loss, gw = orc.mlp_backward(x, t, mlp.weights_fp(), bf16=True)
-    assert float(mlp.loss.item()) == pytest.approx(loss, rel=1e-3)
+    # measured on GB300: loss within 2.5e-6, gradients within 4.1e-5 (2048 rows); bounds with a factor of 5
+    assert float(mlp.loss.item()) == pytest.approx(loss, rel=2e-5)
     g = mlp.grads.double().cpu().numpy()
     sl = mlp._slices()
     print(f"mlp backward R={R}: loss rel {abs(float(mlp.loss.item()) - loss) / abs(loss):.3e}, " +
           ", ".join(f"{k} {rel_l2(g[sl[k]], gw[k].reshape(-1)):.3e}" for k in ("W1", "b1", "W2", "b2", "W3", "b3")))
     for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
-        assert rel_l2(g[sl[name]], gw[name].reshape(-1)) <= 1e-3, (name, rel_l2(g[sl[name]], gw[name].reshape(-1)))
+        assert rel_l2(g[sl[name]], gw[name].reshape(-1)) <= 2e-4, (name, rel_l2(g[sl[name]], gw[name].reshape(-1)))
 
 
 def test_adam_step_and_training(P):
