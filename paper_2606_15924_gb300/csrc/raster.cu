@@ -33,20 +33,33 @@ __device__ __forceinline__ float ex2_approx(float x) {
 
 struct Splat {
   float2 xy;
-  float4 co;   // conic a, b, c, opacity
+  float4 co;   // the conic pre-scaled to base-2 exponents: (-a/2, -b, -c/2) log2(e), then the opacity
   float4 rgb;  // r, g, b, (unused)
 };
 
+// Staging scale of the conic: with a' = -a log2(e) / 2, b' = -b log2(e) and
+// c' = -c log2(e) / 2 the exponent of Eq. 1's Gaussian in base 2 is
+// p = a' dx^2 + b' dx dy + c' dy^2 = log2(e) power.
+constexpr float kPow2A = -0.5f * kLog2e;
+constexpr float kPow2B = -kLog2e;
+// back to the conic: a = a' kInvA, b = b' kInvB, c = c' kInvA
+constexpr float kInvA = -1.3862943611198906f;  // -2 ln 2
+constexpr float kInvB = -0.6931471805599453f;  // -ln 2
+
+// p = log2(e) power at offset (dx, dy) from the splat's centre, with the
+// pre-scaled conic: (a' dx + b' dy) dx + c' dy^2 (explicitly rounded, so
+// every kernel takes the same decisions for the same splat and pixel).
+__device__ __forceinline__ float splat_pow2(const float4& co, float dx, float dy) {
+  const float t = __fmaf_rn(co.x, dx, __fmul_rn(co.y, dy));
+  return __fmaf_rn(t, dx, __fmul_rn(__fmul_rn(co.z, dy), dy));
+}
+
 // alpha of a splat at offset (dx, dy) from its centre; G receives exp(power).
 // Returns false when the splat is skipped (power > 0 or alpha < 1/255).
-// Every operation is an explicitly rounded intrinsic, so the forward and the
-// backward kernels take bit-identical decisions for the same splat and pixel.
 __device__ __forceinline__ bool splat_alpha(const float4& co, float dx, float dy, float& alpha, float& G) {
-  const float ax = __fmul_rn(co.x, dx), cy = __fmul_rn(co.z, dy), by = __fmul_rn(co.y, dy);
-  const float quad = __fmaf_rn(ax, dx, __fmul_rn(cy, dy));          // a dx^2 + c dy^2
-  const float power = __fmaf_rn(-0.5f, quad, -__fmul_rn(by, dx));   // - quad / 2 - b dx dy
-  if (power > 0.f) return false;
-  G = ex2_approx(__fmul_rn(power, kLog2e));
+  const float p = splat_pow2(co, dx, dy);
+  if (p > 0.f) return false;
+  G = ex2_approx(p);
   alpha = fminf(kAlphaMax, __fmul_rn(co.w, G));
   return alpha >= kAlphaMin;
 }
@@ -55,12 +68,10 @@ __device__ __forceinline__ bool splat_alpha(const float4& co, float dx, float dy
 // (for power > 0, G may be +inf and alpha 0.99, finite either way), and the
 // return value says whether the splat counts.
 __device__ __forceinline__ bool splat_alpha_nb(const float4& co, float dx, float dy, float& alpha, float& G) {
-  const float ax = __fmul_rn(co.x, dx), cy = __fmul_rn(co.z, dy), by = __fmul_rn(co.y, dy);
-  const float quad = __fmaf_rn(ax, dx, __fmul_rn(cy, dy));
-  const float power = __fmaf_rn(-0.5f, quad, -__fmul_rn(by, dx));
-  G = ex2_approx(__fmul_rn(power, kLog2e));
+  const float p = splat_pow2(co, dx, dy);
+  G = ex2_approx(p);
   alpha = fminf(kAlphaMax, __fmul_rn(co.w, G));
-  return power <= 0.f && alpha >= kAlphaMin;
+  return p <= 0.f && alpha >= kAlphaMin;
 }
 
 struct RasterArgs {
@@ -80,7 +91,8 @@ struct RasterArgs {
 __device__ __forceinline__ void load_splat(const RasterArgs& a, int k, Splat& sp) {
   const int id = a.vals[k];
   sp.xy = a.xy[id];
-  sp.co = a.conic_opac[id];
+  const float4 c = a.conic_opac[id];
+  sp.co = make_float4(__fmul_rn(c.x, kPow2A), __fmul_rn(c.y, kPow2B), __fmul_rn(c.z, kPow2A), c.w);
   sp.rgb = make_float4(a.rgb[3 * id], a.rgb[3 * id + 1], a.rgb[3 * id + 2], __int_as_float(id));
 }
 
@@ -405,6 +417,20 @@ size_t split_smem_bytes(int G) {
   return NW * 32 * sizeof(Splat) + (size_t)NW * G * (2 * sizeof(float4) + 2 * sizeof(int));
 }
 
+// The adjoints of a splat's centre and conic from the sums over its pixels of
+// dL/dpower times dx, dy, dx^2, dx dy, dy^2 (power = -(a dx^2 + c dy^2)/2 -
+// b dx dy, dx = px - x): dL/dx = a m1 + b m2, dL/dy = c m2 + b m1,
+// dL/da = -m3 / 2, dL/db = -m4, dL/dc = -m5 / 2 (co: the pre-scaled conic).
+__device__ __forceinline__ void power_moments_to_grad(const float4& co, float m1, float m2, float m3, float m4,
+                                                      float m5, float (&g)[5]) {
+  const float A = co.x * kInvA, Bc = co.y * kInvB, Cc = co.z * kInvA;
+  g[0] = A * m1 + Bc * m2;
+  g[1] = Cc * m2 + Bc * m1;
+  g[2] = -0.5f * m3;
+  g[3] = -m4;
+  g[4] = -0.5f * m5;
+}
+
 // Sum of v[0..7] over the warp, scattered: lane l ends with the total of
 // v[(l >> 2) & 7] (halving exchanges at distances 16, 8, 4, then a butterfly
 // over the last two bits): 9 shuffles instead of 40.
@@ -508,18 +534,20 @@ __device__ __forceinline__ void render_tile_bwd(const RasterArgs& a, int j, Spla
           v[6] = wgt * g0;
           v[7] = wgt * g1;
           v[8] = wgt * g2;
-          const float dalpha = T * ((sp.rgb.x - S0) * g0 + (sp.rgb.y - S1) * g1 + (sp.rgb.z - S2) * g2);
-          S0 = alpha * sp.rgb.x + (1.f - alpha) * S0;
-          S1 = alpha * sp.rgb.y + (1.f - alpha) * S1;
-          S2 = alpha * sp.rgb.z + (1.f - alpha) * S2;
-          if (__fmul_rn(sp.co.w, G) < kAlphaMax) {
+          const float e0 = sp.rgb.x - S0, e1 = sp.rgb.y - S1, e2 = sp.rgb.z - S2;
+          const float dalpha = T * (e0 * g0 + e1 * g1 + e2 * g2);
+          S0 += alpha * e0;  // the light seen behind the splat in front
+          S1 += alpha * e1;
+          S2 += alpha * e2;
+          if (alpha < kAlphaMax) {  // not clamped
             v[5] = dalpha * G;
             const float dpow = dalpha * alpha;
-            v[0] = dpow * (sp.co.x * dx + sp.co.y * dy);
-            v[1] = dpow * (sp.co.z * dy + sp.co.y * dx);
-            v[2] = -0.5f * dpow * dx * dx;
-            v[3] = -dpow * dx * dy;
-            v[4] = -0.5f * dpow * dy * dy;
+            const float tx = dpow * dx, ty = dpow * dy;
+            v[0] = tx;  // the moments of dL/dpower; the conic is applied per splat
+            v[1] = ty;
+            v[2] = tx * dx;
+            v[3] = tx * dy;
+            v[4] = ty * dy;
           }
         }
       }
@@ -535,9 +563,12 @@ __device__ __forceinline__ void render_tile_bwd(const RasterArgs& a, int j, Spla
       const float* r = acc + 9 * threadIdx.x;
       if (r[0] != 0.f || r[1] != 0.f || r[2] != 0.f || r[3] != 0.f || r[4] != 0.f || r[5] != 0.f ||
           r[6] != 0.f || r[7] != 0.f || r[8] != 0.f) {
-        float* gp = grad2d + 12 * (size_t)__float_as_int(sm[threadIdx.x].rgb.w);
-        red_add_v4(gp, r[0], r[1], r[2], r[3]);
-        red_add_v4(gp + 4, r[4], r[5], r[6], r[7]);
+        const Splat& sq = sm[threadIdx.x];
+        float* gp = grad2d + 12 * (size_t)__float_as_int(sq.rgb.w);
+        float gc[5];
+        power_moments_to_grad(sq.co, r[0], r[1], r[2], r[3], r[4], gc);
+        red_add_v4(gp, gc[0], gc[1], gc[2], gc[3]);
+        red_add_v4(gp + 4, gc[4], r[5], r[6], r[7]);
         atomicAdd(gp + 8, r[8]);
       }
     }
@@ -652,19 +683,20 @@ __device__ __forceinline__ void render_piece_bwd_warp(const RasterArgs& a, int j
         v[6] += wgt * g0[u];
         v[7] += wgt * g1[u];
         v[8] += wgt * g2[u];
-        const float dalpha = T[u] * ((sp.rgb.x - S0[u]) * g0[u] + (sp.rgb.y - S1[u]) * g1[u] +
-                                     (sp.rgb.z - S2[u]) * g2[u]);
-        S0[u] = alpha * sp.rgb.x + (1.f - alpha) * S0[u];
-        S1[u] = alpha * sp.rgb.y + (1.f - alpha) * S1[u];
-        S2[u] = alpha * sp.rgb.z + (1.f - alpha) * S2[u];
-        if (__fmul_rn(sp.co.w, G) < kAlphaMax) {
+        const float e0 = sp.rgb.x - S0[u], e1 = sp.rgb.y - S1[u], e2 = sp.rgb.z - S2[u];
+        const float dalpha = T[u] * (e0 * g0[u] + e1 * g1[u] + e2 * g2[u]);
+        S0[u] += alpha * e0;  // the light seen behind the splat in front
+        S1[u] += alpha * e1;
+        S2[u] += alpha * e2;
+        if (alpha < kAlphaMax) {  // not clamped
           v[5] += dalpha * G;
           const float dpow = dalpha * alpha;
-          v[0] += dpow * (sp.co.x * dx + sp.co.y * dy);
-          v[1] += dpow * (sp.co.z * dy + sp.co.y * dx);
-          v[2] += -0.5f * dpow * dx * dx;
-          v[3] += -dpow * dx * dy;
-          v[4] += -0.5f * dpow * dy * dy;
+          const float tx = dpow * dx, ty = dpow * dy;
+          v[0] += tx;  // the moments of dL/dpower; the conic is applied per splat
+          v[1] += ty;
+          v[2] += tx * dx;
+          v[3] += tx * dy;
+          v[4] += ty * dy;
         }
       }
       if (!__any_sync(0xffffffffu, hit)) continue;
@@ -675,8 +707,15 @@ __device__ __forceinline__ void render_piece_bwd_warp(const RasterArgs& a, int j
       const float c2 = __shfl_down_sync(0xffffffffu, r8, 8);
       const float c3 = __shfl_down_sync(0xffffffffu, r8, 12);
       float* gp = grad2d + 12 * (size_t)__float_as_int(sp.rgb.w);
-      if (lane == 0 || lane == 16) red_add_v4(gp + (lane >> 2), r8, c1, c2, c3);
-      else if (lane == 1) atomicAdd(gp + 8, r9);
+      if (lane == 0) {
+        float gc[5];
+        power_moments_to_grad(sp.co, r8, c1, c2, c3, 0.f, gc);
+        red_add_v4(gp, gc[0], gc[1], gc[2], gc[3]);
+      } else if (lane == 16) {
+        red_add_v4(gp + 4, -0.5f * r8, c1, c2, c3);  // dL/dc from the dy^2 moment
+      } else if (lane == 1) {
+        atomicAdd(gp + 8, r9);
+      }
     }
   }
 }
@@ -684,7 +723,7 @@ __device__ __forceinline__ void render_piece_bwd_warp(const RasterArgs& a, int j
 constexpr int kBwdWarps = 4;  // pieces per block of the one-view split backward
 
 template <int PPL>
-__global__ void __launch_bounds__(32 * kBwdWarps) k_render_bwd_warp(RasterArgs a, const float* __restrict__ T_final,
+__global__ void __launch_bounds__(32 * kBwdWarps, PPL <= 3 ? 8 : 1) k_render_bwd_warp(RasterArgs a, const float* __restrict__ T_final,
                                                                    const int32_t* __restrict__ n_last,
                                                                    const float* __restrict__ dL_drgb,
                                                                    float* __restrict__ grad2d, Ckpt ck) {
@@ -744,7 +783,8 @@ __global__ void k_error_stats(RasterArgs a, const int32_t* __restrict__ n_last, 
         float alpha, G;
         if (splat_alpha(sp.co, dx, dy, alpha, G)) {
           const float w = alpha * T;
-          const float qf = sp.co.x * dx * dx + 2.f * sp.co.y * dx * dy + sp.co.z * dy * dy;
+          // a dx^2 + 2 b dx dy + c dy^2 = -2 power = -2 ln(2) p
+          const float qf = splat_pow2(sp.co, dx, dy) * kInvA;
           const float D = sqrtf(fmaxf(qf, 0.f));
           v0 = e * w;
           v1 = w;
@@ -882,6 +922,11 @@ static bool raster_args(const tgs_projected* proj, const int32_t* tile_ranges, c
 static int block_for(int n_pix_max) { return std::min(256, std::max(32, (n_pix_max + 31) / 32 * 32)); }
 
 
+// Whether the automatic choice may pick the split walk: measured slower than
+// the sequential walk at 500k Gaussians, 720 tiles of 85 pixels (0.085-0.089
+// against 0.067 ms), so only an explicit setting selects it.
+constexpr bool kSplitAuto = false;
+
 // The split forward's group count: 0 = chosen per launch (below), or fixed
 // at 1, 2 or 4 by tgs_set_forward_split (tuning and tests).
 static int g_fwd_split = 0;
@@ -893,6 +938,7 @@ static int split_groups(int n_active, int B) {
   const int wp = B / 32;  // 1..8
   const bool nw_ok[2] = {4 * B <= 1024, 2 * B <= 1024};
   if (g_fwd_split) return (g_fwd_split == 4 && !nw_ok[0]) || (g_fwd_split == 2 && !nw_ok[1]) ? 1 : g_fwd_split;
+  if (!kSplitAuto) return 1;
   static int per_sm[64][9][2] = {};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;

@@ -36,7 +36,10 @@ class Trainer:
     def __init__(self, params: dict, cam: dict, target: torch.Tensor, tile_fraction: float = 0.2,
                  pixel_rate: float = 1.0 / 3.0, cfg: Config | None = None, dense: bool = False,
                  capacity: int | None = None, seed: int = 0, bg=(0.0, 0.0, 0.0), sh_degree: int = 3,
-                 view: int = 0, train: bool = True, fuse_update: bool = True):
+                 view: int = 0, train: bool = True, fuse_update: bool = True, share: "Trainer | None" = None):
+        """share: another view's trainer of the same Gaussians whose optimiser
+        state (gradients, moments, step and iteration counters) this one uses,
+        so that steps of several views' trainers form one training run."""
         self.cfg = cfg or Config()
         self.fuse_update = fuse_update
         self.params = params
@@ -60,7 +63,9 @@ class Trainer:
         self.P_max = P
         # optimiser state (not needed for render-only use)
         self.train = train
-        if train:
+        if train and share is not None:
+            self.grads, self.m, self.v = share.grads, share.m, share.v
+        elif train:
             self.grads = zeros_like_params(params)
             self.m = zeros_like_params(params)
             self.v = zeros_like_params(params)
@@ -109,8 +114,11 @@ class Trainer:
             self.ws_adj = torch.empty(B.project_backward_multi_workspace_size(N), dtype=u8, device=dev)
             self.adj = B.MultiAdjoint([self.ccam], [self.proj["radius"]], [self.grad2d])
         # device-side counters (graph replays read them)
-        self.it_dev = torch.zeros(1, dtype=i64, device=dev)
-        self.step_dev = torch.ones(1, dtype=i32, device=dev)
+        if share is not None:
+            self.it_dev, self.step_dev = share.it_dev, share.step_dev
+        else:
+            self.it_dev = torch.zeros(1, dtype=i64, device=dev)
+            self.step_dev = torch.ones(1, dtype=i32, device=dev)
         self.graph = None
         o = self.cfg.opt
         self.opt = dict(lr=[o.lr_means, o.lr_scales, o.lr_quats, o.lr_opacity, o.lr_sh_dc, o.lr_sh_rest],
