@@ -96,6 +96,8 @@ def _declare(L):
     L.orc_project_backward.restype = _i32
     L.orc_loss.argtypes = [_i32, _i32, _i32, _p, _p, _p, _p, _p, _p, _d, _d, _d, _p, _p, _p, _p, _p, _p]
     L.orc_loss.restype = _i32
+    L.orc_loss_ssim.argtypes = [_i32, _i32, _i32, _p, _p, _p, _p, _p, _p, _d, _d, _p, _p, _p, _p, _p, _p]
+    L.orc_loss_ssim.restype = _i32
     L.orc_cholesky_solve.argtypes = [_p, _p, _p, _i32]
     L.orc_cholesky_solve.restype = _i32
     L.orc_hybrid_step.argtypes = [_i64, _p, _p, _p, _p, _p, _p, _i32, _i32, _i32, _p]
@@ -352,6 +354,33 @@ def loss(width, height, sel, rgb, target, err_f16_bits=None, age=None, lambda_in
     lib().orc_loss(width, height, A, _ptr(active), _ptr(off), _ptr(idx if idx.size else np.zeros(1, np.uint8)),
                    _ptr(rgb), _ptr(tgt), _ptr(lam_in), eps_c, eps_n, beta, _ptr(err), _ptr(ag),
                    _ptr(out["dL_drgb"]), _ptr(out["lam"]), _ptr(out["err"]), _ptr(out["loss"]))
+    out["lam"] = out["lam"][:A]
+    out["err"] = out["err"][:P]
+    out["loss"] = float(out["loss"][0])
+    out["err_map"] = err
+    out["age_map"] = ag
+    return out
+
+
+def loss_ssim(width, height, sel, rgb, target, err_f16_bits=None, age=None, lambda_in=None,
+              eps_c=EPS_CHARBONNIER, beta=BETA_EMA):
+    """The sparse loss with the SSIM structure term (Table 4's S-SSIM
+    variant); arguments and outputs as ``loss``."""
+    active = _c(sel["active_tiles"], np.int32)
+    off = _c(sel["pix_off"], np.int32)
+    idx = _c(sel["pix_idx"], np.uint8)
+    A = int(active.shape[0])
+    P = int(off[A])
+    rgb = _c(rgb, np.float64).reshape(-1, 3)
+    tgt = _c(target, np.float64)
+    err = None if err_f16_bits is None else np.array(err_f16_bits, dtype=np.uint16, copy=True)
+    ag = None if age is None else np.array(age, dtype=np.uint16, copy=True)
+    lam_in = _c(lambda_in, np.float64)
+    out = dict(dL_drgb=np.zeros((P, 3)), lam=np.zeros(max(A, 1)), err=np.zeros(max(P, 1)), loss=np.zeros(1))
+    lib().orc_loss_ssim(width, height, A, _ptr(active), _ptr(off),
+                        _ptr(idx if idx.size else np.zeros(1, np.uint8)), _ptr(rgb), _ptr(tgt), _ptr(lam_in),
+                        eps_c, beta, _ptr(err), _ptr(ag), _ptr(out["dL_drgb"]), _ptr(out["lam"]), _ptr(out["err"]),
+                        _ptr(out["loss"]))
     out["lam"] = out["lam"][:A]
     out["err"] = out["err"][:P]
     out["loss"] = float(out["loss"][0])

@@ -1100,6 +1100,126 @@ int orc_loss(int width, int height, int n_active, const int32_t* active_tiles, c
 }
 
 /* ------------------------------------------------------------------------ */
+/* sparse loss with the SSIM structure term (Sec. 4, Table 4: S-SSIM)       */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The ablation of Table 4 that replaces sparse NCC by sparse SSIM.  The paper
+ * names the variant only; this is its reading: the structure term of each
+ * active tile is SSIM (Wang et al. 2004, dynamic range 1: C1 = 0.01^2,
+ * C2 = 0.03^2) computed per colour channel from population moments over the
+ * tile's sampled pixels, as the sparse NCC is:
+ *   SSIM_c = (2 mx my + C1)(2 cov + C2) / ((mx^2 + my^2 + C1)(var_x + var_y + C2))
+ *   S-SSIM_tau = 1 - mean_c SSIM_c
+ *   lambda_tau = clip(mean_p |grad l1(p)|_1 / (mean_p g_s(p) + 1e-8), 0, 1),
+ *     g_s(p) = sum_c |n dSSIM_c/dx_p,c| (per-pixel scale, no 1/n, as for NCC)
+ *   L = (1/|P|) sum_p l1(p) + (1/A) sum_tau lambda_tau S-SSIM_tau, lambda fixed.
+ * With a1 = 2 mx my + C1, a2 = 2 cov + C2, b1 = mx^2 + my^2 + C1,
+ * b2 = var_x + var_y + C2 and SSIM = a1 a2 / (b1 b2), the derivative for one
+ * pixel's channel value x (dx = x - mx, dy = y - my) is
+ *   n dSSIM/dx = 2 ((my a2 + a1 dy) / (b1 b2) - SSIM (mx / b1 + dx / b2)).
+ * Everything else (Charbonnier L1, e, the error and age map updates, the
+ * arguments and outputs) is as orc_loss.
+ */
+int orc_loss_ssim(int width, int height, int n_active, const int32_t* active_tiles, const int32_t* pix_off,
+                  const uint8_t* pix_idx, const double* rgb, const double* target, const double* lambda_in,
+                  double eps_c, double beta, uint16_t* err_map, uint16_t* age_map, double* dL_drgb,
+                  double* lambda_out, double* err_pix, double* loss_out) {
+  const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;
+  int tx_n = (width + ORC_TILE - 1) / ORC_TILE;
+  int64_t P = pix_off[n_active];
+  double loss = 0.0;
+  for (int j = 0; j < n_active; ++j) {
+    int t = active_tiles[j];
+    int tx = t % tx_n, ty = t / tx_n;
+    int64_t s0 = pix_off[j], s1 = pix_off[j + 1];
+    int nn = (int)(s1 - s0);
+    if (nn <= 0) { lambda_out[j] = 0.0; continue; }
+    double mx[3] = {0, 0, 0}, my[3] = {0, 0, 0};
+    for (int64_t s = s0; s < s1; ++s) {
+      int l = pix_idx[s];
+      int x = tx * ORC_TILE + (l % ORC_TILE), y = ty * ORC_TILE + (l / ORC_TILE);
+      for (int c = 0; c < 3; ++c) {
+        mx[c] += rgb[3 * s + c];
+        my[c] += target[((int64_t)y * width + x) * 3 + c];
+      }
+    }
+    for (int c = 0; c < 3; ++c) { mx[c] /= nn; my[c] /= nn; }
+    double vx[3] = {0, 0, 0}, vy[3] = {0, 0, 0}, cv[3] = {0, 0, 0};
+    for (int64_t s = s0; s < s1; ++s) {
+      int l = pix_idx[s];
+      int x = tx * ORC_TILE + (l % ORC_TILE), y = ty * ORC_TILE + (l / ORC_TILE);
+      for (int c = 0; c < 3; ++c) {
+        double dx = rgb[3 * s + c] - mx[c], dy = target[((int64_t)y * width + x) * 3 + c] - my[c];
+        vx[c] += dx * dx; vy[c] += dy * dy; cv[c] += dx * dy;
+      }
+    }
+    double a1[3], a2[3], b1[3], b2[3], ss[3];
+    for (int c = 0; c < 3; ++c) {
+      vx[c] /= nn; vy[c] /= nn; cv[c] /= nn;
+      a1[c] = 2.0 * mx[c] * my[c] + C1;
+      a2[c] = 2.0 * cv[c] + C2;
+      b1[c] = mx[c] * mx[c] + my[c] * my[c] + C1;
+      b2[c] = vx[c] + vy[c] + C2;
+      ss[c] = a1[c] * a2[c] / (b1[c] * b2[c]);
+    }
+    double sum_g1 = 0.0, sum_gs = 0.0;
+    for (int64_t s = s0; s < s1; ++s) {
+      int l = pix_idx[s];
+      int x = tx * ORC_TILE + (l % ORC_TILE), y = ty * ORC_TILE + (l / ORC_TILE);
+      for (int c = 0; c < 3; ++c) {
+        double xv = rgb[3 * s + c], yv = target[((int64_t)y * width + x) * 3 + c];
+        double d = xv - yv;
+        sum_g1 += fabs(d / sqrt(d * d + eps_c * eps_c));
+        double gsn = 2.0 * ((my[c] * a2[c] + a1[c] * (yv - my[c])) / (b1[c] * b2[c]) -
+                            ss[c] * (mx[c] / b1[c] + (xv - mx[c]) / b2[c]));
+        sum_gs += fabs(gsn);
+      }
+    }
+    double lam = (sum_g1 / nn) / (sum_gs / nn + 1e-8);
+    lam = clampd(lam, 0.0, 1.0);
+    if (lambda_in) lam = lambda_in[j];
+    lambda_out[j] = lam;
+    loss += lam * (1.0 - (ss[0] + ss[1] + ss[2]) / 3.0) / n_active;
+    for (int64_t s = s0; s < s1; ++s) {
+      int l = pix_idx[s];
+      int x = tx * ORC_TILE + (l % ORC_TILE), y = ty * ORC_TILE + (l / ORC_TILE);
+      double e = 0.0;
+      for (int c = 0; c < 3; ++c) {
+        double xv = rgb[3 * s + c], yv = target[((int64_t)y * width + x) * 3 + c];
+        double d = xv - yv;
+        double r = sqrt(d * d + eps_c * eps_c);
+        loss += r / (double)P;
+        e += fabs(d);
+        double dss = 2.0 * ((my[c] * a2[c] + a1[c] * (yv - my[c])) / (b1[c] * b2[c]) -
+                            ss[c] * (mx[c] / b1[c] + (xv - mx[c]) / b2[c])) / nn;
+        dL_drgb[3 * s + c] = d / r / (double)P - lam / (3.0 * n_active) * dss;
+      }
+      err_pix[s] = e;
+    }
+  }
+  *loss_out = loss;
+  if (age_map) {
+    for (int64_t k = 0; k < (int64_t)width * height; ++k)
+      if (age_map[k] < 65535) age_map[k]++;
+  }
+  for (int j = 0; j < n_active; ++j) {
+    int t = active_tiles[j];
+    int tx = t % tx_n, ty = t / tx_n;
+    for (int64_t s = pix_off[j]; s < pix_off[j + 1]; ++s) {
+      int l = pix_idx[s];
+      int64_t k = (int64_t)(ty * ORC_TILE + l / ORC_TILE) * width + tx * ORC_TILE + (l % ORC_TILE);
+      if (err_map) {
+        double old = orc_half_to_double(err_map[k]);
+        err_map[k] = orc_double_to_half((1.0 - beta) * old + beta * err_pix[s]);
+      }
+      if (age_map) age_map[k] = 0;
+    }
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* hybrid solver: moment-damped LM blocks + Adam (Sec. 3.9, App. A)         */
 /* ------------------------------------------------------------------------ */
 

@@ -260,9 +260,27 @@ MUTATIONS = [
     ('score_d_by_e', 'test_oracle_density.py',
      'double d = r[2] / (r[1] + eps);',
      'double d = r[2] / (r[0] + eps);'),
+    ('ssim_cov_sign', 'test_oracle_ssim.py',
+     'a2[c] = 2.0 * cv[c] + C2;',
+     'a2[c] = -2.0 * cv[c] + C2;'),
+    ('ssim_C1', 'test_oracle_ssim.py',
+     'const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;',
+     'const double C1 = 0.03 * 0.03, C2 = 0.03 * 0.03;'),
+    ('ssim_C2', 'test_oracle_ssim.py',
+     'const double C1 = 0.01 * 0.01, C2 = 0.03 * 0.03;',
+     'const double C1 = 0.01 * 0.01, C2 = 0.01 * 0.01;'),
+    ('ssim_grad_factor', 'test_oracle_ssim.py',
+     'double dss = 2.0 * ((my[c] * a2[c]',
+     'double dss = 1.0 * ((my[c] * a2[c]'),
+    ('ssim_grad_b2', 'test_oracle_ssim.py',
+     'ss[c] * (mx[c] / b1[c] + (xv - mx[c]) / b2[c])) / nn;',
+     'ss[c] * (mx[c] / b1[c] + (xv - mx[c]) / b1[c])) / nn;'),
+    ('ssim_luminance_mean', 'test_oracle_ssim.py',
+     'b1[c] = mx[c] * mx[c] + my[c] * my[c] + C1;',
+     'b1[c] = 2.0 * mx[c] * my[c] + C1;'),
 ]
 
-DEFAULT = {"no_dilation", "T_stop", "stats_D", "bwd_dalpha", "ncc_sample_var", "ema_swap", "lm_damp",
+DEFAULT = {"ssim_cov_sign", "no_dilation", "T_stop", "stats_D", "bwd_dalpha", "ncc_sample_var", "ema_swap", "lm_damp",
            "split_floor", "hard_key_inv", "view_key_sign", "mlp_relu2", "feat_centre", "bwd_clamp_dz"}
 ALL = os.environ.get("TURBOGS_ALL_MUTATIONS") == "1"
 CASES = [m for m in MUTATIONS if ALL or m[0] in DEFAULT]
