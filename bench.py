@@ -361,32 +361,52 @@ def replica_throughput(total_ms: float, steps: int, world: int, dist=None, devic
     return world * steps / (tot.item() * 1e-3)
 
 
-def error_stats_time(tr, info, flush, clocks, peaks, reps: int = 5) -> dict:
-    """The error back-projection statistics of Sec. 3.8 (a pass after the
-    loss, not part of the timed step) on the step's sampled pixels: device ms
-    per call (events on the launch stream, L2 flushed before each) and its
-    FP32 rate (15 FLOPs for the alpha test + 12 for the weights and the
-    distance per (pixel, splat) walked)."""
+def error_stats_time(tr, info, flush, clocks, peaks, reps: int = 7) -> dict:
+    """The error back-projection statistics of Sec. 3.8 (Eq. 12) over the
+    step's sampled pixels, two ways: fused into the backward replay
+    (render_backward_sampled_stats: the backward's time with the sums less
+    its time without) and as the separate pass after the loss
+    (error_stats_sampled).  Device ms per call (events on the launch stream,
+    L2 flushed before each; median of reps)."""
     import torch
     from paper_2606_15924_gb300 import binding as B
     stats = torch.zeros(tr.n, 4, device=tr.params["means"].device)
     stream = torch.cuda.current_stream()
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ms = []
-    for _ in range(reps):
-        flush.fill_(1.0)
-        a.record(stream)
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ms = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return sorted(ms)[len(ms) // 2]
+
+    def separate():
         B.error_stats_sampled(tr.proj, tr.ranges, tr.vals, tr.active_tiles, tr.n_active, tr.n_select, tr.pix_off,
                               tr.pix_idx, tr.n_pix, tr.ccam, tr.n_last, tr.err_pix, stats, stream=stream)
-        b.record(stream)
-        b.synchronize()
-        ms.append(a.elapsed_time(b))
-    t = sorted(ms)[len(ms) // 2]
+
+    def plain():
+        B.render_backward_sampled(tr.proj, tr.ranges, tr.vals, tr.active_tiles, tr.n_active, tr.n_select,
+                                  tr.pix_off, tr.pix_idx, tr.n_pix, tr.ccam, tr.bg, tr.T_final, tr.n_last, tr.dL,
+                                  tr.grad2d, ckpt=tr.ckpt, stream=stream)
+
+    def fused():
+        B.render_backward_sampled_stats(tr.proj, tr.ranges, tr.vals, tr.active_tiles, tr.n_active, tr.n_select,
+                                        tr.pix_off, tr.pix_idx, tr.n_pix, tr.ccam, tr.bg, tr.T_final, tr.n_last,
+                                        tr.dL, tr.grad2d, tr.err_pix, stats, ckpt=tr.ckpt, stream=stream)
+    t_sep, t_plain, t_fused = timed(separate), timed(plain), timed(fused)
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     alu_peak = alu_peak_tflops(sm_mhz)
-    achieved = info["evals_per_step"] * 27 / (t * 1e-3) / 1e12
-    return {"ms": t, "bound": "alu", "achieved": achieved, "unit": "TFLOP/s", "frac": achieved / alu_peak,
-            "note": "Sec. 3.8 statistics over the step's sampled pixels; not in the timed step"}
+    achieved = info["evals_per_step"] * 27 / (t_sep * 1e-3) / 1e12
+    return {"fused_backward_ms": t_fused, "plain_backward_ms": t_plain, "fused_extra_ms": t_fused - t_plain,
+            "separate_pass_ms": t_sep, "separate_pass_roofline": {"bound": "alu", "achieved": achieved,
+                                                                  "unit": "TFLOP/s", "frac": achieved / alu_peak},
+            "note": "Sec. 3.8 statistics over the step's sampled pixels, fused into the backward replay or as the "
+                    "separate walk; not in the timed step"}
 
 
 VIEWS_V, VIEWS_K = 256, 10
@@ -637,6 +657,13 @@ def run_ours(args):
     e2e_v, h2d, d2h = e2e_replays(sampled, tgt_host, args.steps)
     res["e2e"] = {"value": e2e_v * world, "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
     res["mlp"] = mlp_bench(device, peaks)
+    if not args.no_batched:
+        del sampled, dense
+        torch.cuda.empty_cache()
+        sampled = dense = None
+        res["batched"] = batched_summary(batched_measure(argparse.Namespace(rate=args.rate, warmup=3, steps=5,
+                                                                            profile=False)))
+        torch.cuda.empty_cache()
     if not args.no_quality:
         from paper_2606_15924_gb300.quality import compare
         del sampled, dense
@@ -693,7 +720,25 @@ def batched_scene(device):
 
 def run_batched(args):
     """8 views per iteration in one persistent launch (forward and backward)
-    against one launch per view, both inside a captured graph."""
+    against one launch per view, both inside a captured graph (one JSON
+    line)."""
+    print(json.dumps(batched_measure(args)))
+
+
+def batched_summary(res: dict) -> dict:
+    """The batched workload's figures for the headline line."""
+    keep = ("iters_per_s", "ms_per_step", "views_per_step", "sampled_pixels", "render_fwd_ms", "render_bwd_ms",
+            "fwd_bwd_mpix_per_s", "grid")
+    out = {"workload": res["config"]["workload"], "speedup_vs_per_view": res["speedup_vs_per_view"]}
+    for arm in ("persistent", "per_view"):
+        a = res[arm]
+        out[arm] = {k: a[k] for k in keep}
+        out[arm]["render_fwd_roofline"] = a["render_fwd_roofline"]
+        out[arm]["stage_ms"] = a["stage_ms"]
+    return out
+
+
+def batched_measure(args):
     import torch
     from paper_2606_15924_gb300 import binding as B
     from paper_2606_15924_gb300.batched import MultiViewTrainer, autotune_grid
@@ -760,7 +805,7 @@ def run_batched(args):
                       "l2": "flushed between timed steps (256 MB write)"},
            "peak_source": peak_kind, **out,
            "speedup_vs_per_view": out["per_view"]["ms_per_step"] / out["persistent"]["ms_per_step"]}
-    print(json.dumps(res))
+    return res
 
 
 MLP_ROWS = 200 * 8487   # tile rows of a 200-view orbit at 1957x1091
@@ -906,6 +951,8 @@ def main():
                          "sampled training until it is within 0.1 dB of the dense PSNR (device time)")
     ap.add_argument("--dense-iters", type=int, default=2000)
     ap.add_argument("--no-quality", action="store_true", help="skip the equal-PSNR comparison in the default run")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched multi-view workload's summary in the default run")
     ap.add_argument("--mlp-rows", type=int, default=0,
                     help="only the tile-error MLP kernels on this many rows (for a small profile), one JSON line")
     ap.add_argument("--workload", default="step", choices=["step", "batched"],

@@ -387,6 +387,24 @@ tgs_status tgs_loss_sparse_ncc(const float* rgb, const float* target, int32_t wi
                                tgs_stream stream);
 
 /*
+ * loss_sparse_ssim - the same fused loss with the structure term of Table 4's
+ * S-SSIM variant in place of the sparse NCC (the paper names the variant
+ * only; this is its reading): per active tile and colour channel, SSIM
+ * (Wang et al. 2004, C1 = 0.01^2, C2 = 0.03^2) from population moments over
+ * the tile's sampled pixels, S-SSIM_tau = 1 - mean_c SSIM_c, weighted by the
+ * same clipped gradient ratio lambda_tau (with n dSSIM/dx in place of the NCC
+ * derivative).  params->eps_ncc is not used.  Everything else (Charbonnier L1,
+ * e, the error and age map updates, arguments, outputs, errors) is as
+ * loss_sparse_ncc.
+ */
+tgs_status tgs_loss_sparse_ssim(const float* rgb, const float* target, int32_t width, int32_t height,
+                                const int32_t* active_tiles, const int32_t* n_active, int32_t n_active_max,
+                                const int32_t* pix_off, const uint8_t* pix_idx, int32_t n_pix_max,
+                                const tgs_loss_params* params, uint16_t* err_map, uint16_t* age_map,
+                                float* dL_drgb, float* lambda_tile, float* err_pix, double* loss,
+                                tgs_stream stream);
+
+/*
  * error_stats_sampled - error back-projection statistics (Sec. 3.8, Eq. 12;
  * Alg. 1 step 11), a pass of its own after the loss.  For
  * every sampled pixel p and every splat k it blended (list positions below
@@ -444,6 +462,31 @@ tgs_status tgs_render_backward_sampled(const tgs_projected* proj, const int32_t*
                                        const tgs_camera* cam, const float* bg, const float* T_final,
                                        const int32_t* n_last, const float* dL_drgb, float* grad2d,
                                        int64_t n_gaussians, const tgs_checkpoints* ckpt, tgs_stream stream);
+
+/*
+ * render_backward_sampled_stats - render_backward_sampled, and in the same
+ * replay the error back-projection statistics of Sec. 3.8 (Eq. 12; Alg. 1
+ * step 11) over the same sampled pixels: for every splat a pixel blends with
+ * compositing weight w = T alpha, stats[i] += (e w, w, D w, 0), with e the
+ * pixel's error err_pix [P] (from loss_sparse_ncc) and D the conic
+ * Mahalanobis distance of the pixel centre from the splat.  The weights are
+ * the ones the backward recovers (T by division from the end of the walk),
+ * equal to the forward's up to rounding.  stats: device [N,4] float, 16-byte
+ * aligned, zeroed first unless accumulate_stats = 1 (so the views of a step
+ * and several steps can add up).  With checkpoints the sums ride on the
+ * warp-per-piece replay (one more 4-value warp reduction and one vector
+ * atomic per warp and splat); without, error_stats_sampled runs after the
+ * whole-tile backward.  Other arguments and results as
+ * render_backward_sampled.
+ */
+tgs_status tgs_render_backward_sampled_stats(const tgs_projected* proj, const int32_t* tile_ranges,
+                                             const int32_t* vals, const int32_t* active_tiles,
+                                             const int32_t* n_active, int32_t n_active_max, const int32_t* pix_off,
+                                             const uint8_t* pix_idx, int32_t n_pix_max, const tgs_camera* cam,
+                                             const float* bg, const float* T_final, const int32_t* n_last,
+                                             const float* dL_drgb, float* grad2d, int64_t n_gaussians,
+                                             const tgs_checkpoints* ckpt, const float* err_pix, float* stats,
+                                             int32_t accumulate_stats, tgs_stream stream);
 
 /*
  * project_backward - the projection adjoint alone (the second half of
@@ -549,6 +592,15 @@ tgs_status tgs_render_sampled_batched(const tgs_view_batch* views, int32_t n_vie
                                       int32_t* counter, tgs_stream stream);
 tgs_status tgs_render_backward_batched(const tgs_view_batch* views, int32_t n_views, int32_t grid_ctas,
                                        int32_t* counter, tgs_stream stream);
+/* The batched backward with Eq. 12's statistics over the sampled pixels of
+ * every view of the batch (Sec. 3.8: the sums run over the views and pixels
+ * of the iteration), as render_backward_sampled_stats does for one view.
+ * err_pix: host array [n_views] of device pointers to each view's per-pixel
+ * errors; stats: device [n_gaussians,4] float shared by the views, 16-byte
+ * aligned, zeroed first unless accumulate_stats = 1. */
+tgs_status tgs_render_backward_batched_stats(const tgs_view_batch* views, int32_t n_views, int32_t grid_ctas,
+                                             int32_t* counter, const float* const* err_pix, float* stats,
+                                             int64_t n_gaussians, int32_t accumulate_stats, tgs_stream stream);
 
 /*
  * hybrid_step - moment-damped LM / Adam update (Sec. 3.9, Eq. 14; App. A;

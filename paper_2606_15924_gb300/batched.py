@@ -43,7 +43,7 @@ class MultiViewTrainer:
                  pixel_rate: float = 1.0 / 3.0, cfg: Config | None = None, seed: int = 0, bg=(0.0, 0.0, 0.0),
                  sh_degree: int = 3, view_ids: list | None = None, grid: tuple | None = None,
                  view_rows: bool | None = None, persistent: bool = True, checkpoints: bool | None = None,
-                 max_active: int | None = None):
+                 max_active: int | None = None, stats: bool = False):
         if not cams or len(cams) != len(targets) or len(cams) != len(tile_fractions):
             raise ValueError("one target and one tile fraction per view")
         # views trained together (one batch of the persistent launches)
@@ -74,6 +74,10 @@ class MultiViewTrainer:
         self.m = zeros_like_params(params)
         self.v = zeros_like_params(params)
         self.touched = torch.zeros(self.n, dtype=torch.uint8, device=dev)
+        # Eq. 12's statistics over the views' sampled pixels, accumulated step after step (persistent launch)
+        if stats and not persistent:
+            raise ValueError("the statistics ride on the persistent backward")
+        self.stats = torch.zeros(self.n, 4, device=dev) if stats else None
         self.ws_hybrid = torch.empty(B.hybrid_step_workspace_size(self.n), dtype=torch.uint8, device=dev)
         self.ws_adj = torch.empty(B.project_backward_multi_workspace_size(self.n), dtype=torch.uint8, device=dev)
         o = self.cfg.opt
@@ -173,8 +177,16 @@ class MultiViewTrainer:
             for k, v in enumerate(self.views):
                 B.render_sampled_batched(self.fwd_single[k], max(1, v.n_select), self.counters[2 + k:3 + k])
 
+    def reset_stats(self):
+        """Zeroes the accumulated statistics (after a density-control step)."""
+        if self.stats is not None:
+            self.stats.zero_()
+
     def _render_bwd(self):
-        if self.persistent:
+        if self.persistent and self.stats is not None:
+            B.render_backward_batched_stats(self.bwd_batch, self.grid[1], self.counters[1:2],
+                                            [v.err_pix for v in self.views], self.stats, accumulate=True)
+        elif self.persistent:
             B.render_backward_batched(self.bwd_batch, self.grid[1], self.counters[1:2])
         else:
             for k, v in enumerate(self.views):

@@ -132,6 +132,9 @@ _lib.tgs_render_sampled.argtypes = [_P(Projected), _p, _p, _p, _p, _i32, _p, _p,
 _lib.tgs_loss_sparse_ncc.restype = _i32
 _lib.tgs_loss_sparse_ncc.argtypes = [_p, _p, _i32, _i32, _p, _p, _i32, _p, _p, _i32, _P(LossParams), _p, _p, _p,
                                      _p, _p, _p, _p]
+_lib.tgs_loss_sparse_ssim.restype = _i32
+_lib.tgs_loss_sparse_ssim.argtypes = [_p, _p, _i32, _i32, _p, _p, _i32, _p, _p, _i32, _P(LossParams), _p, _p, _p,
+                                     _p, _p, _p, _p]
 _lib.tgs_backward_sampled.restype = _i32
 _lib.tgs_backward_sampled.argtypes = [_P(Gaussians), _P(Camera), _P(Projected), _p, _p, _p, _p, _i32, _p, _p,
                                       _i32, _p, _p, _p, _p, _p, _P(ParamPtrs), _p, _i32, _P(Checkpoints), _p]
@@ -141,6 +144,9 @@ _lib.tgs_error_stats_sampled.argtypes = [_P(Projected), _p, _p, _p, _p, _i32, _p
                                          _i64, _i32, _p]
 _lib.tgs_render_backward_sampled.argtypes = [_P(Projected), _p, _p, _p, _p, _i32, _p, _p, _i32, _P(Camera), _p, _p,
                                              _p, _p, _p, _i64, _P(Checkpoints), _p]
+_lib.tgs_render_backward_sampled_stats.restype = _i32
+_lib.tgs_render_backward_sampled_stats.argtypes = [_P(Projected), _p, _p, _p, _p, _i32, _p, _p, _i32, _P(Camera), _p,
+                                                   _p, _p, _p, _p, _i64, _P(Checkpoints), _p, _p, _i32, _p]
 _lib.tgs_project_backward.restype = _i32
 _lib.tgs_project_backward.argtypes = [_P(Gaussians), _P(Camera), _P(Projected), _p, _P(ParamPtrs), _p, _i32, _i32,
                                       _p, _p]
@@ -158,6 +164,8 @@ _lib.tgs_render_sampled_batched.restype = _i32
 _lib.tgs_render_sampled_batched.argtypes = [_P(ViewBatch), _i32, _i32, _p, _p]
 _lib.tgs_render_backward_batched.restype = _i32
 _lib.tgs_render_backward_batched.argtypes = [_P(ViewBatch), _i32, _i32, _p, _p]
+_lib.tgs_render_backward_batched_stats.restype = _i32
+_lib.tgs_render_backward_batched_stats.argtypes = [_P(ViewBatch), _i32, _i32, _p, _P(_p), _p, _i64, _i32, _p]
 _lib.tgs_hybrid_step.restype = _i32
 _lib.tgs_hybrid_step_workspace_size.restype = _sz
 _lib.tgs_hybrid_step_workspace_size.argtypes = [_i64]
@@ -193,11 +201,11 @@ EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_devi
             "tgs_select_tiles_workspace_size", "tgs_select_tiles", "tgs_select_tiles_noalloc",
             "tgs_project_gaussians",
             "tgs_bin_tiles_workspace_size", "tgs_bin_tiles", "tgs_checkpoint_bytes", "tgs_set_forward_split", "tgs_render_sampled",
-            "tgs_loss_sparse_ncc",
-            "tgs_backward_sampled", "tgs_render_backward_sampled", "tgs_error_stats_sampled", "tgs_project_backward", "tgs_project_backward_multi_workspace_size",
+            "tgs_loss_sparse_ncc", "tgs_loss_sparse_ssim",
+            "tgs_backward_sampled", "tgs_render_backward_sampled", "tgs_render_backward_sampled_stats", "tgs_error_stats_sampled", "tgs_project_backward", "tgs_project_backward_multi_workspace_size",
             "tgs_project_backward_multi", "tgs_project_backward_update",
             "tgs_render_batched_resident", "tgs_render_sampled_batched",
-            "tgs_render_backward_batched", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step",
+            "tgs_render_backward_batched", "tgs_render_backward_batched_stats", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step",
             "tgs_mlp_param_count", "tgs_mlp_forward", "tgs_mlp_forward_tc", "tgs_mlp_tc_wait_drill", "tgs_mlp_backward_workspace_size",
             "tgs_mlp_backward",
             "tgs_mlp_adam", "tgs_tile_observe", "tgs_tile_features", "tgs_tile_refresh",
@@ -354,15 +362,26 @@ def render_sampled(proj: dict, tile_ranges, vals, active_tiles, n_active, n_acti
 
 
 def loss_sparse_ncc(rgb, target, width, height, active_tiles, n_active, n_active_max, pix_off, pix_idx, n_pix_max,
-                    loss_params, err_map, age_map, dL_drgb, lambda_tile, err_pix, loss, stream=None):
+                    loss_params, err_map, age_map, dL_drgb, lambda_tile, err_pix, loss, stream=None, structure="ncc"):
+    """The fused sparse loss; structure="ssim" takes the S-SSIM variant
+    (tgs_loss_sparse_ssim) in place of the sparse NCC term."""
     vals = [float(v) for v in loss_params]
     if len(vals) == 3:
         vals.append(1.0)  # one view
     lp = LossParams(*vals)
-    _check("tgs_loss_sparse_ncc", _lib.tgs_loss_sparse_ncc(
+    name = {"ncc": "tgs_loss_sparse_ncc", "ssim": "tgs_loss_sparse_ssim"}[structure]
+    _check(name, getattr(_lib, name)(
         _ptr(rgb), _ptr(target), int(width), int(height), _ptr(active_tiles), _ptr(n_active), int(n_active_max),
         _ptr(pix_off), _ptr(pix_idx), int(n_pix_max), C.byref(lp), _ptr(err_map), _ptr(age_map), _ptr(dL_drgb),
         _ptr(lambda_tile), _ptr(err_pix), _ptr(loss), _stream(stream)))
+
+
+def loss_sparse_ssim(rgb, target, width, height, active_tiles, n_active, n_active_max, pix_off, pix_idx, n_pix_max,
+                     loss_params, err_map, age_map, dL_drgb, lambda_tile, err_pix, loss, stream=None):
+    """The fused sparse loss with Table 4's S-SSIM structure term."""
+    loss_sparse_ncc(rgb, target, width, height, active_tiles, n_active, n_active_max, pix_off, pix_idx, n_pix_max,
+                    loss_params, err_map, age_map, dL_drgb, lambda_tile, err_pix, loss, stream=stream,
+                    structure="ssim")
 
 
 def backward_sampled(g: dict, cam, proj: dict, tile_ranges, vals, active_tiles, n_active, n_active_max, pix_off,
@@ -377,6 +396,21 @@ def backward_sampled(g: dict, cam, proj: dict, tile_ranges, vals, active_tiles, 
         C.byref(gs), C.byref(cc), C.byref(pr), _ptr(tile_ranges), _ptr(vals), _ptr(active_tiles), _ptr(n_active),
         int(n_active_max), _ptr(pix_off), _ptr(pix_idx), int(n_pix_max), bgv, _ptr(T_final), _ptr(n_last),
         _ptr(dL_drgb), _ptr(grad2d), C.byref(gp), _ptr(touched), 1 if write_untouched else 0, _ck(ckpt),
+        _stream(stream)))
+
+
+def render_backward_sampled_stats(proj: dict, tile_ranges, vals, active_tiles, n_active, n_active_max, pix_off,
+                                  pix_idx, n_pix_max, cam, bg, T_final, n_last, dL_drgb, grad2d, err_pix, stats,
+                                  accumulate=False, stream=None, ckpt=None):
+    """render_backward_sampled plus Eq. 12's statistics of the same pixels
+    into stats [N,4] (zeroed first unless accumulate)."""
+    pr = projected(proj)
+    cc = cam if isinstance(cam, Camera) else camera(cam)
+    bgv = (C.c_float * 3)(*[float(b) for b in bg])
+    _check("tgs_render_backward_sampled_stats", _lib.tgs_render_backward_sampled_stats(
+        C.byref(pr), _ptr(tile_ranges), _ptr(vals), _ptr(active_tiles), _ptr(n_active), int(n_active_max),
+        _ptr(pix_off), _ptr(pix_idx), int(n_pix_max), C.byref(cc), bgv, _ptr(T_final), _ptr(n_last), _ptr(dL_drgb),
+        _ptr(grad2d), int(grad2d.shape[0]), _ck(ckpt), _ptr(err_pix), _ptr(stats), 1 if accumulate else 0,
         _stream(stream)))
 
 
@@ -478,6 +512,16 @@ def render_sampled_batched(views, grid_ctas, counter, stream=None):
     arr = views if isinstance(views, C.Array) else view_batch(views)
     _check("tgs_render_sampled_batched", _lib.tgs_render_sampled_batched(arr, len(arr), int(grid_ctas),
                                                                            _ptr(counter), _stream(stream)))
+
+
+def render_backward_batched_stats(views, grid_ctas, counter, err_pix: list, stats, accumulate=False, stream=None):
+    """The batched backward with Eq. 12's statistics of every view's sampled
+    pixels into stats [N,4] (zeroed first unless accumulate)."""
+    arr = views if isinstance(views, C.Array) else view_batch(views)
+    errs = (_p * len(arr))(*[_ptr(e) for e in err_pix])
+    _check("tgs_render_backward_batched_stats", _lib.tgs_render_backward_batched_stats(
+        arr, len(arr), int(grid_ctas), _ptr(counter), errs, _ptr(stats), int(stats.shape[0]), 1 if accumulate else 0,
+        _stream(stream)))
 
 
 def render_backward_batched(views, grid_ctas, counter, stream=None):

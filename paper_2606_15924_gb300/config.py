@@ -31,6 +31,7 @@ class LossConfig:
     eps_charbonnier: float = 1e-3   # App. A, Charbonnier epsilon (value not given)
     eps_ncc: float = 1e-8           # App. A, NCC epsilon (value not given)
     beta_ema: float = 0.4           # Table 6, EMA blending ratio of pixel errors
+    structure: str = "ncc"          # "ncc" (Sec. 3.7) or "ssim" (Table 4's S-SSIM variant)
 
 
 @dataclass

@@ -1,5 +1,6 @@
 // Fused sparse supervision (Sec. 3.7, Eqs. 9-11; App. A): Charbonnier L1,
-// tile-level sparse NCC with the gradient-balanced weight, the per-pixel error
+// tile-level sparse NCC (or, for Table 4's S-SSIM variant, SSIM) with the
+// gradient-balanced weight, the per-pixel error
 // of Eq. 2 and the error/age map updates of Eqs. 3-4.  One thread block per
 // active tile, one thread per sampled pixel; tile moments are two-pass block
 // reductions.
@@ -43,6 +44,13 @@ struct LossArgs {
   double* loss;
 };
 
+// SSIM constants (Wang et al. 2004, dynamic range 1) of the S-SSIM variant.
+constexpr float kC1 = 1e-4f, kC2 = 9e-4f;
+
+// STRUCT 0: the sparse NCC term (Sec. 3.7); 1: the SSIM term of Table 4's
+// S-SSIM variant, per channel from the same tile moments:
+// SSIM = (2 mx my + C1)(2 cov + C2) / ((mx^2 + my^2 + C1)(var_x + var_y + C2)).
+template <int STRUCT>
 __global__ void k_loss(LossArgs a) {
   __shared__ float sm[8][9];
   const int j = blockIdx.x;
@@ -87,14 +95,26 @@ __global__ void k_loss(LossArgs a) {
   float mom[9] = {dx[0] * dx[0], dx[1] * dx[1], dx[2] * dx[2], dy[0] * dy[0], dy[1] * dy[1],
                   dy[2] * dy[2], dx[0] * dy[0], dx[1] * dy[1], dx[2] * dy[2]};
   block_sum<9>(mom, sm);
-  float vy[3], D[3], ncc[3];
+  // NCC: D = sqrt(var_x var_y + eps), ncc = cov / D.  SSIM: ncc holds SSIM,
+  // q1 = 1 / (b1 b2), q2 = mx / b1, D = b2 (a1, a2, b1, b2 as in the SSIM formula)
+  float vy[3], D[3], ncc[3], a1[3], a2[3], q1[3], q2[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const float vx = mom[c] * inv_n;
     vy[c] = mom[3 + c] * inv_n;
     const float cv = mom[6 + c] * inv_n;
-    D[c] = sqrtf(vx * vy[c] + a.eps_n);
-    ncc[c] = cv / D[c];
+    if (STRUCT == 0) {
+      D[c] = sqrtf(vx * vy[c] + a.eps_n);
+      ncc[c] = cv / D[c];
+    } else {
+      a1[c] = 2.f * mx[c] * my[c] + kC1;
+      a2[c] = 2.f * cv + kC2;
+      const float b1 = mx[c] * mx[c] + my[c] * my[c] + kC1;
+      D[c] = vx + vy[c] + kC2;
+      q1[c] = 1.f / (b1 * D[c]);
+      q2[c] = mx[c] / b1;
+      ncc[c] = a1[c] * a2[c] * q1[c];
+    }
   }
   // per-pixel gradients of both terms and the balancing weight
   float d1[3], dn[3], l1 = 0.f, e = 0.f;
@@ -104,7 +124,10 @@ __global__ void k_loss(LossArgs a) {
     const float d = x[c] - y[c];
     const float r = sqrtf(d * d + a.eps_c2);
     d1[c] = d / r;                                             // dl1/dx
-    dn[c] = (dy[c] - ncc[c] * vy[c] * dx[c] / D[c]) / D[c];    // n dNCC_c/dx
+    if (STRUCT == 0)
+      dn[c] = (dy[c] - ncc[c] * vy[c] * dx[c] / D[c]) / D[c];  // n dNCC_c/dx
+    else                                                        // n dSSIM_c/dx
+      dn[c] = 2.f * ((my[c] * a2[c] + a1[c] * dy[c]) * q1[c] - ncc[c] * (q2[c] + dx[c] / D[c]));
     if (on) {
       l1 += r;
       e += fabsf(d);
@@ -162,12 +185,11 @@ __global__ void k_age_inc(uint16_t* __restrict__ age, int64_t n) {
 
 using namespace tgs;
 
-extern "C" tgs_status tgs_loss_sparse_ncc(const float* rgb, const float* target, int32_t width, int32_t height,
-                                          const int32_t* active_tiles, const int32_t* n_active,
-                                          int32_t n_active_max, const int32_t* pix_off, const uint8_t* pix_idx,
-                                          int32_t n_pix_max, const tgs_loss_params* params, uint16_t* err_map,
-                                          uint16_t* age_map, float* dL_drgb, float* lambda_tile, float* err_pix,
-                                          double* loss, tgs_stream stream) {
+static tgs_status loss_impl(int structure, const float* rgb, const float* target, int32_t width, int32_t height,
+                            const int32_t* active_tiles, const int32_t* n_active, int32_t n_active_max,
+                            const int32_t* pix_off, const uint8_t* pix_idx, int32_t n_pix_max,
+                            const tgs_loss_params* params, uint16_t* err_map, uint16_t* age_map, float* dL_drgb,
+                            float* lambda_tile, float* err_pix, double* loss, tgs_stream stream) {
   if (!rgb || !target || width <= 0 || height <= 0 || !n_active || n_active_max < 0 || !pix_off || !pix_idx ||
       n_pix_max < 1 || n_pix_max > 256 || !params || !dL_drgb || !lambda_tile || !err_pix || !loss)
     return TGS_ERR_INVALID_ARG;
@@ -194,7 +216,28 @@ extern "C" tgs_status tgs_loss_sparse_ncc(const float* rgb, const float* target,
     a.err_map = err_map; a.age_map = age_map; a.dL = dL_drgb; a.lambda = lambda_tile; a.err_pix = err_pix;
     a.loss = loss;
     const int B = std::min(256, std::max(32, (n_pix_max + 31) / 32 * 32));
-    k_loss<<<n_active_max, B, 0, s>>>(a);
+    if (structure == 0) k_loss<0><<<n_active_max, B, 0, s>>>(a);
+    else k_loss<1><<<n_active_max, B, 0, s>>>(a);
   }
   return check_launch();
+}
+
+extern "C" tgs_status tgs_loss_sparse_ncc(const float* rgb, const float* target, int32_t width, int32_t height,
+                                          const int32_t* active_tiles, const int32_t* n_active,
+                                          int32_t n_active_max, const int32_t* pix_off, const uint8_t* pix_idx,
+                                          int32_t n_pix_max, const tgs_loss_params* params, uint16_t* err_map,
+                                          uint16_t* age_map, float* dL_drgb, float* lambda_tile, float* err_pix,
+                                          double* loss, tgs_stream stream) {
+  return loss_impl(0, rgb, target, width, height, active_tiles, n_active, n_active_max, pix_off, pix_idx,
+                   n_pix_max, params, err_map, age_map, dL_drgb, lambda_tile, err_pix, loss, stream);
+}
+
+extern "C" tgs_status tgs_loss_sparse_ssim(const float* rgb, const float* target, int32_t width, int32_t height,
+                                           const int32_t* active_tiles, const int32_t* n_active,
+                                           int32_t n_active_max, const int32_t* pix_off, const uint8_t* pix_idx,
+                                           int32_t n_pix_max, const tgs_loss_params* params, uint16_t* err_map,
+                                           uint16_t* age_map, float* dL_drgb, float* lambda_tile, float* err_pix,
+                                           double* loss, tgs_stream stream) {
+  return loss_impl(1, rgb, target, width, height, active_tiles, n_active, n_active_max, pix_off, pix_idx,
+                   n_pix_max, params, err_map, age_map, dL_drgb, lambda_tile, err_pix, loss, stream);
 }

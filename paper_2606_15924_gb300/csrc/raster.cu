@@ -56,6 +56,14 @@ __device__ __forceinline__ float splat_pow2(const float4& co, float dx, float dy
 
 // alpha of a splat at offset (dx, dy) from its centre; G receives exp(power).
 // Returns false when the splat is skipped (power > 0 or alpha < 1/255).
+__device__ __forceinline__ bool splat_alpha_p(const float4& co, float dx, float dy, float& alpha, float& G, float& p) {
+  p = splat_pow2(co, dx, dy);
+  if (p > 0.f) return false;
+  G = ex2_approx(p);
+  alpha = fminf(kAlphaMax, __fmul_rn(co.w, G));
+  return alpha >= kAlphaMin;
+}
+
 __device__ __forceinline__ bool splat_alpha(const float4& co, float dx, float dy, float& alpha, float& G) {
   const float p = splat_pow2(co, dx, dy);
   if (p > 0.f) return false;
@@ -461,6 +469,36 @@ __device__ __forceinline__ float warp_reduce_scatter8(const float (&v)[9], int l
   return c;
 }
 
+// Sum of v[0..3] over the warp, scattered: lane l ends with the total of
+// v[(l >> 3) & 3] (halving exchanges at distances 16 and 8, then a butterfly
+// over the last three bits): 6 shuffles.
+__device__ __forceinline__ float warp_reduce_scatter4(const float (&v)[4], int lane) {
+  float b2[2];
+  {
+    const bool up = lane & 16;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float send = up ? v[k] : v[2 + k];
+      const float keep = up ? v[2 + k] : v[k];
+      b2[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+  }
+  const bool up = lane & 8;
+  float c = (up ? b2[1] : b2[0]) + __shfl_xor_sync(0xffffffffu, up ? b2[0] : b2[1], 8);
+  c += __shfl_xor_sync(0xffffffffu, c, 4);
+  c += __shfl_xor_sync(0xffffffffu, c, 2);
+  c += __shfl_xor_sync(0xffffffffu, c, 1);
+  return c;
+}
+
+// Where the backward also accumulates the error back-projection statistics of
+// Sec. 3.8 (Eq. 12): the per-pixel error e (from the loss) and the per-
+// Gaussian rows (E, W, D, 0) they are added to.
+struct StatsK {
+  const float* err;
+  float4* stats;
+};
+
 // Per-splat adjoints of a batch are summed over the block in shared memory
 // (acc, 9 floats per batch slot) and flushed once per block and splat with
 // vector atomics, instead of once per warp and splat.
@@ -595,12 +633,17 @@ __global__ void k_render_bwd(RasterArgs a, const float* __restrict__ T_final, co
 // totals go straight to the Gaussian's gradient row (two vector atomics and
 // one scalar).  Warps never wait on each other: each stages its splats, one
 // per lane, in its own slice of shared memory (sm, 32 entries).
-template <int PPL>
+//
+// STATS: the same replay also sums, per splat, Eq. 12's e w, w and D w over
+// the pixels (w = T alpha the compositing weight, e the pixel's error, D the
+// conic Mahalanobis distance of the pixel centre) into its statistics row.
+template <int PPL, bool STATS>
 __device__ __forceinline__ void render_piece_bwd_warp(const RasterArgs& a, int j, int c, Splat* sm,
                                                       const float* __restrict__ T_final,
                                                       const int32_t* __restrict__ n_last,
                                                       const float* __restrict__ dL_drgb,
-                                                      float* __restrict__ grad2d, const Ckpt& ck) {
+                                                      float* __restrict__ grad2d, const Ckpt& ck,
+                                                      const StatsK st = StatsK{nullptr, nullptr}) {
   constexpr int E = kCkptEvery;
   const int lane = threadIdx.x & 31;
   const int t = a.active_tiles ? a.active_tiles[j] : j;
@@ -623,6 +666,7 @@ __device__ __forceinline__ void render_piece_bwd_warp(const RasterArgs& a, int j
   const int hi_pos = c < ck.n_slots ? min(lo_pos + E, max_last) : max_last;
   if (hi_pos <= lo_pos) return;  // warp-uniform: nothing blended here
   float px[PPL], py[PPL], T[PPL], g0[PPL], g1[PPL], g2[PPL], S0[PPL], S1[PPL], S2[PPL];
+  float ep[STATS ? PPL : 1];
   int last[PPL];
   int warp_last = 0;
 #pragma unroll
@@ -633,6 +677,7 @@ __device__ __forceinline__ void render_piece_bwd_warp(const RasterArgs& a, int j
     px[u] = py[u] = 0.f;
     T[u] = 1.f;
     g0[u] = g1[u] = g2[u] = 0.f;
+    if (STATS) ep[u] = last[u] > 0 ? st.err[s] : 0.f;
     S0[u] = a.bg[0];
     S1[u] = a.bg[1];
     S2[u] = a.bg[2];
@@ -670,16 +715,24 @@ __device__ __forceinline__ void render_piece_bwd_warp(const RasterArgs& a, int j
       const Splat sp = sm[q];
       const int pos = lo + q - range.x;  // position in the tile list
       float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float sv[4] = {0.f, 0.f, 0.f, 0.f};
       bool hit = false;
 #pragma unroll
       for (int u = 0; u < PPL; ++u) {
         if (pos >= last[u]) continue;
         const float dx = __fsub_rn(px[u], sp.xy.x), dy = __fsub_rn(py[u], sp.xy.y);
-        float alpha, G;
-        if (!splat_alpha(sp.co, dx, dy, alpha, G)) continue;
+        float alpha, G, pw;
+        if (!splat_alpha_p(sp.co, dx, dy, alpha, G, pw)) continue;
         hit = true;
         T[u] = __fdividef(T[u], 1.f - alpha);  // transmittance in front of this splat (1 - alpha >= 0.01)
         const float wgt = alpha * T[u];
+        if (STATS) {
+          // a dx^2 + 2 b dx dy + c dy^2 = -2 power = -2 ln(2) p
+          const float D = sqrtf(fmaxf(pw * kInvA, 0.f));
+          sv[0] += ep[u] * wgt;
+          sv[1] += wgt;
+          sv[2] += D * wgt;
+        }
         v[6] += wgt * g0[u];
         v[7] += wgt * g1[u];
         v[8] += wgt * g2[u];
@@ -716,24 +769,29 @@ __device__ __forceinline__ void render_piece_bwd_warp(const RasterArgs& a, int j
       } else if (lane == 1) {
         atomicAdd(gp + 8, r9);
       }
+      if (STATS) {
+        const float rs = warp_reduce_scatter4(sv, lane);  // lane 8 k + (0..7): statistic k
+        const float s1 = __shfl_down_sync(0xffffffffu, rs, 8);
+        const float s2 = __shfl_down_sync(0xffffffffu, rs, 16);
+        if (lane == 0) red_add_v4(reinterpret_cast<float*>(st.stats + __float_as_int(sp.rgb.w)), rs, s1, s2, 0.f);
+      }
     }
   }
 }
 
 constexpr int kBwdWarps = 4;  // pieces per block of the one-view split backward
 
-template <int PPL>
-__global__ void __launch_bounds__(32 * kBwdWarps, PPL <= 3 ? 8 : 1) k_render_bwd_warp(RasterArgs a, const float* __restrict__ T_final,
-                                                                   const int32_t* __restrict__ n_last,
-                                                                   const float* __restrict__ dL_drgb,
-                                                                   float* __restrict__ grad2d, Ckpt ck) {
+template <int PPL, bool STATS>
+__global__ void __launch_bounds__(32 * kBwdWarps, PPL <= 3 ? 8 : 1)
+    k_render_bwd_warp(RasterArgs a, const float* __restrict__ T_final, const int32_t* __restrict__ n_last,
+                      const float* __restrict__ dL_drgb, float* __restrict__ grad2d, Ckpt ck, StatsK st) {
   __shared__ Splat sm[kBwdWarps][32];
   const int j = blockIdx.x;
   if (j >= *a.n_active) return;
   const int w = threadIdx.x >> 5;
   const int c = blockIdx.y * kBwdWarps + w;
   if (c > ck.n_slots) return;  // warp-uniform; the kernel has no block-wide barrier
-  render_piece_bwd_warp<PPL>(a, j, c, sm[w], T_final, n_last, dL_drgb, grad2d, ck);
+  render_piece_bwd_warp<PPL, STATS>(a, j, c, sm[w], T_final, n_last, dL_drgb, grad2d, ck, st);
 }
 
 // Error back-projection statistics (Sec. 3.8, Eq. 12): one
@@ -820,6 +878,8 @@ struct BatchArgs {
   const float* dL[kMaxViews];
   float* grad2d[kMaxViews];
   Ckpt ck[kMaxViews];
+  const float* err[kMaxViews];  // per-pixel errors, when the statistics are accumulated
+  float4* stats;                // [N] (E, W, D, 0) rows shared by the views
 };
 
 __device__ __forceinline__ bool next_item(const BatchArgs& b, int* counter, int* s_item, int& v, int& j) {
@@ -874,7 +934,7 @@ __global__ void k_render_bwd_batched(BatchArgs b, int* __restrict__ counter) {
 constexpr int kPieceClaim = 4;
 constexpr int kBatchBwdWarps = 4;
 
-template <int PPL>
+template <int PPL, bool STATS>
 __global__ void __launch_bounds__(32 * kBatchBwdWarps) k_render_bwd_batched_warp(BatchArgs b,
                                                                                 int* __restrict__ counter) {
   __shared__ Splat sm[kBatchBwdWarps][32];
@@ -891,7 +951,8 @@ __global__ void __launch_bounds__(32 * kBatchBwdWarps) k_render_bwd_batched_warp
       item_view(b, item, v, q);
       const int j = q / b.pieces, c = q - j * b.pieces;
       if (j >= *b.a[v].n_active) continue;
-      render_piece_bwd_warp<PPL>(b.a[v], j, c, sm[w], b.T[v], b.last[v], b.dL[v], b.grad2d[v], b.ck[v]);
+      render_piece_bwd_warp<PPL, STATS>(b.a[v], j, c, sm[w], b.T[v], b.last[v], b.dL[v], b.grad2d[v], b.ck[v],
+                                        StatsK{b.err[v], b.stats});
     }
   }
 }
@@ -1022,6 +1083,56 @@ extern "C" tgs_status tgs_render_sampled(const tgs_projected* proj, const int32_
   return check_launch();
 }
 
+// The one-view backward; with st.stats set, Eq. 12's statistics of the same
+// pixels too (fused into the warp-per-piece replay, or as the separate pass
+// after the whole-tile backward).
+static tgs_status render_backward_impl(const tgs_projected* proj, const int32_t* tile_ranges, const int32_t* vals,
+                                       const int32_t* active_tiles, const int32_t* n_active, int32_t n_active_max,
+                                       const int32_t* pix_off, const uint8_t* pix_idx, int32_t n_pix_max,
+                                       const tgs_camera* cam, const float* bg, const float* T_final,
+                                       const int32_t* n_last, const float* dL_drgb, float* grad2d,
+                                       int64_t n_gaussians, const tgs_checkpoints* ckpt, StatsK st,
+                                       int32_t accumulate_stats, tgs_stream stream) {
+  RasterArgs a;
+  if (n_gaussians < 0 || n_active_max < 0 || n_pix_max < 1 || n_pix_max > 256) return TGS_ERR_INVALID_ARG;
+  if (!raster_args(proj, tile_ranges, vals, active_tiles, n_active, pix_off, pix_idx, cam, bg, a))
+    return TGS_ERR_INVALID_ARG;
+  if (!T_final || !n_last || !dL_drgb) return TGS_ERR_INVALID_ARG;
+  if (n_gaussians > 0 && (!grad2d || !aligned16(grad2d))) return TGS_ERR_INVALID_ARG;
+  const bool stats = st.stats != nullptr;
+  Ckpt ck;
+  if (!ckpt_of(ckpt, n_active_max, n_pix_max, ckpt ? ckpt->rgb : nullptr, ck)) return TGS_ERR_INVALID_ARG;
+  if (ck.data && !ck.rgb) return TGS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (n_gaussians == 0) return TGS_OK;
+  cudaMemsetAsync(grad2d, 0, sizeof(float) * 12 * (size_t)n_gaussians, s);
+  if (stats && !accumulate_stats) cudaMemsetAsync(st.stats, 0, sizeof(float4) * (size_t)n_gaussians, s);
+  if (n_active_max > 0) {
+    const int B = block_for(n_pix_max);
+    const size_t smem = B * (sizeof(Splat) + 9 * sizeof(float));
+    if (ck.data) {
+      // one warp per piece, kBwdWarps pieces per block, B / 32 pixels per lane
+      const dim3 grid(n_active_max, (ck.n_slots + 1 + kBwdWarps - 1) / kBwdWarps);
+      switch ((B / 32) * 2 + (stats ? 1 : 0)) {
+#define TGS_BWD_WARP(P)                                                                                         \
+  case 2 * P: k_render_bwd_warp<P, false><<<grid, 32 * kBwdWarps, 0, s>>>(a, T_final, n_last, dL_drgb, grad2d, \
+                                                                         ck, st); break;                       \
+  case 2 * P + 1: k_render_bwd_warp<P, true><<<grid, 32 * kBwdWarps, 0, s>>>(a, T_final, n_last, dL_drgb,       \
+                                                                            grad2d, ck, st); break;
+        TGS_BWD_WARP(1) TGS_BWD_WARP(2) TGS_BWD_WARP(3) TGS_BWD_WARP(4)
+        TGS_BWD_WARP(5) TGS_BWD_WARP(6) TGS_BWD_WARP(7) TGS_BWD_WARP(8)
+#undef TGS_BWD_WARP
+        default: break;
+      }
+    } else {
+      k_render_bwd<<<n_active_max, B, smem, s>>>(a, T_final, n_last, dL_drgb, grad2d);
+      if (stats)
+        k_error_stats<<<n_active_max, B, B * sizeof(Splat), s>>>(a, n_last, st.err, reinterpret_cast<float*>(st.stats));
+    }
+  }
+  return check_launch();
+}
+
 extern "C" tgs_status tgs_render_backward_sampled(const tgs_projected* proj, const int32_t* tile_ranges,
                                                   const int32_t* vals, const int32_t* active_tiles,
                                                   const int32_t* n_active, int32_t n_active_max,
@@ -1030,36 +1141,21 @@ extern "C" tgs_status tgs_render_backward_sampled(const tgs_projected* proj, con
                                                   const int32_t* n_last, const float* dL_drgb, float* grad2d,
                                                   int64_t n_gaussians, const tgs_checkpoints* ckpt,
                                                   tgs_stream stream) {
-  RasterArgs a;
-  if (n_gaussians < 0 || n_active_max < 0 || n_pix_max < 1 || n_pix_max > 256) return TGS_ERR_INVALID_ARG;
-  if (!raster_args(proj, tile_ranges, vals, active_tiles, n_active, pix_off, pix_idx, cam, bg, a))
-    return TGS_ERR_INVALID_ARG;
-  if (!T_final || !n_last || !dL_drgb) return TGS_ERR_INVALID_ARG;
-  if (n_gaussians > 0 && (!grad2d || !aligned16(grad2d))) return TGS_ERR_INVALID_ARG;
-  Ckpt ck;
-  if (!ckpt_of(ckpt, n_active_max, n_pix_max, ckpt ? ckpt->rgb : nullptr, ck)) return TGS_ERR_INVALID_ARG;
-  if (ck.data && !ck.rgb) return TGS_ERR_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
-  if (n_gaussians == 0) return TGS_OK;
-  cudaMemsetAsync(grad2d, 0, sizeof(float) * 12 * (size_t)n_gaussians, s);
-  if (n_active_max > 0) {
-    const int B = block_for(n_pix_max);
-    const size_t smem = B * (sizeof(Splat) + 9 * sizeof(float));
-    if (ck.data) {
-      // one warp per piece, kBwdWarps pieces per block, B / 32 pixels per lane
-      const dim3 grid(n_active_max, (ck.n_slots + 1 + kBwdWarps - 1) / kBwdWarps);
-      switch (B / 32) {
-#define TGS_BWD_WARP(P) \
-  case P: k_render_bwd_warp<P><<<grid, 32 * kBwdWarps, 0, s>>>(a, T_final, n_last, dL_drgb, grad2d, ck); break;
-        TGS_BWD_WARP(1) TGS_BWD_WARP(2) TGS_BWD_WARP(3) TGS_BWD_WARP(4)
-        TGS_BWD_WARP(5) TGS_BWD_WARP(6) TGS_BWD_WARP(7)
-        default: k_render_bwd_warp<8><<<grid, 32 * kBwdWarps, 0, s>>>(a, T_final, n_last, dL_drgb, grad2d, ck);
-#undef TGS_BWD_WARP
-      }
-    } else
-      k_render_bwd<<<n_active_max, B, smem, s>>>(a, T_final, n_last, dL_drgb, grad2d);
-  }
-  return check_launch();
+  return render_backward_impl(proj, tile_ranges, vals, active_tiles, n_active, n_active_max, pix_off, pix_idx,
+                              n_pix_max, cam, bg, T_final, n_last, dL_drgb, grad2d, n_gaussians, ckpt,
+                              StatsK{nullptr, nullptr}, 0, stream);
+}
+
+extern "C" tgs_status tgs_render_backward_sampled_stats(
+    const tgs_projected* proj, const int32_t* tile_ranges, const int32_t* vals, const int32_t* active_tiles,
+    const int32_t* n_active, int32_t n_active_max, const int32_t* pix_off, const uint8_t* pix_idx,
+    int32_t n_pix_max, const tgs_camera* cam, const float* bg, const float* T_final, const int32_t* n_last,
+    const float* dL_drgb, float* grad2d, int64_t n_gaussians, const tgs_checkpoints* ckpt, const float* err_pix,
+    float* stats, int32_t accumulate_stats, tgs_stream stream) {
+  if (!err_pix || (n_gaussians > 0 && (!stats || !aligned16(stats)))) return TGS_ERR_INVALID_ARG;
+  return render_backward_impl(proj, tile_ranges, vals, active_tiles, n_active, n_active_max, pix_off, pix_idx,
+                              n_pix_max, cam, bg, T_final, n_last, dL_drgb, grad2d, n_gaussians, ckpt,
+                              StatsK{err_pix, reinterpret_cast<float4*>(stats)}, accumulate_stats, stream);
 }
 
 extern "C" tgs_status tgs_error_stats_sampled(const tgs_projected* proj, const int32_t* tile_ranges,
@@ -1113,6 +1209,8 @@ extern "C" tgs_status tgs_backward_sampled(const tgs_gaussians* g, const tgs_cam
 static tgs_status batch_args(const tgs_view_batch* views, int32_t n_views, bool backward, BatchArgs& b, int& B) {
   if (!views || n_views < 1 || n_views > kMaxViews) return TGS_ERR_INVALID_ARG;
   b.n_views = n_views;
+  b.stats = nullptr;
+  for (int v = 0; v < kMaxViews; ++v) b.err[v] = nullptr;
   b.base[0] = 0;
   B = 32;
   // checkpoints: all views or none, with one slot count
@@ -1146,9 +1244,9 @@ static int bwd_warp_blocks_per_sm(int ppl) {
   const int T = 32 * kBatchBwdWarps;
   switch (ppl) {
 #define TGS_OCC(P) \
-  case P: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd_batched_warp<P>, T, 0); break;
+  case P: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd_batched_warp<P, false>, T, 0); break;
     TGS_OCC(1) TGS_OCC(2) TGS_OCC(3) TGS_OCC(4) TGS_OCC(5) TGS_OCC(6) TGS_OCC(7)
-    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd_batched_warp<8>, T, 0);
+    default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_bwd_batched_warp<8, false>, T, 0);
 #undef TGS_OCC
   }
   return per_sm;
@@ -1185,32 +1283,62 @@ extern "C" tgs_status tgs_render_sampled_batched(const tgs_view_batch* views, in
   return check_launch();
 }
 
-extern "C" tgs_status tgs_render_backward_batched(const tgs_view_batch* views, int32_t n_views, int32_t grid_ctas,
-                                                  int32_t* counter, tgs_stream stream) {
+static tgs_status render_backward_batched_impl(const tgs_view_batch* views, int32_t n_views, int32_t grid_ctas,
+                                               int32_t* counter, const float* const* err_pix, float* stats,
+                                               int64_t n_stats, int32_t accumulate_stats, tgs_stream stream) {
   BatchArgs b;
   int B = 32;
   tgs_status st = batch_args(views, n_views, true, b, B);
   if (st != TGS_OK) return st;
   if (grid_ctas < 1 || !counter) return TGS_ERR_INVALID_ARG;
+  const bool with_stats = err_pix != nullptr;
+  b.stats = reinterpret_cast<float4*>(stats);
+  for (int v = 0; v < n_views; ++v) {
+    b.err[v] = with_stats ? err_pix[v] : nullptr;
+    if (with_stats && (!b.err[v] || views[v].n_gaussians > n_stats)) return TGS_ERR_INVALID_ARG;
+  }
   cudaStream_t s = (cudaStream_t)stream;
   for (int v = 0; v < n_views; ++v)
     if (views[v].n_gaussians > 0)
       cudaMemsetAsync(views[v].grad2d, 0, sizeof(float) * 12 * (size_t)views[v].n_gaussians, s);
+  if (with_stats && !accumulate_stats && n_stats > 0) cudaMemsetAsync(stats, 0, sizeof(float4) * (size_t)n_stats, s);
   cudaMemsetAsync(counter, 0, sizeof(int32_t), s);
   if (b.base[n_views] == 0) return check_launch();
   if (b.pieces == 1) {
     k_render_bwd_batched<<<grid_ctas, B, B * (sizeof(Splat) + 9 * sizeof(float)), s>>>(b, counter);
+    // without checkpoints the statistics are the separate pass, view by view
+    for (int v = 0; with_stats && v < n_views; ++v)
+      if (views[v].n_active_max > 0) {
+        const int Bv = block_for(views[v].n_pix_max);
+        k_error_stats<<<views[v].n_active_max, Bv, Bv * sizeof(Splat), s>>>(b.a[v], b.last[v], b.err[v], stats);
+      }
     return check_launch();
   }
-  switch (B / 32) {
-#define TGS_BWD_BATCH(P) \
-  case P: k_render_bwd_batched_warp<P><<<grid_ctas, 32 * kBatchBwdWarps, 0, s>>>(b, counter); break;
+  switch ((B / 32) * 2 + (with_stats ? 1 : 0)) {
+#define TGS_BWD_BATCH(P)                                                                                        \
+  case 2 * P: k_render_bwd_batched_warp<P, false><<<grid_ctas, 32 * kBatchBwdWarps, 0, s>>>(b, counter); break; \
+  case 2 * P + 1: k_render_bwd_batched_warp<P, true><<<grid_ctas, 32 * kBatchBwdWarps, 0, s>>>(b, counter); break;
     TGS_BWD_BATCH(1) TGS_BWD_BATCH(2) TGS_BWD_BATCH(3) TGS_BWD_BATCH(4)
-    TGS_BWD_BATCH(5) TGS_BWD_BATCH(6) TGS_BWD_BATCH(7)
-    default: k_render_bwd_batched_warp<8><<<grid_ctas, 32 * kBatchBwdWarps, 0, s>>>(b, counter);
+    TGS_BWD_BATCH(5) TGS_BWD_BATCH(6) TGS_BWD_BATCH(7) TGS_BWD_BATCH(8)
 #undef TGS_BWD_BATCH
+    default: break;
   }
   return check_launch();
+}
+
+extern "C" tgs_status tgs_render_backward_batched(const tgs_view_batch* views, int32_t n_views, int32_t grid_ctas,
+                                                  int32_t* counter, tgs_stream stream) {
+  return render_backward_batched_impl(views, n_views, grid_ctas, counter, nullptr, nullptr, 0, 0, stream);
+}
+
+extern "C" tgs_status tgs_render_backward_batched_stats(const tgs_view_batch* views, int32_t n_views,
+                                                        int32_t grid_ctas, int32_t* counter,
+                                                        const float* const* err_pix, float* stats,
+                                                        int64_t n_gaussians, int32_t accumulate_stats,
+                                                        tgs_stream stream) {
+  if (!err_pix || n_gaussians < 0 || (n_gaussians > 0 && (!stats || !aligned16(stats)))) return TGS_ERR_INVALID_ARG;
+  return render_backward_batched_impl(views, n_views, grid_ctas, counter, err_pix, stats, n_gaussians,
+                                      accumulate_stats, stream);
 }
 
 extern "C" tgs_status tgs_project_backward(const tgs_gaussians* g, const tgs_camera* cam, const tgs_projected* proj,

@@ -36,10 +36,14 @@ class Trainer:
     def __init__(self, params: dict, cam: dict, target: torch.Tensor, tile_fraction: float = 0.2,
                  pixel_rate: float = 1.0 / 3.0, cfg: Config | None = None, dense: bool = False,
                  capacity: int | None = None, seed: int = 0, bg=(0.0, 0.0, 0.0), sh_degree: int = 3,
-                 view: int = 0, train: bool = True, fuse_update: bool = True, share: "Trainer | None" = None):
+                 view: int = 0, train: bool = True, fuse_update: bool = True, share: "Trainer | None" = None,
+                 stats: bool = False):
         """share: another view's trainer of the same Gaussians whose optimiser
         state (gradients, moments, step and iteration counters) this one uses,
-        so that steps of several views' trainers form one training run."""
+        so that steps of several views' trainers form one training run.
+        stats: the backward also accumulates the error back-projection
+        statistics of Sec. 3.8 (Eq. 12) into self.stats [N,4] (E, W, D, 0),
+        step after step until reset_stats()."""
         self.cfg = cfg or Config()
         self.fuse_update = fuse_update
         self.params = params
@@ -105,6 +109,7 @@ class Trainer:
             self.ck_data = torch.empty(B.checkpoint_bytes(S, self.n_pix, n_slots) // 4, device=dev)
             self.ck_last = torch.zeros(S, dtype=torch.int32, device=dev)
             self.ckpt = B.checkpoints(self.ck_data, n_slots, S * self.n_pix, self.rgb, self.ck_last)
+        self.stats = torch.zeros(N, 4, device=dev) if (train and stats) else None
         if train:
             self.grad2d = torch.zeros(N, 12, device=dev)
             self.touched = torch.zeros(N, dtype=u8, device=dev)
@@ -175,10 +180,23 @@ class Trainer:
         """Fused loss with the error/age map update (Alg. 1 steps 4, 6, 7)."""
         B.loss_sparse_ncc(self.rgb, self.target, self.W, self.H, self.active_tiles, self.n_active, self.n_select,
                           self.pix_off, self.pix_idx, self.n_pix, self.loss_params, self.err_map, self.age_map,
-                          self.dL, self.lam, self.err_pix, self.loss)
+                          self.dL, self.lam, self.err_pix, self.loss, structure=self.cfg.loss.structure)
+
+    def reset_stats(self):
+        """Zeroes the accumulated statistics (after a density-control step)."""
+        if self.stats is not None:
+            self.stats.zero_()
 
     def render_backward(self):
-        """Compositing adjoint into grad2d (first half of Alg. 1 step 8)."""
+        """Compositing adjoint into grad2d (first half of Alg. 1 step 8); with
+        stats, Eq. 12's sums of the same pixels in the same replay (Alg. 1
+        step 11's back-projection)."""
+        if self.stats is not None:
+            B.render_backward_sampled_stats(self.proj, self.ranges, self.vals, self.active_tiles, self.n_active,
+                                            self.n_select, self.pix_off, self.pix_idx, self.n_pix, self.ccam,
+                                            self.bg, self.T_final, self.n_last, self.dL, self.grad2d, self.err_pix,
+                                            self.stats, accumulate=True, ckpt=self.ckpt)
+            return
         B.render_backward_sampled(self.proj, self.ranges, self.vals, self.active_tiles, self.n_active,
                                   self.n_select, self.pix_off, self.pix_idx, self.n_pix, self.ccam, self.bg,
                                   self.T_final, self.n_last, self.dL, self.grad2d, ckpt=self.ckpt)

@@ -24,10 +24,12 @@ from . import scenes
 from .pipeline import Trainer
 
 
-def perturbed_init(gt: dict, extent: float, seed: int = scenes.SEED_NOISE) -> dict:
+def perturbed_init(gt: dict, extent: float, seed: int = scenes.SEED_NOISE, mean_sigma: float = 0.02) -> dict:
+    """The ground truth with means moved by N(0, (mean_sigma extent)^2),
+    log-scales by N(0, 0.3^2), and opacities and SH coefficients re-drawn."""
     rng = np.random.default_rng(seed)
     n = gt["means"].shape[0]
-    return dict(means=(gt["means"] + rng.normal(0.0, 0.02 * extent, size=(n, 3))).astype(np.float32),
+    return dict(means=(gt["means"] + rng.normal(0.0, mean_sigma * extent, size=(n, 3))).astype(np.float32),
                 log_scales=(gt["log_scales"] + rng.normal(0.0, 0.3, size=(n, 3))).astype(np.float32),
                 quats=gt["quats"].copy(),
                 opacity_logits=rng.normal(size=n).astype(np.float32),
@@ -271,7 +273,7 @@ def _run_curve(step, ev, max_iters: int, eval_every: int, stop_psnr=None, max_ms
 def compare_views(device, n: int = 500_000, width: int = 1280, height: int = 720, distance: float = 15.0,
                   extent: float = 5.0, n_views: int = 64, hold_every: int = 8, noise: float = 0.01,
                   dense_iters: int = 3000, eval_every: int = 250, time_cap: float = 1.5, settings=None,
-                  scheduled: bool = True, scheduled_fraction: float = 1.0) -> dict:
+                  scheduled: bool = True, scheduled_fraction: float = 1.0, mean_sigma: float = 0.02) -> dict:
     """Dense against sampled training on an orbit of views with every
     hold_every-th view held out, at equal held-out PSNR (device time).
 
@@ -295,10 +297,11 @@ def compare_views(device, n: int = 500_000, width: int = 1280, height: int = 720
     gt_d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in gt.items()}
     targets, masks = _gt_views(gt_d, cams, noise, scenes.SEED_NOISE)
     del gt_d
-    init = perturbed_init(gt, extent)
+    init = perturbed_init(gt, extent, mean_sigma=mean_sigma)
     fg = float(np.mean([m.float().mean().item() for m in masks]))
     out = {"workload": f"{n} Gaussians, {len(train)} training and {len(held)} held-out views of a {n_views}-view "
-                       f"orbit at {width}x{height}, perturbed ground truth, targets + N(0, {noise:g}^2)",
+                       f"orbit at {width}x{height}, perturbed ground truth (means sigma {mean_sigma:g} x extent), "
+                       f"targets + N(0, {noise:g}^2)",
            "psnr": f"mean over the held-out views of the PSNR over foreground pixels (ground-truth T < 1/2; "
                    f"{100 * fg:.0f}% of the pixels)"}
     runs = {}

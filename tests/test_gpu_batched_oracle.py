@@ -9,8 +9,10 @@ forward's checkpoints, and the fused projection adjoint of all views with
 the hybrid update (diagonal LM, mode 1).  The oracle runs the same chain
 view by view on its own: selection, projection, per-pixel render, loss,
 compositing adjoint, projection adjoint summed over the views, one hybrid
-step on the sum.  Every oracle input is the scene, the maps and the seeds;
-nothing comes from the CUDA path."""
+step on the sum; and the error back-projection statistics of Sec. 3.8
+(Eq. 12) that the batched backward accumulates over the views' pixels.
+Every oracle input is the scene, the maps and the seeds; nothing comes from
+the CUDA path."""
 import numpy as np
 import pytest
 import torch
@@ -85,7 +87,10 @@ def test_batched_step_against_oracle(orc):
     # --- the GPU: one multi-view iteration, phase by phase, as step() runs it
     mv.forward()
     mv.loss_and_maps()
-    mv._render_bwd()
+    # the backward with Eq. 12's statistics of every view's sampled pixels (Sec. 3.8)
+    stats = torch.zeros(N, 4, device="cuda")
+    B.render_backward_batched_stats(mv.bwd_batch, mv.grid[1], mv.counters[1:2], [v.err_pix for v in mv.views],
+                                    stats)
     step = 1
     B.project_backward_update(mv.params, mv.adj, mv.m, mv.v, mv.touched, mv.opt, step, step_dev=mv.step_dev)
     torch.cuda.synchronize()
@@ -93,6 +98,7 @@ def test_batched_step_against_oracle(orc):
     # --- the oracle, view by view
     g64 = {k: np.asarray(v, np.float64) for k, v in g.items()}
     grad_sum = np.zeros((N, 59))
+    stats_o = np.zeros((N, 3))
     touched_o = np.zeros(N, bool)
     sure_g = np.ones(N, bool)
     n_pix_checked = 0
@@ -129,8 +135,13 @@ def test_batched_step_against_oracle(orc):
         else:
             assert k == 3 and not np.any(g2g)          # the view looking away sees nothing
         grad_sum += orc.project_backward(g64, cams[k], g2o, tile_rank=sel_o["tile_rank"])
+        stats_o += orc.error_stats(prw, W, H, pix, lo["err"])
         touched_o |= (np.abs(g2o).sum(1) > 0) & (prw["radius"] > 0)
     assert n_pix_checked > 3000
+    st_g = stats.cpu().numpy().astype(np.float64)
+    assert (stats_o[sure_g, 1] > 0).sum() > 500
+    for c in range(3):
+        assert rel_l2(st_g[sure_g, c], stats_o[sure_g, c]) <= 1e-3, c
 
     # the fused adjoint of all views + one hybrid step on the summed gradient
     cfgv = np.array(mv.opt["lr"] + [mv.opt["beta1"], mv.opt["beta2"], mv.opt["eps_adam"], mv.opt["eps_lm"]])

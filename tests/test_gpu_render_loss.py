@@ -200,9 +200,12 @@ def _loss_inputs(W, H, n_select, n_pix, seed):
     return err, age, target
 
 
+@pytest.mark.parametrize("structure", ["ncc", "ssim"])
 @pytest.mark.parametrize("W,H,n_select,n_pix", [(256, 256, 64, 256), (200, 130, 40, 25), (1280, 720, 720, 84),
                                                  (64, 48, 12, 1)])
-def test_loss_parity(B, orc, W, H, n_select, n_pix):
+def test_loss_parity(B, orc, W, H, n_select, n_pix, structure):
+    """The fused loss with its error/age map updates against the oracle's;
+    structure: the sparse NCC term (Sec. 3.7) or Table 4's S-SSIM variant."""
     from gpu_util import dev, select_dev, select_host
     err, age, target = _loss_inputs(W, H, n_select, n_pix, seed=W)
     sel = select_dev(B, err, age, W, H, n_select, n_pix, seed=9)
@@ -218,8 +221,10 @@ def test_loss_parity(B, orc, W, H, n_select, n_pix):
     e = torch.zeros(max(P, 1), device="cuda")
     loss = torch.zeros(1, dtype=torch.float64, device="cuda")
     B.loss_sparse_ncc(dev(rgb), dev(target), W, H, sel["active_tiles"], sel["n_active"], sel["n_sel"],
-                      sel["pix_off"], sel["pix_idx"], n_pix, (1e-3, 1e-8, 0.4), err_d, age_d, dL, lam, e, loss)
-    want = orc.loss(W, H, sh, rgb[:P].astype(np.float64), target.astype(np.float64), err_f16_bits=err, age=age)
+                      sel["pix_off"], sel["pix_idx"], n_pix, (1e-3, 1e-8, 0.4), err_d, age_d, dL, lam, e, loss,
+                      structure=structure)
+    oloss = orc.loss if structure == "ncc" else orc.loss_ssim
+    want = oloss(W, H, sh, rgb[:P].astype(np.float64), target.astype(np.float64), err_f16_bits=err, age=age)
     assert float(loss.item()) == pytest.approx(want["loss"], rel=1e-5)
     np.testing.assert_allclose(lam[:A].cpu().numpy(), want["lam"], rtol=1e-4, atol=1e-7)
     np.testing.assert_allclose(e[:P].cpu().numpy(), want["err"], atol=1e-6)
@@ -376,4 +381,61 @@ def test_error_stats_parity(B, orc, n_select, n_pix):
     B.error_stats_sampled(*args, stats, accumulate=True)
     torch.cuda.synchronize()
     # float atomics sum in a different order on each call: equal up to rounding
+    np.testing.assert_allclose(stats.cpu().numpy()[:, :3], 2.0 * got[:, :3], rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("split", [False, True])
+def test_statistics_fused_into_backward(B, orc, split):
+    """Eq. 12's statistics accumulated inside the backward replay
+    (render_backward_sampled_stats) against the oracle; the gradients equal
+    those of the plain backward; accumulate adds a second call's sums.
+    split: the warp-per-piece replay from checkpoints (the sums ride on it);
+    otherwise the whole-tile backward followed by the statistics pass."""
+    from gpu_util import bin_dev, dev, empty_projected, gaussians_dev, select_dev, select_host
+    g, cam = _c0(seed=5, n=3000)
+    g["log_scales"] += 1.0
+    W = H = 256
+    n = 3000
+    n_select, n_pix = 64, 85
+    err, age = scenes.error_map(W, H), scenes.age_map(W, H)
+    sel = select_dev(B, err, age, W, H, n_select, n_pix, seed=4)
+    sh = select_host(sel)
+    pd = empty_projected(n)
+    B.project_gaussians(gaussians_dev(g), cam, sel["tile_rank"], pd)
+    binned = bin_dev(B, pd, n, cam, sel["tile_rank"], sel["n_sel"], capacity=300000)
+    Pm = sel["n_sel"] * n_pix
+    rgb, T = torch.zeros(Pm, 3, device="cuda"), torch.zeros(Pm, device="cuda")
+    n_last = torch.zeros(Pm, dtype=torch.int32, device="cuda")
+    ck = None
+    if split:
+        slots = 64
+        data = torch.empty(B.checkpoint_bytes(sel["n_sel"], n_pix, slots) // 4, device="cuda")
+        ck = B.checkpoints(data, slots, Pm, rgb, torch.zeros(sel["n_sel"], dtype=torch.int32, device="cuda"))
+    B.render_sampled(pd, binned["ranges"], binned["vals"], sel["active_tiles"], sel["n_active"], sel["n_sel"],
+                     sel["pix_off"], sel["pix_idx"], n_pix, cam, (0.0, 0.0, 0.0), rgb, T, n_last, ckpt=ck)
+    P = int(sh["pix_off"][-1])
+    rng = np.random.default_rng(19)
+    e = rng.uniform(0.0, 2.0, Pm).astype(np.float32)
+    dL = rng.normal(0.0, 1e-3, (Pm, 3)).astype(np.float32)
+    args = (pd, binned["ranges"], binned["vals"], sel["active_tiles"], sel["n_active"], sel["n_sel"], sel["pix_off"],
+            sel["pix_idx"], n_pix, cam, (0.0, 0.0, 0.0), T, n_last, dev(dL))
+    g_plain = torch.zeros(n, 12, device="cuda")
+    B.render_backward_sampled(*args, g_plain, ckpt=ck)
+    g_fused = torch.zeros(n, 12, device="cuda")
+    stats = torch.full((n, 4), 5.0, device="cuda")           # zeroed by the call
+    B.render_backward_sampled_stats(*args, g_fused, dev(e), stats, ckpt=ck)
+    torch.cuda.synchronize()
+    a, b = g_fused.cpu().numpy(), g_plain.cpu().numpy()
+    assert np.abs(a - b).max() <= 1e-5 * np.abs(b).max()
+    got = stats.cpu().numpy().astype(np.float64)
+    pix = orc.pixel_coords(sh["active_tiles"], sh["pix_off"], sh["pix_idx"], W)
+    prw = orc.project({k: v.astype(np.float64) for k, v in g.items()}, cam, tile_rank=sh["tile_rank"])
+    want = orc.error_stats(prw, W, H, pix, e[:P].astype(np.float64))
+    ok = prw["margin"] > MARGIN
+    assert (want[ok, 1] > 0).sum() > 200
+    for c in range(3):
+        assert rel_l2(got[ok, c], want[ok, c]) <= 1e-3, (c, rel_l2(got[ok, c], want[ok, c]))
+    assert np.all(got[:, 3] == 0.0)
+    B.render_backward_sampled_stats(*args, g_fused, dev(e), stats, accumulate=True, ckpt=ck)
+    torch.cuda.synchronize()
     np.testing.assert_allclose(stats.cpu().numpy()[:, :3], 2.0 * got[:, :3], rtol=1e-5, atol=1e-6)
