@@ -122,6 +122,11 @@ def _declare(L):
     L.orc_view_pose.restype = None
     L.orc_sample_views.argtypes = [_p, _p, _i32, _i32, _d, _d, _u64, _u64, _p, _p]
     L.orc_sample_views.restype = None
+    L.orc_accumulate_screen_grad.argtypes = [_i64, _p, _p]
+    L.orc_accumulate_screen_grad.restype = None
+    L.orc_density_control.argtypes = [_i64, _p, _p, _p, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float,
+                                      _i32, _i32, _i32, _i64, _p, _p, _p]
+    L.orc_density_control.restype = _i64
     L.orc_gaussian_scores.argtypes = [_i64, _p, _i32, _d, _d, _d, _p, _p]
     L.orc_gaussian_scores.restype = None
 
@@ -560,3 +565,32 @@ def gaussian_scores(stats, t, tau_until=3500, lambda_base=0.8, eps=1e-8):
     rho = min(1.0, max(0.0, t / tau_until))
     lib().orc_gaussian_scores(n, _ptr(st), stride, float(lambda_base), rho, float(eps), _ptr(e), _ptr(s))
     return e, s
+
+
+def accumulate_screen_grad(grad2d, accum):
+    """accum [N,2] float32 (updated in place) += (|(dx, dy)|, 1) where the
+    view's grad2d [N,12] row is not all zero."""
+    g = _c(grad2d, np.float32)
+    assert accum.dtype == np.float32 and accum.flags.c_contiguous
+    lib().orc_accumulate_screen_grad(g.shape[0], _ptr(g), _ptr(accum))
+    return accum
+
+
+def density_control(params, stats, accum, lam_eff, tau_grad, log_split, logit_prune, topk_pm=800, final=False,
+                    final_pm=900, eps=1e-8):
+    """One density-control step (Sec. 3.8, Eq. 13; the procedure's reading in
+    the C source).  params: packed [N,59] float32 rows.  Returns (out [M,59]
+    float64, src [M] input index, kind [M]: 0 kept, 1 clone copy, 2/3 split
+    children)."""
+    p = _c(params, np.float32)
+    st = _c(stats, np.float32)
+    ac = _c(accum, np.float32)
+    n = p.shape[0]
+    cap = 2 * max(n, 1)
+    out = np.zeros((cap, 59))
+    src = np.zeros(cap, np.int64)
+    kind = np.zeros(cap, np.int32)
+    m = lib().orc_density_control(n, _ptr(p), _ptr(st), _ptr(ac), float(lam_eff), float(eps), float(tau_grad),
+                                  float(log_split), float(logit_prune), int(topk_pm), 1 if final else 0,
+                                  int(final_pm), cap, _ptr(out), _ptr(src), _ptr(kind))
+    return out[:m], src[:m], kind[:m]

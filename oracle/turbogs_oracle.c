@@ -1672,3 +1672,139 @@ void orc_gaussian_scores(int64_t n, const double* stats, int stride, double lamb
     s_out[i] = e + lambda_eff * d;
   }
 }
+
+/* ------------------------------------------------------------------------ */
+/* error-driven densification and pruning (Sec. 3.8; Alg. 1 step 11)        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The screen-space gradient statistic that selects densification candidates
+ * (Alg. 1 step 11 passes the screen-space gradients; Table 6's tau_grad):
+ * for every Gaussian with a non-zero compositing adjoint in a view,
+ * accum[i] += (|(dL/dx, dL/dy)|, 1), from grad2d rows [N,12] of that view.
+ * Single precision, as the library's kernel (sqrtf of x^2 + y^2, one add).
+ */
+void orc_accumulate_screen_grad(int64_t n, const float* grad2d, float* accum) {
+  for (int64_t i = 0; i < n; ++i) {
+    const float* g = grad2d + 12 * i;
+    int any = 0;
+    for (int k = 0; k < 9; ++k) any |= g[k] != 0.0f;
+    if (!any) continue;
+    float xx = g[0] * g[0];
+    float yy = g[1] * g[1];
+    accum[2 * i] = accum[2 * i] + sqrtf(xx + yy);
+    accum[2 * i + 1] = accum[2 * i + 1] + 1.0f;
+  }
+}
+
+typedef struct {
+  float s;
+  int64_t i;
+} dens_t;
+
+static int cmp_dens(const void* a, const void* b) {  /* descending score, ties by index */
+  const dens_t* x = (const dens_t*)a;
+  const dens_t* y = (const dens_t*)b;
+  if (x->s != y->s) return x->s > y->s ? -1 : 1;
+  return x->i < y->i ? -1 : (x->i > y->i);
+}
+
+/*
+ * One step of error-driven density control (Sec. 3.8, Eq. 13; Alg. 1 step
+ * 11; Table 6).  The paper fixes the scores and says that percentile
+ * thresholds of them drive densification and pruning; the procedure is this
+ * reading of it.  Every decision is taken in single precision, in the order
+ * written here (the kernel takes the same decisions):
+ *   e_i = E_i / (W_i + eps), d_i = D_i / (W_i + eps), s_i = e_i + lam_eff d_i
+ *   (Eq. 13; lam_eff = lambda_base (1 - rho) is computed by the caller);
+ *   g_i = G_i / max(1, c_i), the mean screen-space gradient norm (accum);
+ *   candidate: W_i > 0 and g_i >= tau_grad, and not pruned;
+ *   densified: the floor(n_cand topk_pm / 1000) candidates with the largest
+ *   s_i (ties: lower index);
+ *   a densified Gaussian whose largest log-scale is at most log_split is
+ *   cloned (kept, plus an identical copy after it), otherwise split: two
+ *   children at mu +- sigma_k R e_k (k the axis of the largest scale, ties to
+ *   the lower axis; one standard deviation along it), log-scales lowered by
+ *   ln 1.6, the rest copied;
+ *   pruned: opacity logit < logit_prune; with final = 1 (the final pruning of
+ *   Table 6) also every Gaussian outside the floor(n final_pm / 1000) with the
+ *   largest W_i (ties: lower index), and nothing is densified.
+ * params: packed rows [N,59] float (means 3, log-scales 3, quaternion 4,
+ * opacity logit 1, SH 48); stats [N,4] (E, W, D, -); accum [N,2].
+ * Output in input order, each surviving Gaussian in place (a clone's copy and
+ * a split's second child right after it): out [cap,59] double, src [cap] the
+ * input index, kind [cap] 0 kept, 1 clone copy, 2 split child +, 3 split
+ * child -.  Returns the output count (cap must hold it).
+ */
+int64_t orc_density_control(int64_t n, const float* params, const float* stats, const float* accum, float lam_eff,
+                            float eps, float tau_grad, float log_split, float logit_prune, int topk_pm, int final,
+                            int final_pm, int64_t cap, double* out, int64_t* src, int32_t* kind) {
+  uint8_t* prune = (uint8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+  uint8_t* dens = (uint8_t*)calloc((size_t)(n > 0 ? n : 1), 1);
+  dens_t* list = (dens_t*)malloc(sizeof(dens_t) * (size_t)(n > 0 ? n : 1));
+  int64_t nc = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    const float* p = params + 59 * i;
+    prune[i] = p[10] < logit_prune;
+    const float* r = stats + 4 * i;
+    float W = r[1];
+    float e = r[0] / (W + eps);
+    float d = r[2] / (W + eps);
+    float s = e + lam_eff * d;
+    float c = accum[2 * i + 1];
+    float g = accum[2 * i] / (c > 1.0f ? c : 1.0f);
+    if (!final && !prune[i] && W > 0.0f && g >= tau_grad) {
+      list[nc].s = s;
+      list[nc].i = i;
+      ++nc;
+    }
+  }
+  if (!final) {
+    qsort(list, (size_t)nc, sizeof(dens_t), cmp_dens);
+    int64_t k = nc * topk_pm / 1000;
+    for (int64_t q = 0; q < k; ++q) dens[list[q].i] = 1;
+  } else {
+    for (int64_t i = 0; i < n; ++i) {
+      list[i].s = stats[4 * i + 1];
+      list[i].i = i;
+    }
+    qsort(list, (size_t)n, sizeof(dens_t), cmp_dens);
+    int64_t keep = n * final_pm / 1000;
+    for (int64_t q = keep; q < n; ++q) prune[list[q].i] = 1;
+  }
+  int64_t m = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (prune[i]) continue;
+    const float* p = params + 59 * i;
+    int ax = 0;
+    for (int a = 1; a < 3; ++a)
+      if (p[3 + a] > p[3 + ax]) ax = a;
+    int split = dens[i] && p[3 + ax] > log_split;
+    int copies = dens[i] ? 2 : 1;
+    if (m + copies > cap) { m += copies; continue; }
+    for (int q = 0; q < copies; ++q) {
+      double* o = out + 59 * (m + q);
+      for (int k = 0; k < 59; ++k) o[k] = p[k];
+      src[m + q] = i;
+      kind[m + q] = dens[i] ? (split ? 2 + q : q) : 0;
+    }
+    if (split) {
+      double qn[4], R[9];
+      double nq = sqrt((double)p[6] * p[6] + (double)p[7] * p[7] + (double)p[8] * p[8] + (double)p[9] * p[9]);
+      for (int k = 0; k < 4; ++k) qn[k] = p[6 + k] / nq;
+      quat_to_rot(qn, R);
+      double sig = exp((double)p[3 + ax]);
+      for (int q = 0; q < 2; ++q) {
+        double* o = out + 59 * (m + q);
+        double sgn = q == 0 ? 1.0 : -1.0;
+        for (int a = 0; a < 3; ++a) o[a] = p[a] + sgn * sig * R[3 * a + ax];
+        for (int a = 0; a < 3; ++a) o[3 + a] = p[3 + a] - log(1.6);
+      }
+    }
+    m += copies;
+  }
+  free(prune);
+  free(dens);
+  free(list);
+  return m;
+}
