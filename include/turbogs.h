@@ -489,6 +489,67 @@ tgs_status tgs_render_backward_sampled_stats(const tgs_projected* proj, const in
                                              int32_t accumulate_stats, tgs_stream stream);
 
 /*
+ * accumulate_screen_grad - the screen-space gradient statistic that selects
+ * densification candidates (Alg. 1 step 11 takes the screen-space gradients;
+ * Table 6's tau_grad): for every Gaussian whose grad2d row [N,12] (one view,
+ * as render_backward_sampled writes it) is not all zero,
+ * accum[i] += (|(dL/dx, dL/dy)|, 1), in single precision (sqrt of the sum of
+ * squares, IEEE-rounded).  grad2d: device, 16-byte aligned; accum: device
+ * [N,2] float, 8-byte aligned, added to (zero it after a density step).
+ */
+tgs_status tgs_accumulate_screen_grad(const float* grad2d, int64_t n, float* accum, tgs_stream stream);
+
+/*
+ * density_control - one step of error-driven densification and pruning
+ * (Sec. 3.8, Eq. 13; Alg. 1 step 11; Table 6).  The paper fixes the
+ * difficulty score and says that percentile thresholds of it drive the
+ * density control; this is the procedure as read here, every decision an
+ * IEEE single-precision operation in this order:
+ *   e_i = E_i / (W_i + eps), d_i = D_i / (W_i + eps), s_i = e_i + lambda_eff d_i
+ *   (stats rows (E, W, D, -) of Eq. 12; lambda_eff = lambda_base (1 - rho)
+ *   computed by the caller); g_i = accum_i.x / max(1, accum_i.y);
+ *   pruned: opacity logit < opacity_logit_prune;
+ *   candidates: not pruned, W_i > 0 and g_i >= tau_grad;
+ *   densified: the floor(n_candidates topk_permille / 1000) candidates with
+ *   the largest s_i (equal scores: the lower index first);
+ *   a densified Gaussian is cloned (an identical copy follows it) when its
+ *   largest log-scale is at most log_scale_split, else split into two
+ *   children at mu +- sigma_k (R e_k) (k: the axis of the largest scale, the
+ *   lower axis on ties; R the rotation of the normalised quaternion) with
+ *   every log-scale lowered by ln 1.6;
+ *   final_prune = 1 (the final pruning of Table 6): nothing is densified and
+ *   every Gaussian outside the floor(N final_permille / 1000) with the
+ *   largest W_i (ties: lower index) is pruned as well.
+ * Inputs: the parameters (g, n = g->n < 2^31), moments m_in, v_in (layout of
+ * tgs_gaussians), stats [N,4] (16-byte aligned), accum [N,2] (8-byte
+ * aligned).  Outputs, in input order (each surviving Gaussian in place, a
+ * clone's copy or a split's second child right after it): parameters and
+ * moments g_out, m_out, v_out with room for `capacity` Gaussians (the copy
+ * and both children start from zero moments; the rest keep theirs),
+ * n_out (device) = the output count, which may exceed capacity (then rows
+ * past it are not written: retry with more), src_out (device, nullable)
+ * [capacity] = the input index of every output row.  Outputs must not alias
+ * inputs.  workspace: density_control_workspace_size(N) bytes.
+ */
+typedef struct {
+  float lambda_eff;          /* lambda_base (1 - rho) of Eq. 13 */
+  float eps;                 /* Eq. 13's epsilon */
+  float tau_grad;            /* Table 6: gradient threshold for densification */
+  float log_scale_split;     /* log of the clone/split size (Table 6's percent dense x scene extent) */
+  float opacity_logit_prune; /* logit of the pruning opacity */
+  int32_t topk_permille;     /* Table 6: fraction for top-k densification, x 1000 */
+  int32_t final_prune;       /* 1: the final pruning step, 0: densify and prune */
+  int32_t final_permille;    /* Table 6: fraction retained by the final pruning, x 1000 */
+} tgs_density_params;
+
+size_t tgs_density_control_workspace_size(int64_t n);
+tgs_status tgs_density_control(const tgs_gaussians* g, const tgs_param_ptrs* m_in, const tgs_param_ptrs* v_in,
+                               const float* stats, const float* accum, const tgs_density_params* cfg,
+                               const tgs_param_ptrs* g_out, const tgs_param_ptrs* m_out,
+                               const tgs_param_ptrs* v_out, int64_t capacity, int64_t* n_out, int64_t* src_out,
+                               void* workspace, size_t workspace_bytes, tgs_stream stream);
+
+/*
  * project_backward - the projection adjoint alone (the second half of
  * backward_sampled, Alg. 1 step 8): grad2d [N,12] of one view -> parameter
  * gradients.  accumulate = 0 overwrites grads and touched as backward_sampled

@@ -67,6 +67,12 @@ class LossParams(C.Structure):
                 ("view_weight", C.c_float)]
 
 
+class DensityParams(C.Structure):
+    _fields_ = [("lambda_eff", C.c_float), ("eps", C.c_float), ("tau_grad", C.c_float),
+                ("log_scale_split", C.c_float), ("opacity_logit_prune", C.c_float), ("topk_permille", C.c_int32),
+                ("final_prune", C.c_int32), ("final_permille", C.c_int32)]
+
+
 class Mlp(C.Structure):
     _fields_ = [("w1", C.c_void_p), ("b1", C.c_void_p), ("w2", C.c_void_p), ("b2", C.c_void_p), ("w3", C.c_void_p),
                 ("b3", C.c_void_p)]
@@ -147,6 +153,13 @@ _lib.tgs_render_backward_sampled.argtypes = [_P(Projected), _p, _p, _p, _p, _i32
 _lib.tgs_render_backward_sampled_stats.restype = _i32
 _lib.tgs_render_backward_sampled_stats.argtypes = [_P(Projected), _p, _p, _p, _p, _i32, _p, _p, _i32, _P(Camera), _p,
                                                    _p, _p, _p, _p, _i64, _P(Checkpoints), _p, _p, _i32, _p]
+_lib.tgs_accumulate_screen_grad.restype = _i32
+_lib.tgs_accumulate_screen_grad.argtypes = [_p, _i64, _p, _p]
+_lib.tgs_density_control_workspace_size.restype = _sz
+_lib.tgs_density_control_workspace_size.argtypes = [_i64]
+_lib.tgs_density_control.restype = _i32
+_lib.tgs_density_control.argtypes = [_P(Gaussians), _P(ParamPtrs), _P(ParamPtrs), _p, _p, _P(DensityParams),
+                                     _P(ParamPtrs), _P(ParamPtrs), _P(ParamPtrs), _i64, _p, _p, _p, _sz, _p]
 _lib.tgs_project_backward.restype = _i32
 _lib.tgs_project_backward.argtypes = [_P(Gaussians), _P(Camera), _P(Projected), _p, _P(ParamPtrs), _p, _i32, _i32,
                                       _p, _p]
@@ -209,7 +222,8 @@ EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_devi
             "tgs_mlp_param_count", "tgs_mlp_forward", "tgs_mlp_forward_tc", "tgs_mlp_tc_wait_drill", "tgs_mlp_backward_workspace_size",
             "tgs_mlp_backward",
             "tgs_mlp_adam", "tgs_tile_observe", "tgs_tile_features", "tgs_tile_refresh",
-            "tgs_view_error_sums", "tgs_sample_views"]
+            "tgs_view_error_sums", "tgs_sample_views", "tgs_accumulate_screen_grad",
+            "tgs_density_control_workspace_size", "tgs_density_control"]
 
 
 def _check(fn, status):
@@ -664,3 +678,37 @@ def sample_views(err_sums, cams, k, lambda_d, lambda_theta, seed, it, stack, vie
     _check("tgs_sample_views", _lib.tgs_sample_views(
         _ptr(err_sums), _ptr(cams), V, int(k), float(lambda_d), float(lambda_theta), int(seed) & (2**64 - 1),
         int(it) & (2**64 - 1), _ptr(stack), _ptr(views), _stream(stream)))
+
+
+# ----------------------------------------------------------------------------
+# error-driven density control (Sec. 3.8)
+# ----------------------------------------------------------------------------
+
+def accumulate_screen_grad(grad2d, accum, stream=None):
+    """accum [N,2] += (|(dL/dx, dL/dy)|, 1) where the view's grad2d row is not zero."""
+    _check("tgs_accumulate_screen_grad", _lib.tgs_accumulate_screen_grad(_ptr(grad2d), int(grad2d.shape[0]),
+                                                                          _ptr(accum), _stream(stream)))
+
+
+def density_control_workspace_size(n: int) -> int:
+    return int(_lib.tgs_density_control_workspace_size(int(n)))
+
+
+def density_params(lambda_eff, tau_grad, log_scale_split, opacity_logit_prune, topk_permille=800, final=False,
+                   final_permille=900, eps=1e-8) -> DensityParams:
+    return DensityParams(float(lambda_eff), float(eps), float(tau_grad), float(log_scale_split),
+                         float(opacity_logit_prune), int(topk_permille), 1 if final else 0, int(final_permille))
+
+
+def density_control(params: dict, m: dict, v: dict, stats, accum, cfg: DensityParams, params_out: dict, m_out: dict,
+                    v_out: dict, capacity: int, n_out, src_out=None, workspace=None, sh_degree=3, stream=None):
+    """One density-control step; n_out (device int64 [1]) receives the output
+    count (rows past capacity are not written)."""
+    n = int(params["means"].shape[0])
+    if workspace is None:
+        workspace = torch.empty(density_control_workspace_size(n), dtype=torch.uint8, device=params["means"].device)
+    gs = gaussians(params, sh_degree)
+    _check("tgs_density_control", _lib.tgs_density_control(
+        C.byref(gs), C.byref(param_ptrs(m)), C.byref(param_ptrs(v)), _ptr(stats), _ptr(accum), C.byref(cfg),
+        C.byref(param_ptrs(params_out)), C.byref(param_ptrs(m_out)), C.byref(param_ptrs(v_out)), int(capacity),
+        _ptr(n_out), _ptr(src_out), _ptr(workspace), workspace.numel(), _stream(stream)))

@@ -20,7 +20,7 @@ __device__ __forceinline__ int rs_count(const int32_t* n_dev, int32_t n_host) {
 }
 
 // hist[digit * nb + block] = count of that digit in the block's pairs
-__global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint32_t* __restrict__ keys, const int32_t* n_dev,
+static __global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint32_t* __restrict__ keys, const int32_t* n_dev,
                                                            int32_t n_host, int shift, uint32_t* __restrict__ hist,
                                                            int nb) {
   __shared__ uint32_t h[RS_WARPS][RS_BINS];
@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_upsweep(const uint32_t* __res
 
 // One block per digit: exclusive scan of the digit's nb block counts in place;
 // bin_total[digit] = total.
-__global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ hist, int nb,
+static __global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ hist, int nb,
                                                   uint32_t* __restrict__ bin_total) {
   __shared__ uint32_t wt[32];
   uint32_t* row = hist + (size_t)blockIdx.x * nb;
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(1024) k_rs_scan(uint32_t* __restrict__ hist, i
 // Stable scatter.  Pairs are taken in rounds of 256 (thread t of round r
 // holds pair base + 256 r + t); equal digits keep their input order through
 // the running per-digit counts, the per-warp prefix and the lane rank.
-__global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(
+static __global__ void __launch_bounds__(RS_THREADS) k_rs_downsweep(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, const int32_t* n_dev, int32_t n_host, int shift,
     const uint32_t* __restrict__ hist, int nb, const uint32_t* __restrict__ bin_total) {

@@ -24,6 +24,21 @@ from . import scenes
 from .pipeline import Trainer
 
 
+def jittered_init(gt: dict, extent: float, seed: int = scenes.SEED_NOISE, mean_sigma: float = 0.004,
+                  scale_sigma: float = 0.1, opacity_sigma: float = 0.5, sh_sigma: float = 0.1) -> dict:
+    """The ground truth with every parameter moved by Gaussian noise: means
+    by N(0, (mean_sigma extent)^2), log-scales by N(0, scale_sigma^2), opacity
+    logits by N(0, opacity_sigma^2), SH coefficients by N(0, sh_sigma^2) (a
+    partly fitted scene, in place of one whose colours are drawn anew)."""
+    rng = np.random.default_rng(seed)
+    n = gt["means"].shape[0]
+    return dict(means=(gt["means"] + rng.normal(0.0, mean_sigma * extent, size=(n, 3))).astype(np.float32),
+                log_scales=(gt["log_scales"] + rng.normal(0.0, scale_sigma, size=(n, 3))).astype(np.float32),
+                quats=gt["quats"].copy(),
+                opacity_logits=(gt["opacity_logits"] + rng.normal(0.0, opacity_sigma, size=n)).astype(np.float32),
+                sh=(gt["sh"] + rng.normal(0.0, sh_sigma, size=gt["sh"].shape)).astype(np.float32))
+
+
 def perturbed_init(gt: dict, extent: float, seed: int = scenes.SEED_NOISE, mean_sigma: float = 0.02) -> dict:
     """The ground truth with means moved by N(0, (mean_sigma extent)^2),
     log-scales by N(0, 0.3^2), and opacities and SH coefficients re-drawn."""
@@ -273,7 +288,8 @@ def _run_curve(step, ev, max_iters: int, eval_every: int, stop_psnr=None, max_ms
 def compare_views(device, n: int = 500_000, width: int = 1280, height: int = 720, distance: float = 15.0,
                   extent: float = 5.0, n_views: int = 64, hold_every: int = 8, noise: float = 0.01,
                   dense_iters: int = 3000, eval_every: int = 250, time_cap: float = 1.5, settings=None,
-                  scheduled: bool = True, scheduled_fraction: float = 1.0, mean_sigma: float = 0.02) -> dict:
+                  scheduled: bool = True, scheduled_fraction: float = 1.0, mean_sigma: float = 0.02,
+                  init: str = "perturbed") -> dict:
     """Dense against sampled training on an orbit of views with every
     hold_every-th view held out, at equal held-out PSNR (device time).
 
@@ -297,10 +313,14 @@ def compare_views(device, n: int = 500_000, width: int = 1280, height: int = 720
     gt_d = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in gt.items()}
     targets, masks = _gt_views(gt_d, cams, noise, scenes.SEED_NOISE)
     del gt_d
-    init = perturbed_init(gt, extent, mean_sigma=mean_sigma)
+    init_kind = init
+    if init_kind == "jitter":
+        init = jittered_init(gt, extent, mean_sigma=mean_sigma)
+    else:
+        init = perturbed_init(gt, extent, mean_sigma=mean_sigma)
     fg = float(np.mean([m.float().mean().item() for m in masks]))
     out = {"workload": f"{n} Gaussians, {len(train)} training and {len(held)} held-out views of a {n_views}-view "
-                       f"orbit at {width}x{height}, perturbed ground truth (means sigma {mean_sigma:g} x extent), "
+                       f"orbit at {width}x{height}, {init_kind} ground truth (means sigma {mean_sigma:g} x extent), "
                        f"targets + N(0, {noise:g}^2)",
            "psnr": f"mean over the held-out views of the PSNR over foreground pixels (ground-truth T < 1/2; "
                    f"{100 * fg:.0f}% of the pixels)"}

@@ -50,7 +50,8 @@ def test_ctypes_structs_match_the_header_layout(tmp_path):
     from paper_2606_15924_gb300 import binding as B
     mirrors = {"tgs_camera": B.Camera, "tgs_gaussians": B.Gaussians, "tgs_param_ptrs": B.ParamPtrs,
                "tgs_projected": B.Projected, "tgs_sampling": B.Sampling, "tgs_loss_params": B.LossParams,
-               "tgs_mlp": B.Mlp, "tgs_opt": B.Opt, "tgs_view_batch": B.ViewBatch}
+               "tgs_mlp": B.Mlp, "tgs_opt": B.Opt, "tgs_view_batch": B.ViewBatch,
+               "tgs_density_params": B.DensityParams}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "turbogs.h"', "int main(void) {"]
     for cname, py in mirrors.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')

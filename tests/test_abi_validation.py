@@ -142,3 +142,24 @@ def test_forward_split_knob(B):
         assert f(bad) == INVALID
     for ok in (1, 2, 4, 0):
         assert f(ok) == 0
+
+
+def test_density_control_checks(B):
+    """Density control refuses a bad configuration before any device work."""
+    import torch
+    f = B._lib.tgs_density_control
+    g = B.Gaussians(None, None, None, None, None, 0, 3)
+    pp = B.ParamPtrs(None, None, None, None, None)
+    ws = (C.c_uint8 * 256)()
+    n_out = C.c_int64(5)
+    for bad in (B.density_params(0.5, 2e-4, -2.0, -5.3, topk_permille=1001),
+                B.density_params(0.5, 2e-4, -2.0, -5.3, final_permille=-1),
+                B.density_params(0.5, 2e-4, -2.0, -5.3, eps=-1.0)):
+        assert f(C.byref(g), C.byref(pp), C.byref(pp), None, None, C.byref(bad), C.byref(pp), C.byref(pp),
+                 C.byref(pp), 0, C.byref(n_out), None, ws, 256, None) == INVALID
+    cfg = B.density_params(0.5, 2e-4, -2.0, -5.3)
+    assert f(C.byref(g), C.byref(pp), C.byref(pp), None, None, None, C.byref(pp), C.byref(pp),
+             C.byref(pp), 0, C.byref(n_out), None, ws, 256, None) == INVALID           # no configuration
+    assert f(C.byref(g), C.byref(pp), C.byref(pp), None, None, C.byref(cfg), C.byref(pp), C.byref(pp),
+             C.byref(pp), -1, C.byref(n_out), None, ws, 256, None) == INVALID          # negative capacity
+    assert B._lib.tgs_accumulate_screen_grad(None, 10, None, None) == INVALID

@@ -1,0 +1,131 @@
+"""Error-driven densification and pruning on the GPU (Sec. 3.8, Eq. 13;
+Alg. 1 step 11) against the oracle, on seeded statistics: the selected,
+cloned, split and pruned sets and the output order bit for bit (both sides
+take every decision in single precision), copied rows and moments exactly,
+split children's means and log-scales to float rounding; the screen-gradient
+statistic exactly; a capacity too small reports the true count and writes
+the rows that fit."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2606_15924_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+N = 20000
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2606_15924_gb300 import binding
+    binding.device_check()
+    return binding
+
+
+def _pack(d):
+    n = d["means"].shape[0]
+    return np.concatenate([d["means"], d["log_scales"], d["quats"], d["opacity_logits"][:, None],
+                           np.asarray(d["sh"]).reshape(n, 48)], 1)
+
+
+def _inputs(seed):
+    g = scenes.gaussians(N, seed=seed)
+    rng = np.random.default_rng(seed + 100)
+    st = np.zeros((N, 4), np.float32)
+    st[:, 1] = np.where(rng.uniform(size=N) < 0.2, 0.0, rng.uniform(0.01, 3.0, N))   # a fifth unseen
+    st[:, 0] = np.round(rng.uniform(0, 1, N) * 8) / 8 * st[:, 1]                       # coarse errors: ties
+    st[:, 2] = rng.uniform(0, 2, N) * st[:, 1]
+    ac = np.zeros((N, 2), np.float32)
+    ac[:, 1] = rng.integers(0, 5, N)
+    ac[:, 0] = rng.exponential(2e-4, N) * ac[:, 1]
+    return g, st, ac
+
+
+def _dev_params(d):
+    return {k: torch.from_numpy(np.ascontiguousarray(v)).cuda() for k, v in d.items()}
+
+
+def _empty(cap):
+    return dict(means=torch.zeros(cap, 3, device="cuda"), log_scales=torch.zeros(cap, 3, device="cuda"),
+                quats=torch.zeros(cap, 4, device="cuda"), opacity_logits=torch.zeros(cap, device="cuda"),
+                sh=torch.zeros(cap, 16, 3, device="cuda"))
+
+
+def _host(d, m):
+    return _pack({k: v[:m].cpu().numpy() for k, v in d.items()}).astype(np.float64)
+
+
+def test_screen_grad_accumulation(B, orc):
+    rng = np.random.default_rng(3)
+    g2 = rng.normal(0, 1e-3, (N, 12)).astype(np.float32)
+    g2[rng.uniform(size=N) < 0.5] = 0.0
+    acc0 = rng.uniform(0, 1e-2, (N, 2)).astype(np.float32)
+    want = orc.accumulate_screen_grad(g2, acc0.copy())
+    acc = torch.from_numpy(acc0).cuda()
+    B.accumulate_screen_grad(torch.from_numpy(g2).cuda(), acc)
+    np.testing.assert_array_equal(acc.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("final", [False, True])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_density_control_against_oracle(B, orc, seed, final):
+    g, st, ac = _inputs(seed)
+    p = _pack(g).astype(np.float32)
+    lam = np.float32(0.8 * (1.0 - 0.3))
+    log_split = np.float32(np.log(0.045))           # about half the densified ones split
+    lp = np.float32(np.log(0.005 / 0.995))
+    out, src, kind = orc.density_control(p, st, ac, lam, 2e-4, log_split, lp, topk_pm=700, final=final,
+                                         final_pm=850)
+    M = len(src)
+    if not final:                                   # both clones and splits occur
+        assert (kind == 1).sum() > 100 and (kind == 2).sum() > 100
+    else:
+        assert np.all(kind == 0) and M < 0.9 * N
+    rng = np.random.default_rng(seed + 7)
+    m0 = {k: torch.from_numpy(rng.normal(0, 1e-3, v.shape).astype(np.float32)).cuda() for k, v in g.items()}
+    v0 = {k: torch.from_numpy(rng.uniform(0, 1e-4, v.shape).astype(np.float32)).cuda() for k, v in g.items()}
+    cap = 2 * N
+    po, mo, vo = _empty(cap), _empty(cap), _empty(cap)
+    n_out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    src_d = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+    cfg = B.density_params(lam, 2e-4, log_split, lp, topk_permille=700, final=final, final_permille=850)
+    B.density_control(_dev_params(g), m0, v0, torch.from_numpy(st).cuda(), torch.from_numpy(ac).cuda(), cfg, po, mo,
+                      vo, cap, n_out, src_d)
+    torch.cuda.synchronize()
+    assert int(n_out.item()) == M
+    np.testing.assert_array_equal(src_d[:M].cpu().numpy(), src)
+    got = _host(po, M)
+    split = kind >= 2
+    # copied rows (kept, clones) exactly; split children to float rounding in means and log-scales
+    np.testing.assert_array_equal(got[~split], out[~split])
+    np.testing.assert_array_equal(got[split][:, 6:], out[split][:, 6:])
+    np.testing.assert_allclose(got[split][:, :6], out[split][:, :6], rtol=2e-6, atol=2e-6)
+    # moments: the originals keep theirs, the copies and children start from zero
+    m_src = _pack({k: v.cpu().numpy() for k, v in m0.items()})
+    m_got = _host(mo, M)
+    fresh = kind != 0
+    assert np.all(m_got[fresh] == 0.0)
+    np.testing.assert_array_equal(m_got[~fresh], m_src[src[~fresh]].astype(np.float64))
+
+
+def test_capacity_too_small_reports_the_count(B, orc):
+    g, st, ac = _inputs(2)
+    p = _pack(g).astype(np.float32)
+    lp = np.float32(np.log(0.005 / 0.995))
+    out, src, kind = orc.density_control(p, st, ac, 0.5, 2e-4, np.float32(-2.0), lp, topk_pm=1000)
+    M = len(src)
+    cap = M - 1000
+    po, mo, vo = _empty(cap), _empty(cap), _empty(cap)
+    n_out = torch.zeros(1, dtype=torch.int64, device="cuda")
+    src_d = torch.full((cap,), -1, dtype=torch.int64, device="cuda")
+    cfg = B.density_params(0.5, 2e-4, -2.0, lp, topk_permille=1000)
+    zeros = {k: torch.zeros_like(v) for k, v in _dev_params(g).items()}
+    B.density_control(_dev_params(g), zeros, zeros, torch.from_numpy(st).cuda(), torch.from_numpy(ac).cuda(), cfg,
+                      po, mo, vo, cap, n_out, src_d)
+    torch.cuda.synchronize()
+    assert int(n_out.item()) == M
+    s = src_d.cpu().numpy()
+    # every Gaussian whose rows fit is written; a pair that would straddle the end is not
+    written = s >= 0
+    np.testing.assert_array_equal(s[written], src[:cap][written])
+    assert written[:cap - 1].all()
