@@ -71,8 +71,26 @@ class ScheduleConfig:
 
 
 @dataclass
+class DensityConfig:
+    """Error-driven density control (Sec. 3.8; Table 6 ranges, one value
+    chosen in each)."""
+    tau_from: int = 200            # first densification iteration
+    tau_until: int = 3500          # last densification iteration
+    interval: int = 250            # densification interval (100 to 350)
+    prune_interval: int = 500      # final pruning interval
+    topk: float = 0.8              # fraction for top-k densification (0.5 to 0.95)
+    final_keep: float = 0.9        # fraction retained by final pruning (0.8 to 0.95)
+    tau_grad: float = 2e-4         # gradient threshold for densification (1e-4 to 2e-4)
+    percent_dense: float = 0.01    # clone/split size as a fraction of the scene extent (0.001 to 0.02)
+    lambda_base: float = 0.8       # base weight of the distance term of Eq. 13
+    prune_opacity: float = 0.005   # opacity below which a Gaussian is pruned (the 3DGS value; not in Table 6)
+    eps: float = 1e-8              # Eq. 13's epsilon (not given)
+
+
+@dataclass
 class Config:
     sampling: SamplingConfig = field(default_factory=SamplingConfig)
     loss: LossConfig = field(default_factory=LossConfig)
     opt: OptConfig = field(default_factory=OptConfig)
     schedule: ScheduleConfig = field(default_factory=ScheduleConfig)
+    density: DensityConfig = field(default_factory=DensityConfig)

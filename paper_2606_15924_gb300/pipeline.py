@@ -110,6 +110,8 @@ class Trainer:
             self.ck_last = torch.zeros(S, dtype=torch.int32, device=dev)
             self.ckpt = B.checkpoints(self.ck_data, n_slots, S * self.n_pix, self.rgb, self.ck_last)
         self.stats = torch.zeros(N, 4, device=dev) if (train and stats) else None
+        # the screen-space gradient statistic of the densification candidates (|dL/dxy| sum, count)
+        self.accum = torch.zeros(N, 2, device=dev) if (train and stats) else None
         if train:
             self.grad2d = torch.zeros(N, 12, device=dev)
             self.touched = torch.zeros(N, dtype=u8, device=dev)
@@ -186,6 +188,7 @@ class Trainer:
         """Zeroes the accumulated statistics (after a density-control step)."""
         if self.stats is not None:
             self.stats.zero_()
+            self.accum.zero_()
 
     def render_backward(self):
         """Compositing adjoint into grad2d (first half of Alg. 1 step 8); with
@@ -196,6 +199,7 @@ class Trainer:
                                             self.n_select, self.pix_off, self.pix_idx, self.n_pix, self.ccam,
                                             self.bg, self.T_final, self.n_last, self.dL, self.grad2d, self.err_pix,
                                             self.stats, accumulate=True, ckpt=self.ckpt)
+            B.accumulate_screen_grad(self.grad2d, self.accum)
             return
         B.render_backward_sampled(self.proj, self.ranges, self.vals, self.active_tiles, self.n_active,
                                   self.n_select, self.pix_off, self.pix_idx, self.n_pix, self.ccam, self.bg,
@@ -337,6 +341,34 @@ class Trainer:
         img = torch.zeros(self.H, self.W, per_pixel.shape[-1], device=per_pixel.device, dtype=per_pixel.dtype)
         img[xy[:, 1], xy[:, 0]] = per_pixel[:xy.shape[0]]
         return img
+
+
+def density_step(tr: Trainer, t: int, extent: float, final: bool = False) -> tuple[dict, dict, dict, int]:
+    """One step of error-driven density control (Sec. 3.8, Eq. 13; Alg. 1
+    step 11) on the statistics tr accumulated (Trainer(stats=True)) since its
+    last reset, with the settings of tr.cfg.density: returns the new
+    parameters, first and second moments (device tensors of the new count)
+    and the count.  The caller builds the trainer of the new Gaussians and
+    resets the statistics."""
+    d = tr.cfg.density
+    if tr.stats is None:
+        raise ValueError("the trainer accumulates no statistics (stats=True)")
+    rho = min(1.0, max(0.0, t / d.tau_until))
+    cfg = B.density_params(d.lambda_base * (1.0 - rho), d.tau_grad, math.log(d.percent_dense * extent),
+                           math.log(d.prune_opacity / (1.0 - d.prune_opacity)), topk_permille=round(1000 * d.topk),
+                           final=final, final_permille=round(1000 * d.final_keep), eps=d.eps)
+    cap = 2 * tr.n
+    dev = tr.params["means"].device
+
+    def alloc():
+        return {k: torch.zeros((cap,) + tuple(v.shape[1:]), dtype=v.dtype, device=dev) for k, v in tr.params.items()}
+    po, mo, vo = alloc(), alloc(), alloc()
+    n_out = torch.zeros(1, dtype=torch.int64, device=dev)
+    B.density_control(tr.params, tr.m, tr.v, tr.stats, tr.accum, cfg, po, mo, vo, cap, n_out,
+                      sh_degree=tr.sh_degree)
+    m = int(n_out.item())   # at most 2 N by construction
+    cut = lambda d_: {k: v[:m].clone() for k, v in d_.items()}
+    return cut(po), cut(mo), cut(vo), m
 
 
 def psnr(img: torch.Tensor, ref: torch.Tensor) -> float:

@@ -129,3 +129,37 @@ def test_capacity_too_small_reports_the_count(B, orc):
     written = s >= 0
     np.testing.assert_array_equal(s[written], src[:cap][written])
     assert written[:cap - 1].all()
+
+
+def test_trainer_density_step(B):
+    """A trainer that accumulates the statistics in its backward (stats=True)
+    runs density control between captured steps: the statistics are non-zero,
+    the new Gaussian count is what the step reports and lies within (0, 2N],
+    and a trainer of the new Gaussians steps on with finite values."""
+    from paper_2606_15924_gb300.pipeline import Trainer, density_step
+    g = scenes.gaussians(10000, seed=4)
+    cam = scenes.look_at((0.0, 0.0, -4.0), width=256, height=256)
+    tgt = torch.from_numpy(scenes.smooth_image(256, 256, seed=8)).cuda()
+    params = _dev_params(g)
+    tr = Trainer(params, cam, tgt, tile_fraction=0.5, pixel_rate=1 / 3, stats=True)
+    tr.init_error_map()
+    tr.capture()
+    for _ in range(30):
+        tr.replay()
+    torch.cuda.synchronize()
+    assert float(tr.stats[:, 1].sum()) > 0 and float(tr.accum[:, 1].sum()) > 0
+    p2, m2, v2, n2 = density_step(tr, t=1000, extent=1.0)
+    assert 0 < n2 <= 2 * tr.n and n2 != tr.n
+    assert all(v.shape[0] == n2 for v in p2.values())
+    tr2 = Trainer(p2, cam, tgt, tile_fraction=0.5, pixel_rate=1 / 3, stats=True)
+    for k in tr2.m:
+        tr2.m[k].copy_(m2[k])
+        tr2.v[k].copy_(v2[k])
+    tr2.err_map.copy_(tr.err_map)
+    tr2.age_map.copy_(tr.age_map)
+    for _ in range(5):
+        tr2.step()
+    torch.cuda.synchronize()
+    assert np.isfinite(float(tr2.loss.item()))
+    for v in p2.values():
+        assert torch.isfinite(v).all()
