@@ -330,23 +330,17 @@ size_t tgs_checkpoint_bytes(int32_t n_active_max, int32_t n_pix_max, int32_t n_s
 
 /*
  * set_forward_split - a tuning knob of render_sampled with checkpoints (not in
- * the paper).  With checkpoints in a buffer of exactly
- * tgs_checkpoint_bytes(n_active_max, n_pix_max, n_slots) bytes (stride =
- * n_active_max n_pix_max), the forward can walk each tile's list as
- * independent runs of 32 positions (the checkpoint runs, and one tail run
- * past the last slot), one warp per (tile, run) over all of the tile's
- * sampled pixels, each run from a local transmittance of 1; the warp that
- * completes a tile then composes the runs in list order,
- * (T, C) -> (T T_run, C + T C_run), walks the run in which the composed
- * transmittance falls below the stopping value again from its entry state to
- * find the exact stop, and rewrites the slots before it as the ordinary
- * checkpoints.  The result equals the sequential walk up to the rounding of
- * the composition.  Every run is walked whole, so a tile whose pixels all
- * saturate early costs its whole list.  groups = 0 (the default) takes the
- * run-parallel walk whenever it applies; 1 always takes the sequential walk;
- * 2 is the run-parallel walk.  Process-wide; TGS_ERR_INVALID_ARG for other
- * values.  (The buffer size of tgs_checkpoint_bytes includes the run walk's
- * scratch after the slots.)
+ * the paper).  With checkpoints and few active tiles, the forward walks each
+ * tile's list in NW runs of 32 positions at once (NW groups of one thread per
+ * sampled pixel, each run from a local transmittance of 1) and composes the
+ * runs' results in list order, (T, C) -> (T T_run, C + T C_run); the run in
+ * which the composed transmittance falls below the stopping value is walked
+ * again from its entry state to find the exact stop.  The result equals the
+ * sequential walk up to the rounding of the composition.  groups = 0 (the
+ * default) leaves the choice to the library, which currently takes the
+ * sequential walk (measured faster on GB300 at 720 tiles of 85 pixels);
+ * 1, 2 or 4 fix it (1 = sequential).  Process-wide; returns
+ * TGS_ERR_INVALID_ARG for other values.
  */
 tgs_status tgs_set_forward_split(int32_t groups);
 

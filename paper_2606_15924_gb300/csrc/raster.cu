@@ -237,58 +237,28 @@ __global__ void k_render_fwd(RasterArgs a, float* __restrict__ out_rgb, float* _
 }
 
 // ---------------------------------------------------------------------------
-// Run-parallel forward (sampled training with checkpoints).  A tile's list is
-// cut into runs of 32 positions (the checkpoint runs; the positions past the
-// last slot form one tail run).  One warp per (tile, run) walks its run for
-// every sampled pixel of the tile, PPL pixels per lane, from a local
-// transmittance of 1: a run walked to local transmittance T_r and colour C_r
-// turns the state (T, C) in front of it into (T T_r, C + T C_r).  The warp
-// writes its local result into the run's checkpoint slot (the tail run into
-// the extra area) and bumps the tile's counter; the warp that finishes the
-// tile's last run composes all of them in list order, with no waiting: the
-// first run whose composed product falls below the stopping transmittance
-// (or whose local walk stopped by itself: T_r (1 - alpha) < 1e-4 implies the
-// same for the global T <= 1) is walked again from its true entry state to
-// find the stopping splat, and every slot before it is rewritten as the
-// global checkpoint the sequential walk writes.  The composition rounds
+// Split forward (few active tiles: a sparse step).  One block per active
+// tile holds NW groups of G threads, one thread per sampled pixel in each
+// group.  In round r, group g walks run r NW + g of the tile's list (the 32
+// positions [32 (r NW + g), 32 (r NW + g + 1))) from a local transmittance of
+// 1, so the NW runs of a round are walked at once and the tile's walk is NW
+// times shorter.  A run walked from T = 1 to local transmittance T_l and
+// local colour D_l turns the state (T, C) in front of it into
+// (T T_l, C + T D_l); the groups' results are composed per pixel in list
+// order through shared memory.  The walk stops in the first run where the
+// composed product falls below the stopping transmittance, or whose local
+// walk stopped by itself (T_l (1 - alpha) < 1e-4 implies the same for the
+// global T <= T_l); that run is walked again by its group from its true entry
+// state to find the exact stopping splat.  Checkpoints (the state at the end
+// of each run) are written from the composed state, as the sequential walk
+// writes them, so the backward is unchanged.  The composition rounds
 // differently from the sequential product (one more rounding per run); when
-// that product lands within rounding of the stopping value and the re-walk
-// does not stop, the walk ends with that run.  Every run is walked whole, so
-// the parallel work is the whole list (the sequential walk stops once all of
-// a tile's pixels have saturated).
+// the product lands within rounding of the stopping value and the re-walk
+// does not stop, the walk ends at the end of that run.  Rounds repeat until
+// every pixel has stopped or the list ends, so work past the tile's last
+// stopping point is bounded by one round.
 // ---------------------------------------------------------------------------
-constexpr int kLocalStop = 64;          // flag beside a run-local last position (runs of 32)
-constexpr int kTailStop = 1 << 30;      // the same for the tail run's local last position
-constexpr int kRunWarps = 4;            // runs per block
-constexpr bool kRunsAuto = true;        // the automatic choice takes the run-parallel walk
-
-// The extra area after the checkpoint slots (when stride = n_active_max n_pix_max):
-// the tail run's local state and last position, each run's local last position,
-// and one counter per active rank.
-struct RunArea {
-  float4* tail_state;  // [stride]
-  int32_t* tail_last;  // [stride]
-  uint8_t* run_last;   // [n_slots][stride]
-  int32_t* tile_done;  // [n_active_max]
-};
-
-__host__ __device__ inline size_t run_area_bytes(int64_t stride, int n_slots, int n_active_max) {
-  return 16 * (size_t)stride + 4 * (size_t)stride + (size_t)n_slots * (size_t)stride + 4 * (size_t)n_active_max + 64;
-}
-
-__host__ __device__ inline RunArea run_area(float4* data, int n_slots, int64_t stride) {
-  RunArea r;
-  char* p = reinterpret_cast<char*>(data + (size_t)n_slots * stride);
-  r.tail_state = reinterpret_cast<float4*>(p);
-  p += 16 * (size_t)stride;
-  r.tail_last = reinterpret_cast<int32_t*>(p);
-  p += 4 * (size_t)stride;
-  r.run_last = reinterpret_cast<uint8_t*>(p);
-  p += (size_t)n_slots * stride;
-  p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15));
-  r.tile_done = reinterpret_cast<int32_t*>(p);
-  return r;
-}
+constexpr int kLocalStop = 64;  // flag bit beside the run-local last position (0..32)
 
 __device__ __forceinline__ void compose_run(float& T, float& C0, float& C1, float& C2, const float4& e) {
   C0 = __fmaf_rn(T, e.y, C0);
@@ -297,158 +267,162 @@ __device__ __forceinline__ void compose_run(float& T, float& C0, float& C1, floa
   T = __fmul_rn(T, e.x);
 }
 
-// The walk of positions [k0, k1) of tile list `range` for one pixel from the
-// state (T, C, last) with the stopping rule (the re-walk of a stopping run;
-// splat records read through L2).
-__device__ __forceinline__ void walk_from(const RasterArgs& a, int2 range, int k0, int k1, float px, float py,
-                                          float& T, float& C0, float& C1, float& C2, int& last) {
-  for (int k = k0; k < k1; ++k) {
-    Splat sp;
-    load_splat(a, range.x + k, sp);
-    float al, G;
-    if (!splat_alpha(sp.co, __fsub_rn(px, sp.xy.x), __fsub_rn(py, sp.xy.y), al, G)) continue;
-    const float Tn = __fmul_rn(T, __fsub_rn(1.f, al));
-    if (Tn < kTStop) break;
-    const float w = al * T;
-    C0 += w * sp.rgb.x;
-    C1 += w * sp.rgb.y;
-    C2 += w * sp.rgb.z;
-    T = Tn;
-    last = k + 1;
-  }
-}
-
-template <int PPL>
-__global__ void __launch_bounds__(32 * kRunWarps) k_render_fwd_runs(RasterArgs a, float* __restrict__ out_rgb,
-                                                                   float* __restrict__ out_T,
-                                                                   int32_t* __restrict__ out_last, Ckpt ck) {
-  __shared__ Splat sm_all[kRunWarps][32];
+template <int NW>
+__global__ void k_render_fwd_split(RasterArgs a, float* __restrict__ out_rgb, float* __restrict__ out_T,
+                                   int32_t* __restrict__ out_last, Ckpt ck) {
+  extern __shared__ float4 smem_f4[];
+  __shared__ int s_tl;
   const int j = blockIdx.x;
   if (j >= *a.n_active) return;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int c = blockIdx.y * kRunWarps + w;
-  const int2 range = a.ranges[j];
-  const int L = range.y - range.x;
-  const int n_runs = min((L + kCkptEvery - 1) / kCkptEvery, ck.n_slots + 1);
-  if (c >= n_runs) return;  // warp-uniform; the kernel has no block-wide barrier
-  const RunArea ra = run_area(ck.data, ck.n_slots, ck.stride);
-  Splat* sm = sm_all[w];
+  const int G = blockDim.x / NW;
+  Splat* sp = reinterpret_cast<Splat*>(smem_f4);           // [NW][32]
+  float4* loc = reinterpret_cast<float4*>(sp + NW * 32);   // [NW][G] (T_l, D_l)
+  float4* rec = loc + NW * G;                              // [NW][G] state after a stopping run
+  int* lastl = reinterpret_cast<int*>(rec + NW * G);       // [NW][G] local last | kLocalStop
+  int* rec_last = lastl + NW * G;                          // [NW][G]
+  const int g = threadIdx.x / G, i = threadIdx.x - g * G;
   const int t = a.active_tiles ? a.active_tiles[j] : j;
   const int p0 = a.pix_off[j], p1 = a.pix_off[j + 1];
-  float px[PPL], py[PPL];
-  bool has[PPL];
+  const bool has_pix = p0 + i < p1;
+  const int s = p0 + i;
+  float px = 0.f, py = 0.f;
+  if (has_pix) {
+    const int l = a.pix_idx[s];
+    px = (float)((t % a.tiles_x) * TGS_TILE + (l & 15)) + 0.5f;
+    py = (float)((t / a.tiles_x) * TGS_TILE + (l >> 4)) + 0.5f;
+  }
+  const int2 range = a.ranges[j];
+  const int L = range.y - range.x;
+  const int n_runs = (L + kCkptEvery - 1) / kCkptEvery;
+  // the running state of pixel i in front of the current round (the same in every group)
+  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+  int last = 0;
+  bool done = !has_pix;
+  const Splat* S = sp + 32 * g;
+  Splat nxt;
+  if (i < 32 && 32 * g + i < L) load_splat(a, range.x + 32 * g + i, nxt);
+  for (int r0 = 0; r0 < n_runs; r0 += NW) {
+    const int run = r0 + g;
+    // the previous round's reads of sp ended before its second barrier
+    if (i < 32 && 32 * run + i < L) sp[32 * g + i] = nxt;
+    if (__syncthreads_count(done) == (int)blockDim.x) break;
+    if (i < 32 && 32 * (run + NW) + i < L) load_splat(a, range.x + 32 * (run + NW) + i, nxt);
+    // 1. the group's run from a local T = 1 (alphas of kUnroll splats together, blend with selects)
+    const int cnt = min(kCkptEvery, L - 32 * run);
+    float Tl = 1.f, D0 = 0.f, D1 = 0.f, D2 = 0.f;
+    int ll = 0;
+    bool lstop = false;
+    if (!done && cnt > 0) {
+      for (int q0 = 0; q0 < cnt && !lstop; q0 += kUnroll) {
+        float al[kUnroll];
+        bool ok[kUnroll];
 #pragma unroll
-  for (int u = 0; u < PPL; ++u) {
-    const int s = p0 + lane + 32 * u;
-    has[u] = s < p1;
-    px[u] = py[u] = 0.f;
-    if (has[u]) {
-      const int l = a.pix_idx[s];
-      px[u] = (float)((t % a.tiles_x) * TGS_TILE + (l & 15)) + 0.5f;
-      py[u] = (float)((t / a.tiles_x) * TGS_TILE + (l >> 4)) + 0.5f;
+        for (int u = 0; u < kUnroll; ++u) {
+          const float2 xy = S[q0 + u].xy;
+          float Gv;
+          ok[u] = splat_alpha_nb(S[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], Gv) &&
+                  q0 + u < cnt;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const float Tn = __fmul_rn(Tl, __fsub_rn(1.f, al[u]));
+          const bool stop = ok[u] && !lstop && Tn < kTStop;
+          const bool take = ok[u] && !lstop && !stop;
+          lstop = lstop || stop;
+          const float4 rgb = S[q0 + u].rgb;
+          const float w = al[u] * Tl;
+          D0 = take ? D0 + w * rgb.x : D0;
+          D1 = take ? D1 + w * rgb.y : D1;
+          D2 = take ? D2 + w * rgb.z : D2;
+          Tl = take ? Tn : Tl;
+          ll = take ? q0 + u + 1 : ll;
+        }
+      }
     }
-  }
-  // 1. the run from a local transmittance of 1 (the tail run may be longer than 32)
-  const int k0 = c * kCkptEvery, k1 = c < ck.n_slots ? min(L, k0 + kCkptEvery) : L;
-  float Tl[PPL], D0[PPL], D1[PPL], D2[PPL];
-  int ll[PPL];
-  bool stop[PPL];
+    loc[g * G + i] = make_float4(Tl, D0, D1, D2);
+    lastl[g * G + i] = ll | (lstop ? kLocalStop : 0);
+    __syncthreads();
+    // 2. the state in front of this group's run; its checkpoint, or the exact stop inside it
+    if (!done && cnt > 0) {
+      float T2 = T, E0 = C0, E1 = C1, E2 = C2;
+      int l2 = last;
+      bool before = false;
+      for (int h = 0; h < g; ++h) {
+        const float4 e = loc[h * G + i];
+        const int lh = lastl[h * G + i];
+        if ((lh & kLocalStop) || __fmul_rn(T2, e.x) < kTStop) {
+          before = true;
+          break;
+        }
+        compose_run(T2, E0, E1, E2, e);
+        if (lh) l2 = 32 * (r0 + h) + lh;
+      }
+      if (!before) {
+        if (lstop || __fmul_rn(T2, Tl) < kTStop) {
+          for (int q = 0; q < cnt; ++q) {  // the stopping run again, from its entry state
+            const Splat& sq = S[q];
+            float al, Gv;
+            if (!splat_alpha(sq.co, __fsub_rn(px, sq.xy.x), __fsub_rn(py, sq.xy.y), al, Gv)) continue;
+            const float Tn = __fmul_rn(T2, __fsub_rn(1.f, al));
+            if (Tn < kTStop) break;
+            const float w = al * T2;
+            E0 += w * sq.rgb.x;
+            E1 += w * sq.rgb.y;
+            E2 += w * sq.rgb.z;
+            T2 = Tn;
+            l2 = 32 * run + q + 1;
+          }
+          rec[g * G + i] = make_float4(T2, E0, E1, E2);
+          rec_last[g * G + i] = l2;
+        } else if (ck.data && run < ck.n_slots) {
+          compose_run(T2, E0, E1, E2, make_float4(Tl, D0, D1, D2));
+          ck.data[run * ck.stride + s] = make_float4(T2, E0, E1, E2);  // in front of position 32 (run + 1)
+        }
+      }
+    }
+    __syncthreads();
+    // 3. the running state over the whole round (every group the same)
+    if (!done) {
 #pragma unroll
-  for (int u = 0; u < PPL; ++u) {
-    Tl[u] = 1.f;
-    D0[u] = D1[u] = D2[u] = 0.f;
-    ll[u] = 0;
-    stop[u] = !has[u];
-  }
-  for (int b = k0; b < k1; b += 32) {
-    const int cnt = min(32, k1 - b);
-    __syncwarp();
-    if (lane < cnt) load_splat(a, range.x + b + lane, sm[lane]);
-    __syncwarp();
-    for (int q = 0; q < cnt; ++q) {
-      const Splat sp = sm[q];
-#pragma unroll
-      for (int u = 0; u < PPL; ++u) {
-        float al, G;
-        const bool ok = splat_alpha_nb(sp.co, __fsub_rn(px[u], sp.xy.x), __fsub_rn(py[u], sp.xy.y), al, G) &&
-                        !stop[u];
-        const float Tn = __fmul_rn(Tl[u], __fsub_rn(1.f, al));
-        const bool st = ok && Tn < kTStop;
-        const bool take = ok && !st;
-        stop[u] = stop[u] || st;
-        const float wgt = al * Tl[u];
-        D0[u] = take ? D0[u] + wgt * sp.rgb.x : D0[u];
-        D1[u] = take ? D1[u] + wgt * sp.rgb.y : D1[u];
-        D2[u] = take ? D2[u] + wgt * sp.rgb.z : D2[u];
-        Tl[u] = take ? Tn : Tl[u];
-        ll[u] = take ? b - k0 + q + 1 : ll[u];
+      for (int h = 0; h < NW; ++h) {
+        if (r0 + h >= n_runs) break;
+        const float4 e = loc[h * G + i];
+        const int lh = lastl[h * G + i];
+        if ((lh & kLocalStop) || __fmul_rn(T, e.x) < kTStop) {
+          const float4 q = rec[h * G + i];
+          T = q.x;
+          C0 = q.y;
+          C1 = q.z;
+          C2 = q.w;
+          last = rec_last[h * G + i];
+          done = true;
+          break;
+        }
+        compose_run(T, C0, C1, C2, e);
+        if (lh) last = 32 * (r0 + h) + lh;
       }
     }
   }
-#pragma unroll
-  for (int u = 0; u < PPL; ++u) {
-    const int s = p0 + lane + 32 * u;
-    if (!has[u]) continue;
-    const bool lstop = stop[u];  // has[u]: stop means the walk stopped by itself
-    const float4 e = make_float4(Tl[u], D0[u], D1[u], D2[u]);
-    if (c < ck.n_slots) {
-      ck.data[c * ck.stride + s] = e;
-      ra.run_last[c * ck.stride + s] = (uint8_t)(ll[u] | (lstop ? kLocalStop : 0));
-    } else {
-      ra.tail_state[s] = e;
-      ra.tail_last[s] = ll[u] | (lstop ? kTailStop : 0);
-    }
-  }
-  // 2. the warp that completes the tile composes its runs
-  __threadfence();
-  int prev = 0;
-  if (lane == 0) prev = atomicAdd(ra.tile_done + j, 1);
-  prev = __shfl_sync(0xffffffffu, prev, 0);
-  if (prev != n_runs - 1) return;
-  __threadfence();
-  int tl = 0;
-#pragma unroll
-  for (int u = 0; u < PPL; ++u) {
-    const int s = p0 + lane + 32 * u;
-    if (!has[u]) continue;
-    float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
-    int last = 0;
-    for (int r = 0; r < n_runs; ++r) {
-      float4 e;
-      int lr;
-      bool lstop;
-      if (r < ck.n_slots) {
-        e = __ldcg(ck.data + r * ck.stride + s);
-        const int v = __ldcg(ra.run_last + r * ck.stride + s);
-        lr = v & (kLocalStop - 1);
-        lstop = (v & kLocalStop) != 0;
-      } else {
-        e = __ldcg(ra.tail_state + s);
-        const int v = __ldcg(ra.tail_last + s);
-        lr = v & (kTailStop - 1);
-        lstop = (v & kTailStop) != 0;
-      }
-      if (lstop || __fmul_rn(T, e.x) < kTStop) {
-        const int r0 = r * kCkptEvery, r1 = r < ck.n_slots ? min(L, r0 + kCkptEvery) : L;
-        walk_from(a, range, r0, r1, px[u], py[u], T, C0, C1, C2, last);
-        break;
-      }
-      compose_run(T, C0, C1, C2, e);
-      if (lr) last = r * kCkptEvery + lr;
-      if (r < ck.n_slots) ck.data[r * ck.stride + s] = make_float4(T, C0, C1, C2);  // in front of 32 (r + 1)
-    }
+  if (g == 0 && has_pix) {
     out_rgb[3 * s] = C0 + T * a.bg[0];
     out_rgb[3 * s + 1] = C1 + T * a.bg[1];
     out_rgb[3 * s + 2] = C2 + T * a.bg[2];
     out_T[s] = T;
     out_last[s] = last;
-    tl = max(tl, last);
   }
   if (ck.tile_last) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tl = max(tl, __shfl_xor_sync(0xffffffffu, tl, o));
-    if (lane == 0) ck.tile_last[j] = tl;
+    __syncthreads();
+    if (threadIdx.x == 0) s_tl = 0;
+    __syncthreads();
+    if (g == 0 && last > 0) atomicMax(&s_tl, last);
+    __syncthreads();
+    if (threadIdx.x == 0) ck.tile_last[j] = s_tl;
   }
+}
+
+template <int NW>
+size_t split_smem_bytes(int G) {
+  return NW * 32 * sizeof(Splat) + (size_t)NW * G * (2 * sizeof(float4) + 2 * sizeof(int));
 }
 
 // The adjoints of a splat's centre and conic from the sums over its pixels of
@@ -1009,9 +983,43 @@ static bool raster_args(const tgs_projected* proj, const int32_t* tile_ranges, c
 static int block_for(int n_pix_max) { return std::min(256, std::max(32, (n_pix_max + 31) / 32 * 32)); }
 
 
-// The forward's walk: 0 = chosen per call (below), or fixed at 1 (the
-// sequential walk) or 2 (the run-parallel walk) by tgs_set_forward_split.
+// Whether the automatic choice may pick the split walk: measured slower than
+// the sequential walk at 500k Gaussians, 720 tiles of 85 pixels (0.085-0.089
+// against 0.067 ms), so only an explicit setting selects it.
+constexpr bool kSplitAuto = false;
+
+// The split forward's group count: 0 = chosen per launch (below), or fixed
+// at 1, 2 or 4 by tgs_set_forward_split (tuning and tests).
 static int g_fwd_split = 0;
+
+// Groups per tile of the split forward for a launch of n_active tiles of B
+// threads: the largest of 4 and 2 whose blocks all fit on the GPU at once
+// (one wave), else 1 (the sequential walk).
+static int split_groups(int n_active, int B) {
+  const int wp = B / 32;  // 1..8
+  const bool nw_ok[2] = {4 * B <= 1024, 2 * B <= 1024};
+  if (g_fwd_split) return (g_fwd_split == 4 && !nw_ok[0]) || (g_fwd_split == 2 && !nw_ok[1]) ? 1 : g_fwd_split;
+  if (!kSplitAuto) return 1;
+  static int per_sm[64][9][2] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  const int sms = device_sm_count();
+  for (int k = 0; k < 2; ++k) {
+    const int nw = k == 0 ? 4 : 2;
+    if (!nw_ok[k]) continue;
+    int& r = per_sm[dev][wp][k];
+    if (r == 0) {
+      int b = 0;
+      if (nw == 4)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_render_fwd_split<4>, 4 * B, split_smem_bytes<4>(B));
+      else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_render_fwd_split<2>, 2 * B, split_smem_bytes<2>(B));
+      r = b > 0 ? b : -1;
+    }
+    if (r > 0 && (int64_t)n_active <= (int64_t)sms * r) return nw;
+  }
+  return 1;
+}
 
 }  // namespace tgs
 
@@ -1031,16 +1039,14 @@ static bool ckpt_of(const tgs_checkpoints* c, int32_t n_active_max, int32_t n_pi
 }
 
 extern "C" tgs_status tgs_set_forward_split(int32_t groups) {
-  if (groups != 0 && groups != 1 && groups != 2) return TGS_ERR_INVALID_ARG;
+  if (groups != 0 && groups != 1 && groups != 2 && groups != 4) return TGS_ERR_INVALID_ARG;
   g_fwd_split = groups;
   return TGS_OK;
 }
 
 extern "C" size_t tgs_checkpoint_bytes(int32_t n_active_max, int32_t n_pix_max, int32_t n_slots) {
   if (n_active_max <= 0 || n_pix_max <= 0 || n_slots <= 0) return 0;
-  const int64_t stride = (int64_t)n_active_max * n_pix_max;
-  return align_up(sizeof(float4) * (size_t)n_slots * (size_t)stride + run_area_bytes(stride, n_slots, n_active_max),
-                  16);
+  return sizeof(float4) * (size_t)n_slots * (size_t)n_active_max * (size_t)n_pix_max;
 }
 
 extern "C" tgs_status tgs_render_sampled(const tgs_projected* proj, const int32_t* tile_ranges, const int32_t* vals,
@@ -1057,22 +1063,16 @@ extern "C" tgs_status tgs_render_sampled(const tgs_projected* proj, const int32_
   if (!ckpt_of(ckpt, n_active_max, n_pix_max, rgb, ck)) return TGS_ERR_INVALID_ARG;
   if (n_active_max == 0) return TGS_OK;
   const int B = block_for(n_pix_max);
-  // sampled training (checkpoints in their exact-size buffer): the run-parallel walk
-  const bool runs = ck.data && ck.stride == (int64_t)n_active_max * n_pix_max && g_fwd_split != 1 &&
-                    (g_fwd_split == 2 || kRunsAuto);
-  if (runs) {
-    cudaStream_t s = (cudaStream_t)stream;
-    const RunArea ra = run_area(ck.data, ck.n_slots, ck.stride);
-    cudaMemsetAsync(ra.tile_done, 0, sizeof(int32_t) * (size_t)n_active_max, s);
-    const dim3 grid(n_active_max, (ck.n_slots + 1 + kRunWarps - 1) / kRunWarps);
-    switch (B / 32) {
-#define TGS_FWD_RUNS(P) \
-  case P: k_render_fwd_runs<P><<<grid, 32 * kRunWarps, 0, s>>>(a, rgb, T_final, n_last, ck); break;
-      TGS_FWD_RUNS(1) TGS_FWD_RUNS(2) TGS_FWD_RUNS(3) TGS_FWD_RUNS(4)
-      TGS_FWD_RUNS(5) TGS_FWD_RUNS(6) TGS_FWD_RUNS(7)
-      default: k_render_fwd_runs<8><<<grid, 32 * kRunWarps, 0, s>>>(a, rgb, T_final, n_last, ck);
-#undef TGS_FWD_RUNS
-    }
+  // sampled training (checkpoints) with few tiles: the split walk, NW groups per tile
+  const int nw = ck.data ? split_groups(n_active_max, B) : 1;
+  if (nw == 4) {
+    k_render_fwd_split<4><<<n_active_max, 4 * B, split_smem_bytes<4>(B), (cudaStream_t)stream>>>(a, rgb, T_final,
+                                                                                                 n_last, ck);
+    return check_launch();
+  }
+  if (nw == 2) {
+    k_render_fwd_split<2><<<n_active_max, 2 * B, split_smem_bytes<2>(B), (cudaStream_t)stream>>>(a, rgb, T_final,
+                                                                                                 n_last, ck);
     return check_launch();
   }
   // selects when the launch gives fewer than 16 warps per SM

@@ -61,11 +61,7 @@ def test_size_queries(B):
     assert L.tgs_select_tiles_workspace_size(1280, 720) > 0
     assert L.tgs_checkpoint_bytes(0, 85, 64) == 0 and L.tgs_checkpoint_bytes(720, 0, 64) == 0
     L.tgs_checkpoint_bytes.restype = C.c_size_t
-    # the slots, then the run-parallel walk's scratch: the tail run's state and last position, each
-    # run's last position, a counter per tile (and alignment)
-    stride = 720 * 85
-    assert L.tgs_checkpoint_bytes(720, 85, 64) == -(-(16 * stride * 64 + 16 * stride + 4 * stride + 64 * stride +
-                                                       4 * 720 + 64) // 16) * 16
+    assert L.tgs_checkpoint_bytes(720, 85, 64) == 16 * 720 * 85 * 64
     assert L.tgs_bin_tiles_workspace_size(500000, 2000000, 720) > 0
     assert L.tgs_hybrid_step_workspace_size(500000) >= 4 * 500000
     assert L.tgs_mlp_backward_workspace_size(1000) > 0
@@ -139,12 +135,12 @@ def test_hybrid_checks(B):
 
 
 def test_forward_split_knob(B):
-    """The forward's walk knob accepts 0 (automatic), 1 (sequential) and 2
-    (run-parallel) only (no device work)."""
+    """The split forward's tuning knob accepts 0 (automatic), 1, 2 and 4 only
+    (no device work)."""
     f = B._lib.tgs_set_forward_split
-    for bad in (-1, 3, 4, 8):
+    for bad in (-1, 3, 5, 8):
         assert f(bad) == INVALID
-    for ok in (1, 2, 0):
+    for ok in (1, 2, 4, 0):
         assert f(ok) == 0
 
 

@@ -1,10 +1,9 @@
-"""The run-parallel forward (a tile's list walked as independent runs of 32
-positions, one warp each, composed in list order by the warp that completes
-the tile) against the oracle's per-pixel render (Sec. 3.6, Eq. 1) and against
-the sequential walk of the same library.
+"""The split forward (several 32-position runs of a tile's list walked at
+once, composed in list order) against the oracle's per-pixel render
+(Sec. 3.6, Eq. 1) and against the sequential walk of the same library.
 
-Each case renders with checkpoints, once per walk (1 = sequential, 2 =
-run-parallel), at 1, 3, 5 and 8 pixels per 32-lane warp.  Images and final
+Each case renders with checkpoints, once per group count (1 = the sequential
+walk, 2 and 4), at 1, 3, 5 and 8 pixels per 32-lane warp.  Images and final
 transmittances match the oracle within 1e-4 at every sampled pixel whose
 decisions are not within rounding of a threshold; n_last matches exactly
 there.  Against the sequential walk, the split walk's images agree to 1e-5,
@@ -12,7 +11,7 @@ n_last and each tile's last position exactly except where a pixel's
 transmittance ends within rounding of the stopping value, and every
 checkpoint the backward reads (slot c of a pixel that blends past position
 32 (c + 1)) agrees to 1e-5.  An opaque scene, where most pixels stop early,
-exercises the stop inside a run (the re-walk from the run's entry state)."""
+exercises the stop inside a run and the early exit of a tile's rounds."""
 import numpy as np
 import pytest
 import torch
@@ -53,7 +52,7 @@ def _render(B, pd, binned, sel, n_pix, cam, slots):
                      sel["pix_off"], sel["pix_idx"], n_pix, cam, (0.0, 0.0, 0.0), out["rgb"], out["T"],
                      out["n_last"], ckpt=ck)
     torch.cuda.synchronize()
-    out["ck"] = data[:slots * P * 4].view(slots, -1, 4).cpu().numpy()   # the slots (the run walk's scratch follows)
+    out["ck"] = data.view(slots, -1, 4).cpu().numpy()
     out["tile_last"] = tl.cpu().numpy()
     return {k: (v.cpu().numpy() if torch.is_tensor(v) else v) for k, v in out.items()}
 
@@ -76,7 +75,7 @@ def test_split_forward_against_oracle_and_sequential(B, orc, opaque):
         P = int(sh["pix_off"][-1])
         A = sh["n_active"]
         outs = {}
-        for groups in (1, 2):
+        for groups in (1, 2, 4):
             B.set_forward_split(groups)
             outs[groups] = _render(B, pd, binned, sel, n_pix, cam, slots)
         B.set_forward_split(0)
