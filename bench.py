@@ -267,7 +267,14 @@ def stage_times(tr, steps, flush):
     rl = (tr.ranges[:A, 1] - tr.ranges[:A, 0]).float()
     info_tiles = dict(list_mean=float(rl.mean().item()), list_max=int(rl.max().item()),
                       n_last_mean=float(tr.n_last[:P].float().mean().item()), n_last_max=int(tr.n_last[:P].max().item()))
+    # the forward tests every splat of a pixel's tile list until the pixel saturates: at most
+    # (list length) per pixel; a pixel can have stopped early only if its T_final is below 0.01
+    # (the stop comes before a splat that takes T below 1e-4, with alpha <= 0.99)
+    npix = (tr.pix_off[1:A + 1] - tr.pix_off[:A]).float()
+    walked = float((rl * npix).sum().item())
+    maybe_stopped = float((tr.T_final[:P] < 0.01).float().mean().item())
     info = dict(tiles=info_tiles, P=P, A=A, n_isect=int(tr.n_isect.item()), evals_per_step=evals / steps,
+                walked_per_step=walked, maybe_stopped=maybe_stopped,
                 touched=int(tr.touched.sum().item()) if tr.train else 0,
                 visible=int((tr.proj["radius"] > 0).sum().item()))
     return {n: acc[n] / steps for n in acc}, info
@@ -324,12 +331,19 @@ def roofline(stage_ms, info, peaks, peak_kind, clocks, tr, dom=None):
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     alu_peak = alu_peak_tflops(sm_mhz)  # TFLOP/s FP32 at the sampled clock
     n = tr.n
-    if dom in ("render_sampled", "render_backward"):
-        per = FLOPS_ALPHA + FLOPS_BLEND if dom == "render_sampled" else FLOPS_BWD
-        work = info["evals_per_step"] * per / 1e12
+    if dom == "render_sampled":
+        # an alpha test for every (sampled pixel, list position) walked, a blend up to n_last
+        work = (info["walked_per_step"] * FLOPS_ALPHA + info["evals_per_step"] * FLOPS_BLEND) / 1e12
         return dict(kernel=dom, bound="alu", achieved=work / t, peak=alu_peak, unit="TFLOP/s",
                     frac=(work / t) / alu_peak, traffic=measured_traffic(dom),
-                    note=f"{per} FP32 FLOPs per (pixel, splat) walked, at the sampled SM clock")
+                    note=f"{FLOPS_ALPHA} FP32 FLOPs per alpha test over every pixel's whole tile list (an upper "
+                         f"bound: {100 * info['maybe_stopped']:.2f}% of the pixels could have stopped early) + "
+                         f"{FLOPS_BLEND} per blend up to n_last, at the sampled SM clock")
+    if dom == "render_backward":
+        work = info["evals_per_step"] * FLOPS_BWD / 1e12
+        return dict(kernel=dom, bound="alu", achieved=work / t, peak=alu_peak, unit="TFLOP/s",
+                    frac=(work / t) / alu_peak, traffic=measured_traffic(dom),
+                    note=f"{FLOPS_BWD} FP32 FLOPs per (pixel, splat) replayed up to n_last, at the sampled SM clock")
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     if dom == "hybrid_step":
         byts = info["touched"] * 59 * 4 * 7
@@ -637,7 +651,9 @@ def run_ours(args):
            "roofline": roof, "clocks": clocks,
            "sampled": {"iters_per_s": 1e3 / mean_s, "ms_per_step": mean_s, "sampled_pixels": info["P"],
                        "active_tiles": info["A"], "tile_pairs": info["n_isect"], "touched": info["touched"],
-                       "visible": info["visible"], "splat_evals": info["evals_per_step"], "tile_lists": info["tiles"],
+                       "visible": info["visible"], "splat_evals": info["evals_per_step"],
+                       "alpha_tests": info["walked_per_step"], "maybe_stopped": info["maybe_stopped"],
+                       "tile_lists": info["tiles"],
                        "fwd_bwd_mpix_per_s": mpix, "stage_ms": st, "kernels_per_step": launches,
                        "error_stats": err_stats, "view_sampling": view_draw,
                        "stage_rooflines": {k: {"bound": v["bound"], "achieved": v["achieved"], "unit": v["unit"],

@@ -49,6 +49,10 @@ def test_roofline_record(monkeypatch):
     assert r["peak"] == pytest.approx(alu)
     assert r["achieved"] == pytest.approx(1.0e6 * bench.FLOPS_BWD / 1e12 / 1e-4)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    info.update(walked_per_step=2.5e6, maybe_stopped=0.01)
+    f = bench.roofline(st, info, peaks, "measured", clocks, tr, dom="render_sampled")
+    # an alpha test per position walked, a blend per position up to n_last
+    assert f["achieved"] == pytest.approx((2.5e6 * bench.FLOPS_ALPHA + 1.0e6 * bench.FLOPS_BLEND) / 1e12 / 0.05e-3)
     p = bench.roofline(st, info, peaks, "measured", clocks, tr, dom="project_gaussians")
     assert p["bound"] == "hbm" and p["unit"] == "GB/s" and p["peak"] == 6000.0
     byts = tr.n * (44 + 48) + info["visible"] * 192
