@@ -33,6 +33,7 @@ __device__ __forceinline__ float ex2_approx(float x) {
 
 struct Splat {
   float2 xy;
+  float2 yr;   // the rows [y0, y1] outside which alpha < 1/255 (with a margin)
   float4 co;   // the conic pre-scaled to base-2 exponents: (-a/2, -b, -c/2) log2(e), then the opacity
   float4 rgb;  // r, g, b, (unused)
 };
@@ -96,12 +97,39 @@ struct RasterArgs {
   float bg[3];
 };
 
+// Rows a splat can reach: alpha >= 1/255 needs power >= -tau with
+// tau = ln(255 o), i.e. the ellipse a dx^2 + 2 b dx dy + c dy^2 <= 2 tau,
+// whose half-height is sqrt(2 tau a / (a c - b^2)).  The margin (1e-3
+// relative + 1e-3 px) covers the rounding of the kernels' own alpha test, so
+// a pixel outside [y0, y1] never passes it.  Empty when o <= 1/255.
+__device__ __forceinline__ float2 splat_rows(float y, const float4& c) {
+  const float tau = logf(255.f * c.w);
+  if (!(tau > 0.f)) return make_float2(INFINITY, -INFINITY);
+  const float det = c.x * c.z - c.y * c.y;
+  if (!(det > 0.f) || !(c.x > 0.f)) return make_float2(-INFINITY, INFINITY);
+  const float h = sqrtf(2.f * tau * c.x / det) * 1.001f + 1e-3f;
+  return make_float2(y - h, y + h);
+}
+
 __device__ __forceinline__ void load_splat(const RasterArgs& a, int k, Splat& sp) {
   const int id = a.vals[k];
   sp.xy = a.xy[id];
   const float4 c = a.conic_opac[id];
+  sp.yr = splat_rows(sp.xy.y, c);
   sp.co = make_float4(__fmul_rn(c.x, kPow2A), __fmul_rn(c.y, kPow2B), __fmul_rn(c.z, kPow2A), c.w);
   sp.rgb = make_float4(a.rgb[3 * id], a.rgb[3 * id + 1], a.rgb[3 * id + 2], __int_as_float(id));
+}
+
+// The rows [y0, y1] spanned by the sampled pixels of the calling warp
+// (sampled pixels are in row-major order, so a warp's pixels form a band).
+__device__ __forceinline__ float2 warp_rows(bool has, float py) {
+  float lo = has ? py : INFINITY, hi = has ? py : -INFINITY;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  return make_float2(lo, hi);
 }
 
 // Forward of active tile j (one thread per sampled pixel; sm holds
@@ -141,6 +169,7 @@ __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Spla
   int last = 0;
   bool done = !has_pix;
   const int B = blockDim.x;
+  const float2 band = warp_rows(has_pix, py);  // splats outside it are skipped by the whole warp
   // the next batch is fetched into registers while the current one is blended
   Splat nxt;
   if (range.x + (int)threadIdx.x < range.y) load_splat(a, range.x + threadIdx.x, nxt);
@@ -163,14 +192,23 @@ __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Spla
       for (int q0 = q32; q0 < qe && !done; q0 += kUnroll) {
         float al[kUnroll];
         bool ok[kUnroll];
+        bool any_in = false;
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-          const float2 xy = sm[q0 + u].xy;
-          float G;
-          ok[u] = (SELECT ? splat_alpha_nb(sm[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G)
-                          : splat_alpha(sm[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G)) &&
-                  q0 + u < qe;
+          // warp-uniform: a splat that cannot reach the warp's rows fails every pixel's alpha test
+          const float2 yr = sm[q0 + u].yr;
+          const bool in = q0 + u < qe && yr.y >= band.x && yr.x <= band.y;
+          any_in = any_in || in;
+          ok[u] = false;
+          al[u] = 0.f;
+          if (in) {
+            const float2 xy = sm[q0 + u].xy;
+            float G;
+            ok[u] = SELECT ? splat_alpha_nb(sm[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G)
+                           : splat_alpha(sm[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G);
+          }
         }
+        if (!any_in) continue;
         if (!SELECT) {
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) {
@@ -535,6 +573,7 @@ __device__ __forceinline__ void render_tile_bwd(const RasterArgs& a, int j, Spla
   int warp_last = last;  // the warp skips splats none of its pixels blended
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) warp_last = max(warp_last, __shfl_xor_sync(0xffffffffu, warp_last, o));
+  const float2 band = warp_rows(last > 0, py);  // and splats that cannot reach its rows
   Splat nxt;
   if (end - B + (int)threadIdx.x >= range.x && (int)threadIdx.x < B && end > range.x) {
     const int k = end - B + threadIdx.x;
@@ -562,6 +601,7 @@ __device__ __forceinline__ void render_tile_bwd(const RasterArgs& a, int j, Spla
       const int pos = lo + q - range.x;  // position in the tile list
       float v[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
       bool hit = false;
+      if (sp.yr.y < band.x || sp.yr.x > band.y) continue;  // warp-uniform: no pixel of the warp is reached
       if (pos < last) {
         const float dx = __fsub_rn(px, sp.xy.x), dy = __fsub_rn(py, sp.xy.y);
         float alpha, G;
@@ -704,6 +744,11 @@ __device__ __forceinline__ void render_piece_bwd_warp(const RasterArgs& a, int j
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) warp_last = max(warp_last, __shfl_xor_sync(0xffffffffu, warp_last, o));
+  // slot u of the lanes holds 32 consecutive sampled pixels (row-major): a band of rows; a splat
+  // outside a slot's band is skipped for that slot by the whole warp
+  float2 band[PPL];
+#pragma unroll
+  for (int u = 0; u < PPL; ++u) band[u] = warp_rows(last[u] > 0, py[u]);
   const int2 range = a.ranges[j];
   const int first = range.x + lo_pos, end = range.x + min(hi_pos, warp_last);
   for (int top = end; top > first; top -= 32) {
@@ -719,6 +764,7 @@ __device__ __forceinline__ void render_piece_bwd_warp(const RasterArgs& a, int j
       bool hit = false;
 #pragma unroll
       for (int u = 0; u < PPL; ++u) {
+        if (sp.yr.y < band[u].x || sp.yr.x > band[u].y) continue;  // warp-uniform
         if (pos >= last[u]) continue;
         const float dx = __fsub_rn(px[u], sp.xy.x), dy = __fsub_rn(py[u], sp.xy.y);
         float alpha, G, pw;
@@ -827,6 +873,7 @@ __global__ void k_error_stats(RasterArgs a, const int32_t* __restrict__ n_last, 
   const int2 range = a.ranges[j];
   const int end = range.x + s_max_last;
   const int B = blockDim.x;
+  const float2 band = warp_rows(last > 0, py);  // splats that cannot reach the warp's rows are skipped
   for (int base = range.x; base < end; base += B) {
     __syncthreads();  // the previous batch is no longer read
     if (base + (int)threadIdx.x < end) load_splat(a, base + threadIdx.x, sm[threadIdx.x]);
@@ -834,6 +881,7 @@ __global__ void k_error_stats(RasterArgs a, const int32_t* __restrict__ n_last, 
     const int cnt = min(B, end - base);
     for (int q = 0; q < cnt; ++q) {
       const Splat sp = sm[q];
+      if (sp.yr.y < band.x || sp.yr.x > band.y) continue;  // warp-uniform
       float v0 = 0.f, v1 = 0.f, v2 = 0.f;
       bool on = false;
       if (base + q - range.x < last) {
