@@ -267,12 +267,15 @@ def stage_times(tr, steps, flush):
     rl = (tr.ranges[:A, 1] - tr.ranges[:A, 0]).float()
     info_tiles = dict(list_mean=float(rl.mean().item()), list_max=int(rl.max().item()),
                       n_last_mean=float(tr.n_last[:P].float().mean().item()), n_last_max=int(tr.n_last[:P].max().item()))
-    # the forward tests every splat of a pixel's tile list until the pixel saturates: at most
-    # (list length) per pixel; a pixel can have stopped early only if its T_final is below 0.01
-    # (the stop comes before a splat that takes T below 1e-4, with alpha <= 0.99)
-    npix = (tr.pix_off[1:A + 1] - tr.pix_off[:A]).float()
-    walked = float((rl * npix).sum().item())
-    maybe_stopped = float((tr.T_final[:P] < 0.01).float().mean().item())
+    # the forward tests every splat of a pixel's tile list until the pixel saturates; a pixel can
+    # have stopped early only if its T_final is below 0.01 (the stop comes before a splat that
+    # takes T below 1e-4, with alpha <= 0.99): such pixels count up to n_last only, the rest the
+    # whole list (a lower bound of the alpha tests the method needs)
+    npix = (tr.pix_off[1:A + 1] - tr.pix_off[:A]).long()
+    L_pix = torch.repeat_interleave(rl, npix)
+    maybe = tr.T_final[:P] < 0.01
+    walked = float(torch.where(maybe, tr.n_last[:P].float(), L_pix).sum().item())
+    maybe_stopped = float(maybe.float().mean().item())
     info = dict(tiles=info_tiles, P=P, A=A, n_isect=int(tr.n_isect.item()), evals_per_step=evals / steps,
                 walked_per_step=walked, maybe_stopped=maybe_stopped,
                 touched=int(tr.touched.sum().item()) if tr.train else 0,
@@ -336,9 +339,9 @@ def roofline(stage_ms, info, peaks, peak_kind, clocks, tr, dom=None):
         work = (info["walked_per_step"] * FLOPS_ALPHA + info["evals_per_step"] * FLOPS_BLEND) / 1e12
         return dict(kernel=dom, bound="alu", achieved=work / t, peak=alu_peak, unit="TFLOP/s",
                     frac=(work / t) / alu_peak, traffic=measured_traffic(dom),
-                    note=f"{FLOPS_ALPHA} FP32 FLOPs per alpha test over every pixel's whole tile list (an upper "
-                         f"bound: {100 * info['maybe_stopped']:.2f}% of the pixels could have stopped early) + "
-                         f"{FLOPS_BLEND} per blend up to n_last, at the sampled SM clock")
+                    note=f"{FLOPS_ALPHA} FP32 FLOPs per alpha test, over the whole tile list for pixels that "
+                         f"cannot have saturated and up to n_last for the {100 * info['maybe_stopped']:.1f}% that "
+                         f"may have (a lower bound), + {FLOPS_BLEND} per blend up to n_last, at the sampled SM clock")
     if dom == "render_backward":
         work = info["evals_per_step"] * FLOPS_BWD / 1e12
         return dict(kernel=dom, bound="alu", achieved=work / t, peak=alu_peak, unit="TFLOP/s",

@@ -170,6 +170,7 @@ __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Spla
   bool done = !has_pix;
   const int B = blockDim.x;
   const float2 band = warp_rows(has_pix, py);  // splats outside it are skipped by the whole warp
+  const int lane = threadIdx.x & 31;
   // the next batch is fetched into registers while the current one is blended
   Splat nxt;
   if (range.x + (int)threadIdx.x < range.y) load_splat(a, range.x + threadIdx.x, nxt);
@@ -179,36 +180,39 @@ __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Spla
     __syncthreads();
     if (base + B + (int)threadIdx.x < range.y) load_splat(a, base + B + threadIdx.x, nxt);
     const int cnt = min(B, range.y - base);
-    // Runs of kCkptEvery positions (B is a multiple of it): the checkpoint in
-    // front of each run, then kUnroll splats at a time: their alphas do not
-    // depend on T, so they are evaluated together and only the blend runs in
-    // list order (sm[q0 .. q0 + kUnroll - 1] stays inside the batch).
-    for (int q32 = 0; q32 < cnt && !done; q32 += kCkptEvery) {
-      if (ck.data) {
+    // Runs of kCkptEvery positions (B is a multiple of it), walked by every
+    // thread so that the warp's ballot below stays converged: the checkpoint
+    // in front of each run, then the run's splats that can reach the warp's
+    // rows (a bit mask from one ballot), kUnroll at a time: their alphas do
+    // not depend on T, so they are evaluated together and only the blend runs
+    // in list order.  The splats left out fail every alpha test of the warp.
+    for (int q32 = 0; q32 < cnt; q32 += kCkptEvery) {
+      if (ck.data && !done) {
         const int c = (base - range.x + q32) / kCkptEvery - 1;  // state in front of this run
         if (c >= 0 && c < ck.n_slots) ck.data[c * ck.stride + s] = make_float4(T, C0, C1, C2);
       }
       const int qe = min(cnt, q32 + kCkptEvery);
-      for (int q0 = q32; q0 < qe && !done; q0 += kUnroll) {
+      bool in_l = false;
+      if (q32 + lane < qe) {
+        const float2 yr = sm[q32 + lane].yr;
+        in_l = yr.y >= band.x && yr.x <= band.y;
+      }
+      unsigned mask = __ballot_sync(0xffffffffu, in_l);
+      while (mask && !done) {
+        int qq[kUnroll];
         float al[kUnroll];
         bool ok[kUnroll];
-        bool any_in = false;
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-          // warp-uniform: a splat that cannot reach the warp's rows fails every pixel's alpha test
-          const float2 yr = sm[q0 + u].yr;
-          const bool in = q0 + u < qe && yr.y >= band.x && yr.x <= band.y;
-          any_in = any_in || in;
-          ok[u] = false;
-          al[u] = 0.f;
-          if (in) {
-            const float2 xy = sm[q0 + u].xy;
-            float G;
-            ok[u] = SELECT ? splat_alpha_nb(sm[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G)
-                           : splat_alpha(sm[q0 + u].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G);
-          }
+          const bool val = mask != 0u;
+          qq[u] = val ? q32 + __ffs(mask) - 1 : q32;
+          mask &= mask - 1u;
+          const float2 xy = sm[qq[u]].xy;
+          float G;
+          ok[u] = (SELECT ? splat_alpha_nb(sm[qq[u]].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G)
+                          : splat_alpha(sm[qq[u]].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G)) &&
+                  val;
         }
-        if (!any_in) continue;
         if (!SELECT) {
 #pragma unroll
           for (int u = 0; u < kUnroll; ++u) {
@@ -218,13 +222,13 @@ __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Spla
               done = true;
               break;
             }
-            const float4 rgb = sm[q0 + u].rgb;
+            const float4 rgb = sm[qq[u]].rgb;
             const float w = al[u] * T;
             C0 += w * rgb.x;
             C1 += w * rgb.y;
             C2 += w * rgb.z;
             T = Tn;
-            last = base + q0 + u + 1 - range.x;
+            last = base + qq[u] + 1 - range.x;
           }
           continue;
         }
@@ -236,13 +240,13 @@ __device__ __forceinline__ void render_tile_fwd(const RasterArgs& a, int j, Spla
           const bool stop = ok[u] && !done && Tn < kTStop;
           const bool take = ok[u] && !done && !stop;
           done = done || stop;
-          const float4 rgb = sm[q0 + u].rgb;
+          const float4 rgb = sm[qq[u]].rgb;
           const float w = al[u] * T;
           C0 = take ? C0 + w * rgb.x : C0;
           C1 = take ? C1 + w * rgb.y : C1;
           C2 = take ? C2 + w * rgb.z : C2;
           T = take ? Tn : T;
-          last = take ? base + q0 + u + 1 - range.x : last;
+          last = take ? base + qq[u] + 1 - range.x : last;
         }
       }
     }
@@ -828,7 +832,7 @@ __device__ __forceinline__ void render_piece_bwd_warp(const RasterArgs& a, int j
 constexpr int kBwdWarps = 4;  // pieces per block of the one-view split backward
 
 template <int PPL, bool STATS>
-__global__ void __launch_bounds__(32 * kBwdWarps, PPL <= 3 ? 8 : 1)
+__global__ void __launch_bounds__(32 * kBwdWarps, PPL <= 3 ? 7 : 1)
     k_render_bwd_warp(RasterArgs a, const float* __restrict__ T_final, const int32_t* __restrict__ n_last,
                       const float* __restrict__ dL_drgb, float* __restrict__ grad2d, Ckpt ck, StatsK st) {
   __shared__ Splat sm[kBwdWarps][32];
