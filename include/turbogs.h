@@ -336,11 +336,15 @@ size_t tgs_checkpoint_bytes(int32_t n_active_max, int32_t n_pix_max, int32_t n_s
  * runs' results in list order, (T, C) -> (T T_run, C + T C_run); the run in
  * which the composed transmittance falls below the stopping value is walked
  * again from its entry state to find the exact stop.  The result equals the
- * sequential walk up to the rounding of the composition.  groups = 0 (the
- * default) leaves the choice to the library, which currently takes the
- * sequential walk (measured faster on GB300 at 720 tiles of 85 pixels);
- * 1, 2 or 4 fix it (1 = sequential).  Process-wide; returns
- * TGS_ERR_INVALID_ARG for other values.
+ * sequential walk up to the rounding of the composition.  groups = 3 takes
+ * the sequential walk with every warp on its own (each stages its own splat
+ * batches and stops when its own pixels have saturated; the same bits as
+ * the sequential walk), several tiles per block when tiles have few sampled
+ * pixels.  groups = 0 (the default) leaves the choice to the library (the
+ * warp-independent walk for sparse launches of tiles with at most 32 sampled
+ * pixels, else the block's walk); 1 is the block's sequential walk; 2 or 4
+ * the split walk.
+ * Process-wide; returns TGS_ERR_INVALID_ARG for other values.
  */
 tgs_status tgs_set_forward_split(int32_t groups);
 

@@ -2,8 +2,10 @@
 once, composed in list order) against the oracle's per-pixel render
 (Sec. 3.6, Eq. 1) and against the sequential walk of the same library.
 
-Each case renders with checkpoints, once per group count (1 = the sequential
-walk, 2 and 4), at 1, 3, 5 and 8 pixels per 32-lane warp.  Images and final
+Each case renders with checkpoints, once per walk (1 = the sequential walk,
+2 and 4 = the split walk of that many runs at once, 3 = the sequential walk
+with every warp on its own, which must give the same bits as 1), at 1, 3, 5
+and 8 pixels per 32-lane warp.  Images and final
 transmittances match the oracle within 1e-4 at every sampled pixel whose
 decisions are not within rounding of a threshold; n_last matches exactly
 there.  Against the sequential walk, the split walk's images agree to 1e-5,
@@ -75,7 +77,7 @@ def test_split_forward_against_oracle_and_sequential(B, orc, opaque):
         P = int(sh["pix_off"][-1])
         A = sh["n_active"]
         outs = {}
-        for groups in (1, 2, 4):
+        for groups in (1, 2, 3, 4):
             B.set_forward_split(groups)
             outs[groups] = _render(B, pd, binned, sel, n_pix, cam, slots)
         B.set_forward_split(0)
@@ -89,6 +91,11 @@ def test_split_forward_against_oracle_and_sequential(B, orc, opaque):
         stopped_seen += int(stopped.sum())
         if not opaque:      # the longest walk spans several rounds
             assert seq["n_last"][:P].max() > 5 * 32
+        # the warp-independent walk (3) takes the same per-pixel operations in the same order
+        for k in ("rgb", "T", "n_last", "tile_last"):
+            np.testing.assert_array_equal(outs[3][k], seq[k])
+        np.testing.assert_array_equal(outs[3]["ck"][:, :P][np.isfinite(seq["ck"][:, :P])],
+                                      seq["ck"][:, :P][np.isfinite(seq["ck"][:, :P])])
         for groups, o in outs.items():
             np.testing.assert_array_equal(o["n_last"][:P][sure], want["n_last"][sure])
             assert np.abs(o["rgb"][:P][sure] - want["rgb"][sure]).max() <= 1e-4, groups
