@@ -202,7 +202,10 @@ def make_trainer(g_np, cam, target, dense, frac, rate, device):
     import numpy as np
     import torch
     from paper_2606_15924_gb300.pipeline import Trainer
-    params = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in g_np.items()}
+    from paper_2606_15924_gb300.pipeline import as_geo_rows
+    # geometric fields in 64-byte rows (the update of scattered Gaussians then
+    # moves whole rows); gradients and moments follow the same layout
+    params = as_geo_rows({k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in g_np.items()})
     tr = Trainer(params, cam, target, tile_fraction=frac, pixel_rate=rate, dense=dense)
     tr.init_error_map()
     return tr
@@ -602,9 +605,10 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
     sampled = make_trainer(g_np, cam, target, False, args.fraction, args.rate, device)
     dense = None if args.no_dense else make_trainer(g_np, cam, target, True, 1.0, 1.0, device)
-    sampled.capture()
+    # each replay makes the next iteration's selection beside its own backward
+    sampled.capture(overlap=True)
     if dense is not None:
-        dense.capture()
+        dense.capture(overlap=True)
     for _ in range(args.warmup):
         sampled.replay()
         if dense is not None:
@@ -730,7 +734,8 @@ def batched_scene(device):
     del gt_d
     torch.cuda.empty_cache()
     g = scenes.gaussians(N_BATCH_GAUSS, seed=scenes.SEED_SCENE, extent=EXTENT)
-    params = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in g.items()}
+    from paper_2606_15924_gb300.pipeline import as_geo_rows
+    params = as_geo_rows({k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in g.items()})
     return params, cams, targets, ids, fracs
 
 
@@ -860,6 +865,17 @@ def mlp_bench(device, peaks, steps: int = 10, rows: int = MLP_ROWS) -> dict:
         B.mlp_backward(mlp.net(), x, h1, h2, y, t, mlp.grads, mlp.loss, workspace=ws)
         B.mlp_adam(mlp.params, mlp.grads, mlp.m, mlp.v, 1, 1e-4, 0.9, 0.999, 1e-8, mlp.net())
 
+    def train_tc():
+        fwd_tc()
+        B.mlp_backward_tc(mlp.net(), x, h1, h2, y, t, mlp.grads, mlp.loss, status=status, workspace=ws)
+        B.mlp_adam(mlp.params, mlp.grads, mlp.m, mlp.v, 1, 1e-4, 0.9, 0.999, 1e-8, mlp.net())
+
+    def bwd():
+        B.mlp_backward(mlp.net(), x, h1, h2, y, t, mlp.grads, mlp.loss, workspace=ws)
+
+    def bwd_tc():
+        B.mlp_backward_tc(mlp.net(), x, h1, h2, y, t, mlp.grads, mlp.loss, status=status, workspace=ws)
+
     def timed(fn):
         for _ in range(3):
             fn()
@@ -873,6 +889,7 @@ def mlp_bench(device, peaks, steps: int = 10, rows: int = MLP_ROWS) -> dict:
         return a.elapsed_time(b) / steps
     f_ms, t_ms = timed(fwd), timed(train)
     ftc_ms, itc_ms = timed(fwd_tc), timed(infer_tc)
+    b_ms, btc_ms, ttc_ms = timed(bwd), timed(bwd_tc), timed(train_tc)
     flop = 2.0 * R * (16 * 128 + 128 * 128 + 128)
     peak = float(peaks.get("bf16_tflops", 1900.0))
 
@@ -886,7 +903,12 @@ def mlp_bench(device, peaks, steps: int = 10, rows: int = MLP_ROWS) -> dict:
             "inference_tc_roofline": roof(itc_ms, "tcgen05.mma bf16, TMEM accumulators, y only"),
             "peak_note": "peak = measured cuBLAS bf16 (burst)",
             "train_roofline": {"achieved": 3 * flop / (t_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
-                               "frac": 3 * flop / (t_ms * 1e-3) / 1e12 / peak}}
+                               "frac": 3 * flop / (t_ms * 1e-3) / 1e12 / peak},
+            "backward_ms": b_ms, "backward_tc_ms": btc_ms, "train_step_tc_ms": ttc_ms,
+            "train_tc_roofline": {"achieved": 3 * flop / (ttc_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                                  "frac": 3 * flop / (ttc_ms * 1e-3) / 1e12 / peak,
+                                  "note": "tcgen05 forward with stored activations, mma.sync activation "
+                                          "adjoint, tcgen05 weight gradients, Adam"}}
 
 
 def run_quality(args):

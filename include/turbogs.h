@@ -59,12 +59,19 @@ typedef struct {
   float znear;
 } tgs_camera;
 
-/* N Gaussians, structure of arrays (Sec. 3.1: centre, covariance via scale
- * and rotation, opacity, colour coefficients).
+/* N Gaussians (Sec. 3.1: centre, covariance via scale and rotation,
+ * opacity, colour coefficients).
  *   means [N,3], log_scales [N,3] (scale = exp), quats [N,4] (w, x, y, z; the
  *   rotation of q/|q|), opacity_logits [N] (opacity = sigmoid), sh [N,16,3]
  *   (real spherical harmonics of degree <= 3, coefficient-major, RGB inner).
- * Only the first (sh_degree+1)^2 coefficients are used. */
+ * Only the first (sh_degree+1)^2 coefficients are used.
+ * geo_stride: 0 for four packed arrays (3, 3, 4 and 1 floats per Gaussian);
+ * otherwise the distance in floats between consecutive Gaussians of all four
+ * geometric fields, which then lie in one array of rows (a multiple of 4, at
+ * least 12; e.g. 16: means at row + 0, log_scales at + 3, opacity_logits at
+ * + 6, quats at + 8, one 64-byte row per Gaussian, so that an update of
+ * scattered Gaussians reads and writes whole rows).  quats stays 16-byte
+ * aligned.  sh is always [N,16,3]. */
 typedef struct {
   const float* means;
   const float* log_scales;
@@ -73,16 +80,18 @@ typedef struct {
   const float* sh;
   int64_t n;
   int32_t sh_degree;
+  int32_t geo_stride;
 } tgs_gaussians;
 
 /* Mutable arrays with the layout of tgs_gaussians (parameters, gradients,
- * first and second moments). */
+ * first and second moments), geo_stride as there. */
 typedef struct {
   float* means;
   float* log_scales;
   float* quats;
   float* opacity_logits;
   float* sh;
+  int32_t geo_stride;
 } tgs_param_ptrs;
 
 /* Screen-space splats, the output of the projection:
@@ -738,6 +747,20 @@ tgs_status tgs_mlp_backward(const tgs_mlp* w, int64_t rows, const int32_t* rows_
                             const uint16_t* h1,
                             const uint16_t* h2, const float* y, const float* target, float* grads, double* loss,
                             void* workspace, size_t workspace_bytes, tgs_stream stream);
+
+/* The same gradient with the weight gradients on the tcgen05 tensor cores:
+ * dW2 += dH2^T H1 and dW1 += dH1^T bf16(X) as contractions over 128-row tiles
+ * (M = 128 hidden units, K = 128 rows), with the bias gradients as an extra
+ * column of ones in the same contraction, accumulated in tensor memory per
+ * CTA and added to grads once per CTA; dW3 and db3 on the CUDA cores.  The
+ * products are the same bf16 x bf16 products with fp32 sums (the order of
+ * the sums differs).  x, h1, h2 and the workspace 16-byte aligned.  status
+ * (nullable device int32) is set to 1 if a wait for the tensor cores timed
+ * out (grads are then incomplete). */
+tgs_status tgs_mlp_backward_tc(const tgs_mlp* w, int64_t rows, const int32_t* rows_dev, const float* x,
+                               const uint16_t* h1, const uint16_t* h2, const float* y, const float* target,
+                               float* grads, double* loss, int32_t* status, void* workspace, size_t workspace_bytes,
+                               tgs_stream stream);
 
 /* Adam step on the fp32 master vector (params, m, v: tgs_mlp_param_count()
  * floats) with bias correction at `step` (>= 1); writes the bf16 copies of

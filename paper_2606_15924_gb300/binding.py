@@ -44,12 +44,13 @@ class Camera(C.Structure):
 
 class Gaussians(C.Structure):
     _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
-                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p), ("n", C.c_int64), ("sh_degree", C.c_int32)]
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p), ("n", C.c_int64), ("sh_degree", C.c_int32),
+                ("geo_stride", C.c_int32)]
 
 
 class ParamPtrs(C.Structure):
     _fields_ = [("means", C.c_void_p), ("log_scales", C.c_void_p), ("quats", C.c_void_p),
-                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p)]
+                ("opacity_logits", C.c_void_p), ("sh", C.c_void_p), ("geo_stride", C.c_int32)]
 
 
 class Projected(C.Structure):
@@ -196,6 +197,8 @@ _lib.tgs_mlp_backward_workspace_size.restype = _sz
 _lib.tgs_mlp_backward_workspace_size.argtypes = [_i64]
 _lib.tgs_mlp_backward.restype = _i32
 _lib.tgs_mlp_backward.argtypes = [_P(Mlp), _i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]
+_lib.tgs_mlp_backward_tc.restype = _i32
+_lib.tgs_mlp_backward_tc.argtypes = [_P(Mlp), _i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]
 _lib.tgs_tile_observe.restype = _i32
 _lib.tgs_tile_observe.argtypes = [_p, _p, _i32, _p, _p, _p, _p, _u64, _p, _p, _p, _p, _i32, _p]
 _lib.tgs_tile_features.restype = _i32
@@ -220,7 +223,7 @@ EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_devi
             "tgs_render_batched_resident", "tgs_render_sampled_batched",
             "tgs_render_backward_batched", "tgs_render_backward_batched_stats", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step",
             "tgs_mlp_param_count", "tgs_mlp_forward", "tgs_mlp_forward_tc", "tgs_mlp_tc_wait_drill", "tgs_mlp_backward_workspace_size",
-            "tgs_mlp_backward",
+            "tgs_mlp_backward", "tgs_mlp_backward_tc",
             "tgs_mlp_adam", "tgs_tile_observe", "tgs_tile_features", "tgs_tile_refresh",
             "tgs_view_error_sums", "tgs_sample_views", "tgs_accumulate_screen_grad",
             "tgs_density_control_workspace_size", "tgs_density_control"]
@@ -280,14 +283,49 @@ def camera_array(cams, device="cuda") -> torch.Tensor:
     return torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8).to(device)
 
 
+_GEO = ("means", "log_scales", "quats", "opacity_logits")
+_GEO_WIDTH = {"means": 3, "log_scales": 3, "quats": 4, "opacity_logits": 1}
+
+
+def _geo_ptrs(g: dict):
+    """Device pointers of the four geometric fields and their geo_stride: 0
+    when each is a contiguous array, else the common row stride (in floats)
+    of four views into one array of rows (see ``geo_rows``)."""
+    ts = [g[k] for k in _GEO]
+    if all(t.is_contiguous() for t in ts):
+        return [_ptr(t) for t in ts], 0
+    n = ts[0].shape[0]
+    rs = {t.stride(0) for t in ts}
+    if len(rs) != 1:
+        raise ValueError("geometric fields: one row stride for all four, or four contiguous arrays")
+    stride = rs.pop()
+    for k, t in zip(_GEO, ts):
+        if not t.is_cuda or t.dtype != torch.float32 or t.shape[0] != n:
+            raise ValueError(f"{k}: expected a float32 CUDA tensor of {n} rows")
+        if _GEO_WIDTH[k] > 1 and (t.dim() != 2 or t.shape[1] != _GEO_WIDTH[k] or t.stride(1) != 1):
+            raise ValueError(f"{k}: expected [{n}, {_GEO_WIDTH[k]}] with unit inner stride")
+    return [t.data_ptr() for t in ts], int(stride)
+
+
+def geo_rows(n: int, device="cuda", stride: int = 16, dtype=torch.float32) -> dict:
+    """The geometric fields of n Gaussians as views into one [n, stride]
+    array of rows (means at + 0, log_scales at + 3, opacity_logits at + 6,
+    quats at + 8; zero-filled)."""
+    if stride % 4 or stride < 12:
+        raise ValueError("stride: a multiple of 4, at least 12")
+    rows = torch.zeros(n, stride, dtype=dtype, device=device)
+    return {"means": rows[:, 0:3], "log_scales": rows[:, 3:6], "opacity_logits": rows[:, 6],
+            "quats": rows[:, 8:12]}
+
+
 def gaussians(g: dict, sh_degree: int = 3) -> Gaussians:
-    return Gaussians(_ptr(g["means"]), _ptr(g["log_scales"]), _ptr(g["quats"]), _ptr(g["opacity_logits"]),
-                     _ptr(g["sh"]), int(g["means"].shape[0]), int(sh_degree))
+    p, gs = _geo_ptrs(g)
+    return Gaussians(p[0], p[1], p[2], p[3], _ptr(g["sh"]), int(g["means"].shape[0]), int(sh_degree), gs)
 
 
 def param_ptrs(g: dict) -> ParamPtrs:
-    return ParamPtrs(_ptr(g["means"]), _ptr(g["log_scales"]), _ptr(g["quats"]), _ptr(g["opacity_logits"]),
-                     _ptr(g["sh"]))
+    p, gs = _geo_ptrs(g)
+    return ParamPtrs(p[0], p[1], p[2], p[3], _ptr(g["sh"]), gs)
 
 
 def projected(p: dict) -> Projected:
@@ -622,6 +660,17 @@ def mlp_backward(net: dict, x, h1, h2, y, target, grads, loss, workspace=None, s
     _check("tgs_mlp_backward", _lib.tgs_mlp_backward(C.byref(m), int(x.shape[0]), _ptr(rows_dev), _ptr(x), _ptr(h1),
                                                      _ptr(h2), _ptr(y), _ptr(target), _ptr(grads), _ptr(loss),
                                                      _ptr(workspace), workspace.numel(), _stream(stream)))
+
+
+def mlp_backward_tc(net: dict, x, h1, h2, y, target, grads, loss, status=None, workspace=None, stream=None,
+                    rows_dev=None):
+    """mlp_backward with the weight gradients on the tcgen05 tensor cores."""
+    m = mlp_struct(net)
+    if workspace is None:
+        workspace = torch.empty(mlp_backward_workspace_size(x.shape[0]), dtype=torch.uint8, device=x.device)
+    _check("tgs_mlp_backward_tc", _lib.tgs_mlp_backward_tc(
+        C.byref(m), int(x.shape[0]), _ptr(rows_dev), _ptr(x), _ptr(h1), _ptr(h2), _ptr(y), _ptr(target), _ptr(grads),
+        _ptr(loss), _ptr(status), _ptr(workspace), workspace.numel(), _stream(stream)))
 
 
 def mlp_adam(params, grads, m, v, step, lr, beta1, beta2, eps, net: dict, stream=None):

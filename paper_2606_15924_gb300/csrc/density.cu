@@ -18,6 +18,8 @@
 
 namespace tgs {
 
+bool gaussians_ok(const tgs_gaussians* g);
+
 constexpr uint32_t kKeyTop = 0x7F800000u;  // bits of +inf: keys of finite non-negative values fall below
 constexpr uint32_t kKeyNone = 0xFFFFFFFFu;  // not ranked (after every ranked key)
 constexpr float kLogSplit = 0.47000362924573558f;  // ln 1.6: the children's log-scale decrease
@@ -48,13 +50,13 @@ struct DensK {
 
 // (1) prune flag, ranking key and index of every Gaussian; n_rank counts the
 // densification candidates (every Gaussian in the final pruning).
-__global__ void k_dens_keys(const float* __restrict__ ologit, const float4* __restrict__ stats,
+__global__ void k_dens_keys(GeoC geo, const float4* __restrict__ stats,
                             const float2* __restrict__ accum, int64_t n, DensK k, uint8_t* __restrict__ flag,
                             uint32_t* __restrict__ keys, uint32_t* __restrict__ vals, int32_t* __restrict__ n_rank) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool ranked = false;
   if (i < n) {
-    const bool prune = ologit[i] < k.logit_prune;
+    const bool prune = geo.opac(i) < k.logit_prune;
     const float4 st = stats[i];
     uint32_t key = kKeyNone;
     if (k.final_mode) {
@@ -94,39 +96,35 @@ __global__ void k_dens_mark(const uint32_t* __restrict__ order, int64_t n, const
 }
 
 struct ParamsIn {
-  const float* means;
-  const float* ls;
-  const float4* quats;
-  const float* ologit;
+  GeoC g;
   const float4* sh;
 };
 
 struct ParamsOut {
-  float* means;
-  float* ls;
-  float4* quats;
-  float* ologit;
+  GeoW g;
   float4* sh;
 };
 
 // Copies row i of one parameter-shaped array set into row o of another.
 __device__ __forceinline__ void copy_row(const ParamsIn& a, int64_t i, const ParamsOut& b, int64_t o) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    b.means[3 * o + c] = a.means[3 * i + c];
-    b.ls[3 * o + c] = a.ls[3 * i + c];
-  }
-  b.quats[o] = a.quats[i];
-  b.ologit[o] = a.ologit[i];
+  const float3 m = a.g.mean(i), l = a.g.lsc(i);
+  float* bm = b.g.mean(o);
+  float* bl = b.g.lsc(o);
+  bm[0] = m.x; bm[1] = m.y; bm[2] = m.z;
+  bl[0] = l.x; bl[1] = l.y; bl[2] = l.z;
+  *b.g.quat(o) = a.g.quat(i);
+  *b.g.opac(o) = a.g.opac(i);
 #pragma unroll
   for (int c = 0; c < 12; ++c) b.sh[12 * o + c] = a.sh[12 * i + c];
 }
 
 __device__ __forceinline__ void zero_row(const ParamsOut& b, int64_t o) {
+  float* bm = b.g.mean(o);
+  float* bl = b.g.lsc(o);
 #pragma unroll
-  for (int c = 0; c < 3; ++c) b.means[3 * o + c] = b.ls[3 * o + c] = 0.f;
-  b.quats[o] = make_float4(0.f, 0.f, 0.f, 0.f);
-  b.ologit[o] = 0.f;
+  for (int c = 0; c < 3; ++c) bm[c] = bl[c] = 0.f;
+  *b.g.quat(o) = make_float4(0.f, 0.f, 0.f, 0.f);
+  *b.g.opac(o) = 0.f;
 #pragma unroll
   for (int c = 0; c < 12; ++c) b.sh[12 * o + c] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
@@ -146,11 +144,13 @@ __global__ void k_dens_scatter(ParamsIn P, ParamsIn M, ParamsIn V, const uint8_t
   const int copies = dens ? 2 : 1;
   if (o + copies > capacity) return;
   int ax = 0;
-  float lmax = P.ls[3 * i];
+  const float3 ls3 = P.g.lsc(i);
+  const float lsa[3] = {ls3.x, ls3.y, ls3.z};
+  float lmax = lsa[0];
 #pragma unroll
   for (int a = 1; a < 3; ++a)
-    if (P.ls[3 * i + a] > lmax) {
-      lmax = P.ls[3 * i + a];
+    if (lsa[a] > lmax) {
+      lmax = lsa[a];
       ax = a;
     }
   const bool split = dens && lmax > k.log_split;
@@ -170,7 +170,7 @@ __global__ void k_dens_scatter(ParamsIn P, ParamsIn M, ParamsIn V, const uint8_t
     copy_row(V, i, VO, o);
   }
   if (split) {
-    const float4 qr = P.quats[i];
+    const float4 qr = P.g.quat(i);
     const float inv = rsqrtf(qr.x * qr.x + qr.y * qr.y + qr.z * qr.z + qr.w * qr.w);
     const float w = qr.x * inv, x = qr.y * inv, y = qr.z * inv, z = qr.w * inv;
     // column ax of the rotation matrix of (w, x, y, z)
@@ -183,13 +183,17 @@ __global__ void k_dens_scatter(ParamsIn P, ParamsIn M, ParamsIn V, const uint8_t
       col[0] = 2.f * (x * z + w * y); col[1] = 2.f * (y * z - w * x); col[2] = 1.f - 2.f * (x * x + y * y);
     }
     const float sig = expf(lmax);
+    const float3 mu3 = P.g.mean(i);
+    const float mu[3] = {mu3.x, mu3.y, mu3.z};
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const float sgn = q == 0 ? 1.f : -1.f;
+      float* om = PO.g.mean(o + q);
+      float* ol = PO.g.lsc(o + q);
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        PO.means[3 * (o + q) + c] = P.means[3 * i + c] + sgn * sig * col[c];
-        PO.ls[3 * (o + q) + c] = P.ls[3 * i + c] - kLogSplit;
+        om[c] = mu[c] + sgn * sig * col[c];
+        ol[c] = lsa[c] - kLogSplit;
       }
     }
   }
@@ -228,19 +232,11 @@ DensWs carve_dens(void* base, int64_t n, size_t* bytes) {
   return w;
 }
 
-bool params_in_ok(const float* m, const float* l, const float* q, const float* o, const float* sh) {
-  return m && l && q && o && sh && aligned16(q) && aligned16(sh);
-}
-
 ParamsIn in_of(const tgs_param_ptrs& p) {
-  return ParamsIn{p.means, p.log_scales, reinterpret_cast<const float4*>(p.quats), p.opacity_logits,
-                  reinterpret_cast<const float4*>(p.sh)};
+  return ParamsIn{geo_const(geo_of(p)), reinterpret_cast<const float4*>(p.sh)};
 }
 
-ParamsOut out_of(const tgs_param_ptrs& p) {
-  return ParamsOut{p.means, p.log_scales, reinterpret_cast<float4*>(p.quats), p.opacity_logits,
-                   reinterpret_cast<float4*>(p.sh)};
-}
+ParamsOut out_of(const tgs_param_ptrs& p) { return ParamsOut{geo_of(p), reinterpret_cast<float4*>(p.sh)}; }
 
 }  // namespace
 
@@ -273,14 +269,8 @@ extern "C" tgs_status tgs_density_control(const tgs_gaussians* g, const tgs_para
   if (!workspace || workspace_bytes < tgs_density_control_workspace_size(n)) return TGS_ERR_INVALID_ARG;
   if (n > 0) {
     if (!stats || !accum || !aligned16(stats) || !aligned8(accum)) return TGS_ERR_INVALID_ARG;
-    if (!params_in_ok(g->means, g->log_scales, g->quats, g->opacity_logits, g->sh) ||
-        !params_in_ok(m_in->means, m_in->log_scales, m_in->quats, m_in->opacity_logits, m_in->sh) ||
-        !params_in_ok(v_in->means, v_in->log_scales, v_in->quats, v_in->opacity_logits, v_in->sh))
-      return TGS_ERR_INVALID_ARG;
-    if (capacity > 0 &&
-        (!params_in_ok(g_out->means, g_out->log_scales, g_out->quats, g_out->opacity_logits, g_out->sh) ||
-         !params_in_ok(m_out->means, m_out->log_scales, m_out->quats, m_out->opacity_logits, m_out->sh) ||
-         !params_in_ok(v_out->means, v_out->log_scales, v_out->quats, v_out->opacity_logits, v_out->sh)))
+    if (!gaussians_ok(g) || !param_ptrs_ok(m_in) || !param_ptrs_ok(v_in)) return TGS_ERR_INVALID_ARG;
+    if (capacity > 0 && (!param_ptrs_ok(g_out) || !param_ptrs_ok(m_out) || !param_ptrs_ok(v_out)))
       return TGS_ERR_INVALID_ARG;
   }
   cudaStream_t s = (cudaStream_t)stream;
@@ -293,7 +283,7 @@ extern "C" tgs_status tgs_density_control(const tgs_gaussians* g, const tgs_para
           cfg->topk_permille, cfg->final_prune, cfg->final_permille};
   const int blocks = (int)((n + 255) / 256);
   cudaMemsetAsync(w.n_rank, 0, sizeof(int32_t), s);
-  k_dens_keys<<<blocks, 256, 0, s>>>(g->opacity_logits, reinterpret_cast<const float4*>(stats),
+  k_dens_keys<<<blocks, 256, 0, s>>>(geo_of(*g), reinterpret_cast<const float4*>(stats),
                                      reinterpret_cast<const float2*>(accum), n, k, w.flag, w.k0, w.v0, w.n_rank);
   const int cur = radix_sort_pairs(w.k0, w.v0, w.k1, w.v1, nullptr, (int32_t)n, 0, 32, w.rs, nullptr, s);
   const uint32_t* order = cur ? w.v1 : w.v0;
@@ -306,7 +296,7 @@ extern "C" tgs_status tgs_density_control(const tgs_gaussians* g, const tgs_para
   if (capacity > 0) {
     const tgs_param_ptrs gin{const_cast<float*>(g->means), const_cast<float*>(g->log_scales),
                              const_cast<float*>(g->quats), const_cast<float*>(g->opacity_logits),
-                             const_cast<float*>(g->sh)};
+                             const_cast<float*>(g->sh), g->geo_stride};
     k_dens_scatter<<<blocks, 256, 0, s>>>(in_of(gin), in_of(*m_in), in_of(*v_in), w.flag, w.off, n, k,
                                           out_of(*g_out), out_of(*m_out), out_of(*v_out), capacity, src_out);
   }

@@ -31,16 +31,19 @@ __global__ void __launch_bounds__(128) k_hybrid_lm(tgs_param_ptrs P, tgs_param_p
   for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += (int64_t)gridDim.x * blockDim.x) {
   const int64_t i = list[q];
   float gg[10];
+  const GeoW gG = geo_of(G);
+  const float* gm = gG.mean(i);
+  const float* gl = gG.lsc(i);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    gg[k] = G.means[3 * i + k];
-    gg[3 + k] = G.log_scales[3 * i + k];
+    gg[k] = gm[k];
+    gg[3 + k] = gl[k];
   }
-  const float4 b = reinterpret_cast<const float4*>(G.quats)[i];
+  const float4 b = *gG.quat(i);
   gg[6] = b.x; gg[7] = b.y; gg[8] = b.z; gg[9] = b.w;
   const float4 g0 = reinterpret_cast<const float4*>(G.sh)[12 * i];
   const float sg[4] = {g0.x, g0.y, g0.z, g0.w};
-  lm_update_one<MODE>(P, M, V, n, i, gg, sg, G.opacity_logits[i], rows, k_rows, o);
+  lm_update_one<MODE>(P, M, V, n, i, gg, sg, *gG.opac(i), rows, k_rows, o);
   }
 }
 
@@ -57,11 +60,6 @@ __global__ void __launch_bounds__(256) k_adam_sh(tgs_param_ptrs P, tgs_param_ptr
   const int64_t i = list[q];
   adam_sh_one(P, M, V, i, k, reinterpret_cast<const float4*>(G.sh)[12 * i + k], o);
   }
-}
-
-static bool ptrs_ok(const tgs_param_ptrs* p) {
-  return p && p->means && p->log_scales && p->quats && p->opacity_logits && p->sh && aligned16(p->quats) &&
-         aligned16(p->sh);
 }
 
 }  // namespace tgs
@@ -81,7 +79,8 @@ extern "C" tgs_status tgs_hybrid_step(const tgs_param_ptrs* params, const tgs_pa
       !(opt->beta1 >= 0.f && opt->beta1 < 1.f) || !(opt->beta2 >= 0.f && opt->beta2 < 1.f) || n >= INT32_MAX)
     return TGS_ERR_INVALID_ARG;
   if (n == 0) return TGS_OK;
-  if (!ptrs_ok(params) || !ptrs_ok(grads) || !ptrs_ok(m) || !ptrs_ok(v)) return TGS_ERR_INVALID_ARG;
+  if (!param_ptrs_ok(params) || !param_ptrs_ok(grads) || !param_ptrs_ok(m) || !param_ptrs_ok(v))
+    return TGS_ERR_INVALID_ARG;
   if (!workspace || workspace_bytes < tgs_hybrid_step_workspace_size(n)) return TGS_ERR_INVALID_ARG;
   OptK o = make_optk(opt, step, step_dev);
   cudaStream_t s = (cudaStream_t)stream;

@@ -112,15 +112,22 @@ __device__ __forceinline__ void lm_update_one(const tgs_param_ptrs& P, const tgs
                                               const float (&sg)[4], float og, const float* __restrict__ rows,
                                               int k_rows, const OptK& o) {
   float gp[10], gm[10], gv[10];
+  const GeoW gP = geo_of(P), gM = geo_of(M), gV = geo_of(V);
+  {
+    const float* a = gP.mean(i);
+    const float* b = gM.mean(i);
+    const float* c = gV.mean(i);
+    const float* d = gP.lsc(i);
+    const float* e = gM.lsc(i);
+    const float* f = gV.lsc(i);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    gp[k] = P.means[3 * i + k]; gm[k] = M.means[3 * i + k]; gv[k] = V.means[3 * i + k];
-    gp[3 + k] = P.log_scales[3 * i + k];
-    gm[3 + k] = M.log_scales[3 * i + k]; gv[3 + k] = V.log_scales[3 * i + k];
+    for (int k = 0; k < 3; ++k) {
+      gp[k] = a[k]; gm[k] = b[k]; gv[k] = c[k];
+      gp[3 + k] = d[k]; gm[3 + k] = e[k]; gv[3 + k] = f[k];
+    }
   }
   {
-    const float4 a = reinterpret_cast<const float4*>(P.quats)[i];
-    const float4 c = reinterpret_cast<const float4*>(M.quats)[i], d = reinterpret_cast<const float4*>(V.quats)[i];
+    const float4 a = *gP.quat(i), c = *gM.quat(i), d = *gV.quat(i);
     gp[6] = a.x; gp[7] = a.y; gp[8] = a.z; gp[9] = a.w;
     gm[6] = c.x; gm[7] = c.y; gm[8] = c.z; gm[9] = c.w;
     gv[6] = d.x; gv[7] = d.y; gv[8] = d.z; gv[9] = d.w;
@@ -129,7 +136,7 @@ __device__ __forceinline__ void lm_update_one(const tgs_param_ptrs& P, const tgs
   const float4 m0 = reinterpret_cast<const float4*>(M.sh)[12 * i], v0 = reinterpret_cast<const float4*>(V.sh)[12 * i];
   float sp[4] = {p0.x, p0.y, p0.z, p0.w};
   float smm[4] = {m0.x, m0.y, m0.z, m0.w}, sv[4] = {v0.x, v0.y, v0.z, v0.w};
-  float op = P.opacity_logits[i], om = M.opacity_logits[i], ov = V.opacity_logits[i];
+  float op = *gP.opac(i), om = *gM.opac(i), ov = *gV.opac(i);
 #pragma unroll
   for (int k = 0; k < 10; ++k) moments(gg[k], gm[k], gv[k], o);
 #pragma unroll
@@ -155,15 +162,23 @@ __device__ __forceinline__ void lm_update_one(const tgs_param_ptrs& P, const tgs
     op += o.lr[3] * dapp[3];
   }
   sp[3] += adam_delta(smm[3], sv[3], o.lr[5], o);
+  {
+    float* a = gP.mean(i);
+    float* b = gM.mean(i);
+    float* c = gV.mean(i);
+    float* d = gP.lsc(i);
+    float* e = gM.lsc(i);
+    float* f = gV.lsc(i);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    P.means[3 * i + k] = gp[k]; M.means[3 * i + k] = gm[k]; V.means[3 * i + k] = gv[k];
-    P.log_scales[3 * i + k] = gp[3 + k]; M.log_scales[3 * i + k] = gm[3 + k]; V.log_scales[3 * i + k] = gv[3 + k];
+    for (int k = 0; k < 3; ++k) {
+      a[k] = gp[k]; b[k] = gm[k]; c[k] = gv[k];
+      d[k] = gp[3 + k]; e[k] = gm[3 + k]; f[k] = gv[3 + k];
+    }
   }
-  reinterpret_cast<float4*>(P.quats)[i] = make_float4(gp[6], gp[7], gp[8], gp[9]);
-  reinterpret_cast<float4*>(M.quats)[i] = make_float4(gm[6], gm[7], gm[8], gm[9]);
-  reinterpret_cast<float4*>(V.quats)[i] = make_float4(gv[6], gv[7], gv[8], gv[9]);
-  P.opacity_logits[i] = op; M.opacity_logits[i] = om; V.opacity_logits[i] = ov;
+  *gP.quat(i) = make_float4(gp[6], gp[7], gp[8], gp[9]);
+  *gM.quat(i) = make_float4(gm[6], gm[7], gm[8], gm[9]);
+  *gV.quat(i) = make_float4(gv[6], gv[7], gv[8], gv[9]);
+  *gP.opac(i) = op; *gM.opac(i) = om; *gV.opac(i) = ov;
   reinterpret_cast<float4*>(P.sh)[12 * i] = make_float4(sp[0], sp[1], sp[2], sp[3]);
   reinterpret_cast<float4*>(M.sh)[12 * i] = make_float4(smm[0], smm[1], smm[2], smm[3]);
   reinterpret_cast<float4*>(V.sh)[12 * i] = make_float4(sv[0], sv[1], sv[2], sv[3]);

@@ -384,6 +384,10 @@ static int mlp_grid(int64_t R) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((tiles + 3) / 4, (int64_t)device_sm_count() * 8));
 }
 
+tgs_status launch_mlp_wgrad_tc(const float* x, const uint16_t* h1, const uint16_t* h2, const float* dy,
+                               const uint16_t* dh2, const uint16_t* dh1, int64_t R, float* grads, int32_t* status,
+                               cudaStream_t s);
+
 }  // namespace tgs
 
 using namespace tgs;
@@ -412,12 +416,14 @@ extern "C" size_t tgs_mlp_backward_workspace_size(int64_t rows) {
   return align_up(R * 4, 256) + 2 * align_up(R * MH * 2, 256);
 }
 
-extern "C" tgs_status tgs_mlp_backward(const tgs_mlp* w, int64_t rows, const int32_t* rows_dev, const float* x,
-                                       const uint16_t* h1,
-                                       const uint16_t* h2, const float* y, const float* target, float* grads,
-                                       double* loss, void* workspace, size_t workspace_bytes, tgs_stream stream) {
+static tgs_status mlp_backward_impl(const tgs_mlp* w, int64_t rows, const int32_t* rows_dev, const float* x,
+                                    const uint16_t* h1, const uint16_t* h2, const float* y, const float* target,
+                                    float* grads, double* loss, void* workspace, size_t workspace_bytes,
+                                    bool tc, int32_t* status, tgs_stream stream) {
   if (!mlp_ok(w) || rows < 0 || !grads || !loss) return TGS_ERR_INVALID_ARG;
   if (rows > 0 && (!x || !h1 || !h2 || !y || !target || !aligned4(h1) || !aligned4(h2))) return TGS_ERR_INVALID_ARG;
+  if (tc && rows > 0 && (!aligned16(x) || !aligned16(h1) || !aligned16(h2) || !aligned16(workspace)))
+    return TGS_ERR_INVALID_ARG;
   if (!workspace || workspace_bytes < tgs_mlp_backward_workspace_size(rows)) return TGS_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   cudaMemsetAsync(grads, 0, sizeof(float) * N_PARAMS, s);
@@ -438,6 +444,11 @@ extern "C" tgs_status tgs_mlp_backward(const tgs_mlp* w, int64_t rows, const int
   k_mlp_backward_act<<<mlp_grid(rows), 128, smem, s>>>(mlp_k(w), h1, h2, y, target, rows, rows_dev, dy, dh2, dh1,
                                                         loss);
   // chunks: whole kWgRows groups, at most 4 blocks per SM's worth
+  if (tc) {
+    const tgs_status st = check_launch();
+    if (st != TGS_OK) return st;
+    return launch_mlp_wgrad_tc(x, h1, h2, dy, dh2, dh1, rows, grads, status, s);
+  }
   const int64_t groups = (rows + kWgRows - 1) / kWgRows;
   const int64_t waves = (int64_t)device_sm_count() * 4;
   const int64_t per = std::max<int64_t>(1, (groups + waves - 1) / waves);
@@ -445,6 +456,22 @@ extern "C" tgs_status tgs_mlp_backward(const tgs_mlp* w, int64_t rows, const int
   k_mlp_wgrad<<<(unsigned)((rows + chunk - 1) / chunk), kWgThreads, 0, s>>>(x, h1, h2, dy, dh2, dh1, rows, chunk,
                                                                           grads);
   return check_launch();
+}
+
+extern "C" tgs_status tgs_mlp_backward(const tgs_mlp* w, int64_t rows, const int32_t* rows_dev, const float* x,
+                                       const uint16_t* h1, const uint16_t* h2, const float* y, const float* target,
+                                       float* grads, double* loss, void* workspace, size_t workspace_bytes,
+                                       tgs_stream stream) {
+  return mlp_backward_impl(w, rows, rows_dev, x, h1, h2, y, target, grads, loss, workspace, workspace_bytes, false,
+                           nullptr, stream);
+}
+
+extern "C" tgs_status tgs_mlp_backward_tc(const tgs_mlp* w, int64_t rows, const int32_t* rows_dev, const float* x,
+                                          const uint16_t* h1, const uint16_t* h2, const float* y,
+                                          const float* target, float* grads, double* loss, int32_t* status,
+                                          void* workspace, size_t workspace_bytes, tgs_stream stream) {
+  return mlp_backward_impl(w, rows, rows_dev, x, h1, h2, y, target, grads, loss, workspace, workspace_bytes, true,
+                           status, stream);
 }
 
 extern "C" tgs_status tgs_mlp_adam(float* params, const float* grads, float* m, float* v, int32_t step, float lr,

@@ -176,15 +176,14 @@ __device__ __forceinline__ bool touches_active(const CamK& cam, const float xy[2
 }
 
 __global__ void __launch_bounds__(256) k_project(
-    const float* __restrict__ means, const float* __restrict__ log_scales, const float4* __restrict__ quats,
-    const float* __restrict__ ologit, const float4* __restrict__ sh, int64_t n, int sh_degree, CamK cam,
+    GeoC geo, const float4* __restrict__ sh, int64_t n, int sh_degree, CamK cam,
     const int32_t* __restrict__ tile_rank, float2* __restrict__ xy_out, float4* __restrict__ conic_out,
     float* __restrict__ rgb_out, float* __restrict__ depth_out, int32_t* __restrict__ radius_out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  float3 mu = make_float3(means[3 * i], means[3 * i + 1], means[3 * i + 2]);
-  float3 ls = make_float3(log_scales[3 * i], log_scales[3 * i + 1], log_scales[3 * i + 2]);
-  float4 qr = quats[i];
+  float3 mu = geo.mean(i);
+  float3 ls = geo.lsc(i);
+  float4 qr = geo.quat(i);
   Geo g;
   bool vis = geometry(cam, mu, ls, qr, g) && touches_active(cam, g.xy, g.radius, tile_rank);
   if (!vis) {
@@ -220,7 +219,7 @@ __global__ void __launch_bounds__(256) k_project(
     }
   }
   xy_out[i] = make_float2(g.xy[0], g.xy[1]);
-  conic_out[i] = make_float4(g.conic[0], g.conic[1], g.conic[2], 1.f / (1.f + expf(-ologit[i])));
+  conic_out[i] = make_float4(g.conic[0], g.conic[1], g.conic[2], 1.f / (1.f + expf(-geo.opac(i))));
   rgb_out[3 * i] = fmaxf(acc[0], 0.f);
   rgb_out[3 * i + 1] = fmaxf(acc[1], 0.f);
   rgb_out[3 * i + 2] = fmaxf(acc[2], 0.f);
@@ -286,8 +285,6 @@ template <class Sh>
 __device__ __forceinline__ void view_adjoint(const CamK& cam, float3 mu, float3 ls, float4 qr, float o,
                                              const float4* __restrict__ shp, int sh_degree, float4 ga, float4 gb,
                                              float4 gc, float* __restrict__ rw, AdjAcc<Sh>& acc) {
-  Geo g;
-  geometry(cam, mu, ls, qr, g);  // visible by construction (radius > 0)
   const float d_x = ga.x, d_y = ga.y, d_a = ga.z, d_b = ga.w, d_c = gb.x, d_o = gb.y;
   const float drgb[3] = {gb.z, gb.w, gc.x};
   const float g_o = d_o * o * (1.f - o);
@@ -356,6 +353,10 @@ __device__ __forceinline__ void view_adjoint(const CamK& cam, float3 mu, float3 
   sh_basis_grad(dx, dy, dz, sh_degree, sk, gd);
   const float dot = gd[0] * dx + gd[1] * dy + gd[2] * dz;
   float dmu[3] = {(gd[0] - dx * dot) * il, (gd[1] - dy * dot) * il, (gd[2] - dz * dot) * il};
+  // the geometry after the colour part, so that its state and the SH basis
+  // are not live at the same time
+  Geo g;
+  geometry(cam, mu, ls, qr, g);  // visible by construction (radius > 0)
   // centre
   const float z = g.pc[2], iz = 1.f / z, iz2 = iz * iz;
   float dpc[3];
@@ -483,9 +484,8 @@ __device__ __forceinline__ void store_sh(const DirectSh&, float4*, Put4) {}  // 
 
 // Writes (add = false) or adds (add = true) acc into the gradient arrays.
 template <class Sh>
-__device__ __forceinline__ void acc_store(const AdjAcc<Sh>& a, int64_t i, bool add, float* __restrict__ g_means,
-                                          float* __restrict__ g_ls, float4* __restrict__ g_quats,
-                                          float* __restrict__ g_ologit, float4* __restrict__ g_sh) {
+__device__ __forceinline__ void acc_store(const AdjAcc<Sh>& a, int64_t i, bool add, const GeoW& gw,
+                                          float4* __restrict__ g_sh) {
   auto put = [&](float* p, float v) { *p = add ? *p + v : v; };
   auto put4 = [&](float4* p, float4 v) {
     if (add) {
@@ -494,13 +494,15 @@ __device__ __forceinline__ void acc_store(const AdjAcc<Sh>& a, int64_t i, bool a
     }
     *p = v;
   };
+  float* gm = gw.mean(i);
+  float* gl = gw.lsc(i);
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    put(g_means + 3 * i + k, a.mu[k]);
-    put(g_ls + 3 * i + k, a.ls[k]);
+    put(gm + k, a.mu[k]);
+    put(gl + k, a.ls[k]);
   }
-  put4(g_quats + i, make_float4(a.q[0], a.q[1], a.q[2], a.q[3]));
-  put(g_ologit + i, a.o);
+  put4(gw.quat(i), make_float4(a.q[0], a.q[1], a.q[2], a.q[3]));
+  put(gw.opac(i), a.o);
   store_sh(a.sh, g_sh + 12 * i, put4);
 }
 
@@ -510,22 +512,20 @@ __device__ __forceinline__ void zero_row(float* row, int64_t i) {
   for (int k = 0; k < 7; ++k) r2[k] = make_float2(0.f, 0.f);
 }
 
-__device__ __forceinline__ void zero_grads(int64_t i, float* __restrict__ g_means, float* __restrict__ g_ls,
-                                           float4* __restrict__ g_quats, float* __restrict__ g_ologit,
-                                           float4* __restrict__ g_sh) {
-  g_means[3 * i] = 0.f; g_means[3 * i + 1] = 0.f; g_means[3 * i + 2] = 0.f;
-  g_ls[3 * i] = 0.f; g_ls[3 * i + 1] = 0.f; g_ls[3 * i + 2] = 0.f;
-  g_quats[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  g_ologit[i] = 0.f;
+__device__ __forceinline__ void zero_grads(int64_t i, const GeoW& gw, float4* __restrict__ g_sh) {
+  float* gm = gw.mean(i);
+  float* gl = gw.lsc(i);
+  gm[0] = 0.f; gm[1] = 0.f; gm[2] = 0.f;
+  gl[0] = 0.f; gl[1] = 0.f; gl[2] = 0.f;
+  *gw.quat(i) = make_float4(0.f, 0.f, 0.f, 0.f);
+  *gw.opac(i) = 0.f;
 #pragma unroll
   for (int k = 0; k < 12; ++k) g_sh[12 * i + k] = make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
 __global__ void __launch_bounds__(256) k_project_bwd(
-    const float* __restrict__ means, const float* __restrict__ log_scales, const float4* __restrict__ quats,
-    const float* __restrict__ ologit, const float4* __restrict__ sh, int64_t n, int sh_degree, CamK cam,
-    const int32_t* __restrict__ radius, const float4* __restrict__ grad2d, float* __restrict__ g_means,
-    float* __restrict__ g_ls, float4* __restrict__ g_quats, float* __restrict__ g_ologit, float4* __restrict__ g_sh,
+    GeoC geo, const float4* __restrict__ sh, int64_t n, int sh_degree, CamK cam,
+    const int32_t* __restrict__ radius, const float4* __restrict__ grad2d, GeoW gw, float4* __restrict__ g_sh,
     uint8_t* __restrict__ touched, int write_untouched, int accumulate, float* __restrict__ row) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -546,18 +546,19 @@ __global__ void __launch_bounds__(256) k_project_bwd(
   }
   if (!any) {
     if (row) zero_row(row, i);
-    if (write_untouched && !accumulate) zero_grads(i, g_means, g_ls, g_quats, g_ologit, g_sh);
+    if (write_untouched && !accumulate) zero_grads(i, gw, g_sh);
     return;
   }
-  const float3 mu = make_float3(means[3 * i], means[3 * i + 1], means[3 * i + 2]);
-  const float3 ls = make_float3(log_scales[3 * i], log_scales[3 * i + 1], log_scales[3 * i + 2]);
-  const float o = 1.f / (1.f + expf(-ologit[i]));
+  const float3 mu = geo.mean(i);
+  const float3 ls = geo.lsc(i);
+  const float o = 1.f / (1.f + expf(-geo.opac(i)));
   AdjAcc<DirectSh> acc;
   acc_zero(acc);
   acc.sh.out = g_sh + 12 * i;
   acc.sh.accumulate = add;
-  view_adjoint(cam, mu, ls, quats[i], o, sh + 12 * i, sh_degree, ga, gb, gc, row ? row + 14 * i : nullptr, acc);
-  acc_store(acc, i, add, g_means, g_ls, g_quats, g_ologit, g_sh);
+  view_adjoint(cam, mu, ls, geo.quat(i), o, sh + 12 * i, sh_degree, ga, gb, gc, row ? row + 14 * i : nullptr,
+               acc);
+  acc_store(acc, i, add, gw, g_sh);
 }
 
 void launch_project_bwd(const tgs_gaussians& g, const tgs_camera& cam, const int32_t* radius, const float* grad2d,
@@ -566,10 +567,8 @@ void launch_project_bwd(const tgs_gaussians& g, const tgs_camera& cam, const int
   if (g.n <= 0) return;
   CamK k = make_cam(cam);
   int blocks = (int)((g.n + 255) / 256);
-  k_project_bwd<<<blocks, 256, 0, s>>>(g.means, g.log_scales, reinterpret_cast<const float4*>(g.quats),
-                                       g.opacity_logits, reinterpret_cast<const float4*>(g.sh), g.n, g.sh_degree, k,
-                                       radius, reinterpret_cast<const float4*>(grad2d), grads.means, grads.log_scales,
-                                       reinterpret_cast<float4*>(grads.quats), grads.opacity_logits,
+  k_project_bwd<<<blocks, 256, 0, s>>>(geo_of(g), reinterpret_cast<const float4*>(g.sh), g.n, g.sh_degree, k,
+                                       radius, reinterpret_cast<const float4*>(grad2d), geo_of(grads),
                                        reinterpret_cast<float4*>(grads.sh), touched, write_untouched, accumulate, row);
 }
 
@@ -590,9 +589,7 @@ struct MultiAdj {
 // ones with their view masks (order of the list is irrelevant: every entry is
 // computed on its own).
 __global__ void __launch_bounds__(256) k_adj_mark(int64_t n, MultiAdj mv, uint8_t* __restrict__ touched,
-                                                  int write_untouched, float* __restrict__ g_means,
-                                                  float* __restrict__ g_ls, float4* __restrict__ g_quats,
-                                                  float* __restrict__ g_ologit, float4* __restrict__ g_sh,
+                                                  int write_untouched, GeoW gw, float4* __restrict__ g_sh,
                                                   uint2* __restrict__ list, int32_t* __restrict__ count) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = i < n;
@@ -608,7 +605,7 @@ __global__ void __launch_bounds__(256) k_adj_mark(int64_t n, MultiAdj mv, uint8_
       else if (mv.row[v]) zero_row(mv.row[v], i);
     }
     if (touched) touched[i] = hit ? 1 : 0;
-    if (!hit && write_untouched) zero_grads(i, g_means, g_ls, g_quats, g_ologit, g_sh);
+    if (!hit && write_untouched) zero_grads(i, gw, g_sh);
   }
   const int64_t pos = block_append(hit != 0, count);
   if (hit) list[pos] = make_uint2((uint32_t)i, hit);
@@ -618,21 +615,18 @@ constexpr int kAdjThreads = 128;
 
 // Pass 2 over the touched Gaussians: the sum of their views' adjoints.
 __global__ void __launch_bounds__(kAdjThreads, 4) k_adj_multi(
-    const float* __restrict__ means, const float* __restrict__ log_scales, const float4* __restrict__ quats,
-    const float* __restrict__ ologit, const float4* __restrict__ sh, int sh_degree, MultiAdj mv,
-    const uint2* __restrict__ list, const int32_t* __restrict__ count, float* __restrict__ g_means,
-    float* __restrict__ g_ls, float4* __restrict__ g_quats, float* __restrict__ g_ologit,
-    float4* __restrict__ g_sh) {
+    GeoC geo, const float4* __restrict__ sh, int sh_degree, MultiAdj mv, const uint2* __restrict__ list,
+    const int32_t* __restrict__ count, GeoW gw, float4* __restrict__ g_sh) {
   __shared__ float s_sh[48 * kAdjThreads];
   const int cnt = *count;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
     const uint2 it = list[e];
     const int64_t i = it.x;
     unsigned hit = it.y;
-    const float3 mu = make_float3(means[3 * i], means[3 * i + 1], means[3 * i + 2]);
-    const float3 ls = make_float3(log_scales[3 * i], log_scales[3 * i + 1], log_scales[3 * i + 2]);
-    const float4 qr = quats[i];
-    const float o = 1.f / (1.f + expf(-ologit[i]));
+    const float3 mu = geo.mean(i);
+    const float3 ls = geo.lsc(i);
+    const float4 qr = geo.quat(i);
+    const float o = 1.f / (1.f + expf(-geo.opac(i)));
     AdjAcc<SmemSh> acc;
     acc.sh.base = s_sh + threadIdx.x;
     acc.sh.stride = kAdjThreads;
@@ -644,7 +638,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4) k_adj_multi(
       view_adjoint(mv.cam[v], mu, ls, qr, o, sh + 12 * i, sh_degree, gp[0], gp[1], gp[2],
                    mv.row[v] ? mv.row[v] + 14 * i : nullptr, acc);
     }
-    acc_store(acc, i, false, g_means, g_ls, g_quats, g_ologit, g_sh);
+    acc_store(acc, i, false, gw, g_sh);
   }
 }
 
@@ -661,18 +655,21 @@ __global__ void __launch_bounds__(kAdjThreads, 4) k_adj_multi(
 // and load), eight Gaussians per warp, every load of a lane issued before its
 // first store.  The column stride kShStride = 130 keeps both phases free of
 // shared-memory bank conflicts (phase 1: bank 2k + t; phase 2: bank
-// 8 kk + g8 + const over the warp's lanes).
+// 8 kk + g8 + const over the warp's lanes).  Two blocks per SM: the adjoint
+// then fits its registers without spilling (three blocks at 168 registers
+// spilled 356 bytes a thread and measured 80.5 against 76.8 us at the 500k
+// workload).
 constexpr int kShStride = 130;
 
 template <int MODE>
-__global__ void __launch_bounds__(kAdjThreads, 3) k_adj_update(
+__global__ void __launch_bounds__(kAdjThreads, 2) k_adj_update(
     tgs_param_ptrs P, tgs_param_ptrs M, tgs_param_ptrs V, int64_t n, int sh_degree, MultiAdj mv,
     const uint2* __restrict__ list, const int32_t* __restrict__ count, OptK o) {
   __shared__ float s_sh[48 * kShStride];
   __shared__ uint32_t s_idx[kAdjThreads];
   bias_corrections(o);
   const int cnt = *count;
-  const float4* quats = reinterpret_cast<const float4*>(P.quats);
+  const GeoC geo = geo_const(geo_of(P));
   const float4* sh = reinterpret_cast<const float4*>(P.sh);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int kk = lane >> 3, g8 = lane & 7;
@@ -682,10 +679,10 @@ __global__ void __launch_bounds__(kAdjThreads, 3) k_adj_update(
       const uint2 it = list[e];
       const int64_t i = it.x;
       unsigned hit = it.y;
-      const float3 mu = make_float3(P.means[3 * i], P.means[3 * i + 1], P.means[3 * i + 2]);
-      const float3 ls = make_float3(P.log_scales[3 * i], P.log_scales[3 * i + 1], P.log_scales[3 * i + 2]);
-      const float4 qr = quats[i];
-      const float o_s = 1.f / (1.f + expf(-P.opacity_logits[i]));
+      const float3 mu = geo.mean(i);
+      const float3 ls = geo.lsc(i);
+      const float4 qr = geo.quat(i);
+      const float o_s = 1.f / (1.f + expf(-geo.opac(i)));
       AdjAcc<SmemSh> acc;
       acc.sh.base = s_sh + threadIdx.x;
       acc.sh.stride = kShStride;
@@ -758,9 +755,7 @@ extern "C" tgs_status tgs_project_backward_multi(const tgs_gaussians* g, int32_t
                                                  void* workspace, size_t workspace_bytes, tgs_stream stream) {
   if (!gaussians_ok(g) || n_views < 1 || n_views > kMaxAdjViews || !cams || !radius || !grad2d || !grads)
     return TGS_ERR_INVALID_ARG;
-  if (!grads->means || !grads->log_scales || !grads->quats || !grads->opacity_logits || !grads->sh ||
-      !aligned16(grads->quats) || !aligned16(grads->sh))
-    return TGS_ERR_INVALID_ARG;
+  if (!param_ptrs_ok(grads)) return TGS_ERR_INVALID_ARG;
   if (!workspace || !aligned16(workspace) || workspace_bytes < tgs_project_backward_multi_workspace_size(g->n))
     return TGS_ERR_INVALID_ARG;
   MultiAdj mv;
@@ -779,10 +774,8 @@ extern "C" tgs_status tgs_project_backward_multi(const tgs_gaussians* g, int32_t
   int32_t* count = reinterpret_cast<int32_t*>(workspace);
   uint2* list = reinterpret_cast<uint2*>(reinterpret_cast<char*>(workspace) + 256);
   cudaMemsetAsync(count, 0, sizeof(int32_t), s);
-  k_adj_mark<<<(int)((g->n + 255) / 256), 256, 0, s>>>(g->n, mv, touched, write_untouched, grads->means,
-                                                       grads->log_scales, reinterpret_cast<float4*>(grads->quats),
-                                                       grads->opacity_logits, reinterpret_cast<float4*>(grads->sh),
-                                                       list, count);
+  k_adj_mark<<<(int)((g->n + 255) / 256), 256, 0, s>>>(g->n, mv, touched, write_untouched, geo_of(*grads),
+                                                       reinterpret_cast<float4*>(grads->sh), list, count);
   static int grid_dev[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -794,11 +787,8 @@ extern "C" tgs_status tgs_project_backward_multi(const tgs_gaussians* g, int32_t
     grid_dev[dev] = std::max(1, sms * std::max(1, per_sm));
   }
   const int grid = (int)std::min<int64_t>(grid_dev[dev], (g->n + kAdjThreads - 1) / kAdjThreads);
-  k_adj_multi<<<grid, kAdjThreads, 0, s>>>(g->means, g->log_scales, reinterpret_cast<const float4*>(g->quats),
-                                           g->opacity_logits, reinterpret_cast<const float4*>(g->sh), g->sh_degree,
-                                           mv, list, count, grads->means, grads->log_scales,
-                                           reinterpret_cast<float4*>(grads->quats), grads->opacity_logits,
-                                           reinterpret_cast<float4*>(grads->sh));
+  k_adj_multi<<<grid, kAdjThreads, 0, s>>>(geo_of(*g), reinterpret_cast<const float4*>(g->sh), g->sh_degree, mv,
+                                           list, count, geo_of(*grads), reinterpret_cast<float4*>(grads->sh));
   return check_launch();
 }
 
@@ -814,13 +804,11 @@ extern "C" tgs_status tgs_project_backward_update(const tgs_param_ptrs* params, 
       opt->mode > 1 || !(opt->beta1 >= 0.f && opt->beta1 < 1.f) || !(opt->beta2 >= 0.f && opt->beta2 < 1.f))
     return TGS_ERR_INVALID_ARG;
   const tgs_gaussians gs{params->means, params->log_scales, params->quats, params->opacity_logits, params->sh, n,
-                         sh_degree};
+                         sh_degree, params->geo_stride};
   const tgs_gaussians* g = &gs;
   if (!gaussians_ok(g)) return TGS_ERR_INVALID_ARG;
   for (const tgs_param_ptrs* q : {m, v})
-    if (!q->means || !q->log_scales || !q->quats || !q->opacity_logits || !q->sh || !aligned16(q->quats) ||
-        !aligned16(q->sh))
-      return TGS_ERR_INVALID_ARG;
+    if (!param_ptrs_ok(q)) return TGS_ERR_INVALID_ARG;
   if (!workspace || !aligned16(workspace) || workspace_bytes < tgs_project_backward_multi_workspace_size(g->n))
     return TGS_ERR_INVALID_ARG;
   MultiAdj mv;
@@ -838,8 +826,7 @@ extern "C" tgs_status tgs_project_backward_update(const tgs_param_ptrs* params, 
   uint2* list = reinterpret_cast<uint2*>(reinterpret_cast<char*>(workspace) + 256);
   cudaMemsetAsync(count, 0, sizeof(int32_t), s);
   // the mark pass writes no gradients (nothing to zero)
-  k_adj_mark<<<(int)((g->n + 255) / 256), 256, 0, s>>>(g->n, mv, touched, 0, nullptr, nullptr, nullptr, nullptr,
-                                                       nullptr, list, count);
+  k_adj_mark<<<(int)((g->n + 255) / 256), 256, 0, s>>>(g->n, mv, touched, 0, GeoW{}, nullptr, list, count);
   static int grid_dev[64][2] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -865,7 +852,7 @@ extern "C" tgs_status tgs_project_backward_update(const tgs_param_ptrs* params, 
 namespace tgs {
 
 bool gaussians_ok(const tgs_gaussians* g) {
-  if (!g || g->n < 0 || g->sh_degree < 0 || g->sh_degree > 3) return false;
+  if (!g || g->n < 0 || g->sh_degree < 0 || g->sh_degree > 3 || !geo_stride_ok(g->geo_stride)) return false;
   if (g->n == 0) return true;
   return g->means && g->log_scales && g->quats && g->opacity_logits && g->sh && aligned4(g->means) &&
          aligned4(g->log_scales) && aligned16(g->quats) && aligned4(g->opacity_logits) && aligned16(g->sh);
@@ -890,8 +877,7 @@ extern "C" tgs_status tgs_project_gaussians(const tgs_gaussians* g, const tgs_ca
   CamK k = make_cam(*cam);
   int blocks = (int)((g->n + 255) / 256);
   k_project<<<blocks, 256, 0, (cudaStream_t)stream>>>(
-      g->means, g->log_scales, reinterpret_cast<const float4*>(g->quats), g->opacity_logits,
-      reinterpret_cast<const float4*>(g->sh), g->n, g->sh_degree, k, tile_rank,
+      geo_of(*g), reinterpret_cast<const float4*>(g->sh), g->n, g->sh_degree, k, tile_rank,
       reinterpret_cast<float2*>(out->xy), reinterpret_cast<float4*>(out->conic_opac), out->rgb, out->depth,
       out->radius);
   return check_launch();

@@ -1434,8 +1434,7 @@ extern "C" tgs_status tgs_backward_sampled(const tgs_gaussians* g, const tgs_cam
   if (!raster_args(proj, tile_ranges, vals, active_tiles, n_active, pix_off, pix_idx, cam, bg, a))
     return TGS_ERR_INVALID_ARG;
   if (!T_final || !n_last || !dL_drgb || !grads || !proj->radius) return TGS_ERR_INVALID_ARG;
-  if (g->n > 0 && (!grad2d || !aligned16(grad2d) || !grads->means || !grads->log_scales || !grads->quats ||
-                   !grads->opacity_logits || !grads->sh || !aligned16(grads->quats) || !aligned16(grads->sh)))
+  if (g->n > 0 && (!grad2d || !aligned16(grad2d) || !param_ptrs_ok(grads)))
     return TGS_ERR_INVALID_ARG;
   const tgs_status st = tgs_render_backward_sampled(proj, tile_ranges, vals, active_tiles, n_active, n_active_max,
                                                     pix_off, pix_idx, n_pix_max, cam, bg, T_final, n_last, dL_drgb,
@@ -1589,8 +1588,7 @@ extern "C" tgs_status tgs_project_backward(const tgs_gaussians* g, const tgs_cam
   if (accumulate && !touched) return TGS_ERR_INVALID_ARG;
   if (view_row && !aligned8(view_row)) return TGS_ERR_INVALID_ARG;
   if (g->n == 0) return TGS_OK;
-  if (!proj->radius || !grad2d || !aligned16(grad2d) || !grads->means || !grads->log_scales || !grads->quats ||
-      !grads->opacity_logits || !grads->sh || !aligned16(grads->quats) || !aligned16(grads->sh))
+  if (!proj->radius || !grad2d || !aligned16(grad2d) || !param_ptrs_ok(grads))
     return TGS_ERR_INVALID_ARG;
   launch_project_bwd(*g, *cam, proj->radius, grad2d, *grads, touched, write_untouched, accumulate, view_row,
                      (cudaStream_t)stream);

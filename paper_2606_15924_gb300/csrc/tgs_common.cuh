@@ -32,6 +32,66 @@ inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 inline bool aligned8(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 7u) == 0; }
 inline bool aligned4(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 3u) == 0; }
 
+// ---------------------------------------------------------------------------
+// Geometric fields of Gaussian i (means, log-scales, quats, opacity logits)
+// in either layout of tgs_gaussians::geo_stride: four packed arrays (stride
+// 0: 3, 3, 4 and 1 floats per Gaussian) or views into one array of rows of
+// geo_stride floats.
+// ---------------------------------------------------------------------------
+inline bool geo_stride_ok(int32_t s) { return s == 0 || (s >= 12 && s % 4 == 0); }
+
+struct GeoC {  // read-only view
+  const float* m;
+  const float* l;
+  const float4* q;
+  const float* o;
+  int s3, s4, s1;  // strides: means / log-scales (floats), quats (float4s), opacity (floats)
+  __device__ __forceinline__ float3 mean(int64_t i) const {
+    const float* p = m + i * s3;
+    return make_float3(p[0], p[1], p[2]);
+  }
+  __device__ __forceinline__ float3 lsc(int64_t i) const {
+    const float* p = l + i * s3;
+    return make_float3(p[0], p[1], p[2]);
+  }
+  __device__ __forceinline__ float4 quat(int64_t i) const { return q[i * s4]; }
+  __device__ __forceinline__ float opac(int64_t i) const { return o[i * s1]; }
+};
+
+struct GeoW {  // writable view
+  float* m;
+  float* l;
+  float4* q;
+  float* o;
+  int s3, s4, s1;
+  __device__ __forceinline__ float* mean(int64_t i) const { return m + i * s3; }
+  __device__ __forceinline__ float* lsc(int64_t i) const { return l + i * s3; }
+  __device__ __forceinline__ float4* quat(int64_t i) const { return q + i * s4; }
+  __device__ __forceinline__ float* opac(int64_t i) const { return o + i * s1; }
+};
+
+__host__ __device__ inline GeoC geo_of(const tgs_gaussians& g) {
+  const int s = g.geo_stride;
+  return GeoC{g.means, g.log_scales, reinterpret_cast<const float4*>(g.quats), g.opacity_logits, s ? s : 3,
+              s ? s / 4 : 1, s ? s : 1};
+}
+
+__host__ __device__ inline GeoW geo_of(const tgs_param_ptrs& p) {
+  const int s = p.geo_stride;
+  return GeoW{p.means, p.log_scales, reinterpret_cast<float4*>(p.quats), p.opacity_logits, s ? s : 3,
+              s ? s / 4 : 1, s ? s : 1};
+}
+
+__host__ __device__ inline GeoC geo_const(const GeoW& w) { return GeoC{w.m, w.l, w.q, w.o, w.s3, w.s4, w.s1}; }
+
+// Pointers, alignment and stride of a parameter set (quats and sh 16-byte
+// aligned, the rest 4-byte aligned).
+inline bool param_ptrs_ok(const tgs_param_ptrs* p) {
+  return p && p->means && p->log_scales && p->quats && p->opacity_logits && p->sh && aligned4(p->means) &&
+         aligned4(p->log_scales) && aligned16(p->quats) && aligned4(p->opacity_logits) && aligned16(p->sh) &&
+         geo_stride_ok(p->geo_stride);
+}
+
 inline int tiles_x(int w) { return (w + TGS_TILE - 1) / TGS_TILE; }
 inline int tiles_y(int h) { return (h + TGS_TILE - 1) / TGS_TILE; }
 

@@ -25,8 +25,46 @@ def tiles_of(width: int, height: int) -> int:
     return ((width + TILE - 1) // TILE) * ((height + TILE - 1) // TILE)
 
 
-def zeros_like_params(g: dict) -> dict:
-    return {k: torch.zeros_like(v) for k, v in g.items()}
+_GEO = ("means", "log_scales", "quats", "opacity_logits")
+
+
+def geo_stride_of(g: dict) -> int:
+    """0 when the geometric fields are four packed arrays, else their row
+    stride (views into one array of rows, ``binding.geo_rows``)."""
+    return 0 if all(g[k].is_contiguous() for k in _GEO) else int(g["means"].stride(0))
+
+
+def zeros_like_params(g: dict, n: int | None = None) -> dict:
+    """Zero arrays shaped like the parameter set g (n rows, default g's), in
+    the same layout of the geometric fields."""
+    n = int(g["means"].shape[0]) if n is None else n
+    dev, s = g["means"].device, geo_stride_of(g)
+    if s:
+        out = B.geo_rows(n, dev, s)
+    else:
+        out = {k: torch.zeros((n,) + tuple(g[k].shape[1:]), dtype=g[k].dtype, device=dev) for k in _GEO}
+    out["sh"] = torch.zeros((n,) + tuple(g["sh"].shape[1:]), dtype=g["sh"].dtype, device=dev)
+    return out
+
+
+def as_geo_rows(g: dict, stride: int = 16) -> dict:
+    """A copy of the parameter set g with its geometric fields in one array of
+    rows of `stride` floats (64-byte rows at 16: an update of scattered
+    Gaussians then moves whole rows instead of four partial sectors)."""
+    n = int(g["means"].shape[0])
+    out = B.geo_rows(n, g["means"].device, stride)
+    for k in _GEO:
+        out[k].copy_(g[k])
+    out["sh"] = g["sh"].clone().contiguous()
+    return out
+
+
+def head_of(g: dict, m: int) -> dict:
+    """The first m rows of g as a new parameter set of the same layout."""
+    out = zeros_like_params(g, m)
+    for k in out:
+        out[k].copy_(g[k][:m])
+    return out
 
 
 class Trainer:
@@ -243,24 +281,103 @@ class Trainer:
         B.advance_counters(self.it_dev, self.step_dev)
 
     # ------------------------------------------------------------------ graph
-    def capture(self):
-        """Capture one step in a CUDA graph (after a warm-up step)."""
+    SELECTION = ("ws_sel", "active_tiles", "n_active", "tile_rank", "pix_off", "pix_idx")
+
+    def _selection(self) -> dict:
+        return {k: getattr(self, k) for k in self.SELECTION}
+
+    def _use_selection(self, sel: dict):
+        for k, v in sel.items():
+            setattr(self, k, v)
+
+    def step_overlapped(self, nxt: dict):
+        """One iteration on the selection already made for it, and the next
+        iteration's selection (Alg. 1 step 3) into the buffers nxt.  The next
+        selection needs only the error and age maps the loss has just written
+        and the iteration counter, so it runs on a second stream beside the
+        backward and the update, which touch neither."""
+        B.project_gaussians(self.params, self.ccam, self.tile_rank, self.proj, self.sh_degree)
+        B.bin_tiles(self.proj, self.n, self.ccam, self.tile_rank, self.n_select, self.ws_bin, self.capacity,
+                    self.vals, None, self.ranges, self.n_isect)
+        B.render_sampled(self.proj, self.ranges, self.vals, self.active_tiles, self.n_active, self.n_select,
+                         self.pix_off, self.pix_idx, self.n_pix, self.ccam, self.bg, self.rgb, self.T_final,
+                         self.n_last, ckpt=self.ckpt)
+        self.loss_and_maps()
+        B.advance_counters(self.it_dev, None)        # the next iteration's number
+        main = torch.cuda.current_stream()
+        self._side.wait_stream(main)
+        cur = self._selection()
+        with torch.cuda.stream(self._side):
+            self._use_selection(nxt)
+            self._select()
+        self._use_selection(cur)
+        if self.fused:
+            self.render_backward()
+            self.backward_update()
+        else:
+            self.backward()
+            self.update()
+        B.advance_counters(None, self.step_dev)
+        main.wait_stream(self._side)
+
+    def capture(self, overlap: bool = False):
+        """Capture one step in a CUDA graph (after a warm-up step).  With
+        overlap, two graphs that alternate between two sets of selection
+        buffers: each runs its iteration on one set and makes the next
+        iteration's selection in the other, beside its backward and update
+        (``step_overlapped``); ``replay`` alternates them.  The results are
+        those of the plain step: the same selections, from the same maps and
+        counters."""
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
             self.step()
         torch.cuda.current_stream().wait_stream(s)
         torch.cuda.synchronize()
-        self.graph = torch.cuda.CUDAGraph(keep_graph=True)
-        with torch.cuda.graph(self.graph):
-            self.step()
-        self.kernels_per_step = B.graph_count_kernels(self.graph)
-        self.graph.instantiate()
+        self.overlap = overlap
+        if not overlap:
+            self.graph = torch.cuda.CUDAGraph(keep_graph=True)
+            with torch.cuda.graph(self.graph):
+                self.step()
+            self.kernels_per_step = B.graph_count_kernels(self.graph)
+            self.graph.instantiate()
+            torch.cuda.synchronize()
+            return self.graph
+        self._side = torch.cuda.Stream()
+        sets = [self._selection(), {k: torch.empty_like(v) for k, v in self._selection().items()}]
+        self._select()                                  # the first replayed iteration's selection, in set 0
+        torch.cuda.synchronize()
+        self.graphs = []
+        for k in range(2):
+            self._use_selection(sets[k])
+            g = torch.cuda.CUDAGraph(keep_graph=True)
+            with torch.cuda.graph(g):
+                self.step_overlapped(sets[1 - k])
+            self.graphs.append(g)
+        self.kernels_per_step = B.graph_count_kernels(self.graphs[0])
+        for g in self.graphs:
+            g.instantiate()
+        self._sets, self._phase = sets, 0
+        self._use_selection(sets[0])
+        self.graph = self.graphs[0]
         torch.cuda.synchronize()
         return self.graph
 
     def replay(self):
-        self.graph.replay()
+        """One captured iteration.  With overlap, the selection attributes
+        then name the buffers that iteration used (its rgb, n_last, ... go with
+        them), and the next selection is already in the other set."""
+        if not getattr(self, "overlap", False):
+            self.graph.replay()
+            return
+        k = self._phase
+        self._use_selection(self._sets[k])
+        self.graphs[k].replay()
+        self._phase = 1 - k
+
+    def next_selection(self) -> dict:
+        """With overlap: the selection buffers of the next replayed iteration."""
+        return self._sets[self._phase]
 
     STAGES = ("select_tiles", "project_gaussians", "bin_tiles", "render_sampled", "loss_sparse_ncc",
               "render_backward", "project_backward", "hybrid_step")
@@ -360,15 +477,12 @@ def density_step(tr: Trainer, t: int, extent: float, final: bool = False) -> tup
     cap = 2 * tr.n
     dev = tr.params["means"].device
 
-    def alloc():
-        return {k: torch.zeros((cap,) + tuple(v.shape[1:]), dtype=v.dtype, device=dev) for k, v in tr.params.items()}
-    po, mo, vo = alloc(), alloc(), alloc()
+    po, mo, vo = (zeros_like_params(x, cap) for x in (tr.params, tr.m, tr.v))
     n_out = torch.zeros(1, dtype=torch.int64, device=dev)
     B.density_control(tr.params, tr.m, tr.v, tr.stats, tr.accum, cfg, po, mo, vo, cap, n_out,
                       sh_degree=tr.sh_degree)
     m = int(n_out.item())   # at most 2 N by construction
-    cut = lambda d_: {k: v[:m].clone() for k, v in d_.items()}
-    return cut(po), cut(mo), cut(vo), m
+    return head_of(po, m), head_of(mo, m), head_of(vo, m), m
 
 
 def psnr(img: torch.Tensor, ref: torch.Tensor) -> float:

@@ -81,7 +81,7 @@ class TileErrorMLP:
         h1 = torch.empty(R, HID, dtype=torch.int16, device=x.device)
         h2 = torch.empty(R, HID, dtype=torch.int16, device=x.device)
         B.mlp_forward_tc(self.net(), x, y, h1, h2)
-        B.mlp_backward(self.net(), x, h1, h2, y, target.contiguous(), self.grads, self.loss, rows_dev=rows_dev)
+        B.mlp_backward_tc(self.net(), x, h1, h2, y, target.contiguous(), self.grads, self.loss, rows_dev=rows_dev)
         self.step_count += 1
         B.mlp_adam(self.params, self.grads, self.m, self.v, self.step_count, self.lr, 0.9, 0.999, 1e-8, self.net())
         return self.loss

@@ -21,7 +21,7 @@ import numpy as np
 import torch
 
 from . import scenes
-from .pipeline import Trainer
+from .pipeline import Trainer, as_geo_rows
 
 
 def jittered_init(gt: dict, extent: float, seed: int = scenes.SEED_NOISE, mean_sigma: float = 0.004,
@@ -127,7 +127,7 @@ def compare(device, n: int = 500_000, width: int = 1280, height: int = 720, dist
     out = {"workload": f"{n} Gaussians, {width}x{height}, perturbed ground truth"}
     runs = {}
     for name, (frac, rate) in [("dense", (1.0, 1.0))] + [(f"sampled_{f:g}_{r:.3g}", (f, r)) for f, r in settings]:
-        params = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in init.items()}
+        params = as_geo_rows({k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in init.items()})
         dense = name == "dense"
         tr = Trainer(params, cam, target, tile_fraction=frac, pixel_rate=rate, dense=dense)
         ev = Evaluator(params, cam, target)
@@ -205,7 +205,7 @@ class ViewCycle:
         keep = [{k: v.clone() for k, v in d.items()} for d in (self.params, t0.m, t0.v)]
         step, it = t0.step_dev.clone(), t0.it_dev.clone()
         for tr in self.trs:
-            tr.capture()
+            tr.capture(overlap=True)
         for d, saved in zip((self.params, t0.m, t0.v), keep):
             for k in d:
                 d[k].copy_(saved[k])
@@ -329,7 +329,7 @@ def compare_views(device, n: int = 500_000, width: int = 1280, height: int = 720
     if scheduled:
         arms.append((f"scheduled_{scheduled_fraction:g}", "scheduled"))
     for name, setting in arms:
-        params = {k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in init.items()}
+        params = as_geo_rows({k: torch.from_numpy(np.ascontiguousarray(v)).to(device) for k, v in init.items()})
         ev = HeldOutEvaluator(params, [cams[k] for k in held], [targets[k] for k in held], [masks[k] for k in held])
         t_init = 0.0
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

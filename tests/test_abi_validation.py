@@ -163,3 +163,22 @@ def test_density_control_checks(B):
     assert f(C.byref(g), C.byref(pp), C.byref(pp), None, None, C.byref(cfg), C.byref(pp), C.byref(pp),
              C.byref(pp), -1, C.byref(n_out), None, ws, 256, None) == INVALID          # negative capacity
     assert B._lib.tgs_accumulate_screen_grad(None, 10, None, None) == INVALID
+
+
+def test_geo_stride_checks(B):
+    """A geo_stride that is not 0 or a multiple of 4 of at least 12 is refused
+    before any device work, in tgs_gaussians and in tgs_param_ptrs."""
+    cam = B.camera(dict(viewmat=[1, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 4, 0, 0, 0, 1], fx=100, fy=100, cx=32, cy=32,
+                        width=64, height=64))
+    proj = B.Projected(P16, P16, P16, P16, P16)
+    for bad in (3, 8, 13, -16):
+        g = B.Gaussians(P16, P16, P16, P16, P16, 10, 3, bad)
+        assert B._lib.tgs_project_gaussians(C.byref(g), C.byref(cam), None, C.byref(proj), None) == INVALID
+        pp = B.ParamPtrs(P16, P16, P16, P16, P16, bad)
+        ok = B.ParamPtrs(P16, P16, P16, P16, P16, 16)
+        opt = B.Opt((C.c_float * 6)(*[1e-3] * 6), 0.9, 0.999, 1e-15, 1e-8, 1)
+        ws = (C.c_uint8 * 1024)()       # enough for 10 Gaussians: only the stride is wrong
+        assert B._lib.tgs_hybrid_step_workspace_size(10) <= 1024
+        for args in ((pp, ok, ok, ok), (ok, pp, ok, ok), (ok, ok, pp, ok), (ok, ok, ok, pp)):
+            assert B._lib.tgs_hybrid_step(*[C.byref(a) for a in args], 10, None, None, 0, 1, None, C.byref(opt),
+                                          ws, 1024, None) == INVALID

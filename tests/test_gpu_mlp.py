@@ -61,8 +61,11 @@ def test_forward_parity(P, orc, R, tc):
         assert np.all(np.abs(hv[diff] - hw[diff]) <= 1.01 * ulp)
 
 
-@pytest.mark.parametrize("R", [33, 2048, 5000])
-def test_backward_parity(P, orc, R):
+@pytest.mark.parametrize("tc", [False, True])
+@pytest.mark.parametrize("R", [33, 130, 2048, 5000])
+def test_backward_parity(P, orc, R, tc):
+    """tc: the weight gradients as tcgen05 contractions over 128-row tiles
+    (the last one ragged); otherwise on the CUDA cores."""
     B, TileErrorMLP = P
     mlp = TileErrorMLP(seed=7)
     x = _features(R, 11)
@@ -72,13 +75,18 @@ def test_backward_parity(P, orc, R):
     h1 = torch.empty(R, 128, dtype=torch.int16, device="cuda")
     h2 = torch.empty(R, 128, dtype=torch.int16, device="cuda")
     B.mlp_forward(mlp.net(), xd, y, h1, h2)
-    B.mlp_backward(mlp.net(), xd, h1, h2, y, td, mlp.grads, mlp.loss)
+    if tc:
+        status = torch.zeros(1, dtype=torch.int32, device="cuda")
+        B.mlp_backward_tc(mlp.net(), xd, h1, h2, y, td, mlp.grads, mlp.loss, status=status)
+        assert int(status.item()) == 0
+    else:
+        B.mlp_backward(mlp.net(), xd, h1, h2, y, td, mlp.grads, mlp.loss)
     loss, gw = orc.mlp_backward(x, t, mlp.weights_fp(), bf16=True)
     # measured on GB300: loss within 2.5e-6, gradients within 4.1e-5 (2048 rows); bounds with a factor of 5
     assert float(mlp.loss.item()) == pytest.approx(loss, rel=2e-5)
     g = mlp.grads.double().cpu().numpy()
     sl = mlp._slices()
-    print(f"mlp backward R={R}: loss rel {abs(float(mlp.loss.item()) - loss) / abs(loss):.3e}, " +
+    print(f"mlp backward R={R} tc={tc}: loss rel {abs(float(mlp.loss.item()) - loss) / abs(loss):.3e}, " +
           ", ".join(f"{k} {rel_l2(g[sl[k]], gw[k].reshape(-1)):.3e}" for k in ("W1", "b1", "W2", "b2", "W3", "b3")))
     for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
         assert rel_l2(g[sl[name]], gw[name].reshape(-1)) <= 2e-4, (name, rel_l2(g[sl[name]], gw[name].reshape(-1)))
