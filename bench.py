@@ -907,7 +907,7 @@ def mlp_bench(device, peaks, steps: int = 10, rows: int = MLP_ROWS) -> dict:
             "backward_ms": b_ms, "backward_tc_ms": btc_ms, "train_step_tc_ms": ttc_ms,
             "train_tc_roofline": {"achieved": 3 * flop / (ttc_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                                   "frac": 3 * flop / (ttc_ms * 1e-3) / 1e12 / peak,
-                                  "note": "tcgen05 forward with stored activations, mma.sync activation "
+                                  "note": "tcgen05 forward with stored activations, tcgen05 activation "
                                           "adjoint, tcgen05 weight gradients, Adam"}}
 
 

@@ -748,8 +748,10 @@ tgs_status tgs_mlp_backward(const tgs_mlp* w, int64_t rows, const int32_t* rows_
                             const uint16_t* h2, const float* y, const float* target, float* grads, double* loss,
                             void* workspace, size_t workspace_bytes, tgs_stream stream);
 
-/* The same gradient with the weight gradients on the tcgen05 tensor cores:
- * dW2 += dH2^T H1 and dW1 += dH1^T bf16(X) as contractions over 128-row tiles
+/* The same gradient on the tcgen05 tensor cores: the activation adjoint
+ * dH1 = [H1 > 0] (dH2 W2) as one 128-row tile contraction per tile (operands
+ * in shared memory, the accumulator in tensor memory), and the weight
+ * gradients dW2 += dH2^T H1 and dW1 += dH1^T bf16(X) as contractions over 128-row tiles
  * (M = 128 hidden units, K = 128 rows), with the bias gradients as an extra
  * column of ones in the same contraction, accumulated in tensor memory per
  * CTA and added to grads once per CTA; dW3 and db3 on the CUDA cores.  The

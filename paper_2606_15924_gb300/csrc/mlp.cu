@@ -387,6 +387,9 @@ static int mlp_grid(int64_t R) {
 tgs_status launch_mlp_wgrad_tc(const float* x, const uint16_t* h1, const uint16_t* h2, const float* dy,
                                const uint16_t* dh2, const uint16_t* dh1, int64_t R, float* grads, int32_t* status,
                                cudaStream_t s);
+tgs_status launch_mlp_act_tc(const tgs_mlp* w, const uint16_t* h1, const uint16_t* h2, const float* y,
+                             const float* target, int64_t R, const int32_t* R_dev, float* dy, uint16_t* dh2,
+                             uint16_t* dh1, double* loss, int32_t* status, cudaStream_t s);
 
 }  // namespace tgs
 
@@ -433,6 +436,11 @@ static tgs_status mlp_backward_impl(const tgs_mlp* w, int64_t rows, const int32_
   float* dy = c.take<float>((size_t)rows);
   uint16_t* dh2 = c.take<uint16_t>((size_t)rows * MH);
   uint16_t* dh1 = c.take<uint16_t>((size_t)rows * MH);
+  if (tc) {
+    const tgs_status st = launch_mlp_act_tc(w, h1, h2, y, target, rows, rows_dev, dy, dh2, dh1, loss, status, s);
+    if (st != TGS_OK) return st;
+    return launch_mlp_wgrad_tc(x, h1, h2, dy, dh2, dh1, rows, grads, status, s);
+  }
   const size_t smem = sizeof(MlpSmem) + MH * S2 * sizeof(uint16_t);
   static bool attr[64] = {};
   int dev = 0;
@@ -444,11 +452,7 @@ static tgs_status mlp_backward_impl(const tgs_mlp* w, int64_t rows, const int32_
   k_mlp_backward_act<<<mlp_grid(rows), 128, smem, s>>>(mlp_k(w), h1, h2, y, target, rows, rows_dev, dy, dh2, dh1,
                                                         loss);
   // chunks: whole kWgRows groups, at most 4 blocks per SM's worth
-  if (tc) {
-    const tgs_status st = check_launch();
-    if (st != TGS_OK) return st;
-    return launch_mlp_wgrad_tc(x, h1, h2, dy, dh2, dh1, rows, grads, status, s);
-  }
+
   const int64_t groups = (rows + kWgRows - 1) / kWgRows;
   const int64_t waves = (int64_t)device_sm_count() * 4;
   const int64_t per = std::max<int64_t>(1, (groups + waves - 1) / waves);

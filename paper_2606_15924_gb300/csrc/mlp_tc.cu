@@ -492,7 +492,161 @@ __global__ void __launch_bounds__(kWgTcThreads, 1) k_mlp_wgrad_tc(const float* _
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWgTmemCols));
 }
 
+// ---------------------------------------------------------------------------
+// Activation adjoint on the tensor cores, per 128-row tile (one thread per
+// row, the forward's layer-2 structure run backwards):
+//   dy = (y - t) / R, dh2 = bf16([h2 > 0] dy W3) into the K-major A tile,
+//   D = dH2 W2 (M 128 rows, N 128 units j, K 128 units k; B [j][k] = W2 [k][j],
+//   staged once per CTA) into TMEM, dh1 = bf16([h1 > 0] D);
+// dy, dh2 and dh1 rows go to memory for the weight gradients, and the loss
+// is summed.  The same roundings as the mma.sync kernel (dh2 and dh1 to bf16,
+// fp32 sums of bf16 products).
+constexpr uint32_t OFF_W2T = 0;                     // W2^T [128 j][128 k]
+constexpr uint32_t OFF_DA = OFF_W2T + TH * TH * 2;  // dH2 [128 r][128 k]
+constexpr uint32_t OFF_W3A = OFF_DA + TM * TH * 2;  // w3 (fp32) [128]
+constexpr uint32_t ACT_SMEM = OFF_W3A + TH * 4;
+constexpr uint32_t kActTmemCols = 128;
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_backward_act_tc(
+    TcArgs w, const uint16_t* __restrict__ h1, const uint16_t* __restrict__ h2, const float* __restrict__ y,
+    const float* __restrict__ tgt, int64_t R, const int32_t* __restrict__ R_dev, float* __restrict__ dy_out,
+    uint16_t* __restrict__ dh2_out, uint16_t* __restrict__ dh1_out, double* __restrict__ loss,
+    int32_t* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_mbar;
+  const int t = threadIdx.x, warp = t >> 5;
+  float* w3f = reinterpret_cast<float*>(sm + OFF_W3A);
+  // B [n = j][k] = W2 [k][j]: eight k of one j (a strided gather of w2) per 16-byte chunk
+  for (int i = t; i < TH * (TH / 8); i += kTcThreads) {
+    const int n = i % TH, k8 = (i / TH) * 8;
+    uint32_t q[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      q[e] = (uint32_t)w.w2[(k8 + 2 * e) * TH + n] | ((uint32_t)w.w2[(k8 + 2 * e + 1) * TH + n] << 16);
+    *reinterpret_cast<uint4*>(sm + OFF_W2T + core_off(n, k8, SBO_K128)) = make_uint4(q[0], q[1], q[2], q[3]);
+  }
+  for (int i = t; i < TH; i += kTcThreads) w3f[i] = __uint_as_float((uint32_t)w.w3[i] << 16);
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(kActTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t mbar = smem_u32(&s_mbar);
+  const uint32_t base = smem_u32(sm);
+  const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
+  // rows past Re are padding: no error, no gradient
+  const int64_t Re = R_dev ? (*R_dev > 0 ? (*R_dev < R ? (int64_t)*R_dev : R) : 0) : R;
+  const float inv = Re > 0 ? 1.f / (float)Re : 0.f;
+  double lsum = 0.0;
+  uint32_t phase = 0;
+  bool failed = false, pending = false;
+  const int64_t tiles = (R + TM - 1) / TM;
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t row = tile * TM + t;
+    const bool valid = row < R;
+    const float e = row < Re ? y[row] - tgt[row] : 0.f;
+    lsum += 0.5 * (double)e * (double)e * (double)inv;
+    const float d = e * inv;
+    if (valid) dy_out[row] = d;
+    // dh2 row -> A tile (and memory)
+#pragma unroll 1
+    for (int c8 = 0; c8 < TH; c8 += 8) {
+      const uint4 hv = valid ? *reinterpret_cast<const uint4*>(h2 + row * TH + c8) : make_uint4(0u, 0u, 0u, 0u);
+      const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+      uint32_t pk[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float a0 = __uint_as_float(hw[q] << 16) > 0.f ? d * w3f[c8 + 2 * q] : 0.f;
+        const float a1 = __uint_as_float(hw[q] & 0xffff0000u) > 0.f ? d * w3f[c8 + 2 * q + 1] : 0.f;
+        pk[q] = pack2(a0, a1);
+      }
+      const uint4 u = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      *reinterpret_cast<uint4*>(sm + OFF_DA + core_off(t, c8, SBO_K128)) = u;
+      if (valid) *reinterpret_cast<uint4*>(dh2_out + row * TH + c8) = u;
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t == 0) {
+#pragma unroll
+      for (int kk = 0; kk < TH / 16; ++kk)
+        mma_bf16(tmem, sdesc(base + OFF_DA + kk * 256, 128, SBO_K128), sdesc(base + OFF_W2T + kk * 256, 128, SBO_K128),
+                 kk > 0 ? 1u : 0u);
+      commit(mbar);
+    }
+    if (__syncthreads_or(!wait_parity(mbar, phase))) {
+      failed = pending = true;
+      break;
+    }
+    phase ^= 1u;
+    fence_after();
+    // dh1 = bf16([h1 > 0] D)
+#pragma unroll 1
+    for (int c0 = 0; c0 < TH; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + lane_addr + (uint32_t)c0, v);
+#pragma unroll
+      for (int q8 = 0; q8 < 4; ++q8) {
+        const int c8 = c0 + 8 * q8;
+        const uint4 hv = valid ? *reinterpret_cast<const uint4*>(h1 + row * TH + c8) : make_uint4(0u, 0u, 0u, 0u);
+        const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
+        uint32_t pk[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          pk[q] = pack2(__uint_as_float(hw[q] << 16) > 0.f ? v[8 * q8 + 2 * q] : 0.f,
+                        __uint_as_float(hw[q] & 0xffff0000u) > 0.f ? v[8 * q8 + 2 * q + 1] : 0.f);
+        if (valid) *reinterpret_cast<uint4*>(dh1_out + row * TH + c8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      }
+    }
+    // every thread is done reading TMEM and the A tile before the next MMA
+    fence_before();
+    __syncthreads();
+    fence_after();
+  }
+  if (failed) {
+    if (t == 0 && status) atomicExch(status, 1);
+    if (pending) wait_parity(mbar, phase);
+  }
+  lsum = warp_sum_d(lsum);
+  if ((t & 31) == 0 && lsum != 0.0) atomicAdd(loss, lsum);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kActTmemCols));
+}
+
 }  // namespace
+
+// Launches k_mlp_backward_act_tc over the rows (two CTAs per SM at most:
+// 2 x 128 TMEM columns).
+tgs_status launch_mlp_act_tc(const tgs_mlp* w, const uint16_t* h1, const uint16_t* h2, const float* y,
+                             const float* target, int64_t R, const int32_t* R_dev, float* dy, uint16_t* dh2,
+                             uint16_t* dh1, double* loss, int32_t* status, cudaStream_t s) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return check_launch();
+  static bool attr[64] = {};
+  if (dev < 0 || dev >= 64) return TGS_ERR_DEVICE;
+  if (!attr[dev]) {
+    cudaFuncSetAttribute(k_mlp_backward_act_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ACT_SMEM);
+    attr[dev] = true;
+  }
+  const int64_t tiles = (R + TM - 1) / TM;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 2ll * device_sm_count()));
+  k_mlp_backward_act_tc<<<grid, kTcThreads, ACT_SMEM, s>>>(TcArgs{w->w1, w->w2, w->w3, w->b1, w->b2, w->b3}, h1, h2,
+                                                           y, target, R, R_dev, dy, dh2, dh1, loss, status);
+  return check_launch();
+}
 
 // Launches k_mlp_wgrad_tc over the rows (one CTA per SM at most: its shared
 // memory allows one per SM, and each CTA accumulates all its tiles in TMEM).
