@@ -350,9 +350,13 @@ size_t tgs_checkpoint_bytes(int32_t n_active_max, int32_t n_pix_max, int32_t n_s
  * batches and stops when its own pixels have saturated; the same bits as
  * the sequential walk), several tiles per block when tiles have few sampled
  * pixels.  groups = 0 (the default) leaves the choice to the library (the
- * warp-independent walk for sparse launches of tiles with at most 32 sampled
- * pixels, else the block's walk); 1 is the block's sequential walk; 2 or 4
- * the split walk.
+ * walk with two threads per pixel for sparse launches of tiles with at most
+ * 32 sampled pixels, else the block's walk); 1 is the block's sequential walk; 2 or 4
+ * the split walk; 5 the walk with two threads per pixel (each walks one half
+ * of every 32-position run at once, the second from a local transmittance of
+ * 1; the halves compose as above, and the second half walks again from the
+ * composed state where the stop may lie in it, so that the stops and n_last
+ * are the sequential walk's).
  * Process-wide; returns TGS_ERR_INVALID_ARG for other values.
  */
 tgs_status tgs_set_forward_split(int32_t groups);

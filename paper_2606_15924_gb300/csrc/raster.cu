@@ -306,6 +306,181 @@ __global__ void k_render_fwd(RasterArgs a, float* __restrict__ out_rgb, float* _
   render_tile_fwd<SELECT>(a, j, sm, out_rgb, out_T, out_last, ck);
 }
 
+// The same forward with two threads per sampled pixel: a warp holds 16
+// pixels twice, and of every 32-position run the first half (lanes 0-15)
+// walks positions 0-15 from the pixel's state, exactly as the walk above,
+// while the second half (lanes 16-31) walks positions 16-31 at the same time
+// from a local (T, C) = (1, 0), without stopping.  The halves then compose,
+// (T, C) -> (T T_b, C + T C_b); where the product comes within 1e-5 of the
+// stopping transmittance the second half walks its positions again from the
+// composed entry state, with the stop, so every stop and n_last is the
+// sequential walk's.  The walk of a run is half as long and the block has
+// twice the warps; T and C differ from the sequential walk's by the rounding
+// of the composition only.
+constexpr float kTStopPairMargin = kTStop * (1.f + 1e-5f);
+
+template <bool SELECT>
+__device__ __forceinline__ void pair_walk(const Splat* sm, int q0, unsigned mask, float px, float py, int base_pos,
+                                          bool can_stop, float& T, float& C0, float& C1, float& C2, int& last,
+                                          bool& done) {
+  while (mask && !done) {
+    int qq[kUnroll];
+    float al[kUnroll];
+    bool ok[kUnroll];
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const bool val = mask != 0u;
+      qq[u] = val ? q0 + __ffs(mask) - 1 : q0;
+      mask &= mask - 1u;
+      const float2 xy = sm[qq[u]].xy;
+      float G;
+      ok[u] = (SELECT ? splat_alpha_nb(sm[qq[u]].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G)
+                      : splat_alpha(sm[qq[u]].co, __fsub_rn(px, xy.x), __fsub_rn(py, xy.y), al[u], G)) &&
+              val;
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const float Tn = __fmul_rn(T, __fsub_rn(1.f, al[u]));
+      const bool stop = ok[u] && !done && can_stop && Tn < kTStop;
+      const bool take = ok[u] && !done && !stop;
+      done = done || stop;
+      const float4 rgb = sm[qq[u]].rgb;
+      const float w = al[u] * T;
+      C0 = take ? C0 + w * rgb.x : C0;
+      C1 = take ? C1 + w * rgb.y : C1;
+      C2 = take ? C2 + w * rgb.z : C2;
+      T = take ? Tn : T;
+      last = take ? base_pos + qq[u] + 1 : last;
+    }
+  }
+}
+
+template <bool SELECT>
+__device__ __forceinline__ void render_tile_fwd_pair(const RasterArgs& a, int j, Splat* sm,
+                                                     float* __restrict__ out_rgb, float* __restrict__ out_T,
+                                                     int32_t* __restrict__ out_last, const Ckpt& ck) {
+  const unsigned full = 0xffffffffu;
+  const int t = a.active_tiles ? a.active_tiles[j] : j;
+  const int p0 = a.pix_off[j], p1 = a.pix_off[j + 1];
+  const int lane = threadIdx.x & 31, h = lane >> 4;
+  const int s = p0 + 16 * (int)(threadIdx.x >> 5) + (lane & 15);
+  const bool has_pix = s < p1;
+  float px = 0.f, py = 0.f;
+  if (has_pix) {
+    const int l = a.pix_idx[s];
+    px = (float)((t % a.tiles_x) * TGS_TILE + (l & 15)) + 0.5f;
+    py = (float)((t / a.tiles_x) * TGS_TILE + (l >> 4)) + 0.5f;
+  }
+  const int2 range = a.ranges[j];
+  float T = 1.f, C0 = 0.f, C1 = 0.f, C2 = 0.f;
+  int last = 0;
+  bool done = !has_pix;
+  const int B = blockDim.x;
+  const float2 band = warp_rows(has_pix, py);
+  SplatRaw nxt;
+  int idn = 0;
+  const int tid = threadIdx.x;
+  if (range.x + tid < range.y) fetch_splat(a, a.vals[range.x + tid], nxt);
+  if (range.x + B + tid < range.y) idn = a.vals[range.x + B + tid];
+  for (int base = range.x; base < range.y; base += B) {
+    if (__syncthreads_count(done) == B) break;
+    if (base + tid < range.y) finish_splat(nxt, sm[tid]);
+    __syncthreads();
+    if (base + B + tid < range.y) fetch_splat(a, idn, nxt);
+    if (base + 2 * B + tid < range.y) idn = a.vals[base + 2 * B + tid];
+    const int cnt = min(B, range.y - base);
+    const int base_pos = base - range.x;
+    for (int q32 = 0; q32 < cnt; q32 += kCkptEvery) {
+      if (ck.data && !done && h == 0) {
+        const int c = (base_pos + q32) / kCkptEvery - 1;  // state in front of this run
+        if (c >= 0 && c < ck.n_slots) ck.data[c * ck.stride + s] = make_float4(T, C0, C1, C2);
+      }
+      const int qe = min(cnt, q32 + kCkptEvery);
+      bool in_l = false;
+      if (q32 + lane < qe) {
+        const float2 yr = sm[q32 + lane].yr;
+        in_l = yr.y >= band.x && yr.x <= band.y;
+      }
+      const unsigned m32 = __ballot_sync(full, in_l);
+      const unsigned hm = h ? (m32 >> 16) : (m32 & 0xFFFFu);
+      const int q0 = q32 + 16 * h;
+      // half 0: the pixel's state, with the stop; half 1: a local state from (1, 0)
+      float Tw = h ? 1.f : T, W0 = h ? 0.f : C0, W1 = h ? 0.f : C1, W2 = h ? 0.f : C2;
+      int lw = h ? 0 : last;
+      bool dw = done;
+      pair_walk<SELECT>(sm, q0, hm, px, py, base_pos, h == 0, Tw, W0, W1, W2, lw, dw);
+      __syncwarp();
+      const float oT = __shfl_xor_sync(full, Tw, 16), o0 = __shfl_xor_sync(full, W0, 16),
+                  o1 = __shfl_xor_sync(full, W1, 16), o2 = __shfl_xor_sync(full, W2, 16);
+      const int ol = __shfl_xor_sync(full, lw, 16);
+      const bool od = __shfl_xor_sync(full, (int)dw, 16) != 0;
+      // A: the first half's state (exact), Bh: the second half's local walk
+      const float aT = h ? oT : Tw, a0 = h ? o0 : W0, a1 = h ? o1 : W1, a2 = h ? o2 : W2;
+      const int al_ = h ? ol : lw;
+      const bool ad = h ? od : dw;
+      const float bT = h ? Tw : oT, b0 = h ? W0 : o0, b1 = h ? W1 : o1, b2 = h ? W2 : o2;
+      const int bl = h ? lw : ol;
+      // stopped in the first half, or nothing blended in the second: the first half's state
+      const bool first = ad || bl == 0;
+      const float Tc = __fmul_rn(aT, bT);
+      // the stop may lie in the second half: it walks its positions again from the exact entry state
+      const bool again = !first && Tc < kTStopPairMargin;
+      if (__any_sync(full, again)) {  // warp-uniform, so that every lane takes part in the shuffles
+        float rT = aT, r0 = a0, r1 = a1, r2 = a2;
+        int rl = al_;
+        bool rd = false;
+        if (h && again) pair_walk<false>(sm, q0, hm, px, py, base_pos, true, rT, r0, r1, r2, rl, rd);
+        __syncwarp();
+        const int src = (lane & 15) + 16;
+        rT = __shfl_sync(full, rT, src);
+        r0 = __shfl_sync(full, r0, src);
+        r1 = __shfl_sync(full, r1, src);
+        r2 = __shfl_sync(full, r2, src);
+        rl = __shfl_sync(full, rl, src);
+        rd = __shfl_sync(full, (int)rd, src) != 0;
+        if (again) {
+          T = rT; C0 = r0; C1 = r1; C2 = r2; last = rl; done = rd;
+          continue;
+        }
+      }
+      if (first) {
+        T = aT; C0 = a0; C1 = a1; C2 = a2; last = al_; done = ad;
+      } else {
+        T = Tc;
+        C0 = a0 + aT * b0;
+        C1 = a1 + aT * b1;
+        C2 = a2 + aT * b2;
+        last = bl;
+      }
+    }
+  }
+  if (has_pix && h == 0) {
+    out_rgb[3 * s] = C0 + T * a.bg[0];
+    out_rgb[3 * s + 1] = C1 + T * a.bg[1];
+    out_rgb[3 * s + 2] = C2 + T * a.bg[2];
+    out_T[s] = T;
+    out_last[s] = last;
+  }
+  if (ck.tile_last) {
+    __shared__ int s_tl;
+    __syncthreads();
+    if (threadIdx.x == 0) s_tl = 0;
+    __syncthreads();
+    if (last > 0 && h == 0) atomicMax(&s_tl, last);
+    __syncthreads();
+    if (threadIdx.x == 0) ck.tile_last[j] = s_tl;
+  }
+}
+
+template <bool SELECT>
+__global__ void k_render_fwd_pair(RasterArgs a, float* __restrict__ out_rgb, float* __restrict__ out_T,
+                                  int32_t* __restrict__ out_last, Ckpt ck) {
+  extern __shared__ Splat sm[];
+  const int j = blockIdx.x;
+  if (j >= *a.n_active) return;
+  render_tile_fwd_pair<SELECT>(a, j, sm, out_rgb, out_T, out_last, ck);
+}
+
 // The same forward with every warp on its own: a warp takes 32 sampled
 // pixels of one tile (piece `piece` of tile j; j < 0 for none), stages its
 // own 32-splat batches of the tile's list (one per lane, the next batch
@@ -1212,13 +1387,16 @@ constexpr bool kSplitAuto = false;
 // at 1, 2 or 4 by tgs_set_forward_split (tuning and tests).
 static int g_fwd_split = 0;
 
-// The automatic choice of the warp-independent walk: for tiles of at most 32
-// sampled pixels (one warp each, so no splat is staged twice; eight tiles
-// per block) in a sparse launch.  Measured at 500k Gaussians, 1280x720:
-// 720 tiles of 25 pixels 0.054 ms against 0.064 for one 32-thread block per
-// tile; 3600 tiles of 25 pixels 0.103 against 0.101; 720 tiles of 85 pixels
-// (three warps staging the same splats) 0.065 against 0.060.
-static bool warp_walk_auto(int B, bool sparse) { return B == 32 && sparse; }
+// The automatic choice of the walk with two threads per pixel: for tiles of
+// at most 32 sampled pixels in a sparse launch, where one warp per tile
+// leaves the GPU short of warps.  Measured at 500k Gaussians, 1280x720, 720
+// tiles of 25 pixels: 0.046 ms, against 0.054 for the warp-independent walk
+// (eight tiles per block) and 0.064 for one 32-thread block per tile.  At 85
+// pixels per tile (0.068 against 0.060) and in launches of several waves
+// (3600 tiles of 85 pixels: 0.216 against 0.162) the sequential block walk
+// stays faster: the composition and the second half's walk past the stop
+// cost more than the shorter chains gain.
+static bool pair_walk_auto(int B, bool sparse) { return B == 32 && sparse; }
 
 // Groups per tile of the split forward for a launch of n_active tiles of B
 // threads: the largest of 4 and 2 whose blocks all fit on the GPU at once
@@ -1227,7 +1405,7 @@ static bool warp_walk_auto(int B, bool sparse) { return B == 32 && sparse; }
 static int split_groups(int n_active, int B) {
   const int wp = B / 32;  // 1..8
   const bool nw_ok[2] = {4 * B <= 1024, 2 * B <= 1024};
-  if (g_fwd_split == 1 || g_fwd_split == 3) return 1;
+  if (g_fwd_split == 1 || g_fwd_split == 3 || g_fwd_split == 5) return 1;
   if (g_fwd_split) return (g_fwd_split == 4 && !nw_ok[0]) || (g_fwd_split == 2 && !nw_ok[1]) ? 1 : g_fwd_split;
   if (!kSplitAuto) return 1;
   static int per_sm[64][9][2] = {};
@@ -1269,7 +1447,7 @@ static bool ckpt_of(const tgs_checkpoints* c, int32_t n_active_max, int32_t n_pi
 }
 
 extern "C" tgs_status tgs_set_forward_split(int32_t groups) {
-  if (groups != 0 && groups != 1 && groups != 2 && groups != 3 && groups != 4) return TGS_ERR_INVALID_ARG;
+  if (groups < 0 || groups > 5) return TGS_ERR_INVALID_ARG;
   g_fwd_split = groups;
   return TGS_OK;
 }
@@ -1307,7 +1485,17 @@ extern "C" tgs_status tgs_render_sampled(const tgs_projected* proj, const int32_
   }
   // selects when the launch gives fewer than 16 warps per SM
   const bool sparse = (int64_t)n_active_max * (B / 32) < 16 * (int64_t)device_sm_count();
-  if (g_fwd_split == 3 || (g_fwd_split == 0 && warp_walk_auto(B, sparse))) {
+  if (g_fwd_split == 5 || (g_fwd_split == 0 && pair_walk_auto(B, sparse))) {  // two threads per pixel
+    const int B2 = 32 * ((n_pix_max + 15) / 16);
+    if (sparse)
+      k_render_fwd_pair<true><<<n_active_max, B2, B2 * sizeof(Splat), (cudaStream_t)stream>>>(a, rgb, T_final, n_last,
+                                                                                              ck);
+    else
+      k_render_fwd_pair<false><<<n_active_max, B2, B2 * sizeof(Splat), (cudaStream_t)stream>>>(a, rgb, T_final,
+                                                                                               n_last, ck);
+    return check_launch();
+  }
+  if (g_fwd_split == 3) {
     const int wpt = B / 32, tpb = 8 / wpt;
     const int grid = (n_active_max + tpb - 1) / tpb;
     if (sparse)

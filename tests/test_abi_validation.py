@@ -136,11 +136,12 @@ def test_hybrid_checks(B):
 
 def test_forward_split_knob(B):
     """The forward's walk knob accepts 0 (automatic), 1 (sequential), 2 and 4
-    (split) and 3 (warp-independent) only (no device work)."""
+    (split), 3 (warp-independent) and 5 (two threads per pixel) only (no
+    device work)."""
     f = B._lib.tgs_set_forward_split
-    for bad in (-1, 5, 8):
+    for bad in (-1, 6, 8):
         assert f(bad) == INVALID
-    for ok in (1, 2, 3, 4, 0):
+    for ok in (1, 2, 3, 4, 5, 0):
         assert f(ok) == 0
 
 

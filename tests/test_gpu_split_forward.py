@@ -4,8 +4,9 @@ once, composed in list order) against the oracle's per-pixel render
 
 Each case renders with checkpoints, once per walk (1 = the sequential walk,
 2 and 4 = the split walk of that many runs at once, 3 = the sequential walk
-with every warp on its own, which must give the same bits as 1), at 1, 3, 5
-and 8 pixels per 32-lane warp.  Images and final
+with every warp on its own, which must give the same bits as 1, 5 = two
+threads per pixel, each half of every run walked at once), at 1, 3, 5 and 8
+pixels per 32-lane warp.  Images and final
 transmittances match the oracle within 1e-4 at every sampled pixel whose
 decisions are not within rounding of a threshold; n_last matches exactly
 there.  Against the sequential walk, the split walk's images agree to 1e-5,
@@ -77,7 +78,7 @@ def test_split_forward_against_oracle_and_sequential(B, orc, opaque):
         P = int(sh["pix_off"][-1])
         A = sh["n_active"]
         outs = {}
-        for groups in (1, 2, 3, 4):
+        for groups in (1, 2, 3, 4, 5):
             B.set_forward_split(groups)
             outs[groups] = _render(B, pd, binned, sel, n_pix, cam, slots)
         B.set_forward_split(0)
