@@ -390,6 +390,9 @@ tgs_status launch_mlp_wgrad_tc(const float* x, const uint16_t* h1, const uint16_
 tgs_status launch_mlp_act_tc(const tgs_mlp* w, const uint16_t* h1, const uint16_t* h2, const float* y,
                              const float* target, int64_t R, const int32_t* R_dev, float* dy, uint16_t* dh2,
                              uint16_t* dh1, double* loss, int32_t* status, cudaStream_t s);
+tgs_status launch_mlp_backward_tc(const tgs_mlp* w, const float* x, const uint16_t* h1, const uint16_t* h2,
+                                  const float* y, const float* target, int64_t R, const int32_t* R_dev,
+                                  float* grads, double* loss, int32_t* status, cudaStream_t s);
 
 }  // namespace tgs
 
@@ -436,11 +439,7 @@ static tgs_status mlp_backward_impl(const tgs_mlp* w, int64_t rows, const int32_
   float* dy = c.take<float>((size_t)rows);
   uint16_t* dh2 = c.take<uint16_t>((size_t)rows * MH);
   uint16_t* dh1 = c.take<uint16_t>((size_t)rows * MH);
-  if (tc) {
-    const tgs_status st = launch_mlp_act_tc(w, h1, h2, y, target, rows, rows_dev, dy, dh2, dh1, loss, status, s);
-    if (st != TGS_OK) return st;
-    return launch_mlp_wgrad_tc(x, h1, h2, dy, dh2, dh1, rows, grads, status, s);
-  }
+  if (tc) return launch_mlp_backward_tc(w, x, h1, h2, y, target, rows, rows_dev, grads, loss, status, s);
   const size_t smem = sizeof(MlpSmem) + MH * S2 * sizeof(uint16_t);
   static bool attr[64] = {};
   int dev = 0;

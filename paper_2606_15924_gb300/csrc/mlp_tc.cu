@@ -178,6 +178,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(TcArgs w, cons
   // drill: the timeout path on a phase that nothing completes (no MMA issued)
   if (drill && __syncthreads_or(!wait_parity(mbar, phase, kDrillLimit))) failed = true;
   const int64_t tiles = drill ? 0 : (R + TM - 1) / TM;
+  // the x row of the CTA's next tile is loaded while the current one runs
+  float4 xn[TI / 4];
+  auto load_x = [&](int64_t tl) {
+    const int64_t rw = tl * TM + t;
+#pragma unroll
+    for (int k4 = 0; k4 < TI / 4; ++k4)
+      xn[k4] = tl < tiles && rw < R ? *reinterpret_cast<const float4*>(x + rw * TI + 4 * k4)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+  };
+  load_x(blockIdx.x);
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t row = tile * TM + t;
     const bool valid = row < R;
@@ -186,7 +196,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(TcArgs w, cons
       float xv[TI];
 #pragma unroll
       for (int k = 0; k < TI; k += 4) {
-        const float4 v = valid ? *reinterpret_cast<const float4*>(x + row * TI + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 v = xn[k / 4];
         xv[k] = v.x; xv[k + 1] = v.y; xv[k + 2] = v.z; xv[k + 3] = v.w;
       }
 #pragma unroll
@@ -195,6 +205,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(TcArgs w, cons
             make_uint4(pack2(xv[k8], xv[k8 + 1]), pack2(xv[k8 + 2], xv[k8 + 3]), pack2(xv[k8 + 4], xv[k8 + 5]),
                        pack2(xv[k8 + 6], xv[k8 + 7]));
     }
+    load_x(tile + gridDim.x);
     fence_async_smem();
     fence_before();
     __syncthreads();
@@ -626,7 +637,263 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_backward_act_tc(
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kActTmemCols));
 }
 
+// ---------------------------------------------------------------------------
+// The whole backward in one pass over the rows: per 128-row tile the
+// activation adjoint (as k_mlp_backward_act_tc) and the weight gradients (as
+// k_mlp_wgrad_tc) with dH2 and dH1 kept in shared memory, so the rows are read
+// once and no adjoint goes to memory.  256 threads: thread t takes row t % 128
+// and hidden units 64 (t / 128) .. + 63.  dH2 is written twice, as the
+// row-major A tile of dH1 = dH2 W2 and (transposed, 2-byte stores whose eight
+// lanes of a phase hit distinct banks through the padded core matrices) as
+// the A tile of dW2; H1 and X likewise go transposed into the B tiles of the
+// weight gradients.  TMEM: dH1 in columns 0-127, dW2 | db2 in 128-271, dW1 |
+// db1 in 288-319.  The roundings and products are those of the two kernels.
+constexpr int kBwThreads = 256;
+constexpr uint32_t FB_W2T = 0;                            // W2^T [128 j][128 k] (B of dH1)
+constexpr uint32_t FB_DA = FB_W2T + TH * TH * 2;          // dH2 [128 r][128 k] (A of dH1)
+constexpr uint32_t FB_A2 = FB_DA + TM * TH * 2;           // dH2^T (padded)
+constexpr uint32_t FB_B2 = FB_A2 + (TH / 8) * SBO_P;      // [H1^T; 1; 0]
+constexpr uint32_t FB_A1 = FB_B2 + (N2 / 8) * SBO_P;      // dH1^T
+constexpr uint32_t FB_B1 = FB_A1 + (TH / 8) * SBO_P;      // [X^T; 1; 0]
+constexpr uint32_t FB_H2 = FB_B1 + (N1 / 8) * SBO_P;      // h2 rows (bf16), for dW3
+constexpr uint32_t FB_DY = FB_H2 + TM * TH * 2;           // dy [128]
+constexpr uint32_t FB_W3 = FB_DY + TM * 4;                // w3 (fp32) [128]
+constexpr uint32_t FB_SMEM = FB_W3 + TH * 4;
+static_assert(FB_SMEM <= 227 * 1024, "the fused backward's tiles fit one CTA's shared memory");
+constexpr uint32_t kBwTmemCols = 512;
+constexpr uint32_t kColW2 = 128, kColW1 = 288;
+
+__global__ void __launch_bounds__(kBwThreads, 1) k_mlp_backward_tc(
+    TcArgs w, const float* __restrict__ x, const uint16_t* __restrict__ h1, const uint16_t* __restrict__ h2,
+    const float* __restrict__ y, const float* __restrict__ tgt, int64_t R, const int32_t* __restrict__ R_dev,
+    float* __restrict__ grads, double* __restrict__ loss, int32_t* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_mbar;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int r = t & (TM - 1), hf = t >> 7, u0 = 64 * hf;  // row of the tile, first unit of this half
+  float* w3f = reinterpret_cast<float*>(sm + FB_W3);
+  float* s_dy = reinterpret_cast<float*>(sm + FB_DY);
+  const uint16_t* s_h2 = reinterpret_cast<const uint16_t*>(sm + FB_H2);
+  for (int i = t; i < TH * (TH / 8); i += kBwThreads) {  // B [n = j][k] = W2 [k][j]
+    const int n = i % TH, k8 = (i / TH) * 8;
+    uint32_t q[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      q[e] = (uint32_t)w.w2[(k8 + 2 * e) * TH + n] | ((uint32_t)w.w2[(k8 + 2 * e + 1) * TH + n] << 16);
+    *reinterpret_cast<uint4*>(sm + FB_W2T + core_off(n, k8, SBO_K128)) = make_uint4(q[0], q[1], q[2], q[3]);
+  }
+  for (int i = t; i < TH; i += kBwThreads) w3f[i] = __uint_as_float((uint32_t)w.w3[i] << 16);
+  for (int i = t; i < 16 * (TM / 8); i += kBwThreads) {  // the constant rows of the B tiles
+    const int n = i / (TM / 8), k8 = (i % (TM / 8)) * 8;
+    const uint32_t one2 = 0x3F803F80u;
+    const uint4 u = n == 0 ? make_uint4(one2, one2, one2, one2) : make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(sm + FB_B2 + core_off_p(TH + n, k8)) = u;
+    *reinterpret_cast<uint4*>(sm + FB_B1 + core_off_p(TI + n, k8)) = u;
+  }
+  if (t == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(kBwTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t mbar = smem_u32(&s_mbar);
+  const uint32_t base = smem_u32(sm);
+  const uint32_t lane_addr = (uint32_t)((warp & 3) * 32) << 16;  // TMEM lanes of this warp's rows
+  const int64_t Re = R_dev ? (*R_dev > 0 ? (*R_dev < R ? (int64_t)*R_dev : R) : 0) : R;
+  const float inv = Re > 0 ? 1.f / (float)Re : 0.f;
+  double lsum = 0.0;
+  float w3 = 0.f, b3 = 0.f;
+  uint32_t phase = 0;
+  bool failed = false, pending = false, any = false;
+  const int64_t tiles = (R + TM - 1) / TM;
+  auto put_t = [&](uint32_t off, int n, int k, uint32_t bits16) {  // 2-byte store into a padded K-major tile
+    *reinterpret_cast<uint16_t*>(sm + off + core_off_p(n, k)) = (uint16_t)bits16;
+  };
+  // The half rows of h2 and h1 (and the row's error) are loaded in one round,
+  // and those of the CTA's next tile are issued as soon as the current ones are
+  // staged, so they arrive while the tensor cores run (a loop that waited for
+  // each pair of loads in turn bounded the kernel).
+  uint4 G2[8], G1[8];
+  float4 XR[TI / 4];
+  float e = 0.f;
+  auto load_rows = [&](int64_t tl) {
+    const int64_t rw = tl * TM + r;
+    const bool in = tl < tiles && rw < R;
+#pragma unroll
+    for (int q8 = 0; q8 < 8; ++q8) {
+      G2[q8] = in ? *reinterpret_cast<const uint4*>(h2 + rw * TH + u0 + 8 * q8) : make_uint4(0u, 0u, 0u, 0u);
+      G1[q8] = in ? *reinterpret_cast<const uint4*>(h1 + rw * TH + u0 + 8 * q8) : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int k4 = 0; k4 < TI / 4; ++k4)
+      XR[k4] = in && hf == 0 ? *reinterpret_cast<const float4*>(x + rw * TI + 4 * k4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    e = (tl < tiles && rw < Re) ? y[rw] - tgt[rw] : 0.f;
+  };
+  load_rows(blockIdx.x);
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const float d = e * inv;
+    if (hf == 0) {
+      lsum += 0.5 * (double)e * (double)e * (double)inv;
+      s_dy[r] = d;
+    }
+    uint64_t m1 = 0;  // h1 > 0 of this half's 64 units
+#pragma unroll
+    for (int q8 = 0; q8 < 8; ++q8) {
+      const int c8 = u0 + 8 * q8;
+      const uint4 g2 = G2[q8], g1 = G1[q8];
+      const uint32_t a2[4] = {g2.x, g2.y, g2.z, g2.w}, a1[4] = {g1.x, g1.y, g1.z, g1.w};
+      uint32_t pk[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float v0 = __uint_as_float(a2[q] << 16) > 0.f ? d * w3f[c8 + 2 * q] : 0.f;
+        const float v1 = __uint_as_float(a2[q] & 0xffff0000u) > 0.f ? d * w3f[c8 + 2 * q + 1] : 0.f;
+        pk[q] = pack2(v0, v1);
+        put_t(FB_A2, c8 + 2 * q, r, pk[q] & 0xffffu);
+        put_t(FB_A2, c8 + 2 * q + 1, r, pk[q] >> 16);
+        put_t(FB_B2, c8 + 2 * q, r, a1[q] & 0xffffu);
+        put_t(FB_B2, c8 + 2 * q + 1, r, a1[q] >> 16);
+        const int bit = c8 - u0 + 2 * q;
+        if (__uint_as_float(a1[q] << 16) > 0.f) m1 |= 1ull << bit;
+        if (__uint_as_float(a1[q] & 0xffff0000u) > 0.f) m1 |= 1ull << (bit + 1);
+      }
+      *reinterpret_cast<uint4*>(sm + FB_DA + core_off(r, c8, SBO_K128)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      *reinterpret_cast<uint4*>(sm + FB_H2 + (uint32_t)(r * TH + c8) * 2u) = g2;
+    }
+    if (hf == 0) {  // X^T: the row's 16 features, rounded to bf16
+#pragma unroll
+      for (int k4 = 0; k4 < TI; k4 += 4) {
+        const float4 v = XR[k4 / 4];
+        const uint32_t p0 = pack2(v.x, v.y), p1 = pack2(v.z, v.w);
+        put_t(FB_B1, k4, r, p0 & 0xffffu);
+        put_t(FB_B1, k4 + 1, r, p0 >> 16);
+        put_t(FB_B1, k4 + 2, r, p1 & 0xffffu);
+        put_t(FB_B1, k4 + 3, r, p1 >> 16);
+      }
+    }
+    load_rows(tile + gridDim.x);  // the next tile's rows, in flight during this tile's contractions
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t == 0) {  // dH1 (before the mask) = dH2 W2
+#pragma unroll
+      for (int kk = 0; kk < TH / 16; ++kk)
+        mma_bf16(tmem, sdesc(base + FB_DA + kk * 256, 128, SBO_K128), sdesc(base + FB_W2T + kk * 256, 128, SBO_K128),
+                 kk > 0 ? 1u : 0u);
+      commit(mbar);
+    }
+    {  // dW3, db3 on the CUDA cores while the tensor cores run
+      const int u = t & (TH - 1), rb = 64 * hf;
+#pragma unroll 8
+      for (int q = rb; q < rb + 64; ++q) {
+        w3 += s_dy[q] * __uint_as_float((uint32_t)s_h2[q * TH + u] << 16);
+        if (u == 0) b3 += s_dy[q];
+      }
+    }
+    if (__syncthreads_or(!wait_parity(mbar, phase))) {
+      failed = pending = true;
+      break;
+    }
+    phase ^= 1u;
+    fence_after();
+    // dh1 = bf16([h1 > 0] D), transposed into the A tile of dW1
+#pragma unroll 1
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + lane_addr + (uint32_t)(u0 + c0), v);
+#pragma unroll
+      for (int k = 0; k < 32; k += 2) {
+        const uint32_t pk = pack2((m1 >> (c0 + k)) & 1ull ? v[k] : 0.f, (m1 >> (c0 + k + 1)) & 1ull ? v[k + 1] : 0.f);
+        put_t(FB_A1, u0 + c0 + k, r, pk & 0xffffu);
+        put_t(FB_A1, u0 + c0 + k + 1, r, pk >> 16);
+      }
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t == 0) {
+#pragma unroll
+      for (int kk = 0; kk < TM / 16; ++kk) {
+        const uint32_t acc = (any || kk > 0) ? 1u : 0u;
+        mma_bf16_n(tmem + kColW2, sdesc(base + FB_A2 + kk * 2 * LBO_P, LBO_P, SBO_P),
+                   sdesc(base + FB_B2 + kk * 2 * LBO_P, LBO_P, SBO_P), kIdescN2, acc);
+        mma_bf16_n(tmem + kColW1, sdesc(base + FB_A1 + kk * 2 * LBO_P, LBO_P, SBO_P),
+                   sdesc(base + FB_B1 + kk * 2 * LBO_P, LBO_P, SBO_P), kIdescN1, acc);
+      }
+      commit(mbar);
+    }
+    any = true;
+    if (__syncthreads_or(!wait_parity(mbar, phase))) {
+      failed = pending = true;
+      break;
+    }
+    phase ^= 1u;
+    fence_after();
+  }
+  if (failed) {
+    if (t == 0 && status) atomicExch(status, 1);
+    if (pending) wait_parity(mbar, phase);
+  } else if (any) {
+    if (t < TM) {  // row t of the weight-gradient accumulators: hidden unit t
+#pragma unroll 1
+      for (int c0 = 0; c0 < (int)N2; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + lane_addr + kColW2 + (uint32_t)c0, v);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const int c = c0 + k;
+          if (c < TH) atomicAdd(grads + kOffW2 + t * TH + c, v[k]);
+          else if (c == TH) atomicAdd(grads + kOffB2 + t, v[k]);
+        }
+      }
+      float v[32];
+      tmem_ld32(tmem + lane_addr + kColW1, v);
+#pragma unroll
+      for (int k = 0; k < TI; ++k) atomicAdd(grads + kOffW1 + t * TI + k, v[k]);
+      atomicAdd(grads + kOffB1 + t, v[TI]);
+    }
+    atomicAdd(grads + kOffW3 + (t & (TH - 1)), w3);
+    if ((t & (TH - 1)) == 0) atomicAdd(grads + kOffB3, b3);
+  }
+  lsum = warp_sum_d(lsum);
+  if ((t & 31) == 0 && lsum != 0.0) atomicAdd(loss, lsum);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBwTmemCols));
+}
+
 }  // namespace
+
+// Launches k_mlp_backward_tc over the rows (one CTA per SM: its shared
+// memory and 512 TMEM columns).
+tgs_status launch_mlp_backward_tc(const tgs_mlp* w, const float* x, const uint16_t* h1, const uint16_t* h2,
+                                  const float* y, const float* target, int64_t R, const int32_t* R_dev,
+                                  float* grads, double* loss, int32_t* status, cudaStream_t s) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return check_launch();
+  static bool attr[64] = {};
+  if (dev < 0 || dev >= 64) return TGS_ERR_DEVICE;
+  if (!attr[dev]) {
+    cudaFuncSetAttribute(k_mlp_backward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FB_SMEM);
+    attr[dev] = true;
+  }
+  const int64_t tiles = (R + TM - 1) / TM;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, device_sm_count()));
+  k_mlp_backward_tc<<<grid, kBwThreads, FB_SMEM, s>>>(TcArgs{w->w1, w->w2, w->w3, w->b1, w->b2, w->b3}, x, h1, h2, y,
+                                                      target, R, R_dev, grads, loss, status);
+  return check_launch();
+}
 
 // Launches k_mlp_backward_act_tc over the rows (two CTAs per SM at most:
 // 2 x 128 TMEM columns).
