@@ -384,12 +384,6 @@ static int mlp_grid(int64_t R) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((tiles + 3) / 4, (int64_t)device_sm_count() * 8));
 }
 
-tgs_status launch_mlp_wgrad_tc(const float* x, const uint16_t* h1, const uint16_t* h2, const float* dy,
-                               const uint16_t* dh2, const uint16_t* dh1, int64_t R, float* grads, int32_t* status,
-                               cudaStream_t s);
-tgs_status launch_mlp_act_tc(const tgs_mlp* w, const uint16_t* h1, const uint16_t* h2, const float* y,
-                             const float* target, int64_t R, const int32_t* R_dev, float* dy, uint16_t* dh2,
-                             uint16_t* dh1, double* loss, int32_t* status, cudaStream_t s);
 tgs_status launch_mlp_backward_tc(const tgs_mlp* w, const float* x, const uint16_t* h1, const uint16_t* h2,
                                   const float* y, const float* target, int64_t R, const int32_t* R_dev,
                                   float* grads, double* loss, int32_t* status, cudaStream_t s);

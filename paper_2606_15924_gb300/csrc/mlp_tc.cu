@@ -292,33 +292,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(TcArgs w, cons
 }
 
 // ---------------------------------------------------------------------------
-// Weight gradients on the tensor cores: sums over rows of outer products,
-// i.e. contractions over the row index.  For a 128-row tile
+// Weight gradients as tensor-core contractions over the row index.  For a
+// 128-row tile
 //   dW2 [128 k][128 j] += dH2^T H1,   db2 [k] += sum_r dH2 [r][k],
 //   dW1 [128 j][16 i]  += dH1^T X,    db1 [j] += sum_r dH1 [r][j],
 // with M = 128 hidden units, K = 128 rows and N = 144 (128 units, a column
 // of ones for the bias, 15 zero columns) or N = 32 (16 features, ones, 15
-// zeros), accumulated in TMEM over all the tiles a CTA takes; dW3 and db3
-// (fp32 dy, not a bf16 operand) on the CUDA cores.  The operands are the
-// transposes of the stored rows: each thread moves an 8 x 8 block (8 rows x
-// 16 bytes) through registers into one K-major core-matrix column.  Core
-// matrices along K are 144 bytes apart (16 bytes of padding), so the eight
-// lanes of a store phase hit eight different bank groups.  The products are
-// those of the CUDA-core version: bf16 x bf16, fp32 sums (x rounded to bf16).
-constexpr int kWgTcThreads = 256;
+// zeros).  The operands are transposes of the rows, in K-major tiles whose
+// core matrices along K are 144 bytes apart (16 bytes of padding), so that
+// the 2-byte stores of the eight lanes of a phase (eight consecutive rows)
+// hit eight different bank groups.
 constexpr uint32_t LBO_P = 144;                 // core matrices along K (padded)
 constexpr uint32_t SBO_P = 16 * LBO_P;          // 8-row groups (K = 128)
 constexpr uint32_t N2 = TH + 16, N1 = 32;       // B widths: units + ones + zeros, features + ones + zeros
-constexpr uint32_t OFF_A2 = 0;                              // dH2^T [128 k][128 r]
-constexpr uint32_t OFF_B2 = OFF_A2 + (TH / 8) * SBO_P;      // [H1^T; 1; 0] [144 j][128 r]
-constexpr uint32_t OFF_A1 = OFF_B2 + (N2 / 8) * SBO_P;      // dH1^T [128 j][128 r]
-constexpr uint32_t OFF_B1 = OFF_A1 + (TH / 8) * SBO_P;      // [X^T; 1; 0] [32 i][128 r]
-constexpr uint32_t OFF_H2W = OFF_B1 + (N1 / 8) * SBO_P;     // h2 rows [128 r][128] (bf16), for dW3
-constexpr uint32_t OFF_DYW = OFF_H2W + TM * TH * 2;         // dy [128]
-constexpr uint32_t WG_SMEM = OFF_DYW + TM * 4;
-static_assert(WG_SMEM <= 227 * 1024, "weight-gradient tiles fit one CTA's shared memory");
-constexpr uint32_t kWgTmemCols = 256;           // D2 at columns 0..143, D1 at 160..191
-constexpr uint32_t kColD1 = 160;
 // instruction descriptors of the two contractions (as kIdesc, N = N2 and N1)
 constexpr uint32_t kIdescN2 = (1u << 4) | (1u << 7) | (1u << 10) | ((N2 >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 constexpr uint32_t kIdescN1 = (1u << 4) | (1u << 7) | (1u << 10) | ((N1 >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
@@ -335,319 +321,20 @@ __device__ __forceinline__ void mma_bf16_n(uint32_t d_tmem, uint64_t a, uint64_t
       "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
-// The 8 x 8 transpose of bf16 blocks: v[i] holds row i (8 values); out[c]
-// receives column c (the 8 rows' value c).
-__device__ __forceinline__ void transpose8(const uint4 (&v)[8], uint4 (&out)[8]) {
-  uint32_t w[8][4];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    w[i][0] = v[i].x; w[i][1] = v[i].y; w[i][2] = v[i].z; w[i][3] = v[i].w;
-  }
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    const uint32_t sel = (c & 1) ? 0x7632u : 0x5410u;
-    const int q = c >> 1;
-    out[c] = make_uint4(__byte_perm(w[0][q], w[1][q], sel), __byte_perm(w[2][q], w[3][q], sel),
-                        __byte_perm(w[4][q], w[5][q], sel), __byte_perm(w[6][q], w[7][q], sel));
-  }
-}
-
-// Rows r0 + 8 ro .. + 7, columns 8 co .. + 7 of a [R][128] bf16 array (zero
-// past R), transposed into the K-major tile at sm + off: column c becomes
-// core-matrix row n = 8 co + c at K = 8 ro.
-__device__ __forceinline__ void stage_t(unsigned char* sm, uint32_t off, const uint16_t* __restrict__ src, int64_t r0,
-                                        int64_t R, int ro, int co) {
-  uint4 v[8], o[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int64_t r = r0 + 8 * ro + i;
-    v[i] = r < R ? *reinterpret_cast<const uint4*>(src + r * TH + 8 * co) : make_uint4(0u, 0u, 0u, 0u);
-  }
-  transpose8(v, o);
-#pragma unroll
-  for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4*>(sm + off + core_off_p(8 * co + c, 8 * ro)) = o[c];
-}
-
-__global__ void __launch_bounds__(kWgTcThreads, 1) k_mlp_wgrad_tc(const float* __restrict__ x,
-                                                                 const uint16_t* __restrict__ h1,
-                                                                 const uint16_t* __restrict__ h2,
-                                                                 const float* __restrict__ dy,
-                                                                 const uint16_t* __restrict__ dh2,
-                                                                 const uint16_t* __restrict__ dh1, int64_t R,
-                                                                 float* __restrict__ grads,
-                                                                 int32_t* __restrict__ status) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_mbar;
-  const int t = threadIdx.x, warp = t >> 5;
-  // the constant rows of the B tiles: ones (bias column) and zeros
-  for (int i = t; i < 16 * (TM / 8); i += kWgTcThreads) {
-    const int n = i / (TM / 8), k8 = (i % (TM / 8)) * 8;
-    const uint32_t one2 = 0x3F803F80u;  // two bf16 1.0
-    const uint4 u = n == 0 ? make_uint4(one2, one2, one2, one2) : make_uint4(0u, 0u, 0u, 0u);
-    *reinterpret_cast<uint4*>(sm + OFF_B2 + core_off_p(TH + n, k8)) = u;
-    *reinterpret_cast<uint4*>(sm + OFF_B1 + core_off_p(TI + n, k8)) = u;
-  }
-  if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                 "r"(kWgTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = s_tmem;
-  const uint32_t mbar = smem_u32(&s_mbar);
-  const uint32_t base = smem_u32(sm);
-  const uint16_t* s_h2 = reinterpret_cast<const uint16_t*>(sm + OFF_H2W);
-  const float* s_dy = reinterpret_cast<const float*>(sm + OFF_DYW);
-  uint32_t phase = 0;
-  bool failed = false, pending = false, any = false;
-  float w3 = 0.f, b3 = 0.f;  // thread t: unit t & 127 over rows 64 (t >> 7) .. + 63 of each tile
-  const int64_t tiles = (R + TM - 1) / TM;
-  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int64_t r0 = tile * TM;
-    // stage: three transposed 128 x 128 operands (one 8 x 8 block each per thread), X^T, h2 and dy
-    const int ro = t & 15, co = t >> 4;
-    stage_t(sm, OFF_A2, dh2, r0, R, ro, co);
-    stage_t(sm, OFF_B2, h1, r0, R, ro, co);
-    stage_t(sm, OFF_A1, dh1, r0, R, ro, co);
-    if (t < 32) {  // X^T: features 8 (t >> 4) .. + 7 of rows 8 (t & 15) .. + 7, rounded to bf16
-      uint4 v[8], o[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int64_t r = r0 + 8 * ro + i;
-        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-        if (r < R) {
-          a = *reinterpret_cast<const float4*>(x + r * TI + 8 * co);
-          b = *reinterpret_cast<const float4*>(x + r * TI + 8 * co + 4);
-        }
-        v[i] = make_uint4(pack2(a.x, a.y), pack2(a.z, a.w), pack2(b.x, b.y), pack2(b.z, b.w));
-      }
-      transpose8(v, o);
-#pragma unroll
-      for (int c = 0; c < 8; ++c) *reinterpret_cast<uint4*>(sm + OFF_B1 + core_off_p(8 * co + c, 8 * ro)) = o[c];
-    }
-    for (int i = t; i < TM * (TH / 8); i += kWgTcThreads) {
-      const int r = i / (TH / 8), c8 = (i % (TH / 8)) * 8;
-      *reinterpret_cast<uint4*>(sm + OFF_H2W + (uint32_t)(r * TH + c8) * 2u) =
-          r0 + r < R ? *reinterpret_cast<const uint4*>(h2 + (r0 + r) * TH + c8) : make_uint4(0u, 0u, 0u, 0u);
-    }
-    if (t < TM) reinterpret_cast<float*>(sm + OFF_DYW)[t] = r0 + t < R ? dy[r0 + t] : 0.f;
-    fence_async_smem();
-    fence_before();
-    __syncthreads();
-    fence_after();
-    if (t == 0) {
-#pragma unroll
-      for (int kk = 0; kk < TM / 16; ++kk) {
-        const uint32_t acc = (any || kk > 0) ? 1u : 0u;
-        mma_bf16_n(tmem, sdesc(base + OFF_A2 + kk * 2 * LBO_P, LBO_P, SBO_P),
-                   sdesc(base + OFF_B2 + kk * 2 * LBO_P, LBO_P, SBO_P), kIdescN2, acc);
-        mma_bf16_n(tmem + kColD1, sdesc(base + OFF_A1 + kk * 2 * LBO_P, LBO_P, SBO_P),
-                   sdesc(base + OFF_B1 + kk * 2 * LBO_P, LBO_P, SBO_P), kIdescN1, acc);
-      }
-      commit(mbar);
-    }
-    any = true;
-    // dW3, db3 on the CUDA cores while the tensor cores run
-    {
-      const int u = t & (TH - 1), rb = 64 * (t >> 7);
-#pragma unroll 8
-      for (int r = rb; r < rb + 64; ++r) {
-        w3 += s_dy[r] * __uint_as_float((uint32_t)s_h2[r * TH + u] << 16);
-        if (u == 0) b3 += s_dy[r];
-      }
-    }
-    if (__syncthreads_or(!wait_parity(mbar, phase))) {
-      failed = pending = true;
-      break;
-    }
-    phase ^= 1u;
-    fence_after();
-  }
-  if (failed) {
-    if (t == 0 && status) atomicExch(status, 1);
-    if (pending) wait_parity(mbar, phase);  // the MMAs still in flight (bounded)
-  } else if (any && t < TM) {
-    // row t of the accumulators is hidden unit t: dW2 [t][0..127], db2 [t]; dW1 [t][0..15], db1 [t]
-    const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
-#pragma unroll 1
-    for (int c0 = 0; c0 < (int)N2; c0 += 32) {
-      float v[32];
-      tmem_ld32(tmem + lane_addr + (uint32_t)c0, v);
-#pragma unroll
-      for (int k = 0; k < 32; ++k) {
-        const int c = c0 + k;
-        if (c < TH) atomicAdd(grads + kOffW2 + t * TH + c, v[k]);
-        else if (c == TH) atomicAdd(grads + kOffB2 + t, v[k]);
-      }
-    }
-    float v[32];
-    tmem_ld32(tmem + lane_addr + kColD1, v);
-#pragma unroll
-    for (int k = 0; k < TI; ++k) atomicAdd(grads + kOffW1 + t * TI + k, v[k]);
-    atomicAdd(grads + kOffB1 + t, v[TI]);
-  }
-  if (!failed && any) {
-    atomicAdd(grads + kOffW3 + (t & (TH - 1)), w3);
-    if ((t & (TH - 1)) == 0) atomicAdd(grads + kOffB3, b3);
-  }
-  fence_before();
-  __syncthreads();
-  fence_after();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kWgTmemCols));
-}
-
-// ---------------------------------------------------------------------------
-// Activation adjoint on the tensor cores, per 128-row tile (one thread per
-// row, the forward's layer-2 structure run backwards):
-//   dy = (y - t) / R, dh2 = bf16([h2 > 0] dy W3) into the K-major A tile,
-//   D = dH2 W2 (M 128 rows, N 128 units j, K 128 units k; B [j][k] = W2 [k][j],
-//   staged once per CTA) into TMEM, dh1 = bf16([h1 > 0] D);
-// dy, dh2 and dh1 rows go to memory for the weight gradients, and the loss
-// is summed.  The same roundings as the mma.sync kernel (dh2 and dh1 to bf16,
-// fp32 sums of bf16 products).
-constexpr uint32_t OFF_W2T = 0;                     // W2^T [128 j][128 k]
-constexpr uint32_t OFF_DA = OFF_W2T + TH * TH * 2;  // dH2 [128 r][128 k]
-constexpr uint32_t OFF_W3A = OFF_DA + TM * TH * 2;  // w3 (fp32) [128]
-constexpr uint32_t ACT_SMEM = OFF_W3A + TH * 4;
-constexpr uint32_t kActTmemCols = 128;
-
-__global__ void __launch_bounds__(kTcThreads, 1) k_mlp_backward_act_tc(
-    TcArgs w, const uint16_t* __restrict__ h1, const uint16_t* __restrict__ h2, const float* __restrict__ y,
-    const float* __restrict__ tgt, int64_t R, const int32_t* __restrict__ R_dev, float* __restrict__ dy_out,
-    uint16_t* __restrict__ dh2_out, uint16_t* __restrict__ dh1_out, double* __restrict__ loss,
-    int32_t* __restrict__ status) {
-  extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ uint32_t s_tmem;
-  __shared__ __align__(8) uint64_t s_mbar;
-  const int t = threadIdx.x, warp = t >> 5;
-  float* w3f = reinterpret_cast<float*>(sm + OFF_W3A);
-  // B [n = j][k] = W2 [k][j]: eight k of one j (a strided gather of w2) per 16-byte chunk
-  for (int i = t; i < TH * (TH / 8); i += kTcThreads) {
-    const int n = i % TH, k8 = (i / TH) * 8;
-    uint32_t q[4];
-#pragma unroll
-    for (int e = 0; e < 4; ++e)
-      q[e] = (uint32_t)w.w2[(k8 + 2 * e) * TH + n] | ((uint32_t)w.w2[(k8 + 2 * e + 1) * TH + n] << 16);
-    *reinterpret_cast<uint4*>(sm + OFF_W2T + core_off(n, k8, SBO_K128)) = make_uint4(q[0], q[1], q[2], q[3]);
-  }
-  for (int i = t; i < TH; i += kTcThreads) w3f[i] = __uint_as_float((uint32_t)w.w3[i] << 16);
-  if (t == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                 "r"(kActTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  fence_async_smem();
-  fence_before();
-  __syncthreads();
-  fence_after();
-  const uint32_t tmem = s_tmem;
-  const uint32_t mbar = smem_u32(&s_mbar);
-  const uint32_t base = smem_u32(sm);
-  const uint32_t lane_addr = (uint32_t)(warp * 32) << 16;
-  // rows past Re are padding: no error, no gradient
-  const int64_t Re = R_dev ? (*R_dev > 0 ? (*R_dev < R ? (int64_t)*R_dev : R) : 0) : R;
-  const float inv = Re > 0 ? 1.f / (float)Re : 0.f;
-  double lsum = 0.0;
-  uint32_t phase = 0;
-  bool failed = false, pending = false;
-  const int64_t tiles = (R + TM - 1) / TM;
-  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int64_t row = tile * TM + t;
-    const bool valid = row < R;
-    const float e = row < Re ? y[row] - tgt[row] : 0.f;
-    lsum += 0.5 * (double)e * (double)e * (double)inv;
-    const float d = e * inv;
-    if (valid) dy_out[row] = d;
-    // dh2 row -> A tile (and memory)
-#pragma unroll 1
-    for (int c8 = 0; c8 < TH; c8 += 8) {
-      const uint4 hv = valid ? *reinterpret_cast<const uint4*>(h2 + row * TH + c8) : make_uint4(0u, 0u, 0u, 0u);
-      const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
-      uint32_t pk[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float a0 = __uint_as_float(hw[q] << 16) > 0.f ? d * w3f[c8 + 2 * q] : 0.f;
-        const float a1 = __uint_as_float(hw[q] & 0xffff0000u) > 0.f ? d * w3f[c8 + 2 * q + 1] : 0.f;
-        pk[q] = pack2(a0, a1);
-      }
-      const uint4 u = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-      *reinterpret_cast<uint4*>(sm + OFF_DA + core_off(t, c8, SBO_K128)) = u;
-      if (valid) *reinterpret_cast<uint4*>(dh2_out + row * TH + c8) = u;
-    }
-    fence_async_smem();
-    fence_before();
-    __syncthreads();
-    fence_after();
-    if (t == 0) {
-#pragma unroll
-      for (int kk = 0; kk < TH / 16; ++kk)
-        mma_bf16(tmem, sdesc(base + OFF_DA + kk * 256, 128, SBO_K128), sdesc(base + OFF_W2T + kk * 256, 128, SBO_K128),
-                 kk > 0 ? 1u : 0u);
-      commit(mbar);
-    }
-    if (__syncthreads_or(!wait_parity(mbar, phase))) {
-      failed = pending = true;
-      break;
-    }
-    phase ^= 1u;
-    fence_after();
-    // dh1 = bf16([h1 > 0] D)
-#pragma unroll 1
-    for (int c0 = 0; c0 < TH; c0 += 32) {
-      float v[32];
-      tmem_ld32(tmem + lane_addr + (uint32_t)c0, v);
-#pragma unroll
-      for (int q8 = 0; q8 < 4; ++q8) {
-        const int c8 = c0 + 8 * q8;
-        const uint4 hv = valid ? *reinterpret_cast<const uint4*>(h1 + row * TH + c8) : make_uint4(0u, 0u, 0u, 0u);
-        const uint32_t hw[4] = {hv.x, hv.y, hv.z, hv.w};
-        uint32_t pk[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          pk[q] = pack2(__uint_as_float(hw[q] << 16) > 0.f ? v[8 * q8 + 2 * q] : 0.f,
-                        __uint_as_float(hw[q] & 0xffff0000u) > 0.f ? v[8 * q8 + 2 * q + 1] : 0.f);
-        if (valid) *reinterpret_cast<uint4*>(dh1_out + row * TH + c8) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
-      }
-    }
-    // every thread is done reading TMEM and the A tile before the next MMA
-    fence_before();
-    __syncthreads();
-    fence_after();
-  }
-  if (failed) {
-    if (t == 0 && status) atomicExch(status, 1);
-    if (pending) wait_parity(mbar, phase);
-  }
-  lsum = warp_sum_d(lsum);
-  if ((t & 31) == 0 && lsum != 0.0) atomicAdd(loss, lsum);
-  fence_before();
-  __syncthreads();
-  fence_after();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kActTmemCols));
-}
-
 // ---------------------------------------------------------------------------
 // The whole backward in one pass over the rows: per 128-row tile the
-// activation adjoint (as k_mlp_backward_act_tc) and the weight gradients (as
-// k_mlp_wgrad_tc) with dH2 and dH1 kept in shared memory, so the rows are read
-// once and no adjoint goes to memory.  256 threads: thread t takes row t % 128
+// activation adjoint (dH1 = [H1 > 0] (dH2 W2), the forward's second layer run
+// backwards) and the weight gradients above, with dH2 and dH1 kept in shared
+// memory, so the rows are read once and no adjoint goes to memory; dW3 and
+// db3 (fp32 dy, not a bf16 operand) on the CUDA cores.  256 threads: thread t takes row t % 128
 // and hidden units 64 (t / 128) .. + 63.  dH2 is written twice, as the
 // row-major A tile of dH1 = dH2 W2 and (transposed, 2-byte stores whose eight
 // lanes of a phase hit distinct banks through the padded core matrices) as
 // the A tile of dW2; H1 and X likewise go transposed into the B tiles of the
 // weight gradients.  TMEM: dH1 in columns 0-127, dW2 | db2 in 128-271, dW1 |
-// db1 in 288-319.  The roundings and products are those of the two kernels.
+// db1 in 288-319.  The roundings and products are those of the mma.sync and
+// CUDA-core backward: dH2 and dH1 rounded to bf16, bf16 x bf16 products with
+// fp32 sums, x rounded to bf16.
 constexpr int kBwThreads = 256;
 constexpr uint32_t FB_W2T = 0;                            // W2^T [128 j][128 k] (B of dH1)
 constexpr uint32_t FB_DA = FB_W2T + TH * TH * 2;          // dH2 [128 r][128 k] (A of dH1)
@@ -892,45 +579,6 @@ tgs_status launch_mlp_backward_tc(const tgs_mlp* w, const float* x, const uint16
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, device_sm_count()));
   k_mlp_backward_tc<<<grid, kBwThreads, FB_SMEM, s>>>(TcArgs{w->w1, w->w2, w->w3, w->b1, w->b2, w->b3}, x, h1, h2, y,
                                                       target, R, R_dev, grads, loss, status);
-  return check_launch();
-}
-
-// Launches k_mlp_backward_act_tc over the rows (two CTAs per SM at most:
-// 2 x 128 TMEM columns).
-tgs_status launch_mlp_act_tc(const tgs_mlp* w, const uint16_t* h1, const uint16_t* h2, const float* y,
-                             const float* target, int64_t R, const int32_t* R_dev, float* dy, uint16_t* dh2,
-                             uint16_t* dh1, double* loss, int32_t* status, cudaStream_t s) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return check_launch();
-  static bool attr[64] = {};
-  if (dev < 0 || dev >= 64) return TGS_ERR_DEVICE;
-  if (!attr[dev]) {
-    cudaFuncSetAttribute(k_mlp_backward_act_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ACT_SMEM);
-    attr[dev] = true;
-  }
-  const int64_t tiles = (R + TM - 1) / TM;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, 2ll * device_sm_count()));
-  k_mlp_backward_act_tc<<<grid, kTcThreads, ACT_SMEM, s>>>(TcArgs{w->w1, w->w2, w->w3, w->b1, w->b2, w->b3}, h1, h2,
-                                                           y, target, R, R_dev, dy, dh2, dh1, loss, status);
-  return check_launch();
-}
-
-// Launches k_mlp_wgrad_tc over the rows (one CTA per SM at most: its shared
-// memory allows one per SM, and each CTA accumulates all its tiles in TMEM).
-tgs_status launch_mlp_wgrad_tc(const float* x, const uint16_t* h1, const uint16_t* h2, const float* dy,
-                               const uint16_t* dh2, const uint16_t* dh1, int64_t R, float* grads, int32_t* status,
-                               cudaStream_t s) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return check_launch();
-  static bool attr[64] = {};
-  if (dev < 0 || dev >= 64) return TGS_ERR_DEVICE;
-  if (!attr[dev]) {
-    cudaFuncSetAttribute(k_mlp_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WG_SMEM);
-    attr[dev] = true;
-  }
-  const int64_t tiles = (R + TM - 1) / TM;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, device_sm_count()));
-  k_mlp_wgrad_tc<<<grid, kWgTcThreads, WG_SMEM, s>>>(x, h1, h2, dy, dh2, dh1, R, grads, status);
   return check_launch();
 }
 
