@@ -76,9 +76,9 @@ def test_traffic_figures_follow_their_sources(tmp_path, monkeypatch):
 
 
 def test_quality_settings_unique():
-    args = types.SimpleNamespace(fraction=0.4, rate=bench.PIXEL_RATE)
+    args = types.SimpleNamespace(fraction=1.0, rate=0.1)
     s = bench.quality_settings(args)
-    assert s == [(0.4, bench.PIXEL_RATE), (1.0, bench.PIXEL_RATE), (1.0, 0.1)]
+    assert s == [(1.0, 0.1), (1.0, bench.PIXEL_RATE), (0.5, 0.1)]
     args = types.SimpleNamespace(fraction=0.2, rate=bench.PIXEL_RATE)
     assert len(bench.quality_settings(args)) == 4
 
