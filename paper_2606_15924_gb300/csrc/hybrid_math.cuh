@@ -102,15 +102,60 @@ __device__ __forceinline__ void bias_corrections(OptK& o) {
   }
 }
 
-// Update of Gaussian i's LM blocks (geometry 10, appearance 4: SH DC rgb and
-// opacity logit) and of its first higher SH coefficient (the fourth lane of
-// SH float4 0), from its gradient gg (means, log-scales, quaternion), sg (SH
-// float4 0) and og (opacity logit).
+// The geometry LM block (means, log-scales, quaternion: 10 parameters) of
+// Gaussian i in registers: the moments (gm, gv) take gradient gg, and the
+// parameters gp their step.
 template <int MODE>
-__device__ __forceinline__ void lm_update_one(const tgs_param_ptrs& P, const tgs_param_ptrs& M,
+__device__ __forceinline__ void lm_geo_step(const float (&gg)[10], float (&gp)[10], float (&gm)[10], float (&gv)[10],
+                                            const float* __restrict__ rows, int k_rows, int64_t n, int64_t i,
+                                            const OptK& o) {
+#pragma unroll
+  for (int k = 0; k < 10; ++k) moments(gg[k], gm[k], gv[k], o);
+  if (MODE == 0) {
+#pragma unroll
+    for (int k = 0; k < 10; ++k) gp[k] += adam_delta(gm[k], gv[k], o.lr[k < 3 ? 0 : k < 6 ? 1 : 2], o);
+  } else {
+    float dgeo[10];
+    lm_block<10>(gg, gm, gv, rows, k_rows, n, i, 0, MODE, o.eps_lm, dgeo);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) gp[k] += o.lr[k < 3 ? 0 : k < 6 ? 1 : 2] * dgeo[k];
+  }
+}
+
+// The appearance LM block (SH DC r g b and the opacity logit) and the first
+// higher SH coefficient (the fourth lane of SH float4 0, an Adam step) of
+// Gaussian i in registers, from sg (the gradient of SH float4 0) and og
+// (opacity logit): parameters (sp, op), moments (smm, om) and (sv, ov).
+template <int MODE>
+__device__ __forceinline__ void lm_app_step(const float (&sg)[4], float og, float (&sp)[4], float (&smm)[4],
+                                            float (&sv)[4], float& op, float& om, float& ov,
+                                            const float* __restrict__ rows, int k_rows, int64_t n, int64_t i,
+                                            const OptK& o) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) moments(sg[k], smm[k], sv[k], o);
+  moments(og, om, ov, o);
+  if (MODE == 0) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sp[k] += adam_delta(smm[k], sv[k], o.lr[4], o);
+    op += adam_delta(om, ov, o.lr[3], o);
+  } else {
+    const float ag[4] = {sg[0], sg[1], sg[2], og}, am[4] = {smm[0], smm[1], smm[2], om},
+                av[4] = {sv[0], sv[1], sv[2], ov};
+    float dapp[4];
+    lm_block<4>(ag, am, av, rows, k_rows, n, i, 10, MODE, o.eps_lm, dapp);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) sp[k] += o.lr[4] * dapp[k];
+    op += o.lr[3] * dapp[3];
+  }
+  sp[3] += adam_delta(smm[3], sv[3], o.lr[5], o);
+}
+
+// The geometry LM block of Gaussian i (means, log-scales, quaternion: 10
+// parameters) from its gradient gg, read from and written to memory.
+template <int MODE>
+__device__ __forceinline__ void lm_update_geo(const tgs_param_ptrs& P, const tgs_param_ptrs& M,
                                               const tgs_param_ptrs& V, int64_t n, int64_t i, const float (&gg)[10],
-                                              const float (&sg)[4], float og, const float* __restrict__ rows,
-                                              int k_rows, const OptK& o) {
+                                              const float* __restrict__ rows, int k_rows, const OptK& o) {
   float gp[10], gm[10], gv[10];
   const GeoW gP = geo_of(P), gM = geo_of(M), gV = geo_of(V);
   {
@@ -132,36 +177,7 @@ __device__ __forceinline__ void lm_update_one(const tgs_param_ptrs& P, const tgs
     gm[6] = c.x; gm[7] = c.y; gm[8] = c.z; gm[9] = c.w;
     gv[6] = d.x; gv[7] = d.y; gv[8] = d.z; gv[9] = d.w;
   }
-  const float4 p0 = reinterpret_cast<const float4*>(P.sh)[12 * i];
-  const float4 m0 = reinterpret_cast<const float4*>(M.sh)[12 * i], v0 = reinterpret_cast<const float4*>(V.sh)[12 * i];
-  float sp[4] = {p0.x, p0.y, p0.z, p0.w};
-  float smm[4] = {m0.x, m0.y, m0.z, m0.w}, sv[4] = {v0.x, v0.y, v0.z, v0.w};
-  float op = *gP.opac(i), om = *gM.opac(i), ov = *gV.opac(i);
-#pragma unroll
-  for (int k = 0; k < 10; ++k) moments(gg[k], gm[k], gv[k], o);
-#pragma unroll
-  for (int k = 0; k < 4; ++k) moments(sg[k], smm[k], sv[k], o);
-  moments(og, om, ov, o);
-  if (MODE == 0) {
-#pragma unroll
-    for (int k = 0; k < 10; ++k) gp[k] += adam_delta(gm[k], gv[k], o.lr[k < 3 ? 0 : k < 6 ? 1 : 2], o);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) sp[k] += adam_delta(smm[k], sv[k], o.lr[4], o);
-    op += adam_delta(om, ov, o.lr[3], o);
-  } else {
-    float dgeo[10];
-    lm_block<10>(gg, gm, gv, rows, k_rows, n, i, 0, MODE, o.eps_lm, dgeo);
-#pragma unroll
-    for (int k = 0; k < 10; ++k) gp[k] += o.lr[k < 3 ? 0 : k < 6 ? 1 : 2] * dgeo[k];
-    const float ag[4] = {sg[0], sg[1], sg[2], og}, am[4] = {smm[0], smm[1], smm[2], om},
-                av[4] = {sv[0], sv[1], sv[2], ov};
-    float dapp[4];
-    lm_block<4>(ag, am, av, rows, k_rows, n, i, 10, MODE, o.eps_lm, dapp);
-#pragma unroll
-    for (int k = 0; k < 3; ++k) sp[k] += o.lr[4] * dapp[k];
-    op += o.lr[3] * dapp[3];
-  }
-  sp[3] += adam_delta(smm[3], sv[3], o.lr[5], o);
+  lm_geo_step<MODE>(gg, gp, gm, gv, rows, k_rows, n, i, o);
   {
     float* a = gP.mean(i);
     float* b = gM.mean(i);
@@ -178,10 +194,36 @@ __device__ __forceinline__ void lm_update_one(const tgs_param_ptrs& P, const tgs
   *gP.quat(i) = make_float4(gp[6], gp[7], gp[8], gp[9]);
   *gM.quat(i) = make_float4(gm[6], gm[7], gm[8], gm[9]);
   *gV.quat(i) = make_float4(gv[6], gv[7], gv[8], gv[9]);
+}
+
+// The appearance LM block of Gaussian i and its SH float4 0, read from and
+// written to memory.
+template <int MODE>
+__device__ __forceinline__ void lm_update_app(const tgs_param_ptrs& P, const tgs_param_ptrs& M,
+                                              const tgs_param_ptrs& V, int64_t n, int64_t i, const float (&sg)[4],
+                                              float og, const float* __restrict__ rows, int k_rows, const OptK& o) {
+  const GeoW gP = geo_of(P), gM = geo_of(M), gV = geo_of(V);
+  const float4 p0 = reinterpret_cast<const float4*>(P.sh)[12 * i];
+  const float4 m0 = reinterpret_cast<const float4*>(M.sh)[12 * i], v0 = reinterpret_cast<const float4*>(V.sh)[12 * i];
+  float sp[4] = {p0.x, p0.y, p0.z, p0.w};
+  float smm[4] = {m0.x, m0.y, m0.z, m0.w}, sv[4] = {v0.x, v0.y, v0.z, v0.w};
+  float op = *gP.opac(i), om = *gM.opac(i), ov = *gV.opac(i);
+  lm_app_step<MODE>(sg, og, sp, smm, sv, op, om, ov, rows, k_rows, n, i, o);
   *gP.opac(i) = op; *gM.opac(i) = om; *gV.opac(i) = ov;
   reinterpret_cast<float4*>(P.sh)[12 * i] = make_float4(sp[0], sp[1], sp[2], sp[3]);
   reinterpret_cast<float4*>(M.sh)[12 * i] = make_float4(smm[0], smm[1], smm[2], smm[3]);
   reinterpret_cast<float4*>(V.sh)[12 * i] = make_float4(sv[0], sv[1], sv[2], sv[3]);
+}
+
+// Both LM blocks and SH float4 0 of Gaussian i: gradient gg (means,
+// log-scales, quaternion), sg (SH float4 0) and og (opacity logit).
+template <int MODE>
+__device__ __forceinline__ void lm_update_one(const tgs_param_ptrs& P, const tgs_param_ptrs& M,
+                                              const tgs_param_ptrs& V, int64_t n, int64_t i, const float (&gg)[10],
+                                              const float (&sg)[4], float og, const float* __restrict__ rows,
+                                              int k_rows, const OptK& o) {
+  lm_update_geo<MODE>(P, M, V, n, i, gg, rows, k_rows, o);
+  lm_update_app<MODE>(P, M, V, n, i, sg, og, rows, k_rows, o);
 }
 
 // Adam update of Gaussian i's SH float4 k (1..11) from its gradient g.

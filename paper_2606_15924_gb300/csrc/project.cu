@@ -238,11 +238,12 @@ bool camera_ok(const tgs_camera* c);
 struct SmemSh {
   float* base;  // element k at base[k * stride]
   int stride;
+  bool fresh = false;  // set: add() stores (the first view, no zeroing pass)
   __device__ __forceinline__ void zero() {
 #pragma unroll
     for (int k = 0; k < 48; ++k) base[k * stride] = 0.f;
   }
-  __device__ __forceinline__ void add(int k, float x) { base[k * stride] += x; }
+  __device__ __forceinline__ void add(int k, float x) { base[k * stride] = fresh ? x : base[k * stride] + x; }
   __device__ __forceinline__ float get(int k) const { return base[k * stride]; }
 };
 
@@ -278,19 +279,16 @@ __device__ __forceinline__ bool grad2d_nonzero(float4 ga, float4 gb, float4 gc) 
          gb.w != 0.f || gc.x != 0.f;
 }
 
-// Adds one view's adjoint of the projection of Gaussian (mu, ls, qr, opacity
-// o, SH block shp) into acc; rw (nullable) receives this view's own gradient
-// row (means, log-scales, quaternion, DC r g b, opacity logit).
+// The colour part of one view's adjoint: the SH coefficients' gradient
+// (Sh::add, coefficient j = 3 k + c of basis function k, channel c), given
+// the colour gradient (dr, dg, db) of the view's projected Gaussian, and the
+// direction term of the mean's gradient, dmu.  rw (nullable): the DC colour
+// gradient of this view goes to rw[10..12].
 template <class Sh>
-__device__ __forceinline__ void view_adjoint(const CamK& cam, float3 mu, float3 ls, float4 qr, float o,
-                                             const float4* __restrict__ shp, int sh_degree, float4 ga, float4 gb,
-                                             float4 gc, float* __restrict__ rw, AdjAcc<Sh>& acc) {
-  const float d_x = ga.x, d_y = ga.y, d_a = ga.z, d_b = ga.w, d_c = gb.x, d_o = gb.y;
-  const float drgb[3] = {gb.z, gb.w, gc.x};
-  const float g_o = d_o * o * (1.f - o);
-  acc.o += g_o;
-  if (rw) rw[13] = g_o;
-  // colour
+__device__ __forceinline__ void view_colour(const CamK& cam, float3 mu, const float4* __restrict__ shp,
+                                            int sh_degree, float dr, float dg, float db, float* __restrict__ rw,
+                                            Sh& shacc, float (&dmu)[3]) {
+  const float drgb[3] = {dr, dg, db};
   float vx = mu.x - cam.campos[0], vy = mu.y - cam.campos[1], vz = mu.z - cam.campos[2];
   const float il = rsqrtf(vx * vx + vy * vy + vz * vz);
   const float dx = vx * il, dy = vy * il, dz = vz * il;
@@ -327,11 +325,15 @@ __device__ __forceinline__ void view_adjoint(const CamK& cam, float3 mu, float3 
   float sk[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) sk[k] = 0.f;
+  // an opaque copy of the row pointer: the compiler may not keep the first
+  // pass's 48 values live in registers for this pass
+  const float4* shp2 = shp;
+  asm volatile("" : "+l"(shp2));
 #pragma unroll
   for (int g4 = 0; g4 < 12; g4 += 4) {
     float4 q[4];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) q[r] = shp[g4 + r];
+    for (int r = 0; r < 4; ++r) q[r] = shp2[g4 + r];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const float e[4] = {q[r].x, q[r].y, q[r].z, q[r].w};
@@ -340,7 +342,7 @@ __device__ __forceinline__ void view_adjoint(const CamK& cam, float3 mu, float3 
         const int j = 4 * (g4 + r) + u;
         const bool on = j < 3 * nb;
         if (on) sk[j / 3] += dcv[j % 3] * e[u];
-        acc.sh.add(j, on ? dcv[j % 3] * Y[j / 3] : 0.f);
+        shacc.add(j, on ? dcv[j % 3] * Y[j / 3] : 0.f);
       }
     }
   }
@@ -352,9 +354,18 @@ __device__ __forceinline__ void view_adjoint(const CamK& cam, float3 mu, float3 
   float gd[3];
   sh_basis_grad(dx, dy, dz, sh_degree, sk, gd);
   const float dot = gd[0] * dx + gd[1] * dy + gd[2] * dz;
-  float dmu[3] = {(gd[0] - dx * dot) * il, (gd[1] - dy * dot) * il, (gd[2] - dz * dot) * il};
-  // the geometry after the colour part, so that its state and the SH basis
-  // are not live at the same time
+  dmu[0] = (gd[0] - dx * dot) * il;
+  dmu[1] = (gd[1] - dy * dot) * il;
+  dmu[2] = (gd[2] - dz * dot) * il;
+}
+
+// The geometry part of one view's adjoint, given the gradient (d_x, d_y) of
+// the projected centre and (d_a, d_b, d_c) of the conic: the screen-space
+// term of the mean's gradient dmu, and the gradients of the log-scales dls
+// and the raw quaternion dq.
+__device__ __forceinline__ void view_geometry(const CamK& cam, float3 mu, float3 ls, float4 qr, float d_x,
+                                              float d_y, float d_a, float d_b, float d_c, float (&dmu)[3],
+                                              float (&dls)[3], float (&dq4)[4]) {
   Geo g;
   geometry(cam, mu, ls, qr, g);  // visible by construction (radius > 0)
   // centre
@@ -418,11 +429,7 @@ __device__ __forceinline__ void view_adjoint(const CamK& cam, float3 mu, float3 
     dpc[2] += dJ12 * (cam.fy * lim * iz2);
   }
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    dmu[a] += Wm[a] * dpc[0] + Wm[3 + a] * dpc[1] + Wm[6 + a] * dpc[2];
-    acc.mu[a] += dmu[a];
-    if (rw) rw[a] = dmu[a];
-  }
+  for (int a = 0; a < 3; ++a) dmu[a] = Wm[a] * dpc[0] + Wm[3 + a] * dpc[1] + Wm[6 + a] * dpc[2];
   // Sigma = M M^T, M = R diag(s): dM = 2 dSigma M
   const float* R = g.R;
   float M[9], dM[9];
@@ -439,8 +446,7 @@ __device__ __forceinline__ void view_adjoint(const CamK& cam, float3 mu, float3 
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     const float ds = R[c] * dM[c] + R[3 + c] * dM[3 + c] + R[6 + c] * dM[6 + c];
-    acc.ls[c] += ds * g.s[c];
-    if (rw) rw[3 + c] = ds * g.s[c];
+    dls[c] = ds * g.s[c];
 #pragma unroll
     for (int r = 0; r < 3; ++r) dR[r * 3 + c] = dM[r * 3 + c] * g.s[c];
   }
@@ -457,9 +463,41 @@ __device__ __forceinline__ void view_adjoint(const CamK& cam, float3 mu, float3 
   const float iq = 1.f / g.qnorm;
   const float gq[4] = {(dq[0] - w * qd) * iq, (dq[1] - x * qd) * iq, (dq[2] - y * qd) * iq, (dq[3] - zq * qd) * iq};
 #pragma unroll
+  for (int a = 0; a < 4; ++a) dq4[a] = gq[a];
+}
+
+
+// Adds one view's adjoint of the projection of Gaussian (mu, ls, qr, opacity
+// o, SH block shp) into acc; rw (nullable) receives this view's own gradient
+// row (means, log-scales, quaternion, DC r g b, opacity logit).
+template <class Sh>
+__device__ __forceinline__ void view_adjoint(const CamK& cam, float3 mu, float3 ls, float4 qr, float o,
+                                             const float4* __restrict__ shp, int sh_degree, float4 ga, float4 gb,
+                                             float4 gc, float* __restrict__ rw, AdjAcc<Sh>& acc) {
+  const float g_o = gb.y * o * (1.f - o);
+  acc.o += g_o;
+  if (rw) rw[13] = g_o;
+  float dmu_c[3];
+  view_colour(cam, mu, shp, sh_degree, gb.z, gb.w, gc.x, rw, acc.sh, dmu_c);
+  // the geometry after the colour part, so that its state and the SH basis
+  // are not live at the same time
+  float dmu_g[3], dls[3], dq[4];
+  view_geometry(cam, mu, ls, qr, ga.x, ga.y, ga.z, ga.w, gb.x, dmu_g, dls, dq);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float d = dmu_c[a] + dmu_g[a];
+    acc.mu[a] += d;
+    if (rw) rw[a] = d;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    acc.ls[c] += dls[c];
+    if (rw) rw[3 + c] = dls[c];
+  }
+#pragma unroll
   for (int a = 0; a < 4; ++a) {
-    acc.q[a] += gq[a];
-    if (rw) rw[6 + a] = gq[a];
+    acc.q[a] += dq[a];
+    if (rw) rw[6 + a] = dq[a];
   }
 }
 
@@ -647,63 +685,103 @@ __global__ void __launch_bounds__(kAdjThreads, 4) k_adj_multi(
 // the update of each Gaussian needs only its own gradient), so the gradient
 // never goes to memory.
 //
-// A block takes 128 list entries at a time in two phases.  Phase 1, one
-// thread per Gaussian: the adjoint (SH gradient into a shared-memory column)
-// and the update of the LM blocks and SH float4 0.  Phase 2, the whole block:
-// the Adam update of SH float4s 1..11 of the 128 Gaussians, a quad of lanes
-// on four consecutive float4s of one row (64 contiguous bytes per Gaussian
-// and load), eight Gaussians per warp, every load of a lane issued before its
-// first store.  The column stride kShStride = 130 keeps both phases free of
-// shared-memory bank conflicts (phase 1: bank 2k + t; phase 2: bank
-// 8 kk + g8 + const over the warp's lanes).  Two blocks per SM: the adjoint
-// then fits its registers without spilling (three blocks at 168 registers
-// spilled 356 bytes a thread and measured 80.5 against 76.8 us at the 500k
-// workload).
-constexpr int kShStride = 130;
+// A block of 128 threads takes 64 list entries a round, in two roles of two
+// warps each, so that every Gaussian's adjoint runs as two independent
+// chains of about half the length of the whole.  Colour warps (0, 1): the
+// colour part of each view's adjoint (SH gradient into a shared-memory
+// column, the direction term of the mean's gradient into shared memory),
+// the opacity gradient, and the appearance LM block with SH float4 0.
+// Geometry warps (2, 3): the geometry part (centre, covariance and
+// rotation chain) of the same Gaussians.  After a block barrier the
+// geometry warps add the direction term and update the geometry LM block,
+// and all four warps run the Adam update of SH float4s 1..11 of the 64
+// Gaussians, a quad of lanes on four consecutive float4s of one row (64
+// contiguous bytes per Gaussian and load), eight Gaussians per warp, every
+// load of a lane issued before its first store.  The column stride
+// kShStride = 66 keeps both phases free of shared-memory bank conflicts
+// (colour warps: bank 2k + t; Adam phase: bank 8 kk + g8 + const over the
+// warp's lanes).  128 registers, four blocks per SM.
+constexpr int kUpdG = 64;
+constexpr int kShStride = 66;
 
 template <int MODE>
-__global__ void __launch_bounds__(kAdjThreads, 2) k_adj_update(
+__global__ void __launch_bounds__(kAdjThreads, 4) k_adj_update(
     tgs_param_ptrs P, tgs_param_ptrs M, tgs_param_ptrs V, int64_t n, int sh_degree, MultiAdj mv,
     const uint2* __restrict__ list, const int32_t* __restrict__ count, OptK o) {
   __shared__ float s_sh[48 * kShStride];
-  __shared__ uint32_t s_idx[kAdjThreads];
+  __shared__ float s_dmu[3][kUpdG];
+  __shared__ uint32_t s_idx[kUpdG];
   bias_corrections(o);
   const int cnt = *count;
   const GeoC geo = geo_const(geo_of(P));
   const float4* sh = reinterpret_cast<const float4*>(P.sh);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool colour = warp < 2;
+  const int t = (warp & 1) * 32 + lane;  // the Gaussian's slot in the round
   const int kk = lane >> 3, g8 = lane & 7;
-  for (int b0 = blockIdx.x * kAdjThreads; b0 < cnt; b0 += gridDim.x * kAdjThreads) {
-    const int e = b0 + threadIdx.x;
-    if (e < cnt) {
-      const uint2 it = list[e];
-      const int64_t i = it.x;
-      unsigned hit = it.y;
+  for (int b0 = blockIdx.x * kUpdG; b0 < cnt; b0 += gridDim.x * kUpdG) {
+    const int e = b0 + t;
+    const bool on = e < cnt;
+    const uint2 it = on ? list[e] : make_uint2(0u, 0u);
+    const int64_t i = it.x;
+    unsigned hit = it.y;
+    float gg[10];
+    if (colour) {
+      if (on) {
+        s_idx[t] = it.x;
+        const float3 mu = geo.mean(i);
+        const float o_s = 1.f / (1.f + expf(-geo.opac(i)));
+        SmemSh acc_sh{s_sh + t, kShStride};
+        acc_sh.zero();
+        float og = 0.f, dm[3] = {0.f, 0.f, 0.f};
+        while (hit) {
+          const int v = __ffs(hit) - 1;
+          hit &= hit - 1;
+          const float4* gp = mv.grad2d[v] + 3 * i;
+          const float4 gb = gp[1], gc = gp[2];
+          og += gb.y * o_s * (1.f - o_s);
+          float d[3];
+          view_colour(mv.cam[v], mu, sh + 12 * i, sh_degree, gb.z, gb.w, gc.x, nullptr, acc_sh, d);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) dm[a] += d[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) s_dmu[a][t] = dm[a];
+        const float sg[4] = {acc_sh.get(0), acc_sh.get(1), acc_sh.get(2), acc_sh.get(3)};
+        lm_update_app<MODE>(P, M, V, n, i, sg, og, nullptr, 0, o);
+      }
+    } else if (on) {
       const float3 mu = geo.mean(i);
       const float3 ls = geo.lsc(i);
       const float4 qr = geo.quat(i);
-      const float o_s = 1.f / (1.f + expf(-geo.opac(i)));
-      AdjAcc<SmemSh> acc;
-      acc.sh.base = s_sh + threadIdx.x;
-      acc.sh.stride = kShStride;
-      acc_zero(acc);
+#pragma unroll
+      for (int a = 0; a < 10; ++a) gg[a] = 0.f;
       while (hit) {
         const int v = __ffs(hit) - 1;
         hit &= hit - 1;
         const float4* gp = mv.grad2d[v] + 3 * i;
-        view_adjoint(mv.cam[v], mu, ls, qr, o_s, sh + 12 * i, sh_degree, gp[0], gp[1], gp[2],
-                     mv.row[v] ? mv.row[v] + 14 * i : nullptr, acc);
+        const float4 ga = gp[0];
+        const float d_c = gp[1].x;
+        float dmu[3], dls[3], dq[4];
+        view_geometry(mv.cam[v], mu, ls, qr, ga.x, ga.y, ga.z, ga.w, d_c, dmu, dls, dq);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          gg[a] += dmu[a];
+          gg[3 + a] += dls[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) gg[6 + a] += dq[a];
       }
-      const float gg[10] = {acc.mu[0], acc.mu[1], acc.mu[2], acc.ls[0], acc.ls[1], acc.ls[2],
-                            acc.q[0],  acc.q[1],  acc.q[2],  acc.q[3]};
-      const float sg[4] = {acc.sh.get(0), acc.sh.get(1), acc.sh.get(2), acc.sh.get(3)};
-      lm_update_one<MODE>(P, M, V, n, i, gg, sg, acc.o, nullptr, 0, o);
-      s_idx[threadIdx.x] = it.x;
     }
     __syncthreads();
-    const int ng = min(kAdjThreads, cnt - b0);
+    if (!colour && on) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) gg[a] += s_dmu[a][t];
+      lm_update_geo<MODE>(P, M, V, n, i, gg, nullptr, 0, o);
+    }
+    const int ng = min(kUpdG, cnt - b0);
 #pragma unroll 1
-    for (int pass = 0; pass < kAdjThreads / 32; ++pass) {
+    for (int pass = 0; pass < kUpdG / 32; ++pass) {
       const int gl = 32 * pass + 8 * warp + g8;
       if (gl < ng) {
         const int64_t row = 12 * (int64_t)s_idx[gl];
@@ -735,6 +813,229 @@ __global__ void __launch_bounds__(kAdjThreads, 2) k_adj_update(
           reinterpret_cast<float4*>(V.sh)[row + k4] = vq[r];
         }
       }
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// The fused adjoint + update for geometric fields in 64-byte rows (geo_stride
+// 16, rows on 16-byte boundaries).  The same two roles and the same
+// arithmetic as k_adj_update, but a round first copies the whole rows it
+// needs into shared memory with coalesced asynchronous copies (cp.async):
+// the parameters' and both moments' geometric rows, the parameters' SH rows
+// and the first view's projected-gradient rows, lanes on consecutive 16-byte
+// pieces of a row.  Both roles then read their Gaussian from shared memory,
+// the LM steps update the staged geometric rows in place, and the round ends
+// by writing those rows back whole, again coalesced.  One thread per
+// Gaussian touching its own rows field by field made every warp load and
+// store visit 32 scattered rows, and the L1 pipeline that serves them was the
+// kernel's limit (71 % busy with DRAM at 31 %).  The unused floats of a row
+// (7 and 12..15) are written back with the values read.
+constexpr int kGeoPad = 20;  // floats per staged geometric row: float4 reads by row are conflict-free
+constexpr int kShPad = 52;   // floats per staged SH row
+
+struct __align__(16) AdjRowsSmem {
+  float geo[3][kUpdG][kGeoPad];  // parameters', first and second moments' geometric rows
+  float shp[kUpdG][kShPad];      // the parameters' SH rows
+  float g2d[kUpdG][12];          // the first view's projected-gradient row
+  float sh[48 * kShStride];      // SH gradient columns
+  float dmu[3][kUpdG];           // direction term of the means' gradient
+  uint32_t idx[kUpdG];
+  uint32_t hit[kUpdG];
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(kAdjThreads, 4) k_adj_update_rows(
+    tgs_param_ptrs P, tgs_param_ptrs M, tgs_param_ptrs V, int64_t n, int sh_degree, MultiAdj mv,
+    const uint2* __restrict__ list, const int32_t* __restrict__ count, OptK o) {
+  __shared__ AdjRowsSmem S;
+  bias_corrections(o);
+  const int cnt = *count;
+  const float4* sh = reinterpret_cast<const float4*>(P.sh);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool colour = warp < 2;
+  const int t = (warp & 1) * 32 + lane;  // the Gaussian's slot in the round
+  const int kk = lane >> 3, g8 = lane & 7;
+  for (int b0 = blockIdx.x * kUpdG; b0 < cnt; b0 += gridDim.x * kUpdG) {
+    const int ng = min(kUpdG, cnt - b0);
+    if (threadIdx.x < kUpdG) {
+      const uint2 it = threadIdx.x < ng ? list[b0 + threadIdx.x] : make_uint2(0u, 0u);
+      S.idx[threadIdx.x] = it.x;
+      S.hit[threadIdx.x] = it.y;
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < 12 * ng; p += kAdjThreads) {  // geometric rows: 3 arrays x 4 float4
+      const int a = p / (4 * ng), r = p - a * 4 * ng, g = r >> 2, k = r & 3;
+      const float* base = a == 0 ? P.means : a == 1 ? M.means : V.means;
+      cp_async16(&S.geo[a][g][4 * k], base + 16 * (int64_t)S.idx[g] + 4 * k);
+    }
+    for (int p = threadIdx.x; p < 12 * ng; p += kAdjThreads) {  // SH rows: 12 float4
+      const int g = p / 12, k = p - 12 * g;
+      cp_async16(&S.shp[g][4 * k], sh + 12 * (int64_t)S.idx[g] + k);
+    }
+    for (int p = threadIdx.x; p < 3 * ng; p += kAdjThreads) {  // first view's projected gradient: 3 float4
+      const int g = p / 3, k = p - 3 * g;
+      cp_async16(&S.g2d[g][4 * k], mv.grad2d[__ffs(S.hit[g]) - 1] + 3 * (int64_t)S.idx[g] + k);
+    }
+    cp_async_commit_wait_all();
+    __syncthreads();
+    const bool on = t < ng;
+    const int64_t i = S.idx[t];
+    float gg[10];
+    if (colour) {
+      if (on) {
+        float* pr = S.geo[0][t];
+        const float3 mu = make_float3(pr[0], pr[1], pr[2]);
+        const float o_s = 1.f / (1.f + expf(-pr[6]));
+        SmemSh acc_sh{S.sh + t, kShStride};
+        acc_sh.fresh = true;
+        unsigned hit = S.hit[t];
+        float og = 0.f, dm[3] = {0.f, 0.f, 0.f};
+        while (hit) {
+          const int v = __ffs(hit) - 1;
+          hit &= hit - 1;
+          float4 gb, gc;
+          if (acc_sh.fresh) {
+            gb = *reinterpret_cast<const float4*>(&S.g2d[t][4]);
+            gc = *reinterpret_cast<const float4*>(&S.g2d[t][8]);
+          } else {
+            const float4* gp = mv.grad2d[v] + 3 * i;
+            gb = gp[1];
+            gc = gp[2];
+          }
+          og += gb.y * o_s * (1.f - o_s);
+          float d[3];
+          view_colour(mv.cam[v], mu, reinterpret_cast<const float4*>(S.shp[t]), sh_degree, gb.z, gb.w, gc.x,
+                      nullptr, acc_sh, d);
+          acc_sh.fresh = false;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) dm[a] += d[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a) S.dmu[a][t] = dm[a];
+        const float sg[4] = {acc_sh.get(0), acc_sh.get(1), acc_sh.get(2), acc_sh.get(3)};
+        const float4 p0 = *reinterpret_cast<const float4*>(S.shp[t]);
+        const float4 m0 = reinterpret_cast<const float4*>(M.sh)[12 * i];
+        const float4 v0 = reinterpret_cast<const float4*>(V.sh)[12 * i];
+        float sp[4] = {p0.x, p0.y, p0.z, p0.w};
+        float smm[4] = {m0.x, m0.y, m0.z, m0.w}, sv[4] = {v0.x, v0.y, v0.z, v0.w};
+        float op = pr[6], om = S.geo[1][t][6], ov = S.geo[2][t][6];
+        lm_app_step<MODE>(sg, og, sp, smm, sv, op, om, ov, nullptr, 0, n, i, o);
+        pr[6] = op;
+        S.geo[1][t][6] = om;
+        S.geo[2][t][6] = ov;
+        reinterpret_cast<float4*>(P.sh)[12 * i] = make_float4(sp[0], sp[1], sp[2], sp[3]);
+        reinterpret_cast<float4*>(M.sh)[12 * i] = make_float4(smm[0], smm[1], smm[2], smm[3]);
+        reinterpret_cast<float4*>(V.sh)[12 * i] = make_float4(sv[0], sv[1], sv[2], sv[3]);
+      }
+    } else if (on) {
+      const float* pr = S.geo[0][t];
+      const float3 mu = make_float3(pr[0], pr[1], pr[2]);
+      const float3 ls = make_float3(pr[3], pr[4], pr[5]);
+      const float4 qr = *reinterpret_cast<const float4*>(pr + 8);
+#pragma unroll
+      for (int a = 0; a < 10; ++a) gg[a] = 0.f;
+      unsigned hit = S.hit[t];
+      bool first = true;
+      while (hit) {
+        const int v = __ffs(hit) - 1;
+        hit &= hit - 1;
+        float4 ga;
+        float d_c;
+        if (first) {
+          ga = *reinterpret_cast<const float4*>(&S.g2d[t][0]);
+          d_c = S.g2d[t][4];
+        } else {
+          const float4* gp = mv.grad2d[v] + 3 * i;
+          ga = gp[0];
+          d_c = gp[1].x;
+        }
+        first = false;
+        float dmu[3], dls[3], dq[4];
+        view_geometry(mv.cam[v], mu, ls, qr, ga.x, ga.y, ga.z, ga.w, d_c, dmu, dls, dq);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          gg[a] += dmu[a];
+          gg[3 + a] += dls[a];
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) gg[6 + a] += dq[a];
+      }
+    }
+    __syncthreads();
+    if (!colour && on) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a) gg[a] += S.dmu[a][t];
+      float gp[10], gm[10], gv[10];
+      float* rp = S.geo[0][t];
+      float* rm = S.geo[1][t];
+      float* rv = S.geo[2][t];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        gp[k] = rp[k]; gm[k] = rm[k]; gv[k] = rv[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        gp[6 + k] = rp[8 + k]; gm[6 + k] = rm[8 + k]; gv[6 + k] = rv[8 + k];
+      }
+      lm_geo_step<MODE>(gg, gp, gm, gv, nullptr, 0, n, i, o);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        rp[k] = gp[k]; rm[k] = gm[k]; rv[k] = gv[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        rp[8 + k] = gp[6 + k]; rm[8 + k] = gm[6 + k]; rv[8 + k] = gv[6 + k];
+      }
+    }
+#pragma unroll 1
+    for (int pass = 0; pass < kUpdG / 32; ++pass) {
+      const int gl = 32 * pass + 8 * warp + g8;
+      if (gl < ng) {
+        const int64_t row = 12 * (int64_t)S.idx[gl];
+        float4 pp[3], mq[3], vq[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const int k4 = kk + 4 * r;
+          if (k4 == 0) continue;
+          pp[r] = *reinterpret_cast<const float4*>(&S.shp[gl][4 * k4]);
+          mq[r] = reinterpret_cast<const float4*>(M.sh)[row + k4];
+          vq[r] = reinterpret_cast<const float4*>(V.sh)[row + k4];
+        }
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          const int k4 = kk + 4 * r;
+          if (k4 == 0) continue;
+          const float* c = S.sh + (4 * k4) * kShStride + gl;
+          const float gq[4] = {c[0], c[kShStride], c[2 * kShStride], c[3 * kShStride]};
+          float* p4 = &pp[r].x;
+          float* m4 = &mq[r].x;
+          float* v4 = &vq[r].x;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            moments(gq[u], m4[u], v4[u], o);
+            p4[u] += adam_delta(m4[u], v4[u], o.lr[5], o);
+          }
+          reinterpret_cast<float4*>(P.sh)[row + k4] = pp[r];
+          reinterpret_cast<float4*>(M.sh)[row + k4] = mq[r];
+          reinterpret_cast<float4*>(V.sh)[row + k4] = vq[r];
+        }
+      }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < 12 * ng; p += kAdjThreads) {  // the updated geometric rows, whole
+      const int a = p / (4 * ng), r = p - a * 4 * ng, g = r >> 2, k = r & 3;
+      float* base = a == 0 ? P.means : a == 1 ? M.means : V.means;
+      *reinterpret_cast<float4*>(base + 16 * (int64_t)S.idx[g] + 4 * k) =
+          *reinterpret_cast<const float4*>(&S.geo[a][g][4 * k]);
     }
     __syncthreads();
   }
@@ -827,25 +1128,36 @@ extern "C" tgs_status tgs_project_backward_update(const tgs_param_ptrs* params, 
   cudaMemsetAsync(count, 0, sizeof(int32_t), s);
   // the mark pass writes no gradients (nothing to zero)
   k_adj_mark<<<(int)((g->n + 255) / 256), 256, 0, s>>>(g->n, mv, touched, 0, GeoW{}, nullptr, list, count);
-  static int grid_dev[64][2] = {};
+  // 64-byte geometric rows on 16-byte boundaries in all three: the staged-row kernel
+  const bool rows = params->geo_stride == 16 && m->geo_stride == 16 && v->geo_stride == 16 &&
+                    aligned16(params->means) && aligned16(m->means) && aligned16(v->means);
+  static int grid_dev[64][2][2] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64) return TGS_ERR_DEVICE;
   const int md = opt->mode;
-  if (!grid_dev[dev][md]) {
+  int& gd = grid_dev[dev][md][rows ? 1 : 0];
+  if (!gd) {
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (md == 0) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_update<0>, kAdjThreads, 0);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_adj_update<1>, kAdjThreads, 0);
-    grid_dev[dev][md] = std::max(1, sms * std::max(1, per_sm));
+    const void* fn = rows ? (md == 0 ? (const void*)k_adj_update_rows<0> : (const void*)k_adj_update_rows<1>)
+                          : (md == 0 ? (const void*)k_adj_update<0> : (const void*)k_adj_update<1>);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kAdjThreads, 0);
+    gd = std::max(1, sms * std::max(1, per_sm));
   }
-  const int grid = (int)std::min<int64_t>(grid_dev[dev][md], (g->n + kAdjThreads - 1) / kAdjThreads);
+  const int grid = (int)std::min<int64_t>(gd, (g->n + kUpdG - 1) / kUpdG);
   const tgs_param_ptrs P = *params;
   const OptK o = make_optk(opt, step, step_dev);
-  if (md == 0)
+  if (rows) {
+    if (md == 0)
+      k_adj_update_rows<0><<<grid, kAdjThreads, 0, s>>>(P, *m, *v, g->n, g->sh_degree, mv, list, count, o);
+    else
+      k_adj_update_rows<1><<<grid, kAdjThreads, 0, s>>>(P, *m, *v, g->n, g->sh_degree, mv, list, count, o);
+  } else if (md == 0) {
     k_adj_update<0><<<grid, kAdjThreads, 0, s>>>(P, *m, *v, g->n, g->sh_degree, mv, list, count, o);
-  else
+  } else {
     k_adj_update<1><<<grid, kAdjThreads, 0, s>>>(P, *m, *v, g->n, g->sh_degree, mv, list, count, o);
+  }
   return check_launch();
 }
 
