@@ -892,9 +892,16 @@ __global__ void __launch_bounds__(kAdjThreads, 4) k_adj_update_rows(
     float gg[10];
     if (colour) {
       if (on) {
-        float* pr = S.geo[0][t];
-        const float3 mu = make_float3(pr[0], pr[1], pr[2]);
-        const float o_s = 1.f / (1.f + expf(-pr[6]));
+        // rows are read and written as float4s (0..3: means, log-scale 0;
+        // 4..7: log-scales 1, 2, opacity logit, unused; 8..11: quaternion):
+        // scalar accesses at the 20-float row stride would conflict 4 ways
+        float4* r1p = reinterpret_cast<float4*>(S.geo[0][t]) + 1;
+        float4* r1m = reinterpret_cast<float4*>(S.geo[1][t]) + 1;
+        float4* r1v = reinterpret_cast<float4*>(S.geo[2][t]) + 1;
+        const float4 r0 = *reinterpret_cast<const float4*>(S.geo[0][t]);
+        float4 qp = *r1p, qm = *r1m, qv = *r1v;
+        const float3 mu = make_float3(r0.x, r0.y, r0.z);
+        const float o_s = 1.f / (1.f + expf(-qp.z));
         SmemSh acc_sh{S.sh + t, kShStride};
         acc_sh.fresh = true;
         unsigned hit = S.hit[t];
@@ -927,20 +934,19 @@ __global__ void __launch_bounds__(kAdjThreads, 4) k_adj_update_rows(
         const float4 v0 = reinterpret_cast<const float4*>(V.sh)[12 * i];
         float sp[4] = {p0.x, p0.y, p0.z, p0.w};
         float smm[4] = {m0.x, m0.y, m0.z, m0.w}, sv[4] = {v0.x, v0.y, v0.z, v0.w};
-        float op = pr[6], om = S.geo[1][t][6], ov = S.geo[2][t][6];
-        lm_app_step<MODE>(sg, og, sp, smm, sv, op, om, ov, nullptr, 0, n, i, o);
-        pr[6] = op;
-        S.geo[1][t][6] = om;
-        S.geo[2][t][6] = ov;
+        lm_app_step<MODE>(sg, og, sp, smm, sv, qp.z, qm.z, qv.z, nullptr, 0, n, i, o);
+        *r1p = qp;
+        *r1m = qm;
+        *r1v = qv;
         reinterpret_cast<float4*>(P.sh)[12 * i] = make_float4(sp[0], sp[1], sp[2], sp[3]);
         reinterpret_cast<float4*>(M.sh)[12 * i] = make_float4(smm[0], smm[1], smm[2], smm[3]);
         reinterpret_cast<float4*>(V.sh)[12 * i] = make_float4(sv[0], sv[1], sv[2], sv[3]);
       }
     } else if (on) {
-      const float* pr = S.geo[0][t];
-      const float3 mu = make_float3(pr[0], pr[1], pr[2]);
-      const float3 ls = make_float3(pr[3], pr[4], pr[5]);
-      const float4 qr = *reinterpret_cast<const float4*>(pr + 8);
+      const float4* pr = reinterpret_cast<const float4*>(S.geo[0][t]);
+      const float4 r0 = pr[0], r1 = pr[1], qr = pr[2];
+      const float3 mu = make_float3(r0.x, r0.y, r0.z);
+      const float3 ls = make_float3(r0.w, r1.x, r1.y);
 #pragma unroll
       for (int a = 0; a < 10; ++a) gg[a] = 0.f;
       unsigned hit = S.hit[t];
@@ -975,26 +981,30 @@ __global__ void __launch_bounds__(kAdjThreads, 4) k_adj_update_rows(
 #pragma unroll
       for (int a = 0; a < 3; ++a) gg[a] += S.dmu[a][t];
       float gp[10], gm[10], gv[10];
-      float* rp = S.geo[0][t];
-      float* rm = S.geo[1][t];
-      float* rv = S.geo[2][t];
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        gp[k] = rp[k]; gm[k] = rm[k]; gv[k] = rv[k];
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        gp[6 + k] = rp[8 + k]; gm[6 + k] = rm[8 + k]; gv[6 + k] = rv[8 + k];
-      }
+      float4* rp = reinterpret_cast<float4*>(S.geo[0][t]);
+      float4* rm = reinterpret_cast<float4*>(S.geo[1][t]);
+      float4* rv = reinterpret_cast<float4*>(S.geo[2][t]);
+      auto unpack = [](const float4* r, float (&q)[10]) {
+        const float4 a = r[0], b = r[1], c = r[2];
+        q[0] = a.x; q[1] = a.y; q[2] = a.z; q[3] = a.w; q[4] = b.x; q[5] = b.y;
+        q[6] = c.x; q[7] = c.y; q[8] = c.z; q[9] = c.w;
+      };
+      // float 6 (the opacity logit, written by the colour warps) and 7 are re-read and kept
+      auto pack = [](const float (&q)[10], float4* r) {
+        r[0] = make_float4(q[0], q[1], q[2], q[3]);
+        float4 b = r[1];
+        b.x = q[4];
+        b.y = q[5];
+        r[1] = b;
+        r[2] = make_float4(q[6], q[7], q[8], q[9]);
+      };
+      unpack(rp, gp);
+      unpack(rm, gm);
+      unpack(rv, gv);
       lm_geo_step<MODE>(gg, gp, gm, gv, nullptr, 0, n, i, o);
-#pragma unroll
-      for (int k = 0; k < 6; ++k) {
-        rp[k] = gp[k]; rm[k] = gm[k]; rv[k] = gv[k];
-      }
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        rp[8 + k] = gp[6 + k]; rm[8 + k] = gm[6 + k]; rv[8 + k] = gv[6 + k];
-      }
+      pack(gp, rp);
+      pack(gm, rm);
+      pack(gv, rv);
     }
 #pragma unroll 1
     for (int pass = 0; pass < kUpdG / 32; ++pass) {
