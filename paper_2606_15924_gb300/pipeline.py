@@ -415,13 +415,20 @@ class Trainer:
         return self.stage_graphs
 
     # ------------------------------------------------------------------ maps
-    def init_error_map(self, on_dense=None):
+    def init_error_map(self, on_dense=None, want_loss: bool = True):
         """E_v from a dense evaluation of the current Gaussians (Sec. 3.3):
-        every tile and pixel rendered once, E = e, A = 0.  Returns the loss.
-        on_dense(d) (optional) sees the dense evaluation after its loss."""
-        d = self if self.dense else Trainer(self.params, self.cam, self.target, cfg=self.cfg, dense=True,
-                                            seed=self.seed, bg=self.bg, sh_degree=self.sh_degree, view=self.view,
-                                            train=False)
+        every tile and pixel rendered once, E = e, A = 0.  Returns the loss
+        (None without want_loss: nothing waits for the device).  on_dense(d)
+        (optional) sees the dense evaluation after its loss.  The dense
+        evaluator of a sampled trainer is kept for later refreshes."""
+        if self.dense:
+            d = self
+        else:
+            d = getattr(self, "_dense_eval", None)
+            if d is None or d.n != self.n or d.params["means"].data_ptr() != self.params["means"].data_ptr():
+                d = Trainer(self.params, self.cam, self.target, cfg=self.cfg, dense=True, seed=self.seed,
+                            bg=self.bg, sh_degree=self.sh_degree, view=self.view, train=False)
+                self._dense_eval = d
         d.err_map, d.age_map = self.err_map, self.age_map
         d.forward()
         saved = d.loss_params
@@ -431,7 +438,7 @@ class Trainer:
         if on_dense is not None:
             on_dense(d)
         self.age_map.zero_()
-        return float(d.loss.item())
+        return float(d.loss.item()) if want_loss else None
 
     def render_image(self) -> torch.Tensor:
         """Dense render of the current Gaussians as an [H, W, 3] image (for

@@ -111,7 +111,7 @@ class TileErrorPredictor:
     the network (``assess``)."""
 
     def __init__(self, device="cuda", seed: int = 0, lr: float = 1e-3, max_mse: float = 0.02,
-                 min_batches: int = 50, residual: bool = False, replay: int = 2048):
+                 min_batches: int = 50, residual: bool = False, replay: int = 2048, score_every: int = 1):
         self.mlp = TileErrorMLP(device, seed, lr)
         self.residual = residual
         self.device = device
@@ -120,6 +120,9 @@ class TileErrorPredictor:
         self.batches = 0
         self.recent_mse = None
         self.refreshes = {"predicted": 0, "plain": 0}
+        # the network's error on the step's rows (a host read, so a wait for
+        # the device) is taken every score_every-th batch
+        self.score_every = max(1, int(score_every))
         # replay ring of the latest observations (features as they were, target):
         # each training step runs on all of it, not only on the step's few tiles
         self.replay = int(replay)
@@ -148,13 +151,13 @@ class TileErrorPredictor:
             self.memories[tr.view] = TileMemory(tr.T, self.device)
         return self.memories[tr.view]
 
-    def init_view(self, tr, it: int = 0) -> float:
-        """The plain initial refresh of a view (dense evaluation), also filling
-        its tile memory; returns the loss."""
+    def init_view(self, tr, it: int = 0, want_loss: bool = True):
+        """The plain refresh of a view (dense evaluation), also filling its
+        tile memory; returns the loss (None without want_loss)."""
         mem = self.memory(tr)
         return tr.init_error_map(on_dense=lambda d: B.tile_observe(
             d.active_tiles, d.n_active, d.n_select, d.pix_off, d.ranges, d.T_final, d.err_pix, mem.mem, mem.it,
-            None, it=it))
+            None, it=it), want_loss=want_loss)
 
     def observe_and_train(self, tr, it: int, view_cos: float = 1.0, train: bool = True):
         """The step's active tiles: features from the memory as it was, then the
@@ -173,15 +176,17 @@ class TileErrorPredictor:
                        mem.it, target, it=it, residual=self.residual)
         if not train:
             return
+        score = self.batches % self.score_every == 0
         if self.replay:
-            mse = float(((self.mlp.predict(x) - target) ** 2).mean().item())
+            mse = float(((self.mlp.predict(x) - target) ** 2).mean().item()) if score else None
             self._push(x, target)
             self.mlp.train_step(self.buf_x[:self.buf_n], self.buf_t[:self.buf_n])
         else:
             loss = self.mlp.train_step(x, target, rows_dev=tr.n_active)
-            mse = 2.0 * float(loss.item())
+            mse = 2.0 * float(loss.item()) if score else None
         self.batches += 1
-        self.recent_mse = mse if self.recent_mse is None else 0.9 * self.recent_mse + 0.1 * mse
+        if mse is not None:
+            self.recent_mse = mse if self.recent_mse is None else 0.9 * self.recent_mse + 0.1 * mse
 
     def features(self, tr, it: int, view_cos: float = 1.0) -> torch.Tensor:
         mem = self.memory(tr)
@@ -204,7 +209,7 @@ class TileErrorPredictor:
             B.tile_refresh(self.mlp.predict(x), tr.err_map, tr.W, tr.H, base=x if self.residual else None)
             self.refreshes["predicted"] += 1
             return "predicted"
-        self.init_view(tr, it)
+        self.init_view(tr, it, want_loss=False)
         self.refreshes["plain"] += 1
         return "plain"
 
