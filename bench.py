@@ -870,6 +870,10 @@ def mlp_bench(device, peaks, steps: int = 10, rows: int = MLP_ROWS) -> dict:
         B.mlp_backward_tc(mlp.net(), x, h1, h2, y, t, mlp.grads, mlp.loss, status=status, workspace=ws)
         B.mlp_adam(mlp.params, mlp.grads, mlp.m, mlp.v, 1, 1e-4, 0.9, 0.999, 1e-8, mlp.net())
 
+    def train_fused():
+        B.mlp_train_tc(mlp.net(), x, t, mlp.grads, mlp.loss, status=status)
+        B.mlp_adam(mlp.params, mlp.grads, mlp.m, mlp.v, 1, 1e-4, 0.9, 0.999, 1e-8, mlp.net())
+
     def bwd():
         B.mlp_backward(mlp.net(), x, h1, h2, y, t, mlp.grads, mlp.loss, workspace=ws)
 
@@ -890,6 +894,7 @@ def mlp_bench(device, peaks, steps: int = 10, rows: int = MLP_ROWS) -> dict:
     f_ms, t_ms = timed(fwd), timed(train)
     ftc_ms, itc_ms = timed(fwd_tc), timed(infer_tc)
     b_ms, btc_ms, ttc_ms = timed(bwd), timed(bwd_tc), timed(train_tc)
+    tfu_ms = timed(train_fused)
     flop = 2.0 * R * (16 * 128 + 128 * 128 + 128)
     peak = float(peaks.get("bf16_tflops", 1900.0))
 
@@ -908,7 +913,12 @@ def mlp_bench(device, peaks, steps: int = 10, rows: int = MLP_ROWS) -> dict:
             "train_tc_roofline": {"achieved": 3 * flop / (ttc_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
                                   "frac": 3 * flop / (ttc_ms * 1e-3) / 1e12 / peak,
                                   "note": "tcgen05 forward with stored activations, tcgen05 activation "
-                                          "adjoint, tcgen05 weight gradients, Adam"}}
+                                          "adjoint, tcgen05 weight gradients, Adam"},
+            "train_step_fused_ms": tfu_ms,
+            "train_fused_roofline": {"achieved": 3 * flop / (tfu_ms * 1e-3) / 1e12, "unit": "TFLOP/s",
+                                     "frac": 3 * flop / (tfu_ms * 1e-3) / 1e12 / peak,
+                                     "note": "one tcgen05 kernel: forward recomputed, activation adjoint and "
+                                             "weight gradients with the activations on chip; then Adam"}}
 
 
 def run_quality(args):

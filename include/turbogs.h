@@ -768,6 +768,20 @@ tgs_status tgs_mlp_backward_tc(const tgs_mlp* w, int64_t rows, const int32_t* ro
                                float* grads, double* loss, int32_t* status, void* workspace, size_t workspace_bytes,
                                tgs_stream stream);
 
+/* One training pass on the tcgen05 tensor cores with the forward recomputed
+ * in the same kernel: per 128-row tile the two hidden layers (as
+ * tgs_mlp_forward_tc) and the gradient (as tgs_mlp_backward_tc), with the
+ * activations kept on chip, so neither h1 nor h2 goes to memory.  Writes the
+ * gradient of L = (1/R) sum (y - t)^2 / 2 into grads (packed layout, fp32,
+ * overwritten) and L into *loss (device double); R as in tgs_mlp_backward.
+ * y (nullable, [rows] fp32) receives the forward's outputs; they equal
+ * tgs_mlp_forward_tc's up to the order of the sum over the hidden units.
+ * x, w1 and w2 16-byte aligned.  status (nullable device int32) is set to 1
+ * if a wait for the tensor cores timed out (grads are then incomplete). */
+tgs_status tgs_mlp_train_tc(const tgs_mlp* w, int64_t rows, const int32_t* rows_dev, const float* x,
+                            const float* target, float* y, float* grads, double* loss, int32_t* status,
+                            tgs_stream stream);
+
 /* Adam step on the fp32 master vector (params, m, v: tgs_mlp_param_count()
  * floats) with bias correction at `step` (>= 1); writes the bf16 copies of
  * W1, W2, W3. */

@@ -199,6 +199,8 @@ _lib.tgs_mlp_backward.restype = _i32
 _lib.tgs_mlp_backward.argtypes = [_P(Mlp), _i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]
 _lib.tgs_mlp_backward_tc.restype = _i32
 _lib.tgs_mlp_backward_tc.argtypes = [_P(Mlp), _i64, _p, _p, _p, _p, _p, _p, _p, _p, _p, _p, _sz, _p]
+_lib.tgs_mlp_train_tc.restype = _i32
+_lib.tgs_mlp_train_tc.argtypes = [_P(Mlp), _i64, _p, _p, _p, _p, _p, _p, _p, _p]
 _lib.tgs_tile_observe.restype = _i32
 _lib.tgs_tile_observe.argtypes = [_p, _p, _i32, _p, _p, _p, _p, _u64, _p, _p, _p, _p, _i32, _p]
 _lib.tgs_tile_features.restype = _i32
@@ -223,7 +225,7 @@ EXPORTED = ["tgs_version", "tgs_last_cuda_error", "tgs_status_string", "tgs_devi
             "tgs_render_batched_resident", "tgs_render_sampled_batched",
             "tgs_render_backward_batched", "tgs_render_backward_batched_stats", "tgs_hybrid_step_workspace_size", "tgs_hybrid_step",
             "tgs_mlp_param_count", "tgs_mlp_forward", "tgs_mlp_forward_tc", "tgs_mlp_tc_wait_drill", "tgs_mlp_backward_workspace_size",
-            "tgs_mlp_backward", "tgs_mlp_backward_tc",
+            "tgs_mlp_backward", "tgs_mlp_backward_tc", "tgs_mlp_train_tc",
             "tgs_mlp_adam", "tgs_tile_observe", "tgs_tile_features", "tgs_tile_refresh",
             "tgs_view_error_sums", "tgs_sample_views", "tgs_accumulate_screen_grad",
             "tgs_density_control_workspace_size", "tgs_density_control"]
@@ -671,6 +673,15 @@ def mlp_backward_tc(net: dict, x, h1, h2, y, target, grads, loss, status=None, w
     _check("tgs_mlp_backward_tc", _lib.tgs_mlp_backward_tc(
         C.byref(m), int(x.shape[0]), _ptr(rows_dev), _ptr(x), _ptr(h1), _ptr(h2), _ptr(y), _ptr(target), _ptr(grads),
         _ptr(loss), _ptr(status), _ptr(workspace), workspace.numel(), _stream(stream)))
+
+
+def mlp_train_tc(net: dict, x, target, grads, loss, y=None, status=None, stream=None, rows_dev=None):
+    """The loss's gradient with the forward recomputed in the same tcgen05
+    kernel (no stored activations); y (optional) receives the outputs."""
+    m = mlp_struct(net)
+    _check("tgs_mlp_train_tc", _lib.tgs_mlp_train_tc(
+        C.byref(m), int(x.shape[0]), _ptr(rows_dev), _ptr(x), _ptr(target), _ptr(y), _ptr(grads), _ptr(loss),
+        _ptr(status), _stream(stream)))
 
 
 def mlp_adam(params, grads, m, v, step, lr, beta1, beta2, eps, net: dict, stream=None):

@@ -387,6 +387,9 @@ static int mlp_grid(int64_t R) {
 tgs_status launch_mlp_backward_tc(const tgs_mlp* w, const float* x, const uint16_t* h1, const uint16_t* h2,
                                   const float* y, const float* target, int64_t R, const int32_t* R_dev,
                                   float* grads, double* loss, int32_t* status, cudaStream_t s);
+tgs_status launch_mlp_train_tc(const tgs_mlp* w, const float* x, const float* target, int64_t R,
+                               const int32_t* R_dev, float* y, float* grads, double* loss, int32_t* status,
+                               cudaStream_t s);
 
 }  // namespace tgs
 
@@ -469,6 +472,19 @@ extern "C" tgs_status tgs_mlp_backward_tc(const tgs_mlp* w, int64_t rows, const 
                                           void* workspace, size_t workspace_bytes, tgs_stream stream) {
   return mlp_backward_impl(w, rows, rows_dev, x, h1, h2, y, target, grads, loss, workspace, workspace_bytes, true,
                            status, stream);
+}
+
+extern "C" tgs_status tgs_mlp_train_tc(const tgs_mlp* w, int64_t rows, const int32_t* rows_dev, const float* x,
+                                       const float* target, float* y, float* grads, double* loss, int32_t* status,
+                                       tgs_stream stream) {
+  if (!mlp_ok(w) || rows < 0 || !grads || !loss) return TGS_ERR_INVALID_ARG;
+  if (rows > 0 && (!x || !target || !aligned16(x) || !aligned16(w->w1) || !aligned16(w->w2)))
+    return TGS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaMemsetAsync(grads, 0, sizeof(float) * N_PARAMS, s);
+  cudaMemsetAsync(loss, 0, sizeof(double), s);
+  if (rows == 0) return check_launch();
+  return launch_mlp_train_tc(w, x, target, rows, rows_dev, y, grads, loss, status, s);
 }
 
 extern "C" tgs_status tgs_mlp_adam(float* params, const float* grads, float* m, float* v, int32_t step, float lr,

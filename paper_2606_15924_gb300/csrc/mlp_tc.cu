@@ -560,6 +560,325 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_backward_tc(
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBwTmemCols));
 }
 
+// ---------------------------------------------------------------------------
+// One training pass (the loss's gradient) with the forward recomputed in the
+// same kernel: per 128-row tile, D1 = X W1^T and D2 = H1 W2^T on the tensor
+// cores, h1, h2 and y from them in the epilogues, then the backward above
+// (dH1 = [H1 > 0] (dH2 W2), dW2 | db2 and dW1 | db1 as contractions over the
+// rows).  The activations never leave the SM: the pair of kernels that stores
+// h1 and h2 (512 bytes a row) and reads them back moved about 1.7 GB at the
+// 200-view size.  256 threads, thread t on row t % 128 and hidden units
+// 64 (t / 128) .. + 63; dW3 and db3 (fp32 dy times the bf16 h2, as in the
+// backward above) in registers per thread over the whole pass, reduced once.
+// TMEM: D1, then dH1, in columns 0-127; dW2 | db2 in 128-271; dW1 | db1 in
+// 288-319; D2 in 320-447.  Shared memory: the H1 A tile becomes the dH2 A
+// tile once layer 2 has read it, and the X A tile lies in the dH1^T tile's
+// first 4 KB (read by layer 1 before dH1 is written).  The roundings are the
+// forward's and the backward's: x, h1, h2, dH2 and dH1 in bf16, fp32 sums; y
+// sums its two halves of 64 units and then adds b3.
+constexpr uint32_t FT_W2T = 0;                            // W2^T [128 j][128 k] (B of dH1)
+constexpr uint32_t FT_W2 = FT_W2T + TH * TH * 2;          // W2 [128 n][128 k] (B of layer 2)
+constexpr uint32_t FT_W1 = FT_W2 + TH * TH * 2;           // W1 [128 n][16 k] (B of layer 1)
+constexpr uint32_t FT_HA = FT_W1 + TH * TI * 2;           // H1 [128 r][128 k], then dH2 (A tiles)
+constexpr uint32_t FT_A2 = FT_HA + TM * TH * 2;           // dH2^T (padded)
+constexpr uint32_t FT_B2 = FT_A2 + (TH / 8) * SBO_P;      // [H1^T; 1; 0]
+constexpr uint32_t FT_A1 = FT_B2 + (N2 / 8) * SBO_P;      // dH1^T; X [128 r][16 k] in its first 4 KB
+constexpr uint32_t FT_XA = FT_A1;
+constexpr uint32_t FT_B1 = FT_A1 + (TH / 8) * SBO_P;      // [X^T; 1; 0]
+constexpr uint32_t FT_PAR = FT_B1 + (N1 / 8) * SBO_P;     // b1, b2, w3 (fp32) [128 each], b3, y halves [2][128]
+constexpr uint32_t FT_SMEM = FT_PAR + (3 * TH + 4) * 4 + 2 * TM * 4;
+static_assert(FT_SMEM <= 227 * 1024, "the training pass's tiles fit one CTA's shared memory");
+static_assert(TM * TI * 2 <= (TH / 8) * SBO_P, "the X tile fits in the dH1^T tile");
+constexpr uint32_t kColD2 = 320;
+
+__global__ void __launch_bounds__(kBwThreads, 1) k_mlp_train_tc(
+    TcArgs w, const float* __restrict__ x, const float* __restrict__ tgt, int64_t R,
+    const int32_t* __restrict__ R_dev, float* __restrict__ y_out, float* __restrict__ grads,
+    double* __restrict__ loss, int32_t* __restrict__ status) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_mbar;
+  const int t = threadIdx.x, warp = t >> 5;
+  const int r = t & (TM - 1), hf = t >> 7, u0 = 64 * hf;
+  float* par = reinterpret_cast<float*>(sm + FT_PAR);  // b1 | b2 | w3 | b3 | y halves
+  float* s_yh = par + 3 * TH + 4;
+  for (int i = t; i < TH * (TH / 8); i += kBwThreads) {
+    const int n = i % TH, k8 = (i / TH) * 8;
+    uint32_t q[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      q[e] = (uint32_t)w.w2[(k8 + 2 * e) * TH + n] | ((uint32_t)w.w2[(k8 + 2 * e + 1) * TH + n] << 16);
+    *reinterpret_cast<uint4*>(sm + FT_W2T + core_off(n, k8, SBO_K128)) = make_uint4(q[0], q[1], q[2], q[3]);
+    *reinterpret_cast<uint4*>(sm + FT_W2 + core_off(n, k8, SBO_K128)) =
+        *reinterpret_cast<const uint4*>(w.w2 + n * TH + k8);
+  }
+  for (int i = t; i < TH * (TI / 8); i += kBwThreads) {
+    const int n = i / (TI / 8), k8 = (i % (TI / 8)) * 8;
+    *reinterpret_cast<uint4*>(sm + FT_W1 + core_off(n, k8, SBO_K16)) =
+        *reinterpret_cast<const uint4*>(w.w1 + n * TI + k8);
+  }
+  for (int i = t; i < TH; i += kBwThreads) {
+    par[i] = w.b1[i];
+    par[TH + i] = w.b2[i];
+    par[2 * TH + i] = __uint_as_float((uint32_t)w.w3[i] << 16);
+  }
+  for (int i = t; i < 16 * (TM / 8); i += kBwThreads) {  // the constant rows of the B tiles
+    const int n = i / (TM / 8), k8 = (i % (TM / 8)) * 8;
+    const uint32_t one2 = 0x3F803F80u;
+    const uint4 u = n == 0 ? make_uint4(one2, one2, one2, one2) : make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(sm + FT_B2 + core_off_p(TH + n, k8)) = u;
+    *reinterpret_cast<uint4*>(sm + FT_B1 + core_off_p(TI + n, k8)) = u;
+  }
+  if (t == 0) {
+    par[3 * TH] = w.b3[0];
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(kBwTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  fence_async_smem();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t mbar = smem_u32(&s_mbar);
+  const uint32_t base = smem_u32(sm);
+  const uint32_t lane_addr = (uint32_t)((warp & 3) * 32) << 16;  // TMEM lanes of this warp's rows
+  const int64_t Re = R_dev ? (*R_dev > 0 ? (*R_dev < R ? (int64_t)*R_dev : R) : 0) : R;
+  const float inv = Re > 0 ? 1.f / (float)Re : 0.f;
+  double lsum = 0.0;
+  float w3acc[64];
+#pragma unroll
+  for (int k = 0; k < 64; ++k) w3acc[k] = 0.f;
+  float b3 = 0.f;
+  uint32_t phase = 0;
+  bool failed = false, pending = false, any = false;
+  const int64_t tiles = (R + TM - 1) / TM;
+  auto put_t = [&](uint32_t off, int n, int k, uint32_t bits16) {
+    *reinterpret_cast<uint16_t*>(sm + off + core_off_p(n, k)) = (uint16_t)bits16;
+  };
+  auto mma_wait = [&]() -> bool {  // every thread: the committed MMAs are complete
+    if (__syncthreads_or(!wait_parity(mbar, phase))) return false;
+    phase ^= 1u;
+    fence_after();
+    return true;
+  };
+  // the x row and target of the CTA's next tile, loaded while this one runs
+  float4 XR[TI / 4];
+  float tg = 0.f;
+  auto load_rows = [&](int64_t tl) {
+    const int64_t rw = tl * TM + r;
+    const bool in = tl < tiles && rw < R;
+#pragma unroll
+    for (int k4 = 0; k4 < TI / 4; ++k4)
+      XR[k4] = in && hf == 0 ? *reinterpret_cast<const float4*>(x + rw * TI + 4 * k4) : make_float4(0.f, 0.f, 0.f, 0.f);
+    tg = (tl < tiles && rw < Re) ? tgt[rw] : 0.f;
+  };
+  load_rows(blockIdx.x);
+  for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+    const int64_t row = tile * TM + r;
+    const bool valid = row < R, counted = row < Re;
+    const float tgv = tg;
+    if (hf == 0) {  // the row's 16 features in bf16: X A tile and X^T
+      float xv[TI];
+#pragma unroll
+      for (int k = 0; k < TI; k += 4) {
+        const float4 v = XR[k / 4];
+        xv[k] = v.x; xv[k + 1] = v.y; xv[k + 2] = v.z; xv[k + 3] = v.w;
+      }
+#pragma unroll
+      for (int k8 = 0; k8 < TI; k8 += 8) {
+        const uint32_t p[4] = {pack2(xv[k8], xv[k8 + 1]), pack2(xv[k8 + 2], xv[k8 + 3]),
+                               pack2(xv[k8 + 4], xv[k8 + 5]), pack2(xv[k8 + 6], xv[k8 + 7])};
+        *reinterpret_cast<uint4*>(sm + FT_XA + core_off(r, k8, SBO_K16)) = make_uint4(p[0], p[1], p[2], p[3]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          put_t(FT_B1, k8 + 2 * q, r, p[q] & 0xffffu);
+          put_t(FT_B1, k8 + 2 * q + 1, r, p[q] >> 16);
+        }
+      }
+    }
+    load_rows(tile + gridDim.x);  // in flight during this tile's contractions
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t == 0) {  // layer 1: D1 = X W1^T
+      mma_bf16(tmem, sdesc(base + FT_XA, 128, SBO_K16), sdesc(base + FT_W1, 128, SBO_K16), 0u);
+      commit(mbar);
+    }
+    if (!mma_wait()) {
+      failed = pending = true;
+      break;
+    }
+    // h1 = bf16(relu(D1 + b1)): the H1 A tile, [H1^T; 1; 0] and the mask h1 > 0
+    uint64_t m1 = 0;
+#pragma unroll 1
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + lane_addr + (uint32_t)(u0 + c0), v);
+      uint32_t pk[16];
+#pragma unroll
+      for (int k = 0; k < 32; k += 2)
+        pk[k / 2] = pack2(fmaxf(v[k] + par[u0 + c0 + k], 0.f), fmaxf(v[k + 1] + par[u0 + c0 + k + 1], 0.f));
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(sm + FT_HA + core_off(r, u0 + c0 + 8 * q, SBO_K128)) =
+            make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        put_t(FT_B2, u0 + c0 + 2 * k, r, pk[k] & 0xffffu);
+        put_t(FT_B2, u0 + c0 + 2 * k + 1, r, pk[k] >> 16);
+        if (__uint_as_float(pk[k] << 16) > 0.f) m1 |= 1ull << (c0 + 2 * k);
+        if (__uint_as_float(pk[k] & 0xffff0000u) > 0.f) m1 |= 1ull << (c0 + 2 * k + 1);
+      }
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t == 0) {  // layer 2: D2 = H1 W2^T
+#pragma unroll
+      for (int kk = 0; kk < TH / 16; ++kk)
+        mma_bf16(tmem + kColD2, sdesc(base + FT_HA + kk * 256, 128, SBO_K128),
+                 sdesc(base + FT_W2 + kk * 256, 128, SBO_K128), kk > 0 ? 1u : 0u);
+      commit(mbar);
+    }
+    if (!mma_wait()) {
+      failed = pending = true;
+      break;
+    }
+    // h2 = bf16(relu(D2 + b2)); y = W3 . h2 + b3 from the two halves
+    uint32_t h2p[32];
+    float acc = 0.f;
+#pragma unroll
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + lane_addr + kColD2 + (uint32_t)(u0 + c0), v);
+#pragma unroll
+      for (int k = 0; k < 32; k += 2) {
+        const int c = u0 + c0 + k;
+        const uint32_t pk = pack2(fmaxf(v[k] + par[TH + c], 0.f), fmaxf(v[k + 1] + par[TH + c + 1], 0.f));
+        h2p[(c0 + k) / 2] = pk;
+        acc += __uint_as_float(pk << 16) * par[2 * TH + c] + __uint_as_float(pk & 0xffff0000u) * par[2 * TH + c + 1];
+      }
+    }
+    s_yh[hf * TM + r] = acc;
+    __syncthreads();
+    const float yv = s_yh[r] + s_yh[TM + r] + par[3 * TH];
+    if (y_out && valid && hf == 0) y_out[row] = yv;
+    const float e = counted ? yv - tgv : 0.f;
+    const float d = e * inv;
+    if (hf == 0) {
+      lsum += 0.5 * (double)e * (double)e * (double)inv;
+      b3 += d;
+    }
+    // dH2 = [h2 > 0] d w3 (bf16): the A tile of dH1 (over the H1 tile, which layer 2
+    // has read) and dH2^T; dW3 partials d h2
+#pragma unroll
+    for (int q8 = 0; q8 < 8; ++q8) {
+      uint32_t pk[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int j = 8 * q8 + 2 * q, c = u0 + j;
+        const float lo = __uint_as_float(h2p[j / 2] << 16), hi = __uint_as_float(h2p[j / 2] & 0xffff0000u);
+        pk[q] = pack2(lo > 0.f ? d * par[2 * TH + c] : 0.f, hi > 0.f ? d * par[2 * TH + c + 1] : 0.f);
+        put_t(FT_A2, c, r, pk[q] & 0xffffu);
+        put_t(FT_A2, c + 1, r, pk[q] >> 16);
+        w3acc[j] += d * lo;
+        w3acc[j + 1] += d * hi;
+      }
+      *reinterpret_cast<uint4*>(sm + FT_HA + core_off(r, u0 + 8 * q8, SBO_K128)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t == 0) {  // dH1 (before the mask) = dH2 W2
+#pragma unroll
+      for (int kk = 0; kk < TH / 16; ++kk)
+        mma_bf16(tmem, sdesc(base + FT_HA + kk * 256, 128, SBO_K128), sdesc(base + FT_W2T + kk * 256, 128, SBO_K128),
+                 kk > 0 ? 1u : 0u);
+      commit(mbar);
+    }
+    if (!mma_wait()) {
+      failed = pending = true;
+      break;
+    }
+    // dh1 = bf16([h1 > 0] D), transposed into the A tile of dW1 (over the X tile, which layer 1 has read)
+#pragma unroll 1
+    for (int c0 = 0; c0 < 64; c0 += 32) {
+      float v[32];
+      tmem_ld32(tmem + lane_addr + (uint32_t)(u0 + c0), v);
+#pragma unroll
+      for (int k = 0; k < 32; k += 2) {
+        const uint32_t pk = pack2((m1 >> (c0 + k)) & 1ull ? v[k] : 0.f, (m1 >> (c0 + k + 1)) & 1ull ? v[k + 1] : 0.f);
+        put_t(FT_A1, u0 + c0 + k, r, pk & 0xffffu);
+        put_t(FT_A1, u0 + c0 + k + 1, r, pk >> 16);
+      }
+    }
+    fence_async_smem();
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (t == 0) {  // dW2 | db2 and dW1 | db1, accumulated over the CTA's tiles
+#pragma unroll
+      for (int kk = 0; kk < TM / 16; ++kk) {
+        const uint32_t accu = (any || kk > 0) ? 1u : 0u;
+        mma_bf16_n(tmem + kColW2, sdesc(base + FT_A2 + kk * 2 * LBO_P, LBO_P, SBO_P),
+                   sdesc(base + FT_B2 + kk * 2 * LBO_P, LBO_P, SBO_P), kIdescN2, accu);
+        mma_bf16_n(tmem + kColW1, sdesc(base + FT_A1 + kk * 2 * LBO_P, LBO_P, SBO_P),
+                   sdesc(base + FT_B1 + kk * 2 * LBO_P, LBO_P, SBO_P), kIdescN1, accu);
+      }
+      commit(mbar);
+    }
+    any = true;
+    if (!mma_wait()) {
+      failed = pending = true;
+      break;
+    }
+  }
+  if (failed) {
+    if (t == 0 && status) atomicExch(status, 1);
+    if (pending) wait_parity(mbar, phase);
+  } else if (any) {
+    if (t < TM) {  // row t of the weight-gradient accumulators: hidden unit t
+#pragma unroll 1
+      for (int c0 = 0; c0 < (int)N2; c0 += 32) {
+        float v[32];
+        tmem_ld32(tmem + lane_addr + kColW2 + (uint32_t)c0, v);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+          const int c = c0 + k;
+          if (c < TH) atomicAdd(grads + kOffW2 + t * TH + c, v[k]);
+          else if (c == TH) atomicAdd(grads + kOffB2 + t, v[k]);
+        }
+      }
+      float v[32];
+      tmem_ld32(tmem + lane_addr + kColW1, v);
+#pragma unroll
+      for (int k = 0; k < TI; ++k) atomicAdd(grads + kOffW1 + t * TI + k, v[k]);
+      atomicAdd(grads + kOffB1 + t, v[TI]);
+    }
+    // dW3 and db3: the rows' partials summed over each warp, one atomic per warp and unit
+#pragma unroll
+    for (int k = 0; k < 64; ++k) {
+      const float sum = warp_sum(w3acc[k]);
+      if ((t & 31) == 0) atomicAdd(grads + kOffW3 + u0 + k, sum);
+    }
+    b3 = warp_sum(b3);
+    if ((t & 31) == 0 && hf == 0) atomicAdd(grads + kOffB3, b3);
+  }
+  lsum = warp_sum_d(lsum);
+  if ((t & 31) == 0 && lsum != 0.0) atomicAdd(loss, lsum);
+  fence_before();
+  __syncthreads();
+  fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBwTmemCols));
+}
 }  // namespace
 
 // Launches k_mlp_backward_tc over the rows (one CTA per SM: its shared
@@ -579,6 +898,26 @@ tgs_status launch_mlp_backward_tc(const tgs_mlp* w, const float* x, const uint16
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, device_sm_count()));
   k_mlp_backward_tc<<<grid, kBwThreads, FB_SMEM, s>>>(TcArgs{w->w1, w->w2, w->w3, w->b1, w->b2, w->b3}, x, h1, h2, y,
                                                       target, R, R_dev, grads, loss, status);
+  return check_launch();
+}
+
+// Launches k_mlp_train_tc over the rows (one CTA per SM: its shared memory
+// and 512 TMEM columns).
+tgs_status launch_mlp_train_tc(const tgs_mlp* w, const float* x, const float* target, int64_t R,
+                               const int32_t* R_dev, float* y, float* grads, double* loss, int32_t* status,
+                               cudaStream_t s) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return check_launch();
+  static bool attr[64] = {};
+  if (dev < 0 || dev >= 64) return TGS_ERR_DEVICE;
+  if (!attr[dev]) {
+    cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FT_SMEM);
+    attr[dev] = true;
+  }
+  const int64_t tiles = (R + TM - 1) / TM;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, device_sm_count()));
+  k_mlp_train_tc<<<grid, kBwThreads, FT_SMEM, s>>>(TcArgs{w->w1, w->w2, w->w3, w->b1, w->b2, w->b3}, x, target, R,
+                                                   R_dev, y, grads, loss, status);
   return check_launch();
 }
 

@@ -75,13 +75,8 @@ class TileErrorMLP:
     def train_step(self, x: torch.Tensor, target: torch.Tensor, rows_dev=None) -> torch.Tensor:
         """One Adam step on mean (y - t)^2 / 2 over the first rows_dev rows (all
         when None); returns the loss of the batch before the step (device)."""
-        R = x.shape[0]
-        x = x.contiguous()
-        y = torch.empty(R, device=x.device)
-        h1 = torch.empty(R, HID, dtype=torch.int16, device=x.device)
-        h2 = torch.empty(R, HID, dtype=torch.int16, device=x.device)
-        B.mlp_forward_tc(self.net(), x, y, h1, h2)
-        B.mlp_backward_tc(self.net(), x, h1, h2, y, target.contiguous(), self.grads, self.loss, rows_dev=rows_dev)
+        # forward and gradient in one tensor-core pass (no stored activations)
+        B.mlp_train_tc(self.net(), x.contiguous(), target.contiguous(), self.grads, self.loss, rows_dev=rows_dev)
         self.step_count += 1
         B.mlp_adam(self.params, self.grads, self.m, self.v, self.step_count, self.lr, 0.9, 0.999, 1e-8, self.net())
         return self.loss

@@ -73,7 +73,7 @@ def test_size_queries(B):
     "tgs_select_tiles", "tgs_select_tiles_noalloc", "tgs_project_gaussians", "tgs_bin_tiles", "tgs_render_sampled",
     "tgs_loss_sparse_ncc", "tgs_backward_sampled", "tgs_render_backward_sampled", "tgs_error_stats_sampled",
     "tgs_project_backward", "tgs_project_backward_multi", "tgs_project_backward_update", "tgs_hybrid_step",
-    "tgs_mlp_forward", "tgs_mlp_forward_tc", "tgs_mlp_backward", "tgs_mlp_adam", "tgs_mlp_tc_wait_drill",
+    "tgs_mlp_forward", "tgs_mlp_forward_tc", "tgs_mlp_backward", "tgs_mlp_train_tc", "tgs_mlp_adam", "tgs_mlp_tc_wait_drill",
     "tgs_tile_observe", "tgs_tile_features", "tgs_tile_refresh", "tgs_view_error_sums", "tgs_sample_views",
     "tgs_render_batched_resident", "tgs_advance_counters"])
 def test_null_arguments_are_rejected(B, name):

@@ -92,6 +92,44 @@ def test_backward_parity(P, orc, R, tc):
         assert rel_l2(g[sl[name]], gw[name].reshape(-1)) <= 2e-4, (name, rel_l2(g[sl[name]], gw[name].reshape(-1)))
 
 
+@pytest.mark.parametrize("R,R_dev", [(33, None), (130, None), (2048, None), (5000, None), (5000, 4321)])
+def test_train_pass_parity(P, orc, R, R_dev):
+    """The training pass with the forward recomputed in the same tcgen05 kernel
+    (no stored activations): loss, gradients and outputs against the oracle,
+    the last 128-row tile ragged; R_dev: only the first rows count."""
+    B, TileErrorMLP = P
+    mlp = TileErrorMLP(seed=7)
+    x = _features(R, 11)
+    t = np.random.default_rng(12).normal(size=R).astype(np.float32)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    y = torch.full((R,), float("nan"), device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rd = None if R_dev is None else torch.tensor([R_dev], dtype=torch.int32, device="cuda")
+    B.mlp_train_tc(mlp.net(), xd, td, mlp.grads, mlp.loss, y=y, status=status, rows_dev=rd)
+    assert int(status.item()) == 0
+    Re = R if R_dev is None else R_dev
+    loss, gw = orc.mlp_backward(x[:Re], t[:Re], mlp.weights_fp(), bf16=True)
+    yw = orc.mlp_forward(x, mlp.weights_fp(), bf16=True)[0]
+    got = y.cpu().numpy()
+    # fp32 (tensor memory) against fp64 sums may move an h1 or h2 value across a
+    # bf16 rounding; measured on GB300: 1.15e-4 at 2048 rows of this seed
+    assert rel_l2(got, yw) <= 3e-4
+    # one such flip moves y by about 2^-8 |h| |w3|: a few rows only
+    assert np.mean(np.abs(got - yw) > 1e-3 * max(1.0, np.abs(yw).max())) <= 0.005
+    # the forward kernel's own outputs: the same products, only the order of the
+    # sum over the hidden units differs
+    y_f = torch.empty(R, device="cuda")
+    B.mlp_forward_tc(mlp.net(), xd, y_f, status=status)
+    assert rel_l2(got, y_f.cpu().numpy()) <= 1e-6
+    assert float(mlp.loss.item()) == pytest.approx(loss, rel=2e-5)
+    g = mlp.grads.double().cpu().numpy()
+    sl = mlp._slices()
+    print(f"mlp train pass R={R}: loss rel {abs(float(mlp.loss.item()) - loss) / abs(loss):.3e}, " +
+          ", ".join(f"{k} {rel_l2(g[sl[k]], gw[k].reshape(-1)):.3e}" for k in ("W1", "b1", "W2", "b2", "W3", "b3")))
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3"):
+        assert rel_l2(g[sl[name]], gw[name].reshape(-1)) <= 2e-4, (name, rel_l2(g[sl[name]], gw[name].reshape(-1)))
+
+
 def test_adam_step_and_training(P):
     B, TileErrorMLP = P
     mlp = TileErrorMLP(seed=3, lr=2e-3)
