@@ -839,49 +839,54 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
 // store visit 32 scattered rows, and the L1 pipeline that serves them was the
 // kernel's limit (71 % busy with DRAM at 31 %).  The unused floats of a row
 // (7 and 12..15) are written back with the values read.
+constexpr int kRowsG = 64;  // Gaussians a round of the staged-row kernel (128 threads a block)
 constexpr int kGeoPad = 20;  // floats per staged geometric row: float4 reads by row are conflict-free
 constexpr int kShPad = 52;   // floats per staged SH row
 
+template <int G>
 struct __align__(16) AdjRowsSmem {
-  float geo[3][kUpdG][kGeoPad];  // parameters', first and second moments' geometric rows
-  float shp[kUpdG][kShPad];      // the parameters' SH rows
-  float g2d[kUpdG][12];          // the first view's projected-gradient row
-  float sh[48 * kShStride];      // SH gradient columns
-  float dmu[3][kUpdG];           // direction term of the means' gradient
-  uint32_t idx[kUpdG];
-  uint32_t hit[kUpdG];
+  float geo[3][G][kGeoPad];  // parameters', first and second moments' geometric rows
+  float shp[G][kShPad];      // the parameters' SH rows
+  float g2d[G][12];          // the first view's projected-gradient row
+  float sh[48 * (G + 2)];    // SH gradient columns (stride G + 2 = 2 mod 8: conflict-free)
+  float dmu[3][G];           // direction term of the means' gradient
+  uint32_t idx[G];
+  uint32_t hit[G];
 };
 
-template <int MODE>
-__global__ void __launch_bounds__(kAdjThreads, 4) k_adj_update_rows(
+// G Gaussians a round, 2 G threads (G / 32 colour warps, then as many
+// geometry warps).
+template <int MODE, int G>
+__global__ void __launch_bounds__(2 * G, 256 / G) k_adj_update_rows(
     tgs_param_ptrs P, tgs_param_ptrs M, tgs_param_ptrs V, int64_t n, int sh_degree, MultiAdj mv,
     const uint2* __restrict__ list, const int32_t* __restrict__ count, OptK o) {
-  __shared__ AdjRowsSmem S;
+  constexpr int NT = 2 * G, NW = NT / 32, SS = G + 2;
+  __shared__ AdjRowsSmem<G> S;
   bias_corrections(o);
   const int cnt = *count;
   const float4* sh = reinterpret_cast<const float4*>(P.sh);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool colour = warp < 2;
-  const int t = (warp & 1) * 32 + lane;  // the Gaussian's slot in the round
+  const bool colour = warp < NW / 2;
+  const int t = (warp % (NW / 2)) * 32 + lane;  // the Gaussian's slot in the round
   const int kk = lane >> 3, g8 = lane & 7;
-  for (int b0 = blockIdx.x * kUpdG; b0 < cnt; b0 += gridDim.x * kUpdG) {
-    const int ng = min(kUpdG, cnt - b0);
-    if (threadIdx.x < kUpdG) {
+  for (int b0 = blockIdx.x * G; b0 < cnt; b0 += gridDim.x * G) {
+    const int ng = min(G, cnt - b0);
+    if (threadIdx.x < G) {
       const uint2 it = threadIdx.x < ng ? list[b0 + threadIdx.x] : make_uint2(0u, 0u);
       S.idx[threadIdx.x] = it.x;
       S.hit[threadIdx.x] = it.y;
     }
     __syncthreads();
-    for (int p = threadIdx.x; p < 12 * ng; p += kAdjThreads) {  // geometric rows: 3 arrays x 4 float4
+    for (int p = threadIdx.x; p < 12 * ng; p += NT) {  // geometric rows: 3 arrays x 4 float4
       const int a = p / (4 * ng), r = p - a * 4 * ng, g = r >> 2, k = r & 3;
       const float* base = a == 0 ? P.means : a == 1 ? M.means : V.means;
       cp_async16(&S.geo[a][g][4 * k], base + 16 * (int64_t)S.idx[g] + 4 * k);
     }
-    for (int p = threadIdx.x; p < 12 * ng; p += kAdjThreads) {  // SH rows: 12 float4
+    for (int p = threadIdx.x; p < 12 * ng; p += NT) {  // SH rows: 12 float4
       const int g = p / 12, k = p - 12 * g;
       cp_async16(&S.shp[g][4 * k], sh + 12 * (int64_t)S.idx[g] + k);
     }
-    for (int p = threadIdx.x; p < 3 * ng; p += kAdjThreads) {  // first view's projected gradient: 3 float4
+    for (int p = threadIdx.x; p < 3 * ng; p += NT) {  // first view's projected gradient: 3 float4
       const int g = p / 3, k = p - 3 * g;
       cp_async16(&S.g2d[g][4 * k], mv.grad2d[__ffs(S.hit[g]) - 1] + 3 * (int64_t)S.idx[g] + k);
     }
@@ -902,7 +907,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4) k_adj_update_rows(
         float4 qp = *r1p, qm = *r1m, qv = *r1v;
         const float3 mu = make_float3(r0.x, r0.y, r0.z);
         const float o_s = 1.f / (1.f + expf(-qp.z));
-        SmemSh acc_sh{S.sh + t, kShStride};
+        SmemSh acc_sh{S.sh + t, SS};
         acc_sh.fresh = true;
         unsigned hit = S.hit[t];
         float og = 0.f, dm[3] = {0.f, 0.f, 0.f};
@@ -1007,8 +1012,8 @@ __global__ void __launch_bounds__(kAdjThreads, 4) k_adj_update_rows(
       pack(gv, rv);
     }
 #pragma unroll 1
-    for (int pass = 0; pass < kUpdG / 32; ++pass) {
-      const int gl = 32 * pass + 8 * warp + g8;
+    for (int pass = 0; pass < G / (8 * NW); ++pass) {
+      const int gl = 8 * NW * pass + 8 * warp + g8;
       if (gl < ng) {
         const int64_t row = 12 * (int64_t)S.idx[gl];
         float4 pp[3], mq[3], vq[3];
@@ -1024,8 +1029,8 @@ __global__ void __launch_bounds__(kAdjThreads, 4) k_adj_update_rows(
         for (int r = 0; r < 3; ++r) {
           const int k4 = kk + 4 * r;
           if (k4 == 0) continue;
-          const float* c = S.sh + (4 * k4) * kShStride + gl;
-          const float gq[4] = {c[0], c[kShStride], c[2 * kShStride], c[3 * kShStride]};
+          const float* c = S.sh + (4 * k4) * SS + gl;
+          const float gq[4] = {c[0], c[SS], c[2 * SS], c[3 * SS]};
           float* p4 = &pp[r].x;
           float* m4 = &mq[r].x;
           float* v4 = &vq[r].x;
@@ -1041,7 +1046,7 @@ __global__ void __launch_bounds__(kAdjThreads, 4) k_adj_update_rows(
       }
     }
     __syncthreads();
-    for (int p = threadIdx.x; p < 12 * ng; p += kAdjThreads) {  // the updated geometric rows, whole
+    for (int p = threadIdx.x; p < 12 * ng; p += NT) {  // the updated geometric rows, whole
       const int a = p / (4 * ng), r = p - a * 4 * ng, g = r >> 2, k = r & 3;
       float* base = a == 0 ? P.means : a == 1 ? M.means : V.means;
       *reinterpret_cast<float4*>(base + 16 * (int64_t)S.idx[g] + 4 * k) =
@@ -1150,19 +1155,20 @@ extern "C" tgs_status tgs_project_backward_update(const tgs_param_ptrs* params, 
   if (!gd) {
     int sms = 0, per_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const void* fn = rows ? (md == 0 ? (const void*)k_adj_update_rows<0> : (const void*)k_adj_update_rows<1>)
+    const void* fn = rows ? (md == 0 ? (const void*)k_adj_update_rows<0, kRowsG> : (const void*)k_adj_update_rows<1, kRowsG>)
                           : (md == 0 ? (const void*)k_adj_update<0> : (const void*)k_adj_update<1>);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kAdjThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, rows ? 2 * kRowsG : kAdjThreads, 0);
     gd = std::max(1, sms * std::max(1, per_sm));
   }
-  const int grid = (int)std::min<int64_t>(gd, (g->n + kUpdG - 1) / kUpdG);
+  const int per_round = rows ? kRowsG : kUpdG;
+  const int grid = (int)std::min<int64_t>(gd, (g->n + per_round - 1) / per_round);
   const tgs_param_ptrs P = *params;
   const OptK o = make_optk(opt, step, step_dev);
   if (rows) {
     if (md == 0)
-      k_adj_update_rows<0><<<grid, kAdjThreads, 0, s>>>(P, *m, *v, g->n, g->sh_degree, mv, list, count, o);
+      k_adj_update_rows<0, kRowsG><<<grid, 2 * kRowsG, 0, s>>>(P, *m, *v, g->n, g->sh_degree, mv, list, count, o);
     else
-      k_adj_update_rows<1><<<grid, kAdjThreads, 0, s>>>(P, *m, *v, g->n, g->sh_degree, mv, list, count, o);
+      k_adj_update_rows<1, kRowsG><<<grid, 2 * kRowsG, 0, s>>>(P, *m, *v, g->n, g->sh_degree, mv, list, count, o);
   } else if (md == 0) {
     k_adj_update<0><<<grid, kAdjThreads, 0, s>>>(P, *m, *v, g->n, g->sh_degree, mv, list, count, o);
   } else {
