@@ -290,21 +290,30 @@ class Trainer:
         for k, v in sel.items():
             setattr(self, k, v)
 
-    def step_overlapped(self, nxt: dict):
+    def step_overlapped(self, nxt: dict, target_host=None):
         """One iteration on the selection already made for it, and the next
         iteration's selection (Alg. 1 step 3) into the buffers nxt.  The next
         selection needs only the error and age maps the loss has just written
         and the iteration counter, so it runs on a second stream beside the
-        backward and the update, which touch neither."""
+        backward and the update, which touch neither.  target_host (pinned
+        host memory): the view's target is first copied in on a third stream,
+        beside the projection, binning and render, which do not read it; the
+        loss waits for it."""
+        main = torch.cuda.current_stream()
+        if target_host is not None:
+            self._copy.wait_stream(main)
+            with torch.cuda.stream(self._copy):
+                self.target.copy_(target_host, non_blocking=True)
         B.project_gaussians(self.params, self.ccam, self.tile_rank, self.proj, self.sh_degree)
         B.bin_tiles(self.proj, self.n, self.ccam, self.tile_rank, self.n_select, self.ws_bin, self.capacity,
                     self.vals, None, self.ranges, self.n_isect)
         B.render_sampled(self.proj, self.ranges, self.vals, self.active_tiles, self.n_active, self.n_select,
                          self.pix_off, self.pix_idx, self.n_pix, self.ccam, self.bg, self.rgb, self.T_final,
                          self.n_last, ckpt=self.ckpt)
+        if target_host is not None:
+            main.wait_stream(self._copy)
         self.loss_and_maps()
         B.advance_counters(self.it_dev, None)        # the next iteration's number
-        main = torch.cuda.current_stream()
         self._side.wait_stream(main)
         cur = self._selection()
         with torch.cuda.stream(self._side):
@@ -320,14 +329,16 @@ class Trainer:
         B.advance_counters(None, self.step_dev)
         main.wait_stream(self._side)
 
-    def capture(self, overlap: bool = False):
+    def capture(self, overlap: bool = False, target_host=None):
         """Capture one step in a CUDA graph (after a warm-up step).  With
         overlap, two graphs that alternate between two sets of selection
         buffers: each runs its iteration on one set and makes the next
         iteration's selection in the other, beside its backward and update
         (``step_overlapped``); ``replay`` alternates them.  The results are
         those of the plain step: the same selections, from the same maps and
-        counters."""
+        counters.  With overlap and target_host (a pinned host copy of the
+        target), a second pair of graphs whose steps also copy the target in
+        from the host (``replay(with_copy=True)``)."""
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
@@ -344,18 +355,24 @@ class Trainer:
             torch.cuda.synchronize()
             return self.graph
         self._side = torch.cuda.Stream()
+        self._copy = torch.cuda.Stream()
         sets = [self._selection(), {k: torch.empty_like(v) for k, v in self._selection().items()}]
         self._select()                                  # the first replayed iteration's selection, in set 0
         torch.cuda.synchronize()
-        self.graphs = []
-        for k in range(2):
-            self._use_selection(sets[k])
-            g = torch.cuda.CUDAGraph(keep_graph=True)
-            with torch.cuda.graph(g):
-                self.step_overlapped(sets[1 - k])
-            self.graphs.append(g)
+
+        def pair(host):
+            out = []
+            for k in range(2):
+                self._use_selection(sets[k])
+                g = torch.cuda.CUDAGraph(keep_graph=True)
+                with torch.cuda.graph(g):
+                    self.step_overlapped(sets[1 - k], host)
+                out.append(g)
+            return out
+        self.graphs = pair(None)
+        self.graphs_copy = pair(target_host) if target_host is not None else None
         self.kernels_per_step = B.graph_count_kernels(self.graphs[0])
-        for g in self.graphs:
+        for g in self.graphs + (self.graphs_copy or []):
             g.instantiate()
         self._sets, self._phase = sets, 0
         self._use_selection(sets[0])
@@ -363,16 +380,18 @@ class Trainer:
         torch.cuda.synchronize()
         return self.graph
 
-    def replay(self):
+    def replay(self, with_copy: bool = False):
         """One captured iteration.  With overlap, the selection attributes
         then name the buffers that iteration used (its rgb, n_last, ... go with
-        them), and the next selection is already in the other set."""
+        them), and the next selection is already in the other set.  with_copy:
+        the iteration that first copies the target in from the host (captured
+        with target_host)."""
         if not getattr(self, "overlap", False):
             self.graph.replay()
             return
         k = self._phase
         self._use_selection(self._sets[k])
-        self.graphs[k].replay()
+        (self.graphs_copy if with_copy else self.graphs)[k].replay()
         self._phase = 1 - k
 
     def next_selection(self) -> dict:

@@ -83,3 +83,28 @@ def test_overlapped_training_follows_the_plain_step(B):
     # the render backward may order differently
     np.testing.assert_allclose(a[:5], b[:5], rtol=1e-4)
     assert b[-1] < b[0] and abs(a[-1] - b[-1]) <= 0.02 * a[-1]
+
+
+def test_step_that_copies_its_target_in(B):
+    """capture(overlap=True, target_host=...): each replayed step copies the
+    target in from pinned host memory on its own stream (the loss waits for
+    it).  With the device target cleared first, training must follow the step
+    whose target is already on the device."""
+    runs = []
+    for copy in (False, True):
+        tr, _ = _trainer(seed=7)
+        host = tr.target.detach().cpu().pin_memory()
+        tr.capture(overlap=True, target_host=host if copy else None)
+        if copy:
+            tr.target.zero_()
+        ls = []
+        for _ in range(12):
+            tr.replay(with_copy=copy)
+            ls.append(tr.loss.clone())
+        torch.cuda.synchronize()
+        runs.append([float(x.item()) for x in ls])
+        if copy:
+            assert torch.equal(tr.target.cpu(), host)
+    a, b = (np.array(x) for x in runs)
+    np.testing.assert_allclose(a[:4], b[:4], rtol=1e-4)
+    assert abs(a[-1] - b[-1]) <= 0.02 * a[-1]
