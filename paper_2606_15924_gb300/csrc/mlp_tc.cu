@@ -571,24 +571,36 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_backward_tc(
 // 64 (t / 128) .. + 63; dW3 and db3 (fp32 dy times the bf16 h2, as in the
 // backward above) in registers per thread over the whole pass, reduced once.
 // TMEM: D1, then dH1, in columns 0-127; dW2 | db2 in 128-271; dW1 | db1 in
-// 288-319; D2 in 320-447.  Shared memory: the H1 A tile becomes the dH2 A
-// tile once layer 2 has read it, and the X A tile lies in the dH1^T tile's
-// first 4 KB (read by layer 1 before dH1 is written).  The roundings are the
+// 288-319; D2 in 320-447.  Shared memory holds each operand once, as rows
+// (bf16 X, H1, dH2 and dH1 of the tile's 128 rows): the forward's
+// contractions read them K-major, the weight gradients (contractions over the
+// rows) MN-major through the same core matrices, so no operand is copied
+// transposed; X and H1 carry a column of ones for the bias gradients.  The roundings are the
 // forward's and the backward's: x, h1, h2, dH2 and dH1 in bf16, fp32 sums; y
 // sums its two halves of 64 units and then adds b3.
 constexpr uint32_t FT_W2T = 0;                            // W2^T [128 j][128 k] (B of dH1)
 constexpr uint32_t FT_W2 = FT_W2T + TH * TH * 2;          // W2 [128 n][128 k] (B of layer 2)
 constexpr uint32_t FT_W1 = FT_W2 + TH * TH * 2;           // W1 [128 n][16 k] (B of layer 1)
-constexpr uint32_t FT_HA = FT_W1 + TH * TI * 2;           // H1 [128 r][128 k], then dH2 (A tiles)
-constexpr uint32_t FT_A2 = FT_HA + TM * TH * 2;           // dH2^T (padded)
-constexpr uint32_t FT_B2 = FT_A2 + (TH / 8) * SBO_P;      // [H1^T; 1; 0]
-constexpr uint32_t FT_A1 = FT_B2 + (N2 / 8) * SBO_P;      // dH1^T; X [128 r][16 k] in its first 4 KB
-constexpr uint32_t FT_XA = FT_A1;
-constexpr uint32_t FT_B1 = FT_A1 + (TH / 8) * SBO_P;      // [X^T; 1; 0]
-constexpr uint32_t FT_PAR = FT_B1 + (N1 / 8) * SBO_P;     // b1, b2, w3 (fp32) [128 each], b3, y halves [2][128]
+// Row tiles, rows r of the 128-row tile in 8-row core-matrix groups (core_off):
+// read K-major (rows = M) by the forward's contractions and MN-major (rows =
+// K) by the weight gradients, so nothing is copied transposed.
+constexpr uint32_t XW = 32, HW = TH + 16;                 // widths: 16 features | 1 | 15 zeros; 128 units | 1 | 15 zeros
+constexpr uint32_t SBO_X = (XW / 8) * 128, SBO_H = (HW / 8) * 128;
+constexpr uint32_t FT_X = FT_W1 + TH * TI * 2;            // [X | 1 | 0]   [128 r][32]: A of layer 1, B of dW1
+constexpr uint32_t FT_H1 = FT_X + TM * XW * 2;            // [H1 | 1 | 0]  [128 r][144]: A of layer 2, B of dW2
+constexpr uint32_t FT_DH2 = FT_H1 + TM * HW * 2;          // dH2 [128 r][128]: A of dH1 and of dW2
+constexpr uint32_t FT_DH1 = FT_DH2 + TM * TH * 2;         // dH1 [128 r][128]: A of dW1
+constexpr uint32_t FT_PAR = FT_DH1 + TM * TH * 2;         // b1, b2, w3 (fp32) [128 each], b3, y halves [2][128]
 constexpr uint32_t FT_SMEM = FT_PAR + (3 * TH + 4) * 4 + 2 * TM * 4;
-static_assert(FT_SMEM <= 227 * 1024, "the training pass's tiles fit one CTA's shared memory");
-static_assert(TM * TI * 2 <= (TH / 8) * SBO_P, "the X tile fits in the dH1^T tile");
+static_assert(FT_SMEM <= 227 * 1024 && 2 * FT_SMEM > 228 * 1024,
+              "the training pass's tiles fit one CTA's shared memory, and only one CTA an SM (512 TMEM columns)");
+// requested: more than the tiles use, so that every operand the contractions
+// address, read with either stride order, lies inside the CTA's allocation
+constexpr uint32_t FT_SMEM_REQ = 225 * 1024;
+static_assert(FT_SMEM <= FT_SMEM_REQ, "request covers the layout");
+// the weight-gradient contractions read both operands MN-major (transpose bits 15, 16)
+constexpr uint32_t kIdescN2T = kIdescN2 | (1u << 15) | (1u << 16);
+constexpr uint32_t kIdescN1T = kIdescN1 | (1u << 15) | (1u << 16);
 constexpr uint32_t kColD2 = 320;
 
 __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_train_tc(
@@ -622,12 +634,12 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_train_tc(
     par[TH + i] = w.b2[i];
     par[2 * TH + i] = __uint_as_float((uint32_t)w.w3[i] << 16);
   }
-  for (int i = t; i < 16 * (TM / 8); i += kBwThreads) {  // the constant rows of the B tiles
-    const int n = i / (TM / 8), k8 = (i % (TM / 8)) * 8;
-    const uint32_t one2 = 0x3F803F80u;
-    const uint4 u = n == 0 ? make_uint4(one2, one2, one2, one2) : make_uint4(0u, 0u, 0u, 0u);
-    *reinterpret_cast<uint4*>(sm + FT_B2 + core_off_p(TH + n, k8)) = u;
-    *reinterpret_cast<uint4*>(sm + FT_B1 + core_off_p(TI + n, k8)) = u;
+  for (int r = t; r < TM; r += kBwThreads) {  // the constant columns: a one, then zeros (the bias gradients)
+    const uint4 one = make_uint4(0x3F80u, 0u, 0u, 0u), zero = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(sm + FT_X + core_off(r, TI, SBO_X)) = one;
+    *reinterpret_cast<uint4*>(sm + FT_X + core_off(r, TI + 8, SBO_X)) = zero;
+    *reinterpret_cast<uint4*>(sm + FT_H1 + core_off(r, TH, SBO_H)) = one;
+    *reinterpret_cast<uint4*>(sm + FT_H1 + core_off(r, TH + 8, SBO_H)) = zero;
   }
   if (t == 0) {
     par[3 * TH] = w.b3[0];
@@ -657,9 +669,6 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_train_tc(
   uint32_t phase = 0;
   bool failed = false, pending = false, any = false;
   const int64_t tiles = (R + TM - 1) / TM;
-  auto put_t = [&](uint32_t off, int n, int k, uint32_t bits16) {
-    *reinterpret_cast<uint16_t*>(sm + off + core_off_p(n, k)) = (uint16_t)bits16;
-  };
   auto mma_wait = [&]() -> bool {  // every thread: the committed MMAs are complete
     if (__syncthreads_or(!wait_parity(mbar, phase))) return false;
     phase ^= 1u;
@@ -693,12 +702,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_train_tc(
       for (int k8 = 0; k8 < TI; k8 += 8) {
         const uint32_t p[4] = {pack2(xv[k8], xv[k8 + 1]), pack2(xv[k8 + 2], xv[k8 + 3]),
                                pack2(xv[k8 + 4], xv[k8 + 5]), pack2(xv[k8 + 6], xv[k8 + 7])};
-        *reinterpret_cast<uint4*>(sm + FT_XA + core_off(r, k8, SBO_K16)) = make_uint4(p[0], p[1], p[2], p[3]);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          put_t(FT_B1, k8 + 2 * q, r, p[q] & 0xffffu);
-          put_t(FT_B1, k8 + 2 * q + 1, r, p[q] >> 16);
-        }
+        *reinterpret_cast<uint4*>(sm + FT_X + core_off(r, k8, SBO_X)) = make_uint4(p[0], p[1], p[2], p[3]);
       }
     }
     load_rows(tile + gridDim.x);  // in flight during this tile's contractions
@@ -707,7 +711,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_train_tc(
     __syncthreads();
     fence_after();
     if (t == 0) {  // layer 1: D1 = X W1^T
-      mma_bf16(tmem, sdesc(base + FT_XA, 128, SBO_K16), sdesc(base + FT_W1, 128, SBO_K16), 0u);
+      mma_bf16(tmem, sdesc(base + FT_X, 128, SBO_X), sdesc(base + FT_W1, 128, SBO_K16), 0u);
       commit(mbar);
     }
     if (!mma_wait()) {
@@ -726,12 +730,10 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_train_tc(
         pk[k / 2] = pack2(fmaxf(v[k] + par[u0 + c0 + k], 0.f), fmaxf(v[k + 1] + par[u0 + c0 + k + 1], 0.f));
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        *reinterpret_cast<uint4*>(sm + FT_HA + core_off(r, u0 + c0 + 8 * q, SBO_K128)) =
+        *reinterpret_cast<uint4*>(sm + FT_H1 + core_off(r, u0 + c0 + 8 * q, SBO_H)) =
             make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        put_t(FT_B2, u0 + c0 + 2 * k, r, pk[k] & 0xffffu);
-        put_t(FT_B2, u0 + c0 + 2 * k + 1, r, pk[k] >> 16);
         if (__uint_as_float(pk[k] << 16) > 0.f) m1 |= 1ull << (c0 + 2 * k);
         if (__uint_as_float(pk[k] & 0xffff0000u) > 0.f) m1 |= 1ull << (c0 + 2 * k + 1);
       }
@@ -743,7 +745,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_train_tc(
     if (t == 0) {  // layer 2: D2 = H1 W2^T
 #pragma unroll
       for (int kk = 0; kk < TH / 16; ++kk)
-        mma_bf16(tmem + kColD2, sdesc(base + FT_HA + kk * 256, 128, SBO_K128),
+        mma_bf16(tmem + kColD2, sdesc(base + FT_H1 + kk * 256, 128, SBO_H),
                  sdesc(base + FT_W2 + kk * 256, 128, SBO_K128), kk > 0 ? 1u : 0u);
       commit(mbar);
     }
@@ -786,12 +788,10 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_train_tc(
         const int j = 8 * q8 + 2 * q, c = u0 + j;
         const float lo = __uint_as_float(h2p[j / 2] << 16), hi = __uint_as_float(h2p[j / 2] & 0xffff0000u);
         pk[q] = pack2(lo > 0.f ? d * par[2 * TH + c] : 0.f, hi > 0.f ? d * par[2 * TH + c + 1] : 0.f);
-        put_t(FT_A2, c, r, pk[q] & 0xffffu);
-        put_t(FT_A2, c + 1, r, pk[q] >> 16);
         w3acc[j] += d * lo;
         w3acc[j + 1] += d * hi;
       }
-      *reinterpret_cast<uint4*>(sm + FT_HA + core_off(r, u0 + 8 * q8, SBO_K128)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      *reinterpret_cast<uint4*>(sm + FT_DH2 + core_off(r, u0 + 8 * q8, SBO_K128)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
     }
     fence_async_smem();
     fence_before();
@@ -800,7 +800,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_train_tc(
     if (t == 0) {  // dH1 (before the mask) = dH2 W2
 #pragma unroll
       for (int kk = 0; kk < TH / 16; ++kk)
-        mma_bf16(tmem, sdesc(base + FT_HA + kk * 256, 128, SBO_K128), sdesc(base + FT_W2T + kk * 256, 128, SBO_K128),
+        mma_bf16(tmem, sdesc(base + FT_DH2 + kk * 256, 128, SBO_K128), sdesc(base + FT_W2T + kk * 256, 128, SBO_K128),
                  kk > 0 ? 1u : 0u);
       commit(mbar);
     }
@@ -813,12 +813,14 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_train_tc(
     for (int c0 = 0; c0 < 64; c0 += 32) {
       float v[32];
       tmem_ld32(tmem + lane_addr + (uint32_t)(u0 + c0), v);
+      uint32_t pk[16];
 #pragma unroll
-      for (int k = 0; k < 32; k += 2) {
-        const uint32_t pk = pack2((m1 >> (c0 + k)) & 1ull ? v[k] : 0.f, (m1 >> (c0 + k + 1)) & 1ull ? v[k + 1] : 0.f);
-        put_t(FT_A1, u0 + c0 + k, r, pk & 0xffffu);
-        put_t(FT_A1, u0 + c0 + k + 1, r, pk >> 16);
-      }
+      for (int k = 0; k < 32; k += 2)
+        pk[k / 2] = pack2((m1 >> (c0 + k)) & 1ull ? v[k] : 0.f, (m1 >> (c0 + k + 1)) & 1ull ? v[k + 1] : 0.f);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(sm + FT_DH1 + core_off(r, u0 + c0 + 8 * q, SBO_K128)) =
+            make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
     }
     fence_async_smem();
     fence_before();
@@ -828,10 +830,11 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_train_tc(
 #pragma unroll
       for (int kk = 0; kk < TM / 16; ++kk) {
         const uint32_t accu = (any || kk > 0) ? 1u : 0u;
-        mma_bf16_n(tmem + kColW2, sdesc(base + FT_A2 + kk * 2 * LBO_P, LBO_P, SBO_P),
-                   sdesc(base + FT_B2 + kk * 2 * LBO_P, LBO_P, SBO_P), kIdescN2, accu);
-        mma_bf16_n(tmem + kColW1, sdesc(base + FT_A1 + kk * 2 * LBO_P, LBO_P, SBO_P),
-                   sdesc(base + FT_B1 + kk * 2 * LBO_P, LBO_P, SBO_P), kIdescN1, accu);
+        // MN-major: LBO steps along K (the rows, 8 at a time), SBO along M / N (8 units)
+        mma_bf16_n(tmem + kColW2, sdesc(base + FT_DH2 + kk * 2 * SBO_K128, SBO_K128, 128),
+                   sdesc(base + FT_H1 + kk * 2 * SBO_H, SBO_H, 128), kIdescN2T, accu);
+        mma_bf16_n(tmem + kColW1, sdesc(base + FT_DH1 + kk * 2 * SBO_K128, SBO_K128, 128),
+                   sdesc(base + FT_X + kk * 2 * SBO_X, SBO_X, 128), kIdescN1T, accu);
       }
       commit(mbar);
     }
@@ -911,12 +914,12 @@ tgs_status launch_mlp_train_tc(const tgs_mlp* w, const float* x, const float* ta
   static bool attr[64] = {};
   if (dev < 0 || dev >= 64) return TGS_ERR_DEVICE;
   if (!attr[dev]) {
-    cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FT_SMEM);
+    cudaFuncSetAttribute(k_mlp_train_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FT_SMEM_REQ);
     attr[dev] = true;
   }
   const int64_t tiles = (R + TM - 1) / TM;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, device_sm_count()));
-  k_mlp_train_tc<<<grid, kBwThreads, FT_SMEM, s>>>(TcArgs{w->w1, w->w2, w->w3, w->b1, w->b2, w->b3}, x, target, R,
+  k_mlp_train_tc<<<grid, kBwThreads, FT_SMEM_REQ, s>>>(TcArgs{w->w1, w->w2, w->w3, w->b1, w->b2, w->b3}, x, target, R,
                                                    R_dev, y, grads, loss, status);
   return check_launch();
 }
