@@ -298,20 +298,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_mlp_forward_tc(TcArgs w, cons
 //   dW1 [128 j][16 i]  += dH1^T X,    db1 [j] += sum_r dH1 [r][j],
 // with M = 128 hidden units, K = 128 rows and N = 144 (128 units, a column
 // of ones for the bias, 15 zero columns) or N = 32 (16 features, ones, 15
-// zeros).  The operands are transposes of the rows, in K-major tiles whose
-// core matrices along K are 144 bytes apart (16 bytes of padding), so that
-// the 2-byte stores of the eight lanes of a phase (eight consecutive rows)
-// hit eight different bank groups.
-constexpr uint32_t LBO_P = 144;                 // core matrices along K (padded)
-constexpr uint32_t SBO_P = 16 * LBO_P;          // 8-row groups (K = 128)
+// zeros).  The operands are the row tiles themselves, read MN-major: a core
+// matrix of a row tile (8 rows x 8 consecutive units or features) is, for a
+// contraction over the rows, 8 K-rows x 8 contiguous M (or N) values.
 constexpr uint32_t N2 = TH + 16, N1 = 32;       // B widths: units + ones + zeros, features + ones + zeros
 // instruction descriptors of the two contractions (as kIdesc, N = N2 and N1)
 constexpr uint32_t kIdescN2 = (1u << 4) | (1u << 7) | (1u << 10) | ((N2 >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 constexpr uint32_t kIdescN1 = (1u << 4) | (1u << 7) | (1u << 10) | ((N1 >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 
-__device__ __forceinline__ uint32_t core_off_p(int n, int k) {
-  return (uint32_t)(n >> 3) * SBO_P + (uint32_t)(k >> 3) * LBO_P + (uint32_t)(n & 7) * 16u + (uint32_t)(k & 7) * 2u;
-}
+// Row tiles, rows r of the 128-row tile in 8-row core-matrix groups (core_off):
+// read K-major (rows = M) by the forward's contractions and MN-major (rows =
+// K) by the weight gradients, so nothing is copied transposed.
+constexpr uint32_t XW = 32, HW = TH + 16;                 // widths: 16 features | 1 | 15 zeros; 128 units | 1 | 15 zeros
+constexpr uint32_t SBO_X = (XW / 8) * 128, SBO_H = (HW / 8) * 128;
+// the weight-gradient contractions read both operands MN-major (transpose bits 15, 16)
+constexpr uint32_t kIdescN2T = kIdescN2 | (1u << 15) | (1u << 16);
+constexpr uint32_t kIdescN1T = kIdescN1 | (1u << 15) | (1u << 16);
 
 __device__ __forceinline__ void mma_bf16_n(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                            uint32_t accumulate) {
@@ -327,26 +329,28 @@ __device__ __forceinline__ void mma_bf16_n(uint32_t d_tmem, uint64_t a, uint64_t
 // backwards) and the weight gradients above, with dH2 and dH1 kept in shared
 // memory, so the rows are read once and no adjoint goes to memory; dW3 and
 // db3 (fp32 dy, not a bf16 operand) on the CUDA cores.  256 threads: thread t takes row t % 128
-// and hidden units 64 (t / 128) .. + 63.  dH2 is written twice, as the
-// row-major A tile of dH1 = dH2 W2 and (transposed, 2-byte stores whose eight
-// lanes of a phase hit distinct banks through the padded core matrices) as
-// the A tile of dW2; H1 and X likewise go transposed into the B tiles of the
-// weight gradients.  TMEM: dH1 in columns 0-127, dW2 | db2 in 128-271, dW1 |
+// and hidden units 64 (t / 128) .. + 63.  dH2, H1, dH1 and X are written once
+// each, as row tiles: dH2 is the A operand of dH1 = dH2 W2 (K-major) and of
+// dW2 (MN-major); H1, dH1 and X are read MN-major by the weight gradients.
+// TMEM: dH1 in columns 0-127, dW2 | db2 in 128-271, dW1 |
 // db1 in 288-319.  The roundings and products are those of the mma.sync and
 // CUDA-core backward: dH2 and dH1 rounded to bf16, bf16 x bf16 products with
 // fp32 sums, x rounded to bf16.
 constexpr int kBwThreads = 256;
 constexpr uint32_t FB_W2T = 0;                            // W2^T [128 j][128 k] (B of dH1)
-constexpr uint32_t FB_DA = FB_W2T + TH * TH * 2;          // dH2 [128 r][128 k] (A of dH1)
-constexpr uint32_t FB_A2 = FB_DA + TM * TH * 2;           // dH2^T (padded)
-constexpr uint32_t FB_B2 = FB_A2 + (TH / 8) * SBO_P;      // [H1^T; 1; 0]
-constexpr uint32_t FB_A1 = FB_B2 + (N2 / 8) * SBO_P;      // dH1^T
-constexpr uint32_t FB_B1 = FB_A1 + (TH / 8) * SBO_P;      // [X^T; 1; 0]
-constexpr uint32_t FB_H2 = FB_B1 + (N1 / 8) * SBO_P;      // h2 rows (bf16), for dW3
+constexpr uint32_t FB_DA = FB_W2T + TH * TH * 2;          // dH2 [128 r][128 k]: A of dH1 (K-major) and of dW2 (MN-major)
+constexpr uint32_t FB_H1 = FB_DA + TM * TH * 2;           // [H1 | 1 | 0] [128 r][144]: B of dW2 (MN-major)
+constexpr uint32_t FB_DH1 = FB_H1 + TM * HW * 2;          // dH1 [128 r][128]: A of dW1 (MN-major)
+constexpr uint32_t FB_X = FB_DH1 + TM * TH * 2;           // [X | 1 | 0] [128 r][32]: B of dW1 (MN-major)
+constexpr uint32_t FB_H2 = FB_X + TM * XW * 2;            // h2 rows (bf16), for dW3
 constexpr uint32_t FB_DY = FB_H2 + TM * TH * 2;           // dy [128]
 constexpr uint32_t FB_W3 = FB_DY + TM * 4;                // w3 (fp32) [128]
 constexpr uint32_t FB_SMEM = FB_W3 + TH * 4;
-static_assert(FB_SMEM <= 227 * 1024, "the fused backward's tiles fit one CTA's shared memory");
+// requested: more than the tiles use, so that every operand the contractions
+// address, read with either stride order, lies inside the CTA's allocation
+constexpr uint32_t FB_SMEM_REQ = 225 * 1024;
+static_assert(FB_SMEM <= FB_SMEM_REQ && FB_SMEM_REQ <= 227 * 1024,
+              "the fused backward's tiles fit one CTA's shared memory");
 constexpr uint32_t kBwTmemCols = 512;
 constexpr uint32_t kColW2 = 128, kColW1 = 288;
 
@@ -371,12 +375,12 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_backward_tc(
     *reinterpret_cast<uint4*>(sm + FB_W2T + core_off(n, k8, SBO_K128)) = make_uint4(q[0], q[1], q[2], q[3]);
   }
   for (int i = t; i < TH; i += kBwThreads) w3f[i] = __uint_as_float((uint32_t)w.w3[i] << 16);
-  for (int i = t; i < 16 * (TM / 8); i += kBwThreads) {  // the constant rows of the B tiles
-    const int n = i / (TM / 8), k8 = (i % (TM / 8)) * 8;
-    const uint32_t one2 = 0x3F803F80u;
-    const uint4 u = n == 0 ? make_uint4(one2, one2, one2, one2) : make_uint4(0u, 0u, 0u, 0u);
-    *reinterpret_cast<uint4*>(sm + FB_B2 + core_off_p(TH + n, k8)) = u;
-    *reinterpret_cast<uint4*>(sm + FB_B1 + core_off_p(TI + n, k8)) = u;
+  for (int rr = t; rr < TM; rr += kBwThreads) {  // the constant columns: a one, then zeros (the bias gradients)
+    const uint4 one = make_uint4(0x3F80u, 0u, 0u, 0u), zero = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(sm + FB_X + core_off(rr, TI, SBO_X)) = one;
+    *reinterpret_cast<uint4*>(sm + FB_X + core_off(rr, TI + 8, SBO_X)) = zero;
+    *reinterpret_cast<uint4*>(sm + FB_H1 + core_off(rr, TH, SBO_H)) = one;
+    *reinterpret_cast<uint4*>(sm + FB_H1 + core_off(rr, TH + 8, SBO_H)) = zero;
   }
   if (t == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_mbar)));
@@ -402,9 +406,6 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_backward_tc(
   uint32_t phase = 0;
   bool failed = false, pending = false, any = false;
   const int64_t tiles = (R + TM - 1) / TM;
-  auto put_t = [&](uint32_t off, int n, int k, uint32_t bits16) {  // 2-byte store into a padded K-major tile
-    *reinterpret_cast<uint16_t*>(sm + off + core_off_p(n, k)) = (uint16_t)bits16;
-  };
   // The half rows of h2 and h1 (and the row's error) are loaded in one round,
   // and those of the CTA's next tile are issued as soon as the current ones are
   // staged, so they arrive while the tensor cores run (a loop that waited for
@@ -444,26 +445,20 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_backward_tc(
         const float v0 = __uint_as_float(a2[q] << 16) > 0.f ? d * w3f[c8 + 2 * q] : 0.f;
         const float v1 = __uint_as_float(a2[q] & 0xffff0000u) > 0.f ? d * w3f[c8 + 2 * q + 1] : 0.f;
         pk[q] = pack2(v0, v1);
-        put_t(FB_A2, c8 + 2 * q, r, pk[q] & 0xffffu);
-        put_t(FB_A2, c8 + 2 * q + 1, r, pk[q] >> 16);
-        put_t(FB_B2, c8 + 2 * q, r, a1[q] & 0xffffu);
-        put_t(FB_B2, c8 + 2 * q + 1, r, a1[q] >> 16);
         const int bit = c8 - u0 + 2 * q;
         if (__uint_as_float(a1[q] << 16) > 0.f) m1 |= 1ull << bit;
         if (__uint_as_float(a1[q] & 0xffff0000u) > 0.f) m1 |= 1ull << (bit + 1);
       }
       *reinterpret_cast<uint4*>(sm + FB_DA + core_off(r, c8, SBO_K128)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+      *reinterpret_cast<uint4*>(sm + FB_H1 + core_off(r, c8, SBO_H)) = g1;
       *reinterpret_cast<uint4*>(sm + FB_H2 + (uint32_t)(r * TH + c8) * 2u) = g2;
     }
-    if (hf == 0) {  // X^T: the row's 16 features, rounded to bf16
+    if (hf == 0) {  // the row's 16 features, rounded to bf16
 #pragma unroll
-      for (int k4 = 0; k4 < TI; k4 += 4) {
-        const float4 v = XR[k4 / 4];
-        const uint32_t p0 = pack2(v.x, v.y), p1 = pack2(v.z, v.w);
-        put_t(FB_B1, k4, r, p0 & 0xffffu);
-        put_t(FB_B1, k4 + 1, r, p0 >> 16);
-        put_t(FB_B1, k4 + 2, r, p1 & 0xffffu);
-        put_t(FB_B1, k4 + 3, r, p1 >> 16);
+      for (int k8 = 0; k8 < TI; k8 += 8) {
+        const float4 a = XR[k8 / 4], b = XR[k8 / 4 + 1];
+        *reinterpret_cast<uint4*>(sm + FB_X + core_off(r, k8, SBO_X)) =
+            make_uint4(pack2(a.x, a.y), pack2(a.z, a.w), pack2(b.x, b.y), pack2(b.z, b.w));
       }
     }
     load_rows(tile + gridDim.x);  // the next tile's rows, in flight during this tile's contractions
@@ -492,17 +487,19 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_backward_tc(
     }
     phase ^= 1u;
     fence_after();
-    // dh1 = bf16([h1 > 0] D), transposed into the A tile of dW1
+    // dh1 = bf16([h1 > 0] D): the row tile of dW1's A
 #pragma unroll 1
     for (int c0 = 0; c0 < 64; c0 += 32) {
       float v[32];
       tmem_ld32(tmem + lane_addr + (uint32_t)(u0 + c0), v);
+      uint32_t pk[16];
 #pragma unroll
-      for (int k = 0; k < 32; k += 2) {
-        const uint32_t pk = pack2((m1 >> (c0 + k)) & 1ull ? v[k] : 0.f, (m1 >> (c0 + k + 1)) & 1ull ? v[k + 1] : 0.f);
-        put_t(FB_A1, u0 + c0 + k, r, pk & 0xffffu);
-        put_t(FB_A1, u0 + c0 + k + 1, r, pk >> 16);
-      }
+      for (int k = 0; k < 32; k += 2)
+        pk[k / 2] = pack2((m1 >> (c0 + k)) & 1ull ? v[k] : 0.f, (m1 >> (c0 + k + 1)) & 1ull ? v[k + 1] : 0.f);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        *reinterpret_cast<uint4*>(sm + FB_DH1 + core_off(r, u0 + c0 + 8 * q, SBO_K128)) =
+            make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
     }
     fence_async_smem();
     fence_before();
@@ -512,10 +509,11 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_backward_tc(
 #pragma unroll
       for (int kk = 0; kk < TM / 16; ++kk) {
         const uint32_t acc = (any || kk > 0) ? 1u : 0u;
-        mma_bf16_n(tmem + kColW2, sdesc(base + FB_A2 + kk * 2 * LBO_P, LBO_P, SBO_P),
-                   sdesc(base + FB_B2 + kk * 2 * LBO_P, LBO_P, SBO_P), kIdescN2, acc);
-        mma_bf16_n(tmem + kColW1, sdesc(base + FB_A1 + kk * 2 * LBO_P, LBO_P, SBO_P),
-                   sdesc(base + FB_B1 + kk * 2 * LBO_P, LBO_P, SBO_P), kIdescN1, acc);
+        // MN-major: LBO steps along K (the rows, 8 at a time), SBO along M / N (8 units)
+        mma_bf16_n(tmem + kColW2, sdesc(base + FB_DA + kk * 2 * SBO_K128, SBO_K128, 128),
+                   sdesc(base + FB_H1 + kk * 2 * SBO_H, SBO_H, 128), kIdescN2T, acc);
+        mma_bf16_n(tmem + kColW1, sdesc(base + FB_DH1 + kk * 2 * SBO_K128, SBO_K128, 128),
+                   sdesc(base + FB_X + kk * 2 * SBO_X, SBO_X, 128), kIdescN1T, acc);
       }
       commit(mbar);
     }
@@ -581,11 +579,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_backward_tc(
 constexpr uint32_t FT_W2T = 0;                            // W2^T [128 j][128 k] (B of dH1)
 constexpr uint32_t FT_W2 = FT_W2T + TH * TH * 2;          // W2 [128 n][128 k] (B of layer 2)
 constexpr uint32_t FT_W1 = FT_W2 + TH * TH * 2;           // W1 [128 n][16 k] (B of layer 1)
-// Row tiles, rows r of the 128-row tile in 8-row core-matrix groups (core_off):
-// read K-major (rows = M) by the forward's contractions and MN-major (rows =
-// K) by the weight gradients, so nothing is copied transposed.
-constexpr uint32_t XW = 32, HW = TH + 16;                 // widths: 16 features | 1 | 15 zeros; 128 units | 1 | 15 zeros
-constexpr uint32_t SBO_X = (XW / 8) * 128, SBO_H = (HW / 8) * 128;
+// the row tiles (XW, HW, SBO_X, SBO_H above)
 constexpr uint32_t FT_X = FT_W1 + TH * TI * 2;            // [X | 1 | 0]   [128 r][32]: A of layer 1, B of dW1
 constexpr uint32_t FT_H1 = FT_X + TM * XW * 2;            // [H1 | 1 | 0]  [128 r][144]: A of layer 2, B of dW2
 constexpr uint32_t FT_DH2 = FT_H1 + TM * HW * 2;          // dH2 [128 r][128]: A of dH1 and of dW2
@@ -598,9 +592,6 @@ static_assert(FT_SMEM <= 227 * 1024 && 2 * FT_SMEM > 228 * 1024,
 // address, read with either stride order, lies inside the CTA's allocation
 constexpr uint32_t FT_SMEM_REQ = 225 * 1024;
 static_assert(FT_SMEM <= FT_SMEM_REQ, "request covers the layout");
-// the weight-gradient contractions read both operands MN-major (transpose bits 15, 16)
-constexpr uint32_t kIdescN2T = kIdescN2 | (1u << 15) | (1u << 16);
-constexpr uint32_t kIdescN1T = kIdescN1 | (1u << 15) | (1u << 16);
 constexpr uint32_t kColD2 = 320;
 
 __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_train_tc(
@@ -894,12 +885,12 @@ tgs_status launch_mlp_backward_tc(const tgs_mlp* w, const float* x, const uint16
   static bool attr[64] = {};
   if (dev < 0 || dev >= 64) return TGS_ERR_DEVICE;
   if (!attr[dev]) {
-    cudaFuncSetAttribute(k_mlp_backward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FB_SMEM);
+    cudaFuncSetAttribute(k_mlp_backward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FB_SMEM_REQ);
     attr[dev] = true;
   }
   const int64_t tiles = (R + TM - 1) / TM;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, device_sm_count()));
-  k_mlp_backward_tc<<<grid, kBwThreads, FB_SMEM, s>>>(TcArgs{w->w1, w->w2, w->w3, w->b1, w->b2, w->b3}, x, h1, h2, y,
+  k_mlp_backward_tc<<<grid, kBwThreads, FB_SMEM_REQ, s>>>(TcArgs{w->w1, w->w2, w->w3, w->b1, w->b2, w->b3}, x, h1, h2, y,
                                                       target, R, R_dev, grads, loss, status);
   return check_launch();
 }
