@@ -29,11 +29,15 @@ constexpr int kSortThreads = 256;
 constexpr int kSortSmem = 4096;  // keys sorted in shared memory (32 KB)
 
 constexpr int kHistBlocks = 1216;         // at most 8 chunks per SM in the count/scatter passes
-constexpr int kHistChunk = 2048;          // Gaussians per chunk below that
+constexpr int kHistChunk = 1536;          // Gaussians per chunk below that (before the rounding to SM waves)
 constexpr int kHistMaxRanks = 49152;      // shared-memory table limit (192 KB)
 
+// Chunks of about kHistChunk Gaussians, rounded up to whole waves of the SMs
+// (every SM then holds the same number of chunks).
 static int hist_blocks(int64_t n) {
-  return (int)std::max<int64_t>(1, std::min<int64_t>(kHistBlocks, (n + kHistChunk - 1) / kHistChunk));
+  const int64_t c = (n + kHistChunk - 1) / kHistChunk;
+  const int64_t sms = std::max(1, device_sm_count());
+  return (int)std::max<int64_t>(1, std::min<int64_t>(kHistBlocks, (c + sms - 1) / sms * sms));
 }
 
 struct BinWs {
