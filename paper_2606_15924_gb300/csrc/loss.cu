@@ -74,6 +74,10 @@ __global__ void k_loss(LossArgs a) {
       y[c] = a.target[3 * pix + c];
     }
   }
+  // the pixel's error-map entry, read now so that the load overlaps the
+  // block reductions (the barriers between would otherwise hold it back)
+  uint16_t old_err = 0;
+  if (on && a.err_map) old_err = a.err_map[pix];
   if (n <= 0) return;  // uniform per block
   const float inv_n = 1.f / (float)n;
   // pass 1: means
@@ -151,7 +155,7 @@ __global__ void k_loss(LossArgs a) {
     for (int c = 0; c < 3; ++c) a.dL[3 * (size_t)s + c] = (d1[c] * invP - cn * dn[c]) * a.weight;
     a.err_pix[s] = e;
     if (a.err_map) {
-      const float old = __half2float(__ushort_as_half(a.err_map[pix]));
+      const float old = __half2float(__ushort_as_half(old_err));
       a.err_map[pix] = __half_as_ushort(__float2half_rn((1.f - a.beta) * old + a.beta * e));
     }
     if (a.age_map) a.age_map[pix] = 0;
