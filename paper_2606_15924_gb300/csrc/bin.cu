@@ -645,9 +645,13 @@ extern "C" tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const 
   BinWs w = carve_bin(workspace, n, capacity, n_active_max, &tot);
   BinGeom geo{tiles_x(cam->width), tiles_y(cam->height), n_active_max};
   const int R = n_active_max;
-  if (R > 0) cudaMemsetAsync(tile_ranges, 0, sizeof(int2) * (size_t)R, s);
-  cudaMemsetAsync(n_isect, 0, sizeof(int64_t), s);
-  if (n == 0 || R == 0) return check_launch();
+  // the scan writes n_isect and the per-rank sort writes every range; they
+  // are cleared here only where those kernels do not run
+  if (n == 0 || R == 0) {
+    if (R > 0) cudaMemsetAsync(tile_ranges, 0, sizeof(int2) * (size_t)R, s);
+    cudaMemsetAsync(n_isect, 0, sizeof(int64_t), s);
+    return check_launch();
+  }
   const float2* xy = reinterpret_cast<const float2*>(proj->xy);
   RangeSrc src{};
   // Per-chunk histograms in shared memory and an offset table, while the
@@ -722,7 +726,10 @@ extern "C" tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const 
     src.start = w.tile_start;
     src.cnt = w.tile_cnt;
   }
-  if (capacity == 0) return check_launch();
+  if (capacity == 0) {
+    cudaMemsetAsync(tile_ranges, 0, sizeof(int2) * (size_t)R, s);
+    return check_launch();
+  }
   if (shared_path) {
     k_hist_scatter<<<G, kHistThreads, smem, s>>>(xy, proj->radius, proj->depth, order, n_vis, n, geo, tile_rank,
                                                  w.table, presort ? nullptr : w.tile_start, w.keys, capacity);

@@ -168,9 +168,11 @@ __global__ void k_loss(LossArgs a) {
   }
 }
 
-// A <- min(A + 1, 65535) on every pixel, eight at a time.
-__global__ void k_age_inc(uint16_t* __restrict__ age, int64_t n) {
+// A <- min(A + 1, 65535) on every pixel, eight at a time; the first thread
+// also clears the loss accumulator the loss kernel adds to next.
+__global__ void k_age_inc(uint16_t* __restrict__ age, int64_t n, double* __restrict__ loss) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0) *loss = 0.0;
   const int64_t n8 = n / 8;
   if (i < n8) {
     uint4 v = reinterpret_cast<uint4*>(age)[i];
@@ -203,11 +205,12 @@ static tgs_status loss_impl(int structure, const float* rgb, const float* target
       !(params->beta <= 1.f))
     return TGS_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaMemsetAsync(loss, 0, sizeof(double), s);
   if (age_map) {
     const int64_t n = (int64_t)width * height;
     const int64_t threads = n / 8 + (n % 8);
-    k_age_inc<<<(int)((threads + 255) / 256), 256, 0, s>>>(age_map, n);
+    k_age_inc<<<(int)((threads + 255) / 256), 256, 0, s>>>(age_map, n, loss);
+  } else {
+    cudaMemsetAsync(loss, 0, sizeof(double), s);
   }
   if (n_active_max > 0) {
     LossArgs a;
