@@ -313,10 +313,12 @@ class Trainer:
         if target_host is not None:
             main.wait_stream(self._copy)
         self.loss_and_maps()
-        B.advance_counters(self.it_dev, None)        # the next iteration's number
         self._side.wait_stream(main)
         cur = self._selection()
         with torch.cuda.stream(self._side):
+            # the next iteration's number, then its selection: off the main
+            # stream, whose backward and update do not read the counter
+            B.advance_counters(self.it_dev, None)
             self._use_selection(nxt)
             self._select()
         self._use_selection(cur)
