@@ -230,6 +230,10 @@ __global__ void __launch_bounds__(kHistThreads) k_hist_count(const float2* __res
 // 3'. shared-memory path: scatter with shared cursors that start at the
 // block's offsets table[r * G + b] (clamped to the capacity; positions at or
 // past the capacity are dropped).
+// With rank_cnt (the ranks' totals, reserve mode): every block first takes
+// the exclusive prefix of the totals itself (R values, from L2), the ranks'
+// starts; block 0 also writes them to rank_start and their sum to n_total for
+// the sort that follows.  This replaces a separate scan launch.
 __global__ void __launch_bounds__(kHistThreads) k_hist_scatter(const float2* __restrict__ xy,
                                                                const int32_t* __restrict__ radius,
                                                                const float* __restrict__ depth,
@@ -237,15 +241,35 @@ __global__ void __launch_bounds__(kHistThreads) k_hist_scatter(const float2* __r
                                                                const int32_t* __restrict__ n_vis, int64_t n,
                                                                BinGeom geo, const int32_t* __restrict__ tile_rank,
                                                                const int64_t* __restrict__ table,
-                                                               const int64_t* __restrict__ rank_start,
+                                                               int64_t* __restrict__ rank_start,
+                                                               const int32_t* __restrict__ rank_cnt,
+                                                               int64_t* __restrict__ n_total,
                                                                uint64_t* __restrict__ keys, int64_t cap) {
   extern __shared__ uint32_t sh[];
+  __shared__ int64_t s_wt[32];
   const int R = geo.n_ranks, G = gridDim.x, b = blockIdx.x;
-  // the table holds absolute offsets, or (rank_start given) offsets within
-  // each rank's list; entries of ranks the block has no pair in are not read
-  // back as positions
-  for (int r = threadIdx.x; r < R; r += blockDim.x)
-    sh[r] = (uint32_t)min(table[(size_t)r * G + b] + (rank_start ? rank_start[r] : 0), cap);
+  if (rank_cnt) {
+    // thread t scans the contiguous run [t * per, (t + 1) * per) of the totals
+    const int per = (R + (int)blockDim.x - 1) / (int)blockDim.x;
+    const int r0 = (int)threadIdx.x * per, r1 = min(R, r0 + per);
+    int64_t run = 0;
+    for (int r = r0; r < r1; ++r) run += rank_cnt[r];
+    int64_t total;
+    int64_t pre = block_exclusive_scan<int64_t>(run, s_wt, total);
+    for (int r = r0; r < r1; ++r) {
+      const int64_t c = rank_cnt[r];
+      if (b == 0) rank_start[r] = pre;
+      sh[r] = (uint32_t)min(table[(size_t)r * G + b] + pre, cap);
+      pre += c;
+    }
+    if (b == 0 && threadIdx.x == 0) *n_total = total;
+  } else {
+    // the table holds absolute offsets, or (rank_start given) offsets within
+    // each rank's list; entries of ranks the block has no pair in are not read
+    // back as positions
+    for (int r = threadIdx.x; r < R; r += blockDim.x)
+      sh[r] = (uint32_t)min(table[(size_t)r * G + b] + (rank_start ? rank_start[r] : 0), cap);
+  }
   __syncthreads();
   int64_t i0, i1;
   vis_chunk(n_vis, n, i0, i1);
@@ -701,15 +725,10 @@ extern "C" tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const 
       src.total = n_isect;
     } else {
       // lists are sorted whole afterwards: blocks reserve their runs with
-      // per-rank atomics, and only the R rank totals are scanned
+      // per-rank atomics; the scatter scans the R rank totals itself
       cudaMemsetAsync(w.tile_cnt, 0, sizeof(int32_t) * (size_t)R, s);
       k_hist_count<<<G, kHistThreads, smem, s>>>(xy, proj->radius, order, n_vis, n, geo, tile_rank, w.table,
                                                  w.tile_cnt);
-      const int32_t* cnt = w.tile_cnt;
-      int64_t* start = w.tile_start;
-      auto load = [=] __device__(int64_t r) -> int64_t { return cnt[r]; };
-      auto store = [=] __device__(int64_t r, int64_t pre, int64_t) { start[r] = pre; };
-      exclusive_scan<int64_t>(load, store, nullptr, R, w.scan_sums, n_isect, s);
       src.start = w.tile_start;
       src.cnt = w.tile_cnt;
     }
@@ -726,13 +745,22 @@ extern "C" tgs_status tgs_bin_tiles(const tgs_projected* proj, int64_t n, const 
     src.start = w.tile_start;
     src.cnt = w.tile_cnt;
   }
+  const bool scan_in_scatter = shared_path && !presort;
   if (capacity == 0) {
+    if (scan_in_scatter) {  // the pair count still comes from the totals
+      const int32_t* cnt = w.tile_cnt;
+      int64_t* start = w.tile_start;
+      auto load = [=] __device__(int64_t r) -> int64_t { return cnt[r]; };
+      auto store = [=] __device__(int64_t r, int64_t pre, int64_t) { start[r] = pre; };
+      exclusive_scan<int64_t>(load, store, nullptr, R, w.scan_sums, n_isect, s);
+    }
     cudaMemsetAsync(tile_ranges, 0, sizeof(int2) * (size_t)R, s);
     return check_launch();
   }
   if (shared_path) {
     k_hist_scatter<<<G, kHistThreads, smem, s>>>(xy, proj->radius, proj->depth, order, n_vis, n, geo, tile_rank,
-                                                 w.table, presort ? nullptr : w.tile_start, w.keys, capacity);
+                                                 w.table, presort ? nullptr : w.tile_start,
+                                                 scan_in_scatter ? w.tile_cnt : nullptr, n_isect, w.keys, capacity);
   } else {
     k_scatter_pairs<<<(int)((n + 255) / 256), 256, 0, s>>>(xy, proj->radius, proj->depth, n, geo, tile_rank,
                                                            w.tile_start, w.tile_fill, w.keys, capacity);
