@@ -769,8 +769,8 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_train_tc(
       lsum += 0.5 * (double)e * (double)e * (double)inv;
       b3 += d;
     }
-    // dH2 = [h2 > 0] d w3 (bf16): the A tile of dH1 (over the H1 tile, which layer 2
-    // has read) and dH2^T; dW3 partials d h2
+    // dH2 = [h2 > 0] d w3 (bf16): its row tile, the A operand of dH1 and of dW2;
+    // dW3 partials d h2
 #pragma unroll
     for (int q8 = 0; q8 < 8; ++q8) {
       uint32_t pk[4];
@@ -799,7 +799,7 @@ __global__ void __launch_bounds__(kBwThreads, 1) k_mlp_train_tc(
       failed = pending = true;
       break;
     }
-    // dh1 = bf16([h1 > 0] D), transposed into the A tile of dW1 (over the X tile, which layer 1 has read)
+    // dh1 = bf16([h1 > 0] D): the row tile of dW1's A
 #pragma unroll 1
     for (int c0 = 0; c0 < 64; c0 += 32) {
       float v[32];
