@@ -184,6 +184,13 @@ def test_bin_tiles_edge_cases(B, orc):
     want = orc.bin_tiles(pr["xy"], pr["radius"], pr["depth"], W, H)[1]
     out = bin_dev(B, projected_dev(pr), 500, cam, None, 256, capacity=10)
     assert int(out["n_isect"].item()) == len(want)
+    # capacity 0 (the pair-count query): the count, and every range cleared
+    ws = torch.empty(B.bin_tiles_workspace_size(500, 0, 256), dtype=torch.uint8, device="cuda")
+    ranges = torch.full((256, 2), -1, dtype=torch.int32, device="cuda")
+    n_isect = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    B.bin_tiles(projected_dev(pr), 500, cam, None, 256, ws, 0, None, None, ranges, n_isect)
+    assert int(n_isect.item()) == len(want)
+    assert int(ranges.abs().sum().item()) == 0
     torch.cuda.synchronize()
 
 
