@@ -470,26 +470,26 @@ def views_bench(device, peaks, flush, reps: int = 5) -> dict:
             "note": "Sec. 3.4 view draw of the multi-view step; not in the timed single-view step"}
 
 
-def e2e_replays(tr, target_host, steps):
+def e2e_replays(tr, loss_host, steps):
     """Public-API step with the view's target copied in from pinned host memory
     and the loss read back, every step.  The trainer was captured with
-    target_host: each replayed step copies the target in itself, beside the
-    kernels that do not read it (the loss waits for the copy)."""
+    target_host and loss_host: each replayed step copies the target in itself,
+    beside the kernels that do not read it (the loss waits for the copy), and
+    its loss out to loss_host, beside the backward and update."""
     import torch
-    loss_host = torch.zeros(1, dtype=torch.float64, pin_memory=True)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for _ in range(4):  # warm-up: the first replays of these graphs also upload them
         tr.replay(with_copy=True)
-        loss_host.copy_(tr.loss, non_blocking=True)
     torch.cuda.synchronize()
     a.record()
     for _ in range(steps):
         tr.replay(with_copy=True)
-        loss_host.copy_(tr.loss, non_blocking=True)
     b.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(b)
-    return steps / (ms * 1e-3), tr.target.numel() * 4, 8
+    if not math.isfinite(float(loss_host[0])):
+        raise RuntimeError("end-to-end steps read back a non-finite loss")
+    return steps / (ms * 1e-3), tr.target.numel() * 4, loss_host.numel() * loss_host.element_size()
 
 
 class OracleStep:
@@ -611,9 +611,11 @@ def run_ours(args):
     dense = None if args.no_dense else make_trainer(g_np, cam, target, True, 1.0, 1.0, device)
     # each replay makes the next iteration's selection beside its own backward;
     # the end-to-end steps also copy the target in from pinned host memory,
-    # beside the projection, binning and render
+    # beside the projection, binning and render, and copy the loss out beside
+    # the backward
     tgt_host = target.detach().cpu().pin_memory()
-    sampled.capture(overlap=True, target_host=tgt_host)
+    loss_host = torch.zeros(1, dtype=torch.float64, pin_memory=True)
+    sampled.capture(overlap=True, target_host=tgt_host, loss_host=loss_host)
     if dense is not None:
         dense.capture(overlap=True)
     for _ in range(args.warmup):
@@ -683,7 +685,7 @@ def run_ours(args):
                         "stage_ms": st_d}
         res["speedup_vs_dense"] = mean_d / mean_s
     # end to end through the public API: target in from pinned host memory, loss out
-    e2e_v, h2d, d2h = e2e_replays(sampled, tgt_host, args.steps)
+    e2e_v, h2d, d2h = e2e_replays(sampled, loss_host, args.steps)
     res["e2e"] = {"value": e2e_v * world, "unit": "iters/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
     res["mlp"] = mlp_bench(device, peaks)
     if not args.no_batched:

@@ -290,7 +290,7 @@ class Trainer:
         for k, v in sel.items():
             setattr(self, k, v)
 
-    def step_overlapped(self, nxt: dict, target_host=None):
+    def step_overlapped(self, nxt: dict, target_host=None, loss_host=None):
         """One iteration on the selection already made for it, and the next
         iteration's selection (Alg. 1 step 3) into the buffers nxt.  The next
         selection needs only the error and age maps the loss has just written
@@ -298,7 +298,8 @@ class Trainer:
         backward and the update, which touch neither.  target_host (pinned
         host memory): the view's target is first copied in on a third stream,
         beside the projection, binning and render, which do not read it; the
-        loss waits for it."""
+        loss waits for it.  loss_host (pinned host memory, one float64): the
+        loss is copied out on that stream too, beside the backward and update."""
         main = torch.cuda.current_stream()
         if target_host is not None:
             self._copy.wait_stream(main)
@@ -313,6 +314,10 @@ class Trainer:
         if target_host is not None:
             main.wait_stream(self._copy)
         self.loss_and_maps()
+        if loss_host is not None:
+            self._copy.wait_stream(main)
+            with torch.cuda.stream(self._copy):
+                loss_host.copy_(self.loss, non_blocking=True)
         self._side.wait_stream(main)
         cur = self._selection()
         with torch.cuda.stream(self._side):
@@ -330,8 +335,10 @@ class Trainer:
             self.update()
         B.advance_counters(None, self.step_dev)
         main.wait_stream(self._side)
+        if loss_host is not None:
+            main.wait_stream(self._copy)
 
-    def capture(self, overlap: bool = False, target_host=None):
+    def capture(self, overlap: bool = False, target_host=None, loss_host=None):
         """Capture one step in a CUDA graph (after a warm-up step).  With
         overlap, two graphs that alternate between two sets of selection
         buffers: each runs its iteration on one set and makes the next
@@ -340,7 +347,9 @@ class Trainer:
         those of the plain step: the same selections, from the same maps and
         counters.  With overlap and target_host (a pinned host copy of the
         target), a second pair of graphs whose steps also copy the target in
-        from the host (``replay(with_copy=True)``)."""
+        from the host (``replay(with_copy=True)``); with loss_host too (pinned,
+        one float64), those steps also copy their loss out to it, so that a
+        replay leaves its loss in host memory once the device is done with it."""
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
@@ -362,17 +371,17 @@ class Trainer:
         self._select()                                  # the first replayed iteration's selection, in set 0
         torch.cuda.synchronize()
 
-        def pair(host):
+        def pair(host, out_host):
             out = []
             for k in range(2):
                 self._use_selection(sets[k])
                 g = torch.cuda.CUDAGraph(keep_graph=True)
                 with torch.cuda.graph(g):
-                    self.step_overlapped(sets[1 - k], host)
+                    self.step_overlapped(sets[1 - k], host, out_host)
                 out.append(g)
             return out
-        self.graphs = pair(None)
-        self.graphs_copy = pair(target_host) if target_host is not None else None
+        self.graphs = pair(None, None)
+        self.graphs_copy = pair(target_host, loss_host) if target_host is not None else None
         self.kernels_per_step = B.graph_count_kernels(self.graphs[0])
         for g in self.graphs + (self.graphs_copy or []):
             g.instantiate()

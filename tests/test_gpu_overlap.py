@@ -86,21 +86,26 @@ def test_overlapped_training_follows_the_plain_step(B):
 
 
 def test_step_that_copies_its_target_in(B):
-    """capture(overlap=True, target_host=...): each replayed step copies the
-    target in from pinned host memory on its own stream (the loss waits for
-    it).  With the device target cleared first, training must follow the step
-    whose target is already on the device."""
+    """capture(overlap=True, target_host=..., loss_host=...): each replayed
+    step copies the target in from pinned host memory on its own stream (the
+    loss waits for it) and its loss out to pinned host memory.  With the
+    device target cleared first, training must follow the step whose target
+    is already on the device, and every step's loss must reach the host."""
     runs = []
     for copy in (False, True):
         tr, _ = _trainer(seed=7)
         host = tr.target.detach().cpu().pin_memory()
-        tr.capture(overlap=True, target_host=host if copy else None)
+        loss_host = torch.full((1,), -1.0, dtype=torch.float64).pin_memory()
+        tr.capture(overlap=True, target_host=host if copy else None, loss_host=loss_host if copy else None)
         if copy:
             tr.target.zero_()
         ls = []
         for _ in range(12):
             tr.replay(with_copy=copy)
             ls.append(tr.loss.clone())
+            if copy:
+                torch.cuda.synchronize()
+                assert float(loss_host[0]) == float(ls[-1].item())  # this step's loss, in host memory
         torch.cuda.synchronize()
         runs.append([float(x.item()) for x in ls])
         if copy:
